@@ -1,0 +1,760 @@
+/*
+ * imloc_oracle.c -- plain FP64 CPU oracle of the ImLoc localization hot path
+ * (lift + LO-RANSAC PnP, ImLoc Sec. 3.3).
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the CPU
+ * baseline leg of the benchmark, never by the product path.  Written for
+ * reading, not speed: every step follows the definition in the order the
+ * paper states it, in double precision, one query on one thread.  Decisions
+ * that the paper leaves open are the readings listed in the design notes
+ * (pixel centres at +0.5, z-depth, reject-on-invalid-tap, deterministic
+ * stride subsampling, Philox counter layout, round-level LO trigger, LO and
+ * Cauchy refinement schedules).
+ */
+#include "imloc_oracle.h"
+
+#include <complex.h>
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ======================================================================== */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies, with a   */
+/* Weyl-sequence key schedule.                                                */
+/* ======================================================================== */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t mult0 = 0xD2511F53u, mult1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t c[4] = {ctr[0], ctr[1], ctr[2], ctr[3]};
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += weyl0;
+            k1 += weyl1;
+        }
+        uint64_t p0 = (uint64_t)mult0 * c[0];
+        uint64_t p1 = (uint64_t)mult1 * c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        uint32_t n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+    }
+    out[0] = c[0]; out[1] = c[1]; out[2] = c[2]; out[3] = c[3];
+}
+
+/* ======================================================================== */
+/* Lift (Sec. 3.3, "Query Time Matching and 2D-3D Lifting"): keep a match    */
+/* whose confidence exceeds 0.05 and whose depth is valid; query->database   */
+/* matches take the bilinear depth at the subpixel database position,        */
+/* database->query matches look the depth up; back-project through the      */
+/* database intrinsics and pose into the world.                              */
+/* ======================================================================== */
+static int depth_ok(float d) { return isfinite(d) && d > 0.0f; }
+
+int64_t orc_lift(const orc_view* views, int64_t n_views,
+                 const float* q_u, const float* q_v, const float* db_u, const float* db_v,
+                 const float* conf, const int64_t* seg_off, const int32_t* seg_view,
+                 const int32_t* seg_dir, int64_t n_seg, float conf_min,
+                 double* out_x, double* out_y, double* out_X, double* out_w, int64_t* out_src)
+{
+    int64_t n_out = 0;
+    for (int64_t s = 0; s < n_seg; ++s) {
+        if (seg_view[s] < 0 || seg_view[s] >= n_views) continue;
+        const orc_view* v = &views[seg_view[s]];
+        for (int64_t i = seg_off[s]; i < seg_off[s + 1]; ++i) {
+            /* the threshold decision is taken in the precision of the input (float) */
+            if (!(conf[i] > conf_min)) continue;
+            double u = db_u[i], vv = db_v[i];
+            if (!isfinite(u) || !isfinite(vv)) continue;
+            double d;
+            if (seg_dir[s] == 0) {
+                /* bilinear between the four surrounding pixel centres */
+                double a = u - 0.5, b = vv - 0.5;
+                double fa = floor(a), fb = floor(b);
+                if (fa < 0.0 || fa + 1.0 > (double)(v->width - 1)) continue;
+                if (fb < 0.0 || fb + 1.0 > (double)(v->height - 1)) continue;
+                int64_t i0 = (int64_t)fa, j0 = (int64_t)fb;
+                float d00 = v->depth[j0 * v->pitch + i0];
+                float d01 = v->depth[j0 * v->pitch + i0 + 1];
+                float d10 = v->depth[(j0 + 1) * v->pitch + i0];
+                float d11 = v->depth[(j0 + 1) * v->pitch + i0 + 1];
+                if (!depth_ok(d00) || !depth_ok(d01) || !depth_ok(d10) || !depth_ok(d11)) continue;
+                double al = a - fa, be = b - fb;
+                d = (1.0 - be) * ((1.0 - al) * d00 + al * d01) + be * ((1.0 - al) * d10 + al * d11);
+            } else {
+                double fa = floor(u), fb = floor(vv);
+                if (fa < 0.0 || fa > (double)(v->width - 1)) continue;
+                if (fb < 0.0 || fb > (double)(v->height - 1)) continue;
+                float dd = v->depth[(int64_t)fb * v->pitch + (int64_t)fa];
+                if (!depth_ok(dd)) continue;
+                d = dd;
+            }
+            /* z-depth: the camera-frame point is d * K^-1 [u, v, 1]^T */
+            double Xc[3] = {d * (u - v->cx) / v->fx, d * (vv - v->cy) / v->fy, d};
+            double D[3] = {Xc[0] - v->t[0], Xc[1] - v->t[1], Xc[2] - v->t[2]};
+            /* X_w = R^T (X_c - t) */
+            for (int r = 0; r < 3; ++r)
+                out_X[3 * n_out + r] = v->R[0 * 3 + r] * D[0] + v->R[1 * 3 + r] * D[1] + v->R[2 * 3 + r] * D[2];
+            out_x[n_out] = q_u[i];
+            out_y[n_out] = q_v[i];
+            out_w[n_out] = conf[i];
+            out_src[n_out] = i;
+            ++n_out;
+        }
+    }
+    return n_out;
+}
+
+/* ======================================================================== */
+/* Uniform subsampling to at most m scoring correspondences (Sec. 3.3):      */
+/* deterministic stride idx_k = floor(k n / m).                              */
+/* ======================================================================== */
+void orc_subsample(int64_t n, int64_t m, int64_t* idx)
+{
+    for (int64_t k = 0; k < m; ++k) idx[k] = (int64_t)(((__int128)k * n) / m);
+}
+
+/* ======================================================================== */
+/* Minimal sample: key = seed, counter = (sample, query, attempt, 0); the    */
+/* first three outputs map to [0,m) by the high word of r*m.                 */
+/* ======================================================================== */
+int orc_sample(uint64_t seed, uint32_t query_id, uint32_t sample_id, int64_t m, int64_t out[3])
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (uint32_t attempt = 0; attempt < 16; ++attempt) {
+        uint32_t ctr[4] = {sample_id, query_id, attempt, 0u};
+        uint32_t r[4];
+        orc_philox4x32_10(ctr, key, r);
+        for (int k = 0; k < 3; ++k) out[k] = (int64_t)(((uint64_t)r[k] * (uint64_t)m) >> 32);
+        if (out[0] != out[1] && out[0] != out[2] && out[1] != out[2]) return (int)attempt;
+    }
+    return -1;
+}
+
+/* ======================================================================== */
+/* P3P.  Independent formulation from the GPU path: Grunert's substitution   */
+/* lambda2 = u lambda1, lambda3 = v lambda1 turns the three distance         */
+/* equations into two conics in (u, v); their resultant in u is a quartic in */
+/* v whose real roots are found as polynomial roots (Durand-Kerner + Newton  */
+/* polish).  The pose follows from the three camera-frame points by Horn's   */
+/* closed-form absolute orientation (unit quaternion, 4x4 eigenvector).      */
+/* ======================================================================== */
+static void poly_mul(const double* a, int da, const double* b, int db, double* out)
+{
+    for (int k = 0; k <= da + db; ++k) out[k] = 0.0;
+    for (int i = 0; i <= da; ++i)
+        for (int j = 0; j <= db; ++j) out[i + j] += a[i] * b[j];
+}
+
+static double poly_eval(const double* c, int deg, double x)
+{
+    double acc = 0.0;
+    for (int k = deg; k >= 0; --k) acc = acc * x + c[k];
+    return acc;
+}
+
+static double poly_deriv_eval(const double* c, int deg, double x)
+{
+    double acc = 0.0;
+    for (int k = deg; k >= 1; --k) acc = acc * x + k * c[k];
+    return acc;
+}
+
+/* real roots of sum_k c[k] x^k (deg <= 4); returns the count */
+static int poly_real_roots(const double* c_in, int deg, double* roots)
+{
+    double c[5];
+    double cmax = 0.0;
+    for (int k = 0; k <= deg; ++k) { c[k] = c_in[k]; cmax = fmax(cmax, fabs(c[k])); }
+    if (cmax == 0.0) return 0;
+    while (deg > 0 && fabs(c[deg]) <= 1e-14 * cmax) --deg;
+    if (deg == 0) return 0;
+    if (deg == 1) { roots[0] = -c[0] / c[1]; return 1; }
+    double complex z[4];
+    double a[5];
+    for (int k = 0; k <= deg; ++k) a[k] = c[k] / c[deg];
+    double bound = 1.0;
+    for (int k = 0; k < deg; ++k) bound = fmax(bound, 1.0 + fabs(a[k]));
+    double complex seed = 0.4 + 0.9 * I;
+    double complex p = 1.0;
+    for (int k = 0; k < deg; ++k) { p *= seed; z[k] = p * (0.5 * bound); }
+    for (int it = 0; it < 2000; ++it) {
+        double change = 0.0;
+        for (int k = 0; k < deg; ++k) {
+            double complex num = 0.0;
+            for (int j = deg; j >= 0; --j) num = num * z[k] + a[j];
+            double complex den = 1.0;
+            for (int j = 0; j < deg; ++j)
+                if (j != k) den *= (z[k] - z[j]);
+            if (cabs(den) == 0.0) den = 1e-300;
+            double complex dz = num / den;
+            z[k] -= dz;
+            change = fmax(change, cabs(dz) / (1.0 + cabs(z[k])));
+        }
+        if (change < 1e-16) break;
+    }
+    int nr = 0;
+    for (int k = 0; k < deg; ++k) {
+        if (fabs(cimag(z[k])) > 1e-6 * (1.0 + cabs(z[k]))) continue;
+        double x = creal(z[k]);
+        for (int it = 0; it < 8; ++it) {
+            double d = poly_deriv_eval(c, deg, x);
+            if (d == 0.0) break;
+            double step = poly_eval(c, deg, x) / d;
+            x -= step;
+            if (fabs(step) <= 1e-17 * (1.0 + fabs(x))) break;
+        }
+        int dup = 0;
+        for (int j = 0; j < nr; ++j)
+            if (fabs(roots[j] - x) <= 1e-10 * (1.0 + fabs(x))) dup = 1;
+        if (!dup) roots[nr++] = x;
+    }
+    return nr;
+}
+
+/* eigenvector of the largest eigenvalue of a symmetric 4x4 (cyclic Jacobi) */
+static void sym4_top_eigvec(const double Ain[16], double v_out[4])
+{
+    double A[4][4], V[4][4];
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) { A[i][j] = Ain[4 * i + j]; V[i][j] = (i == j) ? 1.0 : 0.0; }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                tot += A[i][j] * A[i][j];
+                if (i != j) off += A[i][j] * A[i][j];
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < 3; ++p)
+            for (int q = p + 1; q < 4; ++q) {
+                if (A[p][q] == 0.0) continue;
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double cs = 1.0 / sqrt(tt * tt + 1.0), sn = tt * cs;
+                for (int k = 0; k < 4; ++k) { /* A <- A J */
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = cs * akp - sn * akq;
+                    A[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < 4; ++k) { /* A <- J^T A */
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = cs * apk - sn * aqk;
+                    A[q][k] = sn * apk + cs * aqk;
+                }
+                for (int k = 0; k < 4; ++k) {
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = cs * vkp - sn * vkq;
+                    V[k][q] = sn * vkp + cs * vkq;
+                }
+            }
+    }
+    int best = 0;
+    for (int i = 1; i < 4; ++i)
+        if (A[i][i] > A[best][best]) best = i;
+    for (int k = 0; k < 4; ++k) v_out[k] = V[k][best];
+}
+
+/* Horn (1987): rotation R and translation t with C_i = R X_i + t */
+static void horn_absolute_orientation(const double Xw[9], const double Xc[9], double R[9], double t[3])
+{
+    double mw[3] = {0, 0, 0}, mc[3] = {0, 0, 0};
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) { mw[a] += Xw[3 * i + a] / 3.0; mc[a] += Xc[3 * i + a] / 3.0; }
+    double S[3][3] = {{0}};
+    for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) S[a][b] += (Xw[3 * i + a] - mw[a]) * (Xc[3 * i + b] - mc[b]);
+    double Sxx = S[0][0], Sxy = S[0][1], Sxz = S[0][2];
+    double Syx = S[1][0], Syy = S[1][1], Syz = S[1][2];
+    double Szx = S[2][0], Szy = S[2][1], Szz = S[2][2];
+    double N[16] = {
+        Sxx + Syy + Szz, Syz - Szy,        Szx - Sxz,        Sxy - Syx,
+        Syz - Szy,       Sxx - Syy - Szz,  Sxy + Syx,        Szx + Sxz,
+        Szx - Sxz,       Sxy + Syx,        -Sxx + Syy - Szz, Syz + Szy,
+        Sxy - Syx,       Szx + Sxz,        Syz + Szy,        -Sxx - Syy + Szz};
+    double q[4];
+    sym4_top_eigvec(N, q);
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    double nq = sqrt(w * w + x * x + y * y + z * z);
+    w /= nq; x /= nq; y /= nq; z /= nq;
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+    for (int a = 0; a < 3; ++a) t[a] = mc[a] - (R[3 * a] * mw[0] + R[3 * a + 1] * mw[1] + R[3 * a + 2] * mw[2]);
+}
+
+/* residuals of the three distance equations lambda_i^2 + lambda_j^2 - 2 b_ij lambda_i lambda_j = a_ij */
+static void p3p_residual(const double L[3], const double a[3], const double b[3], double f[3])
+{
+    f[0] = L[0] * L[0] + L[1] * L[1] - 2 * b[0] * L[0] * L[1] - a[0];
+    f[1] = L[0] * L[0] + L[2] * L[2] - 2 * b[1] * L[0] * L[2] - a[1];
+    f[2] = L[1] * L[1] + L[2] * L[2] - 2 * b[2] * L[1] * L[2] - a[2];
+}
+
+static int solve3(double A[3][3], const double b[3], double x[3])
+{
+    double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+               - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+               + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (det == 0.0 || !isfinite(det)) return 0;
+    for (int c = 0; c < 3; ++c) {
+        double M[3][3];
+        memcpy(M, A, sizeof(M));
+        for (int r = 0; r < 3; ++r) M[r][c] = b[r];
+        x[c] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+              - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+              + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+    }
+    return 1;
+}
+
+int orc_p3p(const double y[9], const double X[9], double R_out[36], double t_out[12], double lambda_out[12])
+{
+    double a12 = 0, a13 = 0, a23 = 0;
+    for (int k = 0; k < 3; ++k) {
+        a12 += (X[k] - X[3 + k]) * (X[k] - X[3 + k]);
+        a13 += (X[k] - X[6 + k]) * (X[k] - X[6 + k]);
+        a23 += (X[3 + k] - X[6 + k]) * (X[3 + k] - X[6 + k]);
+    }
+    double b12 = y[0] * y[3] + y[1] * y[4] + y[2] * y[5];
+    double b13 = y[0] * y[6] + y[1] * y[7] + y[2] * y[8];
+    double b23 = y[3] * y[6] + y[4] * y[7] + y[5] * y[8];
+    if (!(a12 > 0) || !(a13 > 0) || !(a23 > 0)) return 0;
+
+    /* With lambda2 = u lambda1 and lambda3 = v lambda1 the ratios of the
+     * distance equations give two quadratics in u whose coefficients are
+     * polynomials in v:
+     *   P(u) = a13 (1 + u^2 - 2 b12 u) - a12 (1 + v^2 - 2 b13 v)
+     *   Q(u) = a23 (1 + u^2 - 2 b12 u) - a12 (u^2 + v^2 - 2 b23 u v)    */
+    double p2 = a13, p1 = -2.0 * a13 * b12;
+    double p0[3] = {a13 - a12, 2.0 * a12 * b13, -a12};
+    double q2 = a23 - a12;
+    double q1[2] = {-2.0 * a23 * b12, 2.0 * a12 * b23};
+    double q0[3] = {a23, 0.0, -a12};
+    /* Resultant of two quadratics: (p2 q0 - q2 p0)^2 - (p2 q1 - q2 p1)(p1 q0 - q1 p0) */
+    double A[3], Bv[2], C[4], A2[5], BC[5], res[5];
+    for (int k = 0; k < 3; ++k) A[k] = p2 * q0[k] - q2 * p0[k];
+    Bv[0] = p2 * q1[0] - q2 * p1;
+    Bv[1] = p2 * q1[1];
+    double q1p0[4];
+    poly_mul(q1, 1, p0, 2, q1p0);
+    for (int k = 0; k < 4; ++k) C[k] = (k < 3 ? p1 * q0[k] : 0.0) - q1p0[k];
+    poly_mul(A, 2, A, 2, A2);
+    poly_mul(Bv, 1, C, 3, BC);
+    for (int k = 0; k < 5; ++k) res[k] = A2[k] - BC[k];
+
+    double vr[4];
+    int nv = poly_real_roots(res, 4, vr);
+    double sol_L[4][3];
+    int ns = 0;
+    const double av[3] = {a12, a13, a23}, bv[3] = {b12, b13, b23};
+    for (int k = 0; k < nv; ++k) {
+        double v = vr[k];
+        double den = -(Bv[0] + Bv[1] * v); /* q2 p1 - p2 q1(v) */
+        double num = A[0] + A[1] * v + A[2] * v * v;
+        if (fabs(den) <= 1e-14 * (fabs(num) + 1e-300)) continue;
+        double u = num / den;
+        double s = 1.0 + v * v - 2.0 * b13 * v;
+        if (!(s > 0)) continue;
+        double L[3];
+        L[0] = sqrt(a13 / s);
+        L[1] = u * L[0];
+        L[2] = v * L[0];
+        /* Newton polish on the three distance equations */
+        for (int it = 0; it < 4; ++it) {
+            double f[3];
+            p3p_residual(L, av, bv, f);
+            double J[3][3] = {
+                {2 * L[0] - 2 * b12 * L[1], 2 * L[1] - 2 * b12 * L[0], 0},
+                {2 * L[0] - 2 * b13 * L[2], 0, 2 * L[2] - 2 * b13 * L[0]},
+                {0, 2 * L[1] - 2 * b23 * L[2], 2 * L[2] - 2 * b23 * L[1]}};
+            double dl[3];
+            if (!solve3(J, f, dl)) break;
+            for (int a = 0; a < 3; ++a) L[a] -= dl[a];
+        }
+        if (!(L[0] > 0 && L[1] > 0 && L[2] > 0)) continue;
+        double f[3];
+        p3p_residual(L, av, bv, f);
+        if (fabs(f[0]) > 1e-8 * a12 || fabs(f[1]) > 1e-8 * a13 || fabs(f[2]) > 1e-8 * a23) continue;
+        int dup = 0;
+        for (int j = 0; j < ns; ++j)
+            if (fabs(sol_L[j][0] - L[0]) <= 1e-9 * L[0] && fabs(sol_L[j][1] - L[1]) <= 1e-9 * L[1] &&
+                fabs(sol_L[j][2] - L[2]) <= 1e-9 * L[2])
+                dup = 1;
+        if (dup) continue;
+        memcpy(sol_L[ns++], L, sizeof(L));
+    }
+    /* canonical order: ascending depth of the first point */
+    for (int i = 1; i < ns; ++i)
+        for (int j = i; j > 0 && sol_L[j][0] < sol_L[j - 1][0]; --j) {
+            double tmp[3];
+            memcpy(tmp, sol_L[j], sizeof(tmp));
+            memcpy(sol_L[j], sol_L[j - 1], sizeof(tmp));
+            memcpy(sol_L[j - 1], tmp, sizeof(tmp));
+        }
+    for (int k = 0; k < ns; ++k) {
+        double Xc[9];
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 3; ++a) Xc[3 * i + a] = sol_L[k][i] * y[3 * i + a];
+        horn_absolute_orientation(X, Xc, &R_out[9 * k], &t_out[3 * k]);
+        if (lambda_out)
+            for (int i = 0; i < 3; ++i) lambda_out[3 * k + i] = sol_L[k][i];
+    }
+    return ns;
+}
+
+/* ======================================================================== */
+/* Scoring: confidence-weighted truncated squared reprojection error (MSAC). */
+/* A point behind the camera (Z <= 0) counts as an outlier.                  */
+/* ======================================================================== */
+static int project_residual(const orc_corr* c, int64_t i, const orc_cam* cam, const double R[9],
+                            const double t[3], double Xc[3], double r[2])
+{
+    const double* Xw = &c->X[3 * i];
+    for (int a = 0; a < 3; ++a) Xc[a] = R[3 * a] * Xw[0] + R[3 * a + 1] * Xw[1] + R[3 * a + 2] * Xw[2] + t[a];
+    if (!(Xc[2] > 0.0)) return 0;
+    r[0] = cam->fx * Xc[0] / Xc[2] + cam->cx - c->x[i];
+    r[1] = cam->fy * Xc[1] / Xc[2] + cam->cy - c->y[i];
+    return 1;
+}
+
+double orc_score(const orc_corr* c, const int64_t* idx, int64_t m, const orc_cam* cam,
+                 const double R[9], const double t[3], double tau, int64_t* inliers)
+{
+    double tau2 = tau * tau, s = 0.0;
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = idx ? idx[k] : k;
+        double Xc[3], r[2];
+        double r2 = tau2;
+        if (project_residual(c, i, cam, R, t, Xc, r)) {
+            r2 = r[0] * r[0] + r[1] * r[1];
+            if (r2 < tau2) ++cnt;
+        }
+        s += c->w[i] * (r2 < tau2 ? r2 : tau2);
+    }
+    if (inliers) *inliers = cnt;
+    return s;
+}
+
+/* ======================================================================== */
+/* Gauss-Newton on SE(3) with a left perturbation X_c' = Exp(w) X_c + v.     */
+/* ======================================================================== */
+static void jacobian(const double Xc[3], const orc_cam* cam, double J[2][6])
+{
+    double X = Xc[0], Y = Xc[1], Z = Xc[2];
+    double du[3] = {cam->fx / Z, 0.0, -cam->fx * X / (Z * Z)};
+    double dv[3] = {0.0, cam->fy / Z, -cam->fy * Y / (Z * Z)};
+    /* d X_c' / d w = -[X_c]_x */
+    double M[3][3] = {{0.0, Z, -Y}, {-Z, 0.0, X}, {Y, -X, 0.0}};
+    for (int k = 0; k < 3; ++k) {
+        J[0][k] = du[0] * M[0][k] + du[1] * M[1][k] + du[2] * M[2][k];
+        J[1][k] = dv[0] * M[0][k] + dv[1] * M[1][k] + dv[2] * M[2][k];
+        J[0][3 + k] = du[k];
+        J[1][3 + k] = dv[k];
+    }
+}
+
+static void so3_exp(const double w[3], double E[9])
+{
+    double th2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+    double th = sqrt(th2);
+    double A, B;
+    if (th < 1e-8) { A = 1.0 - th2 / 6.0; B = 0.5 - th2 / 24.0; }
+    else { A = sin(th) / th; B = (1.0 - cos(th)) / th2; }
+    double K[9] = {0, -w[2], w[1], w[2], 0, -w[0], -w[1], w[0], 0};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double K2 = 0;
+            for (int k = 0; k < 3; ++k) K2 += K[3 * i + k] * K[3 * k + j];
+            E[3 * i + j] = (i == j ? 1.0 : 0.0) + A * K[3 * i + j] + B * K2;
+        }
+}
+
+static void apply_update(const double d[6], const double R[9], const double t[3], double Rn[9], double tn[3])
+{
+    double E[9];
+    so3_exp(d, E);
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j)
+            Rn[3 * i + j] = E[3 * i] * R[j] + E[3 * i + 1] * R[3 + j] + E[3 * i + 2] * R[6 + j];
+        tn[i] = E[3 * i] * t[0] + E[3 * i + 1] * t[1] + E[3 * i + 2] * t[2] + d[3 + i];
+    }
+}
+
+static int cholesky_solve6(const double H[36], const double g[6], double x[6])
+{
+    double L[36] = {0};
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = H[6 * i + j];
+            for (int k = 0; k < j; ++k) s -= L[6 * i + k] * L[6 * j + k];
+            if (i == j) {
+                if (!(s > 0.0)) return 0;
+                L[6 * i + i] = sqrt(s);
+            } else {
+                L[6 * i + j] = s / L[6 * j + j];
+            }
+        }
+    double z[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = g[i];
+        for (int k = 0; k < i; ++k) s -= L[6 * i + k] * z[k];
+        z[i] = s / L[6 * i + i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = z[i];
+        for (int k = i + 1; k < 6; ++k) s -= L[6 * k + i] * x[k];
+        x[i] = s / L[6 * i + i];
+    }
+    return 1;
+}
+
+enum { LOSS_TRUNCATED = 0, LOSS_CAUCHY = 1 };
+
+static double robust_cost(const orc_corr* c, const int64_t* idx, int64_t m, const orc_cam* cam,
+                          int loss, double tau, double cs, const double R[9], const double t[3])
+{
+    double tau2 = tau * tau, cs2 = cs * cs, s = 0.0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = idx ? idx[k] : k;
+        double Xc[3], r[2], r2 = tau2;
+        if (project_residual(c, i, cam, R, t, Xc, r)) r2 = r[0] * r[0] + r[1] * r[1];
+        if (loss == LOSS_TRUNCATED) s += c->w[i] * (r2 < tau2 ? r2 : tau2);
+        else s += c->w[i] * cs2 * log1p(r2 / cs2);
+    }
+    return s;
+}
+
+/* Returns the number of accepted steps; R, t updated in place; *cost_io holds the cost. */
+static int gauss_newton(const orc_corr* c, const int64_t* idx, int64_t m, const orc_cam* cam, int loss,
+                        double tau, double cs, int64_t iters, double R[9], double t[3], double* cost_io)
+{
+    double tau2 = tau * tau, cs2 = cs * cs;
+    double cost = robust_cost(c, idx, m, cam, loss, tau, cs, R, t);
+    int accepted_steps = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        double H[36] = {0}, g[6] = {0};
+        int64_t used = 0;
+        for (int64_t k = 0; k < m; ++k) {
+            int64_t i = idx ? idx[k] : k;
+            double Xc[3], r[2];
+            if (!project_residual(c, i, cam, R, t, Xc, r)) continue;
+            double r2 = r[0] * r[0] + r[1] * r[1];
+            double wt;
+            if (loss == LOSS_TRUNCATED) {
+                if (!(r2 < tau2)) continue; /* outliers sit on the flat part of the loss */
+                wt = c->w[i];
+            } else {
+                wt = c->w[i] / (1.0 + r2 / cs2); /* IRLS weight of the Cauchy loss */
+            }
+            double J[2][6];
+            jacobian(Xc, cam, J);
+            for (int a = 0; a < 6; ++a) {
+                g[a] += wt * (J[0][a] * r[0] + J[1][a] * r[1]);
+                for (int b = 0; b < 6; ++b) H[6 * a + b] += wt * (J[0][a] * J[0][b] + J[1][a] * J[1][b]);
+            }
+            ++used;
+        }
+        if (used < 3) break;
+        double mu = 0.0;
+        int ok = 0;
+        double d[6], Rn[9], tn[3], cn = cost;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            double Hd[36], mg[6];
+            memcpy(Hd, H, sizeof(Hd));
+            for (int a = 0; a < 6; ++a) { Hd[7 * a] += mu * H[7 * a]; mg[a] = -g[a]; }
+            if (cholesky_solve6(Hd, mg, d)) {
+                apply_update(d, R, t, Rn, tn);
+                cn = robust_cost(c, idx, m, cam, loss, tau, cs, Rn, tn);
+                if (cn < cost) { ok = 1; break; }
+            }
+            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
+        }
+        if (!ok) break;
+        memcpy(R, Rn, sizeof(Rn));
+        memcpy(t, tn, sizeof(tn));
+        cost = cn;
+        ++accepted_steps;
+        double dn = 0;
+        for (int a = 0; a < 6; ++a) dn += d[a] * d[a];
+        if (sqrt(dn) < 1e-10) break;
+    }
+    *cost_io = cost;
+    return accepted_steps;
+}
+
+double orc_lo(const orc_corr* c, const int64_t* idx, int64_t m, const orc_cam* cam, double tau,
+              int64_t iters, double R[9], double t[3])
+{
+    double cost;
+    gauss_newton(c, idx, m, cam, LOSS_TRUNCATED, tau, 1.0, iters, R, t, &cost);
+    return cost;
+}
+
+int orc_refine(const orc_corr* c, const int64_t* sel, int64_t n_sel, const orc_cam* cam, double cauchy_c,
+               double tau, int64_t iters, double R[9], double t[3])
+{
+    double cost;
+    return gauss_newton(c, sel, n_sel, cam, LOSS_CAUCHY, tau, cauchy_c, iters, R, t, &cost);
+}
+
+/* ======================================================================== */
+/* Adaptive stop: the chance that none of k minimal sets of 3 is all-inlier  */
+/* is (1 - eps^3)^k; stop once it falls below p_miss.                        */
+/* ======================================================================== */
+double orc_needed_iters(double eps, double p_miss)
+{
+    double e3 = eps * eps * eps;
+    if (e3 >= 1.0) return 0.0;
+    if (e3 <= 0.0) return INFINITY;
+    return log(p_miss) / log(1.0 - e3);
+}
+
+/* ======================================================================== */
+/* The LO-RANSAC loop (Sec. 3.3): rounds of `batch` minimal sets; score      */
+/* every P3P pose of the round on the subset; if the round's best beats the  */
+/* global best, run LO on it; stop at max_iters or by the adaptive rule;     */
+/* refine on all inliers of the full set with the Cauchy loss.               */
+/* ======================================================================== */
+static void bearing(const orc_corr* c, int64_t i, const orc_cam* cam, double out[3])
+{
+    double b[3] = {(c->x[i] - cam->cx) / cam->fx, (c->y[i] - cam->cy) / cam->fy, 1.0};
+    double n = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    for (int a = 0; a < 3; ++a) out[a] = b[a] / n;
+}
+
+int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o, orc_result* res,
+                   uint8_t* inlier_mask, int64_t* round_best_id, double* round_best_score, int64_t max_rounds)
+{
+    memset(res, 0, sizeof(*res));
+    res->best_hyp = -1;
+    int64_t n = c->n;
+    if (n < 3) { res->status = -1; return -1; }
+    int64_t m = n < o->max_score_corr ? n : o->max_score_corr;
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    orc_subsample(n, m, idx);
+
+    int64_t total, batch;
+    int64_t (*triples)[3] = NULL;
+    if (o->enumerate_all) {
+        total = m * (m - 1) * (m - 2) / 6;
+        triples = malloc(sizeof(*triples) * (size_t)(total > 0 ? total : 1));
+        int64_t s = 0;
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t j = i + 1; j < m; ++j)
+                for (int64_t k = j + 1; k < m; ++k) { triples[s][0] = i; triples[s][1] = j; triples[s][2] = k; ++s; }
+        batch = total > 0 ? total : 1;
+    } else {
+        total = o->max_iters;
+        batch = o->batch;
+    }
+
+    double best_R[9], best_t[3], best_score = INFINITY;
+    int have_best = 0;
+    int64_t subset_inliers = 0, hyps = 0, rounds = 0, iters = 0;
+    for (int64_t r = 0;; ++r) {
+        int64_t s0 = r * batch, s1 = s0 + batch < total ? s0 + batch : total;
+        if (s0 >= total) break;
+        double rb_score = INFINITY, rb_R[9], rb_t[3];
+        int64_t rb_id = -1;
+        for (int64_t s = s0; s < s1; ++s) {
+            int64_t tri[3];
+            if (triples) memcpy(tri, triples[s], sizeof(tri));
+            else if (orc_sample(o->seed, o->query_id, (uint32_t)s, m, tri) < 0) continue;
+            double y[9], X[9];
+            for (int k = 0; k < 3; ++k) {
+                int64_t i = idx[tri[k]];
+                bearing(c, i, cam, &y[3 * k]);
+                for (int a = 0; a < 3; ++a) X[3 * k + a] = c->X[3 * i + a];
+            }
+            double Rs[36], ts[12];
+            int ns = orc_p3p(y, X, Rs, ts, NULL);
+            for (int k = 0; k < ns; ++k) {
+                double sc = orc_score(c, idx, m, cam, &Rs[9 * k], &ts[3 * k], o->tau, NULL);
+                ++hyps;
+                if (sc < rb_score) { /* ascending ids: a tie keeps the lower id */
+                    rb_score = sc;
+                    rb_id = 4 * s + k;
+                    memcpy(rb_R, &Rs[9 * k], sizeof(rb_R));
+                    memcpy(rb_t, &ts[3 * k], sizeof(rb_t));
+                }
+            }
+        }
+        if (r < max_rounds) {
+            if (round_best_id) round_best_id[r] = rb_id;
+            if (round_best_score) round_best_score[r] = rb_score;
+        }
+        if (rb_id >= 0 && rb_score < best_score) {
+            memcpy(best_R, rb_R, sizeof(rb_R));
+            memcpy(best_t, rb_t, sizeof(rb_t));
+            best_score = rb_score;
+            res->best_hyp = rb_id;
+            have_best = 1;
+            if (o->lo_enabled) {
+                double lR[9], lt[3];
+                memcpy(lR, best_R, sizeof(lR));
+                memcpy(lt, best_t, sizeof(lt));
+                double ls = orc_lo(c, idx, m, cam, o->tau, o->lo_iters, lR, lt);
+                res->lo_count++;
+                if (ls < best_score) {
+                    memcpy(best_R, lR, sizeof(lR));
+                    memcpy(best_t, lt, sizeof(lt));
+                    best_score = ls;
+                }
+            }
+            orc_score(c, idx, m, cam, best_R, best_t, o->tau, &subset_inliers);
+        }
+        iters = s1;
+        rounds = r + 1;
+        if (iters >= total) break;
+        if (o->p_miss > 0.0 && have_best &&
+            (double)iters >= orc_needed_iters((double)subset_inliers / (double)m, o->p_miss))
+            break;
+    }
+    free(triples);
+    res->iterations = iters;
+    res->rounds = rounds;
+    res->hypotheses = hyps;
+    if (!have_best) { free(idx); res->status = -1; return -1; }
+    memcpy(res->R_best, best_R, sizeof(best_R));
+    memcpy(res->t_best, best_t, sizeof(best_t));
+    res->score = best_score;
+    res->subset_inliers = subset_inliers;
+
+    double R[9], t[3];
+    memcpy(R, best_R, sizeof(R));
+    memcpy(t, best_t, sizeof(t));
+    if (o->final_enabled) {
+        int64_t* sel = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        int64_t ns = 0;
+        double tau2 = o->tau * o->tau;
+        for (int64_t i = 0; i < n; ++i) {
+            double Xc[3], rr[2];
+            if (project_residual(c, i, cam, R, t, Xc, rr) && rr[0] * rr[0] + rr[1] * rr[1] < tau2) sel[ns++] = i;
+        }
+        orc_refine(c, sel, ns, cam, o->cauchy_scale, o->tau, o->final_iters, R, t);
+        free(sel);
+    }
+    memcpy(res->R, R, sizeof(R));
+    memcpy(res->t, t, sizeof(t));
+    int64_t cnt = 0;
+    double tau2 = o->tau * o->tau;
+    for (int64_t i = 0; i < n; ++i) {
+        double Xc[3], rr[2];
+        int in = project_residual(c, i, cam, R, t, Xc, rr) && rr[0] * rr[0] + rr[1] * rr[1] < tau2;
+        if (inlier_mask) inlier_mask[i] = (uint8_t)in;
+        cnt += in;
+    }
+    res->num_inliers = cnt;
+    free(idx);
+    res->status = 0;
+    return 0;
+}

@@ -1,0 +1,304 @@
+"""Seeded synthetic workloads shaped like ImLoc's localization inputs.
+
+The paper evaluates on public benchmarks (Oxford Day & Night, LaMAR,
+Cambridge Landmarks, Aachen) with RoMa matches; none of that is available, so
+these generators stand in for them with the same shapes: K retrieved database
+views with float32 z-depth maps, thousands of dense matches per pair with a
+confidence, uneven inlier ratios and pixel noise (ImLoc Sec. 3.3, Sec. 4).
+
+This module only MAKES inputs (scene geometry, ground truth and noise).  It
+holds none of the method's arithmetic: no lifting, sampling, solving, scoring
+or refinement.  Both the CUDA path and the CPU oracle consume its output.
+
+Conventions: poses are cam_from_world (X_c = R X_w + t); pixel (i, j) is
+centred at (i + 0.5, j + 0.5); depth maps store z-depth, 0 where no surface
+lies within [1, 50] m.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+CONF_MIN = np.float32(0.05)
+
+
+def random_rotation(rng):
+    """Haar-uniform rotation from a normalised 4-D Gaussian quaternion."""
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def axis_angle(axis, angle):
+    axis = np.asarray(axis, dtype=np.float64)
+    axis = axis / np.linalg.norm(axis)
+    Kx = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    return np.eye(3) + math.sin(angle) * Kx + (1 - math.cos(angle)) * (Kx @ Kx)
+
+
+# ---------------------------------------------------------------------------
+# Direct 2D-3D correspondences (single-query and batched shapes)
+# ---------------------------------------------------------------------------
+def direct_query(rng, n, inlier_ratio, width, height, f, noise_px=1.0, depth_range=(2.0, 20.0),
+                 weights="ones"):
+    """Correspondences of one query with a known pose.
+
+    Inliers: a uniform pixel, a uniform depth in `depth_range`, back-projected
+    through the ground-truth pose; the observed pixel gets N(0, noise_px)
+    noise.  Outliers: the same 3D construction but the observed pixel is
+    uniform in the image.  Returns float32 arrays plus float64 ground truth.
+    """
+    cx, cy = width / 2.0, height / 2.0
+    R = random_rotation(rng)
+    t = rng.normal(size=3)
+    u = rng.uniform(0, width, n)
+    v = rng.uniform(0, height, n)
+    d = rng.uniform(depth_range[0], depth_range[1], n)
+    Xc = np.stack([(u - cx) / f * d, (v - cy) / f * d, d], axis=1)
+    Xw = (Xc - t) @ R  # R^T (X_c - t), row-wise
+    n_in = int(round(inlier_ratio * n))
+    inl = np.zeros(n, dtype=bool)
+    inl[rng.permutation(n)[:n_in]] = True
+    x = np.where(inl, u + rng.normal(0, noise_px, n), rng.uniform(0, width, n))
+    y = np.where(inl, v + rng.normal(0, noise_px, n), rng.uniform(0, height, n))
+    if weights == "ones":
+        w = np.ones(n)
+    else:
+        w = np.where(inl, rng.uniform(0.3, 1.0, n), rng.uniform(0.05, 1.0, n))
+    return dict(x=x.astype(np.float32), y=y.astype(np.float32), X=Xw.astype(np.float32),
+                w=w.astype(np.float32), K=(float(f), float(f), cx, cy), width=width, height=height,
+                R_gt=R, t_gt=t, inlier=inl)
+
+
+def config1(seed=0):
+    """Single query, plain LO-RANSAC PnP: 2,000 correspondences, 640x480,
+    f=500, principal point at the centre, R uniform, t ~ N(0, 1 m), depth
+    U[2, 20] m, 30% inliers with N(0, 1 px) noise, 1,000 hypotheses, 4 px."""
+    rng = np.random.default_rng(seed)
+    q = direct_query(rng, 2000, 0.30, 640, 480, 500.0, noise_px=1.0)
+    q.update(hypotheses=1000, tau=4.0)
+    return q
+
+
+def config3(seed=0, n_queries=256, n_range=(2000, 100000)):
+    """Batched: queries with N log-uniform in [2k, 100k], inlier ratio
+    U[5%, 70%], 4,096-16,384 hypotheses (multiples of 1,024), 1024x768, f=800."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for qi in range(n_queries):
+        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1])))))
+        ratio = rng.uniform(0.05, 0.70)
+        q = direct_query(rng, n, ratio, 1024, 768, 800.0, noise_px=1.0, depth_range=(2.0, 40.0), weights="conf")
+        q.update(hypotheses=int(rng.integers(4, 17)) * 1024, tau=4.0, query_id=qi)
+        out.append(q)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Piecewise-planar scene, database views with depth maps, dense matches
+# ---------------------------------------------------------------------------
+class PlanarScene:
+    """Disk-shaped planar patches plus one large backdrop, in world frame."""
+
+    def __init__(self, rng, R_q, t_q, K, width, height, n_planes=8):
+        fx, fy, cx, cy = K
+        self.planes = []  # (normal_w, offset_w, centre_w, radius)
+        for p in range(n_planes):
+            if p == 0:
+                ray = np.array([0.0, 0.0, 1.0])
+                depth0 = rng.uniform(35.0, 45.0)
+                tilt = rng.uniform(0, math.radians(20))
+                radius = depth0 * rng.uniform(0.7, 1.2)  # leaves some 'sky' (no depth) at the corners
+            else:
+                u = rng.uniform(-0.1 * width, 1.1 * width)
+                v = rng.uniform(-0.1 * height, 1.1 * height)
+                ray = np.array([(u - cx) / fx, (v - cy) / fy, 1.0])
+                depth0 = rng.uniform(3.0, 32.0)
+                tilt = rng.uniform(0, math.radians(55))
+                radius = rng.uniform(0.25, 0.7) * depth0
+            centre_c = depth0 * ray
+            n_c = -ray / np.linalg.norm(ray)
+            axis = np.cross(n_c, rng.normal(size=3))
+            n_c = axis_angle(axis, tilt) @ n_c
+            off_c = float(n_c @ centre_c)
+            n_w = R_q.T @ n_c
+            off_w = off_c - float(n_c @ t_q)
+            centre_w = R_q.T @ (centre_c - t_q)
+            self.planes.append((n_w, off_w, centre_w, radius))
+
+    def raycast(self, R, t, K, u, v):
+        """z-depth of the first surface hit along the rays through pixels
+        (u, v) of camera (R, t, K); 0 where nothing lies in [1, 50] m."""
+        fx, fy, cx, cy = K
+        u = np.asarray(u, dtype=np.float64)
+        v = np.asarray(v, dtype=np.float64)
+        rays = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones_like(u)], axis=-1)
+        dirs = rays @ R  # R^T r per ray: world direction with unit camera-z
+        C = -R.T @ t
+        best = np.full(u.shape, np.inf)
+        for n_w, off_w, centre_w, radius in self.planes:
+            den = dirs @ n_w
+            with np.errstate(divide="ignore", invalid="ignore"):
+                s = (off_w - n_w @ C) / den
+            hit = C + s[..., None] * dirs
+            inside = np.linalg.norm(hit - centre_w, axis=-1) < radius
+            ok = np.isfinite(s) & (s > 0) & inside & (s < best)
+            best = np.where(ok, s, best)
+        return np.where(np.isfinite(best) & (best >= 1.0) & (best <= 50.0), best, 0.0)
+
+    def depth_map(self, R, t, K, width, height):
+        jj, ii = np.meshgrid(np.arange(height) + 0.5, np.arange(width) + 0.5, indexing="ij")
+        return self.raycast(R, t, K, ii, jj).astype(np.float32)
+
+
+def _project(R, t, K, Xw):
+    fx, fy, cx, cy = K
+    Xc = Xw @ R.T + t
+    z = Xc[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return fx * Xc[:, 0] / z + cx, fy * Xc[:, 1] / z + cy, z
+
+
+def _backproject(R, t, K, u, v, d):
+    fx, fy, cx, cy = K
+    Xc = np.stack([(u - cx) / fx * d, (v - cy) / fy * d, d], axis=1)
+    return (Xc - t) @ R
+
+
+def _bilinear_taps_ok(depth, u, v):
+    """All four bilinear taps lie inside and carry a depth (generator-side check)."""
+    h, w = depth.shape
+    a = u - 0.5
+    b = v - 0.5
+    ok = (a >= 0) & (a < w - 1) & (b >= 0) & (b < h - 1)
+    i = np.clip(np.floor(a).astype(np.int64), 0, w - 2)
+    j = np.clip(np.floor(b).astype(np.int64), 0, h - 2)
+    taps = np.stack([depth[j, i], depth[j, i + 1], depth[j + 1, i], depth[j + 1, i + 1]])
+    return ok & np.all(taps > 0, axis=0)
+
+
+def localization_query(rng, n_views=10, matches_per_pair=5000, width=1024, height=768, f=800.0,
+                       pixel_noise=0.5, depth_noise=0.0, inlier_range=(0.10, 0.60), scene=None,
+                       max_rot_deg=15.0, max_shift_m=3.0):
+    """One query of the lift + RANSAC workload.
+
+    A query camera with a random pose looks at a piecewise-planar scene; each
+    of `n_views` database views is the query pose perturbed by <= 15 deg and
+    <= 3 m and stores a float32 z-depth map (optionally multiplied by
+    1 + N(0, depth_noise)).  Per pair, half of the matches run query->database
+    (subpixel database position) and half database->query (database pixel
+    centre); a fraction U[inlier_range] are true matches with N(0, pixel_noise)
+    noise on the query pixel, the rest are uniform.  Confidence: inliers
+    U[0.3, 1], outliers U[0, 1].
+    """
+    K = (f, f, width / 2.0, height / 2.0)
+    R_q = random_rotation(rng)
+    t_q = rng.normal(size=3)
+    if scene is None:
+        scene = PlanarScene(rng, R_q, t_q, K, width, height)
+    C_q = -R_q.T @ t_q
+    views = []
+    segs_q_u, segs_q_v, segs_db_u, segs_db_v, segs_conf = [], [], [], [], []
+    seg_off = [0]
+    seg_view, seg_dir = [], []
+    truth_inlier = []
+    for k in range(n_views):
+        dR = axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, max_rot_deg)))
+        R_d = dR @ R_q
+        dirn = rng.normal(size=3)
+        C_d = C_q + dirn / np.linalg.norm(dirn) * rng.uniform(0, max_shift_m)
+        t_d = -R_d @ C_d
+        depth_true = scene.depth_map(R_d, t_d, K, width, height)
+        depth = depth_true
+        if depth_noise > 0:
+            depth = (depth_true * (1.0 + rng.normal(0, depth_noise, depth_true.shape))).astype(np.float32)
+        views.append(dict(depth=depth, fx=K[0], fy=K[1], cx=K[2], cy=K[3], R=R_d, t=t_d))
+        ratio = rng.uniform(*inlier_range)
+        for direction in (0, 1):
+            n_pair = matches_per_pair // 2 if direction == 0 else matches_per_pair - matches_per_pair // 2
+            n_in = int(round(ratio * n_pair))
+            if direction == 0:
+                # query pixel -> 3D by the scene -> database subpixel
+                cu = rng.uniform(0, width, 6 * n_in + 64)
+                cv = rng.uniform(0, height, 6 * n_in + 64)
+                zq = scene.raycast(R_q, t_q, K, cu, cv)
+                Xw = _backproject(R_q, t_q, K, cu, cv, zq)
+                du, dv, dz = _project(R_d, t_d, K, Xw)
+                zd = scene.raycast(R_d, t_d, K, np.nan_to_num(du), np.nan_to_num(dv))
+                ok = (zq > 0) & (dz > 0) & np.isfinite(du) & np.isfinite(dv)
+                ok &= _bilinear_taps_ok(depth_true, np.nan_to_num(du), np.nan_to_num(dv))
+                ok &= np.abs(zd - dz) < 1e-3 * np.maximum(dz, 1e-9)
+                sel = np.nonzero(ok)[0][:n_in]
+                in_qu, in_qv, in_du, in_dv = cu[sel], cv[sel], du[sel], dv[sel]
+            else:
+                # database pixel centre -> depth -> 3D -> query subpixel
+                valid_pix = np.flatnonzero(depth_true.ravel() > 0)
+                pick = valid_pix[rng.integers(0, len(valid_pix), 6 * n_in + 64)] if len(valid_pix) else np.zeros(0, int)
+                pj, pi = np.divmod(pick, width)
+                du = pi + 0.5
+                dv = pj + 0.5
+                Xw = _backproject(R_d, t_d, K, du, dv, depth_true[pj, pi].astype(np.float64))
+                qu, qv, qz = _project(R_q, t_q, K, Xw)
+                ok = (qz > 0) & np.isfinite(qu) & (qu >= 0) & (qu < width) & (qv >= 0) & (qv < height)
+                zq = scene.raycast(R_q, t_q, K, np.nan_to_num(qu), np.nan_to_num(qv))
+                ok &= np.abs(zq - qz) < 1e-3 * np.maximum(qz, 1e-9)
+                sel = np.nonzero(ok)[0][:n_in]
+                in_qu, in_qv, in_du, in_dv = qu[sel], qv[sel], du[sel], dv[sel]
+            n_in_eff = len(sel)
+            n_out = n_pair - n_in_eff
+            in_qu = in_qu + rng.normal(0, pixel_noise, n_in_eff)
+            in_qv = in_qv + rng.normal(0, pixel_noise, n_in_eff)
+            out_qu = rng.uniform(0, width, n_out)
+            out_qv = rng.uniform(0, height, n_out)
+            if direction == 0:
+                out_du = rng.uniform(0, width, n_out)
+                out_dv = rng.uniform(0, height, n_out)
+            else:
+                out_du = rng.integers(0, width, n_out) + 0.5
+                out_dv = rng.integers(0, height, n_out) + 0.5
+            q_u = np.concatenate([in_qu, out_qu])
+            q_v = np.concatenate([in_qv, out_qv])
+            d_u = np.concatenate([in_du, out_du])
+            d_v = np.concatenate([in_dv, out_dv])
+            conf = np.concatenate([rng.uniform(0.3, 1.0, n_in_eff), rng.uniform(0.0, 1.0, n_out)])
+            truth = np.concatenate([np.ones(n_in_eff, bool), np.zeros(n_out, bool)])
+            perm = rng.permutation(n_pair)
+            segs_q_u.append(q_u[perm]); segs_q_v.append(q_v[perm])
+            segs_db_u.append(d_u[perm]); segs_db_v.append(d_v[perm])
+            segs_conf.append(conf[perm]); truth_inlier.append(truth[perm])
+            seg_off.append(seg_off[-1] + n_pair)
+            seg_view.append(k)
+            seg_dir.append(direction)
+    matches = dict(q_u=np.concatenate(segs_q_u).astype(np.float32), q_v=np.concatenate(segs_q_v).astype(np.float32),
+                   db_u=np.concatenate(segs_db_u).astype(np.float32), db_v=np.concatenate(segs_db_v).astype(np.float32),
+                   conf=np.concatenate(segs_conf).astype(np.float32), seg_off=np.array(seg_off, dtype=np.int64),
+                   seg_view=np.array(seg_view, dtype=np.int32), seg_dir=np.array(seg_dir, dtype=np.int32))
+    return dict(views=views, matches=matches, K=K, width=width, height=height, R_gt=R_q, t_gt=t_q,
+                truth_inlier=np.concatenate(truth_inlier), scene=scene)
+
+
+def config2(seed=0, **kw):
+    """Lift + RANSAC per query: 1024x768 query, 10 views with float32 depth
+    of an 8-plane scene (depth 1-50 m), 5,000 matches per pair (50k),
+    inlier ratio U[10%, 60%], pixel noise N(0, 0.5 px), 10,000 hypotheses."""
+    rng = np.random.default_rng(seed)
+    q = localization_query(rng, **kw)
+    q.update(hypotheses=10000, tau=4.0)
+    return q
+
+
+def config4(seed=0, n_queries=64, **kw):
+    """Precision study: queries of 50k matches through the planar pipeline
+    with 1% depth noise and pixel noise in {0.5, 1, 1.5, 2} px (16 each)."""
+    rng = np.random.default_rng(seed)
+    sigmas = [0.5, 1.0, 1.5, 2.0]
+    out = []
+    for qi in range(n_queries):
+        q = localization_query(rng, pixel_noise=sigmas[qi * len(sigmas) // n_queries], depth_noise=0.01, **kw)
+        q.update(hypotheses=10000, tau=4.0, query_id=qi)
+        out.append(q)
+    return out
