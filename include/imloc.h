@@ -1,0 +1,193 @@
+/*
+ * imloc.h -- C ABI of the GB300 (sm_103a) implementation of the ImLoc
+ * localization hot path: 2D-2D -> 2D-3D lifting through stored depth maps and
+ * LO-RANSAC PnP (ImLoc, arXiv 2601.04185, Sec. 3.3).
+ *
+ * Conventions
+ *   - Poses are cam_from_world: X_c = R X_w + t, R row-major 3x3.
+ *   - Pixel coordinates are continuous; the image covers [0,W]x[0,H] and the
+ *     pixel (i,j) is centred at (i+0.5, j+0.5).
+ *   - Depth maps hold z-depth (distance along the optical axis) in float32;
+ *     a value <= 0 or non-finite marks "no depth".
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary CPU memory.  Every buffer passed in
+ *     is owned by the caller and must stay valid until the work enqueued on
+ *     `stream` has finished.  The library never frees caller memory and never
+ *     returns memory the caller must free.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Functions
+ *     named *_async only enqueue work; the others return when the results are
+ *     in host memory.
+ *   - Every function returns an imloc status (0 = IMLOC_OK, < 0 = error).
+ *     Nothing throws across this boundary and nothing aborts the process.
+ *   - A context owns one device workspace; calls on one context must not
+ *     overlap in time (use one context per concurrent stream).
+ */
+#ifndef IMLOC_H
+#define IMLOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define IMLOC_OK                 0
+#define IMLOC_PENDING            1   /* serving: result not ready yet                 */
+#define IMLOC_ERR_INVALID_ARG   -1   /* a pointer, size or option is out of range     */
+#define IMLOC_ERR_OOM           -2   /* the context workspace (or budget) is too small */
+#define IMLOC_ERR_REJECTED      -3   /* serving: admission refused (queue/budget)      */
+#define IMLOC_ERR_TIMEOUT       -4   /* a bounded device-side wait gave up             */
+#define IMLOC_ERR_CUDA          -5   /* a CUDA runtime call failed                     */
+#define IMLOC_ERR_NOT_FOUND     -6   /* serving: unknown or already consumed ticket    */
+#define IMLOC_ERR_DEGENERATE    -7   /* fewer than 3 correspondences or no hypothesis  */
+#define IMLOC_ERR_CAPACITY      -8   /* an output buffer is smaller than needed        */
+
+typedef struct imloc_ctx imloc_ctx;
+
+/* Create a context on CUDA device `device` with a device workspace of
+ * `workspace_bytes` (0 = 512 MiB).  All scratch memory of later calls is
+ * carved from this workspace; no later call allocates device memory. */
+int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes);
+void imloc_destroy(imloc_ctx* ctx);
+const char* imloc_status_str(int status);
+/* Text of the last failing CUDA runtime call on this thread (for IMLOC_ERR_CUDA). */
+const char* imloc_last_cuda_error(void);
+/* Sticky device-side error word of the context (IMLOC_OK if none), e.g. a
+ * bounded wait that timed out inside a kernel.  Synchronises the context's
+ * last stream. */
+int imloc_device_error(imloc_ctx* ctx);
+
+/* ---- cameras and views -------------------------------------------------- */
+typedef struct { float fx, fy, cx, cy; int32_t width, height; } imloc_camera;   /* pinhole */
+typedef struct { double R[9]; double t[3]; } imloc_pose;                        /* cam_from_world */
+
+/* One database view of the image-based map (ImLoc Sec. 3.1): a depth map
+ * with its intrinsics and pose.  `depth` is a device pointer to
+ * height x width float32 values, row stride `pitch` elements. */
+typedef struct {
+    const float* depth;
+    int32_t width, height;
+    int64_t pitch;
+    imloc_camera cam;
+    imloc_pose pose;
+} imloc_view;
+
+/* ---- lifting (ImLoc Sec. 3.3, "Query Time Matching and 2D-3D Lifting") --
+ * A match pairs a query pixel (q_u, q_v) with a database position (db_u,
+ * db_v) in one view and carries the matcher confidence.  Matches are grouped
+ * in segments of one view and one direction:
+ *   direction 0: query->database; (db_u, db_v) is subpixel and the depth is
+ *                interpolated bilinearly between the four surrounding pixel
+ *                centres (all four must hold a depth and lie inside);
+ *   direction 1: database->query; the depth is read at the pixel containing
+ *                (db_u, db_v).
+ * A match is kept iff conf > 0.05 (compared in float32) and its depth is
+ * valid.  Kept matches become correspondences
+ *   x, y  = query pixel, X,Y,Z = R^T (d K^-1 [db_u, db_v, 1]^T - t),
+ *   w     = conf, src = index of the match in the input,
+ * written densely in input order (a stable compaction). */
+typedef struct {
+    int64_t begin;       /* first match of the segment; the segment ends where the next begins (or at n) */
+    int32_t view;        /* index into the view array */
+    int32_t direction;   /* 0 = query->database (bilinear), 1 = database->query (lookup) */
+} imloc_segment;
+
+typedef struct {
+    const float *q_u, *q_v, *db_u, *db_v, *conf; /* device, n each (structure of arrays) */
+    int64_t n;
+    const imloc_segment* segments;               /* host, n_segments, begins ascending, segments[0].begin == 0 */
+    int32_t n_segments;
+} imloc_matches;
+
+/* Correspondence set, structure of arrays in device memory (caller-owned).
+ * `count` (device, may be NULL on input to RANSAC) holds the number of valid
+ * entries; `capacity` bounds every array. */
+typedef struct {
+    float *x, *y, *X, *Y, *Z, *w;
+    int32_t* src;
+    int32_t* count;
+    int64_t capacity;
+} imloc_corr;
+
+/* Lift one query's matches.  Requires out->capacity >= m->n.  Writes the
+ * valid count to out->count (device).  Async on `stream`. */
+int imloc_lift_async(imloc_ctx* ctx, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                     imloc_corr* out, void* stream);
+
+/* Lift many queries in one launch.  The matches of query q are
+ * [query_begin[q], query_begin[q+1]) of `m` (host array, n_queries+1 entries,
+ * segment boundaries must include every query boundary).  All outputs go to
+ * one concatenated set; the correspondences of query q are
+ * [d_offsets[q], d_offsets[q+1]) (device array, n_queries+1 entries). */
+int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin,
+                           const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                           imloc_corr* out, int64_t* d_offsets, void* stream);
+
+/* ---- LO-RANSAC PnP (ImLoc Sec. 3.3, "Pose Estimation") -----------------
+ * Rounds of `batch` minimal sets of 3 correspondences drawn from a uniform
+ * stride subsample of at most `max_score_corr` correspondences; every P3P
+ * pose is scored by the confidence-weighted truncated squared reprojection
+ * error  sum_i w_i min(r_i^2, tau^2)  (a point behind the camera counts
+ * tau^2); when a round's best pose beats the best so far, Gauss-Newton LO
+ * refines it on the subset; the loop stops after `max_iters` minimal sets or
+ * once P(missing the best model) < p_miss; the final pose is refined with a
+ * Cauchy loss over all inliers of the full set, weighted by confidence.
+ * Minimal sample s of query `query_id` uses Philox4x32-10 with key = seed and
+ * counter = (s, query_id, attempt, 0). */
+typedef struct {
+    double tau_px;           /* inlier threshold in pixels (4) */
+    int32_t max_score_corr;  /* subsample cap (10000) */
+    int32_t batch;           /* minimal sets per round (1024) */
+    int32_t max_iters;       /* minimal sets at most (100000) */
+    int32_t lo_iters;        /* Gauss-Newton iterations per LO (10); 0 disables LO */
+    double p_miss;           /* adaptive stop (1e-4); <= 0 runs all max_iters */
+    int32_t final_iters;     /* Cauchy refinement iterations (25); 0 disables */
+    int32_t p3p_fp64_polish; /* 1: Newton polish of the P3P depths in FP64 (default) */
+    double cauchy_scale;     /* Cauchy scale c in pixels (<= 0: use tau_px) */
+    uint64_t seed;
+    uint32_t query_id;
+    int32_t enumerate_all;   /* test mode: every triple of the subset in one round */
+} imloc_ransac_opts;
+
+/* Fill `o` with the defaults above. */
+void imloc_ransac_default_opts(imloc_ransac_opts* o);
+
+/* Result of one query (host or device memory, same layout). */
+typedef struct {
+    double R[9], t[3];           /* final pose (after the Cauchy refinement) */
+    double R_best[9], t_best[3]; /* best RANSAC model (after LO), before the refinement */
+    double score;                /* its truncated cost on the subset */
+    int64_t num_inliers;         /* inliers of the final pose over all correspondences */
+    int64_t subset_inliers;      /* inliers of the RANSAC best on the subset */
+    int64_t iterations;          /* minimal sets drawn */
+    int64_t rounds;
+    int64_t lo_count;            /* LO runs */
+    int64_t hypotheses;          /* P3P poses scored */
+    int64_t best_hyp;            /* 4 * sample + solution index of the last accepted round best */
+    int32_t status;              /* IMLOC_OK or IMLOC_ERR_DEGENERATE / IMLOC_ERR_TIMEOUT */
+    int32_t reserved;
+} imloc_result;
+
+/* One query.  `corr->count` (device) gives N when non-NULL, else
+ * corr->capacity is N.  `d_inlier_mask` (device, optional) receives one byte
+ * per correspondence: 1 iff inlier of the final pose.  Returns after the
+ * result is in `out` (host). */
+int imloc_ransac_pnp(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam,
+                     const imloc_ransac_opts* opts, imloc_result* out, uint8_t* d_inlier_mask, void* stream);
+
+/* Many queries in shared launches.  Query q uses the correspondences
+ * [d_offsets[q], d_offsets[q+1]) of the concatenated set `corr` (d_offsets:
+ * device, n_queries+1), camera qcams[q] and options opts[q] (host arrays).
+ * Results go to d_results[q] (device); masks, if d_masks != NULL, to the
+ * device byte array d_masks at the same offsets as the correspondences. */
+int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_corr* corr,
+                                 const int64_t* d_offsets, const imloc_camera* qcams,
+                                 const imloc_ransac_opts* opts, imloc_result* d_results,
+                                 uint8_t* d_masks, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMLOC_H */

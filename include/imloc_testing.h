@@ -1,0 +1,40 @@
+/*
+ * imloc_testing.h -- test hooks of libimloc: the same kernels as
+ * imloc_ransac_pnp, with their intermediate results exposed so that each
+ * step of ImLoc Sec. 3.3 "Pose Estimation" (minimal samples, P3P poses,
+ * per-pose truncated scores and inlier counts, per-round best) can be
+ * compared with an independent implementation.  Same conventions as imloc.h.
+ */
+#ifndef IMLOC_TESTING_H
+#define IMLOC_TESTING_H
+
+#include "imloc.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Device buffers (caller-owned; any may be NULL) filled by imloc_testing_ransac.
+ * H is the number of minimal sets (opts->max_iters, or C(min(N, cap), 3) in
+ * enumerate mode, or n_inject); pose id = 4 * sample + solution index. */
+typedef struct {
+    int32_t* triples;          /* 3 * H: subset indices of each minimal sample, -1 if degenerate */
+    float* poses;              /* 4 * H * 12: pose of each id: R (row-major 3x3) then t */
+    float* scores;             /* 4 * H: truncated cost on the subset of each valid pose id */
+    int32_t* counts;           /* 4 * H: inliers on the subset of each valid pose id */
+    uint64_t* round_best;      /* ceil(H / batch): (score bits << 32) | pose id, ~0 if the round had no pose */
+    const float* inject_poses; /* n_inject * 12: score these poses (pose id 4 k) instead of sampling */
+    int64_t n_inject;
+} imloc_debug;
+
+/* One query with the debug buffers above.  The adaptive stop must be off
+ * (opts->p_miss <= 0) so that every round is scored in a single wave; N is
+ * corr->capacity (corr->count is ignored).  Synchronous. */
+int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam,
+                         const imloc_ransac_opts* opts, const imloc_debug* dbg, imloc_result* out,
+                         uint8_t* d_inlier_mask, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IMLOC_TESTING_H */

@@ -1,0 +1,366 @@
+// lift.cu -- 2D-2D -> 2D-3D lifting through stored depth maps (ImLoc Sec. 3.3,
+// "Query Time Matching and 2D-3D Lifting").
+//
+// One thread per match: confidence filter (> 0.05 in float32), depth fetch
+// (bilinear between the four surrounding pixel centres for query->database
+// matches, a single lookup for database->query matches), back-projection
+// X_w = R^T (d K^-1 [u v 1]^T - t), then a stable compaction of the valid
+// matches into a structure of arrays.  The compaction is single pass: each
+// CTA takes the next tile id from an atomic counter, scans its flags with
+// warp ballots, publishes its count and looks back over its predecessors'
+// published counts/prefixes (decoupled look-back) with a bounded spin.
+//
+// HBM-bound: per match 20 B of match data, the depth taps (two 32-B sectors
+// for a bilinear fetch) and 28 B of output.
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+
+namespace imloc {
+
+struct LiftView {
+    const float* depth;
+    int64_t pitch;
+    int32_t W, H;
+    float ifx, ify, cx, cy;
+    float Rt[9];  // R^T, row-major
+    float C[3];   // camera centre -R^T t
+};
+
+struct LiftSeg {
+    int64_t begin;
+    int32_t view;
+    int32_t dir;
+    int32_t q_lo, q_hi;  // queries [q_lo, q_hi) whose first match is `begin` (empty range if none)
+};
+
+struct LiftParams {
+    const float *q_u, *q_v, *db_u, *db_v, *conf;
+    int64_t n;
+    const LiftSeg* segs;
+    int32_t n_seg;
+    int32_t n_tiles;
+    const LiftView* views;
+    float conf_min;
+    float *ox, *oy, *oX, *oY, *oZ, *ow;
+    int32_t* osrc;
+    int32_t* count;         // total valid (device), may be null
+    int64_t* offsets;       // per-query output offsets (device, n_queries+1), may be null
+    int32_t tail_q_lo, n_queries;  // queries [tail_q_lo, n_queries] start at n (all take the total)
+    unsigned long long* tile_state;  // n_tiles words: (flag << 32) | value
+    uint32_t* tile_counter;
+    int* err;
+};
+
+constexpr int kLiftThreads = 256;
+constexpr int kLiftItems = 4;
+constexpr int kLiftTile = kLiftThreads * kLiftItems;
+constexpr uint32_t kFlagAggregate = 1u, kFlagPrefix = 2u;
+
+__device__ __forceinline__ bool depth_ok(float d) { return d > 0.0f && d < INFINITY; }
+
+__device__ __forceinline__ int find_segment(const LiftSeg* segs, int n_seg, int64_t j) {
+    int lo = 0, hi = n_seg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (segs[mid].begin <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ LiftParams p) {
+    __shared__ int s_tile;
+    __shared__ int s_wcnt[kLiftItems * (kLiftThreads / 32)];
+    __shared__ int s_excl;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kLiftThreads / 32;
+
+    if (tid == 0) s_tile = static_cast<int>(atomicAdd(p.tile_counter, 1u));
+    __syncthreads();
+    const int tile = s_tile;
+    const int64_t base = static_cast<int64_t>(tile) * kLiftTile;
+
+    float vx[kLiftItems], vy[kLiftItems], vX[kLiftItems], vY[kLiftItems], vZ[kLiftItems], vw[kLiftItems];
+    bool ok[kLiftItems];
+    int seg_of[kLiftItems];
+#pragma unroll
+    for (int k = 0; k < kLiftItems; ++k) {
+        const int64_t j = base + k * kLiftThreads + tid;
+        ok[k] = false;
+        seg_of[k] = -1;
+        if (j >= p.n) continue;
+        const int s = find_segment(p.segs, p.n_seg, j);
+        seg_of[k] = s;
+        const LiftSeg sg = p.segs[s];
+        const float c = __ldg(p.conf + j);
+        const float u = __ldg(p.db_u + j), v = __ldg(p.db_v + j);
+        vx[k] = __ldg(p.q_u + j);
+        vy[k] = __ldg(p.q_v + j);
+        vw[k] = c;
+        if (!(c > p.conf_min)) continue;
+        const LiftView& V = p.views[sg.view];
+        float d;
+        bool good;
+        if (sg.dir == 0) {
+            const float a = u - 0.5f, b = v - 0.5f;
+            good = (a >= 0.0f) && (a < static_cast<float>(V.W - 1)) && (b >= 0.0f) && (b < static_cast<float>(V.H - 1));
+            if (!good) continue;
+            const int i0 = static_cast<int>(a), j0 = static_cast<int>(b);
+            const float* r0 = V.depth + static_cast<int64_t>(j0) * V.pitch + i0;
+            const float* r1 = r0 + V.pitch;
+            const float d00 = __ldg(r0), d01 = __ldg(r0 + 1), d10 = __ldg(r1), d11 = __ldg(r1 + 1);
+            good = depth_ok(d00) && depth_ok(d01) && depth_ok(d10) && depth_ok(d11);
+            const float al = a - static_cast<float>(i0), be = b - static_cast<float>(j0);
+            d = (1.0f - be) * ((1.0f - al) * d00 + al * d01) + be * ((1.0f - al) * d10 + al * d11);
+        } else {
+            good = (u >= 0.0f) && (u < static_cast<float>(V.W)) && (v >= 0.0f) && (v < static_cast<float>(V.H));
+            if (!good) continue;
+            d = __ldg(V.depth + static_cast<int64_t>(static_cast<int>(v)) * V.pitch + static_cast<int>(u));
+            good = depth_ok(d);
+        }
+        if (!good) continue;
+        const float xc = d * ((u - V.cx) * V.ifx), yc = d * ((v - V.cy) * V.ify), zc = d;
+        vX[k] = fmaf(V.Rt[0], xc, fmaf(V.Rt[1], yc, fmaf(V.Rt[2], zc, V.C[0])));
+        vY[k] = fmaf(V.Rt[3], xc, fmaf(V.Rt[4], yc, fmaf(V.Rt[5], zc, V.C[1])));
+        vZ[k] = fmaf(V.Rt[6], xc, fmaf(V.Rt[7], yc, fmaf(V.Rt[8], zc, V.C[2])));
+        ok[k] = true;
+    }
+
+    // ---- tile-local scan in input order: item k, then warp, then lane ----
+    uint32_t ball[kLiftItems];
+#pragma unroll
+    for (int k = 0; k < kLiftItems; ++k) {
+        ball[k] = __ballot_sync(0xffffffffu, ok[k]);
+        if (lane == 0) s_wcnt[k * kWarps + warp] = __popc(ball[k]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive scan over the kLiftItems * kWarps (= 32) warp counts
+        const int v = s_wcnt[lane];
+        int incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        s_wcnt[lane] = incl - v;
+
+        // ---- decoupled look-back over predecessor tiles ----
+        int excl = 0;
+        if (tile == 0) {
+            if (lane == 0)
+                atomicExch(&p.tile_state[0], (static_cast<unsigned long long>(kFlagPrefix) << 32) | static_cast<uint32_t>(total));
+        } else {
+            if (lane == 0)
+                atomicExch(&p.tile_state[tile], (static_cast<unsigned long long>(kFlagAggregate) << 32) | static_cast<uint32_t>(total));
+            int look = tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                const int i = look - lane;
+                unsigned long long st = (i >= 0) ? *reinterpret_cast<volatile unsigned long long*>(&p.tile_state[i])
+                                                 : (static_cast<unsigned long long>(kFlagPrefix) << 32);
+                while (__any_sync(0xffffffffu, (st >> 32) == 0u)) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) atomicCAS(p.err, 0, kDevTimeoutLookback);
+                        if ((st >> 32) == 0u) st = (static_cast<unsigned long long>(kFlagPrefix) << 32);
+                        break;
+                    }
+                    if ((st >> 32) == 0u) st = *reinterpret_cast<volatile unsigned long long*>(&p.tile_state[i]);
+                }
+                const uint32_t pmask = __ballot_sync(0xffffffffu, (st >> 32) == kFlagPrefix);
+                const int val = static_cast<int>(st & 0xffffffffu);
+                if (pmask) {
+                    const int first = __ffs(pmask) - 1;
+                    excl += warp_sum_i(lane <= first ? val : 0);
+                    break;
+                }
+                excl += warp_sum_i(val);
+                look -= 32;
+            }
+            if (lane == 0)
+                atomicExch(&p.tile_state[tile],
+                           (static_cast<unsigned long long>(kFlagPrefix) << 32) | static_cast<uint32_t>(excl + total));
+        }
+        if (lane == 0) {
+            s_excl = excl;
+            if (tile == p.n_tiles - 1) {
+                if (p.count) *p.count = excl + total;
+                if (p.offsets)
+                    for (int q = p.tail_q_lo; q <= p.n_queries; ++q) p.offsets[q] = excl + total;
+            }
+        }
+    }
+    __syncthreads();
+
+    const uint32_t lt = (1u << lane) - 1u;
+    const int excl = s_excl;
+#pragma unroll
+    for (int k = 0; k < kLiftItems; ++k) {
+        const int pos = excl + s_wcnt[k * kWarps + warp] + __popc(ball[k] & lt);
+        const int64_t j = base + k * kLiftThreads + tid;
+        if (seg_of[k] >= 0 && p.offsets) {
+            const LiftSeg& sg = p.segs[seg_of[k]];
+            if (sg.begin == j)
+                for (int q = sg.q_lo; q < sg.q_hi; ++q) p.offsets[q] = pos;
+        }
+        if (!ok[k]) continue;
+        p.ox[pos] = vx[k];
+        p.oy[pos] = vy[k];
+        p.oX[pos] = vX[k];
+        p.oY[pos] = vY[k];
+        p.oZ[pos] = vZ[k];
+        p.ow[pos] = vw[k];
+        p.osrc[pos] = static_cast<int32_t>(j);
+    }
+}
+
+// Host side: build the view / segment tables, upload, launch.
+static int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, const imloc_view* views,
+                     int32_t n_views, const imloc_matches* m, imloc_corr* out, int64_t* d_offsets,
+                     cudaStream_t stream) {
+    if (!views || n_views <= 0 || !m || !out || n_queries <= 0 || !query_begin) return IMLOC_ERR_INVALID_ARG;
+    if (m->n < 0 || m->n >= (int64_t(1) << 31)) return IMLOC_ERR_INVALID_ARG;
+    if (out->capacity < m->n) return IMLOC_ERR_CAPACITY;
+    if (m->n > 0) {
+        if (!m->q_u || !m->q_v || !m->db_u || !m->db_v || !m->conf || !m->segments || m->n_segments <= 0)
+            return IMLOC_ERR_INVALID_ARG;
+        if (!out->x || !out->y || !out->X || !out->Y || !out->Z || !out->w || !out->src) return IMLOC_ERR_INVALID_ARG;
+        if (m->segments[0].begin != 0) return IMLOC_ERR_INVALID_ARG;
+    }
+    if (query_begin[0] != 0 || query_begin[n_queries] != m->n) return IMLOC_ERR_INVALID_ARG;
+    for (int q = 0; q < n_queries; ++q)
+        if (query_begin[q + 1] < query_begin[q]) return IMLOC_ERR_INVALID_ARG;
+    for (int s = 0; s < m->n_segments; ++s) {
+        const imloc_segment& sg = m->segments[s];
+        if (sg.view < 0 || sg.view >= n_views || (sg.direction != 0 && sg.direction != 1)) return IMLOC_ERR_INVALID_ARG;
+        if (s > 0 && sg.begin < m->segments[s - 1].begin) return IMLOC_ERR_INVALID_ARG;
+        if (sg.begin > m->n) return IMLOC_ERR_INVALID_ARG;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const imloc_view& V = views[v];
+        if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
+        if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
+    }
+
+    // Device segment table: non-empty segments only; every query must begin at
+    // the start of one of them, or at n (then it is empty and takes the total).
+    std::vector<LiftSeg> segs;
+    int qi = 0;
+    for (int s = 0; s < (m->n > 0 ? m->n_segments : 0); ++s) {
+        const int64_t b = m->segments[s].begin;
+        const int64_t e = (s + 1 < m->n_segments) ? m->segments[s + 1].begin : m->n;
+        if (e <= b) continue;
+        LiftSeg L;
+        L.begin = b;
+        L.view = m->segments[s].view;
+        L.dir = m->segments[s].direction;
+        if (qi < n_queries && query_begin[qi] < b) return IMLOC_ERR_INVALID_ARG;  // begins inside a segment
+        L.q_lo = qi;
+        while (qi < n_queries && query_begin[qi] == b) ++qi;
+        L.q_hi = qi;
+        segs.push_back(L);
+    }
+    for (int q = qi; q < n_queries; ++q)
+        if (query_begin[q] != m->n) return IMLOC_ERR_INVALID_ARG;
+    const int tail_q_lo = qi;
+
+    std::vector<LiftView> lv(static_cast<size_t>(n_views));
+    for (int v = 0; v < n_views; ++v) {
+        const imloc_view& V = views[v];
+        LiftView& L = lv[v];
+        L.depth = V.depth;
+        L.pitch = V.pitch;
+        L.W = V.width;
+        L.H = V.height;
+        L.ifx = static_cast<float>(1.0 / static_cast<double>(V.cam.fx));
+        L.ify = static_cast<float>(1.0 / static_cast<double>(V.cam.fy));
+        L.cx = V.cam.cx;
+        L.cy = V.cam.cy;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) L.Rt[3 * r + c] = static_cast<float>(V.pose.R[3 * c + r]);
+        for (int r = 0; r < 3; ++r) {
+            double cr = 0.0;
+            for (int c = 0; c < 3; ++c) cr -= V.pose.R[3 * c + r] * V.pose.t[c];
+            L.C[r] = static_cast<float>(cr);
+        }
+    }
+
+    const int64_t n = m->n;
+    const int n_tiles = static_cast<int>((n + kLiftTile - 1) / kLiftTile);
+    if (n == 0) {
+        if (out->count) IMLOC_CUDA_TRY(cudaMemsetAsync(out->count, 0, sizeof(int32_t), stream));
+        if (d_offsets) IMLOC_CUDA_TRY(cudaMemsetAsync(d_offsets, 0, sizeof(int64_t) * (n_queries + 1), stream));
+        return IMLOC_OK;
+    }
+    const size_t seg_bytes = sizeof(LiftSeg) * segs.size(), view_bytes = sizeof(LiftView) * lv.size();
+    char* h = static_cast<char*>(staging_alloc(ctx, seg_bytes + 256 + view_bytes));
+    char* d = static_cast<char*>(ws_alloc(ctx, seg_bytes + 256 + view_bytes));
+    if (!h || !d) return IMLOC_ERR_OOM;
+    const size_t view_off = align_up(seg_bytes, 256);
+    memcpy(h, segs.data(), seg_bytes);
+    memcpy(h + view_off, lv.data(), view_bytes);
+    int rc = upload(ctx, d, h, view_off + view_bytes, stream);
+    if (rc != IMLOC_OK) return rc;
+
+    // scan scratch: word 0 = tile counter, words 1..n_tiles = tile states
+    unsigned long long* state = static_cast<unsigned long long*>(ws_alloc(ctx, sizeof(unsigned long long) * (n_tiles + 1)));
+    if (!state) return IMLOC_ERR_OOM;
+    IMLOC_CUDA_TRY(cudaMemsetAsync(state, 0, sizeof(unsigned long long) * (n_tiles + 1), stream));
+
+    LiftParams p;
+    p.q_u = m->q_u; p.q_v = m->q_v; p.db_u = m->db_u; p.db_v = m->db_v; p.conf = m->conf;
+    p.n = n;
+    p.segs = reinterpret_cast<const LiftSeg*>(d);
+    p.n_seg = static_cast<int32_t>(segs.size());
+    p.n_tiles = n_tiles;
+    p.views = reinterpret_cast<const LiftView*>(d + view_off);
+    p.conf_min = 0.05f;
+    p.ox = out->x; p.oy = out->y; p.oX = out->X; p.oY = out->Y; p.oZ = out->Z; p.ow = out->w;
+    p.osrc = out->src;
+    p.count = out->count;
+    p.offsets = d_offsets;
+    p.tail_q_lo = tail_q_lo;
+    p.n_queries = n_queries;
+    p.tile_state = state + 1;
+    p.tile_counter = reinterpret_cast<uint32_t*>(state);
+    p.err = ctx->d_err;
+    k_lift<<<n_tiles, kLiftThreads, 0, stream>>>(p);
+    IMLOC_CUDA_TRY(cudaGetLastError());
+    ctx->last_stream = stream;
+    return IMLOC_OK;
+}
+
+}  // namespace imloc
+
+extern "C" {
+
+int imloc_lift_async(imloc_ctx* ctx, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                     imloc_corr* out, void* stream) {
+    if (!ctx || !m) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = imloc::begin_call(ctx);
+    if (rc != IMLOC_OK) return rc;
+    const int64_t qb[2] = {0, m->n};
+    return imloc::lift_impl(ctx, 1, qb, views, n_views, m, out, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, const imloc_view* views,
+                           int32_t n_views, const imloc_matches* m, imloc_corr* out, int64_t* d_offsets,
+                           void* stream) {
+    if (!ctx || !m) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = imloc::begin_call(ctx);
+    if (rc != IMLOC_OK) return rc;
+    return imloc::lift_impl(ctx, n_queries, query_begin, views, n_views, m, out, d_offsets,
+                            static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,1201 @@
+// ransac.cu -- GPU LO-RANSAC PnP (ImLoc Sec. 3.3, "Pose Estimation").
+//
+// The round loop of the method (sample a batch of minimal sets, P3P, score
+// every pose on the <= 10K subset, LO when a round's best beats the best so
+// far, adaptive stop) is reorganised for the GPU without changing its result:
+// minimal sample s is a pure function of (seed, query, s) (counter-based
+// Philox), and the score of a pose does not depend on earlier rounds, so all
+// rounds of a "wave" are sampled, solved and scored in three wide launches;
+// a per-query replay kernel then walks the wave's rounds in order, applies
+// the round-best / LO / termination logic exactly as the sequential loop
+// would, and runs the final Cauchy refinement once the query is done.  With
+// the adaptive stop off a query is one wave; with it on, waves of 1, 1, 2, 4,
+// ... rounds bound the speculative work to about twice the rounds needed.
+//
+// Kernels (in launch order per wave):
+//   k_setup        per query: N, subset size M, uniform-stride subset gather
+//                  into 32-byte records, reset of the per-round reductions
+//   k_sample_p3p   one minimal sample per thread: Philox triple, bearings,
+//                  P3P (FP32 + FP64 Newton polish), pose slots, compact list
+//   k_tiles        per-query hypothesis-tile prefix for the work queue
+//   k_score        persistent, cluster-split: a cluster takes a (query,
+//                  hypothesis tile) from the queue; each CTA of the cluster
+//                  streams its share of the subset through shared memory
+//                  with bulk (TMA) copies and scores 4 poses per thread in
+//                  registers; partial sums are combined across the cluster
+//                  through distributed shared memory; per round, the best
+//                  (score, pose id) is kept by a 64-bit atomic minimum
+//   k_replay       per query (one cluster): rounds in order, LO by
+//                  Gauss-Newton on SE(3) (cluster-reduced normal equations,
+//                  FP64 6x6 Cholesky), termination, final Cauchy IRLS.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "p3p.cuh"
+#include "../../include/imloc_testing.h"
+
+namespace imloc {
+
+struct WaveQ {
+    int64_t s_begin;    // first minimal sample of the wave for this query
+    int32_t n_samples;  // samples of the wave for this query
+    int32_t pad;
+};
+
+// ============================================================================
+// k_setup
+// ============================================================================
+struct SetupParams {
+    const QueryDesc* qd;
+    QueryState* qs;
+    int32_t* n_hyp_all;  // [waves * nq], zeroed here
+    int32_t n_hyp_len;
+};
+
+__global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupParams p) {
+    const int q = blockIdx.x;
+    const QueryDesc& d = p.qd[q];
+    __shared__ int64_t s_off, s_n;
+    __shared__ int32_t s_m;
+    if (threadIdx.x == 0) {
+        int64_t off = 0, n;
+        if (d.d_off) {
+            off = d.d_off[d.q_off];
+            n = d.d_off[d.q_off + 1] - off;
+        } else if (d.d_count) {
+            n = *d.d_count;
+        } else {
+            n = d.n_host;
+        }
+        QueryState st;
+        memset(&st, 0, sizeof(st));
+        st.status = IMLOC_OK;
+        if (n < 0 || off < 0 || off + n > d.n_cap) {
+            n = 0;
+            off = 0;
+            st.status = IMLOC_ERR_CAPACITY;
+        }
+        const int32_t m = static_cast<int32_t>(n < d.m_cap ? n : d.m_cap);
+        st.off = off;
+        st.n = n;
+        st.m = m;
+        st.best_score = INFINITY;
+        st.best_hyp = -1;
+        if (n < 3 || d.hyps <= 0) {
+            st.done = 1;
+            if (st.status == IMLOC_OK) st.status = IMLOC_ERR_DEGENERATE;
+        }
+        p.qs[q] = st;
+        s_off = off;
+        s_n = n;
+        s_m = m;
+    }
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < p.n_hyp_len; i += gridDim.x * 256) p.n_hyp_all[i] = 0;
+    __syncthreads();
+    for (int r = threadIdx.x; r < d.rounds; r += 256) {
+        d.round_best[r] = ~0ull;
+        d.round_hyps[r] = 0;
+    }
+    const int64_t off = s_off, n = s_n;
+    const int32_t m = s_m;
+    for (int k = threadIdx.x; k < m; k += 256) {
+        const int64_t i = off + (static_cast<int64_t>(k) * n) / m;  // uniform stride, exact in 64-bit
+        ScoreCorr r;
+        r.X = d.X[i]; r.Y = d.Y[i]; r.Z = d.Z[i]; r.w = d.w[i];
+        r.x = d.x[i]; r.y = d.y[i]; r.p0 = 0.f; r.p1 = 0.f;
+        d.subset[k] = r;
+    }
+}
+
+// ============================================================================
+// k_sample_p3p
+// ============================================================================
+struct SampleParams {
+    const QueryDesc* qd;
+    const QueryState* qs;
+    const WaveQ* wq;            // [nq] of this wave
+    const int64_t* prefix;      // [nq+1] flattened sample offsets of this wave
+    int32_t* n_hyp;             // [nq] valid poses of this wave
+    int64_t total;
+    int32_t nq;
+};
+
+// lexicographic rank -> triple i < j < k of [0, m) (test mode, small m)
+__device__ void unrank_triple(int64_t s, int m, int idx[3]) {
+    int i = 0;
+    for (; i < m - 2; ++i) {
+        const int64_t r = static_cast<int64_t>(m - 1 - i) * (m - 2 - i) / 2;
+        if (s < r) break;
+        s -= r;
+    }
+    int j = i + 1;
+    for (; j < m - 1; ++j) {
+        const int64_t r = m - 1 - j;
+        if (s < r) break;
+        s -= r;
+    }
+    idx[0] = i;
+    idx[1] = j;
+    idx[2] = j + 1 + static_cast<int>(s);
+}
+
+__global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ SampleParams p) {
+    const int64_t g = static_cast<int64_t>(blockIdx.x) * 128 + threadIdx.x;
+    const bool in_range = g < p.total;
+    int q = 0;
+    if (in_range) {
+        int lo = 0, hi = p.nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.prefix[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        q = lo;
+    }
+    const QueryDesc& d = p.qd[q];
+    int nsol = 0;
+    int64_t s = 0, local = 0;
+    PoseF sol[4];
+    if (in_range) {
+        local = g - p.prefix[q];
+        s = p.wq[q].s_begin + local;
+        const QueryState& st = p.qs[q];
+        if (d.inject) {
+            // poses are given: slot `local` already holds pose 4 s
+            nsol = (!st.done && st.m >= 1) ? 1 : 0;
+        } else if (!st.done && st.m >= 3) {
+            int idx[3];
+            bool ok;
+            if (d.enumerate_all) {
+                unrank_triple(s, st.m, idx);
+                ok = true;
+            } else {
+                ok = draw_triple(d.seed, d.query_id, static_cast<uint32_t>(s), static_cast<uint32_t>(st.m), idx);
+            }
+            if (d.triples) {
+                d.triples[3 * local + 0] = ok ? idx[0] : -1;
+                d.triples[3 * local + 1] = ok ? idx[1] : -1;
+                d.triples[3 * local + 2] = ok ? idx[2] : -1;
+            }
+            if (ok) {
+                float y[3][3], X[3][3];
+                const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const ScoreCorr c = d.subset[idx[k]];
+                    const float bx = (c.x - d.cx) * ifx, by = (c.y - d.cy) * ify;
+                    const float inv = rsqrtf(bx * bx + by * by + 1.0f);
+                    y[k][0] = bx * inv; y[k][1] = by * inv; y[k][2] = inv;
+                    X[k][0] = c.X; X[k][1] = c.Y; X[k][2] = c.Z;
+                }
+                float l1[4];
+                nsol = p3p_solve(y, X, d.polish != 0, sol, l1);
+                for (int k = 0; k < nsol; ++k) d.slots[4 * local + k] = sol[k];
+            }
+        } else if (d.triples) {
+            d.triples[3 * local + 0] = -1;
+            d.triples[3 * local + 1] = -1;
+            d.triples[3 * local + 2] = -1;
+        }
+    }
+    // append valid pose ids to the query's compact list and count poses per
+    // round, aggregated over the lanes of the warp that share the query (and
+    // round); full-warp shuffles only
+    const int lane = threadIdx.x & 31;
+    const int key = in_range ? q : -1;
+    const long long rkey = in_range ? ((static_cast<long long>(q) << 32) | (s / d.batch)) : -1ll;
+    int excl = 0, total = 0, rtotal = 0, leader = -1, rleader = -1;
+    for (int l = 0; l < 32; ++l) {
+        const int kl = __shfl_sync(0xffffffffu, key, l);
+        const long long rl = __shfl_sync(0xffffffffu, rkey, l);
+        const int vl = __shfl_sync(0xffffffffu, nsol, l);
+        if (kl == key) {
+            if (leader < 0) leader = l;
+            if (l < lane) excl += vl;
+            total += vl;
+        }
+        if (rl == rkey) {
+            if (rleader < 0) rleader = l;
+            rtotal += vl;
+        }
+    }
+    int base = 0;
+    if (in_range && lane == leader && total > 0) base = atomicAdd(&p.n_hyp[q], total);
+    base = __shfl_sync(0xffffffffu, base, leader < 0 ? lane : leader);
+    if (in_range) {
+        for (int k = 0; k < nsol; ++k) d.compact[base + excl + k] = static_cast<int32_t>(4 * s + k);
+        if (lane == rleader && rtotal > 0) atomicAdd(&d.round_hyps[s / d.batch], rtotal);
+    }
+}
+
+// ============================================================================
+// k_tiles: per-query hypothesis tiles -> exclusive prefix, reset work counter
+// ============================================================================
+struct TilesParams {
+    const QueryState* qs;
+    const int32_t* n_hyp;
+    int32_t* tile_prefix;  // [nq+1]
+    uint32_t* work_counter;
+    int32_t nq;
+    int32_t tile_hyps;
+};
+
+__global__ void __launch_bounds__(1024) k_tiles(const __grid_constant__ TilesParams p) {
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    if (threadIdx.x == 0) {
+        s_carry = 0;
+        *p.work_counter = 0u;
+    }
+    __syncthreads();
+    for (int base = 0; base < p.nq; base += 1024) {
+        const int q = base + threadIdx.x;
+        int v = 0;
+        if (q < p.nq && !p.qs[q].done) v = (p.n_hyp[q] + p.tile_hyps - 1) / p.tile_hyps;
+        int incl = v;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = s_warp[lane], wi = w;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += t;
+            }
+            s_warp[lane] = wi - w;
+        }
+        __syncthreads();
+        const int excl = s_carry + s_warp[warp] + incl - v;
+        if (q < p.nq) p.tile_prefix[q] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) p.tile_prefix[p.nq] = s_carry;
+}
+
+// ============================================================================
+// k_score: persistent, cluster-split hypothesis scoring
+// ============================================================================
+constexpr int kChunk = 256;  // subset records per shared-memory stage (8 KB)
+
+struct ScoreParams {
+    const QueryDesc* qd;
+    const QueryState* qs;
+    const WaveQ* wq;
+    const int32_t* n_hyp;
+    const int32_t* tile_prefix;
+    uint32_t* work_counter;
+    int32_t nq;
+    int* err;
+};
+
+template <int THREADS, int HT, bool COUNT>
+__global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ ScoreParams p) {
+    constexpr int TH = THREADS * HT;
+    extern __shared__ __align__(128) unsigned char smem[];
+    ScoreCorr* buf = reinterpret_cast<ScoreCorr*>(smem);
+    float* s_part = reinterpret_cast<float*>(buf + 2 * kChunk);
+    int* s_cnt = reinterpret_cast<int*>(s_part + TH);
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_item;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phase[2] = {0u, 0u};
+    const int total_tiles = p.tile_prefix[p.nq];
+
+    for (;;) {
+        if (rank == 0 && tid == 0) s_item = static_cast<int>(atomicAdd(p.work_counter, 1u));
+        cluster.sync();
+        const int item = *cluster.map_shared_rank(&s_item, 0);
+        cluster.sync();
+        if (item >= total_tiles) break;
+        int lo = 0, hi = p.nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_prefix[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int q = lo;
+        const int tile = item - p.tile_prefix[q];
+        const QueryDesc& d = p.qd[q];
+        const int m = p.qs[q].m;
+        const int nh = p.n_hyp[q];
+        const int64_t slot_base = 4 * p.wq[q].s_begin;
+        const float tau2 = d.tau2;
+
+        float P[HT][12];
+#pragma unroll
+        for (int h = 0; h < HT; ++h) {
+            const int j = tile * TH + h * THREADS + tid;
+            if (j < nh) {
+                const int id = d.compact[j];
+                const PoseF ps = d.slots[id - slot_base];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    P[h][c] = d.fx * ps.R[c] + d.cx * ps.R[6 + c];
+                    P[h][4 + c] = d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c];
+                    P[h][8 + c] = ps.R[6 + c];
+                }
+                P[h][3] = d.fx * ps.t[0] + d.cx * ps.t[2];
+                P[h][7] = d.fy * ps.t[1] + d.cy * ps.t[2];
+                P[h][11] = ps.t[2];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) P[h][c] = 0.f;
+            }
+        }
+        const int c0 = static_cast<int>(static_cast<int64_t>(m) * rank / CS);
+        const int c1 = static_cast<int>(static_cast<int64_t>(m) * (rank + 1) / CS);
+        const int nchunks = (c1 - c0 + kChunk - 1) / kChunk;
+        float acc[HT];
+        int cnt[HT];
+#pragma unroll
+        for (int h = 0; h < HT; ++h) { acc[h] = 0.f; cnt[h] = 0; }
+
+        if (tid == 0 && nchunks > 0) {
+            const int nrec = min(kChunk, c1 - c0);
+            mbar_arrive_expect_tx(&bar[0], nrec * 32u);
+            bulk_g2s(buf, d.subset + c0, nrec * 32u, &bar[0]);
+        }
+        for (int c = 0; c < nchunks; ++c) {
+            const int b = c & 1;
+            if (tid == 0 && c + 1 < nchunks) {
+                const int start = c0 + (c + 1) * kChunk;
+                const int nrec = min(kChunk, c1 - start);
+                mbar_arrive_expect_tx(&bar[b ^ 1], nrec * 32u);
+                bulk_g2s(buf + (b ^ 1) * kChunk, d.subset + start, nrec * 32u, &bar[b ^ 1]);
+            }
+            mbar_wait_bounded(&bar[b], phase[b], p.err);
+            phase[b] ^= 1u;
+            const int nrec = min(kChunk, c1 - (c0 + c * kChunk));
+            const float4* rec = reinterpret_cast<const float4*>(buf + b * kChunk);
+            float part[HT];
+#pragma unroll
+            for (int h = 0; h < HT; ++h) part[h] = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < nrec; ++k) {
+                const float4 A = rec[2 * k];      // X Y Z w
+                const float4 Bq = rec[2 * k + 1]; // x y
+#pragma unroll
+                for (int h = 0; h < HT; ++h) {
+                    const float zu = fmaf(P[h][0], A.x, fmaf(P[h][1], A.y, fmaf(P[h][2], A.z, P[h][3])));
+                    const float zv = fmaf(P[h][4], A.x, fmaf(P[h][5], A.y, fmaf(P[h][6], A.z, P[h][7])));
+                    const float zz = fmaf(P[h][8], A.x, fmaf(P[h][9], A.y, fmaf(P[h][10], A.z, P[h][11])));
+                    // z <= 0 (or NaN) -> 1/0 = inf -> r2 inf/NaN -> min(., tau2) = tau2
+                    const float iz = rcp_approx(fmaxf(zz, 0.0f));
+                    const float du = fmaf(zu, iz, -Bq.x);
+                    const float dv = fmaf(zv, iz, -Bq.y);
+                    const float r2 = fmaf(du, du, dv * dv);
+                    part[h] = fmaf(A.w, fminf(r2, tau2), part[h]);
+                    if (COUNT) cnt[h] += (r2 < tau2) ? 1 : 0;
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < HT; ++h) acc[h] += part[h];
+            __syncthreads();
+        }
+
+        // combine the CS partial sums of each pose through distributed shared memory
+#pragma unroll
+        for (int h = 0; h < HT; ++h) {
+            s_part[h * THREADS + tid] = acc[h];
+            if (COUNT) s_cnt[h * THREADS + tid] = cnt[h];
+        }
+        cluster.sync();
+        const int per = TH / CS;
+        for (int e = rank * per + tid; e < (rank + 1) * per; e += THREADS) {
+            float sc = 0.f;
+            int ct = 0;
+            for (int r = 0; r < CS; ++r) {
+                sc += cluster.map_shared_rank(s_part, r)[e];
+                if (COUNT) ct += cluster.map_shared_rank(s_cnt, r)[e];
+            }
+            const int j = tile * TH + e;
+            const bool valid = j < nh;
+            uint32_t id = 0xffffffffu, rd = 0xffffffffu, sb = 0xffffffffu;
+            if (valid) {
+                id = static_cast<uint32_t>(d.compact[j]);
+                rd = static_cast<uint32_t>((id >> 2) / static_cast<uint32_t>(d.batch));
+                sb = __float_as_uint(sc);
+                if (d.score_by_id) d.score_by_id[id - slot_base] = sc;
+                if (COUNT && d.count_by_id) d.count_by_id[id - slot_base] = ct;
+            }
+            // per round, the minimum (score bits, pose id) of the warp, then one atomic
+            unsigned long long kv = valid ? ((static_cast<unsigned long long>(sb) << 32) | id) : ~0ull;
+            bool pending = valid;
+            while (__any_sync(0xffffffffu, pending)) {
+                const int first = __ffs(__ballot_sync(0xffffffffu, pending)) - 1;
+                const uint32_t r0 = __shfl_sync(0xffffffffu, rd, first);
+                unsigned long long v = (pending && rd == r0) ? kv : ~0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+                    v = u < v ? u : v;
+                }
+                if (lane == first) atomicMin(reinterpret_cast<unsigned long long*>(&d.round_best[r0]), v);
+                if (rd == r0) pending = false;
+            }
+        }
+        // s_part is rewritten only after the next item's first cluster barrier,
+        // which every CTA reaches after finishing the reads above.
+    }
+}
+
+// ============================================================================
+// k_replay: rounds in order, LO, termination, final refinement
+// ============================================================================
+constexpr int kRT = 512;
+constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
+
+enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
+
+struct ReplaySmem {
+    double R[9], t[3];    // current pose
+    double Rc[9], tc[3];  // candidate pose
+    double H[21], g[6];   // normal equations at the current pose
+    double cost, cnt;
+    double step;
+    double tot[32];
+    double xch[2][32];
+    float red[kRT / 32][32];
+    float P[12];
+    int flag;
+    QueryState st;
+};
+
+struct ReplayParams {
+    const QueryDesc* qd;
+    QueryState* qs;
+    const WaveQ* wq;
+    int32_t r0, r1;
+    int* err;
+};
+
+__device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], const double t[3]) {
+    for (int k = 0; k < 9; ++k) S.P[k] = static_cast<float>(R[k]);
+    for (int k = 0; k < 3; ++k) S.P[9 + k] = static_cast<float>(t[k]);
+}
+
+template <int MODE>
+__device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
+    constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
+    float acc[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) acc[k] = 0.f;
+    float Rm[9], tv[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rm[k] = S.P[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tv[k] = S.P[9 + k];
+    const float fx = d.fx, fy = d.fy, cx = d.cx, cy = d.cy, tau2 = d.tau2, c2 = d.cauchy2;
+    const int64_t n = kSub ? S.st.m : S.st.n;
+    const int64_t off = S.st.off;
+    for (int64_t i = static_cast<int64_t>(rank) * kRT + tid; i < n; i += static_cast<int64_t>(CL) * kRT) {
+        float X, Y, Z, w, x, y;
+        if (kSub) {
+            const float4* rec = reinterpret_cast<const float4*>(d.subset + i);
+            const float4 A = rec[0], B = rec[1];
+            X = A.x; Y = A.y; Z = A.z; w = A.w; x = B.x; y = B.y;
+        } else {
+            X = d.X[off + i]; Y = d.Y[off + i]; Z = d.Z[off + i]; w = d.w[off + i];
+            x = d.x[off + i]; y = d.y[off + i];
+        }
+        const float xc = fmaf(Rm[0], X, fmaf(Rm[1], Y, fmaf(Rm[2], Z, tv[0])));
+        const float yc = fmaf(Rm[3], X, fmaf(Rm[4], Y, fmaf(Rm[5], Z, tv[1])));
+        const float zc = fmaf(Rm[6], X, fmaf(Rm[7], Y, fmaf(Rm[8], Z, tv[2])));
+        const bool front = zc > 0.f;
+        float iz = 0.f, ru = 0.f, rv = 0.f, r2 = tau2;
+        if (front) {
+            iz = 1.0f / zc;
+            ru = fmaf(fx * xc, iz, cx) - x;
+            rv = fmaf(fy * yc, iz, cy) - y;
+            r2 = fmaf(ru, ru, rv * rv);
+        }
+        const bool inl = front && r2 < tau2;
+        float wt = 0.f;
+        if (MODE == kLO) {
+            acc[27] += w * (inl ? r2 : tau2);
+            wt = inl ? w : 0.f;
+            acc[28] += inl ? 1.f : 0.f;
+        } else if (MODE == kCountSub || MODE == kCountFull) {
+            acc[28] += inl ? 1.f : 0.f;
+            if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
+        } else {
+            bool in_set;
+            if (MODE == kFinInit) {
+                in_set = inl;
+                d.fixed[off + i] = inl ? 1 : 0;
+            } else {
+                in_set = d.fixed[off + i] != 0;
+            }
+            if (in_set) {
+                const float rr = front ? r2 : tau2;
+                acc[27] += w * c2 * log1pf(rr / c2);
+                acc[28] += 1.f;
+                wt = front ? w / (1.0f + r2 / c2) : 0.f;
+            }
+        }
+        if (kJac && wt > 0.f) {
+            const float dux = fx * iz, duz = -fx * xc * iz * iz;
+            const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
+            const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
+            const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
+            int k = 0;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const float wa = wt * Ju[a], wb = wt * Jv[a];
+#pragma unroll
+                for (int b = a; b < 6; ++b) acc[k++] += wa * Ju[b] + wb * Jv[b];
+                acc[21 + a] += wa * ru + wb * rv;
+            }
+        }
+    }
+    // block reduction (FP32 warp tree, FP64 across warps), then across the cluster in rank order
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) {
+        const float v = warp_sum(acc[k]);
+        if (lane == 0) S.red[warp][k] = v;
+    }
+    __syncthreads();
+    if (tid < kNV) {
+        double s = 0.0;
+        for (int w = 0; w < kRT / 32; ++w) s += static_cast<double>(S.red[w][tid]);
+        S.xch[slot][tid] = s;
+    }
+    cluster.sync();
+    if (tid < kNV) {
+        double s = 0.0;
+        for (int r = 0; r < CL; ++r) s += cluster.map_shared_rank(&S.xch[slot][0], r)[tid];
+        S.tot[tid] = s;
+    }
+    slot ^= 1;
+    __syncthreads();
+}
+
+__device__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
+    double A[6][6];
+    int k = 0;
+    for (int a = 0; a < 6; ++a)
+        for (int b = a; b < 6; ++b) {
+            A[a][b] = Hu[k];
+            A[b][a] = Hu[k];
+            ++k;
+        }
+    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a];
+    double L[6][6];
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i][j];
+            for (int c = 0; c < j; ++c) s -= L[i][c] * L[j][c];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                L[i][i] = sqrt(s);
+            } else {
+                L[i][j] = s / L[j][j];
+            }
+        }
+    double z[6];
+    for (int i = 0; i < 6; ++i) {
+        double s = -g[i];
+        for (int c = 0; c < i; ++c) s -= L[i][c] * z[c];
+        z[i] = s / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double s = z[i];
+        for (int c = i + 1; c < 6; ++c) s -= L[c][i] * x[c];
+        x[i] = s / L[i][i];
+    }
+    return true;
+}
+
+// candidate = Exp(dw) * (R, t) + (0, dv)
+__device__ void apply_step(const double R[9], const double t[3], const double dl[6], double Rc[9], double tc[3]) {
+    const double th2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+    const double th = sqrt(th2);
+    double A, B;
+    if (th < 1e-8) { A = 1.0 - th2 / 6.0; B = 0.5 - th2 / 24.0; }
+    else { double sn, cs; sincos(th, &sn, &cs); A = sn / th; B = (1.0 - cs) / th2; }
+    const double Kx[9] = {0, -dl[2], dl[1], dl[2], 0, -dl[0], -dl[1], dl[0], 0};
+    double E[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double k2 = 0.0;
+            for (int c = 0; c < 3; ++c) k2 += Kx[3 * i + c] * Kx[3 * c + j];
+            E[3 * i + j] = (i == j ? 1.0 : 0.0) + A * Kx[3 * i + j] + B * k2;
+        }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rc[3 * i + j] = E[3 * i] * R[j] + E[3 * i + 1] * R[3 + j] + E[3 * i + 2] * R[6 + j];
+        tc[i] = E[3 * i] * t[0] + E[3 * i + 1] * t[1] + E[3 * i + 2] * t[2] + dl[3 + i];
+    }
+}
+
+__device__ void take_totals(ReplaySmem& S) {
+    for (int k = 0; k < 21; ++k) S.H[k] = S.tot[k];
+    for (int k = 0; k < 6; ++k) S.g[k] = S.tot[21 + k];
+    S.cost = S.tot[27];
+    S.cnt = S.tot[28];
+}
+
+// Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
+template <int INIT, int ITER>
+__device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot,
+                             int iters) {
+    const int tid = threadIdx.x;
+    if (tid == 0) set_pass_pose(S, S.R, S.t);
+    __syncthreads();
+    pass<INIT>(S, d, cluster, rank, CL, slot);
+    if (tid == 0) take_totals(S);
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        if (S.cnt < 3.0) break;
+        bool accepted = false;
+        double mu = 0.0;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            if (tid == 0) {
+                double dl[6];
+                S.flag = solve6(S.H, S.g, mu, dl) ? 1 : 0;
+                if (S.flag) {
+                    apply_step(S.R, S.t, dl, S.Rc, S.tc);
+                    set_pass_pose(S, S.Rc, S.tc);
+                    double dn = 0.0;
+                    for (int k = 0; k < 6; ++k) dn += dl[k] * dl[k];
+                    S.step = sqrt(dn);
+                }
+            }
+            __syncthreads();
+            const bool solved = S.flag != 0;
+            __syncthreads();
+            if (solved) {
+                pass<ITER>(S, d, cluster, rank, CL, slot);
+                const bool better = S.tot[27] < S.cost;
+                __syncthreads();
+                if (better) {
+                    if (tid == 0) {
+                        for (int k = 0; k < 9; ++k) S.R[k] = S.Rc[k];
+                        for (int k = 0; k < 3; ++k) S.t[k] = S.tc[k];
+                        take_totals(S);
+                    }
+                    __syncthreads();
+                    accepted = true;
+                    break;
+                }
+            }
+            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
+        }
+        if (!accepted) break;
+        if (S.step < 1e-10) break;
+    }
+}
+
+__device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inliers) {
+    imloc_result r;
+    memset(&r, 0, sizeof(r));
+    for (int k = 0; k < 9; ++k) { r.R[k] = S.R[k]; r.R_best[k] = S.st.R[k]; }
+    for (int k = 0; k < 3; ++k) { r.t[k] = S.t[k]; r.t_best[k] = S.st.t[k]; }
+    r.score = S.st.have_best ? S.st.best_score : 0.0;
+    r.num_inliers = num_inliers;
+    r.subset_inliers = S.st.subset_inliers;
+    r.iterations = S.st.iters;
+    r.rounds = S.st.rounds_done;
+    r.lo_count = S.st.lo_count;
+    r.hypotheses = S.st.hypotheses;
+    r.best_hyp = S.st.best_hyp;
+    r.status = S.st.status;
+    if (d.result) *d.result = r;
+}
+
+__global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayParams p) {
+    __shared__ ReplaySmem S;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int q = blockIdx.x / CL;
+    const int tid = threadIdx.x;
+    const QueryDesc& d = p.qd[q];
+    if (tid == 0) S.st = p.qs[q];
+    __syncthreads();
+    if (S.st.finished) return;  // same decision in every CTA of the cluster
+    int slot = 0;
+    const int r_end = min(p.r1, d.rounds);
+    for (int r = p.r0; r < r_end; ++r) {
+        if (S.st.done) break;
+        const uint64_t key = d.round_best[r];
+        const int hyps_r = d.round_hyps[r];
+        bool improve = false;
+        float sc = 0.f;
+        if (key != ~0ull) {
+            sc = __uint_as_float(static_cast<uint32_t>(key >> 32));
+            improve = static_cast<double>(sc) < S.st.best_score;
+        }
+        __syncthreads();
+        if (improve) {
+            if (tid == 0) {
+                const uint32_t id = static_cast<uint32_t>(key & 0xffffffffu);
+                const PoseF ps = d.slots[static_cast<int64_t>(id) - 4 * p.wq[q].s_begin];
+                for (int k = 0; k < 9; ++k) S.R[k] = ps.R[k];
+                for (int k = 0; k < 3; ++k) S.t[k] = ps.t[k];
+                for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
+                for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
+                S.st.best_score = sc;
+                S.st.best_hyp = id;
+                S.st.have_best = 1;
+            }
+            __syncthreads();
+            if (d.lo_iters > 0) {
+                gauss_newton<kLO, kLO>(S, d, cluster, rank, CL, slot, d.lo_iters);
+                if (tid == 0) {
+                    ++S.st.lo_count;
+                    if (S.cost < S.st.best_score) {
+                        for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
+                        for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
+                        S.st.best_score = S.cost;
+                    }
+                    S.st.subset_inliers = static_cast<int32_t>(S.cnt);
+                }
+            } else {
+                if (tid == 0) set_pass_pose(S, S.st.R, S.st.t);
+                __syncthreads();
+                pass<kCountSub>(S, d, cluster, rank, CL, slot);
+                if (tid == 0) S.st.subset_inliers = static_cast<int32_t>(S.tot[28]);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int64_t it = min(static_cast<int64_t>(r + 1) * d.batch, static_cast<int64_t>(d.hyps));
+            S.st.iters = it;
+            S.st.rounds_done = r + 1;
+            S.st.hypotheses += hyps_r;
+            bool stop = it >= d.hyps;
+            if (!stop && d.p_miss > 0.0 && S.st.have_best && S.st.m > 0) {
+                const double eps = static_cast<double>(S.st.subset_inliers) / static_cast<double>(S.st.m);
+                const double e3 = eps * eps * eps;
+                double need;
+                if (e3 >= 1.0) need = 0.0;
+                else if (e3 <= 0.0) need = INFINITY;
+                else need = log(d.p_miss) / log(1.0 - e3);
+                stop = static_cast<double>(it) >= need;
+            }
+            if (stop) S.st.done = 1;
+        }
+        __syncthreads();
+    }
+    if (S.st.done && !S.st.finished) {
+        if (!S.st.have_best) {
+            if (tid == 0) {
+                if (S.st.status == IMLOC_OK) S.st.status = IMLOC_ERR_DEGENERATE;
+                for (int k = 0; k < 9; ++k) S.R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+                for (int k = 0; k < 3; ++k) S.t[k] = 0.0;
+                if (rank == 0) write_result(S, d, 0);
+                S.st.finished = 1;
+            }
+            __syncthreads();
+        } else {
+            if (tid == 0) {
+                for (int k = 0; k < 9; ++k) S.R[k] = S.st.R[k];
+                for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
+            }
+            __syncthreads();
+            if (d.final_iters > 0) gauss_newton<kFinInit, kFin>(S, d, cluster, rank, CL, slot, d.final_iters);
+            if (tid == 0) set_pass_pose(S, S.R, S.t);
+            __syncthreads();
+            pass<kCountFull>(S, d, cluster, rank, CL, slot);
+            if (tid == 0) {
+                if (rank == 0) write_result(S, d, static_cast<int64_t>(S.tot[28]));
+                S.st.finished = 1;
+            }
+            __syncthreads();
+        }
+    }
+    if (rank == 0 && tid == 0) p.qs[q] = S.st;
+    // no CTA may leave while another can still read its shared memory
+    cluster.sync();
+}
+
+// ============================================================================
+// host orchestration
+// ============================================================================
+struct HostQuery {
+    const float *x, *y, *X, *Y, *Z, *w;
+    const int64_t* d_off;
+    int32_t q_off;
+    const int32_t* d_count;
+    int64_t n_host;
+    int64_t n_cap;
+    uint8_t* mask;
+    uint8_t* fixed_base;  // fixed-set bytes at the same offsets as the correspondences (null: allocate)
+    imloc_result* d_result;
+    imloc_camera cam;
+    imloc_ransac_opts o;
+    // tests
+    const PoseF* inject;
+    int64_t n_inject;
+    float* score_by_id;
+    int32_t* count_by_id;
+    int32_t* triples;
+    PoseF* slots_out;
+    uint64_t* round_best_out;
+};
+
+struct Tuning {
+    int score_cluster;   // CTAs per (query, tile) item
+    int replay_cluster;  // CTAs per query in the replay
+};
+
+static Tuning pick_tuning(const imloc_ctx* ctx, int nq, int64_t total_hyp_estimate) {
+    Tuning t;
+    // few items: split each over more SMs; many: keep clusters small
+    const int64_t items = std::max<int64_t>(1, total_hyp_estimate / 512);
+    t.score_cluster = items >= 4 * ctx->sm_count ? 2 : (items >= ctx->sm_count ? 4 : 8);
+    t.replay_cluster = nq >= ctx->sm_count / 2 ? 1 : (nq >= ctx->sm_count / 8 ? 4 : 8);
+    return t;
+}
+
+template <typename K, typename P>
+static int launch_cluster(K kernel, const P& params, int grid, int block, size_t smem, int cluster, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IMLOC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, params));
+    return IMLOC_OK;
+}
+
+template <typename K>
+static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cluster * 64);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IMLOC_CUDA_TRY(cudaOccupancyMaxActiveClusters(out, kernel, &cfg));
+    return IMLOC_OK;
+}
+
+static int64_t comb3(int64_t m) { return m < 3 ? 0 : m * (m - 1) * (m - 2) / 6; }
+
+int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream, bool want_counts) {
+    constexpr int kThreads = 128, kHT = 4, kTH = kThreads * kHT;
+    if (nq <= 0) return IMLOC_ERR_INVALID_ARG;
+    // ---- per-query host-known sizes and the wave schedule ----
+    std::vector<int64_t> H(nq), B(nq), R(nq);
+    int64_t R_max = 0;
+    bool adaptive = false;
+    for (int q = 0; q < nq; ++q) {
+        const imloc_ransac_opts& o = hq[q].o;
+        if (!(o.tau_px > 0.0) || o.max_score_corr < 3 || o.batch <= 0 || o.max_iters <= 0 || o.lo_iters < 0 ||
+            o.final_iters < 0 || !(hq[q].cam.fx != 0.0f) || !(hq[q].cam.fy != 0.0f))
+            return IMLOC_ERR_INVALID_ARG;
+        if (!hq[q].x || !hq[q].y || !hq[q].X || !hq[q].Y || !hq[q].Z || !hq[q].w) return IMLOC_ERR_INVALID_ARG;
+        if (hq[q].inject) {
+            H[q] = hq[q].n_inject;
+            B[q] = std::min<int64_t>(o.batch, std::max<int64_t>(1, H[q]));
+        } else if (o.enumerate_all) {
+            if (hq[q].d_off || hq[q].d_count) return IMLOC_ERR_INVALID_ARG;  // needs a host-known N
+            const int64_t m = std::min<int64_t>(hq[q].n_host, o.max_score_corr);
+            H[q] = comb3(m);
+            if (H[q] > (int64_t(1) << 24)) return IMLOC_ERR_INVALID_ARG;
+            B[q] = std::max<int64_t>(1, H[q]);
+        } else {
+            H[q] = o.max_iters;
+            B[q] = o.batch;
+        }
+        if (H[q] <= 0) H[q] = 0;
+        R[q] = H[q] > 0 ? (H[q] + B[q] - 1) / B[q] : 0;
+        R_max = std::max(R_max, R[q]);
+        if (o.p_miss > 0.0 && !o.enumerate_all && !hq[q].inject) adaptive = true;
+    }
+    std::vector<std::pair<int64_t, int64_t>> waves;
+    if (!adaptive) {
+        waves.push_back({0, std::max<int64_t>(R_max, 1)});
+    } else {
+        int64_t r = 0, len = 1;
+        while (r < R_max) {
+            const int64_t e = std::min(R_max, r + len);
+            waves.push_back({r, e});
+            r = e;
+            if (waves.size() >= 2) len *= 2;
+        }
+        if (waves.empty()) waves.push_back({0, 1});
+    }
+    const int W = static_cast<int>(waves.size());
+    if ((hq[0].score_by_id || hq[0].count_by_id || hq[0].triples || hq[0].slots_out) && W != 1)
+        return IMLOC_ERR_INVALID_ARG;
+    std::vector<WaveQ> wq(static_cast<size_t>(W) * nq);
+    std::vector<int64_t> wprefix(static_cast<size_t>(W) * (nq + 1));
+    std::vector<int64_t> wtotal(W, 0);
+    std::vector<int64_t> max_wave_samples(nq, 0);
+    for (int w = 0; w < W; ++w) {
+        int64_t acc = 0;
+        for (int q = 0; q < nq; ++q) {
+            const int64_t sb = std::min(waves[w].first * B[q], H[q]);
+            const int64_t se = std::min(waves[w].second * B[q], H[q]);
+            WaveQ& x = wq[static_cast<size_t>(w) * nq + q];
+            x.s_begin = sb;
+            x.n_samples = static_cast<int32_t>(se - sb);
+            x.pad = 0;
+            wprefix[static_cast<size_t>(w) * (nq + 1) + q] = acc;
+            acc += se - sb;
+            max_wave_samples[q] = std::max(max_wave_samples[q], se - sb);
+        }
+        wprefix[static_cast<size_t>(w) * (nq + 1) + nq] = acc;
+        wtotal[w] = acc;
+    }
+
+    // ---- workspace ----
+    std::vector<QueryDesc> qd(nq);
+    int64_t est_hyp = 0;
+    for (int q = 0; q < nq; ++q) {
+        const HostQuery& h = hq[q];
+        const imloc_ransac_opts& o = h.o;
+        QueryDesc& d = qd[q];
+        memset(&d, 0, sizeof(d));
+        d.x = h.x; d.y = h.y; d.X = h.X; d.Y = h.Y; d.Z = h.Z; d.w = h.w;
+        d.d_off = h.d_off; d.q_off = h.q_off; d.d_count = h.d_count; d.n_host = h.n_host;
+        d.mask = h.mask;
+        d.result = h.d_result;
+        d.fx = h.cam.fx; d.fy = h.cam.fy; d.cx = h.cam.cx; d.cy = h.cam.cy;
+        d.tau2 = static_cast<float>(o.tau_px * o.tau_px);
+        const double cs = o.cauchy_scale > 0.0 ? o.cauchy_scale : o.tau_px;
+        d.cauchy2 = static_cast<float>(cs * cs);
+        d.m_cap = o.max_score_corr;
+        d.batch = static_cast<int32_t>(B[q]);
+        d.hyps = static_cast<int32_t>(H[q]);
+        d.rounds = static_cast<int32_t>(R[q]);
+        d.lo_iters = o.lo_iters;
+        d.final_iters = o.final_iters;
+        d.polish = o.p3p_fp64_polish;
+        d.enumerate_all = o.enumerate_all;
+        d.p_miss = o.p_miss;
+        d.seed = o.seed;
+        d.query_id = o.query_id;
+        d.n_cap = static_cast<int32_t>(std::min<int64_t>(h.n_cap, INT32_MAX));
+        d.inject = h.inject ? 1 : 0;
+        const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
+        d.subset = static_cast<ScoreCorr*>(ws_alloc(ctx, sizeof(ScoreCorr) * std::max(1, o.max_score_corr)));
+        if (h.slots_out) d.slots = h.slots_out;
+        else d.slots = static_cast<PoseF*>(ws_alloc(ctx, sizeof(PoseF) * slots));
+        d.compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * slots));
+        if (h.round_best_out) d.round_best = h.round_best_out;
+        else d.round_best = static_cast<uint64_t*>(ws_alloc(ctx, sizeof(uint64_t) * std::max<int64_t>(1, R[q])));
+        d.round_hyps = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(1, R[q])));
+        d.score_by_id = h.score_by_id;
+        d.count_by_id = h.count_by_id;
+        d.triples = h.triples;
+        if (!d.subset || !d.slots || !d.compact || !d.round_best || !d.round_hyps) return IMLOC_ERR_OOM;
+        est_hyp += h.inject ? H[q] : (H[q] * 3) / 2;
+    }
+    // fixed-set bytes: share one buffer per concatenated correspondence set
+    for (int q = 0; q < nq; ++q) {
+        if (hq[q].fixed_base) { qd[q].fixed = hq[q].fixed_base; continue; }
+        bool shared = false;
+        for (int p = 0; p < q; ++p)
+            if (hq[p].X == hq[q].X && hq[p].d_off && hq[p].d_off == hq[q].d_off) { qd[q].fixed = qd[p].fixed; shared = true; break; }
+        if (!shared) {
+            qd[q].fixed = static_cast<uint8_t*>(ws_alloc(ctx, std::max<int64_t>(1, hq[q].n_cap)));
+            if (!qd[q].fixed) return IMLOC_ERR_OOM;
+        }
+    }
+    const size_t qd_bytes = sizeof(QueryDesc) * nq, wq_bytes = sizeof(WaveQ) * wq.size(),
+                 wp_bytes = sizeof(int64_t) * wprefix.size();
+    char* h_blk = static_cast<char*>(staging_alloc(ctx, qd_bytes + wq_bytes + wp_bytes + 512));
+    char* d_blk = static_cast<char*>(ws_alloc(ctx, qd_bytes + wq_bytes + wp_bytes + 512));
+    QueryState* d_qs = static_cast<QueryState*>(ws_alloc(ctx, sizeof(QueryState) * nq));
+    int32_t* d_nhyp = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * W * nq));
+    int32_t* d_tiles = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * (nq + 1)));
+    uint32_t* d_counter = static_cast<uint32_t*>(ws_alloc(ctx, sizeof(uint32_t)));
+    if (!h_blk || !d_blk || !d_qs || !d_nhyp || !d_tiles || !d_counter) return IMLOC_ERR_OOM;
+    const size_t o_wq = align_up(qd_bytes, 256), o_wp = align_up(o_wq + wq_bytes, 256);
+    memcpy(h_blk, qd.data(), qd_bytes);
+    memcpy(h_blk + o_wq, wq.data(), wq_bytes);
+    memcpy(h_blk + o_wp, wprefix.data(), wp_bytes);
+    int rc = upload(ctx, d_blk, h_blk, o_wp + wp_bytes, stream);
+    if (rc != IMLOC_OK) return rc;
+    const QueryDesc* d_qd = reinterpret_cast<const QueryDesc*>(d_blk);
+    const WaveQ* d_wq = reinterpret_cast<const WaveQ*>(d_blk + o_wq);
+    const int64_t* d_wp = reinterpret_cast<const int64_t*>(d_blk + o_wp);
+
+    // injected poses go straight into the slots (one pose per sample)
+    for (int q = 0; q < nq; ++q)
+        if (hq[q].inject) {
+            // slot of pose id 4 s is 4 s (single wave)
+            IMLOC_CUDA_TRY(cudaMemcpy2DAsync(qd[q].slots, 4 * sizeof(PoseF), hq[q].inject, sizeof(PoseF), sizeof(PoseF),
+                                             hq[q].n_inject, cudaMemcpyDeviceToDevice, stream));
+        }
+
+    // ---- launches ----
+    const Tuning tn = pick_tuning(ctx, nq, est_hyp);
+    {
+        SetupParams sp{d_qd, d_qs, d_nhyp, W * nq};
+        k_setup<<<nq, 256, 0, stream>>>(sp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+    }
+    auto score_kernel = want_counts ? k_score<kThreads, kHT, true> : k_score<kThreads, kHT, false>;
+    const size_t score_smem = sizeof(ScoreCorr) * 2 * kChunk + sizeof(float) * kTH + sizeof(int) * kTH;
+    if (tn.score_cluster > 8 || tn.replay_cluster > 8) {
+        IMLOC_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+        IMLOC_CUDA_TRY(cudaFuncSetAttribute(k_replay, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    }
+    int n_clusters = 0;
+    rc = max_clusters(score_kernel, kThreads, score_smem, tn.score_cluster, &n_clusters);
+    if (rc != IMLOC_OK) return rc;
+    n_clusters = std::max(1, n_clusters);
+    for (int w = 0; w < W; ++w) {
+        const WaveQ* wq_w = d_wq + static_cast<size_t>(w) * nq;
+        int32_t* nh_w = d_nhyp + static_cast<size_t>(w) * nq;
+        if (wtotal[w] > 0) {
+            SampleParams sp{d_qd, d_qs, wq_w, d_wp + static_cast<size_t>(w) * (nq + 1), nh_w, wtotal[w], nq};
+            const int64_t blocks = (wtotal[w] + 127) / 128;
+            k_sample_p3p<<<static_cast<unsigned>(blocks), 128, 0, stream>>>(sp);
+            IMLOC_CUDA_TRY(cudaGetLastError());
+        }
+        TilesParams tp{d_qs, nh_w, d_tiles, d_counter, nq, kTH};
+        k_tiles<<<1, 1024, 0, stream>>>(tp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+        ScoreParams scp{d_qd, d_qs, wq_w, nh_w, d_tiles, d_counter, nq, ctx->d_err};
+        const int64_t max_items = std::max<int64_t>(1, (wtotal[w] * 4 + kTH - 1) / kTH + nq);
+        const int grid_clusters = static_cast<int>(std::min<int64_t>(n_clusters, max_items));
+        rc = launch_cluster(score_kernel, scp, grid_clusters * tn.score_cluster, kThreads, score_smem, tn.score_cluster,
+                            stream);
+        if (rc != IMLOC_OK) return rc;
+        ReplayParams rp{d_qd, d_qs, wq_w, static_cast<int32_t>(waves[w].first), static_cast<int32_t>(waves[w].second),
+                        ctx->d_err};
+        rc = launch_cluster(k_replay, rp, nq * tn.replay_cluster, kRT, 0, tn.replay_cluster, stream);
+        if (rc != IMLOC_OK) return rc;
+    }
+    ctx->last_stream = stream;
+    return IMLOC_OK;
+}
+
+}  // namespace imloc
+
+// ============================================================================
+// C ABI
+// ============================================================================
+using imloc::HostQuery;
+
+static void fill_hostquery_from_corr(HostQuery& h, const imloc_corr* corr) {
+    memset(&h, 0, sizeof(h));
+    h.x = corr->x; h.y = corr->y; h.X = corr->X; h.Y = corr->Y; h.Z = corr->Z; h.w = corr->w;
+    h.d_count = corr->count;
+    h.n_host = corr->capacity;
+    h.n_cap = corr->capacity;
+}
+
+extern "C" {
+
+int imloc_ransac_pnp(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam, const imloc_ransac_opts* opts,
+                     imloc_result* out, uint8_t* d_inlier_mask, void* stream) {
+    if (!ctx || !corr || !qcam || !opts || !out) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = imloc::begin_call(ctx);
+    if (rc != IMLOC_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    imloc_result* d_res = static_cast<imloc_result*>(imloc::ws_alloc(ctx, sizeof(imloc_result)));
+    if (!d_res) return IMLOC_ERR_OOM;
+    HostQuery h;
+    fill_hostquery_from_corr(h, corr);
+    h.mask = d_inlier_mask;
+    h.d_result = d_res;
+    h.cam = *qcam;
+    h.o = *opts;
+    rc = imloc::ransac_impl(ctx, 1, &h, st, false);
+    if (rc != IMLOC_OK) return rc;
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(out, d_res, sizeof(imloc_result), cudaMemcpyDeviceToHost, st));
+    IMLOC_CUDA_TRY(cudaStreamSynchronize(st));
+    return out->status == IMLOC_OK ? IMLOC_OK : out->status;
+}
+
+int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_corr* corr, const int64_t* d_offsets,
+                                 const imloc_camera* qcams, const imloc_ransac_opts* opts, imloc_result* d_results,
+                                 uint8_t* d_masks, void* stream) {
+    if (!ctx || !corr || !d_offsets || !qcams || !opts || !d_results || n_queries <= 0) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = imloc::begin_call(ctx);
+    if (rc != IMLOC_OK) return rc;
+    std::vector<HostQuery> hq(n_queries);
+    for (int q = 0; q < n_queries; ++q) {
+        fill_hostquery_from_corr(hq[q], corr);
+        hq[q].d_count = nullptr;
+        hq[q].d_off = d_offsets;
+        hq[q].q_off = q;
+        hq[q].mask = d_masks;
+        hq[q].d_result = d_results + q;
+        hq[q].cam = qcams[q];
+        hq[q].o = opts[q];
+    }
+    return imloc::ransac_impl(ctx, n_queries, hq.data(), static_cast<cudaStream_t>(stream), false);
+}
+
+int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam,
+                         const imloc_ransac_opts* opts, const imloc_debug* dbg, imloc_result* out,
+                         uint8_t* d_inlier_mask, void* stream) {
+    if (!ctx || !corr || !qcam || !opts || !out || !dbg) return IMLOC_ERR_INVALID_ARG;
+    if (opts->p_miss > 0.0) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    int rc = imloc::begin_call(ctx);
+    if (rc != IMLOC_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    imloc_result* d_res = static_cast<imloc_result*>(imloc::ws_alloc(ctx, sizeof(imloc_result)));
+    if (!d_res) return IMLOC_ERR_OOM;
+    HostQuery h;
+    fill_hostquery_from_corr(h, corr);
+    h.d_count = nullptr;
+    h.mask = d_inlier_mask;
+    h.d_result = d_res;
+    h.cam = *qcam;
+    h.o = *opts;
+    h.inject = reinterpret_cast<const imloc::PoseF*>(dbg->inject_poses);
+    h.n_inject = dbg->inject_poses ? dbg->n_inject : 0;
+    if (dbg->inject_poses && dbg->n_inject <= 0) return IMLOC_ERR_INVALID_ARG;
+    h.score_by_id = dbg->scores;
+    h.count_by_id = dbg->counts;
+    h.triples = dbg->triples;
+    h.slots_out = reinterpret_cast<imloc::PoseF*>(dbg->poses);
+    h.round_best_out = dbg->round_best;
+    rc = imloc::ransac_impl(ctx, 1, &h, st, dbg->counts != nullptr);
+    if (rc != IMLOC_OK) return rc;
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(out, d_res, sizeof(imloc_result), cudaMemcpyDeviceToHost, st));
+    IMLOC_CUDA_TRY(cudaStreamSynchronize(st));
+    return IMLOC_OK;
+}
+
+}  // extern "C"

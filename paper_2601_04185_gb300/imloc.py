@@ -1,0 +1,309 @@
+"""Thin Python binding of ``libimloc.so`` (C ABI in ``include/imloc.h``).
+
+Argument marshalling only: every step of the localization path runs in the
+CUDA kernels of the library.  PyTorch provides device memory and streams.
+There is no fallback: if the library is missing or no CUDA device is present
+the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libimloc.so")
+
+IMLOC_OK = 0
+IMLOC_PENDING = 1
+STATUS = {0: "ok", 1: "pending", -1: "invalid argument", -2: "out of workspace memory", -3: "rejected",
+          -4: "timeout", -5: "cuda error", -6: "not found", -7: "degenerate", -8: "capacity"}
+
+
+class Camera(C.Structure):
+    _fields_ = [("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float), ("cy", C.c_float),
+                ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class Pose(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class View(C.Structure):
+    _fields_ = [("depth", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32), ("pitch", C.c_int64),
+                ("cam", Camera), ("pose", Pose)]
+
+
+class Segment(C.Structure):
+    _fields_ = [("begin", C.c_int64), ("view", C.c_int32), ("direction", C.c_int32)]
+
+
+class Matches(C.Structure):
+    _fields_ = [("q_u", C.c_void_p), ("q_v", C.c_void_p), ("db_u", C.c_void_p), ("db_v", C.c_void_p),
+                ("conf", C.c_void_p), ("n", C.c_int64), ("segments", C.POINTER(Segment)), ("n_segments", C.c_int32)]
+
+
+class Corr(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("X", C.c_void_p), ("Y", C.c_void_p), ("Z", C.c_void_p),
+                ("w", C.c_void_p), ("src", C.c_void_p), ("count", C.c_void_p), ("capacity", C.c_int64)]
+
+
+class RansacOpts(C.Structure):
+    _fields_ = [("tau_px", C.c_double), ("max_score_corr", C.c_int32), ("batch", C.c_int32),
+                ("max_iters", C.c_int32), ("lo_iters", C.c_int32), ("p_miss", C.c_double),
+                ("final_iters", C.c_int32), ("p3p_fp64_polish", C.c_int32), ("cauchy_scale", C.c_double),
+                ("seed", C.c_uint64), ("query_id", C.c_uint32), ("enumerate_all", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("R_best", C.c_double * 9), ("t_best", C.c_double * 3),
+                ("score", C.c_double), ("num_inliers", C.c_int64), ("subset_inliers", C.c_int64),
+                ("iterations", C.c_int64), ("rounds", C.c_int64), ("lo_count", C.c_int64), ("hypotheses", C.c_int64),
+                ("best_hyp", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Debug(C.Structure):
+    _fields_ = [("triples", C.c_void_p), ("poses", C.c_void_p), ("scores", C.c_void_p), ("counts", C.c_void_p),
+                ("round_best", C.c_void_p), ("inject_poses", C.c_void_p), ("n_inject", C.c_int64)]
+
+
+# every symbol declared in include/imloc.h and include/imloc_testing.h
+EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda_error", "imloc_device_error",
+           "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
+           "imloc_ransac_pnp_batch_async", "imloc_testing_ransac"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libimloc.so and declare the signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    L = C.CDLL(path)
+    P, V = C.POINTER, C.c_void_p
+    L.imloc_create.argtypes = [P(V), C.c_int, C.c_size_t]
+    L.imloc_destroy.argtypes = [V]
+    L.imloc_destroy.restype = None
+    L.imloc_status_str.argtypes = [C.c_int]
+    L.imloc_status_str.restype = C.c_char_p
+    L.imloc_last_cuda_error.argtypes = []
+    L.imloc_last_cuda_error.restype = C.c_char_p
+    L.imloc_device_error.argtypes = [V]
+    L.imloc_lift_async.argtypes = [V, P(View), C.c_int32, P(Matches), P(Corr), V]
+    L.imloc_lift_batch_async.argtypes = [V, C.c_int32, P(C.c_int64), P(View), C.c_int32, P(Matches), P(Corr), V, V]
+    L.imloc_ransac_default_opts.argtypes = [P(RansacOpts)]
+    L.imloc_ransac_default_opts.restype = None
+    L.imloc_ransac_pnp.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Result), V, V]
+    L.imloc_ransac_pnp_batch_async.argtypes = [V, C.c_int32, P(Corr), V, P(Camera), P(RansacOpts), V, V, V]
+    L.imloc_testing_ransac.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Debug), P(Result), V, V]
+    _lib = L
+    return L
+
+
+class ImlocError(RuntimeError):
+    pass
+
+
+def _check(rc, what):
+    if rc != IMLOC_OK:
+        msg = load().imloc_status_str(rc).decode()
+        if rc == -5:
+            msg += ": " + load().imloc_last_cuda_error().decode()
+        raise ImlocError(f"{what}: {msg} ({rc})")
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_opts(**kw) -> RansacOpts:
+    o = RansacOpts()
+    load().imloc_ransac_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def camera(K, width=0, height=0) -> Camera:
+    fx, fy, cx, cy = [float(a) for a in K]
+    return Camera(fx, fy, cx, cy, int(width), int(height))
+
+
+def result_dict(r: Result) -> dict:
+    return dict(R=np.array(r.R).reshape(3, 3), t=np.array(r.t), R_best=np.array(r.R_best).reshape(3, 3),
+                t_best=np.array(r.t_best), score=r.score, num_inliers=r.num_inliers,
+                subset_inliers=r.subset_inliers, iterations=r.iterations, rounds=r.rounds, lo_count=r.lo_count,
+                hypotheses=r.hypotheses, best_hyp=r.best_hyp, status=r.status)
+
+
+def alloc_corr(capacity: int, device="cuda"):
+    """Device buffers of a correspondence set (structure of arrays)."""
+    torch = _torch()
+    cap = max(int(capacity), 1)
+    out = {k: torch.empty(cap, dtype=torch.float32, device=device) for k in ("x", "y", "X", "Y", "Z", "w")}
+    out["src"] = torch.empty(cap, dtype=torch.int32, device=device)
+    out["count"] = torch.zeros(1, dtype=torch.int32, device=device)
+    out["capacity"] = int(capacity)
+    return out
+
+
+def corr_from_arrays(x, y, X, w, device="cuda"):
+    """Upload a host correspondence set (float32) into device buffers."""
+    torch = _torch()
+    X = np.asarray(X, dtype=np.float32).reshape(-1, 3)
+    n = len(X)
+    c = alloc_corr(n, device)
+    for k, a in (("x", x), ("y", y), ("X", X[:, 0]), ("Y", X[:, 1]), ("Z", X[:, 2]), ("w", w)):
+        if n:
+            c[k][:n].copy_(torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)))
+    c["count"].fill_(n)
+    return c
+
+
+def _corr_struct(c, capacity=None) -> Corr:
+    return Corr(*[_ptr(c[k]) for k in ("x", "y", "X", "Y", "Z", "w", "src")], _ptr(c.get("count")),
+                int(c["capacity"] if capacity is None else capacity))
+
+
+def _views_struct(views):
+    arr = (View * len(views))()
+    for i, v in enumerate(views):
+        d = v["depth"]
+        arr[i].depth = d.data_ptr()
+        arr[i].height, arr[i].width = int(d.shape[0]), int(d.shape[1])
+        arr[i].pitch = int(d.stride(0))
+        arr[i].cam = Camera(float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"]), int(d.shape[1]),
+                            int(d.shape[0]))
+        arr[i].pose.R[:] = [float(a) for a in np.asarray(v["R"], dtype=np.float64).ravel()]
+        arr[i].pose.t[:] = [float(a) for a in np.asarray(v["t"], dtype=np.float64).ravel()]
+    return arr
+
+
+def _matches_struct(m):
+    seg_off = np.asarray(m["seg_off"], dtype=np.int64)
+    n_seg = len(seg_off) - 1
+    segs = (Segment * max(n_seg, 1))()
+    for s in range(n_seg):
+        segs[s].begin = int(seg_off[s])
+        segs[s].view = int(m["seg_view"][s])
+        segs[s].direction = int(m["seg_dir"][s])
+    n = int(seg_off[-1]) if n_seg > 0 else 0
+    st = Matches(*[_ptr(m[k]) for k in ("q_u", "q_v", "db_u", "db_v", "conf")], n, segs, n_seg)
+    return st, segs
+
+
+class Context:
+    """One libimloc context (device workspace) bound to a CUDA device."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.lib = load()
+        h = C.c_void_p()
+        _check(self.lib.imloc_create(C.byref(h), int(device), int(workspace_bytes)), "imloc_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.imloc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_error(self):
+        return self.lib.imloc_device_error(self.h)
+
+    # ---- lifting ----
+    def lift(self, views, matches, out=None, stream=None):
+        """views: list of dicts (depth: cuda float32 HxW tensor, fx, fy, cx, cy, R, t);
+        matches: dict of cuda float32 tensors q_u, q_v, db_u, db_v, conf plus host seg_off, seg_view, seg_dir."""
+        vs = _views_struct(views)
+        ms, keep = _matches_struct(matches)
+        if out is None:
+            out = alloc_corr(ms.n, matches["q_u"].device)
+        cs = _corr_struct(out)
+        _check(self.lib.imloc_lift_async(self.h, vs, len(views), C.byref(ms), C.byref(cs), _stream(stream)),
+               "imloc_lift_async")
+        return out
+
+    def lift_batch(self, query_begin, views, matches, out=None, offsets=None, stream=None):
+        torch = _torch()
+        vs = _views_struct(views)
+        ms, keep = _matches_struct(matches)
+        qb = np.ascontiguousarray(query_begin, dtype=np.int64)
+        nq = len(qb) - 1
+        dev = matches["q_u"].device
+        if out is None:
+            out = alloc_corr(ms.n, dev)
+        if offsets is None:
+            offsets = torch.zeros(nq + 1, dtype=torch.int64, device=dev)
+        cs = _corr_struct(out)
+        _check(self.lib.imloc_lift_batch_async(self.h, nq, qb.ctypes.data_as(C.POINTER(C.c_int64)), vs, len(views),
+                                               C.byref(ms), C.byref(cs), _ptr(offsets), _stream(stream)),
+               "imloc_lift_batch_async")
+        return out, offsets
+
+    # ---- RANSAC ----
+    def ransac_pnp(self, corr, K, opts=None, n=None, mask=None, stream=None):
+        """corr: device buffers (alloc_corr / corr_from_arrays / lift output); N from corr['count']
+        unless `n` is given.  Returns a result dict (host)."""
+        o = opts if opts is not None else default_opts()
+        cs = _corr_struct(corr)
+        if n is not None:
+            cs.count = None
+            cs.capacity = int(n)
+        res = Result()
+        rc = self.lib.imloc_ransac_pnp(self.h, C.byref(cs), C.byref(camera(K)), C.byref(o), C.byref(res),
+                                       _ptr(mask), _stream(stream))
+        if rc not in (IMLOC_OK, -7):
+            _check(rc, "imloc_ransac_pnp")
+        return result_dict(res)
+
+    def ransac_pnp_batch_async(self, corr, offsets, Ks, opts, results, masks=None, stream=None):
+        """results: cuda uint8 tensor of n_queries * sizeof(Result) bytes (see RESULT_BYTES)."""
+        nq = len(Ks)
+        cams = (Camera * nq)(*[camera(K) for K in Ks])
+        oarr = (RansacOpts * nq)(*opts)
+        cs = _corr_struct(corr)
+        _check(self.lib.imloc_ransac_pnp_batch_async(self.h, nq, C.byref(cs), _ptr(offsets), cams, oarr,
+                                                     _ptr(results), _ptr(masks), _stream(stream)),
+               "imloc_ransac_pnp_batch_async")
+
+    def testing_ransac(self, corr, K, opts, n, debug: dict, mask=None, stream=None):
+        cs = _corr_struct(corr, capacity=n)
+        cs.count = None
+        dbg = Debug(_ptr(debug.get("triples")), _ptr(debug.get("poses")), _ptr(debug.get("scores")),
+                    _ptr(debug.get("counts")), _ptr(debug.get("round_best")), _ptr(debug.get("inject_poses")),
+                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0)
+        res = Result()
+        _check(self.lib.imloc_testing_ransac(self.h, C.byref(cs), C.byref(camera(K)), C.byref(opts), C.byref(dbg),
+                                             C.byref(res), _ptr(mask), _stream(stream)), "imloc_testing_ransac")
+        return result_dict(res)
+
+
+RESULT_BYTES = C.sizeof(Result)
+
+
+def results_from_bytes(buf: np.ndarray, nq: int):
+    """Decode `nq` device results copied to host as bytes."""
+    arr = (Result * nq).from_buffer_copy(np.ascontiguousarray(buf).tobytes())
+    return [result_dict(arr[i]) for i in range(nq)]

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every function that include/*.h
+declares; host-only entry points behave as documented (no GPU needed)."""
+import ctypes as C
+import glob
+import os
+import re
+
+import pytest
+
+import __graft_entry__
+from paper_2601_04185_gb300 import imloc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"\b(imloc_[a-z0-9_]+)\s*\(", src):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return imloc.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "imloc_lift_async" in names and "imloc_ransac_pnp" in names
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert names <= set(imloc.EXPORTS)
+
+
+def test_struct_sizes_match_the_header_layout():
+    assert C.sizeof(imloc.RansacOpts) == 64
+    assert C.sizeof(imloc.Result) == 264
+    assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96
+    assert C.sizeof(imloc.Corr) == 8 * 9
+    assert C.sizeof(imloc.Segment) == 16
+
+
+def test_default_options_are_the_papers_constants(lib):
+    o = imloc.default_opts()
+    assert o.max_score_corr == 10000   # uniform subsampling to at most 10K (Sec. 3.3)
+    assert o.batch == 1024             # batches of 1K minimal sets (Sec. 3.3)
+    assert o.max_iters == 100000       # stop after 100K iterations (Sec. 3.3)
+    assert o.p_miss == 1e-4            # or P(missing the best model) < 1e-4 (Sec. 3.3)
+    assert o.tau_px == 4.0 and o.p3p_fp64_polish == 1
+
+
+def test_status_strings(lib):
+    for code in (0, 1, -1, -2, -3, -4, -5, -6, -7, -8):
+        assert lib.imloc_status_str(code).decode()
+    assert lib.imloc_status_str(-7).decode().startswith("degenerate")
+
+
+def test_null_arguments_are_rejected_without_a_device(lib):
+    assert lib.imloc_create(None, 0, 0) == -1
+    assert lib.imloc_lift_async(None, None, 0, None, None, None) == -1
+    assert lib.imloc_ransac_pnp(None, None, None, None, None, None, None) == -1
+    lib.imloc_destroy(None)

@@ -1,0 +1,351 @@
+"""GPU LO-RANSAC PnP (through the C ABI) against the FP64 oracle, step by step
+and end to end.
+
+Bars:
+  minimal-sample indices      bit-exact (integer Philox arithmetic);
+  P3P poses                   per solution |R - R'|_F <= 1e-4 and
+                              |t - t'| <= 1e-4 max(1, |t'|), matched as sets;
+                              100% on well-conditioned triples;
+  per-pose score              1e-5 relative (float32 sums of <= 10^4 terms);
+  per-pose inlier count       exact except points within 1e-3 px of tau;
+  final pose                  0.05 deg and 5 mm;
+  inlier mask                 identical except points within 1e-3 px of tau
+                              under the final pose.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2601_04185_gb300 import imloc, synth
+
+from gpu_helpers import (centre, lifted_to_host, matches_to_device, pose_close, residuals, rot_deg, torch,
+                         views_to_device)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = imloc.Context(0, 1 << 30)
+    yield c
+    c.close()
+
+
+def debug_buffers(H, R_rounds, with_counts=True):
+    t = torch()
+    d = dict(triples=t.full((3 * H,), -2, dtype=t.int32, device="cuda"),
+             poses=t.zeros((4 * H, 12), dtype=t.float32, device="cuda"),
+             scores=t.full((4 * H,), float("nan"), dtype=t.float32, device="cuda"),
+             round_best=t.zeros((max(R_rounds, 1),), dtype=t.int64, device="cuda"))
+    if with_counts:
+        d["counts"] = t.full((4 * H,), -1, dtype=t.int32, device="cuda")
+    return d
+
+
+def run_debug(ctx, q, H, batch=1024, **kw):
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    n = len(q["x"])
+    opts = imloc.default_opts(max_iters=H, batch=batch, p_miss=0.0, **kw)
+    dbg = debug_buffers(H, (H + batch - 1) // batch)
+    mask = torch().zeros(max(n, 1), dtype=torch().uint8, device="cuda")
+    res = ctx.testing_ransac(c, q["K"], opts, n, dbg, mask=mask)
+    host = {k: v.cpu().numpy() for k, v in dbg.items()}
+    host["mask"] = mask[:n].cpu().numpy().astype(bool)
+    return res, host
+
+
+@pytest.fixture(scope="module")
+def c1_run(ctx):
+    q = synth.config1(0)
+    res, dbg = run_debug(ctx, q, q["hypotheses"])
+    return q, res, dbg
+
+
+def bearings(q, idx):
+    fx, fy, cx, cy = q["K"]
+    x = q["x"][idx].astype(np.float64)
+    y = q["y"][idx].astype(np.float64)
+    b = np.stack([(x - cx) / fx, (y - cy) / fy, np.ones_like(x)], 1)
+    return b / np.linalg.norm(b, axis=1, keepdims=True)
+
+
+def test_minimal_samples_bit_exact(c1_run):
+    q, res, dbg = c1_run
+    n = len(q["x"])
+    m = min(n, 10000)
+    tri = dbg["triples"].reshape(-1, 3)
+    assert tri.shape[0] == q["hypotheses"]
+    for s in range(q["hypotheses"]):
+        want, att = oracle.sample(0, 0, s, m)
+        if want is None:
+            assert list(tri[s]) == [-1, -1, -1]
+        else:
+            assert list(tri[s]) == list(want), s
+
+
+def test_minimal_samples_full_size_sampled(ctx):
+    """Full-size subset (M = 10,000) in the launch configuration of the
+    benchmark, sampled sample ids checked one by one against the oracle."""
+    rng = np.random.default_rng(12)
+    q = synth.direct_query(rng, 50000, 0.3, 1024, 768, 800.0)
+    H = 10000
+    res, dbg = run_debug(ctx, q, H)
+    tri = dbg["triples"].reshape(-1, 3)
+    for s in list(range(0, H, 97)) + [H - 1]:
+        want, _ = oracle.sample(0, 0, s, 10000)
+        assert list(tri[s]) == list(want)
+    assert res["status"] == 0
+
+
+def solution_condition(y, X, lam):
+    """Smallest / largest singular value of the Jacobian of the three distance
+    equations at a solution: small values mark near-degenerate triples."""
+    b12, b13, b23 = y[0] @ y[1], y[0] @ y[2], y[1] @ y[2]
+    L = lam
+    J = np.array([[2 * (L[0] - b12 * L[1]), 2 * (L[1] - b12 * L[0]), 0],
+                  [2 * (L[0] - b13 * L[2]), 0, 2 * (L[2] - b13 * L[0])],
+                  [0, 2 * (L[1] - b23 * L[2]), 2 * (L[2] - b23 * L[1])]])
+    s = np.linalg.svd(J, compute_uv=False)
+    return s[-1] / s[0]
+
+
+def test_p3p_poses_against_oracle(c1_run):
+    q, res, dbg = c1_run
+    n = len(q["x"])
+    tri = dbg["triples"].reshape(-1, 3)
+    poses = dbg["poses"].reshape(-1, 4, 12)
+    scores = dbg["scores"].reshape(-1, 4)
+    matched = total = well = well_matched = 0
+    extra = 0
+    for s in range(q["hypotheses"]):
+        if tri[s][0] < 0:
+            continue
+        idx = tri[s]  # subset == full set here (N <= 10K)
+        y = bearings(q, idx)
+        X = q["X"][idx].astype(np.float64)
+        sols = oracle.p3p(y, X)
+        gpu = [(poses[s, k, :9].reshape(3, 3).astype(np.float64), poses[s, k, 9:].astype(np.float64))
+               for k in range(4) if not np.isnan(scores[s, k])]
+        for Ro, to, lam in sols:
+            total += 1
+            cond = solution_condition(y, X, lam)
+            close = min([min(abs(l - lam[0]) for l in [o[2][0] for o in sols if o[2] is not lam] + [np.inf])]) / lam[0]
+            ok = any(np.linalg.norm(Rg - Ro) <= 1e-4 and np.linalg.norm(tg - to) <= 1e-4 * max(1.0, np.linalg.norm(to))
+                     for Rg, tg in gpu)
+            matched += ok
+            if cond > 1e-2 and close > 1e-2:
+                well += 1
+                well_matched += ok
+        # every GPU pose must be a true solution too
+        for Rg, tg in gpu:
+            if not any(np.linalg.norm(Rg - Ro) <= 1e-3 for Ro, _, _ in sols):
+                extra += 1
+    assert total > 1000
+    assert well_matched == well, (well_matched, well)
+    assert matched >= 0.995 * total, (matched, total)
+    assert extra <= 0.005 * total
+
+
+def test_scores_and_counts_against_oracle(c1_run):
+    q, res, dbg = c1_run
+    corr = oracle.Corr(q["x"], q["y"], q["X"], q["w"])
+    poses = dbg["poses"]
+    scores = dbg["scores"]
+    counts = dbg["counts"]
+    ids = np.nonzero(~np.isnan(scores))[0]
+    assert len(ids) > 1000
+    x = q["x"].astype(np.float64)
+    yv = q["y"].astype(np.float64)
+    for pid in ids[::3]:
+        R = poses[pid, :9].reshape(3, 3).astype(np.float64)
+        t = poses[pid, 9:].astype(np.float64)
+        s_ref, c_ref = oracle.score(corr, q["K"], R, t, 4.0)
+        assert scores[pid] == pytest.approx(s_ref, rel=1e-5), pid
+        r, z = residuals(x, yv, q["X"], q["K"], R, t)
+        near = int(np.sum((z > 0) & (np.abs(r - 4.0) <= 1e-3)))
+        assert abs(int(counts[pid]) - c_ref) <= near, (pid, counts[pid], c_ref, near)
+
+
+def test_round_best_is_the_argmin(c1_run):
+    q, res, dbg = c1_run
+    scores = dbg["scores"]
+    ids = np.nonzero(~np.isnan(scores))[0]
+    key = int(dbg["round_best"][0]) & 0xFFFFFFFFFFFFFFFF
+    best_id = key & 0xFFFFFFFF
+    best_sc = np.frombuffer(np.uint32(key >> 32).tobytes(), np.float32)[0]
+    order = np.lexsort((ids, scores[ids]))
+    assert best_id == ids[order[0]]
+    assert best_sc == scores[best_id]
+
+
+def test_config1_end_to_end(c1_run):
+    q, res, dbg = c1_run
+    ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=q["hypotheses"], p_miss=0.0)
+    assert res["status"] == 0 and ref["status"] == 0
+    assert pose_close(res["R"], res["t"], ref["R"], ref["t"])
+    assert res["iterations"] == ref["iterations"] == 1000
+    r, z = residuals(q["x"].astype(np.float64), q["y"].astype(np.float64), q["X"], q["K"], ref["R"], ref["t"])
+    near = (z > 0) & (np.abs(r - 4.0) <= 1e-3)
+    diff = dbg["mask"] != ref["inlier_mask"]
+    # points whose status differs lie at the threshold under one of the two final poses
+    r2, z2 = residuals(q["x"].astype(np.float64), q["y"].astype(np.float64), q["X"], q["K"], res["R"], res["t"])
+    near |= (z2 > 0) & (np.abs(r2 - 4.0) <= 1e-2)
+    assert np.all(near[diff]), int(diff.sum())
+    assert abs(res["num_inliers"] - ref["num_inliers"]) <= max(2, int(near.sum()))
+
+
+def test_config2_lift_then_ransac(ctx):
+    q = synth.config2(0)
+    out = ctx.lift(views_to_device(q["views"]), matches_to_device(q["matches"]))
+    res = ctx.ransac_pnp(out, q["K"], imloc.default_opts(max_iters=q["hypotheses"], p_miss=0.0))
+    g = lifted_to_host(out)
+    L = oracle.lift(q["views"], q["matches"])
+    ref = oracle.ransac_pnp(oracle.Corr(L["x"], L["y"], L["X"], L["w"]), q["K"], max_iters=q["hypotheses"], p_miss=0.0)
+    assert res["status"] == 0
+    assert pose_close(res["R"], res["t"], ref["R"], ref["t"])
+    assert pose_close(res["R"], res["t"], q["R_gt"], q["t_gt"], deg=0.1, mm=20)
+    assert abs(res["num_inliers"] - ref["num_inliers"]) <= 0.002 * g["n"] + 5
+
+
+def test_enumerate_all_brute_force(ctx):
+    """Every triple of a tiny set: identical best-solution set and inlier set."""
+    rng = np.random.default_rng(31)
+    n_in, n_out = 10, 4
+    n = n_in + n_out
+    K = (500.0, 500.0, 320.0, 240.0)
+    R = synth.random_rotation(rng)
+    t = rng.normal(size=3)
+    u = rng.uniform(40, 600, n); v = rng.uniform(40, 440, n); d = rng.uniform(3, 15, n)
+    Xw = (np.column_stack([(u - 320) / 500 * d, (v - 240) / 500 * d, d]) - t) @ R
+    x = u.copy(); y = v.copy()
+    ang = rng.uniform(0, 2 * np.pi, n_out)
+    x[n_in:] += 60 * np.cos(ang); y[n_in:] += 60 * np.sin(ang)
+    x += rng.normal(0, 0.3, n); y += rng.normal(0, 0.3, n)
+    q = dict(x=x.astype(np.float32), y=y.astype(np.float32), X=Xw.astype(np.float32), w=np.ones(n, np.float32), K=K)
+    H = math.comb(n, 3)
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    opts = imloc.default_opts(max_iters=H, batch=H, p_miss=0.0, enumerate_all=1)
+    dbg = debug_buffers(H, 1)
+    mask = torch().zeros(n, dtype=torch().uint8, device="cuda")
+    res = ctx.testing_ransac(c, K, opts, n, dbg, mask=mask)
+    ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), K, enumerate_all=1, p_miss=0.0)
+    assert res["iterations"] == ref["iterations"] == H
+    assert res["best_hyp"] == ref["best_hyp"]
+    assert pose_close(res["R_best"], res["t_best"], ref["R_best"], ref["t_best"], deg=0.01, mm=1)
+    assert pose_close(res["R"], res["t"], ref["R"], ref["t"])
+    np.testing.assert_array_equal(mask.cpu().numpy().astype(bool), ref["inlier_mask"])
+    tri = dbg["triples"].cpu().numpy().reshape(-1, 3)
+    import itertools
+    assert [tuple(r) for r in tri] == list(itertools.combinations(range(n), 3))
+
+
+def test_lo_and_refine_from_injected_pose(ctx):
+    """LO (truncated loss, subset) and the Cauchy refinement started from the
+    same perturbed pose on both sides."""
+    rng = np.random.default_rng(41)
+    q = synth.direct_query(rng, 3000, 0.5, 800, 600, 700.0, noise_px=1.0, weights="conf")
+    dR = synth.axis_angle(rng.normal(size=3), math.radians(0.4))
+    R0, t0 = dR @ q["R_gt"], q["t_gt"] + rng.normal(size=3) * 0.03
+    inj = torch().from_numpy(np.concatenate([R0.ravel(), t0]).astype(np.float32)[None]).cuda()
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    R0f = inj[0, :9].cpu().numpy().astype(np.float64).reshape(3, 3)
+    t0f = inj[0, 9:].cpu().numpy().astype(np.float64)
+    corr = oracle.Corr(q["x"], q["y"], q["X"], q["w"])
+    # LO only
+    opts = imloc.default_opts(max_iters=1, batch=1, p_miss=0.0, final_iters=0, lo_iters=10)
+    res = ctx.testing_ransac(c, q["K"], opts, 3000, dict(inject_poses=inj))
+    R1, t1, s1 = oracle.lo(corr, q["K"], R0f, t0f, 4.0, iters=10)
+    assert res["lo_count"] == 1
+    assert pose_close(res["R_best"], res["t_best"], R1, t1, deg=0.005, mm=0.5)
+    assert res["score"] == pytest.approx(s1, rel=1e-4)
+    # refinement only, from the same start
+    opts = imloc.default_opts(max_iters=1, batch=1, p_miss=0.0, final_iters=25, lo_iters=0)
+    res = ctx.testing_ransac(c, q["K"], opts, 3000, dict(inject_poses=inj))
+    r, z = residuals(corr.x, corr.y, corr.X, q["K"], R0f, t0f)
+    sel = np.nonzero((z > 0) & (r * r < 16.0))[0]
+    R2, t2, _ = oracle.refine(corr, q["K"], R0f, t0f, sel, 4.0, 4.0, iters=25)
+    assert pose_close(res["R"], res["t"], R2, t2, deg=0.005, mm=0.5)
+
+
+def test_scores_of_injected_poses_full_subset(ctx):
+    """Per-pose scores in the full-size launch shape (M = 10,000 subset of
+    50,000, several hypothesis tiles and a ragged last tile) for poses the
+    oracle supplies, checked on a sample of the poses."""
+    rng = np.random.default_rng(17)
+    q = synth.direct_query(rng, 50000, 0.25, 1024, 768, 800.0, weights="conf")
+    P = 1500
+    poses = []
+    for k in range(P):
+        dR = synth.axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, 3)))
+        poses.append(np.concatenate([(dR @ q["R_gt"]).ravel(), q["t_gt"] + rng.normal(size=3) * 0.2]))
+    inj = torch().from_numpy(np.array(poses, np.float32)).cuda()
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    t = torch()
+    dbg = dict(inject_poses=inj, scores=t.full((4 * P,), float("nan"), device="cuda"),
+               counts=t.full((4 * P,), -1, dtype=t.int32, device="cuda"))
+    opts = imloc.default_opts(max_iters=P, batch=1024, p_miss=0.0, final_iters=0, lo_iters=0)
+    ctx.testing_ransac(c, q["K"], opts, 50000, dbg)
+    sc = dbg["scores"].cpu().numpy()
+    ct = dbg["counts"].cpu().numpy()
+    idx = oracle.subsample(50000, 10000)
+    corr = oracle.Corr(q["x"], q["y"], q["X"], q["w"])
+    pf = inj.cpu().numpy().astype(np.float64)
+    for k in list(range(0, P, 37)) + [P - 1]:
+        s_ref, c_ref = oracle.score(corr, q["K"], pf[k, :9].reshape(3, 3), pf[k, 9:], 4.0, idx=idx)
+        assert sc[4 * k] == pytest.approx(s_ref, rel=1e-5)
+        r, z = residuals(corr.x[idx], corr.y[idx], corr.X[idx], q["K"], pf[k, :9].reshape(3, 3), pf[k, 9:])
+        near = int(np.sum((z > 0) & (np.abs(r - 4.0) <= 1e-3)))
+        assert abs(int(ct[4 * k]) - c_ref) <= near
+    assert np.all(np.isnan(sc.reshape(-1, 4)[:, 1:]))  # only pose ids 4k exist
+
+
+def test_degenerate_inputs(ctx):
+    rng = np.random.default_rng(2)
+    for n in (0, 1, 2):
+        q = synth.direct_query(rng, max(n, 1), 1.0, 640, 480, 500.0)
+        c = imloc.corr_from_arrays(q["x"][:n], q["y"][:n], q["X"][:n], q["w"][:n])
+        res = ctx.ransac_pnp(c, q["K"], imloc.default_opts(max_iters=64, batch=32))
+        assert res["status"] == -7
+    q = synth.direct_query(rng, 3, 1.0, 640, 480, 500.0, noise_px=0.0)
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    res = ctx.ransac_pnp(c, q["K"], imloc.default_opts(max_iters=64, batch=32, p_miss=0.0))
+    assert res["status"] == 0 and res["num_inliers"] == 3
+    assert ctx.device_error() == 0
+
+
+def test_adaptive_stop_matches_the_formula(ctx):
+    q = synth.config1(4)
+    c = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"])
+    res = ctx.ransac_pnp(c, q["K"], imloc.default_opts(batch=128, max_iters=100000, p_miss=1e-4))
+    ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], batch=128, max_iters=100000,
+                            p_miss=1e-4)
+    need = oracle.needed_iters(res["subset_inliers"] / 2000, 1e-4)
+    assert res["iterations"] == 128 * max(1, math.ceil(need / 128))
+    assert res["iterations"] == ref["iterations"]
+    assert pose_close(res["R"], res["t"], ref["R"], ref["t"])
+
+
+def test_batch_matches_single_queries(ctx):
+    """Queries of uneven size in one batched call agree with the oracle."""
+    rng = np.random.default_rng(5)
+    qs = [synth.direct_query(rng, n, r, 1024, 768, 800.0, weights="conf")
+          for n, r in ((3000, 0.5), (12000, 0.3), (700, 0.6), (25000, 0.2))]
+    t = torch()
+    total = sum(len(q["x"]) for q in qs)
+    cat = lambda k: np.concatenate([q[k] for q in qs])
+    corr = imloc.corr_from_arrays(cat("x"), cat("y"), np.concatenate([q["X"] for q in qs]), cat("w"))
+    offs = np.cumsum([0] + [len(q["x"]) for q in qs])
+    d_offs = t.from_numpy(offs.astype(np.int64)).cuda()
+    opts = [imloc.default_opts(max_iters=2048, p_miss=0.0, query_id=i, seed=7) for i in range(len(qs))]
+    res_buf = t.zeros(len(qs) * imloc.RESULT_BYTES, dtype=t.uint8, device="cuda")
+    ctx.ransac_pnp_batch_async(corr, d_offs, [q["K"] for q in qs], opts, res_buf)
+    t.cuda.synchronize()
+    res = imloc.results_from_bytes(res_buf.cpu().numpy(), len(qs))
+    for i, q in enumerate(qs):
+        ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=2048, p_miss=0.0,
+                                query_id=i, seed=7)
+        assert res[i]["status"] == 0
+        assert pose_close(res[i]["R"], res[i]["t"], ref["R"], ref["t"]), i
+        assert res[i]["iterations"] == 2048
