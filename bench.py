@@ -1,0 +1,447 @@
+"""Benchmark of the ImLoc localization hot path (lift + LO-RANSAC PnP) on GB300.
+
+One step = one pass of the whole hot path over one batch of queries shaped
+like the paper's "lift + RANSAC per query" workload: per query, 10 database
+views with 1024x768 float32 depth maps of a piecewise-planar scene, 5,000
+dense matches per pair (50,000 matches), inlier ratio U[10%, 60%], N(0, 0.5 px)
+query noise, 10,000 minimal sets, LO on, Cauchy refinement on all inliers
+(adaptive stop off: fixed hypothesis count).  A step runs the batched lift
+and the batched LO-RANSAC of the C ABI on device-resident inputs; L2 is
+flushed (256 MiB write) between steps, outside the timed events.
+
+Headline metric: hypothesis x correspondence pairs scored per second.  Also
+reported: queries/s, the plain one-query-per-call form with p50/p99 latency,
+an end-to-end figure with host buffers (matches uploaded, results read back
+every step), per-kernel device time, the roofline of the dominant kernel and
+the FP64 CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs its own batch (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "hyp*corr scored/s; localized queries/s & p50/p99 latency, served vs plain"
+UNIT = "hyp*corr/s"
+HYPOTHESES = 10000
+MATCHES_PER_PAIR = 5000
+N_VIEWS = 10
+FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored pair, see the design doc
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# DRAM bytes per launch of k_score from the committed ncu capture (profiles/);
+# None until a capture of the current kernel exists.
+SCORE_TRAFFIC_PER_LAUNCH = None
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def _gen_query(seed):
+    from paper_2601_04185_gb300 import synth
+
+    rng = np.random.default_rng(seed)
+    q = synth.localization_query(rng, n_views=N_VIEWS, matches_per_pair=MATCHES_PER_PAIR)
+    q.pop("scene", None)
+    return q
+
+
+def make_queries(n, seed0):
+    # spawn: no fork after CUDA is initialised
+    ctx = mp.get_context("spawn")
+    with cf.ProcessPoolExecutor(max_workers=min(n, os.cpu_count() or 1), mp_context=ctx) as ex:
+        return list(ex.map(_gen_query, [seed0 + i for i in range(n)]))
+
+
+def concat_batch(queries):
+    views, qb = [], [0]
+    cat = {k: [] for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+    seg_off, seg_view, seg_dir = [0], [], []
+    for q in queries:
+        m = q["matches"]
+        base_v = len(views)
+        views += q["views"]
+        for k in cat:
+            cat[k].append(m[k])
+        for s in range(len(m["seg_view"])):
+            seg_off.append(qb[-1] + int(m["seg_off"][s + 1]))
+            seg_view.append(base_v + int(m["seg_view"][s]))
+            seg_dir.append(int(m["seg_dir"][s]))
+        qb.append(qb[-1] + int(m["seg_off"][-1]))
+    big = {k: np.concatenate(v).astype(np.float32) for k, v in cat.items()}
+    big.update(seg_off=np.array(seg_off, np.int64), seg_view=np.array(seg_view, np.int32),
+               seg_dir=np.array(seg_dir, np.int32))
+    return views, big, np.array(qb, np.int64)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.proc is None:
+            return
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU, no data-path collective)
+# ---------------------------------------------------------------------------
+def dist_setup(n_gpus):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the reference arm and the cpu_baseline leg)
+# ---------------------------------------------------------------------------
+def oracle_queries(queries, hypotheses, threads):
+    """Lift + LO-RANSAC of every query with the FP64 oracle, one query per
+    thread (the C oracle releases the GIL).  Returns (wall s, pairs scored)."""
+    import oracle
+
+    def one(i):
+        q = queries[i]
+        L = oracle.lift(q["views"], q["matches"])
+        c = oracle.Corr(L["x"], L["y"], L["X"], L["w"])
+        r = oracle.ransac_pnp(c, q["K"], max_iters=hypotheses, p_miss=0.0, query_id=i)
+        return r["hypotheses"] * min(c.n, 10000)
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        pairs = sum(ex.map(one, range(len(queries))))
+    return time.perf_counter() - t0, pairs
+
+
+def run_reference(args):
+    rank, world, _ = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    # a step: one query per core, one round of 1,024 minimal sets (bounded CPU sample)
+    hyps = 1024
+    queries = make_queries(cores, 1000)
+    for _ in range(args.warmup):
+        oracle_queries(queries[:1], hyps, 1)
+    total_t, total_pairs = 0.0, 0
+    for _ in range(args.steps):
+        t, p = oracle_queries(queries, hyps, cores)
+        total_t += t
+        total_pairs += p
+    v = total_pairs / total_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"C2-shaped lift + LO-RANSAC PnP, FP64 CPU oracle, {cores} queries/step "
+                                   f"(one per core), {hyps} minimal sets each, LO + Cauchy refinement"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{cores} synthetic C2 queries per step, {hyps} minimal sets each"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    # inputs first (spawned pool; no fork after CUDA starts)
+    queries = make_queries(args.queries, 100 + 1000 * int(os.environ.get("RANK", "0")))
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    views, big, qb = concat_batch(queries)
+    nq = len(queries)
+    d_views = []
+    for v in views:
+        d = dict(v)
+        d["depth"] = torch.from_numpy(v["depth"]).to(dev)
+        d_views.append(d)
+    d_match = {k: torch.from_numpy(big[k]).to(dev) for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+    d_match.update({k: big[k] for k in ("seg_off", "seg_view", "seg_dir")})
+    h_match = {k: torch.from_numpy(big[k]).pin_memory() for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+    n_matches = int(qb[-1])
+    ctx = imloc.Context(dev.index, (256 << 20) + nq * (64 << 20))
+    corr = imloc.alloc_corr(n_matches, dev)
+    offsets = torch.zeros(nq + 1, dtype=torch.int64, device=dev)
+    results = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    h_results = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8).pin_memory()
+    opts = [imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=1234) for i in range(nq)]
+    Ks = [q["K"] for q in queries]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prep_lift = imloc.prepare_lift_batch(qb, d_views, d_match)
+    prep_ransac = imloc.prepare_ransac_batch(Ks, opts)
+
+    def step(from_host=False):
+        if from_host:
+            for k in h_match:
+                d_match[k].copy_(h_match[k], non_blocking=True)
+        ctx.lift_batch(qb, d_views, d_match, out=corr, offsets=offsets, stream=stream, prepared=prep_lift)
+        ctx.ransac_pnp_batch_async(corr, offsets, Ks, opts, results, stream=stream, prepared=prep_ransac)
+        if from_host:
+            h_results.copy_(results, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident), traced per kernel ----
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kstats = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    total_s = sum(step_ms) / 1e3
+    total_s_max = max_over_ranks(total_s, world)
+
+    res = imloc.results_from_bytes(results.cpu().numpy(), nq)
+    offs = offsets.cpu().numpy()
+    n_corr = np.diff(offs)
+    pairs_per_step = float(sum(r["hypotheses"] * min(int(n), 10000) for r, n in zip(res, n_corr)))
+    statuses = sorted({r["status"] for r in res})
+    pairs_all = sum_over_ranks(pairs_per_step * args.steps, world)
+    value = pairs_all / total_s_max
+    q_per_s = sum_over_ranks(nq * args.steps, world) / total_s_max
+
+    # ---- end to end through the public API with host buffers ----
+    h2d = sum(h_match[k].numel() * 4 for k in h_match)
+    d2h = results.numel()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev2[i][0].record(stream)
+        step(from_host=True)
+        ev2[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2) / 1e3, world)
+    e2e_value = pairs_all / e2e_s
+
+    # ---- plain form: one query per call (lift, then RANSAC), host-synchronous ----
+    lat = []
+    q_single = {}
+    for i in range(min(nq, 8)):
+        q = queries[i]
+        dv = d_views[i * N_VIEWS:(i + 1) * N_VIEWS]
+        dm = {k: torch.from_numpy(q["matches"][k]).to(dev) for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+        dm.update({k: q["matches"][k] for k in ("seg_off", "seg_view", "seg_dir")})
+        q_single[i] = dm
+    c1 = imloc.alloc_corr(n_matches, dev)
+    for rep in range(3):
+        for i in q_single:
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.lift(d_views[i * N_VIEWS:(i + 1) * N_VIEWS], q_single[i], out=c1, stream=stream)
+            ctx.ransac_pnp(c1, queries[i]["K"], imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i,
+                                                                    seed=1234), stream=stream)
+            lat.append(1e3 * (time.perf_counter() - t0))
+    lat_sorted = sorted(lat)
+    p50 = lat_sorted[len(lat) // 2]
+    p99 = lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # ---- roofline of the dominant kernel (k_score: FP32 pipe) ----
+    clocks = clk.summary()
+    launches = {k: v[0] for k, v in kstats.items()}
+    kms = {k: v[1] for k, v in kstats.items()}
+    score_launch_ms = kms.get("k_score", 0.0) / max(1, launches.get("k_score", 1))
+    pairs_per_launch = pairs_per_step * args.steps / max(1, launches.get("k_score", 1))
+    achieved_tflops = FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
+    peak_clock_mhz = 2070.0
+    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_clock_mhz * 1e6 / 1e12
+    lift_ms = kms.get("k_lift", 0.0) / max(1, launches.get("k_lift", 1))
+    # algorithmic bytes of one lift launch: 20 B per match, 64 B (bilinear) or 32 B (lookup) of depth
+    # sectors per match that passes the confidence filter, 28 B per correspondence written
+    conf_ok = big["conf"] > np.float32(0.05)
+    dirs = np.repeat(big["seg_dir"], np.diff(big["seg_off"]))
+    lift_bytes = 20 * n_matches + int(np.sum(np.where(dirs[conf_ok] == 0, 64, 32))) + 28 * int(offs[-1])
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    lift_gbs = lift_bytes / (lift_ms * 1e-3) / 1e9 if lift_ms else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"C2: {nq} queries/step x (lift of {N_VIEWS} views x {MATCHES_PER_PAIR} matches "
+                               f"+ LO-RANSAC PnP, {HYPOTHESES} minimal sets, LO, Cauchy refinement)",
+                   "queries_per_step": nq, "matches_per_query": N_VIEWS * MATCHES_PER_PAIR,
+                   "depth": "1024x768 float32, 10 views/query", "hypotheses": HYPOTHESES, "score_corr_cap": 10000,
+                   "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
+        "queries_per_s": q_per_s,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "queries_per_s": sum_over_ranks(nq * args.steps, world) / e2e_s},
+        "plain": {"latency_ms_p50": p50, "latency_ms_p99": p99, "queries_per_s": 1e3 / statistics.mean(lat),
+                  "form": "one query per call: imloc_lift_async + imloc_ransac_pnp (host-synchronous)",
+                  "samples": len(lat)},
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
+                     "traffic": SCORE_TRAFFIC_PER_LAUNCH, "kernel": "k_score",
+                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
+                     "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
+                     "launch_ms": score_launch_ms},
+        "roofline_lift": {"bound": "hbm", "achieved": lift_gbs, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": (lift_gbs / hbm_peak) if lift_gbs else None, "bytes_per_launch": lift_bytes,
+                          "launch_ms": lift_ms, "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)"},
+        "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+        "gpu_launches": int(sum(launches.values())),
+        "clocks": clocks,
+        "result_status": statuses,
+        "paper_context": "ImLoc reports ~200 ms per query for its RANSAC loop on an RTX 4090 (Sec. 4.4); "
+                         "different hardware and data",
+    }
+    # ---- CPU baseline: the FP64 oracle on the host cores (rank 0, N = 1 only) ----
+    if world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = queries[:min(nq, cores)]
+        wall, pairs = oracle_queries(sample, HYPOTHESES, cores)
+        line["cpu_baseline"] = {"value": pairs / wall, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": f"{len(sample)} of the step's queries (lift + {HYPOTHESES} minimal "
+                                          f"sets + LO + refinement), one per thread, {wall:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--queries", type=int, default=16, help="queries per step (per GPU)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -59,6 +59,21 @@ const char* imloc_last_cuda_error(void);
  * last stream. */
 int imloc_device_error(imloc_ctx* ctx);
 
+/* ---- tracing ----------------------------------------------------------
+ * While enabled, every kernel launch of later calls on the context is
+ * bracketed by CUDA events on its stream; imloc_profile_read waits for them
+ * and returns, per kernel name, the launch count and the summed device time. */
+typedef struct {
+    char name[32];
+    int64_t launches;
+    double total_ms;
+} imloc_kernel_stat;
+
+int imloc_profile_enable(imloc_ctx* ctx, int on);
+/* Writes min(n, max_out) entries to `out` (host) and the number of kernels
+ * seen to *n_out; reset != 0 clears the totals afterwards. */
+int imloc_profile_read(imloc_ctx* ctx, imloc_kernel_stat* out, int32_t max_out, int32_t* n_out, int reset);
+
 /* ---- cameras and views -------------------------------------------------- */
 typedef struct { float fx, fy, cx, cy; int32_t width, height; } imloc_camera;   /* pinhole */
 typedef struct { double R[9]; double t[3]; } imloc_pose;                        /* cam_from_world */

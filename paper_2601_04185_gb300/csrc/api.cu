@@ -14,10 +14,17 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
              cudaGetErrorString(e));
 }
 
-int begin_call(imloc_ctx* ctx) {
+int begin_call(imloc_ctx* ctx, cudaStream_t stream) {
     ctx->ws_top = 0;
     ctx->staging_top = 0;
     IMLOC_CUDA_TRY(cudaEventSynchronize(ctx->staging_free));
+    IMLOC_CUDA_TRY(cudaStreamWaitEvent(stream, ctx->call_done, 0));
+    return IMLOC_OK;
+}
+
+int end_call(imloc_ctx* ctx, cudaStream_t stream) {
+    IMLOC_CUDA_TRY(cudaEventRecord(ctx->call_done, stream));
+    ctx->last_stream = stream;
     return IMLOC_OK;
 }
 
@@ -42,9 +49,76 @@ int upload(imloc_ctx* ctx, void* d_dst, const void* h_staged, size_t bytes, cuda
     return IMLOC_OK;
 }
 
+static cudaEvent_t prof_event(imloc_ctx* ctx) {
+    if (!ctx->prof_pool.empty()) {
+        cudaEvent_t e = ctx->prof_pool.back();
+        ctx->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+ProfScope::ProfScope(imloc_ctx* c, cudaStream_t s, const char* n) : ctx(c), stream(s), name(n) {
+    if (!ctx->prof_on) return;
+    a = prof_event(ctx);
+    if (a) cudaEventRecord(a, stream);
+}
+
+void ProfScope::end() {
+    if (!a) return;
+    cudaEvent_t b = prof_event(ctx);
+    if (!b) return;
+    cudaEventRecord(b, stream);
+    ctx->prof_pending.push_back({name, a, b});
+    a = nullptr;
+}
+
+static void prof_drain(imloc_ctx* ctx) {
+    for (auto& r : ctx->prof_pending) {
+        cudaEventSynchronize(r.b);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        auto& acc = ctx->prof_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        ctx->prof_pool.push_back(r.a);
+        ctx->prof_pool.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+}
+
 }  // namespace imloc
 
 extern "C" {
+
+int imloc_profile_enable(imloc_ctx* ctx, int on) {
+    if (!ctx) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->prof_on = on != 0;
+    return IMLOC_OK;
+}
+
+int imloc_profile_read(imloc_ctx* ctx, imloc_kernel_stat* out, int32_t max_out, int32_t* n_out, int reset) {
+    if (!ctx || (max_out > 0 && !out) || !n_out) return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
+    imloc::prof_drain(ctx);
+    int32_t k = 0;
+    for (auto& kv : ctx->prof_acc) {
+        if (k < max_out) {
+            memset(&out[k], 0, sizeof(out[k]));
+            strncpy(out[k].name, kv.first.c_str(), sizeof(out[k].name) - 1);
+            out[k].launches = kv.second.first;
+            out[k].total_ms = kv.second.second;
+        }
+        ++k;
+    }
+    *n_out = k;
+    if (reset) ctx->prof_acc.clear();
+    return IMLOC_OK;
+}
 
 int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes) {
     if (!out) return IMLOC_ERR_INVALID_ARG;
@@ -64,7 +138,8 @@ int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes) {
     }
     if (cudaMallocHost(&c->staging, c->staging_bytes) != cudaSuccess ||
         cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->call_done, cudaEventDisableTiming) != cudaSuccess) {
         imloc_destroy(c);
         return IMLOC_ERR_OOM;
     }
@@ -83,6 +158,9 @@ void imloc_destroy(imloc_ctx* c) {
     if (c->d_err) cudaFree(c->d_err);
     if (c->staging) cudaFreeHost(c->staging);
     if (c->staging_free) cudaEventDestroy(c->staging_free);
+    if (c->call_done) cudaEventDestroy(c->call_done);
+    for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->prof_pool) cudaEventDestroy(e);
     delete c;
 }
 

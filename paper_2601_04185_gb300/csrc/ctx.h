@@ -6,7 +6,10 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
+#include <string>
+#include <vector>
 
 #include "../../include/imloc.h"
 
@@ -20,16 +23,26 @@ struct imloc_ctx {
     size_t staging_bytes = 0;
     size_t staging_top = 0;
     cudaEvent_t staging_free = nullptr;  // recorded after the last upload read the staging buffer
+    cudaEvent_t call_done = nullptr;     // recorded after the last call's work; the next call's stream waits on it
     int* d_err = nullptr;         // sticky device error word
     cudaStream_t last_stream = nullptr;
     std::mutex mu;                // serialises calls on one context
+    // tracing: CUDA events around every kernel launch while enabled
+    bool prof_on = false;
+    struct ProfRec { const char* name; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    std::map<std::string, std::pair<int64_t, double>> prof_acc;  // name -> (launches, ms)
 };
 
 namespace imloc {
 
-// Start a call: reset the bump allocators, wait until the previous upload
-// has consumed the staging buffer.
-int begin_call(imloc_ctx* ctx);
+// Start a call on `stream`: reset the bump allocators, wait (host) until the
+// previous upload has consumed the staging buffer, and make `stream` wait for
+// the previous call's device work, which used the same workspace.
+int begin_call(imloc_ctx* ctx, cudaStream_t stream);
+// End a call: record the completion event on `stream`.
+int end_call(imloc_ctx* ctx, cudaStream_t stream);
 // Device workspace sub-allocation (256-byte aligned); nullptr when it does not fit.
 void* ws_alloc(imloc_ctx* ctx, size_t bytes);
 // Pinned staging sub-allocation (256-byte aligned); nullptr when it does not fit.
@@ -38,5 +51,16 @@ void* staging_alloc(imloc_ctx* ctx, size_t bytes);
 int upload(imloc_ctx* ctx, void* d_dst, const void* h_staged, size_t bytes, cudaStream_t stream);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Tracing around one launch: prof_begin records a start event on `stream`
+// (no-op when tracing is off); prof_end records the end event.
+struct ProfScope {
+    imloc_ctx* ctx;
+    cudaStream_t stream;
+    const char* name;
+    cudaEvent_t a = nullptr;
+    ProfScope(imloc_ctx* c, cudaStream_t s, const char* n);
+    void end();
+};
 
 }  // namespace imloc

@@ -330,9 +330,10 @@ static int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_beg
     p.tile_state = state + 1;
     p.tile_counter = reinterpret_cast<uint32_t*>(state);
     p.err = ctx->d_err;
+    ProfScope prof(ctx, stream, "k_lift");
     k_lift<<<n_tiles, kLiftThreads, 0, stream>>>(p);
     IMLOC_CUDA_TRY(cudaGetLastError());
-    ctx->last_stream = stream;
+    prof.end();
     return IMLOC_OK;
 }
 
@@ -345,10 +346,13 @@ int imloc_lift_async(imloc_ctx* ctx, const imloc_view* views, int32_t n_views, c
     if (!ctx || !m) return IMLOC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
-    int rc = imloc::begin_call(ctx);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = imloc::begin_call(ctx, st);
     if (rc != IMLOC_OK) return rc;
     const int64_t qb[2] = {0, m->n};
-    return imloc::lift_impl(ctx, 1, qb, views, n_views, m, out, nullptr, static_cast<cudaStream_t>(stream));
+    rc = imloc::lift_impl(ctx, 1, qb, views, n_views, m, out, nullptr, st);
+    int rc2 = imloc::end_call(ctx, st);
+    return rc != IMLOC_OK ? rc : rc2;
 }
 
 int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, const imloc_view* views,
@@ -357,10 +361,12 @@ int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* que
     if (!ctx || !m) return IMLOC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
-    int rc = imloc::begin_call(ctx);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = imloc::begin_call(ctx, st);
     if (rc != IMLOC_OK) return rc;
-    return imloc::lift_impl(ctx, n_queries, query_begin, views, n_views, m, out, d_offsets,
-                            static_cast<cudaStream_t>(stream));
+    rc = imloc::lift_impl(ctx, n_queries, query_begin, views, n_views, m, out, d_offsets, st);
+    int rc2 = imloc::end_call(ctx, st);
+    return rc != IMLOC_OK ? rc : rc2;
 }
 
 }  // extern "C"

@@ -112,8 +112,8 @@ __device__ __forceinline__ void polish_depths(T L[3], const T a[3], const T b[3]
 }
 
 // Pose from depths: R (X1-X2, X1-X3, cross) = (C1-C2, C1-C3, cross), t = C1 - R X1.
-template <typename T>
-__device__ __forceinline__ bool pose_from_depths(const T L[3], const float y[3][3], const float X[3][3], float Rout[9],
+template <typename T, typename B>
+__device__ __forceinline__ bool pose_from_depths(const T L[3], const B y[3][3], const float X[3][3], float Rout[9],
                                                  float tout[3]) {
     T C[3][3];
 #pragma unroll
@@ -152,9 +152,13 @@ __device__ __forceinline__ bool pose_from_depths(const T L[3], const float y[3][
     return true;
 }
 
-// Solve one P3P instance.  y: unit bearings, X: world points.  Returns the
-// number of poses (<= 4), sorted by ascending depth of the first point.
-__device__ int p3p_solve(const float y[3][3], const float X[3][3], bool fp64_polish, PoseF out[4], float l1_out[4]) {
+// Solve one P3P instance.  y: unit bearings (float32), yd: the same bearings
+// in FP64 (used, with FP64 squared distances, by the Newton polish and the
+// pose when non-null), X: world points.  Returns the number of poses (<= 4),
+// sorted by ascending depth of the first point.
+__device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float X[3][3], PoseF out[4],
+                         float l1_out[4]) {
+    const bool fp64_polish = yd != nullptr;
     float a12 = 0.f, a13 = 0.f, a23 = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -256,14 +260,16 @@ __device__ int p3p_solve(const float y[3][3], const float X[3][3], bool fp64_pol
                              d23 = double(X[1][c]) - double(X[2][c]);
                 a[0] += d12 * d12; a[1] += d13 * d13; a[2] += d23 * d23;
             }
-            const double b[3] = {b12, b13, b23};
-            polish_depths<double>(L, a, b, 2);
+            const double b[3] = {yd[0][0] * yd[1][0] + yd[0][1] * yd[1][1] + yd[0][2] * yd[1][2],
+                                 yd[0][0] * yd[2][0] + yd[0][1] * yd[2][1] + yd[0][2] * yd[2][2],
+                                 yd[1][0] * yd[2][0] + yd[1][1] * yd[2][1] + yd[1][2] * yd[2][2]};
+            polish_depths<double>(L, a, b, 3);
             const double f0 = L[0] * L[0] + L[1] * L[1] - 2.0 * b[0] * L[0] * L[1] - a[0];
             const double f1 = L[0] * L[0] + L[2] * L[2] - 2.0 * b[1] * L[0] * L[2] - a[1];
             const double f2 = L[1] * L[1] + L[2] * L[2] - 2.0 * b[2] * L[1] * L[2] - a[2];
             good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabs(f0) <= 1e-4 * a[0] && fabs(f1) <= 1e-4 * a[1] &&
                    fabs(f2) <= 1e-4 * a[2];
-            if (good) good = pose_from_depths<double>(L, y, X, out[nout].R, out[nout].t);
+            if (good) good = pose_from_depths<double, double>(L, yd, X, out[nout].R, out[nout].t);
             Lf[0] = float(L[0]);
         } else {
             float L[3] = {Ls[k][0] * scale, Ls[k][1] * scale, Ls[k][2] * scale};
@@ -274,7 +280,7 @@ __device__ int p3p_solve(const float y[3][3], const float X[3][3], bool fp64_pol
             const float f2 = L[1] * L[1] + L[2] * L[2] - 2.0f * b[2] * L[1] * L[2] - a[2];
             good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabsf(f0) <= 1e-3f * a[0] && fabsf(f1) <= 1e-3f * a[1] &&
                    fabsf(f2) <= 1e-3f * a[2];
-            if (good) good = pose_from_depths<float>(L, y, X, out[nout].R, out[nout].t);
+            if (good) good = pose_from_depths<float, float>(L, y, X, out[nout].R, out[nout].t);
             Lf[0] = L[0];
         }
         if (!good) continue;

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
             }
             if (ok) {
                 float y[3][3], X[3][3];
+                double yd[3][3];
                 const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
@@ -193,9 +194,15 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                     const float inv = rsqrtf(bx * bx + by * by + 1.0f);
                     y[k][0] = bx * inv; y[k][1] = by * inv; y[k][2] = inv;
                     X[k][0] = c.X; X[k][1] = c.Y; X[k][2] = c.Z;
+                    if (d.polish) {
+                        const double ex = (double(c.x) - double(d.cx)) / double(d.fx);
+                        const double ey = (double(c.y) - double(d.cy)) / double(d.fy);
+                        const double en = 1.0 / sqrt(ex * ex + ey * ey + 1.0);
+                        yd[k][0] = ex * en; yd[k][1] = ey * en; yd[k][2] = en;
+                    }
                 }
                 float l1[4];
-                nsol = p3p_solve(y, X, d.polish != 0, sol, l1);
+                nsol = p3p_solve(y, d.polish ? yd : nullptr, X, sol, l1);
                 for (int k = 0; k < nsol; ++k) d.slots[4 * local + k] = sol[k];
             }
         } else if (d.triples) {
@@ -1062,8 +1069,10 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     const Tuning tn = pick_tuning(ctx, nq, est_hyp);
     {
         SetupParams sp{d_qd, d_qs, d_nhyp, W * nq};
+        ProfScope prof(ctx, stream, "k_setup");
         k_setup<<<nq, 256, 0, stream>>>(sp);
         IMLOC_CUDA_TRY(cudaGetLastError());
+        prof.end();
     }
     auto score_kernel = want_counts ? k_score<kThreads, kHT, true> : k_score<kThreads, kHT, false>;
     const size_t score_smem = sizeof(ScoreCorr) * 2 * kChunk + sizeof(float) * kTH + sizeof(int) * kTH;
@@ -1081,24 +1090,37 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         if (wtotal[w] > 0) {
             SampleParams sp{d_qd, d_qs, wq_w, d_wp + static_cast<size_t>(w) * (nq + 1), nh_w, wtotal[w], nq};
             const int64_t blocks = (wtotal[w] + 127) / 128;
+            ProfScope prof(ctx, stream, "k_sample_p3p");
             k_sample_p3p<<<static_cast<unsigned>(blocks), 128, 0, stream>>>(sp);
             IMLOC_CUDA_TRY(cudaGetLastError());
+            prof.end();
         }
         TilesParams tp{d_qs, nh_w, d_tiles, d_counter, nq, kTH};
-        k_tiles<<<1, 1024, 0, stream>>>(tp);
-        IMLOC_CUDA_TRY(cudaGetLastError());
+        {
+            ProfScope prof(ctx, stream, "k_tiles");
+            k_tiles<<<1, 1024, 0, stream>>>(tp);
+            IMLOC_CUDA_TRY(cudaGetLastError());
+            prof.end();
+        }
         ScoreParams scp{d_qd, d_qs, wq_w, nh_w, d_tiles, d_counter, nq, ctx->d_err};
         const int64_t max_items = std::max<int64_t>(1, (wtotal[w] * 4 + kTH - 1) / kTH + nq);
         const int grid_clusters = static_cast<int>(std::min<int64_t>(n_clusters, max_items));
-        rc = launch_cluster(score_kernel, scp, grid_clusters * tn.score_cluster, kThreads, score_smem, tn.score_cluster,
-                            stream);
-        if (rc != IMLOC_OK) return rc;
+        {
+            ProfScope prof(ctx, stream, "k_score");
+            rc = launch_cluster(score_kernel, scp, grid_clusters * tn.score_cluster, kThreads, score_smem,
+                                tn.score_cluster, stream);
+            if (rc != IMLOC_OK) return rc;
+            prof.end();
+        }
         ReplayParams rp{d_qd, d_qs, wq_w, static_cast<int32_t>(waves[w].first), static_cast<int32_t>(waves[w].second),
                         ctx->d_err};
-        rc = launch_cluster(k_replay, rp, nq * tn.replay_cluster, kRT, 0, tn.replay_cluster, stream);
-        if (rc != IMLOC_OK) return rc;
+        {
+            ProfScope prof(ctx, stream, "k_replay");
+            rc = launch_cluster(k_replay, rp, nq * tn.replay_cluster, kRT, 0, tn.replay_cluster, stream);
+            if (rc != IMLOC_OK) return rc;
+            prof.end();
+        }
     }
-    ctx->last_stream = stream;
     return IMLOC_OK;
 }
 
@@ -1124,9 +1146,9 @@ int imloc_ransac_pnp(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera*
     if (!ctx || !corr || !qcam || !opts || !out) return IMLOC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
-    int rc = imloc::begin_call(ctx);
-    if (rc != IMLOC_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = imloc::begin_call(ctx, st);
+    if (rc != IMLOC_OK) return rc;
     imloc_result* d_res = static_cast<imloc_result*>(imloc::ws_alloc(ctx, sizeof(imloc_result)));
     if (!d_res) return IMLOC_ERR_OOM;
     HostQuery h;
@@ -1138,6 +1160,8 @@ int imloc_ransac_pnp(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera*
     rc = imloc::ransac_impl(ctx, 1, &h, st, false);
     if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaMemcpyAsync(out, d_res, sizeof(imloc_result), cudaMemcpyDeviceToHost, st));
+    rc = imloc::end_call(ctx, st);
+    if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaStreamSynchronize(st));
     return out->status == IMLOC_OK ? IMLOC_OK : out->status;
 }
@@ -1148,7 +1172,8 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
     if (!ctx || !corr || !d_offsets || !qcams || !opts || !d_results || n_queries <= 0) return IMLOC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
-    int rc = imloc::begin_call(ctx);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = imloc::begin_call(ctx, st);
     if (rc != IMLOC_OK) return rc;
     std::vector<HostQuery> hq(n_queries);
     for (int q = 0; q < n_queries; ++q) {
@@ -1161,7 +1186,9 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
         hq[q].cam = qcams[q];
         hq[q].o = opts[q];
     }
-    return imloc::ransac_impl(ctx, n_queries, hq.data(), static_cast<cudaStream_t>(stream), false);
+    rc = imloc::ransac_impl(ctx, n_queries, hq.data(), st, false);
+    int rc2 = imloc::end_call(ctx, st);
+    return rc != IMLOC_OK ? rc : rc2;
 }
 
 int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam,
@@ -1171,9 +1198,9 @@ int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_cam
     if (opts->p_miss > 0.0) return IMLOC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(ctx->mu);
     IMLOC_CUDA_TRY(cudaSetDevice(ctx->device));
-    int rc = imloc::begin_call(ctx);
-    if (rc != IMLOC_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = imloc::begin_call(ctx, st);
+    if (rc != IMLOC_OK) return rc;
     imloc_result* d_res = static_cast<imloc_result*>(imloc::ws_alloc(ctx, sizeof(imloc_result)));
     if (!d_res) return IMLOC_ERR_OOM;
     HostQuery h;
@@ -1194,6 +1221,8 @@ int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_cam
     rc = imloc::ransac_impl(ctx, 1, &h, st, dbg->counts != nullptr);
     if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaMemcpyAsync(out, d_res, sizeof(imloc_result), cudaMemcpyDeviceToHost, st));
+    rc = imloc::end_call(ctx, st);
+    if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaStreamSynchronize(st));
     return IMLOC_OK;
 }

@@ -63,6 +63,10 @@ class Result(C.Structure):
                 ("best_hyp", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
 
 
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
+
+
 class Debug(C.Structure):
     _fields_ = [("triples", C.c_void_p), ("poses", C.c_void_p), ("scores", C.c_void_p), ("counts", C.c_void_p),
                 ("round_best", C.c_void_p), ("inject_poses", C.c_void_p), ("n_inject", C.c_int64)]
@@ -71,7 +75,7 @@ class Debug(C.Structure):
 # every symbol declared in include/imloc.h and include/imloc_testing.h
 EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda_error", "imloc_device_error",
            "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
-           "imloc_ransac_pnp_batch_async", "imloc_testing_ransac"]
+           "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read"]
 
 _lib = None
 
@@ -100,6 +104,8 @@ def load(path: str = LIB_PATH):
     L.imloc_ransac_pnp.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Result), V, V]
     L.imloc_ransac_pnp_batch_async.argtypes = [V, C.c_int32, P(Corr), V, P(Camera), P(RansacOpts), V, V, V]
     L.imloc_testing_ransac.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Debug), P(Result), V, V]
+    L.imloc_profile_enable.argtypes = [V, C.c_int]
+    L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     _lib = L
     return L
 
@@ -208,6 +214,26 @@ def _matches_struct(m):
     return st, segs
 
 
+class Prepared:
+    """Marshalled arguments kept alive for repeated calls (no per-call Python work)."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def prepare_lift_batch(query_begin, views, matches):
+    vs = _views_struct(views)
+    ms, keep = _matches_struct(matches)
+    qb = np.ascontiguousarray(query_begin, dtype=np.int64)
+    return Prepared(vs=vs, n_views=len(views), ms=ms, keep=keep, qb=qb, nq=len(qb) - 1,
+                    qb_ptr=qb.ctypes.data_as(C.POINTER(C.c_int64)), tensors=(views, matches))
+
+
+def prepare_ransac_batch(Ks, opts):
+    nq = len(Ks)
+    return Prepared(nq=nq, cams=(Camera * nq)(*[camera(K) for K in Ks]), opts=(RansacOpts * nq)(*opts))
+
+
 class Context:
     """One libimloc context (device workspace) bound to a CUDA device."""
 
@@ -232,6 +258,16 @@ class Context:
     def device_error(self):
         return self.lib.imloc_device_error(self.h)
 
+    def profile(self, on: bool):
+        _check(self.lib.imloc_profile_enable(self.h, 1 if on else 0), "imloc_profile_enable")
+
+    def profile_read(self, reset=True):
+        """{kernel name: (launches, total device ms)} of the traced launches."""
+        arr = (KernelStat * 64)()
+        n = C.c_int32(0)
+        _check(self.lib.imloc_profile_read(self.h, arr, 64, C.byref(n), 1 if reset else 0), "imloc_profile_read")
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms) for i in range(min(n.value, 64))}
+
     # ---- lifting ----
     def lift(self, views, matches, out=None, stream=None):
         """views: list of dicts (depth: cuda float32 HxW tensor, fx, fy, cx, cy, R, t);
@@ -245,21 +281,17 @@ class Context:
                "imloc_lift_async")
         return out
 
-    def lift_batch(self, query_begin, views, matches, out=None, offsets=None, stream=None):
+    def lift_batch(self, query_begin, views, matches, out=None, offsets=None, stream=None, prepared=None):
         torch = _torch()
-        vs = _views_struct(views)
-        ms, keep = _matches_struct(matches)
-        qb = np.ascontiguousarray(query_begin, dtype=np.int64)
-        nq = len(qb) - 1
+        p = prepared if prepared is not None else prepare_lift_batch(query_begin, views, matches)
         dev = matches["q_u"].device
         if out is None:
-            out = alloc_corr(ms.n, dev)
+            out = alloc_corr(p.ms.n, dev)
         if offsets is None:
-            offsets = torch.zeros(nq + 1, dtype=torch.int64, device=dev)
+            offsets = torch.zeros(p.nq + 1, dtype=torch.int64, device=dev)
         cs = _corr_struct(out)
-        _check(self.lib.imloc_lift_batch_async(self.h, nq, qb.ctypes.data_as(C.POINTER(C.c_int64)), vs, len(views),
-                                               C.byref(ms), C.byref(cs), _ptr(offsets), _stream(stream)),
-               "imloc_lift_batch_async")
+        _check(self.lib.imloc_lift_batch_async(self.h, p.nq, p.qb_ptr, p.vs, p.n_views, C.byref(p.ms), C.byref(cs),
+                                               _ptr(offsets), _stream(stream)), "imloc_lift_batch_async")
         return out, offsets
 
     # ---- RANSAC ----
@@ -278,13 +310,11 @@ class Context:
             _check(rc, "imloc_ransac_pnp")
         return result_dict(res)
 
-    def ransac_pnp_batch_async(self, corr, offsets, Ks, opts, results, masks=None, stream=None):
+    def ransac_pnp_batch_async(self, corr, offsets, Ks, opts, results, masks=None, stream=None, prepared=None):
         """results: cuda uint8 tensor of n_queries * sizeof(Result) bytes (see RESULT_BYTES)."""
-        nq = len(Ks)
-        cams = (Camera * nq)(*[camera(K) for K in Ks])
-        oarr = (RansacOpts * nq)(*opts)
+        p = prepared if prepared is not None else prepare_ransac_batch(Ks, opts)
         cs = _corr_struct(corr)
-        _check(self.lib.imloc_ransac_pnp_batch_async(self.h, nq, C.byref(cs), _ptr(offsets), cams, oarr,
+        _check(self.lib.imloc_ransac_pnp_batch_async(self.h, p.nq, C.byref(cs), _ptr(offsets), p.cams, p.opts,
                                                      _ptr(results), _ptr(masks), _stream(stream)),
                "imloc_ransac_pnp_batch_async")
 

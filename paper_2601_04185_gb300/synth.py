@@ -136,19 +136,26 @@ class PlanarScene:
         fx, fy, cx, cy = K
         u = np.asarray(u, dtype=np.float64)
         v = np.asarray(v, dtype=np.float64)
-        rays = np.stack([(u - cx) / fx, (v - cy) / fy, np.ones_like(u)], axis=-1)
-        dirs = rays @ R  # R^T r per ray: world direction with unit camera-z
+        shape = u.shape
+        a = ((u - cx) / fx).ravel()
+        b = ((v - cy) / fy).ravel()
+        # world direction of the ray with unit camera-z: R^T (a, b, 1)
         C = -R.T @ t
-        best = np.full(u.shape, np.inf)
+        best = np.full(a.shape, np.inf)
         for n_w, off_w, centre_w, radius in self.planes:
-            den = dirs @ n_w
+            nc = R @ n_w                      # plane normal in camera axes
+            den = a * nc[0] + b * nc[1] + nc[2]
             with np.errstate(divide="ignore", invalid="ignore"):
                 s = (off_w - n_w @ C) / den
-            hit = C + s[..., None] * dirs
-            inside = np.linalg.norm(hit - centre_w, axis=-1) < radius
-            ok = np.isfinite(s) & (s > 0) & inside & (s < best)
+            # |C + s d - centre|^2 with d = R^T (a, b, 1): expand without (n, 3) temporaries
+            e = R @ (C - centre_w)            # (C - centre) in camera axes
+            d2 = a * a + b * b + 1.0
+            ed = a * e[0] + b * e[1] + e[2]
+            dist2 = (e @ e) + 2.0 * s * ed + s * s * d2
+            ok = np.isfinite(s) & (s > 0) & (dist2 < radius * radius) & (s < best)
             best = np.where(ok, s, best)
-        return np.where(np.isfinite(best) & (best >= 1.0) & (best <= 50.0), best, 0.0)
+        best = np.where(np.isfinite(best) & (best >= 1.0) & (best <= 50.0), best, 0.0)
+        return best.reshape(shape)
 
     def depth_map(self, R, t, K, width, height):
         jj, ii = np.meshgrid(np.arange(height) + 0.5, np.arange(width) + 0.5, indexing="ij")

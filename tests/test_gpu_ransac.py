@@ -99,26 +99,36 @@ def test_minimal_samples_full_size_sampled(ctx):
     assert res["status"] == 0
 
 
-def solution_condition(y, X, lam):
-    """Smallest / largest singular value of the Jacobian of the three distance
-    equations at a solution: small values mark near-degenerate triples."""
-    b12, b13, b23 = y[0] @ y[1], y[0] @ y[2], y[1] @ y[2]
-    L = lam
-    J = np.array([[2 * (L[0] - b12 * L[1]), 2 * (L[1] - b12 * L[0]), 0],
-                  [2 * (L[0] - b13 * L[2]), 0, 2 * (L[2] - b13 * L[0])],
-                  [0, 2 * (L[1] - b23 * L[2]), 2 * (L[2] - b23 * L[1])]])
-    s = np.linalg.svd(J, compute_uv=False)
-    return s[-1] / s[0]
+def pose_sensitivity(q, idx, Ro, to, rng, trials=3, rel=1e-7):
+    """How far the oracle's solution moves when the float32 inputs of the
+    triple (pixels, world points) are perturbed at float32 rounding level
+    (relative 1e-7): |dR|_F + |dt| / max(1, |t|).  A triple whose solution
+    moves by more than 1e-5 here cannot be expected to match a float32-input
+    solver to 1e-4 and is counted as ill-conditioned."""
+    fx, fy, cx, cy = q["K"]
+    worst = 0.0
+    for _ in range(trials):
+        x = q["x"][idx].astype(np.float64) * (1 + rng.normal(0, rel, 3))
+        y = q["y"][idx].astype(np.float64) * (1 + rng.normal(0, rel, 3))
+        b = np.stack([(x - cx) / fx, (y - cy) / fy, np.ones(3)], 1)
+        b /= np.linalg.norm(b, axis=1, keepdims=True)
+        X = q["X"][idx].astype(np.float64) * (1 + rng.normal(0, rel, (3, 3)))
+        sp = oracle.p3p(b, X)
+        d = min([np.linalg.norm(R - Ro) + np.linalg.norm(t - to) / max(1.0, np.linalg.norm(to)) for R, t, _ in sp]
+                + [np.inf])
+        worst = max(worst, d)
+    return worst
 
 
 def test_p3p_poses_against_oracle(c1_run):
     q, res, dbg = c1_run
-    n = len(q["x"])
+    rng = np.random.default_rng(0)
     tri = dbg["triples"].reshape(-1, 3)
     poses = dbg["poses"].reshape(-1, 4, 12)
     scores = dbg["scores"].reshape(-1, 4)
     matched = total = well = well_matched = 0
     extra = 0
+    misses = []
     for s in range(q["hypotheses"]):
         if tri[s][0] < 0:
             continue
@@ -130,20 +140,22 @@ def test_p3p_poses_against_oracle(c1_run):
                for k in range(4) if not np.isnan(scores[s, k])]
         for Ro, to, lam in sols:
             total += 1
-            cond = solution_condition(y, X, lam)
-            close = min([min(abs(l - lam[0]) for l in [o[2][0] for o in sols if o[2] is not lam] + [np.inf])]) / lam[0]
             ok = any(np.linalg.norm(Rg - Ro) <= 1e-4 and np.linalg.norm(tg - to) <= 1e-4 * max(1.0, np.linalg.norm(to))
                      for Rg, tg in gpu)
             matched += ok
-            if cond > 1e-2 and close > 1e-2:
+            kappa = pose_sensitivity(q, idx, Ro, to, rng)
+            if kappa < 1e-5:
                 well += 1
                 well_matched += ok
+                if not ok:
+                    misses.append((s, kappa, len(sols), len(gpu)))
         # every GPU pose must be a true solution too
         for Rg, tg in gpu:
             if not any(np.linalg.norm(Rg - Ro) <= 1e-3 for Ro, _, _ in sols):
                 extra += 1
+    print(f"p3p: {matched}/{total} matched, well-conditioned {well_matched}/{well}, extra {extra}")
     assert total > 1000
-    assert well_matched == well, (well_matched, well)
+    assert well_matched == well, misses[:10]
     assert matched >= 0.995 * total, (matched, total)
     assert extra <= 0.005 * total
 
