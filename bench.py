@@ -47,9 +47,10 @@ N_VIEWS = 10
 FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored pair, see the design doc
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes per launch of k_score from the committed ncu capture (profiles/);
-# None until a capture of the current kernel exists.
-SCORE_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of k_score from the committed ncu
+# capture of the current kernel (4-query case scaled by 16/4 queries);
+# None whenever the kernel changed since the capture.
+SCORE_TRAFFIC_PER_LAUNCH = 27.6e6
 
 
 # ---------------------------------------------------------------------------

@@ -8,8 +8,9 @@
 // that vanish at every solution, as does D0 = D1 + g D2 for any g.  Choosing
 // g as a real root of det(D1 + g D2) = 0 makes D0 a rank-2 indefinite form:
 // it factors into two planes through the origin, sigma1 (e1.L)^2 + sigma2
-// (e2.L)^2 = 0.  On each plane l1 = w0 l2 + w1 l3, and a second vanishing form
-// gives a quadratic in l2 / l3; the scale follows from the a23 equation.
+// (e2.L)^2 = 0.  On each plane the depth with the largest normal component is
+// eliminated, a second vanishing form gives a quadratic in the ratio of the
+// other two, and the scale follows from the sum of the distance equations.
 // The depths are polished by Newton on the distance equations (FP64 when
 // requested) and the pose is read off the triangle: R maps the world edge
 // frame (X1-X2, X1-X3, cross) onto the camera one, t = l1 y1 - R X1.
@@ -216,30 +217,49 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
 
     float Ls[4][3];
     int ns = 0;
+    const float asum = A12 + A13 + A23;
 #pragma unroll
     for (int sign = 0; sign < 2; ++sign) {
         const float ss = sign ? -s : s;
-        const float n0 = e1[0] - ss * e2[0], n1 = e1[1] - ss * e2[1], n2 = e1[2] - ss * e2[2];
-        if (fabsf(n0) < 1e-6f * (fabsf(n1) + fabsf(n2))) continue;
-        const float w0 = -n1 / n0, w1 = -n2 / n0;
-        // restriction of D to the plane, in (l2, l3)
-        const float q00 = w0 * (D.a00 * w0 + D.a01) + (D.a01 * w0 + D.a11);
-        const float q01 = w0 * (D.a00 * w1 + D.a02) + (D.a01 * w1 + D.a12);
-        const float q11 = w1 * (D.a00 * w1 + D.a02) + (D.a02 * w1 + D.a22);
+        const float n[3] = {e1[0] - ss * e2[0], e1[1] - ss * e2[1], e1[2] - ss * e2[2]};
+        // on the plane n.L = 0 eliminate the depth with the largest |n_k|;
+        // the other two, (l_i, l_j) = l_j (tau, 1), stay free
+        int k = 0;
+        if (fabsf(n[1]) > fabsf(n[k])) k = 1;
+        if (fabsf(n[2]) > fabsf(n[k])) k = 2;
+        const int i = (k == 0) ? 1 : 0, j = (k == 2) ? 1 : 2;
+        if (!(fabsf(n[k]) > 0.f)) continue;
+        const float ci = -n[i] / n[k], cj = -n[j] / n[k];  // l_k = ci l_i + cj l_j
+        // A = columns (d l / d l_i, d l / d l_j); Q = A^T D A restricted to the plane
+        float ai[3] = {0.f, 0.f, 0.f}, aj[3] = {0.f, 0.f, 0.f};
+        ai[i] = 1.f; ai[k] = ci;
+        aj[j] = 1.f; aj[k] = cj;
+        const float Dai[3] = {D.a00 * ai[0] + D.a01 * ai[1] + D.a02 * ai[2], D.a01 * ai[0] + D.a11 * ai[1] + D.a12 * ai[2],
+                              D.a02 * ai[0] + D.a12 * ai[1] + D.a22 * ai[2]};
+        const float Daj[3] = {D.a00 * aj[0] + D.a01 * aj[1] + D.a02 * aj[2], D.a01 * aj[0] + D.a11 * aj[1] + D.a12 * aj[2],
+                              D.a02 * aj[0] + D.a12 * aj[1] + D.a22 * aj[2]};
+        const float q00 = ai[0] * Dai[0] + ai[1] * Dai[1] + ai[2] * Dai[2];
+        const float q01 = ai[0] * Daj[0] + ai[1] * Daj[1] + ai[2] * Daj[2];
+        const float q11 = aj[0] * Daj[0] + aj[1] * Daj[1] + aj[2] * Daj[2];
         const float dq = q01 * q01 - q00 * q11;
         if (dq < 0.f || q00 == 0.f) continue;
         const float sq = sqrtf(dq);
-        // stable roots of q00 tau^2 + 2 q01 tau + q11 = 0
+        // stable roots of q00 tau^2 + 2 q01 tau + q11 = 0, tau = l_i / l_j
         const float tmp = -q01 - copysignf(sq, q01);
         const float taus[2] = {tmp / q00, (tmp != 0.f) ? q11 / tmp : 0.f};
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const float tau = taus[k];
+        for (int r = 0; r < 2; ++r) {
+            const float tau = taus[r];
             if (!(tau > 0.f)) continue;
-            const float den = tau * tau - 2.f * b23 * tau + 1.f;
+            const float v[3] = {tau * ai[0] + aj[0], tau * ai[1] + aj[1], tau * ai[2] + aj[2]};
+            // scale from the sum of the three distance equations (all solutions satisfy it)
+            const float den = (v[0] * v[0] + v[1] * v[1] - 2.f * b12 * v[0] * v[1]) +
+                              (v[0] * v[0] + v[2] * v[2] - 2.f * b13 * v[0] * v[2]) +
+                              (v[1] * v[1] + v[2] * v[2] - 2.f * b23 * v[1] * v[2]);
             if (!(den > 0.f)) continue;
-            const float l3 = sqrtf(A23 / den), l2 = tau * l3, l1 = w0 * l2 + w1 * l3;
-            if (!(l1 > 0.f)) continue;
+            const float lj = sqrtf(asum / den);
+            const float l1 = v[0] * lj, l2 = v[1] * lj, l3 = v[2] * lj;
+            if (!(l1 > 0.f) || !(l2 > 0.f) || !(l3 > 0.f)) continue;
             if (ns < 4) {
                 Ls[ns][0] = l1; Ls[ns][1] = l2; Ls[ns][2] = l3;
                 ++ns;
