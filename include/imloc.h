@@ -140,6 +140,27 @@ int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* que
                            const imloc_view* views, int32_t n_views, const imloc_matches* m,
                            imloc_corr* out, int64_t* d_offsets, void* stream);
 
+/* Allocation-free lift (the paper has no counterpart; this is a deployment
+ * aid).  For callers that cannot allocate device memory -- code running in a
+ * memory pool or budget owned by someone else, processes that reserve all
+ * device memory for other components up front, or callers that must not
+ * create a context (imloc_create allocates its workspace): it lifts one
+ * query exactly like imloc_lift_async but needs no context and performs no
+ * allocation.  Its scratch (scan state of the compaction, view and segment
+ * tables; 113,152 bytes) is a fixed array inside the library that every GPU
+ * loading the library holds until the process exits.
+ *   - Uses the calling thread's current CUDA device.  The first call on a
+ *     device looks the array's device address up (cudaGetSymbolAddress);
+ *     make that first call before any stream capture.
+ *   - Limits: m->n <= 8,388,608 matches, n_views <= 256, n_segments <= 1024;
+ *     larger inputs return IMLOC_ERR_INVALID_ARG without doing any work.
+ *   - Every call shares the one array: calls that overlap on the GPU (on
+ *     different streams, or from several threads without ordering) race and
+ *     give wrong results.  Calls on one stream are ordered and safe.
+ *   - Host buffers (views, segments) may be freed once the call returns. */
+int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views, const imloc_matches* m, imloc_corr* out,
+                             void* stream);
+
 /* ---- LO-RANSAC PnP (ImLoc Sec. 3.3, "Pose Estimation") -----------------
  * Rounds of `batch` minimal sets of 3 correspondences drawn from a uniform
  * stride subsample of at most `max_score_corr` correspondences; every P3P

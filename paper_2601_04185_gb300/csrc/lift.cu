@@ -370,3 +370,148 @@ int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* que
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free lift.
+//
+// Some callers cannot allocate device memory at all: code running inside a
+// memory pool or budget that it does not own, hosts that reserve all device
+// memory up front for other components, and callers that must not create a
+// context (imloc_create allocates a workspace).  imloc_lift_noalloc_async
+// gives them the lift without any allocation: its scratch (the scan state of
+// the stable compaction and the view / segment tables) lives in the
+// fixed-size file-scope array below, which every GPU that loads this library
+// holds until the process exits.
+// ============================================================================
+namespace imloc {
+
+constexpr int kNoAllocMaxTiles = 8192;  // 8192 tiles x 1024 matches = 8,388,608 matches per call
+constexpr int kNoAllocMaxViews = 256;
+constexpr int kNoAllocMaxSegments = 1024;
+constexpr size_t noalloc_round256(size_t v) { return (v + 255) / 256 * 256; }
+constexpr size_t kNoAllocScanBytes = noalloc_round256(sizeof(unsigned long long) * (kNoAllocMaxTiles + 1));
+constexpr size_t kNoAllocSegBytes = noalloc_round256(sizeof(LiftSeg) * kNoAllocMaxSegments);
+constexpr size_t kNoAllocViewBytes = noalloc_round256(sizeof(LiftView) * kNoAllocMaxViews);
+constexpr size_t kNoAllocScratchBytes = kNoAllocScanBytes + kNoAllocSegBytes + kNoAllocViewBytes + 256;
+
+// In host code this name is only a stand-in for the device array: its device
+// address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_lift_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static unsigned char* g_noalloc_addr[kNoAllocMaxDevices];
+
+}  // namespace imloc
+
+extern "C" int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                                        imloc_corr* out, void* stream) {
+    using namespace imloc;
+    if (!views || !m || !out || n_views <= 0) return IMLOC_ERR_INVALID_ARG;
+    // fixed limits of the static scratch
+    if (m->n < 0 || m->n > static_cast<int64_t>(kNoAllocMaxTiles) * kLiftTile) return IMLOC_ERR_INVALID_ARG;
+    if (n_views > kNoAllocMaxViews || m->n_segments > kNoAllocMaxSegments) return IMLOC_ERR_INVALID_ARG;
+    if (out->capacity < m->n) return IMLOC_ERR_CAPACITY;
+    if (m->n > 0) {
+        if (!m->q_u || !m->q_v || !m->db_u || !m->db_v || !m->conf || !m->segments || m->n_segments <= 0)
+            return IMLOC_ERR_INVALID_ARG;
+        if (!out->x || !out->y || !out->X || !out->Y || !out->Z || !out->w || !out->src) return IMLOC_ERR_INVALID_ARG;
+        if (m->segments[0].begin != 0) return IMLOC_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < m->n_segments; ++s) {
+        const imloc_segment& sg = m->segments[s];
+        if (sg.view < 0 || sg.view >= n_views || (sg.direction != 0 && sg.direction != 1)) return IMLOC_ERR_INVALID_ARG;
+        if (s > 0 && sg.begin < m->segments[s - 1].begin) return IMLOC_ERR_INVALID_ARG;
+        if (sg.begin > m->n) return IMLOC_ERR_INVALID_ARG;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const imloc_view& V = views[v];
+        if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
+        if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
+    }
+
+    // device address of the scratch array, looked up once per device
+    int dev = 0;
+    IMLOC_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return IMLOC_ERR_INVALID_ARG;
+    unsigned char* base;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void* ptr = nullptr;
+            IMLOC_CUDA_TRY(cudaGetSymbolAddress(&ptr, g_lift_noalloc_scratch));
+            g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+        }
+        base = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long* scan = reinterpret_cast<unsigned long long*>(base);
+    LiftSeg* d_segs = reinterpret_cast<LiftSeg*>(base + kNoAllocScanBytes);
+    LiftView* d_views = reinterpret_cast<LiftView*>(base + kNoAllocScanBytes + kNoAllocSegBytes);
+    int* d_err = reinterpret_cast<int*>(base + kNoAllocScanBytes + kNoAllocSegBytes + kNoAllocViewBytes);
+
+    if (m->n == 0) {
+        if (out->count) IMLOC_CUDA_TRY(cudaMemsetAsync(out->count, 0, sizeof(int32_t), st));
+        return IMLOC_OK;
+    }
+    // tables in fixed-size host arrays (no heap), copied into the scratch
+    LiftSeg segs[kNoAllocMaxSegments];
+    LiftView lv[kNoAllocMaxViews];
+    int n_seg = 0;
+    for (int s = 0; s < m->n_segments; ++s) {
+        const int64_t b = m->segments[s].begin;
+        const int64_t e = (s + 1 < m->n_segments) ? m->segments[s + 1].begin : m->n;
+        if (e <= b) continue;
+        LiftSeg& L = segs[n_seg++];
+        L.begin = b;
+        L.view = m->segments[s].view;
+        L.dir = m->segments[s].direction;
+        L.q_lo = L.q_hi = 0;
+    }
+    for (int v = 0; v < n_views; ++v) {
+        const imloc_view& V = views[v];
+        LiftView& L = lv[v];
+        L.depth = V.depth;
+        L.pitch = V.pitch;
+        L.W = V.width;
+        L.H = V.height;
+        L.ifx = static_cast<float>(1.0 / static_cast<double>(V.cam.fx));
+        L.ify = static_cast<float>(1.0 / static_cast<double>(V.cam.fy));
+        L.cx = V.cam.cx;
+        L.cy = V.cam.cy;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) L.Rt[3 * r + c] = static_cast<float>(V.pose.R[3 * c + r]);
+        for (int r = 0; r < 3; ++r) {
+            double cr = 0.0;
+            for (int c = 0; c < 3; ++c) cr -= V.pose.R[3 * c + r] * V.pose.t[c];
+            L.C[r] = static_cast<float>(cr);
+        }
+    }
+    const int n_tiles = static_cast<int>((m->n + kLiftTile - 1) / kLiftTile);
+    // the array keeps the previous call's contents: clear the scan state and the error word
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(d_segs, segs, sizeof(LiftSeg) * n_seg, cudaMemcpyHostToDevice, st));
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(d_views, lv, sizeof(LiftView) * n_views, cudaMemcpyHostToDevice, st));
+    IMLOC_CUDA_TRY(cudaMemsetAsync(scan, 0, sizeof(unsigned long long) * (n_tiles + 1), st));
+    IMLOC_CUDA_TRY(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+
+    LiftParams p;
+    p.q_u = m->q_u; p.q_v = m->q_v; p.db_u = m->db_u; p.db_v = m->db_v; p.conf = m->conf;
+    p.n = m->n;
+    p.segs = d_segs;
+    p.n_seg = n_seg;
+    p.n_tiles = n_tiles;
+    p.views = d_views;
+    p.conf_min = 0.05f;
+    p.ox = out->x; p.oy = out->y; p.oX = out->X; p.oY = out->Y; p.oZ = out->Z; p.ow = out->w;
+    p.osrc = out->src;
+    p.count = out->count;
+    p.offsets = nullptr;
+    p.tail_q_lo = 1;
+    p.n_queries = 0;
+    p.tile_state = scan + 1;
+    p.tile_counter = reinterpret_cast<uint32_t*>(scan);
+    p.err = d_err;
+    k_lift<<<n_tiles, kLiftThreads, 0, st>>>(p);
+    IMLOC_CUDA_TRY(cudaGetLastError());
+    return IMLOC_OK;
+}

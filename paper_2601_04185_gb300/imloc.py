@@ -75,7 +75,8 @@ class Debug(C.Structure):
 # every symbol declared in include/imloc.h and include/imloc_testing.h
 EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda_error", "imloc_device_error",
            "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
-           "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read"]
+           "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
+           "imloc_lift_noalloc_async"]
 
 _lib = None
 
@@ -104,6 +105,7 @@ def load(path: str = LIB_PATH):
     L.imloc_ransac_pnp.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Result), V, V]
     L.imloc_ransac_pnp_batch_async.argtypes = [V, C.c_int32, P(Corr), V, P(Camera), P(RansacOpts), V, V, V]
     L.imloc_testing_ransac.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Debug), P(Result), V, V]
+    L.imloc_lift_noalloc_async.argtypes = [P(View), C.c_int32, P(Matches), P(Corr), V]
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     _lib = L
