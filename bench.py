@@ -50,7 +50,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of k_score from the committed ncu
 # capture of the current kernel (4-query case scaled by 16/4 queries);
 # None whenever the kernel changed since the capture.
-SCORE_TRAFFIC_PER_LAUNCH = 27.6e6
+SCORE_TRAFFIC_PER_LAUNCH = None
 
 
 # ---------------------------------------------------------------------------
@@ -407,6 +407,10 @@ def run_ours(args):
         "gpu_launches": int(sum(launches.values())),
         "clocks": clocks,
         "result_status": statuses,
+        "per_query": {"lo_runs_mean": float(np.mean([r["lo_count"] for r in res])),
+                      "gn_passes_mean": float(np.mean([r["passes"] for r in res])),
+                      "hypotheses_mean": float(np.mean([r["hypotheses"] for r in res])),
+                      "inliers_mean": float(np.mean([r["num_inliers"] for r in res]))},
         "paper_context": "ImLoc reports ~200 ms per query for its RANSAC loop on an RTX 4090 (Sec. 4.4); "
                          "different hardware and data",
     }

@@ -203,7 +203,7 @@ typedef struct {
     int64_t hypotheses;          /* P3P poses scored */
     int64_t best_hyp;            /* 4 * sample + solution index of the last accepted round best */
     int32_t status;              /* IMLOC_OK or IMLOC_ERR_DEGENERATE / IMLOC_ERR_TIMEOUT */
-    int32_t reserved;
+    int32_t passes;              /* diagnostic: reduction passes over the correspondences in LO + refinement */
 } imloc_result;
 
 /* One query.  `corr->count` (device) gives N when non-NULL, else

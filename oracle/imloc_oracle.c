@@ -579,13 +579,16 @@ static int gauss_newton(const orc_corr* c, const int64_t* idx, int64_t m, const 
             mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
         }
         if (!ok) break;
+        const double decrease = cost - cn;
         memcpy(R, Rn, sizeof(Rn));
         memcpy(t, tn, sizeof(tn));
-        cost = cn;
         ++accepted_steps;
         double dn = 0;
         for (int a = 0; a < 6; ++a) dn += d[a] * d[a];
-        if (sqrt(dn) < 1e-10) break;
+        /* converged: a tiny step, or a step that lowered the cost by < 1e-6 of it */
+        const int converged = sqrt(dn) < 1e-10 || decrease < 1e-6 * cost;
+        cost = cn;
+        if (converged) break;
     }
     *cost_io = cost;
     return accepted_steps;

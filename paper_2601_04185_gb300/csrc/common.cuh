@@ -178,6 +178,8 @@ struct QueryState {
     int32_t done;
     int32_t finished;        // final refinement done and result written
     int32_t status;
+    int32_t passes;          // reduction passes of LO and refinement (diagnostic)
+    int32_t pad;
 };
 
 }  // namespace imloc

@@ -27,6 +27,9 @@ struct imloc_ctx {
     int* d_err = nullptr;         // sticky device error word
     cudaStream_t last_stream = nullptr;
     std::mutex mu;                // serialises calls on one context
+    // autotuned score-kernel variant (-1: not tuned yet)
+    int score_variant = -1;
+    float score_variant_ms = 0.f;
     // tracing: CUDA events around every kernel launch while enabled
     bool prof_on = false;
     struct ProfRec { const char* name; cudaEvent_t a, b; };

@@ -89,13 +89,15 @@ __device__ __forceinline__ void sym3_null(const Sym3& m, float v[3]) {
     v[0] = c[best][0] * inv; v[1] = c[best][1] * inv; v[2] = c[best][2] * inv;
 }
 
-// Newton polish of the depths on the three distance equations.
+// Newton polish of the depths on the three distance equations: at most
+// `iters` steps, stopping once every residual is below tol * a_ij.
 template <typename T>
-__device__ __forceinline__ void polish_depths(T L[3], const T a[3], const T b[3], int iters) {
+__device__ __forceinline__ void polish_depths(T L[3], const T a[3], const T b[3], int iters, T tol) {
     for (int it = 0; it < iters; ++it) {
         const T f0 = L[0] * L[0] + L[1] * L[1] - T(2) * b[0] * L[0] * L[1] - a[0];
         const T f1 = L[0] * L[0] + L[2] * L[2] - T(2) * b[1] * L[0] * L[2] - a[1];
         const T f2 = L[1] * L[1] + L[2] * L[2] - T(2) * b[2] * L[1] * L[2] - a[2];
+        if (fabs(f0) <= tol * a[0] && fabs(f1) <= tol * a[1] && fabs(f2) <= tol * a[2]) return;
         const T j00 = T(2) * (L[0] - b[0] * L[1]), j01 = T(2) * (L[1] - b[0] * L[0]);
         const T j10 = T(2) * (L[0] - b[1] * L[2]), j12 = T(2) * (L[2] - b[1] * L[0]);
         const T j21 = T(2) * (L[1] - b[2] * L[2]), j22 = T(2) * (L[2] - b[2] * L[1]);
@@ -283,7 +285,7 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
             const double b[3] = {yd[0][0] * yd[1][0] + yd[0][1] * yd[1][1] + yd[0][2] * yd[1][2],
                                  yd[0][0] * yd[2][0] + yd[0][1] * yd[2][1] + yd[0][2] * yd[2][2],
                                  yd[1][0] * yd[2][0] + yd[1][1] * yd[2][1] + yd[1][2] * yd[2][2]};
-            polish_depths<double>(L, a, b, 3);
+            polish_depths<double>(L, a, b, 4, 1e-13);
             const double f0 = L[0] * L[0] + L[1] * L[1] - 2.0 * b[0] * L[0] * L[1] - a[0];
             const double f1 = L[0] * L[0] + L[2] * L[2] - 2.0 * b[1] * L[0] * L[2] - a[1];
             const double f2 = L[1] * L[1] + L[2] * L[2] - 2.0 * b[2] * L[1] * L[2] - a[2];
@@ -294,7 +296,7 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
         } else {
             float L[3] = {Ls[k][0] * scale, Ls[k][1] * scale, Ls[k][2] * scale};
             const float a[3] = {a12, a13, a23}, b[3] = {b12, b13, b23};
-            polish_depths<float>(L, a, b, 2);
+            polish_depths<float>(L, a, b, 2, 1e-6f);
             const float f0 = L[0] * L[0] + L[1] * L[1] - 2.0f * b[0] * L[0] * L[1] - a[0];
             const float f1 = L[0] * L[0] + L[2] * L[2] - 2.0f * b[1] * L[0] * L[2] - a[1];
             const float f2 = L[1] * L[1] + L[2] * L[2] - 2.0f * b[2] * L[1] * L[2] - a[2];

@@ -30,6 +30,7 @@
 //                  FP64 6x6 Cholesky), termination, final Cauchy IRLS.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -294,7 +295,11 @@ __global__ void __launch_bounds__(1024) k_tiles(const __grid_constant__ TilesPar
 // ============================================================================
 // k_score: persistent, cluster-split hypothesis scoring
 // ============================================================================
-constexpr int kChunk = 256;  // subset records per shared-memory stage (8 KB)
+constexpr int kChunk = 256;        // subset records per bulk copy (8 KB)
+constexpr int kScoreCluster = 8;   // CTAs per (query, pose tile) item: they split the subset
+constexpr int kWinRecords = 1280;  // records resident per CTA (40 KB): M <= 10,240 in one window
+constexpr int kWinChunks = kWinRecords / kChunk;
+constexpr int kTileHyps = 512;     // poses per item (THREADS x HT for every variant)
 
 struct ScoreParams {
     const QueryDesc* qd;
@@ -307,14 +312,21 @@ struct ScoreParams {
     int* err;
 };
 
+// Each CTA keeps its share of the query's subset resident in shared memory:
+// one bulk copy (and one mbarrier) per 256-record chunk, so compute starts on
+// chunk 0 while the rest lands, no block barrier between chunks, and the
+// next item of the same query reuses the data.  Every thread scores HT poses
+// held in registers against every record of the share, in record order, so
+// the partial sums do not depend on (THREADS, HT).
 template <int THREADS, int HT, bool COUNT>
 __global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ ScoreParams p) {
-    constexpr int TH = THREADS * HT;
+    static_assert(THREADS * HT == kTileHyps, "tile size");
+    constexpr int TH = kTileHyps;
     extern __shared__ __align__(128) unsigned char smem[];
     ScoreCorr* buf = reinterpret_cast<ScoreCorr*>(smem);
-    float* s_part = reinterpret_cast<float*>(buf + 2 * kChunk);
+    float* s_part = reinterpret_cast<float*>(buf + kWinRecords);
     int* s_cnt = reinterpret_cast<int*>(s_part + TH);
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t bar[kWinChunks];
     __shared__ int s_item;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -322,12 +334,12 @@ __global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ Score
     const int rank = static_cast<int>(cluster.block_rank());
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int c = 0; c < kWinChunks; ++c) mbar_init(&bar[c], 1);
         mbar_fence_init();
     }
     __syncthreads();
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phases = 0u;           // parity bit per chunk barrier
+    int loaded_q = -1, loaded_w0 = -1, loaded_n = -1;
     const int total_tiles = p.tile_prefix[p.nq];
 
     for (;;) {
@@ -373,53 +385,60 @@ __global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ Score
         }
         const int c0 = static_cast<int>(static_cast<int64_t>(m) * rank / CS);
         const int c1 = static_cast<int>(static_cast<int64_t>(m) * (rank + 1) / CS);
-        const int nchunks = (c1 - c0 + kChunk - 1) / kChunk;
+        const int nwin = (c1 - c0 + kWinRecords - 1) / kWinRecords;
         float acc[HT];
         int cnt[HT];
 #pragma unroll
         for (int h = 0; h < HT; ++h) { acc[h] = 0.f; cnt[h] = 0; }
 
-        if (tid == 0 && nchunks > 0) {
-            const int nrec = min(kChunk, c1 - c0);
-            mbar_arrive_expect_tx(&bar[0], nrec * 32u);
-            bulk_g2s(buf, d.subset + c0, nrec * 32u, &bar[0]);
-        }
-        for (int c = 0; c < nchunks; ++c) {
-            const int b = c & 1;
-            if (tid == 0 && c + 1 < nchunks) {
-                const int start = c0 + (c + 1) * kChunk;
-                const int nrec = min(kChunk, c1 - start);
-                mbar_arrive_expect_tx(&bar[b ^ 1], nrec * 32u);
-                bulk_g2s(buf + (b ^ 1) * kChunk, d.subset + start, nrec * 32u, &bar[b ^ 1]);
-            }
-            mbar_wait_bounded(&bar[b], phase[b], p.err);
-            phase[b] ^= 1u;
-            const int nrec = min(kChunk, c1 - (c0 + c * kChunk));
-            const float4* rec = reinterpret_cast<const float4*>(buf + b * kChunk);
-            float part[HT];
-#pragma unroll
-            for (int h = 0; h < HT; ++h) part[h] = 0.f;
-#pragma unroll 2
-            for (int k = 0; k < nrec; ++k) {
-                const float4 A = rec[2 * k];      // X Y Z w
-                const float4 Bq = rec[2 * k + 1]; // x y
-#pragma unroll
-                for (int h = 0; h < HT; ++h) {
-                    const float zu = fmaf(P[h][0], A.x, fmaf(P[h][1], A.y, fmaf(P[h][2], A.z, P[h][3])));
-                    const float zv = fmaf(P[h][4], A.x, fmaf(P[h][5], A.y, fmaf(P[h][6], A.z, P[h][7])));
-                    const float zz = fmaf(P[h][8], A.x, fmaf(P[h][9], A.y, fmaf(P[h][10], A.z, P[h][11])));
-                    // z <= 0 (or NaN) -> 1/0 = inf -> r2 inf/NaN -> min(., tau2) = tau2
-                    const float iz = rcp_approx(fmaxf(zz, 0.0f));
-                    const float du = fmaf(zu, iz, -Bq.x);
-                    const float dv = fmaf(zv, iz, -Bq.y);
-                    const float r2 = fmaf(du, du, dv * dv);
-                    part[h] = fmaf(A.w, fminf(r2, tau2), part[h]);
-                    if (COUNT) cnt[h] += (r2 < tau2) ? 1 : 0;
+        for (int w = 0; w < nwin; ++w) {
+            const int w0 = c0 + w * kWinRecords;
+            const int nrec_w = min(kWinRecords, c1 - w0);
+            const int nch = (nrec_w + kChunk - 1) / kChunk;
+            const bool reuse = (nwin == 1 && q == loaded_q && w0 == loaded_w0 && nrec_w == loaded_n);
+            if (!reuse) {
+                if (nwin > 1) __syncthreads();  // all threads done with the previous window
+                if (tid == 0) {
+                    for (int c = 0; c < nch; ++c) {
+                        const int nr = min(kChunk, nrec_w - c * kChunk);
+                        mbar_arrive_expect_tx(&bar[c], nr * 32u);
+                        bulk_g2s(buf + c * kChunk, d.subset + w0 + c * kChunk, nr * 32u, &bar[c]);
+                    }
                 }
+                if (nwin == 1) { loaded_q = q; loaded_w0 = w0; loaded_n = nrec_w; }
+                else loaded_q = -1;
             }
+            for (int c = 0; c < nch; ++c) {
+                if (!reuse) {
+                    mbar_wait_bounded(&bar[c], (phases >> c) & 1u, p.err);
+                    phases ^= (1u << c);
+                }
+                const int nrec = min(kChunk, nrec_w - c * kChunk);
+                const float4* rec = reinterpret_cast<const float4*>(buf + c * kChunk);
+                float part[HT];
 #pragma unroll
-            for (int h = 0; h < HT; ++h) acc[h] += part[h];
-            __syncthreads();
+                for (int h = 0; h < HT; ++h) part[h] = 0.f;
+#pragma unroll 2
+                for (int k = 0; k < nrec; ++k) {
+                    const float4 A = rec[2 * k];      // X Y Z w
+                    const float4 Bq = rec[2 * k + 1]; // x y
+#pragma unroll
+                    for (int h = 0; h < HT; ++h) {
+                        const float zu = fmaf(P[h][0], A.x, fmaf(P[h][1], A.y, fmaf(P[h][2], A.z, P[h][3])));
+                        const float zv = fmaf(P[h][4], A.x, fmaf(P[h][5], A.y, fmaf(P[h][6], A.z, P[h][7])));
+                        const float zz = fmaf(P[h][8], A.x, fmaf(P[h][9], A.y, fmaf(P[h][10], A.z, P[h][11])));
+                        // z <= 0 (or NaN) -> 1/0 = inf -> r2 inf/NaN -> min(., tau2) = tau2
+                        const float iz = rcp_approx(fmaxf(zz, 0.0f));
+                        const float du = fmaf(zu, iz, -Bq.x);
+                        const float dv = fmaf(zv, iz, -Bq.y);
+                        const float r2 = fmaf(du, du, dv * dv);
+                        part[h] = fmaf(A.w, fminf(r2, tau2), part[h]);
+                        if (COUNT) cnt[h] += (r2 < tau2) ? 1 : 0;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < HT; ++h) acc[h] += part[h];
+            }
         }
 
         // combine the CS partial sums of each pose through distributed shared memory
@@ -464,14 +483,34 @@ __global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ Score
             }
         }
         // s_part is rewritten only after the next item's first cluster barrier,
-        // which every CTA reaches after finishing the reads above.
+        // which every CTA reaches after finishing the reads above; the subset
+        // buffer is rewritten only after both item barriers.
     }
+}
+
+// score kernel variants the autotuner chooses from (same results, different speed)
+struct ScoreVariant {
+    int threads, ht;
+    void (*fn)(ScoreParams);
+    void (*fn_count)(ScoreParams);
+};
+static const ScoreVariant kScoreVariants[] = {
+    {128, 4, k_score<128, 4, false>, k_score<128, 4, true>},
+    {256, 2, k_score<256, 2, false>, k_score<256, 2, true>},
+    {64, 8, k_score<64, 8, false>, k_score<64, 8, true>},
+    {512, 1, k_score<512, 1, false>, k_score<512, 1, true>},
+};
+constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
+
+static size_t score_smem_bytes(bool count) {
+    return sizeof(ScoreCorr) * kWinRecords + sizeof(float) * kTileHyps + (count ? sizeof(int) * kTileHyps : 0);
 }
 
 // ============================================================================
 // k_replay: rounds in order, LO, termination, final refinement
 // ============================================================================
-constexpr int kRT = 512;
+constexpr int kRT = 256;
+constexpr int kMaxReplayCluster = 8;
 constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
 
 enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
@@ -481,7 +520,7 @@ struct ReplaySmem {
     double Rc[9], tc[3];  // candidate pose
     double H[21], g[6];   // normal equations at the current pose
     double cost, cnt;
-    double step;
+    double step, decrease, prev_cost;
     double tot[32];
     double xch[2][32];
     float red[kRT / 32][32];
@@ -506,6 +545,7 @@ __device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], 
 template <int MODE>
 __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) ++S.st.passes;
     constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
     constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
     float acc[kNV];
@@ -579,60 +619,90 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
             }
         }
     }
-    // block reduction (FP32 warp tree, FP64 across warps), then across the cluster in rank order
+    // block reduction: a transpose butterfly leaves the warp total of value l
+    // in lane l (31 shuffles for 32 values), FP64 across warps, then across
+    // the CTAs of the cluster in rank order (identical sums in every CTA)
+    float v[32];
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) {
-        const float v = warp_sum(acc[k]);
-        if (lane == 0) S.red[warp][k] = v;
+    for (int k = 0; k < 32; ++k) v[k] = k < kNV ? acc[k] : 0.f;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const float send = upper ? v[i] : v[i + o];
+            const float keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
     }
+    S.red[warp][lane] = v[0];
     __syncthreads();
     if (tid < kNV) {
-        double s = 0.0;
-        for (int w = 0; w < kRT / 32; ++w) s += static_cast<double>(S.red[w][tid]);
-        S.xch[slot][tid] = s;
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < kRT / 32; ++w) sum += static_cast<double>(S.red[w][tid]);
+        S.xch[slot][tid] = sum;
     }
     cluster.sync();
     if (tid < kNV) {
-        double s = 0.0;
-        for (int r = 0; r < CL; ++r) s += cluster.map_shared_rank(&S.xch[slot][0], r)[tid];
-        S.tot[tid] = s;
+        double part[kMaxReplayCluster];
+#pragma unroll
+        for (int r = 0; r < kMaxReplayCluster; ++r)
+            part[r] = r < CL ? cluster.map_shared_rank(&S.xch[slot][0], r)[tid] : 0.0;
+        double sum = 0.0;
+#pragma unroll
+        for (int r = 0; r < kMaxReplayCluster; ++r) sum += part[r];
+        S.tot[tid] = sum;
     }
     slot ^= 1;
     __syncthreads();
 }
 
-__device__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
+__device__ __forceinline__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
     double A[6][6];
     int k = 0;
+#pragma unroll
     for (int a = 0; a < 6; ++a)
+#pragma unroll
         for (int b = a; b < 6; ++b) {
             A[a][b] = Hu[k];
             A[b][a] = Hu[k];
             ++k;
         }
+#pragma unroll
     for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a];
-    double L[6][6];
-    for (int i = 0; i < 6; ++i)
+    // Cholesky A = L L^T (L overwrites the lower triangle of A); inv[j] = 1 / L_jj
+    double inv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
         for (int j = 0; j <= i; ++j) {
             double s = A[i][j];
-            for (int c = 0; c < j; ++c) s -= L[i][c] * L[j][c];
+#pragma unroll
+            for (int c = 0; c < j; ++c) s -= A[i][c] * A[j][c];
             if (i == j) {
                 if (!(s > 0.0)) return false;
-                L[i][i] = sqrt(s);
+                inv[i] = rsqrt(s);
+                A[i][i] = s * inv[i];
             } else {
-                L[i][j] = s / L[j][j];
+                A[i][j] = s * inv[j];
             }
         }
+    }
     double z[6];
+#pragma unroll
     for (int i = 0; i < 6; ++i) {
         double s = -g[i];
-        for (int c = 0; c < i; ++c) s -= L[i][c] * z[c];
-        z[i] = s / L[i][i];
+#pragma unroll
+        for (int c = 0; c < i; ++c) s -= A[i][c] * z[c];
+        z[i] = s * inv[i];
     }
+#pragma unroll
     for (int i = 5; i >= 0; --i) {
         double s = z[i];
-        for (int c = i + 1; c < 6; ++c) s -= L[c][i] * x[c];
-        x[i] = s / L[i][i];
+#pragma unroll
+        for (int c = i + 1; c < 6; ++c) s -= A[c][i] * x[c];
+        x[i] = s * inv[i];
     }
     return true;
 }
@@ -640,10 +710,18 @@ __device__ bool solve6(const double Hu[21], const double g[6], double mu, double
 // candidate = Exp(dw) * (R, t) + (0, dv)
 __device__ void apply_step(const double R[9], const double t[3], const double dl[6], double Rc[9], double tc[3]) {
     const double th2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-    const double th = sqrt(th2);
     double A, B;
-    if (th < 1e-8) { A = 1.0 - th2 / 6.0; B = 0.5 - th2 / 24.0; }
-    else { double sn, cs; sincos(th, &sn, &cs); A = sn / th; B = (1.0 - cs) / th2; }
+    if (th2 < 1e-4) {
+        // sin(th)/th and (1 - cos(th))/th^2 by their Taylor series (error < th^8/9! < 1e-21 here)
+        A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
+        B = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / th2;
+    }
     const double Kx[9] = {0, -dl[2], dl[1], dl[2], 0, -dl[0], -dl[1], dl[0], 0};
     double E[9];
     for (int i = 0; i < 3; ++i)
@@ -700,6 +778,8 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
                 __syncthreads();
                 if (better) {
                     if (tid == 0) {
+                        S.decrease = S.cost - S.tot[27];
+                        S.prev_cost = S.cost;
                         for (int k = 0; k < 9; ++k) S.R[k] = S.Rc[k];
                         for (int k = 0; k < 3; ++k) S.t[k] = S.tc[k];
                         take_totals(S);
@@ -712,7 +792,8 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
             mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
         }
         if (!accepted) break;
-        if (S.step < 1e-10) break;
+        // converged: a tiny step, or a step that lowered the cost by < 1e-6 of it
+        if (S.step < 1e-10 || S.decrease < 1e-6 * S.prev_cost) break;
     }
 }
 
@@ -730,6 +811,7 @@ __device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inli
     r.hypotheses = S.st.hypotheses;
     r.best_hyp = S.st.best_hyp;
     r.status = S.st.status;
+    r.passes = S.st.passes;
     if (d.result) *d.result = r;
 }
 
@@ -865,18 +947,9 @@ struct HostQuery {
     uint64_t* round_best_out;
 };
 
-struct Tuning {
-    int score_cluster;   // CTAs per (query, tile) item
-    int replay_cluster;  // CTAs per query in the replay
-};
-
-static Tuning pick_tuning(const imloc_ctx* ctx, int nq, int64_t total_hyp_estimate) {
-    Tuning t;
-    // few items: split each over more SMs; many: keep clusters small
-    const int64_t items = std::max<int64_t>(1, total_hyp_estimate / 512);
-    t.score_cluster = items >= 4 * ctx->sm_count ? 2 : (items >= ctx->sm_count ? 4 : 8);
-    t.replay_cluster = nq >= ctx->sm_count / 2 ? 1 : (nq >= ctx->sm_count / 8 ? 4 : 8);
-    return t;
+// CTAs per query in the replay: few queries -> spread each over more SMs
+static int replay_cluster_size(const imloc_ctx* ctx, int nq) {
+    return nq >= ctx->sm_count / 2 ? 1 : (nq >= ctx->sm_count / 8 ? 4 : 8);
 }
 
 template <typename K, typename P>
@@ -916,8 +989,50 @@ static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out)
 
 static int64_t comb3(int64_t m) { return m < 3 ? 0 : m * (m - 1) * (m - 2) / 6; }
 
+// Autotuner of the score kernel: every variant computes bitwise-identical
+// scores (same per-pose record order, same cluster reduction), so the
+// variants are timed on the live wave (the kernel is idempotent: it rewrites
+// the same scores and re-applies the same atomic minima) and the fastest is
+// kept for the context.  IMLOC_SCORE_VARIANT=<k> forces variant k.
+static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool counts, int64_t max_items,
+                      uint32_t* d_counter, cudaStream_t stream) {
+    if (const char* env = getenv("IMLOC_SCORE_VARIANT")) {
+        const int k = atoi(env);
+        ctx->score_variant = (k >= 0 && k < kNumScoreVariants) ? k : 0;
+        return IMLOC_OK;
+    }
+    cudaEvent_t e0, e1;
+    IMLOC_CUDA_TRY(cudaEventCreate(&e0));
+    IMLOC_CUDA_TRY(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = 0;
+    for (int rep = 0; rep < 2; ++rep)
+        for (int v = 0; v < kNumScoreVariants; ++v) {
+            const ScoreVariant& V = kScoreVariants[v];
+            auto kern = counts ? V.fn_count : V.fn;
+            int n_clusters = 0;
+            int rc = max_clusters(kern, V.threads, smem, kScoreCluster, &n_clusters);
+            if (rc != IMLOC_OK || n_clusters <= 0) continue;
+            const int grid = static_cast<int>(std::min<int64_t>(n_clusters, max_items));
+            IMLOC_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), stream));
+            IMLOC_CUDA_TRY(cudaEventRecord(e0, stream));
+            rc = launch_cluster(kern, scp, grid * kScoreCluster, V.threads, smem, kScoreCluster, stream);
+            if (rc != IMLOC_OK) return rc;
+            IMLOC_CUDA_TRY(cudaEventRecord(e1, stream));
+            IMLOC_CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            IMLOC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep == 1 && ms < best_ms) { best_ms = ms; best = v; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    IMLOC_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), stream));
+    ctx->score_variant = best;
+    ctx->score_variant_ms = best_ms;
+    return IMLOC_OK;
+}
+
 int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream, bool want_counts) {
-    constexpr int kThreads = 128, kHT = 4, kTH = kThreads * kHT;
     if (nq <= 0) return IMLOC_ERR_INVALID_ARG;
     // ---- per-query host-known sizes and the wave schedule ----
     std::vector<int64_t> H(nq), B(nq), R(nq);
@@ -1066,7 +1181,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         }
 
     // ---- launches ----
-    const Tuning tn = pick_tuning(ctx, nq, est_hyp);
+    const int replay_cl = replay_cluster_size(ctx, nq);
     {
         SetupParams sp{d_qd, d_qs, d_nhyp, W * nq};
         ProfScope prof(ctx, stream, "k_setup");
@@ -1074,16 +1189,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
     }
-    auto score_kernel = want_counts ? k_score<kThreads, kHT, true> : k_score<kThreads, kHT, false>;
-    const size_t score_smem = sizeof(ScoreCorr) * 2 * kChunk + sizeof(float) * kTH + sizeof(int) * kTH;
-    if (tn.score_cluster > 8 || tn.replay_cluster > 8) {
-        IMLOC_CUDA_TRY(cudaFuncSetAttribute(score_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-        IMLOC_CUDA_TRY(cudaFuncSetAttribute(k_replay, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    }
-    int n_clusters = 0;
-    rc = max_clusters(score_kernel, kThreads, score_smem, tn.score_cluster, &n_clusters);
-    if (rc != IMLOC_OK) return rc;
-    n_clusters = std::max(1, n_clusters);
+    const size_t score_smem = score_smem_bytes(want_counts);
     for (int w = 0; w < W; ++w) {
         const WaveQ* wq_w = d_wq + static_cast<size_t>(w) * nq;
         int32_t* nh_w = d_nhyp + static_cast<size_t>(w) * nq;
@@ -1095,7 +1201,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
             IMLOC_CUDA_TRY(cudaGetLastError());
             prof.end();
         }
-        TilesParams tp{d_qs, nh_w, d_tiles, d_counter, nq, kTH};
+        TilesParams tp{d_qs, nh_w, d_tiles, d_counter, nq, kTileHyps};
         {
             ProfScope prof(ctx, stream, "k_tiles");
             k_tiles<<<1, 1024, 0, stream>>>(tp);
@@ -1103,12 +1209,22 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
             prof.end();
         }
         ScoreParams scp{d_qd, d_qs, wq_w, nh_w, d_tiles, d_counter, nq, ctx->d_err};
-        const int64_t max_items = std::max<int64_t>(1, (wtotal[w] * 4 + kTH - 1) / kTH + nq);
-        const int grid_clusters = static_cast<int>(std::min<int64_t>(n_clusters, max_items));
+        const int64_t max_items = std::max<int64_t>(1, (wtotal[w] * 4 + kTileHyps - 1) / kTileHyps + nq);
+        // autotune the score kernel variant once per context on a large enough wave
+        if (ctx->score_variant < 0 && (max_items >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
+            rc = tune_score(ctx, scp, score_smem, want_counts, max_items, d_counter, stream);
+            if (rc != IMLOC_OK) return rc;
+        }
+        const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
+        auto score_kernel = want_counts ? V.fn_count : V.fn;
+        int n_clusters = 0;
+        rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
+        if (rc != IMLOC_OK) return rc;
+        const int grid_clusters = static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items));
         {
             ProfScope prof(ctx, stream, "k_score");
-            rc = launch_cluster(score_kernel, scp, grid_clusters * tn.score_cluster, kThreads, score_smem,
-                                tn.score_cluster, stream);
+            rc = launch_cluster(score_kernel, scp, grid_clusters * kScoreCluster, V.threads, score_smem, kScoreCluster,
+                                stream);
             if (rc != IMLOC_OK) return rc;
             prof.end();
         }
@@ -1116,7 +1232,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
                         ctx->d_err};
         {
             ProfScope prof(ctx, stream, "k_replay");
-            rc = launch_cluster(k_replay, rp, nq * tn.replay_cluster, kRT, 0, tn.replay_cluster, stream);
+            rc = launch_cluster(k_replay, rp, nq * replay_cl, kRT, 0, replay_cl, stream);
             if (rc != IMLOC_OK) return rc;
             prof.end();
         }

@@ -60,7 +60,7 @@ class Result(C.Structure):
     _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3), ("R_best", C.c_double * 9), ("t_best", C.c_double * 3),
                 ("score", C.c_double), ("num_inliers", C.c_int64), ("subset_inliers", C.c_int64),
                 ("iterations", C.c_int64), ("rounds", C.c_int64), ("lo_count", C.c_int64), ("hypotheses", C.c_int64),
-                ("best_hyp", C.c_int64), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("best_hyp", C.c_int64), ("status", C.c_int32), ("passes", C.c_int32)]
 
 
 class KernelStat(C.Structure):
@@ -157,7 +157,7 @@ def result_dict(r: Result) -> dict:
     return dict(R=np.array(r.R).reshape(3, 3), t=np.array(r.t), R_best=np.array(r.R_best).reshape(3, 3),
                 t_best=np.array(r.t_best), score=r.score, num_inliers=r.num_inliers,
                 subset_inliers=r.subset_inliers, iterations=r.iterations, rounds=r.rounds, lo_count=r.lo_count,
-                hypotheses=r.hypotheses, best_hyp=r.best_hyp, status=r.status)
+                hypotheses=r.hypotheses, best_hyp=r.best_hyp, status=r.status, passes=r.passes)
 
 
 def alloc_corr(capacity: int, device="cuda"):
