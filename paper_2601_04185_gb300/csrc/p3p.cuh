@@ -104,7 +104,14 @@ __device__ __forceinline__ void polish_depths(T L[3], const T a[3], const T b[3]
         // J = [[j00 j01 0], [j10 0 j12], [0 j21 j22]];  solve J d = f by Cramer
         const T det = j00 * (-j12 * j21) - j01 * (j10 * j22) ;
         if (det == T(0)) return;
-        const T inv = T(1) / det;
+        T inv;
+        if constexpr (sizeof(T) == 4) {
+            inv = T(1) / det;
+        } else {
+            // reciprocal: float32 seed, one Newton-Raphson step x (2 - det x) in FP64
+            const T r0 = static_cast<T>(1.0f / static_cast<float>(det));
+            inv = r0 * (T(2) - det * r0);
+        }
         const T d0 = (f0 * (-j12 * j21) - j01 * (f1 * j22 - j12 * f2)) * inv;
         const T d1 = (j00 * (f1 * j22 - j12 * f2) - f0 * (j10 * j22)) * inv;
         const T d2 = (j00 * (-j21 * f1) - j01 * (j10 * f2) + f0 * (j10 * j21)) * inv;
@@ -291,7 +298,11 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
             const double f2 = L[1] * L[1] + L[2] * L[2] - 2.0 * b[2] * L[1] * L[2] - a[2];
             good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabs(f0) <= 1e-4 * a[0] && fabs(f1) <= 1e-4 * a[1] &&
                    fabs(f2) <= 1e-4 * a[2];
-            if (good) good = pose_from_depths<double, double>(L, yd, X, out[nout].R, out[nout].t);
+            if (good) {
+                // the pose from the polished depths in float32 (the poses are scored in float32)
+                const float Lf3[3] = {float(L[0]), float(L[1]), float(L[2])};
+                good = pose_from_depths<float, float>(Lf3, y, X, out[nout].R, out[nout].t);
+            }
             Lf[0] = float(L[0]);
         } else {
             float L[3] = {Ls[k][0] * scale, Ls[k][1] * scale, Ls[k][2] * scale};

@@ -196,9 +196,9 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                     y[k][0] = bx * inv; y[k][1] = by * inv; y[k][2] = inv;
                     X[k][0] = c.X; X[k][1] = c.Y; X[k][2] = c.Z;
                     if (d.polish) {
-                        const double ex = (double(c.x) - double(d.cx)) / double(d.fx);
-                        const double ey = (double(c.y) - double(d.cy)) / double(d.fy);
-                        const double en = 1.0 / sqrt(ex * ex + ey * ey + 1.0);
+                        const double ex = (double(c.x) - double(d.cx)) * d.ifx_d;
+                        const double ey = (double(c.y) - double(d.cy)) * d.ify_d;
+                        const double en = rsqrt(ex * ex + ey * ey + 1.0);
                         yd[k][0] = ex * en; yd[k][1] = ey * en; yd[k][2] = en;
                     }
                 }
@@ -318,8 +318,8 @@ struct ScoreParams {
 // next item of the same query reuses the data.  Every thread scores HT poses
 // held in registers against every record of the share, in record order, so
 // the partial sums do not depend on (THREADS, HT).
-template <int THREADS, int HT, bool COUNT>
-__global__ void __launch_bounds__(THREADS) k_score(const __grid_constant__ ScoreParams p) {
+template <int THREADS, int HT, bool COUNT, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__ ScoreParams p) {
     static_assert(THREADS * HT == kTileHyps, "tile size");
     constexpr int TH = kTileHyps;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -495,10 +495,12 @@ struct ScoreVariant {
     void (*fn_count)(ScoreParams);
 };
 static const ScoreVariant kScoreVariants[] = {
-    {128, 4, k_score<128, 4, false>, k_score<128, 4, true>},
-    {256, 2, k_score<256, 2, false>, k_score<256, 2, true>},
-    {64, 8, k_score<64, 8, false>, k_score<64, 8, true>},
-    {512, 1, k_score<512, 1, false>, k_score<512, 1, true>},
+    {128, 4, k_score<128, 4, false, 1>, k_score<128, 4, true, 1>},
+    {256, 2, k_score<256, 2, false, 1>, k_score<256, 2, true, 1>},
+    {64, 8, k_score<64, 8, false, 1>, k_score<64, 8, true, 1>},
+    {512, 1, k_score<512, 1, false, 1>, k_score<512, 1, true, 1>},
+    {128, 4, k_score<128, 4, false, 5>, k_score<128, 4, true, 5>},   // <= 102 registers: 5 CTAs / SM
+    {256, 2, k_score<256, 2, false, 4>, k_score<256, 2, true, 4>},   // <= 64 registers: 4 CTAs / SM
 };
 constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
 
@@ -1112,6 +1114,8 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.mask = h.mask;
         d.result = h.d_result;
         d.fx = h.cam.fx; d.fy = h.cam.fy; d.cx = h.cam.cx; d.cy = h.cam.cy;
+        d.ifx_d = 1.0 / static_cast<double>(h.cam.fx);
+        d.ify_d = 1.0 / static_cast<double>(h.cam.fy);
         d.tau2 = static_cast<float>(o.tau_px * o.tau_px);
         const double cs = o.cauchy_scale > 0.0 ? o.cauchy_scale : o.tau_px;
         d.cauchy2 = static_cast<float>(cs * cs);
