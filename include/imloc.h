@@ -223,6 +223,52 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
                                  const imloc_ransac_opts* opts, imloc_result* d_results,
                                  uint8_t* d_masks, void* stream);
 
+/* ---- serving: continuous batching (lift + LO-RANSAC PnP) ---------------
+ * A server owns a scheduler thread, a device memory pool and a pinned host
+ * ring.  Queries are submitted with their matches in HOST memory (copied into
+ * the ring before imloc_serve_submit returns) and views whose depth maps are
+ * DEVICE memory of a resident map store (they must stay valid until the
+ * query's result has been polled).  The scheduler admits queued queries in
+ * arrival order while a slot is free and the device pool can hold the
+ * query's footprint (matches, correspondences, scratch), lifts them, and
+ * advances every resident query by its next RANSAC rounds in shared launches;
+ * a query submitted while others run joins at the next step.  Each result
+ * equals the one of a plain single-query call up to floating-point
+ * reduction order (same Philox samples, same rounds). */
+typedef struct imloc_server imloc_server;
+
+typedef struct {
+    int32_t max_slots;          /* queries resident on the GPU at once (64) */
+    int32_t max_queue;          /* queued, not yet admitted (4096); more: IMLOC_ERR_REJECTED */
+    size_t device_budget_bytes; /* device pool for resident queries (1 GiB) */
+    size_t host_staging_bytes;  /* pinned ring for submitted matches (256 MiB) */
+    int32_t rounds_per_step;    /* RANSAC rounds a resident query advances per step (2; the first step: 1) */
+    int32_t reserved;
+} imloc_serve_config;
+
+typedef struct {
+    int64_t submitted, rejected, admitted, completed, steps, pending, resident;
+    size_t device_bytes_in_use;
+} imloc_serve_stats;
+
+void imloc_serve_default_config(imloc_serve_config* cfg);
+/* Create a server on ctx's device (the server allocates its own pool, ring and
+ * internal context; ctx stays free for other calls). */
+int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_server** out);
+/* Queue one query.  m: HOST arrays (n matches) and host segments; views: host
+ * array of views with device depth maps.  IMLOC_ERR_REJECTED when the queue
+ * is full, the staging ring has no room or the query can never fit the
+ * device budget. */
+int imloc_serve_submit(imloc_server* srv, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                       const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket);
+/* IMLOC_PENDING until done; then IMLOC_OK once with the result (out->status
+ * holds the query's own status) and the submit-to-ready latency in ms
+ * (optional); IMLOC_ERR_NOT_FOUND for an unknown or already consumed ticket. */
+int imloc_serve_poll(imloc_server* srv, uint64_t ticket, imloc_result* out, double* latency_ms);
+int imloc_serve_read_stats(imloc_server* srv, imloc_serve_stats* out);
+/* Stops the scheduler after its current step; queued and resident queries are dropped. */
+int imloc_serve_destroy(imloc_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ L
 }
 
 // Host side: build the view / segment tables, upload, launch.
-static int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, const imloc_view* views,
+int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, const imloc_view* views,
                      int32_t n_views, const imloc_matches* m, imloc_corr* out, int64_t* d_offsets,
                      cudaStream_t stream) {
     if (!views || n_views <= 0 || !m || !out || n_queries <= 0 || !query_begin) return IMLOC_ERR_INVALID_ARG;

@@ -39,15 +39,11 @@
 #include "common.cuh"
 #include "ctx.h"
 #include "p3p.cuh"
+#include "ransac_internal.h"
 #include "../../include/imloc_testing.h"
 
 namespace imloc {
 
-struct WaveQ {
-    int64_t s_begin;    // first minimal sample of the wave for this query
-    int32_t n_samples;  // samples of the wave for this query
-    int32_t pad;
-};
 
 // ============================================================================
 // k_setup
@@ -55,12 +51,13 @@ struct WaveQ {
 struct SetupParams {
     const QueryDesc* qd;
     QueryState* qs;
-    int32_t* n_hyp_all;  // [waves * nq], zeroed here
+    int32_t* n_hyp_all;       // [waves * nq], zeroed here (may be null)
     int32_t n_hyp_len;
+    const int32_t* init_list; // if non-null: block b sets up query init_list[b]
 };
 
 __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupParams p) {
-    const int q = blockIdx.x;
+    const int q = p.init_list ? p.init_list[blockIdx.x] : blockIdx.x;
     const QueryDesc& d = p.qd[q];
     __shared__ int64_t s_off, s_n;
     __shared__ int32_t s_m;
@@ -97,7 +94,8 @@ __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupPara
         s_n = n;
         s_m = m;
     }
-    for (int i = blockIdx.x * 256 + threadIdx.x; i < p.n_hyp_len; i += gridDim.x * 256) p.n_hyp_all[i] = 0;
+    if (p.n_hyp_all)
+        for (int i = blockIdx.x * 256 + threadIdx.x; i < p.n_hyp_len; i += gridDim.x * 256) p.n_hyp_all[i] = 0;
     __syncthreads();
     for (int r = threadIdx.x; r < d.rounds; r += 256) {
         d.round_best[r] = ~0ull;
@@ -535,7 +533,6 @@ struct ReplayParams {
     const QueryDesc* qd;
     QueryState* qs;
     const WaveQ* wq;
-    int32_t r0, r1;
     int* err;
 };
 
@@ -829,8 +826,8 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
     __syncthreads();
     if (S.st.finished) return;  // same decision in every CTA of the cluster
     int slot = 0;
-    const int r_end = min(p.r1, d.rounds);
-    for (int r = p.r0; r < r_end; ++r) {
+    const int r_end = min(p.wq[q].r1, d.rounds);
+    for (int r = p.wq[q].r0; r < r_end; ++r) {
         if (S.st.done) break;
         const uint64_t key = d.round_best[r];
         const int hyps_r = d.round_hyps[r];
@@ -1034,6 +1031,63 @@ static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool 
     return IMLOC_OK;
 }
 
+int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t total_samples, bool want_counts,
+             cudaStream_t stream) {
+    int rc;
+    if (n_init > 0) {
+        SetupParams sp{b.d_qd, b.d_qs, b.d_nhyp_all, b.nhyp_all_len, b.d_init};
+        ProfScope prof(ctx, stream, "k_setup");
+        k_setup<<<n_init, 256, 0, stream>>>(sp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+        prof.end();
+    }
+    if (total_samples > 0) {
+        SampleParams sp{b.d_qd, b.d_qs, b.d_wq, b.d_prefix, b.d_nhyp, total_samples, nq};
+        const int64_t blocks = (total_samples + 127) / 128;
+        ProfScope prof(ctx, stream, "k_sample_p3p");
+        k_sample_p3p<<<static_cast<unsigned>(blocks), 128, 0, stream>>>(sp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+        prof.end();
+    }
+    {
+        TilesParams tp{b.d_qs, b.d_nhyp, b.d_tiles, b.d_counter, nq, kTileHyps};
+        ProfScope prof(ctx, stream, "k_tiles");
+        k_tiles<<<1, 1024, 0, stream>>>(tp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+        prof.end();
+    }
+    const size_t score_smem = score_smem_bytes(want_counts);
+    ScoreParams scp{b.d_qd, b.d_qs, b.d_wq, b.d_nhyp, b.d_tiles, b.d_counter, nq, ctx->d_err};
+    const int64_t max_items = std::max<int64_t>(1, (total_samples * 4 + kTileHyps - 1) / kTileHyps + nq);
+    // autotune the score kernel variant once per context on a large enough wave
+    if (ctx->score_variant < 0 && (max_items >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
+        rc = tune_score(ctx, scp, score_smem, want_counts, max_items, b.d_counter, stream);
+        if (rc != IMLOC_OK) return rc;
+    }
+    const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
+    auto score_kernel = want_counts ? V.fn_count : V.fn;
+    int n_clusters = 0;
+    rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
+    if (rc != IMLOC_OK) return rc;
+    const int grid_clusters = static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items));
+    {
+        ProfScope prof(ctx, stream, "k_score");
+        rc = launch_cluster(score_kernel, scp, grid_clusters * kScoreCluster, V.threads, score_smem, kScoreCluster,
+                            stream);
+        if (rc != IMLOC_OK) return rc;
+        prof.end();
+    }
+    {
+        const int cl = replay_cluster_size(ctx, nq);
+        ReplayParams rp{b.d_qd, b.d_qs, b.d_wq, ctx->d_err};
+        ProfScope prof(ctx, stream, "k_replay");
+        rc = launch_cluster(k_replay, rp, nq * cl, kRT, 0, cl, stream);
+        if (rc != IMLOC_OK) return rc;
+        prof.end();
+    }
+    return IMLOC_OK;
+}
+
 int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream, bool want_counts) {
     if (nq <= 0) return IMLOC_ERR_INVALID_ARG;
     // ---- per-query host-known sizes and the wave schedule ----
@@ -1092,6 +1146,8 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
             WaveQ& x = wq[static_cast<size_t>(w) * nq + q];
             x.s_begin = sb;
             x.n_samples = static_cast<int32_t>(se - sb);
+            x.r0 = static_cast<int32_t>(waves[w].first);
+            x.r1 = static_cast<int32_t>(waves[w].second);
             x.pad = 0;
             wprefix[static_cast<size_t>(w) * (nq + 1) + q] = acc;
             acc += se - sb;
@@ -1185,61 +1241,20 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         }
 
     // ---- launches ----
-    const int replay_cl = replay_cluster_size(ctx, nq);
-    {
-        SetupParams sp{d_qd, d_qs, d_nhyp, W * nq};
-        ProfScope prof(ctx, stream, "k_setup");
-        k_setup<<<nq, 256, 0, stream>>>(sp);
-        IMLOC_CUDA_TRY(cudaGetLastError());
-        prof.end();
-    }
-    const size_t score_smem = score_smem_bytes(want_counts);
     for (int w = 0; w < W; ++w) {
-        const WaveQ* wq_w = d_wq + static_cast<size_t>(w) * nq;
-        int32_t* nh_w = d_nhyp + static_cast<size_t>(w) * nq;
-        if (wtotal[w] > 0) {
-            SampleParams sp{d_qd, d_qs, wq_w, d_wp + static_cast<size_t>(w) * (nq + 1), nh_w, wtotal[w], nq};
-            const int64_t blocks = (wtotal[w] + 127) / 128;
-            ProfScope prof(ctx, stream, "k_sample_p3p");
-            k_sample_p3p<<<static_cast<unsigned>(blocks), 128, 0, stream>>>(sp);
-            IMLOC_CUDA_TRY(cudaGetLastError());
-            prof.end();
-        }
-        TilesParams tp{d_qs, nh_w, d_tiles, d_counter, nq, kTileHyps};
-        {
-            ProfScope prof(ctx, stream, "k_tiles");
-            k_tiles<<<1, 1024, 0, stream>>>(tp);
-            IMLOC_CUDA_TRY(cudaGetLastError());
-            prof.end();
-        }
-        ScoreParams scp{d_qd, d_qs, wq_w, nh_w, d_tiles, d_counter, nq, ctx->d_err};
-        const int64_t max_items = std::max<int64_t>(1, (wtotal[w] * 4 + kTileHyps - 1) / kTileHyps + nq);
-        // autotune the score kernel variant once per context on a large enough wave
-        if (ctx->score_variant < 0 && (max_items >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
-            rc = tune_score(ctx, scp, score_smem, want_counts, max_items, d_counter, stream);
-            if (rc != IMLOC_OK) return rc;
-        }
-        const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
-        auto score_kernel = want_counts ? V.fn_count : V.fn;
-        int n_clusters = 0;
-        rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
+        StepBuffers sb;
+        sb.d_qd = const_cast<QueryDesc*>(d_qd);
+        sb.d_qs = d_qs;
+        sb.d_wq = d_wq + static_cast<size_t>(w) * nq;
+        sb.d_prefix = d_wp + static_cast<size_t>(w) * (nq + 1);
+        sb.d_nhyp = d_nhyp + static_cast<size_t>(w) * nq;
+        sb.d_tiles = d_tiles;
+        sb.d_counter = d_counter;
+        sb.d_nhyp_all = d_nhyp;
+        sb.nhyp_all_len = W * nq;
+        sb.d_init = nullptr;
+        rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) return rc;
-        const int grid_clusters = static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items));
-        {
-            ProfScope prof(ctx, stream, "k_score");
-            rc = launch_cluster(score_kernel, scp, grid_clusters * kScoreCluster, V.threads, score_smem, kScoreCluster,
-                                stream);
-            if (rc != IMLOC_OK) return rc;
-            prof.end();
-        }
-        ReplayParams rp{d_qd, d_qs, wq_w, static_cast<int32_t>(waves[w].first), static_cast<int32_t>(waves[w].second),
-                        ctx->d_err};
-        {
-            ProfScope prof(ctx, stream, "k_replay");
-            rc = launch_cluster(k_replay, rp, nq * replay_cl, kRT, 0, replay_cl, stream);
-            if (rc != IMLOC_OK) return rc;
-            prof.end();
-        }
     }
     return IMLOC_OK;
 }

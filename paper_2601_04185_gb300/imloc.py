@@ -63,6 +63,17 @@ class Result(C.Structure):
                 ("best_hyp", C.c_int64), ("status", C.c_int32), ("passes", C.c_int32)]
 
 
+class ServeConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("max_queue", C.c_int32), ("device_budget_bytes", C.c_size_t),
+                ("host_staging_bytes", C.c_size_t), ("rounds_per_step", C.c_int32), ("reserved", C.c_int32)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("admitted", C.c_int64),
+                ("completed", C.c_int64), ("steps", C.c_int64), ("pending", C.c_int64), ("resident", C.c_int64),
+                ("device_bytes_in_use", C.c_size_t)]
+
+
 class KernelStat(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double)]
 
@@ -76,7 +87,8 @@ class Debug(C.Structure):
 EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda_error", "imloc_device_error",
            "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
            "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
-           "imloc_lift_noalloc_async"]
+           "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
+           "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy"]
 
 _lib = None
 
@@ -106,6 +118,13 @@ def load(path: str = LIB_PATH):
     L.imloc_ransac_pnp_batch_async.argtypes = [V, C.c_int32, P(Corr), V, P(Camera), P(RansacOpts), V, V, V]
     L.imloc_testing_ransac.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Debug), P(Result), V, V]
     L.imloc_lift_noalloc_async.argtypes = [P(View), C.c_int32, P(Matches), P(Corr), V]
+    L.imloc_serve_default_config.argtypes = [P(ServeConfig)]
+    L.imloc_serve_default_config.restype = None
+    L.imloc_serve_create.argtypes = [V, P(ServeConfig), P(V)]
+    L.imloc_serve_submit.argtypes = [V, P(View), C.c_int32, P(Matches), P(Camera), P(RansacOpts), P(C.c_uint64)]
+    L.imloc_serve_poll.argtypes = [V, C.c_uint64, P(Result), P(C.c_double)]
+    L.imloc_serve_read_stats.argtypes = [V, P(ServeStats)]
+    L.imloc_serve_destroy.argtypes = [V]
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     _lib = L
@@ -330,6 +349,77 @@ class Context:
         _check(self.lib.imloc_testing_ransac(self.h, C.byref(cs), C.byref(camera(K)), C.byref(opts), C.byref(dbg),
                                              C.byref(res), _ptr(mask), _stream(stream)), "imloc_testing_ransac")
         return result_dict(res)
+
+
+class Server:
+    """Continuous-batching server (imloc_serve_*): submit host matches, poll results."""
+
+    def __init__(self, ctx: Context, **cfg):
+        self.lib = load()
+        c = ServeConfig()
+        self.lib.imloc_serve_default_config(C.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = C.c_void_p()
+        _check(self.lib.imloc_serve_create(ctx.h, C.byref(c), C.byref(h)), "imloc_serve_create")
+        self.h = h
+        self.cfg = c
+
+    @staticmethod
+    def prepare(views, matches, K, opts):
+        """Marshal one query: views with device depth maps, matches as host float32 arrays."""
+        vs = _views_struct(views)
+        arrs = [np.ascontiguousarray(matches[k], dtype=np.float32) for k in ("q_u", "q_v", "db_u", "db_v", "conf")]
+        seg_off = np.asarray(matches["seg_off"], dtype=np.int64)
+        n_seg = len(seg_off) - 1
+        segs = (Segment * max(n_seg, 1))()
+        for s_ in range(n_seg):
+            segs[s_].begin = int(seg_off[s_])
+            segs[s_].view = int(matches["seg_view"][s_])
+            segs[s_].direction = int(matches["seg_dir"][s_])
+        n = int(seg_off[-1]) if n_seg > 0 else 0
+        ms = Matches(*[a.ctypes.data for a in arrs], n, segs, n_seg)
+        return Prepared(vs=vs, n_views=len(views), ms=ms, keep=(arrs, segs, views), cam=camera(K), opts=opts)
+
+    def submit_prepared(self, p):
+        """Returns the ticket, or None when the server refuses the query."""
+        t = C.c_uint64(0)
+        rc = self.lib.imloc_serve_submit(self.h, p.vs, p.n_views, C.byref(p.ms), C.byref(p.cam), C.byref(p.opts),
+                                         C.byref(t))
+        if rc == -3:
+            return None
+        _check(rc, "imloc_serve_submit")
+        return t.value
+
+    def submit(self, views, matches, K, opts):
+        return self.submit_prepared(self.prepare(views, matches, K, opts))
+
+    def poll(self, ticket):
+        """(status, result dict or None, latency ms or None); status 1 = pending, -6 = unknown ticket."""
+        r = Result()
+        lat = C.c_double(0.0)
+        rc = self.lib.imloc_serve_poll(self.h, C.c_uint64(ticket), C.byref(r), C.byref(lat))
+        if rc == 0:
+            return 0, result_dict(r), lat.value
+        return rc, None, None
+
+    def stats(self):
+        st = ServeStats()
+        rc = self.lib.imloc_serve_read_stats(self.h, C.byref(st))
+        d = {k: getattr(st, k) for k, _ in ServeStats._fields_}
+        d["worker_status"] = rc
+        return d
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.imloc_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 RESULT_BYTES = C.sizeof(Result)

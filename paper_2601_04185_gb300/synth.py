@@ -188,6 +188,106 @@ def _bilinear_taps_ok(depth, u, v):
     return ok & np.all(taps > 0, axis=0)
 
 
+def perturbed_view_pose(rng, R_q, t_q, max_rot_deg=15.0, max_shift_m=3.0):
+    """A database pose near a query pose: rotation <= max_rot_deg, centre <= max_shift_m away."""
+    dR = axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, max_rot_deg)))
+    R_d = dR @ R_q
+    C_q = -R_q.T @ t_q
+    dirn = rng.normal(size=3)
+    C_d = C_q + dirn / np.linalg.norm(dirn) * rng.uniform(0, max_shift_m)
+    return R_d, -R_d @ C_d
+
+
+def pair_matches(rng, scene, R_q, t_q, K, width, height, view, n_pair, direction, ratio, pixel_noise):
+    """Matches of one (query, database view) pair in one direction.
+
+    direction 0: query pixel -> 3D by the scene -> database subpixel (visible,
+    all four bilinear taps valid); direction 1: database pixel centre -> depth
+    -> 3D -> query subpixel (visible from the query).  A fraction `ratio` are
+    true matches with N(0, pixel_noise) on the query pixel; the rest are
+    uniform.  Confidence: true U[0.3, 1], false U[0, 1]."""
+    R_d, t_d, depth_true = view["R"], view["t"], view["depth_true"]
+    n_in = int(round(ratio * n_pair))
+    if direction == 0:
+        cu = rng.uniform(0, width, 6 * n_in + 64)
+        cv = rng.uniform(0, height, 6 * n_in + 64)
+        zq = scene.raycast(R_q, t_q, K, cu, cv)
+        Xw = _backproject(R_q, t_q, K, cu, cv, zq)
+        du, dv, dz = _project(R_d, t_d, K, Xw)
+        zd = scene.raycast(R_d, t_d, K, np.nan_to_num(du), np.nan_to_num(dv))
+        ok = (zq > 0) & (dz > 0) & np.isfinite(du) & np.isfinite(dv)
+        ok &= _bilinear_taps_ok(depth_true, np.nan_to_num(du), np.nan_to_num(dv))
+        ok &= np.abs(zd - dz) < 1e-3 * np.maximum(dz, 1e-9)
+        sel = np.nonzero(ok)[0][:n_in]
+        in_qu, in_qv, in_du, in_dv = cu[sel], cv[sel], du[sel], dv[sel]
+    else:
+        valid_pix = np.flatnonzero(depth_true.ravel() > 0)
+        pick = valid_pix[rng.integers(0, len(valid_pix), 6 * n_in + 64)] if len(valid_pix) else np.zeros(0, int)
+        pj, pi = np.divmod(pick, width)
+        du = pi + 0.5
+        dv = pj + 0.5
+        Xw = _backproject(R_d, t_d, K, du, dv, depth_true[pj, pi].astype(np.float64))
+        qu, qv, qz = _project(R_q, t_q, K, Xw)
+        ok = (qz > 0) & np.isfinite(qu) & (qu >= 0) & (qu < width) & (qv >= 0) & (qv < height)
+        zq = scene.raycast(R_q, t_q, K, np.nan_to_num(qu), np.nan_to_num(qv))
+        ok &= np.abs(zq - qz) < 1e-3 * np.maximum(qz, 1e-9)
+        sel = np.nonzero(ok)[0][:n_in]
+        in_qu, in_qv, in_du, in_dv = qu[sel], qv[sel], du[sel], dv[sel]
+    n_in_eff = len(sel)
+    n_out = n_pair - n_in_eff
+    in_qu = in_qu + rng.normal(0, pixel_noise, n_in_eff)
+    in_qv = in_qv + rng.normal(0, pixel_noise, n_in_eff)
+    out_qu = rng.uniform(0, width, n_out)
+    out_qv = rng.uniform(0, height, n_out)
+    if direction == 0:
+        out_du = rng.uniform(0, width, n_out)
+        out_dv = rng.uniform(0, height, n_out)
+    else:
+        out_du = rng.integers(0, width, n_out) + 0.5
+        out_dv = rng.integers(0, height, n_out) + 0.5
+    q_u = np.concatenate([in_qu, out_qu])
+    q_v = np.concatenate([in_qv, out_qv])
+    d_u = np.concatenate([in_du, out_du])
+    d_v = np.concatenate([in_dv, out_dv])
+    conf = np.concatenate([rng.uniform(0.3, 1.0, n_in_eff), rng.uniform(0.0, 1.0, n_out)])
+    truth = np.concatenate([np.ones(n_in_eff, bool), np.zeros(n_out, bool)])
+    perm = rng.permutation(n_pair)
+    return q_u[perm], q_v[perm], d_u[perm], d_v[perm], conf[perm], truth[perm]
+
+
+def query_matches(rng, scene, R_q, t_q, K, width, height, views, view_ids, matches_per_pair, pixel_noise,
+                  inlier_range):
+    """Matches of a query against the listed views (segments: per view, one
+    query->database and one database->query segment)."""
+    cols = {k: [] for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+    truth_all = []
+    seg_off, seg_view, seg_dir = [0], [], []
+    for slot, vid in enumerate(view_ids):
+        ratio = rng.uniform(*inlier_range)
+        for direction in (0, 1):
+            n_pair = matches_per_pair // 2 if direction == 0 else matches_per_pair - matches_per_pair // 2
+            q_u, q_v, d_u, d_v, conf, truth = pair_matches(rng, scene, R_q, t_q, K, width, height, views[vid], n_pair,
+                                                           direction, ratio, pixel_noise)
+            for k, a in zip(cols, (q_u, q_v, d_u, d_v, conf)):
+                cols[k].append(a)
+            truth_all.append(truth)
+            seg_off.append(seg_off[-1] + n_pair)
+            seg_view.append(slot)
+            seg_dir.append(direction)
+    m = {k: np.concatenate(v).astype(np.float32) for k, v in cols.items()}
+    m.update(seg_off=np.array(seg_off, np.int64), seg_view=np.array(seg_view, np.int32),
+             seg_dir=np.array(seg_dir, np.int32))
+    return m, np.concatenate(truth_all)
+
+
+def make_view(scene, R_d, t_d, K, width, height, depth_noise=0.0, rng=None):
+    depth_true = scene.depth_map(R_d, t_d, K, width, height)
+    depth = depth_true
+    if depth_noise > 0:
+        depth = (depth_true * (1.0 + rng.normal(0, depth_noise, depth_true.shape))).astype(np.float32)
+    return dict(depth=depth, depth_true=depth_true, fx=K[0], fy=K[1], cx=K[2], cy=K[3], R=R_d, t=t_d)
+
+
 def localization_query(rng, n_views=10, matches_per_pair=5000, width=1024, height=768, f=800.0,
                        pixel_noise=0.5, depth_noise=0.0, inlier_range=(0.10, 0.60), scene=None,
                        max_rot_deg=15.0, max_shift_m=3.0):
@@ -207,85 +307,46 @@ def localization_query(rng, n_views=10, matches_per_pair=5000, width=1024, heigh
     t_q = rng.normal(size=3)
     if scene is None:
         scene = PlanarScene(rng, R_q, t_q, K, width, height)
-    C_q = -R_q.T @ t_q
     views = []
-    segs_q_u, segs_q_v, segs_db_u, segs_db_v, segs_conf = [], [], [], [], []
-    seg_off = [0]
-    seg_view, seg_dir = [], []
-    truth_inlier = []
     for k in range(n_views):
-        dR = axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, max_rot_deg)))
-        R_d = dR @ R_q
-        dirn = rng.normal(size=3)
-        C_d = C_q + dirn / np.linalg.norm(dirn) * rng.uniform(0, max_shift_m)
-        t_d = -R_d @ C_d
-        depth_true = scene.depth_map(R_d, t_d, K, width, height)
-        depth = depth_true
-        if depth_noise > 0:
-            depth = (depth_true * (1.0 + rng.normal(0, depth_noise, depth_true.shape))).astype(np.float32)
-        views.append(dict(depth=depth, fx=K[0], fy=K[1], cx=K[2], cy=K[3], R=R_d, t=t_d))
-        ratio = rng.uniform(*inlier_range)
-        for direction in (0, 1):
-            n_pair = matches_per_pair // 2 if direction == 0 else matches_per_pair - matches_per_pair // 2
-            n_in = int(round(ratio * n_pair))
-            if direction == 0:
-                # query pixel -> 3D by the scene -> database subpixel
-                cu = rng.uniform(0, width, 6 * n_in + 64)
-                cv = rng.uniform(0, height, 6 * n_in + 64)
-                zq = scene.raycast(R_q, t_q, K, cu, cv)
-                Xw = _backproject(R_q, t_q, K, cu, cv, zq)
-                du, dv, dz = _project(R_d, t_d, K, Xw)
-                zd = scene.raycast(R_d, t_d, K, np.nan_to_num(du), np.nan_to_num(dv))
-                ok = (zq > 0) & (dz > 0) & np.isfinite(du) & np.isfinite(dv)
-                ok &= _bilinear_taps_ok(depth_true, np.nan_to_num(du), np.nan_to_num(dv))
-                ok &= np.abs(zd - dz) < 1e-3 * np.maximum(dz, 1e-9)
-                sel = np.nonzero(ok)[0][:n_in]
-                in_qu, in_qv, in_du, in_dv = cu[sel], cv[sel], du[sel], dv[sel]
-            else:
-                # database pixel centre -> depth -> 3D -> query subpixel
-                valid_pix = np.flatnonzero(depth_true.ravel() > 0)
-                pick = valid_pix[rng.integers(0, len(valid_pix), 6 * n_in + 64)] if len(valid_pix) else np.zeros(0, int)
-                pj, pi = np.divmod(pick, width)
-                du = pi + 0.5
-                dv = pj + 0.5
-                Xw = _backproject(R_d, t_d, K, du, dv, depth_true[pj, pi].astype(np.float64))
-                qu, qv, qz = _project(R_q, t_q, K, Xw)
-                ok = (qz > 0) & np.isfinite(qu) & (qu >= 0) & (qu < width) & (qv >= 0) & (qv < height)
-                zq = scene.raycast(R_q, t_q, K, np.nan_to_num(qu), np.nan_to_num(qv))
-                ok &= np.abs(zq - qz) < 1e-3 * np.maximum(qz, 1e-9)
-                sel = np.nonzero(ok)[0][:n_in]
-                in_qu, in_qv, in_du, in_dv = qu[sel], qv[sel], du[sel], dv[sel]
-            n_in_eff = len(sel)
-            n_out = n_pair - n_in_eff
-            in_qu = in_qu + rng.normal(0, pixel_noise, n_in_eff)
-            in_qv = in_qv + rng.normal(0, pixel_noise, n_in_eff)
-            out_qu = rng.uniform(0, width, n_out)
-            out_qv = rng.uniform(0, height, n_out)
-            if direction == 0:
-                out_du = rng.uniform(0, width, n_out)
-                out_dv = rng.uniform(0, height, n_out)
-            else:
-                out_du = rng.integers(0, width, n_out) + 0.5
-                out_dv = rng.integers(0, height, n_out) + 0.5
-            q_u = np.concatenate([in_qu, out_qu])
-            q_v = np.concatenate([in_qv, out_qv])
-            d_u = np.concatenate([in_du, out_du])
-            d_v = np.concatenate([in_dv, out_dv])
-            conf = np.concatenate([rng.uniform(0.3, 1.0, n_in_eff), rng.uniform(0.0, 1.0, n_out)])
-            truth = np.concatenate([np.ones(n_in_eff, bool), np.zeros(n_out, bool)])
-            perm = rng.permutation(n_pair)
-            segs_q_u.append(q_u[perm]); segs_q_v.append(q_v[perm])
-            segs_db_u.append(d_u[perm]); segs_db_v.append(d_v[perm])
-            segs_conf.append(conf[perm]); truth_inlier.append(truth[perm])
-            seg_off.append(seg_off[-1] + n_pair)
-            seg_view.append(k)
-            seg_dir.append(direction)
-    matches = dict(q_u=np.concatenate(segs_q_u).astype(np.float32), q_v=np.concatenate(segs_q_v).astype(np.float32),
-                   db_u=np.concatenate(segs_db_u).astype(np.float32), db_v=np.concatenate(segs_db_v).astype(np.float32),
-                   conf=np.concatenate(segs_conf).astype(np.float32), seg_off=np.array(seg_off, dtype=np.int64),
-                   seg_view=np.array(seg_view, dtype=np.int32), seg_dir=np.array(seg_dir, dtype=np.int32))
+        R_d, t_d = perturbed_view_pose(rng, R_q, t_q, max_rot_deg, max_shift_m)
+        views.append(make_view(scene, R_d, t_d, K, width, height, depth_noise, rng))
+    matches, truth = query_matches(rng, scene, R_q, t_q, K, width, height, views, list(range(n_views)),
+                                   matches_per_pair, pixel_noise, inlier_range)
+    for v in views:
+        v.pop("depth_true")
     return dict(views=views, matches=matches, K=K, width=width, height=height, R_gt=R_q, t_gt=t_q,
-                truth_inlier=np.concatenate(truth_inlier), scene=scene)
+                truth_inlier=truth, scene=scene)
+
+
+class MapStore:
+    """A resident map store: one planar scene seen by `n_views` database views
+    around a centre pose (<= 15 deg, <= 3 m).  Serving queries are new poses
+    near the centre whose retrieved views are a subset of the store."""
+
+    def __init__(self, seed, n_views, width=1024, height=768, f=800.0):
+        rng = np.random.default_rng(seed)
+        self.K = (f, f, width / 2.0, height / 2.0)
+        self.width, self.height = width, height
+        self.R_c = random_rotation(rng)
+        self.t_c = rng.normal(size=3)
+        self.scene = PlanarScene(rng, self.R_c, self.t_c, self.K, width, height)
+        self.poses = [perturbed_view_pose(rng, self.R_c, self.t_c) for _ in range(n_views)]
+        self.views = [None] * n_views
+
+    def build_view(self, k):
+        R_d, t_d = self.poses[k]
+        v = make_view(self.scene, R_d, t_d, self.K, self.width, self.height)
+        self.views[k] = v
+        return v
+
+    def query(self, rng, n_views, matches_per_pair=5000, pixel_noise=0.5, inlier_range=(0.10, 0.60)):
+        """A query near the centre pose matched against `n_views` random store views."""
+        R_q, t_q = perturbed_view_pose(rng, self.R_c, self.t_c, 8.0, 1.5)
+        ids = sorted(rng.choice(len(self.views), size=n_views, replace=False).tolist())
+        m, truth = query_matches(rng, self.scene, R_q, t_q, self.K, self.width, self.height, self.views, ids,
+                                 matches_per_pair, pixel_noise, inlier_range)
+        return dict(view_ids=ids, matches=m, K=self.K, R_gt=R_q, t_gt=t_q, truth_inlier=truth)
 
 
 def config2(seed=0, **kw):
