@@ -162,6 +162,28 @@ __device__ __forceinline__ bool pose_from_depths(const T L[3], const B y[3][3], 
     return true;
 }
 
+// One Newton-Schulz step towards the nearest rotation: R <- R (3 I - R^T R) / 2
+// (the triangle-frame pose is a rotation up to float32 rounding).
+template <typename T>
+__device__ __forceinline__ void orthonormalize(T R[9]) {
+    T G[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) G[3 * i + j] = R[i] * R[j] + R[3 + i] * R[3 + j] + R[6 + i] * R[6 + j];
+    T N[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const T m0 = (0 == j ? T(3) : T(0)) - G[j], m1 = (1 == j ? T(3) : T(0)) - G[3 + j],
+                    m2 = (2 == j ? T(3) : T(0)) - G[6 + j];
+            N[3 * i + j] = T(0.5) * (R[3 * i] * m0 + R[3 * i + 1] * m1 + R[3 * i + 2] * m2);
+        }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) R[k] = N[k];
+}
+
 // Solve one P3P instance.  y: unit bearings (float32), yd: the same bearings
 // in FP64 (used, with FP64 squared distances, by the Newton polish and the
 // pose when non-null), X: world points.  Returns the number of poses (<= 4),
@@ -302,6 +324,7 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
                 // the pose from the polished depths in float32 (the poses are scored in float32)
                 const float Lf3[3] = {float(L[0]), float(L[1]), float(L[2])};
                 good = pose_from_depths<float, float>(Lf3, y, X, out[nout].R, out[nout].t);
+                if (good) orthonormalize(out[nout].R);
             }
             Lf[0] = float(L[0]);
         } else {
@@ -314,6 +337,7 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
             good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabsf(f0) <= 1e-3f * a[0] && fabsf(f1) <= 1e-3f * a[1] &&
                    fabsf(f2) <= 1e-3f * a[2];
             if (good) good = pose_from_depths<float, float>(L, y, X, out[nout].R, out[nout].t);
+            if (good) orthonormalize(out[nout].R);
             Lf[0] = L[0];
         }
         if (!good) continue;

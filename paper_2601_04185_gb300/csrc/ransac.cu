@@ -844,6 +844,8 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
                 const PoseF ps = d.slots[static_cast<int64_t>(id) - 4 * p.wq[q].s_begin];
                 for (int k = 0; k < 9; ++k) S.R[k] = ps.R[k];
                 for (int k = 0; k < 3; ++k) S.t[k] = ps.t[k];
+                orthonormalize<double>(S.R);  // float32 pose -> rotation to FP64 rounding
+                orthonormalize<double>(S.R);
                 for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
                 for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
                 S.st.best_score = sc;

@@ -40,8 +40,10 @@ def lifted_to_host(out, n=None):
 
 
 def rot_deg(Ra, Rb):
-    c = (np.trace(np.asarray(Ra).T @ np.asarray(Rb)) - 1.0) / 2.0
-    return math.degrees(math.acos(max(-1.0, min(1.0, c))))
+    """Angle between two rotations from the chord |Ra - Rb|_F = 2 sqrt(2) sin(angle / 2):
+    exact for rotations and 0 for identical matrices."""
+    chord = np.linalg.norm(np.asarray(Ra, np.float64) - np.asarray(Rb, np.float64))
+    return math.degrees(2.0 * math.asin(min(1.0, chord / (2.0 * math.sqrt(2.0)))))
 
 
 def centre(R, t):

@@ -196,6 +196,9 @@ def test_config1_end_to_end(c1_run):
     q, res, dbg = c1_run
     ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=q["hypotheses"], p_miss=0.0)
     assert res["status"] == 0 and ref["status"] == 0
+    # the returned rotations are rotations (to FP64 rounding)
+    np.testing.assert_allclose(res["R"] @ res["R"].T, np.eye(3), atol=1e-9)
+    np.testing.assert_allclose(res["R_best"] @ res["R_best"].T, np.eye(3), atol=1e-9)
     assert pose_close(res["R"], res["t"], ref["R"], ref["t"])
     assert res["iterations"] == ref["iterations"] == 1000
     r, z = residuals(q["x"].astype(np.float64), q["y"].astype(np.float64), q["X"], q["K"], ref["R"], ref["t"])
