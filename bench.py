@@ -243,6 +243,140 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson arrivals, served (continuous batching) vs plain
+# ---------------------------------------------------------------------------
+STORE_VIEWS = 64
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
+
+
+def _gen_store_view(args):
+    from paper_2601_04185_gb300 import synth
+
+    seed, k = args
+    st = synth.MapStore(seed, STORE_VIEWS)
+    v = st.build_view(k)
+    v.pop("depth_true", None)
+    return v
+
+
+_STORE = None  # map store shared with forked generator processes
+
+
+def _serve_query_worker(i):
+    rng = np.random.default_rng(10_000 + i)
+    return _STORE.query(rng, int(rng.integers(10, 41)))
+
+
+def make_store_and_queries(seed, n_queries):
+    """The resident map store (64 views, 1024x768 float32 depth) and serving
+    queries against it (10-40 views x 5,000 matches, 50k-200k matches).
+    Must run before CUDA is initialised in this process (fork pool)."""
+    global _STORE
+    from paper_2601_04185_gb300 import synth
+
+    with cf.ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("spawn")) as ex:
+        views = list(ex.map(_gen_store_view, [(seed, k) for k in range(STORE_VIEWS)]))
+    store = synth.MapStore(seed, STORE_VIEWS)
+    store.views = [dict(v, depth_true=v["depth"]) for v in views]
+    _STORE = store
+    with cf.ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("fork")) as ex:
+        queries = list(ex.map(_serve_query_worker, range(n_queries), chunksize=2))
+    return store, views, queries
+
+
+def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
+    """Offer Poisson streams to the server and to the plain loop; returns per-rate q/s and latency percentiles."""
+    import queue
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    def opts_for(i):
+        return imloc.default_opts(max_iters=10000, p_miss=1e-4, query_id=i, seed=4321)
+
+    prepared = [imloc.Server.prepare([dev_views[j] for j in q["view_ids"]], q["matches"], q["K"], opts_for(i))
+                for i, q in enumerate(queries)]
+    out = {"rates": list(rates), "served": [], "plain": []}
+    rng = np.random.default_rng(77)
+    ctx = imloc.Context(dev.index, 512 << 20)
+    srv = imloc.Server(ctx, max_slots=64, device_budget_bytes=64 << 30, host_staging_bytes=1 << 30,
+                       rounds_per_step=2)
+    # warm the server (autotuning, module load)
+    tk = [srv.submit_prepared(prepared[i]) for i in range(8)]
+    while any(srv.poll(t)[0] == 1 for t in tk):
+        time.sleep(0.001)
+    for lam in rates:
+        n = min(per_rate, int(lam * seconds_cap))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n))
+        order = rng.integers(0, len(queries), n)
+        # ---- served ----
+        tickets = []
+        t0 = time.perf_counter()
+        for k in range(n):
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            t = srv.submit_prepared(prepared[order[k]])
+            tickets.append(t)
+        lats, pending = [], [t for t in tickets if t is not None]
+        while pending:
+            keep = []
+            for t in pending:
+                st, res, lat = srv.poll(t)
+                if st == 0:
+                    lats.append(lat)
+                else:
+                    keep.append(t)
+            pending = keep
+            if pending:
+                time.sleep(0.0005)
+        elapsed = time.perf_counter() - t0
+        lats.sort()
+        out["served"].append({"lambda": lam, "queries": n, "refused": sum(t is None for t in tickets),
+                              "q_per_s": len(lats) / elapsed, "p50_ms": lats[len(lats) // 2],
+                              "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))]})
+        # ---- plain: one query at a time, upload + lift + RANSAC per call ----
+        qq = queue.Queue()
+        lat_p = []
+        corr = imloc.alloc_corr(max(len(q["matches"]["q_u"]) for q in queries), dev)
+        pinned = [{k: torch.from_numpy(queries[i]["matches"][k]).pin_memory() for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+                  for i in range(len(queries))] if lam == rates[0] else pinned
+        def worker():
+            stream = torch.cuda.current_stream(dev)
+            while True:
+                item = qq.get()
+                if item is None:
+                    return
+                k, t_arr = item
+                i = order[k]
+                q = queries[i]
+                dm = {kk: v.to(dev, non_blocking=True) for kk, v in pinned[i].items()}
+                dm.update({kk: q["matches"][kk] for kk in ("seg_off", "seg_view", "seg_dir")})
+                ctx.lift([dev_views[j] for j in q["view_ids"]], dm, out=corr, stream=stream)
+                ctx.ransac_pnp(corr, q["K"], opts_for(i), stream=stream)
+                lat_p.append(1e3 * (time.perf_counter() - t_arr))
+        th = threading.Thread(target=worker)
+        th.start()
+        t0 = time.perf_counter()
+        for k in range(n):
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            qq.put((k, time.perf_counter()))
+        qq.put(None)
+        th.join()
+        elapsed = time.perf_counter() - t0
+        lat_p.sort()
+        out["plain"].append({"lambda": lam, "queries": n, "q_per_s": len(lat_p) / elapsed,
+                             "p50_ms": lat_p[len(lat_p) // 2],
+                             "p99_ms": lat_p[min(len(lat_p) - 1, int(0.99 * len(lat_p)))]})
+    out["server_stats"] = srv.stats()
+    srv.close()
+    ctx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def run_ours(args):
@@ -250,8 +384,11 @@ def run_ours(args):
 
     from paper_2601_04185_gb300 import imloc
 
-    # inputs first (spawned pool; no fork after CUDA starts)
+    # inputs first (process pools before CUDA starts in this process)
     queries = make_queries(args.queries, 100 + 1000 * int(os.environ.get("RANK", "0")))
+    serving_inputs = None
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_serving:
+        serving_inputs = make_store_and_queries(2024, args.serve_queries)
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     views, big, qb = concat_batch(queries)
@@ -414,6 +551,18 @@ def run_ours(args):
         "paper_context": "ImLoc reports ~200 ms per query for its RANSAC loop on an RTX 4090 (Sec. 4.4); "
                          "different hardware and data",
     }
+    # ---- serving (C5): Poisson arrivals, served vs plain ----
+    if serving_inputs is not None:
+        store, store_views, sq = serving_inputs
+        dv = []
+        for v in store_views:
+            d = dict(v)
+            d["depth"] = torch.from_numpy(v["depth"]).to(dev)
+            dv.append(d)
+        line["serving"] = run_serving(dev, SERVE_RATES, args.serve_per_rate, sq, dv)
+        line["serving"]["workload"] = (f"C5: map store of {STORE_VIEWS} views (1024x768 float32 depth, resident), "
+                                       f"{len(sq)} distinct queries of 10-40 views x 5,000 matches, "
+                                       "10,000 minimal sets max with the adaptive stop (p = 1e-4); Poisson arrivals")
     # ---- CPU baseline: the FP64 oracle on the host cores (rank 0, N = 1 only) ----
     if world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
@@ -440,6 +589,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--queries", type=int, default=16, help="queries per step (per GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-queries", type=int, default=64, help="distinct serving queries")
+    ap.add_argument("--serve-per-rate", type=int, default=200, help="arrivals per offered rate")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
