@@ -246,7 +246,7 @@ def run_reference(args):
 # serving: Poisson arrivals, served (continuous batching) vs plain
 # ---------------------------------------------------------------------------
 STORE_VIEWS = 64
-SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
 
 
 def _gen_store_view(args):
@@ -374,6 +374,144 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
     srv.close()
     ctx.close()
     return out
+
+
+# ---------------------------------------------------------------------------
+# batched (C3): 256 direct queries in shared launches
+# ---------------------------------------------------------------------------
+def run_batched_c3(dev, steps=5):
+    import torch
+
+    from paper_2601_04185_gb300 import imloc, synth
+
+    qs = synth.config3(0)
+    nq = len(qs)
+    offs = np.cumsum([0] + [len(q["x"]) for q in qs])
+    cat = lambda k: np.concatenate([q[k] for q in qs])
+    corr = imloc.corr_from_arrays(cat("x"), cat("y"), np.concatenate([q["X"] for q in qs]), cat("w"), device=dev)
+    d_offs = torch.from_numpy(offs.astype(np.int64)).to(dev)
+    opts = [imloc.default_opts(max_iters=q["hypotheses"], p_miss=0.0, query_id=i, seed=5) for i, q in enumerate(qs)]
+    ctx = imloc.Context(dev.index, 4 << 30)
+    res_buf = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    prep = imloc.prepare_ransac_batch([q["K"] for q in qs], opts)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        ctx.ransac_pnp_batch_async(corr, d_offs, None, None, res_buf, stream=stream, prepared=prep)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        ctx.ransac_pnp_batch_async(corr, d_offs, None, None, res_buf, stream=stream, prepared=prep)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    kst = ctx.profile_read(reset=True)
+    res = imloc.results_from_bytes(res_buf.cpu().numpy(), nq)
+    pairs = float(sum(r["hypotheses"] * min(int(n), 10000) for r, n in zip(res, np.diff(offs))))
+    ctx.close()
+    score_ms = kst.get("k_score", (1, 0.0))[1] / max(1, kst.get("k_score", (1, 0.0))[0])
+    return {"workload": "C3: 256 direct queries, N log-uniform in [2k, 100k], inlier ratio U[5%, 70%], "
+                        "4,096-16,384 minimal sets, LO + refinement, one batched call",
+            "ms_per_batch": ms, "hyp_corr_per_s": pairs / (ms * 1e-3), "queries_per_s": nq / (ms * 1e-3),
+            "correspondences": int(offs[-1]), "k_score_ms": score_ms,
+            "k_score_tflops": FLOPS_PER_PAIR * pairs / (score_ms * 1e-3) / 1e12 if score_ms else None,
+            "kernels_ms": {k: v[1] / steps for k, v in kst.items()},
+            "status": sorted({r["status"] for r in res})}
+
+
+# ---------------------------------------------------------------------------
+# precision study (C4): P3P polish and LO accumulation variants vs the oracle
+# ---------------------------------------------------------------------------
+def _gen_c4_query(i):
+    from paper_2601_04185_gb300 import synth
+
+    rng = np.random.default_rng(500 + i)
+    sig = (0.5, 1.0, 1.5, 2.0)[i * 4 // PRECISION_QUERIES]
+    q = synth.localization_query(rng, pixel_noise=sig, depth_noise=0.01)
+    q.pop("scene", None)
+    q["sigma"] = sig
+    return q
+
+
+PRECISION_QUERIES = 64
+
+
+def _oracle_pose(args):
+    import oracle
+
+    q, i = args
+    L = oracle.lift(q["views"], q["matches"])
+    c = oracle.Corr(L["x"], L["y"], L["X"], L["w"])
+    r = oracle.ransac_pnp(c, q["K"], max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=31)
+    return r["R"], r["t"]
+
+
+def _rot_err_deg(Ra, Rb):
+    chord = np.linalg.norm(np.asarray(Ra) - np.asarray(Rb))
+    return math.degrees(2.0 * math.asin(min(1.0, chord / (2.0 * math.sqrt(2.0)))))
+
+
+def run_precision_study(args):
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    with cf.ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("spawn")) as ex:
+        qs = list(ex.map(_gen_c4_query, range(PRECISION_QUERIES)))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        ref = list(ex.map(_oracle_pose, [(q, i) for i, q in enumerate(qs)]))
+    oracle_s = time.perf_counter() - t0
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    views, big, qb = concat_batch(qs)
+    d_views = []
+    for v in views:
+        d = dict(v)
+        d["depth"] = torch.from_numpy(v["depth"]).to(dev)
+        d_views.append(d)
+    d_match = {k: torch.from_numpy(big[k]).to(dev) for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+    d_match.update({k: big[k] for k in ("seg_off", "seg_view", "seg_dir")})
+    ctx = imloc.Context(0, 2 << 30)
+    corr, offsets = ctx.lift_batch(qb, d_views, d_match)
+    nq = len(qs)
+    out = {"workload": f"C4: {nq} queries of 50k matches (10 views x 5,000), depth x (1 + N(0, 0.01)), pixel noise "
+                       "0.5/1/1.5/2 px (16 each), 10,000 minimal sets, LO + refinement; errors vs the FP64 oracle's "
+                       "final pose and vs ground truth",
+           "oracle_seconds": oracle_s, "variants": []}
+    for polish in (1, 0):
+        for lo64 in (0, 1):
+            opts = [imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=31, p3p_fp64_polish=polish,
+                                       lo_fp64_accumulate=lo64) for i in range(nq)]
+            res_buf = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+            ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
+            b.record()
+            torch.cuda.synchronize()
+            res = imloc.results_from_bytes(res_buf.cpu().numpy(), nq)
+            rot = np.array([_rot_err_deg(r["R"], o[0]) for r, o in zip(res, ref)])
+            trans = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + o[0].T @ o[1]) for r, o in zip(res, ref)])
+            rot_gt = np.array([_rot_err_deg(r["R"], q["R_gt"]) for r, q in zip(res, qs)])
+            trans_gt = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + q["R_gt"].T @ q["t_gt"])
+                                 for r, q in zip(res, qs)])
+            within = float(np.mean((rot <= 0.05) & (trans <= 5.0)))
+            out["variants"].append({
+                "p3p": "fp32+fp64 polish" if polish else "fp32", "lo_normal_equations": "fp64" if lo64 else "fp32",
+                "vs_oracle_rot_deg": {"median": float(np.median(rot)), "p90": float(np.percentile(rot, 90)),
+                                      "max": float(rot.max())},
+                "vs_oracle_trans_mm": {"median": float(np.median(trans)), "p90": float(np.percentile(trans, 90)),
+                                       "max": float(trans.max())},
+                "within_0.05deg_5mm": within,
+                "vs_gt_rot_deg_median": float(np.median(rot_gt)), "vs_gt_trans_mm_median": float(np.median(trans_gt)),
+                "batch_ms": a.elapsed_time(b), "status": sorted({r["status"] for r in res})})
+    ctx.close()
+    print(json.dumps({"precision_study": out}))
+    return 0
 
 
 # ---------------------------------------------------------------------------
@@ -551,6 +689,9 @@ def run_ours(args):
         "paper_context": "ImLoc reports ~200 ms per query for its RANSAC loop on an RTX 4090 (Sec. 4.4); "
                          "different hardware and data",
     }
+    # ---- batched C3 ----
+    if world == 1 and not args.no_c3:
+        line["batched_c3"] = run_batched_c3(dev)
     # ---- serving (C5): Poisson arrivals, served vs plain ----
     if serving_inputs is not None:
         store, store_views, sq = serving_inputs
@@ -590,6 +731,8 @@ def main():
     ap.add_argument("--queries", type=int, default=16, help="queries per step (per GPU)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--precision-study", action="store_true", help="C4: precision variants vs the oracle")
     ap.add_argument("--serve-queries", type=int, default=64, help="distinct serving queries")
     ap.add_argument("--serve-per-rate", type=int, default=200, help="arrivals per offered rate")
     args = ap.parse_args()
@@ -597,6 +740,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.precision_study:
+        return run_precision_study(args)
     return run_ours(args)
 
 

@@ -185,6 +185,10 @@ typedef struct {
     uint64_t seed;
     uint32_t query_id;
     int32_t enumerate_all;   /* test mode: every triple of the subset in one round */
+    int32_t lo_fp64_accumulate; /* 1: LO / refinement sums each point's normal-equation terms in FP64
+                                   (default 0: FP32 per thread, FP64 across warps and CTAs); the 6x6
+                                   solve is FP64 either way */
+    int32_t reserved;
 } imloc_ransac_opts;
 
 /* Fill `o` with the defaults above. */

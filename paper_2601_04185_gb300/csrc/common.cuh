@@ -143,6 +143,7 @@ struct QueryDesc {
     float tau2, cauchy2;
     int32_t m_cap, batch, hyps, rounds;
     int32_t lo_iters, final_iters, polish, enumerate_all;
+    int32_t lo_fp64, pad2;
     double p_miss;
     uint64_t seed;
     uint32_t query_id;

@@ -523,7 +523,7 @@ struct ReplaySmem {
     double step, decrease, prev_cost;
     double tot[32];
     double xch[2][32];
-    float red[kRT / 32][32];
+    double red[kRT / 32][32];
     float P[12];
     int flag;
     QueryState st;
@@ -541,15 +541,15 @@ __device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], 
     for (int k = 0; k < 3; ++k) S.P[9 + k] = static_cast<float>(t[k]);
 }
 
-template <int MODE>
+template <int MODE, typename ACC = float>
 __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) ++S.st.passes;
     constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
     constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
-    float acc[kNV];
+    ACC acc[kNV];
 #pragma unroll
-    for (int k = 0; k < kNV; ++k) acc[k] = 0.f;
+    for (int k = 0; k < kNV; ++k) acc[k] = ACC(0);
     float Rm[9], tv[3];
 #pragma unroll
     for (int k = 0; k < 9; ++k) Rm[k] = S.P[k];
@@ -613,33 +613,33 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
             for (int a = 0; a < 6; ++a) {
                 const float wa = wt * Ju[a], wb = wt * Jv[a];
 #pragma unroll
-                for (int b = a; b < 6; ++b) acc[k++] += wa * Ju[b] + wb * Jv[b];
-                acc[21 + a] += wa * ru + wb * rv;
+                for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
+                acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
             }
         }
     }
     // block reduction: a transpose butterfly leaves the warp total of value l
     // in lane l (31 shuffles for 32 values), FP64 across warps, then across
     // the CTAs of the cluster in rank order (identical sums in every CTA)
-    float v[32];
+    ACC v[32];
 #pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = k < kNV ? acc[k] : 0.f;
+    for (int k = 0; k < 32; ++k) v[k] = k < kNV ? acc[k] : ACC(0);
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const bool upper = (lane & o) != 0;
 #pragma unroll
         for (int i = 0; i < o; ++i) {
-            const float send = upper ? v[i] : v[i + o];
-            const float keep = upper ? v[i + o] : v[i];
+            const ACC send = upper ? v[i] : v[i + o];
+            const ACC keep = upper ? v[i + o] : v[i];
             v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
         }
     }
-    S.red[warp][lane] = v[0];
+    S.red[warp][lane] = static_cast<double>(v[0]);
     __syncthreads();
     if (tid < kNV) {
         double sum = 0.0;
 #pragma unroll
-        for (int w = 0; w < kRT / 32; ++w) sum += static_cast<double>(S.red[w][tid]);
+        for (int w = 0; w < kRT / 32; ++w) sum += S.red[w][tid];
         S.xch[slot][tid] = sum;
     }
     cluster.sync();
@@ -743,13 +743,13 @@ __device__ void take_totals(ReplaySmem& S) {
 }
 
 // Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
-template <int INIT, int ITER>
+template <int INIT, int ITER, typename ACC>
 __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot,
                              int iters) {
     const int tid = threadIdx.x;
     if (tid == 0) set_pass_pose(S, S.R, S.t);
     __syncthreads();
-    pass<INIT>(S, d, cluster, rank, CL, slot);
+    pass<INIT, ACC>(S, d, cluster, rank, CL, slot);
     if (tid == 0) take_totals(S);
     __syncthreads();
     for (int it = 0; it < iters; ++it) {
@@ -772,7 +772,7 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
             const bool solved = S.flag != 0;
             __syncthreads();
             if (solved) {
-                pass<ITER>(S, d, cluster, rank, CL, slot);
+                pass<ITER, ACC>(S, d, cluster, rank, CL, slot);
                 const bool better = S.tot[27] < S.cost;
                 __syncthreads();
                 if (better) {
@@ -854,7 +854,8 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
             }
             __syncthreads();
             if (d.lo_iters > 0) {
-                gauss_newton<kLO, kLO>(S, d, cluster, rank, CL, slot, d.lo_iters);
+                if (d.lo_fp64) gauss_newton<kLO, kLO, double>(S, d, cluster, rank, CL, slot, d.lo_iters);
+                else gauss_newton<kLO, kLO, float>(S, d, cluster, rank, CL, slot, d.lo_iters);
                 if (tid == 0) {
                     ++S.st.lo_count;
                     if (S.cost < S.st.best_score) {
@@ -907,7 +908,10 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
                 for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
             }
             __syncthreads();
-            if (d.final_iters > 0) gauss_newton<kFinInit, kFin>(S, d, cluster, rank, CL, slot, d.final_iters);
+            if (d.final_iters > 0) {
+                if (d.lo_fp64) gauss_newton<kFinInit, kFin, double>(S, d, cluster, rank, CL, slot, d.final_iters);
+                else gauss_newton<kFinInit, kFin, float>(S, d, cluster, rank, CL, slot, d.final_iters);
+            }
             if (tid == 0) set_pass_pose(S, S.R, S.t);
             __syncthreads();
             pass<kCountFull>(S, d, cluster, rank, CL, slot);
@@ -1185,6 +1189,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.final_iters = o.final_iters;
         d.polish = o.p3p_fp64_polish;
         d.enumerate_all = o.enumerate_all;
+        d.lo_fp64 = o.lo_fp64_accumulate;
         d.p_miss = o.p_miss;
         d.seed = o.seed;
         d.query_id = o.query_id;

@@ -239,6 +239,7 @@ static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     d.final_iters = o.final_iters;
     d.polish = o.p3p_fp64_polish;
     d.enumerate_all = 0;
+    d.lo_fp64 = o.lo_fp64_accumulate;
     d.p_miss = o.p_miss;
     d.seed = o.seed;
     d.query_id = o.query_id;

@@ -53,7 +53,8 @@ class RansacOpts(C.Structure):
     _fields_ = [("tau_px", C.c_double), ("max_score_corr", C.c_int32), ("batch", C.c_int32),
                 ("max_iters", C.c_int32), ("lo_iters", C.c_int32), ("p_miss", C.c_double),
                 ("final_iters", C.c_int32), ("p3p_fp64_polish", C.c_int32), ("cauchy_scale", C.c_double),
-                ("seed", C.c_uint64), ("query_id", C.c_uint32), ("enumerate_all", C.c_int32)]
+                ("seed", C.c_uint64), ("query_id", C.c_uint32), ("enumerate_all", C.c_int32),
+                ("lo_fp64_accumulate", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):

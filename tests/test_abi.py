@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_sizes_match_the_header_layout():
-    assert C.sizeof(imloc.RansacOpts) == 64
+    assert C.sizeof(imloc.RansacOpts) == 72
     assert C.sizeof(imloc.Result) == 264
     assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96
     assert C.sizeof(imloc.Corr) == 8 * 9
