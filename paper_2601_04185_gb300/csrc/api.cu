@@ -161,6 +161,7 @@ void imloc_destroy(imloc_ctx* c) {
     if (c->call_done) cudaEventDestroy(c->call_done);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->prof_pool) cudaEventDestroy(e);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     delete c;
 }
 

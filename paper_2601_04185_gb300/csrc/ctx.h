@@ -27,6 +27,8 @@ struct imloc_ctx {
     int* d_err = nullptr;         // sticky device error word
     cudaStream_t last_stream = nullptr;
     std::mutex mu;                // serialises calls on one context
+    // captured launch sequences of the batched RANSAC, one per size bucket
+    std::map<std::string, cudaGraphExec_t> graphs;
     // autotuned score-kernel variant (-1: not tuned yet)
     int score_variant = -1;
     float score_variant_ms = 0.f;

@@ -73,17 +73,38 @@ __device__ __forceinline__ int find_segment(const LiftSeg* segs, int n_seg, int6
     return lo;
 }
 
+constexpr int kTileSegs = 8;  // segments of one tile staged in shared memory
+
 __global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ LiftParams p) {
     __shared__ int s_tile;
     __shared__ int s_wcnt[kLiftItems * (kLiftThreads / 32)];
     __shared__ int s_excl;
+    __shared__ int s_seg0, s_nseg;
+    __shared__ LiftSeg s_seg[kTileSegs];
+    __shared__ LiftView s_view[kTileSegs];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kLiftThreads / 32;
 
-    if (tid == 0) s_tile = static_cast<int>(atomicAdd(p.tile_counter, 1u));
+    if (tid == 0) {
+        const int t = static_cast<int>(atomicAdd(p.tile_counter, 1u));
+        s_tile = t;
+        // the tile's segments: usually one or two, staged with their views
+        const int64_t b = static_cast<int64_t>(t) * kLiftTile;
+        const int64_t e = min(b + kLiftTile, p.n) - 1;
+        const int s0 = (b < p.n) ? find_segment(p.segs, p.n_seg, b) : 0;
+        const int s1 = (b < p.n) ? find_segment(p.segs, p.n_seg, e) : 0;
+        s_seg0 = s0;
+        s_nseg = (s1 - s0 + 1 <= kTileSegs) ? s1 - s0 + 1 : 0;
+    }
     __syncthreads();
     const int tile = s_tile;
     const int64_t base = static_cast<int64_t>(tile) * kLiftTile;
+    const int nseg_local = s_nseg, seg0 = s_seg0;
+    if (tid < nseg_local) {
+        s_seg[tid] = p.segs[seg0 + tid];
+        s_view[tid] = p.views[s_seg[tid].view];
+    }
+    __syncthreads();
 
     float vx[kLiftItems], vy[kLiftItems], vX[kLiftItems], vY[kLiftItems], vZ[kLiftItems], vw[kLiftItems];
     bool ok[kLiftItems];
@@ -94,16 +115,29 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ L
         ok[k] = false;
         seg_of[k] = -1;
         if (j >= p.n) continue;
-        const int s = find_segment(p.segs, p.n_seg, j);
-        seg_of[k] = s;
-        const LiftSeg sg = p.segs[s];
-        const float c = __ldg(p.conf + j);
-        const float u = __ldg(p.db_u + j), v = __ldg(p.db_v + j);
-        vx[k] = __ldg(p.q_u + j);
-        vy[k] = __ldg(p.q_v + j);
+        // match data is read once: streaming loads keep L2 for the depth taps
+        const float c = __ldcs(p.conf + j);
+        const float u = __ldcs(p.db_u + j), v = __ldcs(p.db_v + j);
+        vx[k] = __ldcs(p.q_u + j);
+        vy[k] = __ldcs(p.q_v + j);
         vw[k] = c;
+        int s;
+        LiftSeg sg;
+        const LiftView* Vp;
+        if (nseg_local > 0) {
+            int ls = nseg_local - 1;
+            while (ls > 0 && s_seg[ls].begin > j) --ls;
+            s = seg0 + ls;
+            sg = s_seg[ls];
+            Vp = &s_view[ls];
+        } else {
+            s = find_segment(p.segs, p.n_seg, j);
+            sg = p.segs[s];
+            Vp = &p.views[sg.view];
+        }
+        seg_of[k] = s;
         if (!(c > p.conf_min)) continue;
-        const LiftView& V = p.views[sg.view];
+        const LiftView& V = *Vp;
         float d;
         bool good;
         if (sg.dir == 0) {

@@ -34,6 +34,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -316,7 +317,7 @@ struct ScoreParams {
 // next item of the same query reuses the data.  Every thread scores HT poses
 // held in registers against every record of the share, in record order, so
 // the partial sums do not depend on (THREADS, HT).
-template <int THREADS, int HT, bool COUNT, int MINB>
+template <int THREADS, int HT, bool COUNT, int MINB, int UNR>
 __global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__ ScoreParams p) {
     static_assert(THREADS * HT == kTileHyps, "tile size");
     constexpr int TH = kTileHyps;
@@ -416,7 +417,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__
                 float part[HT];
 #pragma unroll
                 for (int h = 0; h < HT; ++h) part[h] = 0.f;
-#pragma unroll 2
+#pragma unroll UNR
                 for (int k = 0; k < nrec; ++k) {
                     const float4 A = rec[2 * k];      // X Y Z w
                     const float4 Bq = rec[2 * k + 1]; // x y
@@ -493,12 +494,14 @@ struct ScoreVariant {
     void (*fn_count)(ScoreParams);
 };
 static const ScoreVariant kScoreVariants[] = {
-    {128, 4, k_score<128, 4, false, 1>, k_score<128, 4, true, 1>},
-    {256, 2, k_score<256, 2, false, 1>, k_score<256, 2, true, 1>},
-    {64, 8, k_score<64, 8, false, 1>, k_score<64, 8, true, 1>},
-    {512, 1, k_score<512, 1, false, 1>, k_score<512, 1, true, 1>},
-    {128, 4, k_score<128, 4, false, 5>, k_score<128, 4, true, 5>},   // <= 102 registers: 5 CTAs / SM
-    {256, 2, k_score<256, 2, false, 4>, k_score<256, 2, true, 4>},   // <= 64 registers: 4 CTAs / SM
+    {128, 4, k_score<128, 4, false, 1, 2>, k_score<128, 4, true, 1, 2>},
+    {256, 2, k_score<256, 2, false, 1, 2>, k_score<256, 2, true, 1, 2>},
+    {64, 8, k_score<64, 8, false, 1, 1>, k_score<64, 8, true, 1, 1>},
+    {512, 1, k_score<512, 1, false, 1, 4>, k_score<512, 1, true, 1, 4>},
+    {128, 4, k_score<128, 4, false, 5, 1>, k_score<128, 4, true, 5, 1>},   // <= 102 registers: 5 CTAs / SM
+    {256, 2, k_score<256, 2, false, 1, 4>, k_score<256, 2, true, 1, 4>},
+    {128, 4, k_score<128, 4, false, 1, 1>, k_score<128, 4, true, 1, 1>},
+    {256, 2, k_score<256, 2, false, 3, 1>, k_score<256, 2, true, 3, 1>},   // <= 85 registers: 3 CTAs / SM
 };
 constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
 
@@ -1028,6 +1031,8 @@ static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool 
             float ms = 0.f;
             IMLOC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
             if (rep == 1 && ms < best_ms) { best_ms = ms; best = v; }
+            if (rep == 1 && getenv("IMLOC_VERBOSE"))
+                fprintf(stderr, "imloc: score variant %d (%d threads x %d poses) %.3f ms\n", v, V.threads, V.ht, ms);
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1247,7 +1252,25 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
                                              hq[q].n_inject, cudaMemcpyDeviceToDevice, stream));
         }
 
-    // ---- launches ----
+    // ---- launches: replayed from a CUDA graph per size bucket when possible ----
+    // The workspace is carved in the same order for the same sizes, so equal
+    // (query count, samples per wave, variant, buffers) give equal launches.
+    const bool debug = hq[0].score_by_id || hq[0].count_by_id || hq[0].triples || hq[0].slots_out || hq[0].inject;
+    const bool use_graph = !ctx->prof_on && ctx->score_variant >= 0 && !debug && !getenv("IMLOC_NO_GRAPHS");
+    std::string key;
+    if (use_graph) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
+                 (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
+        key = buf;
+        for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);
+        auto it = ctx->graphs.find(key);
+        if (it != ctx->graphs.end()) {
+            IMLOC_CUDA_TRY(cudaGraphLaunch(it->second, stream));
+            return IMLOC_OK;
+        }
+        IMLOC_CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    }
     for (int w = 0; w < W; ++w) {
         StepBuffers sb;
         sb.d_qd = const_cast<QueryDesc*>(d_qd);
@@ -1261,7 +1284,28 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.nhyp_all_len = W * nq;
         sb.d_init = nullptr;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
-        if (rc != IMLOC_OK) return rc;
+        if (rc != IMLOC_OK) {
+            if (use_graph) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(stream, &g);
+                if (g) cudaGraphDestroy(g);
+            }
+            return rc;
+        }
+    }
+    if (use_graph) {
+        cudaGraph_t g = nullptr;
+        IMLOC_CUDA_TRY(cudaStreamEndCapture(stream, &g));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        IMLOC_CUDA_TRY(e);
+        if (ctx->graphs.size() >= 64) {
+            for (auto& kv : ctx->graphs) cudaGraphExecDestroy(kv.second);
+            ctx->graphs.clear();
+        }
+        ctx->graphs[key] = ge;
+        IMLOC_CUDA_TRY(cudaGraphLaunch(ge, stream));
     }
     return IMLOC_OK;
 }
