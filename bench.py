@@ -624,7 +624,9 @@ def run_ours(args):
     opts = [imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=1234) for i in range(nq)]
     Ks = [q["K"] for q in queries]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    # a dedicated stream (the library captures its launch sequences as CUDA graphs on real streams)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     prep_lift = imloc.prepare_lift_batch(qb, d_views, d_match)
     prep_ransac = imloc.prepare_ransac_batch(Ks, opts)
 

@@ -1256,7 +1256,13 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     // The workspace is carved in the same order for the same sizes, so equal
     // (query count, samples per wave, variant, buffers) give equal launches.
     const bool debug = hq[0].score_by_id || hq[0].count_by_id || hq[0].triples || hq[0].slots_out || hq[0].inject;
-    const bool use_graph = !ctx->prof_on && ctx->score_variant >= 0 && !debug && !getenv("IMLOC_NO_GRAPHS");
+    // capture needs a real stream that nobody is capturing already (not the legacy default stream)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const bool real_stream = stream != nullptr && stream != cudaStreamLegacy && stream != cudaStreamPerThread &&
+                             cudaStreamIsCapturing(stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+    cudaGetLastError();
+    const bool use_graph = real_stream && !ctx->prof_on && ctx->score_variant >= 0 && !debug &&
+                           !getenv("IMLOC_NO_GRAPHS");
     std::string key;
     if (use_graph) {
         char buf[160];
@@ -1269,8 +1275,12 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
             IMLOC_CUDA_TRY(cudaGraphLaunch(it->second, stream));
             return IMLOC_OK;
         }
-        IMLOC_CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        if (cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            key.clear();
+        }
     }
+    const bool capturing = !key.empty();
     for (int w = 0; w < W; ++w) {
         StepBuffers sb;
         sb.d_qd = const_cast<QueryDesc*>(d_qd);
@@ -1285,15 +1295,16 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.d_init = nullptr;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
-            if (use_graph) {
+            if (capturing) {
                 cudaGraph_t g = nullptr;
                 cudaStreamEndCapture(stream, &g);
                 if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
             }
             return rc;
         }
     }
-    if (use_graph) {
+    if (capturing) {
         cudaGraph_t g = nullptr;
         IMLOC_CUDA_TRY(cudaStreamEndCapture(stream, &g));
         cudaGraphExec_t ge = nullptr;

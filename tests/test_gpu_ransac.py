@@ -395,3 +395,30 @@ def test_config3_batch_sampled_against_oracle(ctx):
         ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=q["hypotheses"],
                                 p_miss=0.0, query_id=i, seed=5)
         assert pose_close(res[i]["R"], res[i]["t"], ref["R"], ref["t"]), i
+
+
+def test_graph_replay_on_a_user_stream_matches(ctx):
+    """On a non-default stream the batched call is captured as a CUDA graph
+    (size bucket) and replayed on later calls; the results equal the first,
+    uncaptured call's."""
+    rng = np.random.default_rng(8)
+    qs = [synth.direct_query(rng, n, 0.4, 1024, 768, 800.0, weights="conf") for n in (4000, 9000, 2500)]
+    t = torch()
+    cat = lambda k: np.concatenate([q[k] for q in qs])
+    corr = imloc.corr_from_arrays(cat("x"), cat("y"), np.concatenate([q["X"] for q in qs]), cat("w"))
+    d_offs = t.from_numpy(np.cumsum([0] + [len(q["x"]) for q in qs]).astype(np.int64)).cuda()
+    opts = [imloc.default_opts(max_iters=3072, p_miss=0.0, query_id=i) for i in range(len(qs))]
+    s = t.cuda.Stream()
+    outs = []
+    for rep in range(3):
+        buf = t.zeros(len(qs) * imloc.RESULT_BYTES, dtype=t.uint8, device="cuda")
+        with t.cuda.stream(s):
+            ctx.ransac_pnp_batch_async(corr, d_offs, [q["K"] for q in qs], opts, buf, stream=s)
+        s.synchronize()
+        outs.append(imloc.results_from_bytes(buf.cpu().numpy(), len(qs)))
+    for rep in (1, 2):
+        for a, b in zip(outs[0], outs[rep]):
+            assert a["status"] == b["status"] == 0
+            np.testing.assert_array_equal(a["R"], b["R"])
+            assert a["num_inliers"] == b["num_inliers"]
+    assert ctx.device_error() == 0
