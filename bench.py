@@ -51,8 +51,9 @@ FP32_LANES_PER_SM = 128
 # capture of the current kernel (4-query case scaled by 16/4 queries);
 # None whenever the kernel changed since the capture.
 SCORE_TRAFFIC_PER_LAUNCH = None
-# DRAM bytes per lifted match from the committed ncu capture of k_lift (None until captured)
-LIFT_TRAFFIC_PER_MATCH = None
+# DRAM bytes (read + write) per lifted match from the committed ncu capture of
+# k_lift on the batched 9.48M-match shape (profiles/k_lift_batched_9.5M.md)
+LIFT_TRAFFIC_PER_MATCH = (1.229412e9 + 0.234057e9) / 9.48e6
 
 
 # ---------------------------------------------------------------------------
@@ -569,8 +570,11 @@ def run_lift_batched(dev, store_views_dev, queries, repeats=10):
     conf_ok = big["conf"] > np.float32(0.05)
     dirs = np.repeat(np.array(seg_dir), np.diff(np.array(seg_off)))
     nbytes = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 64, 32))) + 28 * n_valid
+    # the same count with 64-byte DRAM atoms for the random depth taps (2 x 64 B bilinear, 64 B lookup)
+    nbytes64 = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 128, 64))) + 28 * n_valid
     return {"matches_per_launch": n, "valid": n_valid, "bytes_per_launch": nbytes, "launch_ms": launch_ms,
             "achieved_gbs": nbytes / (launch_ms * 1e-3) / 1e9, "store_views": len(views),
+            "bytes_per_launch_64b_atoms": nbytes64, "achieved_gbs_64b_atoms": nbytes64 / (launch_ms * 1e-3) / 1e9,
             "workload": f"{len(queries)} serving queries concatenated ({n} matches) against "
                         f"{len(views)} resident 1024x768 depth maps, L2 flushed before each launch"}
 

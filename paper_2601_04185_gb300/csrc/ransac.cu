@@ -817,6 +817,7 @@ __device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inli
     if (d.result) *d.result = r;
 }
 
+template <typename ACC>
 __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayParams p) {
     __shared__ ReplaySmem S;
     cg::cluster_group cluster = cg::this_cluster();
@@ -825,6 +826,8 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
     const int q = blockIdx.x / CL;
     const int tid = threadIdx.x;
     const QueryDesc& d = p.qd[q];
+    // this instance serves the queries whose accumulation precision it implements
+    if ((d.lo_fp64 != 0) != (sizeof(ACC) == 8)) return;
     if (tid == 0) S.st = p.qs[q];
     __syncthreads();
     if (S.st.finished) return;  // same decision in every CTA of the cluster
@@ -857,8 +860,7 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
             }
             __syncthreads();
             if (d.lo_iters > 0) {
-                if (d.lo_fp64) gauss_newton<kLO, kLO, double>(S, d, cluster, rank, CL, slot, d.lo_iters);
-                else gauss_newton<kLO, kLO, float>(S, d, cluster, rank, CL, slot, d.lo_iters);
+                gauss_newton<kLO, kLO, ACC>(S, d, cluster, rank, CL, slot, d.lo_iters);
                 if (tid == 0) {
                     ++S.st.lo_count;
                     if (S.cost < S.st.best_score) {
@@ -911,10 +913,7 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
                 for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
             }
             __syncthreads();
-            if (d.final_iters > 0) {
-                if (d.lo_fp64) gauss_newton<kFinInit, kFin, double>(S, d, cluster, rank, CL, slot, d.final_iters);
-                else gauss_newton<kFinInit, kFin, float>(S, d, cluster, rank, CL, slot, d.final_iters);
-            }
+            if (d.final_iters > 0) gauss_newton<kFinInit, kFin, ACC>(S, d, cluster, rank, CL, slot, d.final_iters);
             if (tid == 0) set_pass_pose(S, S.R, S.t);
             __syncthreads();
             pass<kCountFull>(S, d, cluster, rank, CL, slot);
@@ -1092,8 +1091,12 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         const int cl = replay_cluster_size(ctx, nq);
         ReplayParams rp{b.d_qd, b.d_qs, b.d_wq, ctx->d_err};
         ProfScope prof(ctx, stream, "k_replay");
-        rc = launch_cluster(k_replay, rp, nq * cl, kRT, 0, cl, stream);
+        rc = launch_cluster(k_replay<float>, rp, nq * cl, kRT, 0, cl, stream);
         if (rc != IMLOC_OK) return rc;
+        if (b.any_fp64) {
+            rc = launch_cluster(k_replay<double>, rp, nq * cl, kRT, 0, cl, stream);
+            if (rc != IMLOC_OK) return rc;
+        }
         prof.end();
     }
     return IMLOC_OK;
@@ -1293,6 +1296,8 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.d_nhyp_all = d_nhyp;
         sb.nhyp_all_len = W * nq;
         sb.d_init = nullptr;
+        sb.any_fp64 = false;
+        for (int q = 0; q < nq; ++q) sb.any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
             if (capturing) {

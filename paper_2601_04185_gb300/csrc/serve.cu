@@ -332,6 +332,9 @@ static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted)
     b.d_nhyp_all = nullptr;
     b.nhyp_all_len = 0;
     b.d_init = S->d_init;
+    b.any_fp64 = false;
+    for (int s = 0; s < ns; ++s)
+        if (S->slots[s] && S->slots[s]->opts.lo_fp64_accumulate) b.any_fp64 = true;
     int rc = run_step(S->ictx, b, ns, n_init, total, false, st);
     if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaMemcpyAsync(S->h_qs, S->d_qs, sizeof(QueryState) * ns, cudaMemcpyDeviceToHost, st));
