@@ -663,6 +663,20 @@ def run_ours(args):
     barrier(world)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kstats = ctx.profile_read(reset=True)
+    # the scoring kernel alone (replay in its own kernel) for its roofline: a few extra steps
+    os.environ["IMLOC_NO_FUSE"] = "1"
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_read(reset=True)
+    n_unfused = max(3, args.steps // 3)
+    for _ in range(n_unfused):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    kstats_unfused = ctx.profile_read(reset=True)
+    del os.environ["IMLOC_NO_FUSE"]
     ctx.profile(False)
     total_s = sum(step_ms) / 1e3
     total_s_max = max_over_ranks(total_s, world)
@@ -719,6 +733,9 @@ def run_ours(args):
     score_launch_ms = kms.get("k_score", 0.0) / max(1, launches.get("k_score", 1))
     pairs_per_launch = pairs_per_step * args.steps / max(1, launches.get("k_score", 1))
     achieved_tflops = FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
+    u_launches, u_ms = kstats_unfused.get("k_score", (1, 0.0))
+    score_only_ms = u_ms / max(1, u_launches)
+    score_only_tflops = FLOPS_PER_PAIR * pairs_per_step / (score_only_ms * 1e-3) / 1e12 if score_only_ms else None
     peak_clock_mhz = 2070.0
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_clock_mhz * 1e6 / 1e12
     lift_ms = kms.get("k_lift", 0.0) / max(1, launches.get("k_lift", 1))
@@ -756,7 +773,14 @@ def run_ours(args):
                      "traffic": SCORE_TRAFFIC_PER_LAUNCH, "kernel": "k_score",
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
                      "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
-                     "launch_ms": score_launch_ms},
+                     "launch_ms": score_launch_ms,
+                     "note": "k_score is fused: each query's replay (LO, termination, Cauchy refinement) runs inside "
+                             "it once the query's last pose tile is scored; launch_ms includes those replays"},
+        "roofline_score_only": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                                "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
+                                "launch_ms": score_only_ms, "replay_kernel_ms": kstats_unfused.get("k_replay", (1, 0))[1]
+                                / max(1, kstats_unfused.get("k_replay", (1, 0))[0]),
+                                "note": "same steps with the replay in its own kernel (IMLOC_NO_FUSE=1)"},
         "lift_in_step": {"bound": "hbm", "achieved": lift_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (lift_gbs / hbm_peak) if lift_gbs else None, "bytes_per_launch": lift_bytes,
                          "launch_ms": lift_ms, "note": "16-query step: 800k matches, latency-bound"},

@@ -247,7 +247,9 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
 struct TilesParams {
     const QueryState* qs;
     const int32_t* n_hyp;
-    int32_t* tile_prefix;  // [nq+1]
+    int32_t* tile_prefix;  // [nq+1] prefix of items = max(tiles, 1)
+    int32_t* ntiles;       // [nq] pose tiles
+    int32_t* qdone;        // [nq] zeroed
     uint32_t* work_counter;
     int32_t nq;
     int32_t tile_hyps;
@@ -264,7 +266,12 @@ __global__ void __launch_bounds__(1024) k_tiles(const __grid_constant__ TilesPar
     for (int base = 0; base < p.nq; base += 1024) {
         const int q = base + threadIdx.x;
         int v = 0;
-        if (q < p.nq && !p.qs[q].done) v = (p.n_hyp[q] + p.tile_hyps - 1) / p.tile_hyps;
+        if (q < p.nq) {
+            const int t = p.qs[q].done ? 0 : (p.n_hyp[q] + p.tile_hyps - 1) / p.tile_hyps;
+            p.ntiles[q] = t;
+            p.qdone[q] = 0;
+            v = t > 0 ? t : 1;  // every query has at least one item (its replay trigger)
+        }
         int incl = v;
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int o = 1; o < 32; o <<= 1) {
@@ -292,6 +299,439 @@ __global__ void __launch_bounds__(1024) k_tiles(const __grid_constant__ TilesPar
 }
 
 // ============================================================================
+// k_replay: rounds in order, LO, termination, final refinement
+// ============================================================================
+constexpr int kRT = 256;             // threads per CTA of the stand-alone replay kernel
+constexpr int kMaxReplayThreads = 512;
+constexpr int kMaxReplayCluster = 8;
+constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
+
+enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
+
+struct ReplaySmem {
+    double R[9], t[3];    // current pose
+    double Rc[9], tc[3];  // candidate pose
+    double H[21], g[6];   // normal equations at the current pose
+    double cost, cnt;
+    double step, decrease, prev_cost;
+    double tot[32];
+    double xch[2][32];
+    double red[kMaxReplayThreads / 32][32];
+    float P[12];
+    int flag;
+    QueryState st;
+};
+
+struct ReplayParams {
+    const QueryDesc* qd;
+    QueryState* qs;
+    const WaveQ* wq;
+    int* err;
+};
+
+__device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], const double t[3]) {
+    for (int k = 0; k < 9; ++k) S.P[k] = static_cast<float>(R[k]);
+    for (int k = 0; k < 3; ++k) S.P[9 + k] = static_cast<float>(t[k]);
+}
+
+template <int MODE, typename ACC, int NT>
+__device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) ++S.st.passes;
+    constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
+    constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
+    ACC acc[kNV];
+#pragma unroll
+    for (int k = 0; k < kNV; ++k) acc[k] = ACC(0);
+    float Rm[9], tv[3];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Rm[k] = S.P[k];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) tv[k] = S.P[9 + k];
+    const float fx = d.fx, fy = d.fy, cx = d.cx, cy = d.cy, tau2 = d.tau2, c2 = d.cauchy2;
+    const int64_t n = kSub ? S.st.m : S.st.n;
+    const int64_t off = S.st.off;
+    for (int64_t i = static_cast<int64_t>(rank) * NT + tid; i < n; i += static_cast<int64_t>(CL) * NT) {
+        float X, Y, Z, w, x, y;
+        if (kSub) {
+            const float4* rec = reinterpret_cast<const float4*>(d.subset + i);
+            const float4 A = rec[0], B = rec[1];
+            X = A.x; Y = A.y; Z = A.z; w = A.w; x = B.x; y = B.y;
+        } else {
+            X = d.X[off + i]; Y = d.Y[off + i]; Z = d.Z[off + i]; w = d.w[off + i];
+            x = d.x[off + i]; y = d.y[off + i];
+        }
+        const float xc = fmaf(Rm[0], X, fmaf(Rm[1], Y, fmaf(Rm[2], Z, tv[0])));
+        const float yc = fmaf(Rm[3], X, fmaf(Rm[4], Y, fmaf(Rm[5], Z, tv[1])));
+        const float zc = fmaf(Rm[6], X, fmaf(Rm[7], Y, fmaf(Rm[8], Z, tv[2])));
+        const bool front = zc > 0.f;
+        float iz = 0.f, ru = 0.f, rv = 0.f, r2 = tau2;
+        if (front) {
+            iz = 1.0f / zc;
+            ru = fmaf(fx * xc, iz, cx) - x;
+            rv = fmaf(fy * yc, iz, cy) - y;
+            r2 = fmaf(ru, ru, rv * rv);
+        }
+        const bool inl = front && r2 < tau2;
+        float wt = 0.f;
+        if (MODE == kLO) {
+            acc[27] += w * (inl ? r2 : tau2);
+            wt = inl ? w : 0.f;
+            acc[28] += inl ? 1.f : 0.f;
+        } else if (MODE == kCountSub || MODE == kCountFull) {
+            acc[28] += inl ? 1.f : 0.f;
+            if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
+        } else {
+            bool in_set;
+            if (MODE == kFinInit) {
+                in_set = inl;
+                d.fixed[off + i] = inl ? 1 : 0;
+            } else {
+                in_set = d.fixed[off + i] != 0;
+            }
+            if (in_set) {
+                const float rr = front ? r2 : tau2;
+                acc[27] += w * c2 * log1pf(rr / c2);
+                acc[28] += 1.f;
+                wt = front ? w / (1.0f + r2 / c2) : 0.f;
+            }
+        }
+        if (kJac && wt > 0.f) {
+            const float dux = fx * iz, duz = -fx * xc * iz * iz;
+            const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
+            const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
+            const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
+            int k = 0;
+#pragma unroll
+            for (int a = 0; a < 6; ++a) {
+                const float wa = wt * Ju[a], wb = wt * Jv[a];
+#pragma unroll
+                for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
+                acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
+            }
+        }
+    }
+    // block reduction: a transpose butterfly leaves the warp total of value l
+    // in lane l (31 shuffles for 32 values), FP64 across warps, then across
+    // the CTAs of the cluster in rank order (identical sums in every CTA)
+    ACC v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = k < kNV ? acc[k] : ACC(0);
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const ACC send = upper ? v[i] : v[i + o];
+            const ACC keep = upper ? v[i + o] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    S.red[warp][lane] = static_cast<double>(v[0]);
+    __syncthreads();
+    if (tid < kNV) {
+        double sum = 0.0;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) sum += S.red[w][tid];
+        S.xch[slot][tid] = sum;
+    }
+    cluster.sync();
+    if (tid < kNV) {
+        double part[kMaxReplayCluster];
+#pragma unroll
+        for (int r = 0; r < kMaxReplayCluster; ++r)
+            part[r] = r < CL ? cluster.map_shared_rank(&S.xch[slot][0], r)[tid] : 0.0;
+        double sum = 0.0;
+#pragma unroll
+        for (int r = 0; r < kMaxReplayCluster; ++r) sum += part[r];
+        S.tot[tid] = sum;
+    }
+    slot ^= 1;
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
+    double A[6][6];
+    int k = 0;
+#pragma unroll
+    for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b) {
+            A[a][b] = Hu[k];
+            A[b][a] = Hu[k];
+            ++k;
+        }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a];
+    // Cholesky A = L L^T (L overwrites the lower triangle of A); inv[j] = 1 / L_jj
+    double inv[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            double s = A[i][j];
+#pragma unroll
+            for (int c = 0; c < j; ++c) s -= A[i][c] * A[j][c];
+            if (i == j) {
+                if (!(s > 0.0)) return false;
+                inv[i] = rsqrt(s);
+                A[i][i] = s * inv[i];
+            } else {
+                A[i][j] = s * inv[j];
+            }
+        }
+    }
+    double z[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        double s = -g[i];
+#pragma unroll
+        for (int c = 0; c < i; ++c) s -= A[i][c] * z[c];
+        z[i] = s * inv[i];
+    }
+#pragma unroll
+    for (int i = 5; i >= 0; --i) {
+        double s = z[i];
+#pragma unroll
+        for (int c = i + 1; c < 6; ++c) s -= A[c][i] * x[c];
+        x[i] = s * inv[i];
+    }
+    return true;
+}
+
+// candidate = Exp(dw) * (R, t) + (0, dv)
+__device__ void apply_step(const double R[9], const double t[3], const double dl[6], double Rc[9], double tc[3]) {
+    const double th2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+    double A, B;
+    if (th2 < 1e-4) {
+        // sin(th)/th and (1 - cos(th))/th^2 by their Taylor series (error < th^8/9! < 1e-21 here)
+        A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
+        B = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
+    } else {
+        const double th = sqrt(th2);
+        double sn, cs;
+        sincos(th, &sn, &cs);
+        A = sn / th;
+        B = (1.0 - cs) / th2;
+    }
+    const double Kx[9] = {0, -dl[2], dl[1], dl[2], 0, -dl[0], -dl[1], dl[0], 0};
+    double E[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double k2 = 0.0;
+            for (int c = 0; c < 3; ++c) k2 += Kx[3 * i + c] * Kx[3 * c + j];
+            E[3 * i + j] = (i == j ? 1.0 : 0.0) + A * Kx[3 * i + j] + B * k2;
+        }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) Rc[3 * i + j] = E[3 * i] * R[j] + E[3 * i + 1] * R[3 + j] + E[3 * i + 2] * R[6 + j];
+        tc[i] = E[3 * i] * t[0] + E[3 * i + 1] * t[1] + E[3 * i + 2] * t[2] + dl[3 + i];
+    }
+}
+
+__device__ void take_totals(ReplaySmem& S) {
+    for (int k = 0; k < 21; ++k) S.H[k] = S.tot[k];
+    for (int k = 0; k < 6; ++k) S.g[k] = S.tot[21 + k];
+    S.cost = S.tot[27];
+    S.cnt = S.tot[28];
+}
+
+// Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
+template <int INIT, int ITER, typename ACC, int NT>
+__device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot,
+                             int iters) {
+    const int tid = threadIdx.x;
+    if (tid == 0) set_pass_pose(S, S.R, S.t);
+    __syncthreads();
+    pass<INIT, ACC, NT>(S, d, cluster, rank, CL, slot);
+    if (tid == 0) take_totals(S);
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        if (S.cnt < 3.0) break;
+        bool accepted = false;
+        double mu = 0.0;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            if (tid == 0) {
+                double dl[6];
+                S.flag = solve6(S.H, S.g, mu, dl) ? 1 : 0;
+                if (S.flag) {
+                    apply_step(S.R, S.t, dl, S.Rc, S.tc);
+                    set_pass_pose(S, S.Rc, S.tc);
+                    double dn = 0.0;
+                    for (int k = 0; k < 6; ++k) dn += dl[k] * dl[k];
+                    S.step = sqrt(dn);
+                }
+            }
+            __syncthreads();
+            const bool solved = S.flag != 0;
+            __syncthreads();
+            if (solved) {
+                pass<ITER, ACC, NT>(S, d, cluster, rank, CL, slot);
+                const bool better = S.tot[27] < S.cost;
+                __syncthreads();
+                if (better) {
+                    if (tid == 0) {
+                        S.decrease = S.cost - S.tot[27];
+                        S.prev_cost = S.cost;
+                        for (int k = 0; k < 9; ++k) S.R[k] = S.Rc[k];
+                        for (int k = 0; k < 3; ++k) S.t[k] = S.tc[k];
+                        take_totals(S);
+                    }
+                    __syncthreads();
+                    accepted = true;
+                    break;
+                }
+            }
+            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
+        }
+        if (!accepted) break;
+        // converged: a tiny step, or a step that lowered the cost by < 1e-6 of it
+        if (S.step < 1e-10 || S.decrease < 1e-6 * S.prev_cost) break;
+    }
+}
+
+__device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inliers) {
+    imloc_result r;
+    memset(&r, 0, sizeof(r));
+    for (int k = 0; k < 9; ++k) { r.R[k] = S.R[k]; r.R_best[k] = S.st.R[k]; }
+    for (int k = 0; k < 3; ++k) { r.t[k] = S.t[k]; r.t_best[k] = S.st.t[k]; }
+    r.score = S.st.have_best ? S.st.best_score : 0.0;
+    r.num_inliers = num_inliers;
+    r.subset_inliers = S.st.subset_inliers;
+    r.iterations = S.st.iters;
+    r.rounds = S.st.rounds_done;
+    r.lo_count = S.st.lo_count;
+    r.hypotheses = S.st.hypotheses;
+    r.best_hyp = S.st.best_hyp;
+    r.status = S.st.status;
+    r.passes = S.st.passes;
+    if (d.result) *d.result = r;
+}
+
+// Rounds [r0, r1) of one query in order, LO, termination and, once done, the
+// final refinement, run by every CTA of one cluster (NT threads each) with
+// identical decisions.  Reads and writes the query's state in global memory.
+template <typename ACC, int NT>
+__device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, QueryState* qs, const WaveQ& wq,
+                                          cg::cluster_group& cluster, int CL, int rank) {
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid == 0) S.st = *qs;
+    // every CTA holds its copy of the state before rank 0 can write it back
+    cluster.sync();
+    if (S.st.finished) return;  // same decision in every CTA of the cluster
+    int slot = 0;
+    const int r_end = min(wq.r1, d.rounds);
+    for (int r = wq.r0; r < r_end; ++r) {
+        if (S.st.done) break;
+        const uint64_t key = d.round_best[r];
+        const int hyps_r = d.round_hyps[r];
+        bool improve = false;
+        float sc = 0.f;
+        if (key != ~0ull) {
+            sc = __uint_as_float(static_cast<uint32_t>(key >> 32));
+            improve = static_cast<double>(sc) < S.st.best_score;
+        }
+        __syncthreads();
+        if (improve) {
+            if (tid == 0) {
+                const uint32_t id = static_cast<uint32_t>(key & 0xffffffffu);
+                const PoseF ps = d.slots[static_cast<int64_t>(id) - 4 * wq.s_begin];
+                for (int k = 0; k < 9; ++k) S.R[k] = ps.R[k];
+                for (int k = 0; k < 3; ++k) S.t[k] = ps.t[k];
+                orthonormalize<double>(S.R);  // float32 pose -> rotation to FP64 rounding
+                orthonormalize<double>(S.R);
+                for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
+                for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
+                S.st.best_score = sc;
+                S.st.best_hyp = id;
+                S.st.have_best = 1;
+            }
+            __syncthreads();
+            if (d.lo_iters > 0) {
+                gauss_newton<kLO, kLO, ACC, NT>(S, d, cluster, rank, CL, slot, d.lo_iters);
+                if (tid == 0) {
+                    ++S.st.lo_count;
+                    if (S.cost < S.st.best_score) {
+                        for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
+                        for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
+                        S.st.best_score = S.cost;
+                    }
+                    S.st.subset_inliers = static_cast<int32_t>(S.cnt);
+                }
+            } else {
+                if (tid == 0) set_pass_pose(S, S.st.R, S.st.t);
+                __syncthreads();
+                pass<kCountSub, float, NT>(S, d, cluster, rank, CL, slot);
+                if (tid == 0) S.st.subset_inliers = static_cast<int32_t>(S.tot[28]);
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int64_t it = min(static_cast<int64_t>(r + 1) * d.batch, static_cast<int64_t>(d.hyps));
+            S.st.iters = it;
+            S.st.rounds_done = r + 1;
+            S.st.hypotheses += hyps_r;
+            bool stop = it >= d.hyps;
+            if (!stop && d.p_miss > 0.0 && S.st.have_best && S.st.m > 0) {
+                const double eps = static_cast<double>(S.st.subset_inliers) / static_cast<double>(S.st.m);
+                const double e3 = eps * eps * eps;
+                double need;
+                if (e3 >= 1.0) need = 0.0;
+                else if (e3 <= 0.0) need = INFINITY;
+                else need = log(d.p_miss) / log(1.0 - e3);
+                stop = static_cast<double>(it) >= need;
+            }
+            if (stop) S.st.done = 1;
+        }
+        __syncthreads();
+    }
+    if (S.st.done && !S.st.finished) {
+        if (!S.st.have_best) {
+            if (tid == 0) {
+                if (S.st.status == IMLOC_OK) S.st.status = IMLOC_ERR_DEGENERATE;
+                for (int k = 0; k < 9; ++k) S.R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+                for (int k = 0; k < 3; ++k) S.t[k] = 0.0;
+                if (rank == 0) write_result(S, d, 0);
+                S.st.finished = 1;
+            }
+            __syncthreads();
+        } else {
+            if (tid == 0) {
+                for (int k = 0; k < 9; ++k) S.R[k] = S.st.R[k];
+                for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
+            }
+            __syncthreads();
+            if (d.final_iters > 0) gauss_newton<kFinInit, kFin, ACC, NT>(S, d, cluster, rank, CL, slot, d.final_iters);
+            if (tid == 0) set_pass_pose(S, S.R, S.t);
+            __syncthreads();
+            pass<kCountFull, float, NT>(S, d, cluster, rank, CL, slot);
+            if (tid == 0) {
+                if (rank == 0) write_result(S, d, static_cast<int64_t>(S.tot[28]));
+                S.st.finished = 1;
+            }
+            __syncthreads();
+        }
+    }
+    if (rank == 0 && tid == 0) *qs = S.st;
+    __syncthreads();
+}
+
+// Stand-alone replay: one cluster per query (queries whose accumulation
+// precision this instance implements; the others are skipped).
+template <typename ACC>
+__global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayParams p) {
+    __shared__ ReplaySmem S;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CL = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int q = blockIdx.x / CL;
+    const QueryDesc& d = p.qd[q];
+    if ((d.lo_fp64 != 0) == (sizeof(ACC) == 8)) replay_query<ACC, kRT>(S, d, p.qs + q, p.wq[q], cluster, CL, rank);
+    // no CTA may leave while another can still read its shared memory
+    cluster.sync();
+}
+
+// ============================================================================
 // k_score: persistent, cluster-split hypothesis scoring
 // ============================================================================
 constexpr int kChunk = 256;        // subset records per bulk copy (8 KB)
@@ -302,10 +742,12 @@ constexpr int kTileHyps = 512;     // poses per item (THREADS x HT for every var
 
 struct ScoreParams {
     const QueryDesc* qd;
-    const QueryState* qs;
+    QueryState* qs;
     const WaveQ* wq;
     const int32_t* n_hyp;
-    const int32_t* tile_prefix;
+    const int32_t* tile_prefix;  // [nq + 1] items: max(tiles, 1) per query
+    const int32_t* ntiles;       // [nq] pose tiles per query (0 for a finished query)
+    int32_t* qdone;              // [nq] items completed (fused replay trigger)
     uint32_t* work_counter;
     int32_t nq;
     int* err;
@@ -317,8 +759,11 @@ struct ScoreParams {
 // next item of the same query reuses the data.  Every thread scores HT poses
 // held in registers against every record of the share, in record order, so
 // the partial sums do not depend on (THREADS, HT).
-template <int THREADS, int HT, bool COUNT, int MINB, int UNR>
-__global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__ ScoreParams p) {
+// FUSED: after its last item of a query, a cluster replays that query
+// (round-best / LO / termination / refinement) while other clusters keep
+// scoring: the replay needs no separate launch and overlaps the scoring.
+template <int THREADS, int HT, bool COUNT, int MINB, int UNR, bool FUSED, int MINB_FUSED>
+__global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(const __grid_constant__ ScoreParams p) {
     static_assert(THREADS * HT == kTileHyps, "tile size");
     constexpr int TH = kTileHyps;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -326,7 +771,8 @@ __global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__
     float* s_part = reinterpret_cast<float*>(buf + kWinRecords);
     int* s_cnt = reinterpret_cast<int*>(s_part + TH);
     __shared__ __align__(8) uint64_t bar[kWinChunks];
-    __shared__ int s_item;
+    __shared__ int s_item, s_last;
+    __shared__ ReplaySmem S_rep;
 
     cg::cluster_group cluster = cg::this_cluster();
     const int CS = static_cast<int>(cluster.num_blocks());
@@ -356,6 +802,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__
         const int q = lo;
         const int tile = item - p.tile_prefix[q];
         const QueryDesc& d = p.qd[q];
+        if (tile < p.ntiles[q]) {
         const int m = p.qs[q].m;
         const int nh = p.n_hyp[q];
         const int64_t slot_base = 4 * p.wq[q].s_begin;
@@ -484,6 +931,23 @@ __global__ void __launch_bounds__(THREADS, MINB) k_score(const __grid_constant__
         // s_part is rewritten only after the next item's first cluster barrier,
         // which every CTA reaches after finishing the reads above; the subset
         // buffer is rewritten only after both item barriers.
+        }  // scored tile
+        if constexpr (FUSED) {
+            // the item is complete in every CTA (its minima are visible device-wide)
+            __threadfence();
+            cluster.sync();
+            if (rank == 0 && threadIdx.x == 0) {
+                const int items_q = p.tile_prefix[q + 1] - p.tile_prefix[q];
+                const int old = atomicAdd(&p.qdone[q], 1);
+                s_last = (old + 1 == items_q) ? 1 : 0;
+            }
+            cluster.sync();
+            const int last = *cluster.map_shared_rank(&s_last, 0);
+            if (last && !d.lo_fp64) {
+                __threadfence();
+                replay_query<float, THREADS>(S_rep, d, p.qs + q, p.wq[q], cluster, CS, rank);
+            }
+        }
     }
 }
 
@@ -492,441 +956,29 @@ struct ScoreVariant {
     int threads, ht;
     void (*fn)(ScoreParams);
     void (*fn_count)(ScoreParams);
+    void (*fused)(ScoreParams);
+    void (*fused_count)(ScoreParams);
 };
+// MF: occupancy bound of the fused instance = the CTAs per SM of the unfused one,
+// so that the replay code does not cost the scoring loop any occupancy
+#define IMLOC_SCORE_VARIANT(T, H, M, U, MF)                                                            \
+    {T, H, k_score<T, H, false, M, U, false, MF>, k_score<T, H, true, M, U, false, MF>,                 \
+     k_score<T, H, false, M, U, true, MF>, k_score<T, H, true, M, U, true, MF>}
 static const ScoreVariant kScoreVariants[] = {
-    {128, 4, k_score<128, 4, false, 1, 2>, k_score<128, 4, true, 1, 2>},
-    {256, 2, k_score<256, 2, false, 1, 2>, k_score<256, 2, true, 1, 2>},
-    {64, 8, k_score<64, 8, false, 1, 1>, k_score<64, 8, true, 1, 1>},
-    {512, 1, k_score<512, 1, false, 1, 4>, k_score<512, 1, true, 1, 4>},
-    {128, 4, k_score<128, 4, false, 5, 1>, k_score<128, 4, true, 5, 1>},   // <= 102 registers: 5 CTAs / SM
-    {256, 2, k_score<256, 2, false, 1, 4>, k_score<256, 2, true, 1, 4>},
-    {128, 4, k_score<128, 4, false, 1, 1>, k_score<128, 4, true, 1, 1>},
-    {256, 2, k_score<256, 2, false, 3, 1>, k_score<256, 2, true, 3, 1>},   // <= 85 registers: 3 CTAs / SM
+    IMLOC_SCORE_VARIANT(128, 4, 1, 2, 4),
+    IMLOC_SCORE_VARIANT(256, 2, 1, 2, 2),
+    IMLOC_SCORE_VARIANT(64, 8, 1, 1, 4),
+    IMLOC_SCORE_VARIANT(512, 1, 1, 4, 1),
+    IMLOC_SCORE_VARIANT(128, 4, 5, 1, 5),  // <= 102 registers: 5 CTAs / SM
+    IMLOC_SCORE_VARIANT(256, 2, 1, 4, 2),
+    IMLOC_SCORE_VARIANT(128, 4, 1, 1, 4),
+    IMLOC_SCORE_VARIANT(256, 2, 3, 1, 3),  // <= 85 registers: 3 CTAs / SM
 };
+#undef IMLOC_SCORE_VARIANT
 constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
 
 static size_t score_smem_bytes(bool count) {
     return sizeof(ScoreCorr) * kWinRecords + sizeof(float) * kTileHyps + (count ? sizeof(int) * kTileHyps : 0);
-}
-
-// ============================================================================
-// k_replay: rounds in order, LO, termination, final refinement
-// ============================================================================
-constexpr int kRT = 256;
-constexpr int kMaxReplayCluster = 8;
-constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
-
-enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
-
-struct ReplaySmem {
-    double R[9], t[3];    // current pose
-    double Rc[9], tc[3];  // candidate pose
-    double H[21], g[6];   // normal equations at the current pose
-    double cost, cnt;
-    double step, decrease, prev_cost;
-    double tot[32];
-    double xch[2][32];
-    double red[kRT / 32][32];
-    float P[12];
-    int flag;
-    QueryState st;
-};
-
-struct ReplayParams {
-    const QueryDesc* qd;
-    QueryState* qs;
-    const WaveQ* wq;
-    int* err;
-};
-
-__device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], const double t[3]) {
-    for (int k = 0; k < 9; ++k) S.P[k] = static_cast<float>(R[k]);
-    for (int k = 0; k < 3; ++k) S.P[9 + k] = static_cast<float>(t[k]);
-}
-
-template <int MODE, typename ACC = float>
-__device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) ++S.st.passes;
-    constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
-    constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
-    ACC acc[kNV];
-#pragma unroll
-    for (int k = 0; k < kNV; ++k) acc[k] = ACC(0);
-    float Rm[9], tv[3];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Rm[k] = S.P[k];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) tv[k] = S.P[9 + k];
-    const float fx = d.fx, fy = d.fy, cx = d.cx, cy = d.cy, tau2 = d.tau2, c2 = d.cauchy2;
-    const int64_t n = kSub ? S.st.m : S.st.n;
-    const int64_t off = S.st.off;
-    for (int64_t i = static_cast<int64_t>(rank) * kRT + tid; i < n; i += static_cast<int64_t>(CL) * kRT) {
-        float X, Y, Z, w, x, y;
-        if (kSub) {
-            const float4* rec = reinterpret_cast<const float4*>(d.subset + i);
-            const float4 A = rec[0], B = rec[1];
-            X = A.x; Y = A.y; Z = A.z; w = A.w; x = B.x; y = B.y;
-        } else {
-            X = d.X[off + i]; Y = d.Y[off + i]; Z = d.Z[off + i]; w = d.w[off + i];
-            x = d.x[off + i]; y = d.y[off + i];
-        }
-        const float xc = fmaf(Rm[0], X, fmaf(Rm[1], Y, fmaf(Rm[2], Z, tv[0])));
-        const float yc = fmaf(Rm[3], X, fmaf(Rm[4], Y, fmaf(Rm[5], Z, tv[1])));
-        const float zc = fmaf(Rm[6], X, fmaf(Rm[7], Y, fmaf(Rm[8], Z, tv[2])));
-        const bool front = zc > 0.f;
-        float iz = 0.f, ru = 0.f, rv = 0.f, r2 = tau2;
-        if (front) {
-            iz = 1.0f / zc;
-            ru = fmaf(fx * xc, iz, cx) - x;
-            rv = fmaf(fy * yc, iz, cy) - y;
-            r2 = fmaf(ru, ru, rv * rv);
-        }
-        const bool inl = front && r2 < tau2;
-        float wt = 0.f;
-        if (MODE == kLO) {
-            acc[27] += w * (inl ? r2 : tau2);
-            wt = inl ? w : 0.f;
-            acc[28] += inl ? 1.f : 0.f;
-        } else if (MODE == kCountSub || MODE == kCountFull) {
-            acc[28] += inl ? 1.f : 0.f;
-            if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
-        } else {
-            bool in_set;
-            if (MODE == kFinInit) {
-                in_set = inl;
-                d.fixed[off + i] = inl ? 1 : 0;
-            } else {
-                in_set = d.fixed[off + i] != 0;
-            }
-            if (in_set) {
-                const float rr = front ? r2 : tau2;
-                acc[27] += w * c2 * log1pf(rr / c2);
-                acc[28] += 1.f;
-                wt = front ? w / (1.0f + r2 / c2) : 0.f;
-            }
-        }
-        if (kJac && wt > 0.f) {
-            const float dux = fx * iz, duz = -fx * xc * iz * iz;
-            const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
-            const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
-            const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
-            int k = 0;
-#pragma unroll
-            for (int a = 0; a < 6; ++a) {
-                const float wa = wt * Ju[a], wb = wt * Jv[a];
-#pragma unroll
-                for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
-                acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
-            }
-        }
-    }
-    // block reduction: a transpose butterfly leaves the warp total of value l
-    // in lane l (31 shuffles for 32 values), FP64 across warps, then across
-    // the CTAs of the cluster in rank order (identical sums in every CTA)
-    ACC v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = k < kNV ? acc[k] : ACC(0);
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-        const bool upper = (lane & o) != 0;
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const ACC send = upper ? v[i] : v[i + o];
-            const ACC keep = upper ? v[i + o] : v[i];
-            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    S.red[warp][lane] = static_cast<double>(v[0]);
-    __syncthreads();
-    if (tid < kNV) {
-        double sum = 0.0;
-#pragma unroll
-        for (int w = 0; w < kRT / 32; ++w) sum += S.red[w][tid];
-        S.xch[slot][tid] = sum;
-    }
-    cluster.sync();
-    if (tid < kNV) {
-        double part[kMaxReplayCluster];
-#pragma unroll
-        for (int r = 0; r < kMaxReplayCluster; ++r)
-            part[r] = r < CL ? cluster.map_shared_rank(&S.xch[slot][0], r)[tid] : 0.0;
-        double sum = 0.0;
-#pragma unroll
-        for (int r = 0; r < kMaxReplayCluster; ++r) sum += part[r];
-        S.tot[tid] = sum;
-    }
-    slot ^= 1;
-    __syncthreads();
-}
-
-__device__ __forceinline__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
-    double A[6][6];
-    int k = 0;
-#pragma unroll
-    for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b = a; b < 6; ++b) {
-            A[a][b] = Hu[k];
-            A[b][a] = Hu[k];
-            ++k;
-        }
-#pragma unroll
-    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a];
-    // Cholesky A = L L^T (L overwrites the lower triangle of A); inv[j] = 1 / L_jj
-    double inv[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-#pragma unroll
-        for (int j = 0; j <= i; ++j) {
-            double s = A[i][j];
-#pragma unroll
-            for (int c = 0; c < j; ++c) s -= A[i][c] * A[j][c];
-            if (i == j) {
-                if (!(s > 0.0)) return false;
-                inv[i] = rsqrt(s);
-                A[i][i] = s * inv[i];
-            } else {
-                A[i][j] = s * inv[j];
-            }
-        }
-    }
-    double z[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        double s = -g[i];
-#pragma unroll
-        for (int c = 0; c < i; ++c) s -= A[i][c] * z[c];
-        z[i] = s * inv[i];
-    }
-#pragma unroll
-    for (int i = 5; i >= 0; --i) {
-        double s = z[i];
-#pragma unroll
-        for (int c = i + 1; c < 6; ++c) s -= A[c][i] * x[c];
-        x[i] = s * inv[i];
-    }
-    return true;
-}
-
-// candidate = Exp(dw) * (R, t) + (0, dv)
-__device__ void apply_step(const double R[9], const double t[3], const double dl[6], double Rc[9], double tc[3]) {
-    const double th2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
-    double A, B;
-    if (th2 < 1e-4) {
-        // sin(th)/th and (1 - cos(th))/th^2 by their Taylor series (error < th^8/9! < 1e-21 here)
-        A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
-        B = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
-    } else {
-        const double th = sqrt(th2);
-        double sn, cs;
-        sincos(th, &sn, &cs);
-        A = sn / th;
-        B = (1.0 - cs) / th2;
-    }
-    const double Kx[9] = {0, -dl[2], dl[1], dl[2], 0, -dl[0], -dl[1], dl[0], 0};
-    double E[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double k2 = 0.0;
-            for (int c = 0; c < 3; ++c) k2 += Kx[3 * i + c] * Kx[3 * c + j];
-            E[3 * i + j] = (i == j ? 1.0 : 0.0) + A * Kx[3 * i + j] + B * k2;
-        }
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) Rc[3 * i + j] = E[3 * i] * R[j] + E[3 * i + 1] * R[3 + j] + E[3 * i + 2] * R[6 + j];
-        tc[i] = E[3 * i] * t[0] + E[3 * i + 1] * t[1] + E[3 * i + 2] * t[2] + dl[3 + i];
-    }
-}
-
-__device__ void take_totals(ReplaySmem& S) {
-    for (int k = 0; k < 21; ++k) S.H[k] = S.tot[k];
-    for (int k = 0; k < 6; ++k) S.g[k] = S.tot[21 + k];
-    S.cost = S.tot[27];
-    S.cnt = S.tot[28];
-}
-
-// Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
-template <int INIT, int ITER, typename ACC>
-__device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot,
-                             int iters) {
-    const int tid = threadIdx.x;
-    if (tid == 0) set_pass_pose(S, S.R, S.t);
-    __syncthreads();
-    pass<INIT, ACC>(S, d, cluster, rank, CL, slot);
-    if (tid == 0) take_totals(S);
-    __syncthreads();
-    for (int it = 0; it < iters; ++it) {
-        if (S.cnt < 3.0) break;
-        bool accepted = false;
-        double mu = 0.0;
-        for (int attempt = 0; attempt < 4; ++attempt) {
-            if (tid == 0) {
-                double dl[6];
-                S.flag = solve6(S.H, S.g, mu, dl) ? 1 : 0;
-                if (S.flag) {
-                    apply_step(S.R, S.t, dl, S.Rc, S.tc);
-                    set_pass_pose(S, S.Rc, S.tc);
-                    double dn = 0.0;
-                    for (int k = 0; k < 6; ++k) dn += dl[k] * dl[k];
-                    S.step = sqrt(dn);
-                }
-            }
-            __syncthreads();
-            const bool solved = S.flag != 0;
-            __syncthreads();
-            if (solved) {
-                pass<ITER, ACC>(S, d, cluster, rank, CL, slot);
-                const bool better = S.tot[27] < S.cost;
-                __syncthreads();
-                if (better) {
-                    if (tid == 0) {
-                        S.decrease = S.cost - S.tot[27];
-                        S.prev_cost = S.cost;
-                        for (int k = 0; k < 9; ++k) S.R[k] = S.Rc[k];
-                        for (int k = 0; k < 3; ++k) S.t[k] = S.tc[k];
-                        take_totals(S);
-                    }
-                    __syncthreads();
-                    accepted = true;
-                    break;
-                }
-            }
-            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
-        }
-        if (!accepted) break;
-        // converged: a tiny step, or a step that lowered the cost by < 1e-6 of it
-        if (S.step < 1e-10 || S.decrease < 1e-6 * S.prev_cost) break;
-    }
-}
-
-__device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inliers) {
-    imloc_result r;
-    memset(&r, 0, sizeof(r));
-    for (int k = 0; k < 9; ++k) { r.R[k] = S.R[k]; r.R_best[k] = S.st.R[k]; }
-    for (int k = 0; k < 3; ++k) { r.t[k] = S.t[k]; r.t_best[k] = S.st.t[k]; }
-    r.score = S.st.have_best ? S.st.best_score : 0.0;
-    r.num_inliers = num_inliers;
-    r.subset_inliers = S.st.subset_inliers;
-    r.iterations = S.st.iters;
-    r.rounds = S.st.rounds_done;
-    r.lo_count = S.st.lo_count;
-    r.hypotheses = S.st.hypotheses;
-    r.best_hyp = S.st.best_hyp;
-    r.status = S.st.status;
-    r.passes = S.st.passes;
-    if (d.result) *d.result = r;
-}
-
-template <typename ACC>
-__global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayParams p) {
-    __shared__ ReplaySmem S;
-    cg::cluster_group cluster = cg::this_cluster();
-    const int CL = static_cast<int>(cluster.num_blocks());
-    const int rank = static_cast<int>(cluster.block_rank());
-    const int q = blockIdx.x / CL;
-    const int tid = threadIdx.x;
-    const QueryDesc& d = p.qd[q];
-    // this instance serves the queries whose accumulation precision it implements
-    if ((d.lo_fp64 != 0) != (sizeof(ACC) == 8)) return;
-    if (tid == 0) S.st = p.qs[q];
-    __syncthreads();
-    if (S.st.finished) return;  // same decision in every CTA of the cluster
-    int slot = 0;
-    const int r_end = min(p.wq[q].r1, d.rounds);
-    for (int r = p.wq[q].r0; r < r_end; ++r) {
-        if (S.st.done) break;
-        const uint64_t key = d.round_best[r];
-        const int hyps_r = d.round_hyps[r];
-        bool improve = false;
-        float sc = 0.f;
-        if (key != ~0ull) {
-            sc = __uint_as_float(static_cast<uint32_t>(key >> 32));
-            improve = static_cast<double>(sc) < S.st.best_score;
-        }
-        __syncthreads();
-        if (improve) {
-            if (tid == 0) {
-                const uint32_t id = static_cast<uint32_t>(key & 0xffffffffu);
-                const PoseF ps = d.slots[static_cast<int64_t>(id) - 4 * p.wq[q].s_begin];
-                for (int k = 0; k < 9; ++k) S.R[k] = ps.R[k];
-                for (int k = 0; k < 3; ++k) S.t[k] = ps.t[k];
-                orthonormalize<double>(S.R);  // float32 pose -> rotation to FP64 rounding
-                orthonormalize<double>(S.R);
-                for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
-                for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
-                S.st.best_score = sc;
-                S.st.best_hyp = id;
-                S.st.have_best = 1;
-            }
-            __syncthreads();
-            if (d.lo_iters > 0) {
-                gauss_newton<kLO, kLO, ACC>(S, d, cluster, rank, CL, slot, d.lo_iters);
-                if (tid == 0) {
-                    ++S.st.lo_count;
-                    if (S.cost < S.st.best_score) {
-                        for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
-                        for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
-                        S.st.best_score = S.cost;
-                    }
-                    S.st.subset_inliers = static_cast<int32_t>(S.cnt);
-                }
-            } else {
-                if (tid == 0) set_pass_pose(S, S.st.R, S.st.t);
-                __syncthreads();
-                pass<kCountSub>(S, d, cluster, rank, CL, slot);
-                if (tid == 0) S.st.subset_inliers = static_cast<int32_t>(S.tot[28]);
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            const int64_t it = min(static_cast<int64_t>(r + 1) * d.batch, static_cast<int64_t>(d.hyps));
-            S.st.iters = it;
-            S.st.rounds_done = r + 1;
-            S.st.hypotheses += hyps_r;
-            bool stop = it >= d.hyps;
-            if (!stop && d.p_miss > 0.0 && S.st.have_best && S.st.m > 0) {
-                const double eps = static_cast<double>(S.st.subset_inliers) / static_cast<double>(S.st.m);
-                const double e3 = eps * eps * eps;
-                double need;
-                if (e3 >= 1.0) need = 0.0;
-                else if (e3 <= 0.0) need = INFINITY;
-                else need = log(d.p_miss) / log(1.0 - e3);
-                stop = static_cast<double>(it) >= need;
-            }
-            if (stop) S.st.done = 1;
-        }
-        __syncthreads();
-    }
-    if (S.st.done && !S.st.finished) {
-        if (!S.st.have_best) {
-            if (tid == 0) {
-                if (S.st.status == IMLOC_OK) S.st.status = IMLOC_ERR_DEGENERATE;
-                for (int k = 0; k < 9; ++k) S.R[k] = (k % 4 == 0) ? 1.0 : 0.0;
-                for (int k = 0; k < 3; ++k) S.t[k] = 0.0;
-                if (rank == 0) write_result(S, d, 0);
-                S.st.finished = 1;
-            }
-            __syncthreads();
-        } else {
-            if (tid == 0) {
-                for (int k = 0; k < 9; ++k) S.R[k] = S.st.R[k];
-                for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
-            }
-            __syncthreads();
-            if (d.final_iters > 0) gauss_newton<kFinInit, kFin, ACC>(S, d, cluster, rank, CL, slot, d.final_iters);
-            if (tid == 0) set_pass_pose(S, S.R, S.t);
-            __syncthreads();
-            pass<kCountFull>(S, d, cluster, rank, CL, slot);
-            if (tid == 0) {
-                if (rank == 0) write_result(S, d, static_cast<int64_t>(S.tot[28]));
-                S.st.finished = 1;
-            }
-            __syncthreads();
-        }
-    }
-    if (rank == 0 && tid == 0) p.qs[q] = S.st;
-    // no CTA may leave while another can still read its shared memory
-    cluster.sync();
 }
 
 // ============================================================================
@@ -1060,14 +1112,16 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         prof.end();
     }
     {
-        TilesParams tp{b.d_qs, b.d_nhyp, b.d_tiles, b.d_counter, nq, kTileHyps};
+        TilesParams tp{b.d_qs, b.d_nhyp, b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1, b.d_counter, nq,
+                       kTileHyps};
         ProfScope prof(ctx, stream, "k_tiles");
         k_tiles<<<1, 1024, 0, stream>>>(tp);
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
     }
     const size_t score_smem = score_smem_bytes(want_counts);
-    ScoreParams scp{b.d_qd, b.d_qs, b.d_wq, b.d_nhyp, b.d_tiles, b.d_counter, nq, ctx->d_err};
+    ScoreParams scp{b.d_qd,       b.d_qs,      b.d_wq, b.d_nhyp,   b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1,
+                    b.d_counter, nq,          ctx->d_err};
     const int64_t max_items = std::max<int64_t>(1, (total_samples * 4 + kTileHyps - 1) / kTileHyps + nq);
     // autotune the score kernel variant once per context on a large enough wave
     if (ctx->score_variant < 0 && (max_items >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
@@ -1075,7 +1129,10 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         if (rc != IMLOC_OK) return rc;
     }
     const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
-    auto score_kernel = want_counts ? V.fn_count : V.fn;
+    // the fused kernel scores and replays each query when its last item is done;
+    // IMLOC_NO_FUSE=1 runs the scoring alone followed by the replay kernel
+    const bool fuse = !getenv("IMLOC_NO_FUSE");
+    auto score_kernel = fuse ? (want_counts ? V.fused_count : V.fused) : (want_counts ? V.fn_count : V.fn);
     int n_clusters = 0;
     rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
     if (rc != IMLOC_OK) return rc;
@@ -1090,14 +1147,19 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
     {
         const int cl = replay_cluster_size(ctx, nq);
         ReplayParams rp{b.d_qd, b.d_qs, b.d_wq, ctx->d_err};
-        ProfScope prof(ctx, stream, "k_replay");
-        rc = launch_cluster(k_replay<float>, rp, nq * cl, kRT, 0, cl, stream);
-        if (rc != IMLOC_OK) return rc;
-        if (b.any_fp64) {
-            rc = launch_cluster(k_replay<double>, rp, nq * cl, kRT, 0, cl, stream);
-            if (rc != IMLOC_OK) return rc;
+        // queries with FP64 accumulation replay in their own kernel after the scoring
+        if (!fuse || b.any_fp64) {
+            ProfScope prof(ctx, stream, "k_replay");
+            if (!fuse) {
+                rc = launch_cluster(k_replay<float>, rp, nq * cl, kRT, 0, cl, stream);
+                if (rc != IMLOC_OK) return rc;
+            }
+            if (b.any_fp64) {
+                rc = launch_cluster(k_replay<double>, rp, nq * cl, kRT, 0, cl, stream);
+                if (rc != IMLOC_OK) return rc;
+            }
+            prof.end();
         }
-        prof.end();
     }
     return IMLOC_OK;
 }
@@ -1234,7 +1296,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     char* d_blk = static_cast<char*>(ws_alloc(ctx, qd_bytes + wq_bytes + wp_bytes + 512));
     QueryState* d_qs = static_cast<QueryState*>(ws_alloc(ctx, sizeof(QueryState) * nq));
     int32_t* d_nhyp = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * W * nq));
-    int32_t* d_tiles = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * (nq + 1)));
+    int32_t* d_tiles = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * (3 * nq + 1)));
     uint32_t* d_counter = static_cast<uint32_t*>(ws_alloc(ctx, sizeof(uint32_t)));
     if (!h_blk || !d_blk || !d_qs || !d_nhyp || !d_tiles || !d_counter) return IMLOC_ERR_OOM;
     const size_t o_wq = align_up(qd_bytes, 256), o_wp = align_up(o_wq + wq_bytes, 256);
@@ -1269,7 +1331,8 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     std::string key;
     if (use_graph) {
         char buf[160];
-        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
+        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
+                 int(getenv("IMLOC_NO_FUSE") != nullptr),
                  (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
         key = buf;
         for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);

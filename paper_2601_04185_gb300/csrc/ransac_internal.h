@@ -23,7 +23,7 @@ struct StepBuffers {
     const WaveQ* d_wq;     // [nq] this step
     const int64_t* d_prefix;  // [nq + 1] flattened sample offsets of this step
     int32_t* d_nhyp;       // [nq] valid poses of this step (zero before the step)
-    int32_t* d_tiles;      // [nq + 1]
+    int32_t* d_tiles;      // [3 nq + 1]: item prefix, pose tiles, completed items
     uint32_t* d_counter;   // work queue counter
     int32_t* d_nhyp_all;   // zeroed by the setup kernel (may be null)
     int32_t nhyp_all_len;

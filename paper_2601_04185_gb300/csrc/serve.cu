@@ -433,7 +433,7 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
     ok = ok && cudaMalloc(&S->d_wq, sizeof(imloc::WaveQ) * ns) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_prefix, sizeof(int64_t) * (ns + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_nhyp, sizeof(int32_t) * ns) == cudaSuccess;
-    ok = ok && cudaMalloc(&S->d_tiles, sizeof(int32_t) * (ns + 1)) == cudaSuccess;
+    ok = ok && cudaMalloc(&S->d_tiles, sizeof(int32_t) * (3 * ns + 1)) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_counter, sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_init, sizeof(int32_t) * ns) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_res, sizeof(imloc_result) * ns) == cudaSuccess;
