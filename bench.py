@@ -774,13 +774,13 @@ def run_ours(args):
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
                      "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
                      "launch_ms": score_launch_ms,
-                     "note": "k_score is fused: each query's replay (LO, termination, Cauchy refinement) runs inside "
-                             "it once the query's last pose tile is scored; launch_ms includes those replays"},
+                     "note": "batches of >= 32 queries run k_score fused (each query's replay inside it once its "
+                             "last pose tile is scored); this 16-query step runs scoring and replay as two kernels"},
         "roofline_score_only": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                                 "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
                                 "launch_ms": score_only_ms, "replay_kernel_ms": kstats_unfused.get("k_replay", (1, 0))[1]
                                 / max(1, kstats_unfused.get("k_replay", (1, 0))[0]),
-                                "note": "same steps with the replay in its own kernel (IMLOC_NO_FUSE=1)"},
+                                "note": "scoring kernel alone, replay in its own kernel (IMLOC_NO_FUSE=1)"},
         "lift_in_step": {"bound": "hbm", "achieved": lift_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (lift_gbs / hbm_peak) if lift_gbs else None, "bytes_per_launch": lift_bytes,
                          "launch_ms": lift_ms, "note": "16-query step: 800k matches, latency-bound"},

@@ -187,11 +187,14 @@ struct QueryState {
 }  // namespace imloc
 
 // host-side error check helper
+// On failure: record the call, clear the runtime's last-error state (so that a
+// later, unrelated call does not report it again) and return IMLOC_ERR_CUDA.
 #define IMLOC_CUDA_TRY(expr)                                  \
     do {                                                      \
         cudaError_t _e = (expr);                              \
         if (_e != cudaSuccess) {                              \
             imloc::record_cuda_error(_e, #expr, __FILE__, __LINE__); \
+            cudaGetLastError();                               \
             return IMLOC_ERR_CUDA;                            \
         }                                                     \
     } while (0)

@@ -34,6 +34,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1029,8 +1031,25 @@ static int launch_cluster(K kernel, const P& params, int grid, int block, size_t
     return IMLOC_OK;
 }
 
+// Dynamic shared memory beyond the 48 KB default needs the function's opt-in.
+template <typename K>
+static int allow_smem(K kernel, size_t smem) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> done;  // largest size already allowed per kernel
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = done.find(reinterpret_cast<const void*>(kernel));
+    if (it != done.end() && it->second >= smem) return IMLOC_OK;
+    IMLOC_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    done[reinterpret_cast<const void*>(kernel)] = smem;
+    return IMLOC_OK;
+}
+
 template <typename K>
 static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out) {
+    if (smem > 0) {
+        const int rc = allow_smem(kernel, smem);
+        if (rc != IMLOC_OK) return rc;
+    }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cluster * 64);
     cfg.blockDim = dim3(block);
@@ -1129,9 +1148,11 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         if (rc != IMLOC_OK) return rc;
     }
     const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
-    // the fused kernel scores and replays each query when its last item is done;
-    // IMLOC_NO_FUSE=1 runs the scoring alone followed by the replay kernel
-    const bool fuse = !getenv("IMLOC_NO_FUSE");
+    // the fused kernel scores and replays each query when its last item is done
+    // (replays overlap the scoring of later queries: worth it with many
+    // queries); otherwise the scoring runs alone, followed by the replay kernel.
+    // IMLOC_FUSE=1 / IMLOC_NO_FUSE=1 force either form.
+    const bool fuse = getenv("IMLOC_NO_FUSE") ? false : (getenv("IMLOC_FUSE") ? true : b.fuse);
     auto score_kernel = fuse ? (want_counts ? V.fused_count : V.fused) : (want_counts ? V.fn_count : V.fn);
     int n_clusters = 0;
     rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
@@ -1332,7 +1353,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     if (use_graph) {
         char buf[160];
         snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
-                 int(getenv("IMLOC_NO_FUSE") != nullptr),
+                 int(getenv("IMLOC_NO_FUSE") != nullptr) + 2 * int(getenv("IMLOC_FUSE") != nullptr),
                  (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
         key = buf;
         for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);
@@ -1361,6 +1382,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.d_init = nullptr;
         sb.any_fp64 = false;
         for (int q = 0; q < nq; ++q) sb.any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
+        sb.fuse = nq >= 32;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
             if (capturing) {

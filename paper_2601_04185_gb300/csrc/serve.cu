@@ -333,6 +333,7 @@ static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted)
     b.nhyp_all_len = 0;
     b.d_init = S->d_init;
     b.any_fp64 = false;
+    b.fuse = true;  // one launch less per step, replays overlap the other queries' scoring
     for (int s = 0; s < ns; ++s)
         if (S->slots[s] && S->slots[s]->opts.lo_fp64_accumulate) b.any_fp64 = true;
     int rc = run_step(S->ictx, b, ns, n_init, total, false, st);
