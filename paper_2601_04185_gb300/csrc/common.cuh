@@ -114,11 +114,48 @@ __device__ __forceinline__ int warp_sum_i(int v) {
     return v;
 }
 
-// ---- scoring record of one subset correspondence (32 B, TMA friendly) ------
-struct __align__(16) ScoreCorr {
-    float X, Y, Z, w;   // world point, confidence
-    float x, y, p0, p1; // observed query pixel, padding
+// ---- scoring records: subset correspondences 2k and 2k+1 interleaved -------
+// (48 B, TMA friendly): every field is a float pair, so that one packed
+// f32x2 instruction evaluates a pose on both records.  The observed pixel is
+// stored negated (the residual is an FMA with it).  An odd subset ends with
+// a zero-weight record.
+struct __align__(16) ScorePair {
+    float X[2], Y[2], Z[2], w[2];  // world points, confidences
+    float nx[2], ny[2];            // -observed query pixel
 };
+
+struct SubsetRecord {
+    float X, Y, Z, w, x, y;
+};
+
+__device__ __forceinline__ SubsetRecord subset_record(const ScorePair* s, int64_t i) {
+    const ScorePair& p = s[i >> 1];
+    const int l = static_cast<int>(i & 1);
+    SubsetRecord r;
+    r.X = p.X[l]; r.Y = p.Y[l]; r.Z = p.Z[l]; r.w = p.w[l];
+    r.x = -p.nx[l]; r.y = -p.ny[l];
+    return r;
+}
+
+// ---- packed FP32 pairs (fma/mul .f32x2: two IEEE FP32 operations per lane) --
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
 
 // ---- hypothesis pose slot: rotation (row-major) + translation, float32 ------
 struct __align__(16) PoseF {
@@ -149,7 +186,7 @@ struct QueryDesc {
     uint32_t query_id;
     int32_t n_cap;          // capacity bound of N (mask / fixed-set buffer)
     // workspace
-    ScoreCorr* subset;      // m_cap
+    ScorePair* subset;      // (m_cap + 1) / 2 record pairs
     PoseF* slots;           // wave_samples * 4
     int32_t* compact;       // wave_samples * 4 pose ids (valid poses of the wave)
     uint64_t* round_best;   // rounds: (score bits << 32) | pose id, min-reduced

@@ -32,6 +32,8 @@ struct imloc_ctx {
     // autotuned score-kernel variant (-1: not tuned yet)
     int score_variant = -1;
     float score_variant_ms = 0.f;
+    // co-resident clusters of the replay kernel (FP32 / FP64 accumulation x cluster size 8, 4, 2, 1); 0 = not queried
+    int replay_occ[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
     // tracing: CUDA events around every kernel launch while enabled
     bool prof_on = false;
     struct ProfRec { const char* name; cudaEvent_t a, b; };

@@ -14,20 +14,22 @@
 //
 // Kernels (in launch order per wave):
 //   k_setup        per query: N, subset size M, uniform-stride subset gather
-//                  into 32-byte records, reset of the per-round reductions
+//                  into 48-byte record pairs, reset of the per-round reductions
 //   k_sample_p3p   one minimal sample per thread: Philox triple, bearings,
 //                  P3P (FP32 + FP64 Newton polish), pose slots, compact list
 //   k_tiles        per-query hypothesis-tile prefix for the work queue
 //   k_score        persistent, cluster-split: a cluster takes a (query,
 //                  hypothesis tile) from the queue; each CTA of the cluster
-//                  streams its share of the subset through shared memory
-//                  with bulk (TMA) copies and scores 4 poses per thread in
-//                  registers; partial sums are combined across the cluster
+//                  keeps its share of the subset resident in shared memory
+//                  (bulk copies) and scores HT poses per thread in registers
+//                  against two records per packed f32x2 instruction; partial
+//                  sums are combined across the cluster
 //                  through distributed shared memory; per round, the best
 //                  (score, pose id) is kept by a 64-bit atomic minimum
 //   k_replay       per query (one cluster): rounds in order, LO by
 //                  Gauss-Newton on SE(3) (cluster-reduced normal equations,
-//                  FP64 6x6 Cholesky), termination, final Cauchy IRLS.
+//                  Jacobi-scaled 6x6 Cholesky), termination, final Cauchy
+//                  IRLS.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -59,8 +61,11 @@ struct SetupParams {
     const int32_t* init_list; // if non-null: block b sets up query init_list[b]
 };
 
+constexpr int kSetupBlocks = 8;  // CTAs per query: they split the subset gather
+
 __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupParams p) {
-    const int q = p.init_list ? p.init_list[blockIdx.x] : blockIdx.x;
+    const int qi = blockIdx.x / kSetupBlocks, g = blockIdx.x % kSetupBlocks;
+    const int q = p.init_list ? p.init_list[qi] : qi;
     const QueryDesc& d = p.qd[q];
     __shared__ int64_t s_off, s_n;
     __shared__ int32_t s_m;
@@ -92,7 +97,7 @@ __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupPara
             st.done = 1;
             if (st.status == IMLOC_OK) st.status = IMLOC_ERR_DEGENERATE;
         }
-        p.qs[q] = st;
+        if (g == 0) p.qs[q] = st;
         s_off = off;
         s_n = n;
         s_m = m;
@@ -100,18 +105,33 @@ __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupPara
     if (p.n_hyp_all)
         for (int i = blockIdx.x * 256 + threadIdx.x; i < p.n_hyp_len; i += gridDim.x * 256) p.n_hyp_all[i] = 0;
     __syncthreads();
-    for (int r = threadIdx.x; r < d.rounds; r += 256) {
-        d.round_best[r] = ~0ull;
-        d.round_hyps[r] = 0;
-    }
+    if (g == 0)
+        for (int r = threadIdx.x; r < d.rounds; r += 256) {
+            d.round_best[r] = ~0ull;
+            d.round_hyps[r] = 0;
+        }
     const int64_t off = s_off, n = s_n;
     const int32_t m = s_m;
-    for (int k = threadIdx.x; k < m; k += 256) {
-        const int64_t i = off + (static_cast<int64_t>(k) * n) / m;  // uniform stride, exact in 64-bit
-        ScoreCorr r;
-        r.X = d.X[i]; r.Y = d.Y[i]; r.Z = d.Z[i]; r.w = d.w[i];
-        r.x = d.x[i]; r.y = d.y[i]; r.p0 = 0.f; r.p1 = 0.f;
-        d.subset[k] = r;
+    // record pair k2 = subset records 2 k2 and 2 k2 + 1 (uniform stride, exact in 64-bit)
+    const int m2 = (m + 1) >> 1;
+    for (int k2 = g * 256 + threadIdx.x; k2 < m2; k2 += kSetupBlocks * 256) {
+        float v[12];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            const int k = 2 * k2 + l;
+            if (k < m) {
+                const int64_t i = off + (static_cast<int64_t>(k) * n) / m;
+                v[0 + l] = __ldg(d.X + i); v[2 + l] = __ldg(d.Y + i); v[4 + l] = __ldg(d.Z + i);
+                v[6 + l] = __ldg(d.w + i); v[8 + l] = -__ldg(d.x + i); v[10 + l] = -__ldg(d.y + i);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) v[2 * c + l] = 0.f;
+            }
+        }
+        float4* dst = reinterpret_cast<float4*>(d.subset + k2);
+        dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+        dst[1] = make_float4(v[4], v[5], v[6], v[7]);
+        dst[2] = make_float4(v[8], v[9], v[10], v[11]);
     }
 }
 
@@ -191,7 +211,7 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                 const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    const ScoreCorr c = d.subset[idx[k]];
+                    const SubsetRecord c = subset_record(d.subset, idx[k]);
                     const float bx = (c.x - d.cx) * ifx, by = (c.y - d.cy) * ify;
                     const float inv = rsqrtf(bx * bx + by * by + 1.0f);
                     y[k][0] = bx * inv; y[k][1] = by * inv; y[k][2] = inv;
@@ -303,24 +323,43 @@ __global__ void __launch_bounds__(1024) k_tiles(const __grid_constant__ TilesPar
 // ============================================================================
 // k_replay: rounds in order, LO, termination, final refinement
 // ============================================================================
-constexpr int kRT = 256;             // threads per CTA of the stand-alone replay kernel
+// threads per CTA of the stand-alone replay kernel: FP32 accumulation fits
+// 128 registers (4 warps per scheduler), FP64 accumulation needs more
+template <typename ACC>
+__host__ __device__ constexpr int replay_threads() { return sizeof(ACC) == 4 ? 512 : 256; }
 constexpr int kMaxReplayThreads = 512;
 constexpr int kMaxReplayCluster = 8;
-constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
+constexpr int kNV = 30;  // H (21, upper triangle), g (6), cost, count, inliers at the pass pose
+constexpr int kPassUnroll = 4;   // correspondences whose loads are in flight together per thread
+constexpr int kKeyCache = 64;    // round minima staged in shared memory at a time
 
 enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
 
+// The serial part of the replay (normal-equation solve, pose update, pose
+// conversions) sits on the critical path of every Gauss-Newton step.  FP64
+// instructions are slow on this part and cost the same for one lane as for
+// 32, so the FP64 pose arithmetic is spread over the lanes of warp 0 (one
+// output entry per lane) and the 6x6 solve runs in FP32 on a Jacobi-scaled
+// system: only the step direction depends on it, the fixed point of the
+// iteration (zero gradient, FP64 sums) does not.
 struct ReplaySmem {
     double R[9], t[3];    // current pose
     double Rc[9], tc[3];  // candidate pose
-    double H[21], g[6];   // normal equations at the current pose
-    double cost, cnt;
-    double step, decrease, prev_cost;
+    double cost, cnt, cnt_all;
+    double decrease, prev_cost;
+    double need;          // iterations needed by the termination rule at the current inlier ratio
     double tot[32];
     double xch[2][32];
     double red[kMaxReplayThreads / 32][32];
+    uint64_t rkey[kKeyCache];
+    int32_t rhyps[kKeyCache];
+    float Hf[21], gf[6];  // normal equations at the current pose (FP32 copy for the solve)
+    float totf[27];
+    float dl[6];          // step of the last solve
+    float step2;          // its squared norm
     float P[12];
     int flag;
+    int skip;             // rounds passed over by the last scan
     QueryState st;
 };
 
@@ -331,9 +370,10 @@ struct ReplayParams {
     int* err;
 };
 
-__device__ __forceinline__ void set_pass_pose(ReplaySmem& S, const double R[9], const double t[3]) {
-    for (int k = 0; k < 9; ++k) S.P[k] = static_cast<float>(R[k]);
-    for (int k = 0; k < 3; ++k) S.P[9 + k] = static_cast<float>(t[k]);
+// warp 0: pass pose <- (R, t) in float32 (lane l converts entry l)
+__device__ __forceinline__ void pass_pose_warp(ReplaySmem& S, const double* R, const double* t) {
+    const int l = threadIdx.x & 31;
+    if (l < 12) S.P[l] = static_cast<float>(l < 9 ? R[l] : t[l - 9]);
 }
 
 template <int MODE, typename ACC, int NT>
@@ -342,6 +382,7 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     if (tid == 0) ++S.st.passes;
     constexpr bool kSub = (MODE == kLO || MODE == kCountSub);
     constexpr bool kJac = (MODE == kLO || MODE == kFinInit || MODE == kFin);
+    constexpr int U = kPassUnroll;
     ACC acc[kNV];
 #pragma unroll
     for (int k = 0; k < kNV; ++k) acc[k] = ACC(0);
@@ -351,65 +392,85 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
 #pragma unroll
     for (int k = 0; k < 3; ++k) tv[k] = S.P[9 + k];
     const float fx = d.fx, fy = d.fy, cx = d.cx, cy = d.cy, tau2 = d.tau2, c2 = d.cauchy2;
+    const float ic2 = 1.0f / c2;
     const int64_t n = kSub ? S.st.m : S.st.n;
     const int64_t off = S.st.off;
-    for (int64_t i = static_cast<int64_t>(rank) * NT + tid; i < n; i += static_cast<int64_t>(CL) * NT) {
-        float X, Y, Z, w, x, y;
-        if (kSub) {
-            const float4* rec = reinterpret_cast<const float4*>(d.subset + i);
-            const float4 A = rec[0], B = rec[1];
-            X = A.x; Y = A.y; Z = A.z; w = A.w; x = B.x; y = B.y;
-        } else {
-            X = d.X[off + i]; Y = d.Y[off + i]; Z = d.Z[off + i]; w = d.w[off + i];
-            x = d.x[off + i]; y = d.y[off + i];
+    const int64_t stride = static_cast<int64_t>(CL) * NT;
+    // thread order of the points: i0, i0 + stride, i0 + 2 stride, ... (the loads
+    // of U consecutive ones are issued before any of them is used)
+    for (int64_t i0 = static_cast<int64_t>(rank) * NT + tid; i0 < n; i0 += U * stride) {
+        float X[U], Y[U], Z[U], w[U], x[U], y[U];
+        bool fixed_in[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            X[u] = Y[u] = Z[u] = w[u] = x[u] = y[u] = 0.f;
+            fixed_in[u] = false;
+            if (i < n) {
+                if (kSub) {
+                    const SubsetRecord c = subset_record(d.subset, i);
+                    X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
+                } else {
+                    X[u] = __ldg(d.X + off + i); Y[u] = __ldg(d.Y + off + i); Z[u] = __ldg(d.Z + off + i);
+                    w[u] = __ldg(d.w + off + i); x[u] = __ldg(d.x + off + i); y[u] = __ldg(d.y + off + i);
+                    // written by this thread in the kFinInit pass: a coherent load
+                    if (MODE == kFin) fixed_in[u] = d.fixed[off + i] != 0;
+                }
+            }
         }
-        const float xc = fmaf(Rm[0], X, fmaf(Rm[1], Y, fmaf(Rm[2], Z, tv[0])));
-        const float yc = fmaf(Rm[3], X, fmaf(Rm[4], Y, fmaf(Rm[5], Z, tv[1])));
-        const float zc = fmaf(Rm[6], X, fmaf(Rm[7], Y, fmaf(Rm[8], Z, tv[2])));
-        const bool front = zc > 0.f;
-        float iz = 0.f, ru = 0.f, rv = 0.f, r2 = tau2;
-        if (front) {
-            iz = 1.0f / zc;
-            ru = fmaf(fx * xc, iz, cx) - x;
-            rv = fmaf(fy * yc, iz, cy) - y;
-            r2 = fmaf(ru, ru, rv * rv);
-        }
-        const bool inl = front && r2 < tau2;
-        float wt = 0.f;
-        if (MODE == kLO) {
-            acc[27] += w * (inl ? r2 : tau2);
-            wt = inl ? w : 0.f;
-            acc[28] += inl ? 1.f : 0.f;
-        } else if (MODE == kCountSub || MODE == kCountFull) {
-            acc[28] += inl ? 1.f : 0.f;
-            if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
-        } else {
-            bool in_set;
-            if (MODE == kFinInit) {
-                in_set = inl;
-                d.fixed[off + i] = inl ? 1 : 0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = i0 + u * stride;
+            if (i >= n) break;
+            const float xc = fmaf(Rm[0], X[u], fmaf(Rm[1], Y[u], fmaf(Rm[2], Z[u], tv[0])));
+            const float yc = fmaf(Rm[3], X[u], fmaf(Rm[4], Y[u], fmaf(Rm[5], Z[u], tv[1])));
+            const float zc = fmaf(Rm[6], X[u], fmaf(Rm[7], Y[u], fmaf(Rm[8], Z[u], tv[2])));
+            const bool front = zc > 0.f;
+            float iz = 0.f, ru = 0.f, rv = 0.f, r2 = tau2;
+            if (front) {
+                iz = rcp_approx(zc);
+                ru = fmaf(fx * xc, iz, cx) - x[u];
+                rv = fmaf(fy * yc, iz, cy) - y[u];
+                r2 = fmaf(ru, ru, rv * rv);
+            }
+            const bool inl = front && r2 < tau2;
+            float wt = 0.f;
+            if (MODE == kLO) {
+                acc[27] += w[u] * (inl ? r2 : tau2);
+                wt = inl ? w[u] : 0.f;
+                acc[28] += inl ? 1.f : 0.f;
+            } else if (MODE == kCountSub || MODE == kCountFull) {
+                acc[28] += inl ? 1.f : 0.f;
+                if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
             } else {
-                in_set = d.fixed[off + i] != 0;
+                bool in_set;
+                if (MODE == kFinInit) {
+                    in_set = inl;
+                    d.fixed[off + i] = inl ? 1 : 0;
+                } else {
+                    in_set = fixed_in[u];
+                }
+                acc[29] += inl ? 1.f : 0.f;
+                if (in_set) {
+                    const float rr = front ? r2 : tau2;
+                    acc[27] += w[u] * c2 * log1pf(rr * ic2);
+                    acc[28] += 1.f;
+                    wt = front ? w[u] * rcp_approx(fmaf(r2, ic2, 1.0f)) : 0.f;
+                }
             }
-            if (in_set) {
-                const float rr = front ? r2 : tau2;
-                acc[27] += w * c2 * log1pf(rr / c2);
-                acc[28] += 1.f;
-                wt = front ? w / (1.0f + r2 / c2) : 0.f;
-            }
-        }
-        if (kJac && wt > 0.f) {
-            const float dux = fx * iz, duz = -fx * xc * iz * iz;
-            const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
-            const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
-            const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
-            int k = 0;
+            if (kJac && wt > 0.f) {
+                const float dux = fx * iz, duz = -fx * xc * iz * iz;
+                const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
+                const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
+                const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
+                int k = 0;
 #pragma unroll
-            for (int a = 0; a < 6; ++a) {
-                const float wa = wt * Ju[a], wb = wt * Jv[a];
+                for (int a = 0; a < 6; ++a) {
+                    const float wa = wt * Ju[a], wb = wt * Jv[a];
 #pragma unroll
-                for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
-                acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
+                    for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
+                    acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
+                }
             }
         }
     }
@@ -447,68 +508,112 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
 #pragma unroll
         for (int r = 0; r < kMaxReplayCluster; ++r) sum += part[r];
         S.tot[tid] = sum;
+        if (tid < 27) S.totf[tid] = static_cast<float>(sum);
     }
     slot ^= 1;
     __syncthreads();
 }
 
-__device__ __forceinline__ bool solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
-    double A[6][6];
+// (H + mu diag H) x = -g for the 6x6 normal equations (H packed upper
+// triangle), in FP32 after Jacobi scaling D = diag(H)^(-1/2): the scaled
+// matrix has the diagonal 1 + mu.  Cholesky with the scaled system; returns
+// false if H is not positive definite.
+__device__ __forceinline__ bool solve6f(const float Hu[21], const float g[6], float mu, float x[6], float* dn) {
+    float A[6][6], s[6];
     int k = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int b = a; b < 6; ++b) {
-            A[a][b] = Hu[k];
-            A[b][a] = Hu[k];
-            ++k;
-        }
+        for (int b = a; b < 6; ++b) A[a][b] = Hu[k++];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) A[a][a] += mu * A[a][a];
-    // Cholesky A = L L^T (L overwrites the lower triangle of A); inv[j] = 1 / L_jj
-    double inv[6];
+    for (int a = 0; a < 6; ++a) {
+        if (!(A[a][a] > 0.f)) return false;
+        s[a] = rsqrtf(A[a][a]);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+        A[a][a] = 1.0f + mu;
+#pragma unroll
+        for (int b = a + 1; b < 6; ++b) {
+            A[a][b] *= s[a] * s[b];
+            A[b][a] = A[a][b];
+        }
+    }
+    float inv[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            double s = A[i][j];
+            float v = A[i][j];
 #pragma unroll
-            for (int c = 0; c < j; ++c) s -= A[i][c] * A[j][c];
+            for (int c = 0; c < j; ++c) v = fmaf(-A[i][c], A[j][c], v);
             if (i == j) {
-                if (!(s > 0.0)) return false;
-                inv[i] = rsqrt(s);
-                A[i][i] = s * inv[i];
+                if (!(v > 0.f)) return false;
+                inv[i] = rsqrtf(v);
+                A[i][i] = v * inv[i];
             } else {
-                A[i][j] = s * inv[j];
+                A[i][j] = v * inv[j];
             }
         }
     }
-    double z[6];
+    float z[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        double s = -g[i];
+        float v = -g[i] * s[i];
 #pragma unroll
-        for (int c = 0; c < i; ++c) s -= A[i][c] * z[c];
-        z[i] = s * inv[i];
+        for (int c = 0; c < i; ++c) v = fmaf(-A[i][c], z[c], v);
+        z[i] = v * inv[i];
     }
+    float y[6];
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        double s = z[i];
+        float v = z[i];
 #pragma unroll
-        for (int c = i + 1; c < 6; ++c) s -= A[c][i] * x[c];
-        x[i] = s * inv[i];
+        for (int c = i + 1; c < 6; ++c) v = fmaf(-A[c][i], y[c], v);
+        y[i] = v * inv[i];
     }
+    float n2 = 0.f;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        x[i] = y[i] * s[i];
+        n2 = fmaf(x[i], x[i], n2);
+    }
+    *dn = n2;
     return true;
 }
 
-// candidate = Exp(dw) * (R, t) + (0, dv)
-__device__ void apply_step(const double R[9], const double t[3], const double dl[6], double Rc[9], double tc[3]) {
-    const double th2 = dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2];
+// warp 0: candidate (Rc, tc) = Exp(dw) (R, t) + (0, dv) for the step (dw, dv)
+// in S.dl, and the pass pose.  Lane l < 9 computes Rc[l], lanes 9..11 tc.
+// Exp(dw) = I + A [dw]x + B (dw dw^T - |dw|^2 I), A = sin(th)/th,
+// B = (1 - cos(th))/th^2 (Rodrigues), by their Taylor series for th < 0.5
+// (remainder < 5e-20) and sincos beyond.
+__device__ void apply_step_warp(ReplaySmem& S) {
+    const int l = threadIdx.x & 31;
+    if (l >= 12) return;
+    const double w0 = S.dl[0], w1 = S.dl[1], w2 = S.dl[2];
+    const double th2 = w0 * w0 + w1 * w1 + w2 * w2;
     double A, B;
     if (th2 < 1e-4) {
-        // sin(th)/th and (1 - cos(th))/th^2 by their Taylor series (error < th^8/9! < 1e-21 here)
         A = 1.0 - th2 * (1.0 / 6.0) * (1.0 - th2 * (1.0 / 20.0) * (1.0 - th2 * (1.0 / 42.0)));
         B = 0.5 - th2 * (1.0 / 24.0) * (1.0 - th2 * (1.0 / 30.0) * (1.0 - th2 * (1.0 / 56.0)));
+    } else if (th2 < 0.25) {
+        // A = sum_k (-th2)^k / (2k+1)!, B = sum_k (-th2)^k / (2k+2)!, k < 8
+        A = 1.0 / 1307674368000.0;  // 1/15!
+        B = 1.0 / 20922789888000.0; // 1/16!
+        A = 1.0 / 6227020800.0 - th2 * A;  // 1/13!
+        B = 1.0 / 87178291200.0 - th2 * B; // 1/14!
+        A = 1.0 / 39916800.0 - th2 * A;    // 1/11!
+        B = 1.0 / 479001600.0 - th2 * B;   // 1/12!
+        A = 1.0 / 362880.0 - th2 * A;      // 1/9!
+        B = 1.0 / 3628800.0 - th2 * B;     // 1/10!
+        A = 1.0 / 5040.0 - th2 * A;
+        B = 1.0 / 40320.0 - th2 * B;
+        A = 1.0 / 120.0 - th2 * A;
+        B = 1.0 / 720.0 - th2 * B;
+        A = 1.0 / 6.0 - th2 * A;
+        B = 1.0 / 24.0 - th2 * B;
+        A = 1.0 - th2 * A;
+        B = 0.5 - th2 * B;
     } else {
         const double th = sqrt(th2);
         double sn, cs;
@@ -516,25 +621,51 @@ __device__ void apply_step(const double R[9], const double t[3], const double dl
         A = sn / th;
         B = (1.0 - cs) / th2;
     }
-    const double Kx[9] = {0, -dl[2], dl[1], dl[2], 0, -dl[0], -dl[1], dl[0], 0};
-    double E[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            double k2 = 0.0;
-            for (int c = 0; c < 3; ++c) k2 += Kx[3 * i + c] * Kx[3 * c + j];
-            E[3 * i + j] = (i == j ? 1.0 : 0.0) + A * Kx[3 * i + j] + B * k2;
-        }
-    for (int i = 0; i < 3; ++i) {
-        for (int j = 0; j < 3; ++j) Rc[3 * i + j] = E[3 * i] * R[j] + E[3 * i + 1] * R[3 + j] + E[3 * i + 2] * R[6 + j];
-        tc[i] = E[3 * i] * t[0] + E[3 * i + 1] * t[1] + E[3 * i + 2] * t[2] + dl[3 + i];
+    const int i = l < 9 ? l / 3 : l - 9;
+    const double wi = i == 0 ? w0 : (i == 1 ? w1 : w2);
+    // row i of [dw]x
+    const double k0 = i == 0 ? 0.0 : (i == 1 ? w2 : -w1);
+    const double k1 = i == 0 ? -w2 : (i == 1 ? 0.0 : w0);
+    const double k2 = i == 0 ? w1 : (i == 1 ? -w0 : 0.0);
+    const double c0 = 1.0 - B * th2, bw = B * wi;
+    const double e0 = fma(bw, w0, fma(A, k0, i == 0 ? c0 : 0.0));
+    const double e1 = fma(bw, w1, fma(A, k1, i == 1 ? c0 : 0.0));
+    const double e2 = fma(bw, w2, fma(A, k2, i == 2 ? c0 : 0.0));
+    double out;
+    if (l < 9) {
+        const int j = l - 3 * i;
+        out = fma(e0, S.R[j], fma(e1, S.R[3 + j], e2 * S.R[6 + j]));
+        S.Rc[l] = out;
+    } else {
+        out = fma(e0, S.t[0], fma(e1, S.t[1], fma(e2, S.t[2], static_cast<double>(S.dl[3 + i]))));
+        S.tc[i] = out;
     }
+    S.P[l] = static_cast<float>(out);
+}
+
+// warp 0: R <- R (3 I - R^T R) / 2 (Newton-Schulz step towards the nearest
+// rotation), lane l < 9 computes entry l; R in shared memory.
+__device__ void orthonormalize_warp(double* R) {
+    const int l = threadIdx.x & 31;
+    const int i = l < 9 ? l / 3 : 0, j = l < 9 ? l - 3 * i : 0;
+    // G = R^T R, entry (i, j) in lane 3i + j
+    const double g = fma(R[i], R[j], fma(R[3 + i], R[3 + j], R[6 + i] * R[6 + j]));
+    const double g0 = __shfl_sync(0xffffffffu, g, j);
+    const double g1 = __shfl_sync(0xffffffffu, g, 3 + j);
+    const double g2 = __shfl_sync(0xffffffffu, g, 6 + j);
+    const double m0 = (j == 0 ? 3.0 : 0.0) - g0, m1 = (j == 1 ? 3.0 : 0.0) - g1, m2 = (j == 2 ? 3.0 : 0.0) - g2;
+    const double v = 0.5 * fma(R[3 * i], m0, fma(R[3 * i + 1], m1, R[3 * i + 2] * m2));
+    __syncwarp();
+    if (l < 9) R[l] = v;
+    __syncwarp();
 }
 
 __device__ void take_totals(ReplaySmem& S) {
-    for (int k = 0; k < 21; ++k) S.H[k] = S.tot[k];
-    for (int k = 0; k < 6; ++k) S.g[k] = S.tot[21 + k];
+    for (int k = 0; k < 21; ++k) S.Hf[k] = S.totf[k];
+    for (int k = 0; k < 6; ++k) S.gf[k] = S.totf[21 + k];
     S.cost = S.tot[27];
     S.cnt = S.tot[28];
+    S.cnt_all = S.tot[29];
 }
 
 // Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
@@ -542,7 +673,7 @@ template <int INIT, int ITER, typename ACC, int NT>
 __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot,
                              int iters) {
     const int tid = threadIdx.x;
-    if (tid == 0) set_pass_pose(S, S.R, S.t);
+    if (tid < 32) pass_pose_warp(S, S.R, S.t);
     __syncthreads();
     pass<INIT, ACC, NT>(S, d, cluster, rank, CL, slot);
     if (tid == 0) take_totals(S);
@@ -550,21 +681,12 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
     for (int it = 0; it < iters; ++it) {
         if (S.cnt < 3.0) break;
         bool accepted = false;
-        double mu = 0.0;
+        float mu = 0.f;
         for (int attempt = 0; attempt < 4; ++attempt) {
-            if (tid == 0) {
-                double dl[6];
-                S.flag = solve6(S.H, S.g, mu, dl) ? 1 : 0;
-                if (S.flag) {
-                    apply_step(S.R, S.t, dl, S.Rc, S.tc);
-                    set_pass_pose(S, S.Rc, S.tc);
-                    double dn = 0.0;
-                    for (int k = 0; k < 6; ++k) dn += dl[k] * dl[k];
-                    S.step = sqrt(dn);
-                }
-            }
+            if (tid == 0) S.flag = solve6f(S.Hf, S.gf, mu, S.dl, &S.step2) ? 1 : 0;
             __syncthreads();
             const bool solved = S.flag != 0;
+            if (solved && tid < 32) apply_step_warp(S);
             __syncthreads();
             if (solved) {
                 pass<ITER, ACC, NT>(S, d, cluster, rank, CL, slot);
@@ -574,20 +696,22 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
                     if (tid == 0) {
                         S.decrease = S.cost - S.tot[27];
                         S.prev_cost = S.cost;
-                        for (int k = 0; k < 9; ++k) S.R[k] = S.Rc[k];
-                        for (int k = 0; k < 3; ++k) S.t[k] = S.tc[k];
                         take_totals(S);
+                    }
+                    if (tid < 12) {
+                        if (tid < 9) S.R[tid] = S.Rc[tid];
+                        else S.t[tid - 9] = S.tc[tid - 9];
                     }
                     __syncthreads();
                     accepted = true;
                     break;
                 }
             }
-            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
+            mu = (mu == 0.f) ? 1e-3f : mu * 10.f;
         }
         if (!accepted) break;
         // converged: a tiny step, or a step that lowered the cost by < 1e-6 of it
-        if (S.step < 1e-10 || S.decrease < 1e-6 * S.prev_cost) break;
+        if (S.step2 < 1e-20f || S.decrease < 1e-6 * S.prev_cost) break;
     }
 }
 
@@ -609,44 +733,121 @@ __device__ void write_result(ReplaySmem& S, const QueryDesc& d, int64_t num_inli
     if (d.result) *d.result = r;
 }
 
+// Iterations the termination rule needs at the current subset inlier ratio:
+// log(p_miss) / log(1 - eps^3) (INFINITY without a model or for eps = 0).
+__device__ double needed_iters(const QueryDesc& d, const QueryState& st) {
+    if (!(d.p_miss > 0.0) || !st.have_best || st.m <= 0) return INFINITY;
+    const double eps = static_cast<double>(st.subset_inliers) / static_cast<double>(st.m);
+    const double e3 = eps * eps * eps;
+    if (e3 >= 1.0) return 0.0;
+    if (e3 <= 0.0) return INFINITY;
+    return log(d.p_miss) / log(1.0 - e3);
+}
+
 // Rounds [r0, r1) of one query in order, LO, termination and, once done, the
 // final refinement, run by every CTA of one cluster (NT threads each) with
 // identical decisions.  Reads and writes the query's state in global memory.
+// Rounds whose minimum does not improve on the best score and that do not
+// end the search only advance the counters: warp 0 scans the staged round
+// minima 32 at a time for the next round that does either.
 template <typename ACC, int NT>
 __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, QueryState* qs, const WaveQ& wq,
                                           cg::cluster_group& cluster, int CL, int rank) {
+    static_assert(sizeof(QueryState) % 8 == 0, "state copied in 8-byte words");
+    constexpr int kWords = static_cast<int>(sizeof(QueryState) / 8);
     const int tid = threadIdx.x;
+    const int r_end = min(wq.r1, d.rounds);
+    int c0 = wq.r0, c1 = min(wq.r0 + kKeyCache, r_end);  // staged rounds [c0, c1)
     __syncthreads();
-    if (tid == 0) S.st = *qs;
+    for (int k = tid; k < kWords; k += NT)
+        reinterpret_cast<uint64_t*>(&S.st)[k] = reinterpret_cast<const uint64_t*>(qs)[k];
+    // the round minima (all final: the scoring of the wave is complete)
+    for (int k = tid; k < c1 - c0; k += NT) {
+        S.rkey[k] = d.round_best[c0 + k];
+        S.rhyps[k] = d.round_hyps[c0 + k];
+    }
+    __syncthreads();
+    if (tid == 0) S.need = needed_iters(d, S.st);
     // every CTA holds its copy of the state before rank 0 can write it back
     cluster.sync();
     if (S.st.finished) return;  // same decision in every CTA of the cluster
     int slot = 0;
-    const int r_end = min(wq.r1, d.rounds);
-    for (int r = wq.r0; r < r_end; ++r) {
-        if (S.st.done) break;
-        const uint64_t key = d.round_best[r];
-        const int hyps_r = d.round_hyps[r];
+    int r = wq.r0;
+    while (r < r_end && !S.st.done) {
+        if (r >= c1) {
+            __syncthreads();
+            c0 = r;
+            c1 = min(r + kKeyCache, r_end);
+            for (int k = tid; k < c1 - c0; k += NT) {
+                S.rkey[k] = d.round_best[c0 + k];
+                S.rhyps[k] = d.round_hyps[c0 + k];
+            }
+            __syncthreads();
+        }
+        if (tid < 32) {
+            // next event among the staged rounds: an improving minimum or a stop
+            int e = c1 - r;
+            for (int base = r; base < c1; base += 32) {
+                const int rr = base + tid;
+                bool ev = false;
+                if (rr < c1) {
+                    const uint64_t key = S.rkey[rr - c0];
+                    const bool imp = key != ~0ull &&
+                                     static_cast<double>(__uint_as_float(static_cast<uint32_t>(key >> 32))) <
+                                         S.st.best_score;
+                    const int64_t it = min(static_cast<int64_t>(rr + 1) * d.batch, static_cast<int64_t>(d.hyps));
+                    ev = imp || it >= d.hyps || static_cast<double>(it) >= S.need;
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ev);
+                if (m != 0u) {
+                    e = base + __ffs(m) - 1 - r;
+                    break;
+                }
+            }
+            long long hs = 0;
+            for (int k = tid; k < e; k += 32) hs += S.rhyps[r - c0 + k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hs += __shfl_xor_sync(0xffffffffu, hs, o);
+            if (tid == 0) {
+                if (e > 0) {
+                    S.st.hypotheses += hs;
+                    S.st.iters = min(static_cast<int64_t>(r + e) * d.batch, static_cast<int64_t>(d.hyps));
+                    S.st.rounds_done = r + e;
+                }
+                S.skip = e;
+            }
+        }
+        __syncthreads();
+        r += S.skip;
+        if (r >= c1) continue;
+        // round r: its minimum improves on the best score, or the search stops after it
+        const uint64_t key = S.rkey[r - c0];
+        const int hyps_r = S.rhyps[r - c0];
         bool improve = false;
         float sc = 0.f;
         if (key != ~0ull) {
             sc = __uint_as_float(static_cast<uint32_t>(key >> 32));
             improve = static_cast<double>(sc) < S.st.best_score;
         }
-        __syncthreads();
+        __syncthreads();  // every thread has read the best score before it changes
         if (improve) {
-            if (tid == 0) {
+            if (tid < 32) {
+                const int l = tid;
                 const uint32_t id = static_cast<uint32_t>(key & 0xffffffffu);
-                const PoseF ps = d.slots[static_cast<int64_t>(id) - 4 * wq.s_begin];
-                for (int k = 0; k < 9; ++k) S.R[k] = ps.R[k];
-                for (int k = 0; k < 3; ++k) S.t[k] = ps.t[k];
-                orthonormalize<double>(S.R);  // float32 pose -> rotation to FP64 rounding
-                orthonormalize<double>(S.R);
-                for (int k = 0; k < 9; ++k) S.st.R[k] = S.R[k];
-                for (int k = 0; k < 3; ++k) S.st.t[k] = S.t[k];
-                S.st.best_score = sc;
-                S.st.best_hyp = id;
-                S.st.have_best = 1;
+                const PoseF& ps = d.slots[static_cast<int64_t>(id) - 4 * wq.s_begin];
+                if (l < 9) S.R[l] = ps.R[l];
+                else if (l < 12) S.t[l - 9] = ps.t[l - 9];
+                __syncwarp();
+                // float32 pose -> rotation to FP64 rounding (quadratic convergence from ~1e-7)
+                orthonormalize_warp(S.R);
+                orthonormalize_warp(S.R);
+                if (l < 9) S.st.R[l] = S.R[l];
+                else if (l < 12) S.st.t[l - 9] = S.t[l - 9];
+                if (l == 0) {
+                    S.st.best_score = sc;
+                    S.st.best_hyp = id;
+                    S.st.have_best = 1;
+                }
             }
             __syncthreads();
             if (d.lo_iters > 0) {
@@ -661,11 +862,12 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
                     S.st.subset_inliers = static_cast<int32_t>(S.cnt);
                 }
             } else {
-                if (tid == 0) set_pass_pose(S, S.st.R, S.st.t);
+                if (tid < 32) pass_pose_warp(S, S.st.R, S.st.t);
                 __syncthreads();
                 pass<kCountSub, float, NT>(S, d, cluster, rank, CL, slot);
                 if (tid == 0) S.st.subset_inliers = static_cast<int32_t>(S.tot[28]);
             }
+            if (tid == 0) S.need = needed_iters(d, S.st);
             __syncthreads();
         }
         if (tid == 0) {
@@ -673,19 +875,10 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
             S.st.iters = it;
             S.st.rounds_done = r + 1;
             S.st.hypotheses += hyps_r;
-            bool stop = it >= d.hyps;
-            if (!stop && d.p_miss > 0.0 && S.st.have_best && S.st.m > 0) {
-                const double eps = static_cast<double>(S.st.subset_inliers) / static_cast<double>(S.st.m);
-                const double e3 = eps * eps * eps;
-                double need;
-                if (e3 >= 1.0) need = 0.0;
-                else if (e3 <= 0.0) need = INFINITY;
-                else need = log(d.p_miss) / log(1.0 - e3);
-                stop = static_cast<double>(it) >= need;
-            }
-            if (stop) S.st.done = 1;
+            if (it >= d.hyps || static_cast<double>(it) >= S.need) S.st.done = 1;
         }
         __syncthreads();
+        ++r;
     }
     if (S.st.done && !S.st.finished) {
         if (!S.st.have_best) {
@@ -698,37 +891,46 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
             }
             __syncthreads();
         } else {
-            if (tid == 0) {
-                for (int k = 0; k < 9; ++k) S.R[k] = S.st.R[k];
-                for (int k = 0; k < 3; ++k) S.t[k] = S.st.t[k];
+            if (tid < 12) {
+                if (tid < 9) S.R[tid] = S.st.R[tid];
+                else S.t[tid - 9] = S.st.t[tid - 9];
             }
             __syncthreads();
+            int64_t num_inliers;
             if (d.final_iters > 0) gauss_newton<kFinInit, kFin, ACC, NT>(S, d, cluster, rank, CL, slot, d.final_iters);
-            if (tid == 0) set_pass_pose(S, S.R, S.t);
-            __syncthreads();
-            pass<kCountFull, float, NT>(S, d, cluster, rank, CL, slot);
+            if (d.final_iters > 0 && d.mask == nullptr) {
+                // every refinement pass counts the inliers at its pose: those of the final one
+                num_inliers = static_cast<int64_t>(S.cnt_all);
+            } else {
+                if (tid < 32) pass_pose_warp(S, S.R, S.t);
+                __syncthreads();
+                pass<kCountFull, float, NT>(S, d, cluster, rank, CL, slot);
+                num_inliers = static_cast<int64_t>(S.tot[28]);
+            }
             if (tid == 0) {
-                if (rank == 0) write_result(S, d, static_cast<int64_t>(S.tot[28]));
+                if (rank == 0) write_result(S, d, num_inliers);
                 S.st.finished = 1;
             }
             __syncthreads();
         }
     }
-    if (rank == 0 && tid == 0) *qs = S.st;
+    if (rank == 0)
+        for (int k = tid; k < kWords; k += NT)
+            reinterpret_cast<uint64_t*>(qs)[k] = reinterpret_cast<const uint64_t*>(&S.st)[k];
     __syncthreads();
 }
 
 // Stand-alone replay: one cluster per query (queries whose accumulation
 // precision this instance implements; the others are skipped).
 template <typename ACC>
-__global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayParams p) {
+__global__ void __launch_bounds__(replay_threads<ACC>()) k_replay(const __grid_constant__ ReplayParams p) {
     __shared__ ReplaySmem S;
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = static_cast<int>(cluster.num_blocks());
     const int rank = static_cast<int>(cluster.block_rank());
     const int q = blockIdx.x / CL;
     const QueryDesc& d = p.qd[q];
-    if ((d.lo_fp64 != 0) == (sizeof(ACC) == 8)) replay_query<ACC, kRT>(S, d, p.qs + q, p.wq[q], cluster, CL, rank);
+    if ((d.lo_fp64 != 0) == (sizeof(ACC) == 8)) replay_query<ACC, replay_threads<ACC>()>(S, d, p.qs + q, p.wq[q], cluster, CL, rank);
     // no CTA may leave while another can still read its shared memory
     cluster.sync();
 }
@@ -736,10 +938,10 @@ __global__ void __launch_bounds__(kRT) k_replay(const __grid_constant__ ReplayPa
 // ============================================================================
 // k_score: persistent, cluster-split hypothesis scoring
 // ============================================================================
-constexpr int kChunk = 256;        // subset records per bulk copy (8 KB)
+constexpr int kChunkPairs = 128;   // subset record pairs per bulk copy (6 KB)
 constexpr int kScoreCluster = 8;   // CTAs per (query, pose tile) item: they split the subset
-constexpr int kWinRecords = 1280;  // records resident per CTA (40 KB): M <= 10,240 in one window
-constexpr int kWinChunks = kWinRecords / kChunk;
+constexpr int kWinPairs = 640;     // record pairs resident per CTA (30 KB): M <= 10,240 in one window
+constexpr int kWinChunks = kWinPairs / kChunkPairs;
 constexpr int kTileHyps = 512;     // poses per item (THREADS x HT for every variant)
 
 struct ScoreParams {
@@ -756,11 +958,18 @@ struct ScoreParams {
 };
 
 // Each CTA keeps its share of the query's subset resident in shared memory:
-// one bulk copy (and one mbarrier) per 256-record chunk, so compute starts on
+// one bulk copy (and one mbarrier) per 128-pair chunk, so compute starts on
 // chunk 0 while the rest lands, no block barrier between chunks, and the
 // next item of the same query reuses the data.  Every thread scores HT poses
-// held in registers against every record of the share, in record order, so
-// the partial sums do not depend on (THREADS, HT).
+// held in registers against every record pair of the share: the projection
+// (9 of the 14 FP32-pipe operations per pose and record) runs as fma.f32x2
+// on both records of a pair (the pose coefficients are duplicated into both
+// halves), the rest in scalar FP32 on the unpacked halves, so that the
+// issue slots the packed instructions free serve the reciprocal, min/max
+// and shared-memory loads and the FP32 pipe, not issue, is the limit.  Per
+// chunk, the even and the odd records of the chunk are summed separately, in
+// order, and the chunk adds even + odd to the pose's total: the partial sums
+// do not depend on (THREADS, HT).
 // FUSED: after its last item of a query, a cluster replays that query
 // (round-best / LO / termination / refinement) while other clusters keep
 // scoring: the replay needs no separate launch and overlaps the scoring.
@@ -769,8 +978,8 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
     static_assert(THREADS * HT == kTileHyps, "tile size");
     constexpr int TH = kTileHyps;
     extern __shared__ __align__(128) unsigned char smem[];
-    ScoreCorr* buf = reinterpret_cast<ScoreCorr*>(smem);
-    float* s_part = reinterpret_cast<float*>(buf + kWinRecords);
+    ScorePair* buf = reinterpret_cast<ScorePair*>(smem);
+    float* s_part = reinterpret_cast<float*>(buf + kWinPairs);
     int* s_cnt = reinterpret_cast<int*>(s_part + TH);
     __shared__ __align__(8) uint64_t bar[kWinChunks];
     __shared__ int s_item, s_last;
@@ -810,50 +1019,58 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
         const int64_t slot_base = 4 * p.wq[q].s_begin;
         const float tau2 = d.tau2;
 
-        float P[HT][12];
+        // pose h as 12 projection coefficients (K [R | t] rows), each duplicated
+        // into both halves of a packed pair
+        uint64_t P[HT][12];
 #pragma unroll
         for (int h = 0; h < HT; ++h) {
             const int j = tile * TH + h * THREADS + tid;
+            float c12[12];
             if (j < nh) {
                 const int id = d.compact[j];
                 const PoseF ps = d.slots[id - slot_base];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    P[h][c] = d.fx * ps.R[c] + d.cx * ps.R[6 + c];
-                    P[h][4 + c] = d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c];
-                    P[h][8 + c] = ps.R[6 + c];
+                    c12[c] = d.fx * ps.R[c] + d.cx * ps.R[6 + c];
+                    c12[4 + c] = d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c];
+                    c12[8 + c] = ps.R[6 + c];
                 }
-                P[h][3] = d.fx * ps.t[0] + d.cx * ps.t[2];
-                P[h][7] = d.fy * ps.t[1] + d.cy * ps.t[2];
-                P[h][11] = ps.t[2];
+                c12[3] = d.fx * ps.t[0] + d.cx * ps.t[2];
+                c12[7] = d.fy * ps.t[1] + d.cy * ps.t[2];
+                c12[11] = ps.t[2];
             } else {
 #pragma unroll
-                for (int c = 0; c < 12; ++c) P[h][c] = 0.f;
+                for (int c = 0; c < 12; ++c) c12[c] = 0.f;
             }
+#pragma unroll
+            for (int c = 0; c < 12; ++c) P[h][c] = f2_pack(c12[c], c12[c]);
         }
-        const int c0 = static_cast<int>(static_cast<int64_t>(m) * rank / CS);
-        const int c1 = static_cast<int>(static_cast<int64_t>(m) * (rank + 1) / CS);
-        const int nwin = (c1 - c0 + kWinRecords - 1) / kWinRecords;
+        // this CTA's share of the record pairs
+        const int m2 = (m + 1) >> 1;
+        const int c0 = static_cast<int>(static_cast<int64_t>(m2) * rank / CS);
+        const int c1 = static_cast<int>(static_cast<int64_t>(m2) * (rank + 1) / CS);
+        const int nwin = (c1 - c0 + kWinPairs - 1) / kWinPairs;
         float acc[HT];
         int cnt[HT];
 #pragma unroll
         for (int h = 0; h < HT; ++h) { acc[h] = 0.f; cnt[h] = 0; }
 
         for (int w = 0; w < nwin; ++w) {
-            const int w0 = c0 + w * kWinRecords;
-            const int nrec_w = min(kWinRecords, c1 - w0);
-            const int nch = (nrec_w + kChunk - 1) / kChunk;
-            const bool reuse = (nwin == 1 && q == loaded_q && w0 == loaded_w0 && nrec_w == loaded_n);
+            const int w0 = c0 + w * kWinPairs;
+            const int npair_w = min(kWinPairs, c1 - w0);
+            const int nch = (npair_w + kChunkPairs - 1) / kChunkPairs;
+            const bool reuse = (nwin == 1 && q == loaded_q && w0 == loaded_w0 && npair_w == loaded_n);
             if (!reuse) {
                 if (nwin > 1) __syncthreads();  // all threads done with the previous window
                 if (tid == 0) {
                     for (int c = 0; c < nch; ++c) {
-                        const int nr = min(kChunk, nrec_w - c * kChunk);
-                        mbar_arrive_expect_tx(&bar[c], nr * 32u);
-                        bulk_g2s(buf + c * kChunk, d.subset + w0 + c * kChunk, nr * 32u, &bar[c]);
+                        const int np = min(kChunkPairs, npair_w - c * kChunkPairs);
+                        const uint32_t bytes = static_cast<uint32_t>(np * sizeof(ScorePair));
+                        mbar_arrive_expect_tx(&bar[c], bytes);
+                        bulk_g2s(buf + c * kChunkPairs, d.subset + w0 + c * kChunkPairs, bytes, &bar[c]);
                     }
                 }
-                if (nwin == 1) { loaded_q = q; loaded_w0 = w0; loaded_n = nrec_w; }
+                if (nwin == 1) { loaded_q = q; loaded_w0 = w0; loaded_n = npair_w; }
                 else loaded_q = -1;
             }
             for (int c = 0; c < nch; ++c) {
@@ -861,31 +1078,41 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
                     mbar_wait_bounded(&bar[c], (phases >> c) & 1u, p.err);
                     phases ^= (1u << c);
                 }
-                const int nrec = min(kChunk, nrec_w - c * kChunk);
-                const float4* rec = reinterpret_cast<const float4*>(buf + c * kChunk);
-                float part[HT];
+                const int np = min(kChunkPairs, npair_w - c * kChunkPairs);
+                const float4* rec = reinterpret_cast<const float4*>(buf + c * kChunkPairs);
+                // partial sums of the chunk: even records and odd records, each in order
+                float pe[HT], po[HT];
 #pragma unroll
-                for (int h = 0; h < HT; ++h) part[h] = 0.f;
+                for (int h = 0; h < HT; ++h) { pe[h] = 0.f; po[h] = 0.f; }
 #pragma unroll UNR
-                for (int k = 0; k < nrec; ++k) {
-                    const float4 A = rec[2 * k];      // X Y Z w
-                    const float4 Bq = rec[2 * k + 1]; // x y
+                for (int k = 0; k < np; ++k) {
+                    const float4 A = rec[3 * k];      // X0 X1 Y0 Y1
+                    const float4 B = rec[3 * k + 1];  // Z0 Z1 w0 w1
+                    const float4 E = rec[3 * k + 2];  // -x0 -x1 -y0 -y1
+                    const uint64_t X2 = f2_pack(A.x, A.y), Y2 = f2_pack(A.z, A.w), Z2 = f2_pack(B.x, B.y);
 #pragma unroll
                     for (int h = 0; h < HT; ++h) {
-                        const float zu = fmaf(P[h][0], A.x, fmaf(P[h][1], A.y, fmaf(P[h][2], A.z, P[h][3])));
-                        const float zv = fmaf(P[h][4], A.x, fmaf(P[h][5], A.y, fmaf(P[h][6], A.z, P[h][7])));
-                        const float zz = fmaf(P[h][8], A.x, fmaf(P[h][9], A.y, fmaf(P[h][10], A.z, P[h][11])));
+                        // the projection of both records: 9 packed FMAs
+                        const uint64_t zu = f2_fma(P[h][0], X2, f2_fma(P[h][1], Y2, f2_fma(P[h][2], Z2, P[h][3])));
+                        const uint64_t zv = f2_fma(P[h][4], X2, f2_fma(P[h][5], Y2, f2_fma(P[h][6], Z2, P[h][7])));
+                        const uint64_t zz = f2_fma(P[h][8], X2, f2_fma(P[h][9], Y2, f2_fma(P[h][10], Z2, P[h][11])));
+                        float u0, u1, v0, v1, z0, z1;
+                        f2_unpack(zu, u0, u1);
+                        f2_unpack(zv, v0, v1);
+                        f2_unpack(zz, z0, z1);
+                        // the rest per record in scalar FP32 (no repacking)
                         // z <= 0 (or NaN) -> 1/0 = inf -> r2 inf/NaN -> min(., tau2) = tau2
-                        const float iz = rcp_approx(fmaxf(zz, 0.0f));
-                        const float du = fmaf(zu, iz, -Bq.x);
-                        const float dv = fmaf(zv, iz, -Bq.y);
-                        const float r2 = fmaf(du, du, dv * dv);
-                        part[h] = fmaf(A.w, fminf(r2, tau2), part[h]);
-                        if (COUNT) cnt[h] += (r2 < tau2) ? 1 : 0;
+                        const float i0 = rcp_approx(fmaxf(z0, 0.0f)), i1 = rcp_approx(fmaxf(z1, 0.0f));
+                        const float du0 = fmaf(u0, i0, E.x), dv0 = fmaf(v0, i0, E.z);
+                        const float du1 = fmaf(u1, i1, E.y), dv1 = fmaf(v1, i1, E.w);
+                        const float r0 = fmaf(du0, du0, dv0 * dv0), r1 = fmaf(du1, du1, dv1 * dv1);
+                        pe[h] = fmaf(B.z, fminf(r0, tau2), pe[h]);
+                        po[h] = fmaf(B.w, fminf(r1, tau2), po[h]);
+                        if (COUNT) cnt[h] += ((r0 < tau2) ? 1 : 0) + ((r1 < tau2) ? 1 : 0);
                     }
                 }
 #pragma unroll
-                for (int h = 0; h < HT; ++h) acc[h] += part[h];
+                for (int h = 0; h < HT; ++h) acc[h] += pe[h] + po[h];
             }
         }
 
@@ -967,20 +1194,19 @@ struct ScoreVariant {
     {T, H, k_score<T, H, false, M, U, false, MF>, k_score<T, H, true, M, U, false, MF>,                 \
      k_score<T, H, false, M, U, true, MF>, k_score<T, H, true, M, U, true, MF>}
 static const ScoreVariant kScoreVariants[] = {
-    IMLOC_SCORE_VARIANT(128, 4, 1, 2, 4),
-    IMLOC_SCORE_VARIANT(256, 2, 1, 2, 2),
-    IMLOC_SCORE_VARIANT(64, 8, 1, 1, 4),
-    IMLOC_SCORE_VARIANT(512, 1, 1, 4, 1),
-    IMLOC_SCORE_VARIANT(128, 4, 5, 1, 5),  // <= 102 registers: 5 CTAs / SM
-    IMLOC_SCORE_VARIANT(256, 2, 1, 4, 2),
-    IMLOC_SCORE_VARIANT(128, 4, 1, 1, 4),
+    IMLOC_SCORE_VARIANT(128, 4, 1, 1, 3),  // ~144 registers: 3 CTAs / SM
+    IMLOC_SCORE_VARIANT(128, 4, 4, 1, 4),  // <= 128 registers: 4 CTAs / SM
+    IMLOC_SCORE_VARIANT(256, 2, 2, 2, 2),
     IMLOC_SCORE_VARIANT(256, 2, 3, 1, 3),  // <= 85 registers: 3 CTAs / SM
+    IMLOC_SCORE_VARIANT(256, 2, 2, 4, 2),
+    IMLOC_SCORE_VARIANT(128, 4, 3, 2, 3),
+    IMLOC_SCORE_VARIANT(512, 1, 1, 4, 1),
 };
 #undef IMLOC_SCORE_VARIANT
 constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
 
 static size_t score_smem_bytes(bool count) {
-    return sizeof(ScoreCorr) * kWinRecords + sizeof(float) * kTileHyps + (count ? sizeof(int) * kTileHyps : 0);
+    return sizeof(ScorePair) * kWinPairs + sizeof(float) * kTileHyps + (count ? sizeof(int) * kTileHyps : 0);
 }
 
 // ============================================================================
@@ -1008,10 +1234,6 @@ struct HostQuery {
     uint64_t* round_best_out;
 };
 
-// CTAs per query in the replay: few queries -> spread each over more SMs
-static int replay_cluster_size(const imloc_ctx* ctx, int nq) {
-    return nq >= ctx->sm_count / 2 ? 1 : (nq >= ctx->sm_count / 8 ? 4 : 8);
-}
 
 template <typename K, typename P>
 static int launch_cluster(K kernel, const P& params, int grid, int block, size_t smem, int cluster, cudaStream_t stream) {
@@ -1062,6 +1284,30 @@ static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     IMLOC_CUDA_TRY(cudaOccupancyMaxActiveClusters(out, kernel, &cfg));
+    return IMLOC_OK;
+}
+
+// CTAs per query in the replay: the largest cluster (8, 4, 2, 1) of which all
+// nq can be resident at once (a query whose cluster waits for another to
+// finish adds a whole replay to the kernel time)
+template <typename ACC>
+static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
+    static const int kCl[4] = {8, 4, 2, 1};
+    const int a = sizeof(ACC) == 8 ? 1 : 0;
+    for (int i = 0; i < 4; ++i) {
+        int& occ = ctx->replay_occ[a][i];
+        if (occ == 0) {
+            int v = 0;
+            const int rc = max_clusters(k_replay<ACC>, replay_threads<ACC>(), 0, kCl[i], &v);
+            if (rc != IMLOC_OK) return rc;
+            occ = v > 0 ? v : -1;
+        }
+        if (occ >= nq) {
+            *cl_out = kCl[i];
+            return IMLOC_OK;
+        }
+    }
+    *cl_out = 1;
     return IMLOC_OK;
 }
 
@@ -1118,7 +1364,7 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
     if (n_init > 0) {
         SetupParams sp{b.d_qd, b.d_qs, b.d_nhyp_all, b.nhyp_all_len, b.d_init};
         ProfScope prof(ctx, stream, "k_setup");
-        k_setup<<<n_init, 256, 0, stream>>>(sp);
+        k_setup<<<n_init * kSetupBlocks, 256, 0, stream>>>(sp);
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
     }
@@ -1166,17 +1412,22 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         prof.end();
     }
     {
-        const int cl = replay_cluster_size(ctx, nq);
         ReplayParams rp{b.d_qd, b.d_qs, b.d_wq, ctx->d_err};
         // queries with FP64 accumulation replay in their own kernel after the scoring
         if (!fuse || b.any_fp64) {
             ProfScope prof(ctx, stream, "k_replay");
             if (!fuse) {
-                rc = launch_cluster(k_replay<float>, rp, nq * cl, kRT, 0, cl, stream);
+                int cl = 1;
+                rc = replay_cluster_size<float>(ctx, nq, &cl);
+                if (rc != IMLOC_OK) return rc;
+                rc = launch_cluster(k_replay<float>, rp, nq * cl, replay_threads<float>(), 0, cl, stream);
                 if (rc != IMLOC_OK) return rc;
             }
             if (b.any_fp64) {
-                rc = launch_cluster(k_replay<double>, rp, nq * cl, kRT, 0, cl, stream);
+                int cl = 1;
+                rc = replay_cluster_size<double>(ctx, nq, &cl);
+                if (rc != IMLOC_OK) return rc;
+                rc = launch_cluster(k_replay<double>, rp, nq * cl, replay_threads<double>(), 0, cl, stream);
                 if (rc != IMLOC_OK) return rc;
             }
             prof.end();
@@ -1287,7 +1538,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.n_cap = static_cast<int32_t>(std::min<int64_t>(h.n_cap, INT32_MAX));
         d.inject = h.inject ? 1 : 0;
         const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
-        d.subset = static_cast<ScoreCorr*>(ws_alloc(ctx, sizeof(ScoreCorr) * std::max(1, o.max_score_corr)));
+        d.subset = static_cast<ScorePair*>(ws_alloc(ctx, sizeof(ScorePair) * ((std::max(1, o.max_score_corr) + 1) / 2)));
         if (h.slots_out) d.slots = h.slots_out;
         else d.slots = static_cast<PoseF*>(ws_alloc(ctx, sizeof(PoseF) * slots));
         d.compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * slots));

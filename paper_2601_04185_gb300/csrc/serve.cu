@@ -121,7 +121,7 @@ static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t 
     L.csrc = take(sizeof(int32_t) * n);
     L.ccount = take(sizeof(int32_t));
     L.fixed = take(static_cast<size_t>(n));
-    L.subset = take(sizeof(ScoreCorr) * static_cast<size_t>(m_cap));
+    L.subset = take(sizeof(ScorePair) * static_cast<size_t>((m_cap + 1) / 2));
     L.slots = take(sizeof(PoseF) * 4 * static_cast<size_t>(step_samples));
     L.compact = take(sizeof(int32_t) * 4 * static_cast<size_t>(step_samples));
     L.round_best = take(sizeof(uint64_t) * static_cast<size_t>(rounds));
@@ -244,7 +244,7 @@ static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     d.seed = o.seed;
     d.query_id = o.query_id;
     d.n_cap = static_cast<int32_t>(q->n);
-    d.subset = reinterpret_cast<ScoreCorr*>(base + L.subset);
+    d.subset = reinterpret_cast<ScorePair*>(base + L.subset);
     d.slots = reinterpret_cast<PoseF*>(base + L.slots);
     d.compact = reinterpret_cast<int32_t*>(base + L.compact);
     d.round_best = reinterpret_cast<uint64_t*>(base + L.round_best);
