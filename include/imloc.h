@@ -180,7 +180,9 @@ typedef struct {
     int32_t lo_iters;        /* Gauss-Newton iterations per LO (10); 0 disables LO */
     double p_miss;           /* adaptive stop (1e-4); <= 0 runs all max_iters */
     int32_t final_iters;     /* Cauchy refinement iterations (25); 0 disables */
-    int32_t p3p_fp64_polish; /* 1: Newton polish of the P3P depths in FP64 (default) */
+    int32_t p3p_fp64_polish; /* 1 (default): Newton polish of the P3P depths with residuals in extended
+                                precision (double-float, ~48-bit significand, evaluated on the FP32
+                                pipe); 0: FP32 polish */
     double cauchy_scale;     /* Cauchy scale c in pixels (<= 0: use tau_px) */
     uint64_t seed;
     uint32_t query_id;

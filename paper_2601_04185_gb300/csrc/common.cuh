@@ -176,7 +176,8 @@ struct QueryDesc {
     imloc_result* result;   // device result slot
     // camera and options
     float fx, fy, cx, cy;
-    double ifx_d, ify_d;    // 1/fx, 1/fy in FP64 (bearings of the P3P polish)
+    float ifx_hi, ifx_lo;   // 1/fx as a double-float hi + lo (bearings of the P3P polish)
+    float ify_hi, ify_lo;   // 1/fy likewise
     float tau2, cauchy2;
     int32_t m_cap, batch, hyps, rounds;
     int32_t lo_iters, final_iters, polish, enumerate_all;

@@ -11,8 +11,8 @@
 // (e2.L)^2 = 0.  On each plane the depth with the largest normal component is
 // eliminated, a second vanishing form gives a quadratic in the ratio of the
 // other two, and the scale follows from the sum of the distance equations.
-// The depths are polished by Newton on the distance equations (FP64 when
-// requested) and the pose is read off the triangle: R maps the world edge
+// The depths are polished by Newton on the distance equations (with
+// double-float residuals when requested) and the pose is read off the triangle: R maps the world edge
 // frame (X1-X2, X1-X3, cross) onto the camera one, t = l1 y1 - R X1.
 #pragma once
 
@@ -121,6 +121,101 @@ __device__ __forceinline__ void polish_depths(T L[3], const T a[3], const T b[3]
     }
 }
 
+// ---- double-float arithmetic --------------------------------------------
+// A value is the unevaluated sum hi + lo of two floats (|lo| <= ulp(hi)/2),
+// about 48 significant bits.  Error-free transformations: two_sum (Knuth),
+// two_prod through the fused multiply-add (the rounding error of a*b is
+// exactly fma(a, b, -a*b)).  Every operation is written with the _rn
+// intrinsics so that the compiler neither contracts nor reassociates them.
+// The Newton polish of the P3P depths needs the residuals of the distance
+// equations to far more than FP32 precision (they cancel terms of size
+// depth^2 down to the triangle's squared sides); double-float gives that on
+// the FP32 pipe, which this GPU runs at 64 times its FP64 rate.
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return dfloat{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return dfloat{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return dfloat{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b) {
+    const dfloat s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfloat df_neg(dfloat a) { return dfloat{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfloat df_mul(dfloat a, dfloat b) {
+    const dfloat p = df_two_prod(a.hi, b.hi);
+    return df_fast_two_sum(p.hi, __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo)));
+}
+
+// Unit bearing of pixel (px, py): ((px - cx) / fx, (py - cy) / fy, 1) / norm,
+// in double-float (1/fx, 1/fy given as double-floats).
+__device__ __forceinline__ void bearing_df(float px, float py, float cx, float cy, dfloat ifx, dfloat ify,
+                                           dfloat out[3]) {
+    const dfloat ex = df_mul(df_two_sum(px, -cx), ifx);
+    const dfloat ey = df_mul(df_two_sum(py, -cy), ify);
+    const dfloat n2 = df_add(df_add(df_mul(ex, ex), df_mul(ey, ey)), dfloat{1.0f, 0.0f});
+    // 1 / sqrt(n2): float seed r0, rho = 1 - n2 r0^2 (small, in double-float),
+    // r = r0 (1 + rho / 2 + 3 rho^2 / 8) (binomial series; the next term is
+    // below 1e-18 for the seed's accuracy)
+    const float r0 = rsqrtf(n2.hi);
+    const dfloat t = df_mul(n2, df_two_prod(r0, r0));
+    const float rho = __fsub_rn(__fsub_rn(1.0f, t.hi), t.lo);
+    const float corr = __fmul_rn(r0, __fmul_rn(rho, __fmaf_rn(0.375f, rho, 0.5f)));
+    const dfloat r = df_fast_two_sum(r0, corr);
+    out[0] = df_mul(ex, r);
+    out[1] = df_mul(ey, r);
+    out[2] = r;
+}
+
+// Li^2 + Lj^2 - 2 b Li Lj - a for float depths and double-float b, a: the
+// terms of size Li^2 cancel exactly (error-free products and sums), so the
+// result is accurate to ~1e-14 of them.
+__device__ __forceinline__ float dist_residual_df(float Li, float Lj, dfloat b, dfloat a) {
+    const dfloat bq = df_mul(b, df_two_prod(Li, Lj));
+    dfloat s = df_add(df_two_prod(Li, Li), df_two_prod(Lj, Lj));
+    s = df_add(s, dfloat{-2.0f * bq.hi, -2.0f * bq.lo});
+    s = df_add(s, df_neg(a));
+    return __fadd_rn(s.hi, s.lo);
+}
+
+// Newton polish of float depths with double-float residuals (Jacobian and
+// step in FP32): at most `iters` steps, stopping once a step no longer
+// changes the depths beyond float resolution.
+__device__ __forceinline__ void polish_depths_df(float L[3], const dfloat a[3], const dfloat b[3], int iters) {
+    for (int it = 0; it < iters; ++it) {
+        const float f0 = dist_residual_df(L[0], L[1], b[0], a[0]);
+        const float f1 = dist_residual_df(L[0], L[2], b[1], a[1]);
+        const float f2 = dist_residual_df(L[1], L[2], b[2], a[2]);
+        const float j00 = 2.0f * (L[0] - b[0].hi * L[1]), j01 = 2.0f * (L[1] - b[0].hi * L[0]);
+        const float j10 = 2.0f * (L[0] - b[1].hi * L[2]), j12 = 2.0f * (L[2] - b[1].hi * L[0]);
+        const float j21 = 2.0f * (L[1] - b[2].hi * L[2]), j22 = 2.0f * (L[2] - b[2].hi * L[1]);
+        // J = [[j00 j01 0], [j10 0 j12], [0 j21 j22]];  solve J d = f by Cramer
+        const float det = j00 * (-j12 * j21) - j01 * (j10 * j22);
+        if (det == 0.0f) return;
+        const float inv = 1.0f / det;
+        const float d0 = (f0 * (-j12 * j21) - j01 * (f1 * j22 - j12 * f2)) * inv;
+        const float d1 = (j00 * (f1 * j22 - j12 * f2) - f0 * (j10 * j22)) * inv;
+        const float d2 = (j00 * (-j21 * f1) - j01 * (j10 * f2) + f0 * (j10 * j21)) * inv;
+        L[0] -= d0;
+        L[1] -= d1;
+        L[2] -= d2;
+        const float tiny = 6e-8f;  // 2^-24: the step is below the depths' float resolution
+        if (fabsf(d0) <= tiny * fabsf(L[0]) && fabsf(d1) <= tiny * fabsf(L[1]) && fabsf(d2) <= tiny * fabsf(L[2]))
+            return;
+    }
+}
+
 // Pose from depths: R (X1-X2, X1-X3, cross) = (C1-C2, C1-C3, cross), t = C1 - R X1.
 template <typename T, typename B>
 __device__ __forceinline__ bool pose_from_depths(const T L[3], const B y[3][3], const float X[3][3], float Rout[9],
@@ -185,10 +280,10 @@ __device__ __forceinline__ void orthonormalize(T R[9]) {
 }
 
 // Solve one P3P instance.  y: unit bearings (float32), yd: the same bearings
-// in FP64 (used, with FP64 squared distances, by the Newton polish and the
-// pose when non-null), X: world points.  Returns the number of poses (<= 4),
-// sorted by ascending depth of the first point.
-__device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float X[3][3], PoseF out[4],
+// in double-float (used, with double-float squared distances, by the Newton
+// polish when non-null), X: world points.  Returns the number of poses
+// (<= 4), sorted by ascending depth of the first point.
+__device__ int p3p_solve(const float y[3][3], const dfloat (*yd)[3], const float X[3][3], PoseF out[4],
                          float l1_out[4]) {
     const bool fp64_polish = yd != nullptr;
     float a12 = 0.f, a13 = 0.f, a23 = 0.f;
@@ -299,34 +394,41 @@ __device__ int p3p_solve(const float y[3][3], const double (*yd)[3], const float
     }
     // rescale, polish, validate, pose
     const float scale = sqrtf(amax);
+    // the distance equations in double-float for the extended-precision polish
+    dfloat a_df[3], b_df[3];
+    if (fp64_polish) {
+        const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            dfloat acc{0.0f, 0.0f};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const dfloat dc = df_two_sum(X[pi[e]][c], -X[pj[e]][c]);
+                acc = df_add(acc, df_mul(dc, dc));
+            }
+            a_df[e] = acc;
+            b_df[e] = df_add(df_add(df_mul(yd[pi[e]][0], yd[pj[e]][0]), df_mul(yd[pi[e]][1], yd[pj[e]][1])),
+                             df_mul(yd[pi[e]][2], yd[pj[e]][2]));
+        }
+    }
     int nout = 0;
     for (int k = 0; k < ns; ++k) {
         bool good;
         float Lf[3];
         if (fp64_polish) {
-            double L[3] = {double(Ls[k][0]) * scale, double(Ls[k][1]) * scale, double(Ls[k][2]) * scale};
-            double a[3] = {0.0, 0.0, 0.0};
-            for (int c = 0; c < 3; ++c) {
-                const double d12 = double(X[0][c]) - double(X[1][c]), d13 = double(X[0][c]) - double(X[2][c]),
-                             d23 = double(X[1][c]) - double(X[2][c]);
-                a[0] += d12 * d12; a[1] += d13 * d13; a[2] += d23 * d23;
-            }
-            const double b[3] = {yd[0][0] * yd[1][0] + yd[0][1] * yd[1][1] + yd[0][2] * yd[1][2],
-                                 yd[0][0] * yd[2][0] + yd[0][1] * yd[2][1] + yd[0][2] * yd[2][2],
-                                 yd[1][0] * yd[2][0] + yd[1][1] * yd[2][1] + yd[1][2] * yd[2][2]};
-            polish_depths<double>(L, a, b, 4, 1e-13);
-            const double f0 = L[0] * L[0] + L[1] * L[1] - 2.0 * b[0] * L[0] * L[1] - a[0];
-            const double f1 = L[0] * L[0] + L[2] * L[2] - 2.0 * b[1] * L[0] * L[2] - a[1];
-            const double f2 = L[1] * L[1] + L[2] * L[2] - 2.0 * b[2] * L[1] * L[2] - a[2];
-            good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabs(f0) <= 1e-4 * a[0] && fabs(f1) <= 1e-4 * a[1] &&
-                   fabs(f2) <= 1e-4 * a[2];
+            float L[3] = {Ls[k][0] * scale, Ls[k][1] * scale, Ls[k][2] * scale};
+            polish_depths_df(L, a_df, b_df, 4);
+            const float f0 = dist_residual_df(L[0], L[1], b_df[0], a_df[0]);
+            const float f1 = dist_residual_df(L[0], L[2], b_df[1], a_df[1]);
+            const float f2 = dist_residual_df(L[1], L[2], b_df[2], a_df[2]);
+            good = L[0] > 0 && L[1] > 0 && L[2] > 0 && fabsf(f0) <= 1e-4f * a_df[0].hi &&
+                   fabsf(f1) <= 1e-4f * a_df[1].hi && fabsf(f2) <= 1e-4f * a_df[2].hi;
             if (good) {
                 // the pose from the polished depths in float32 (the poses are scored in float32)
-                const float Lf3[3] = {float(L[0]), float(L[1]), float(L[2])};
-                good = pose_from_depths<float, float>(Lf3, y, X, out[nout].R, out[nout].t);
+                good = pose_from_depths<float, float>(L, y, X, out[nout].R, out[nout].t);
                 if (good) orthonormalize(out[nout].R);
             }
-            Lf[0] = float(L[0]);
+            Lf[0] = L[0];
         } else {
             float L[3] = {Ls[k][0] * scale, Ls[k][1] * scale, Ls[k][2] * scale};
             const float a[3] = {a12, a13, a23}, b[3] = {b12, b13, b23};

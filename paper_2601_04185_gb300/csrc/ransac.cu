@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
             }
             if (ok) {
                 float y[3][3], X[3][3];
-                double yd[3][3];
+                dfloat yd[3][3];
                 const float ifx = 1.0f / d.fx, ify = 1.0f / d.fy;
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
@@ -216,12 +216,8 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                     const float inv = rsqrtf(bx * bx + by * by + 1.0f);
                     y[k][0] = bx * inv; y[k][1] = by * inv; y[k][2] = inv;
                     X[k][0] = c.X; X[k][1] = c.Y; X[k][2] = c.Z;
-                    if (d.polish) {
-                        const double ex = (double(c.x) - double(d.cx)) * d.ifx_d;
-                        const double ey = (double(c.y) - double(d.cy)) * d.ify_d;
-                        const double en = rsqrt(ex * ex + ey * ey + 1.0);
-                        yd[k][0] = ex * en; yd[k][1] = ey * en; yd[k][2] = en;
-                    }
+                    if (d.polish)
+                        bearing_df(c.x, c.y, d.cx, d.cy, dfloat{d.ifx_hi, d.ifx_lo}, dfloat{d.ify_hi, d.ify_lo}, yd[k]);
                 }
                 float l1[4];
                 nsol = p3p_solve(y, d.polish ? yd : nullptr, X, sol, l1);
@@ -1518,8 +1514,13 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.mask = h.mask;
         d.result = h.d_result;
         d.fx = h.cam.fx; d.fy = h.cam.fy; d.cx = h.cam.cx; d.cy = h.cam.cy;
-        d.ifx_d = 1.0 / static_cast<double>(h.cam.fx);
-        d.ify_d = 1.0 / static_cast<double>(h.cam.fy);
+        {
+            const double ifx = 1.0 / static_cast<double>(h.cam.fx), ify = 1.0 / static_cast<double>(h.cam.fy);
+            d.ifx_hi = static_cast<float>(ifx);
+            d.ifx_lo = static_cast<float>(ifx - static_cast<double>(d.ifx_hi));
+            d.ify_hi = static_cast<float>(ify);
+            d.ify_lo = static_cast<float>(ify - static_cast<double>(d.ify_hi));
+        }
         d.tau2 = static_cast<float>(o.tau_px * o.tau_px);
         const double cs = o.cauchy_scale > 0.0 ? o.cauchy_scale : o.tau_px;
         d.cauchy2 = static_cast<float>(cs * cs);

@@ -225,8 +225,13 @@ static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     d.n_host = q->n;
     d.result = S->d_res + q->slot;
     d.fx = q->cam.fx; d.fy = q->cam.fy; d.cx = q->cam.cx; d.cy = q->cam.cy;
-    d.ifx_d = 1.0 / static_cast<double>(q->cam.fx);
-    d.ify_d = 1.0 / static_cast<double>(q->cam.fy);
+    {
+        const double ifx = 1.0 / static_cast<double>(q->cam.fx), ify = 1.0 / static_cast<double>(q->cam.fy);
+        d.ifx_hi = static_cast<float>(ifx);
+        d.ifx_lo = static_cast<float>(ifx - static_cast<double>(d.ifx_hi));
+        d.ify_hi = static_cast<float>(ify);
+        d.ify_lo = static_cast<float>(ify - static_cast<double>(d.ify_hi));
+    }
     const imloc_ransac_opts& o = q->opts;
     d.tau2 = static_cast<float>(o.tau_px * o.tau_px);
     const double cs = o.cauchy_scale > 0.0 ? o.cauchy_scale : o.tau_px;
