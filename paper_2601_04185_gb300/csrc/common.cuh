@@ -192,7 +192,8 @@ struct QueryDesc {
     int32_t* compact;       // wave_samples * 4 pose ids (valid poses of the wave)
     uint64_t* round_best;   // rounds: (score bits << 32) | pose id, min-reduced
     int32_t* round_hyps;    // rounds: P3P poses produced per round
-    uint8_t* fixed;         // fixed inlier set of the final refinement (same offsets as the correspondences)
+    int32_t* fixidx;        // fixed inlier set of the final refinement: per replay thread, the indices of its
+                            // fixed points at its own positions (same offsets as the correspondences)
     int32_t inject;         // 1: poses are given (one per sample) instead of sampled + solved
     int32_t pad1;
     // optional outputs for the parity tests (one wave only)

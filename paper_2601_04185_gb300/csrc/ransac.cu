@@ -325,7 +325,7 @@ template <typename ACC>
 __host__ __device__ constexpr int replay_threads() { return sizeof(ACC) == 4 ? 512 : 256; }
 constexpr int kMaxReplayThreads = 512;
 constexpr int kMaxReplayCluster = 8;
-constexpr int kNV = 30;  // H (21, upper triangle), g (6), cost, count, inliers at the pass pose
+constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
 constexpr int kPassUnroll = 4;   // correspondences whose loads are in flight together per thread
 constexpr int kKeyCache = 64;    // round minima staged in shared memory at a time
 
@@ -341,7 +341,7 @@ enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 }
 struct ReplaySmem {
     double R[9], t[3];    // current pose
     double Rc[9], tc[3];  // candidate pose
-    double cost, cnt, cnt_all;
+    double cost, cnt;
     double decrease, prev_cost;
     double need;          // iterations needed by the termination rule at the current inlier ratio
     double tot[32];
@@ -356,6 +356,7 @@ struct ReplaySmem {
     float P[12];
     int flag;
     int skip;             // rounds passed over by the last scan
+    int32_t fixcnt[kMaxReplayThreads];  // fixed inliers of each thread (final refinement)
     QueryState st;
 };
 
@@ -392,32 +393,40 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     const int64_t n = kSub ? S.st.m : S.st.n;
     const int64_t off = S.st.off;
     const int64_t stride = static_cast<int64_t>(CL) * NT;
-    // thread order of the points: i0, i0 + stride, i0 + 2 stride, ... (the loads
-    // of U consecutive ones are issued before any of them is used)
-    for (int64_t i0 = static_cast<int64_t>(rank) * NT + tid; i0 < n; i0 += U * stride) {
+    const int64_t i0 = static_cast<int64_t>(rank) * NT + tid;
+    // the thread's points, in order: i0 + j stride (j < nj); in the kFin passes
+    // only the fixed inliers among them, whose indices the kFinInit pass
+    // recorded at the thread's own positions i0 + k stride (k-th inlier)
+    int32_t* fixidx = d.fixidx + off;
+    const int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
+    int64_t nfix = 0;
+    for (int64_t j0 = 0; j0 < nj; j0 += U) {
         float X[U], Y[U], Z[U], w[U], x[U], y[U];
-        bool fixed_in[U];
+        int64_t idx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + u * stride;
+            const int64_t j = j0 + u;
+            // written by this thread in the kFinInit pass: a coherent load
+            idx[u] = j < nj ? (MODE == kFin ? static_cast<int64_t>(fixidx[i0 + j * stride]) : i0 + j * stride) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = idx[u];
             X[u] = Y[u] = Z[u] = w[u] = x[u] = y[u] = 0.f;
-            fixed_in[u] = false;
-            if (i < n) {
+            if (i >= 0) {
                 if (kSub) {
                     const SubsetRecord c = subset_record(d.subset, i);
                     X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
                 } else {
                     X[u] = __ldg(d.X + off + i); Y[u] = __ldg(d.Y + off + i); Z[u] = __ldg(d.Z + off + i);
                     w[u] = __ldg(d.w + off + i); x[u] = __ldg(d.x + off + i); y[u] = __ldg(d.y + off + i);
-                    // written by this thread in the kFinInit pass: a coherent load
-                    if (MODE == kFin) fixed_in[u] = d.fixed[off + i] != 0;
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t i = i0 + u * stride;
-            if (i >= n) break;
+            const int64_t i = idx[u];
+            if (i < 0) break;
             const float xc = fmaf(Rm[0], X[u], fmaf(Rm[1], Y[u], fmaf(Rm[2], Z[u], tv[0])));
             const float yc = fmaf(Rm[3], X[u], fmaf(Rm[4], Y[u], fmaf(Rm[5], Z[u], tv[1])));
             const float zc = fmaf(Rm[6], X[u], fmaf(Rm[7], Y[u], fmaf(Rm[8], Z[u], tv[2])));
@@ -439,14 +448,12 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
                 acc[28] += inl ? 1.f : 0.f;
                 if (MODE == kCountFull && d.mask) d.mask[off + i] = inl ? 1 : 0;
             } else {
-                bool in_set;
-                if (MODE == kFinInit) {
-                    in_set = inl;
-                    d.fixed[off + i] = inl ? 1 : 0;
-                } else {
-                    in_set = fixed_in[u];
+                // kFinInit: the inliers at the initial pose form the fixed set; kFin: a fixed point
+                const bool in_set = (MODE == kFin) || inl;
+                if (MODE == kFinInit && inl) {
+                    fixidx[i0 + nfix * stride] = static_cast<int32_t>(i);
+                    ++nfix;
                 }
-                acc[29] += inl ? 1.f : 0.f;
                 if (in_set) {
                     const float rr = front ? r2 : tau2;
                     acc[27] += w[u] * c2 * log1pf(rr * ic2);
@@ -470,6 +477,7 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
             }
         }
     }
+    if (MODE == kFinInit) S.fixcnt[tid] = static_cast<int32_t>(nfix);
     // block reduction: a transpose butterfly leaves the warp total of value l
     // in lane l (31 shuffles for 32 values), FP64 across warps, then across
     // the CTAs of the cluster in rank order (identical sums in every CTA)
@@ -661,7 +669,6 @@ __device__ void take_totals(ReplaySmem& S) {
     for (int k = 0; k < 6; ++k) S.gf[k] = S.totf[21 + k];
     S.cost = S.tot[27];
     S.cnt = S.tot[28];
-    S.cnt_all = S.tot[29];
 }
 
 // Gauss-Newton with Marquardt damping retries; starts at S.R, S.t.
@@ -892,17 +899,11 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
                 else S.t[tid - 9] = S.st.t[tid - 9];
             }
             __syncthreads();
-            int64_t num_inliers;
             if (d.final_iters > 0) gauss_newton<kFinInit, kFin, ACC, NT>(S, d, cluster, rank, CL, slot, d.final_iters);
-            if (d.final_iters > 0 && d.mask == nullptr) {
-                // every refinement pass counts the inliers at its pose: those of the final one
-                num_inliers = static_cast<int64_t>(S.cnt_all);
-            } else {
-                if (tid < 32) pass_pose_warp(S, S.R, S.t);
-                __syncthreads();
-                pass<kCountFull, float, NT>(S, d, cluster, rank, CL, slot);
-                num_inliers = static_cast<int64_t>(S.tot[28]);
-            }
+            if (tid < 32) pass_pose_warp(S, S.R, S.t);
+            __syncthreads();
+            pass<kCountFull, float, NT>(S, d, cluster, rank, CL, slot);
+            const int64_t num_inliers = static_cast<int64_t>(S.tot[28]);
             if (tid == 0) {
                 if (rank == 0) write_result(S, d, num_inliers);
                 S.st.finished = 1;
@@ -938,7 +939,7 @@ constexpr int kChunkPairs = 128;   // subset record pairs per bulk copy (6 KB)
 constexpr int kScoreCluster = 8;   // CTAs per (query, pose tile) item: they split the subset
 constexpr int kWinPairs = 640;     // record pairs resident per CTA (30 KB): M <= 10,240 in one window
 constexpr int kWinChunks = kWinPairs / kChunkPairs;
-constexpr int kTileHyps = 512;     // poses per item (THREADS x HT for every variant)
+constexpr int kMaxTileHyps = 512;  // poses per item: THREADS x HT of the variant, at most this
 
 struct ScoreParams {
     const QueryDesc* qd;
@@ -971,8 +972,8 @@ struct ScoreParams {
 // scoring: the replay needs no separate launch and overlaps the scoring.
 template <int THREADS, int HT, bool COUNT, int MINB, int UNR, bool FUSED, int MINB_FUSED>
 __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(const __grid_constant__ ScoreParams p) {
-    static_assert(THREADS * HT == kTileHyps, "tile size");
-    constexpr int TH = kTileHyps;
+    constexpr int TH = THREADS * HT;  // poses per item
+    static_assert(TH <= kMaxTileHyps && TH % kScoreCluster == 0, "tile size");
     extern __shared__ __align__(128) unsigned char smem[];
     ScorePair* buf = reinterpret_cast<ScorePair*>(smem);
     float* s_part = reinterpret_cast<float*>(buf + kWinPairs);
@@ -1190,19 +1191,20 @@ struct ScoreVariant {
     {T, H, k_score<T, H, false, M, U, false, MF>, k_score<T, H, true, M, U, false, MF>,                 \
      k_score<T, H, false, M, U, true, MF>, k_score<T, H, true, M, U, true, MF>}
 static const ScoreVariant kScoreVariants[] = {
-    IMLOC_SCORE_VARIANT(128, 4, 1, 1, 3),  // ~144 registers: 3 CTAs / SM
+    IMLOC_SCORE_VARIANT(128, 4, 1, 1, 3),  // 512-pose tiles; ~144 registers: 3 CTAs / SM
     IMLOC_SCORE_VARIANT(128, 4, 4, 1, 4),  // <= 128 registers: 4 CTAs / SM
+    IMLOC_SCORE_VARIANT(128, 4, 3, 2, 3),
     IMLOC_SCORE_VARIANT(256, 2, 2, 2, 2),
     IMLOC_SCORE_VARIANT(256, 2, 3, 1, 3),  // <= 85 registers: 3 CTAs / SM
-    IMLOC_SCORE_VARIANT(256, 2, 2, 4, 2),
-    IMLOC_SCORE_VARIANT(128, 4, 3, 2, 3),
-    IMLOC_SCORE_VARIANT(512, 1, 1, 4, 1),
+    IMLOC_SCORE_VARIANT(128, 2, 5, 1, 5),  // 256-pose tiles (finer work items): 5 CTAs / SM
+    IMLOC_SCORE_VARIANT(128, 2, 6, 2, 5),  // <= 85 registers: 6 CTAs / SM
+    IMLOC_SCORE_VARIANT(64, 4, 6, 1, 5),   // 256-pose tiles, 2 warps per CTA
 };
 #undef IMLOC_SCORE_VARIANT
 constexpr int kNumScoreVariants = sizeof(kScoreVariants) / sizeof(kScoreVariants[0]);
 
-static size_t score_smem_bytes(bool count) {
-    return sizeof(ScorePair) * kWinPairs + sizeof(float) * kTileHyps + (count ? sizeof(int) * kTileHyps : 0);
+static size_t score_smem_bytes(bool count, int tile) {
+    return sizeof(ScorePair) * kWinPairs + sizeof(float) * tile + (count ? sizeof(int) * tile : 0);
 }
 
 // ============================================================================
@@ -1216,7 +1218,7 @@ struct HostQuery {
     int64_t n_host;
     int64_t n_cap;
     uint8_t* mask;
-    uint8_t* fixed_base;  // fixed-set bytes at the same offsets as the correspondences (null: allocate)
+    int32_t* fixidx_base; // fixed-set indices at the same offsets as the correspondences (null: allocate)
     imloc_result* d_result;
     imloc_camera cam;
     imloc_ransac_opts o;
@@ -1309,13 +1311,28 @@ static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
 
 static int64_t comb3(int64_t m) { return m < 3 ? 0 : m * (m - 1) * (m - 2) / 6; }
 
+static int launch_tiles(imloc_ctx* ctx, const StepBuffers& b, int nq, int tile, cudaStream_t stream) {
+    TilesParams tp{b.d_qs, b.d_nhyp, b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1, b.d_counter, nq, tile};
+    ProfScope prof(ctx, stream, "k_tiles");
+    k_tiles<<<1, 1024, 0, stream>>>(tp);
+    IMLOC_CUDA_TRY(cudaGetLastError());
+    prof.end();
+    return IMLOC_OK;
+}
+
+// Upper bound of the work items of a wave with tiles of `tile` poses.
+static int64_t max_items_of(int64_t total_samples, int nq, int tile) {
+    return std::max<int64_t>(1, (total_samples * 4 + tile - 1) / tile + nq);
+}
+
 // Autotuner of the score kernel: every variant computes bitwise-identical
-// scores (same per-pose record order, same cluster reduction), so the
+// scores (same record order and summation structure per pose), so the
 // variants are timed on the live wave (the kernel is idempotent: it rewrites
-// the same scores and re-applies the same atomic minima) and the fastest is
-// kept for the context.  IMLOC_SCORE_VARIANT=<k> forces variant k.
-static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool counts, int64_t max_items,
-                      uint32_t* d_counter, cudaStream_t stream) {
+// the same scores and re-applies the same atomic minima; the tile table is
+// rebuilt for each variant's tile size) and the fastest is kept for the
+// context.  IMLOC_SCORE_VARIANT=<k> forces variant k.
+static int tune_score(imloc_ctx* ctx, const StepBuffers& b, int nq, const ScoreParams& scp, bool counts,
+                      int64_t total_samples, cudaStream_t stream) {
     if (const char* env = getenv("IMLOC_SCORE_VARIANT")) {
         const int k = atoi(env);
         ctx->score_variant = (k >= 0 && k < kNumScoreVariants) ? k : 0;
@@ -1329,12 +1346,15 @@ static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool 
     for (int rep = 0; rep < 2; ++rep)
         for (int v = 0; v < kNumScoreVariants; ++v) {
             const ScoreVariant& V = kScoreVariants[v];
+            const int tile = V.threads * V.ht;
+            const size_t smem = score_smem_bytes(counts, tile);
             auto kern = counts ? V.fn_count : V.fn;
             int n_clusters = 0;
             int rc = max_clusters(kern, V.threads, smem, kScoreCluster, &n_clusters);
             if (rc != IMLOC_OK || n_clusters <= 0) continue;
-            const int grid = static_cast<int>(std::min<int64_t>(n_clusters, max_items));
-            IMLOC_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), stream));
+            const int grid = static_cast<int>(std::min<int64_t>(n_clusters, max_items_of(total_samples, nq, tile)));
+            rc = launch_tiles(ctx, b, nq, tile, stream);
+            if (rc != IMLOC_OK) return rc;
             IMLOC_CUDA_TRY(cudaEventRecord(e0, stream));
             rc = launch_cluster(kern, scp, grid * kScoreCluster, V.threads, smem, kScoreCluster, stream);
             if (rc != IMLOC_OK) return rc;
@@ -1348,7 +1368,6 @@ static int tune_score(imloc_ctx* ctx, const ScoreParams& scp, size_t smem, bool 
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    IMLOC_CUDA_TRY(cudaMemsetAsync(d_counter, 0, sizeof(uint32_t), stream));
     ctx->score_variant = best;
     ctx->score_variant_ms = best_ms;
     return IMLOC_OK;
@@ -1372,24 +1391,19 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
     }
-    {
-        TilesParams tp{b.d_qs, b.d_nhyp, b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1, b.d_counter, nq,
-                       kTileHyps};
-        ProfScope prof(ctx, stream, "k_tiles");
-        k_tiles<<<1, 1024, 0, stream>>>(tp);
-        IMLOC_CUDA_TRY(cudaGetLastError());
-        prof.end();
-    }
-    const size_t score_smem = score_smem_bytes(want_counts);
     ScoreParams scp{b.d_qd,       b.d_qs,      b.d_wq, b.d_nhyp,   b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1,
                     b.d_counter, nq,          ctx->d_err};
-    const int64_t max_items = std::max<int64_t>(1, (total_samples * 4 + kTileHyps - 1) / kTileHyps + nq);
     // autotune the score kernel variant once per context on a large enough wave
-    if (ctx->score_variant < 0 && (max_items >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
-        rc = tune_score(ctx, scp, score_smem, want_counts, max_items, b.d_counter, stream);
+    if (ctx->score_variant < 0 && (max_items_of(total_samples, nq, kMaxTileHyps) >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
+        rc = tune_score(ctx, b, nq, scp, want_counts, total_samples, stream);
         if (rc != IMLOC_OK) return rc;
     }
     const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
+    const int tile = V.threads * V.ht;
+    const size_t score_smem = score_smem_bytes(want_counts, tile);
+    const int64_t max_items = max_items_of(total_samples, nq, tile);
+    rc = launch_tiles(ctx, b, nq, tile, stream);
+    if (rc != IMLOC_OK) return rc;
     // the fused kernel scores and replays each query when its last item is done
     // (replays overlap the scoring of later queries: worth it with many
     // queries); otherwise the scoring runs alone, followed by the replay kernel.
@@ -1552,15 +1566,15 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         if (!d.subset || !d.slots || !d.compact || !d.round_best || !d.round_hyps) return IMLOC_ERR_OOM;
         est_hyp += h.inject ? H[q] : (H[q] * 3) / 2;
     }
-    // fixed-set bytes: share one buffer per concatenated correspondence set
+    // fixed-set indices: share one buffer per concatenated correspondence set
     for (int q = 0; q < nq; ++q) {
-        if (hq[q].fixed_base) { qd[q].fixed = hq[q].fixed_base; continue; }
+        if (hq[q].fixidx_base) { qd[q].fixidx = hq[q].fixidx_base; continue; }
         bool shared = false;
         for (int p = 0; p < q; ++p)
-            if (hq[p].X == hq[q].X && hq[p].d_off && hq[p].d_off == hq[q].d_off) { qd[q].fixed = qd[p].fixed; shared = true; break; }
+            if (hq[p].X == hq[q].X && hq[p].d_off && hq[p].d_off == hq[q].d_off) { qd[q].fixidx = qd[p].fixidx; shared = true; break; }
         if (!shared) {
-            qd[q].fixed = static_cast<uint8_t*>(ws_alloc(ctx, std::max<int64_t>(1, hq[q].n_cap)));
-            if (!qd[q].fixed) return IMLOC_ERR_OOM;
+            qd[q].fixidx = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * std::max<int64_t>(1, hq[q].n_cap)));
+            if (!qd[q].fixidx) return IMLOC_ERR_OOM;
         }
     }
     const size_t qd_bytes = sizeof(QueryDesc) * nq, wq_bytes = sizeof(WaveQ) * wq.size(),

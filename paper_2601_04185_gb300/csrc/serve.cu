@@ -100,7 +100,7 @@ struct ServeQuery {
 
 // Device footprint of one resident query and the offsets inside it.
 struct Layout {
-    size_t match[5], cx, cy, cX, cY, cZ, cw, csrc, ccount, fixed, subset, slots, compact, round_best, round_hyps, total;
+    size_t match[5], cx, cy, cX, cY, cZ, cw, csrc, ccount, fixidx, subset, slots, compact, round_best, round_hyps, total;
 };
 
 static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t rounds) {
@@ -120,7 +120,7 @@ static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t 
     L.cw = take(sizeof(float) * n);
     L.csrc = take(sizeof(int32_t) * n);
     L.ccount = take(sizeof(int32_t));
-    L.fixed = take(static_cast<size_t>(n));
+    L.fixidx = take(sizeof(int32_t) * static_cast<size_t>(n));
     L.subset = take(sizeof(ScorePair) * static_cast<size_t>((m_cap + 1) / 2));
     L.slots = take(sizeof(PoseF) * 4 * static_cast<size_t>(step_samples));
     L.compact = take(sizeof(int32_t) * 4 * static_cast<size_t>(step_samples));
@@ -254,7 +254,7 @@ static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     d.compact = reinterpret_cast<int32_t*>(base + L.compact);
     d.round_best = reinterpret_cast<uint64_t*>(base + L.round_best);
     d.round_hyps = reinterpret_cast<int32_t*>(base + L.round_hyps);
-    d.fixed = reinterpret_cast<uint8_t*>(base + L.fixed);
+    d.fixidx = reinterpret_cast<int32_t*>(base + L.fixidx);
 }
 
 static int64_t step_samples(const imloc_serve_config& c, int64_t B) { return B * std::max(1, c.rounds_per_step); }
