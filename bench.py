@@ -47,10 +47,11 @@ N_VIEWS = 10
 FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored pair, see the design doc
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per launch of k_score from the committed ncu
-# capture of the current kernel (4-query case scaled by 16/4 queries);
-# None whenever the kernel changed since the capture.
-SCORE_TRAFFIC_PER_LAUNCH = None
+# DRAM bytes (read + write) per launch of k_score on the 16-query C2 step, from
+# the committed ncu capture (profiles/k_score_c2_16queries.md), keyed by the
+# scoring variant (threads, poses per thread) it was taken on; the line reports
+# it only when the autotuner picked that variant.
+SCORE_TRAFFIC_PER_LAUNCH = {(64, 4): 25.754e6 + 0.0}
 # DRAM bytes (read + write) per lifted match from the committed ncu capture of
 # k_lift on the batched 9.48M-match shape (profiles/k_lift_batched_9.5M.md)
 LIFT_TRAFFIC_PER_MATCH = (1.229412e9 + 0.234057e9) / 9.48e6
@@ -736,6 +737,8 @@ def run_ours(args):
     u_launches, u_ms = kstats_unfused.get("k_score", (1, 0.0))
     score_only_ms = u_ms / max(1, u_launches)
     score_only_tflops = FLOPS_PER_PAIR * pairs_per_step / (score_only_ms * 1e-3) / 1e12 if score_only_ms else None
+    score_cfg = ctx.score_config()
+    score_traffic = SCORE_TRAFFIC_PER_LAUNCH.get(tuple(score_cfg[:2])) if (score_cfg and nq == 16) else None
     peak_clock_mhz = 2070.0
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_clock_mhz * 1e6 / 1e12
     lift_ms = kms.get("k_lift", 0.0) / max(1, launches.get("k_lift", 1))
@@ -770,7 +773,7 @@ def run_ours(args):
                   "samples": len(lat)},
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
-                     "traffic": SCORE_TRAFFIC_PER_LAUNCH, "kernel": "k_score",
+                     "traffic": score_traffic, "kernel": "k_score", "variant": score_cfg,
                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
                      "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
                      "launch_ms": score_launch_ms,

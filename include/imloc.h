@@ -73,6 +73,12 @@ int imloc_profile_enable(imloc_ctx* ctx, int on);
 /* Writes min(n, max_out) entries to `out` (host) and the number of kernels
  * seen to *n_out; reset != 0 clears the totals afterwards. */
 int imloc_profile_read(imloc_ctx* ctx, imloc_kernel_stat* out, int32_t max_out, int32_t* n_out, int reset);
+/* Configuration of the hypothesis-scoring kernel the context's autotuner chose
+ * on its first large enough RANSAC wave (variants differ in speed only, not in
+ * results; the paper has no counterpart): CTA threads, poses per thread and
+ * poses per work item.  Returns IMLOC_ERR_NOT_FOUND (outputs untouched) before
+ * the first tuning; host pointers, any of them may be NULL. */
+int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_per_thread, int32_t* tile_poses);
 
 /* ---- cameras and views -------------------------------------------------- */
 typedef struct { float fx, fy, cx, cy; int32_t width, height; } imloc_camera;   /* pinhole */

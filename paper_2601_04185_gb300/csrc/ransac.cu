@@ -327,6 +327,10 @@ constexpr int kMaxReplayThreads = 512;
 constexpr int kMaxReplayCluster = 8;
 constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
 constexpr int kPassUnroll = 4;   // correspondences whose loads are in flight together per thread
+// shared memory of the stand-alone replay kernel (one CTA per SM) that caches
+// each thread's own points: its subset records during LO, its fixed inliers
+// during the final refinement (6 floats each, per thread and slot)
+constexpr int kReplayStageBytes = 192 * 1024;
 constexpr int kKeyCache = 64;    // round minima staged in shared memory at a time
 
 enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 };
@@ -356,6 +360,9 @@ struct ReplaySmem {
     float P[12];
     int flag;
     int skip;             // rounds passed over by the last scan
+    float* stg;           // per-thread point cache (null: none): field f, slot j at stg[(f * stg_cap + j) * NT + tid]
+    int stg_cap;          // slots per thread
+    int sub_staged;       // the cache holds this thread's subset records (else: fixed points or nothing)
     int32_t fixcnt[kMaxReplayThreads];  // fixed inliers of each thread (final refinement)
     QueryState st;
 };
@@ -399,6 +406,12 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     // recorded at the thread's own positions i0 + k stride (k-th inlier)
     int32_t* fixidx = d.fixidx + off;
     const int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
+    // the thread's point cache in shared memory: the first J points of the
+    // subset (cached by the first subset pass of the call) or of the fixed set
+    // (cached by kFinInit); the rest come from global memory
+    const int64_t J = S.stg_cap;
+    float* stg = S.stg;
+    const bool sub_cached = kSub && S.sub_staged;
     int64_t nfix = 0;
     for (int64_t j0 = 0; j0 < nj; j0 += U) {
         float X[U], Y[U], Z[U], w[U], x[U], y[U];
@@ -406,21 +419,33 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
-            // written by this thread in the kFinInit pass: a coherent load
-            idx[u] = j < nj ? (MODE == kFin ? static_cast<int64_t>(fixidx[i0 + j * stride]) : i0 + j * stride) : -1;
+            // in the kFin passes: an index this thread wrote in kFinInit (a coherent load)
+            idx[u] = j >= nj ? -1
+                             : (MODE == kFin ? (j < J ? 0 : static_cast<int64_t>(fixidx[i0 + j * stride]))
+                                             : i0 + j * stride);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            const int64_t j = j0 + u;
             const int64_t i = idx[u];
             X[u] = Y[u] = Z[u] = w[u] = x[u] = y[u] = 0.f;
-            if (i >= 0) {
-                if (kSub) {
-                    const SubsetRecord c = subset_record(d.subset, i);
-                    X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
-                } else {
-                    X[u] = __ldg(d.X + off + i); Y[u] = __ldg(d.Y + off + i); Z[u] = __ldg(d.Z + off + i);
-                    w[u] = __ldg(d.w + off + i); x[u] = __ldg(d.x + off + i); y[u] = __ldg(d.y + off + i);
+            if (i < 0) continue;
+            const bool cached = (MODE == kFin || sub_cached) && j < J;
+            if (cached) {
+                X[u] = stg[(0 * J + j) * NT + tid]; Y[u] = stg[(1 * J + j) * NT + tid];
+                Z[u] = stg[(2 * J + j) * NT + tid]; w[u] = stg[(3 * J + j) * NT + tid];
+                x[u] = stg[(4 * J + j) * NT + tid]; y[u] = stg[(5 * J + j) * NT + tid];
+            } else if (kSub) {
+                const SubsetRecord c = subset_record(d.subset, i);
+                X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
+                if (j < J) {
+                    stg[(0 * J + j) * NT + tid] = X[u]; stg[(1 * J + j) * NT + tid] = Y[u];
+                    stg[(2 * J + j) * NT + tid] = Z[u]; stg[(3 * J + j) * NT + tid] = w[u];
+                    stg[(4 * J + j) * NT + tid] = x[u]; stg[(5 * J + j) * NT + tid] = y[u];
                 }
+            } else {
+                X[u] = __ldg(d.X + off + i); Y[u] = __ldg(d.Y + off + i); Z[u] = __ldg(d.Z + off + i);
+                w[u] = __ldg(d.w + off + i); x[u] = __ldg(d.x + off + i); y[u] = __ldg(d.y + off + i);
             }
         }
 #pragma unroll
@@ -451,7 +476,13 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
                 // kFinInit: the inliers at the initial pose form the fixed set; kFin: a fixed point
                 const bool in_set = (MODE == kFin) || inl;
                 if (MODE == kFinInit && inl) {
-                    fixidx[i0 + nfix * stride] = static_cast<int32_t>(i);
+                    if (nfix < J) {
+                        stg[(0 * J + nfix) * NT + tid] = X[u]; stg[(1 * J + nfix) * NT + tid] = Y[u];
+                        stg[(2 * J + nfix) * NT + tid] = Z[u]; stg[(3 * J + nfix) * NT + tid] = w[u];
+                        stg[(4 * J + nfix) * NT + tid] = x[u]; stg[(5 * J + nfix) * NT + tid] = y[u];
+                    } else {
+                        fixidx[i0 + nfix * stride] = static_cast<int32_t>(i);
+                    }
                     ++nfix;
                 }
                 if (in_set) {
@@ -515,6 +546,9 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
         if (tid < 27) S.totf[tid] = static_cast<float>(sum);
     }
     slot ^= 1;
+    // every thread read the cache state at the start of the pass (before the first barrier)
+    if (tid == 0 && kSub) S.sub_staged = 1;
+    if (tid == 0 && MODE == kFinInit) S.sub_staged = 0;
     __syncthreads();
 }
 
@@ -762,6 +796,7 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
     const int r_end = min(wq.r1, d.rounds);
     int c0 = wq.r0, c1 = min(wq.r0 + kKeyCache, r_end);  // staged rounds [c0, c1)
     __syncthreads();
+    if (tid == 0) S.sub_staged = 0;
     for (int k = tid; k < kWords; k += NT)
         reinterpret_cast<uint64_t*>(&S.st)[k] = reinterpret_cast<const uint64_t*>(qs)[k];
     // the round minima (all final: the scoring of the wave is complete)
@@ -922,6 +957,12 @@ __device__ __noinline__ void replay_query(ReplaySmem& S, const QueryDesc& d, Que
 template <typename ACC>
 __global__ void __launch_bounds__(replay_threads<ACC>()) k_replay(const __grid_constant__ ReplayParams p) {
     __shared__ ReplaySmem S;
+    extern __shared__ __align__(16) float replay_stage[];
+    constexpr int NT = replay_threads<ACC>();
+    if (threadIdx.x == 0) {
+        S.stg = replay_stage;
+        S.stg_cap = kReplayStageBytes / (6 * static_cast<int>(sizeof(float)) * NT);
+    }
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = static_cast<int>(cluster.num_blocks());
     const int rank = static_cast<int>(cluster.block_rank());
@@ -1171,6 +1212,10 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
             const int last = *cluster.map_shared_rank(&s_last, 0);
             if (last && !d.lo_fp64) {
                 __threadfence();
+                if (threadIdx.x == 0) {
+                    S_rep.stg = nullptr;
+                    S_rep.stg_cap = 0;
+                }
                 replay_query<float, THREADS>(S_rep, d, p.qs + q, p.wq[q], cluster, CS, rank);
             }
         }
@@ -1296,7 +1341,7 @@ static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
         int& occ = ctx->replay_occ[a][i];
         if (occ == 0) {
             int v = 0;
-            const int rc = max_clusters(k_replay<ACC>, replay_threads<ACC>(), 0, kCl[i], &v);
+            const int rc = max_clusters(k_replay<ACC>, replay_threads<ACC>(), kReplayStageBytes, kCl[i], &v);
             if (rc != IMLOC_OK) return rc;
             occ = v > 0 ? v : -1;
         }
@@ -1430,14 +1475,14 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
                 int cl = 1;
                 rc = replay_cluster_size<float>(ctx, nq, &cl);
                 if (rc != IMLOC_OK) return rc;
-                rc = launch_cluster(k_replay<float>, rp, nq * cl, replay_threads<float>(), 0, cl, stream);
+                rc = launch_cluster(k_replay<float>, rp, nq * cl, replay_threads<float>(), kReplayStageBytes, cl, stream);
                 if (rc != IMLOC_OK) return rc;
             }
             if (b.any_fp64) {
                 int cl = 1;
                 rc = replay_cluster_size<double>(ctx, nq, &cl);
                 if (rc != IMLOC_OK) return rc;
-                rc = launch_cluster(k_replay<double>, rp, nq * cl, replay_threads<double>(), 0, cl, stream);
+                rc = launch_cluster(k_replay<double>, rp, nq * cl, replay_threads<double>(), kReplayStageBytes, cl, stream);
                 if (rc != IMLOC_OK) return rc;
             }
             prof.end();
@@ -1742,6 +1787,17 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
     rc = imloc::ransac_impl(ctx, n_queries, hq.data(), st, false);
     int rc2 = imloc::end_call(ctx, st);
     return rc != IMLOC_OK ? rc : rc2;
+}
+
+int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_per_thread, int32_t* tile_poses) {
+    if (!ctx) return IMLOC_ERR_INVALID_ARG;
+    const int v = ctx->score_variant;
+    if (v < 0 || v >= imloc::kNumScoreVariants) return IMLOC_ERR_NOT_FOUND;
+    const imloc::ScoreVariant& V = imloc::kScoreVariants[v];
+    if (threads) *threads = V.threads;
+    if (poses_per_thread) *poses_per_thread = V.ht;
+    if (tile_poses) *tile_poses = V.threads * V.ht;
+    return IMLOC_OK;
 }
 
 int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_camera* qcam,

@@ -89,7 +89,7 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
            "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
-           "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy"]
+           "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config"]
 
 _lib = None
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
     L.imloc_serve_destroy.argtypes = [V]
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
+    L.imloc_score_config.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
     _lib = L
     return L
 
@@ -282,6 +283,16 @@ class Context:
 
     def profile(self, on: bool):
         _check(self.lib.imloc_profile_enable(self.h, 1 if on else 0), "imloc_profile_enable")
+
+    def score_config(self):
+        """(threads, poses per thread, poses per tile) of the scoring variant the
+        autotuner chose, or None before the first tuning."""
+        t, h, tile = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        rc = self.lib.imloc_score_config(self.h, C.byref(t), C.byref(h), C.byref(tile))
+        if rc == -6:
+            return None
+        _check(rc, "imloc_score_config")
+        return (t.value, h.value, tile.value)
 
     def profile_read(self, reset=True):
         """{kernel name: (launches, total device ms)} of the traced launches."""

@@ -65,3 +65,4 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_lift_async(None, None, 0, None, None, None) == -1
     assert lib.imloc_ransac_pnp(None, None, None, None, None, None, None) == -1
     lib.imloc_destroy(None)
+    assert lib.imloc_score_config(None, None, None, None) == -1
