@@ -78,6 +78,12 @@ def lib():
                                  C.c_int64, P(C.c_double), P(C.c_double)]
         L.orc_needed_iters.restype = C.c_double
         L.orc_needed_iters.argtypes = [C.c_double, C.c_double]
+        L.orc_depth_decode_log8.restype = C.c_double
+        L.orc_depth_decode_log8.argtypes = [C.c_uint8]
+        L.orc_depth_encode_log8.restype = C.c_uint8
+        L.orc_depth_encode_log8.argtypes = [C.c_float]
+        L.orc_depth_encode_log8_n.argtypes = [P(C.c_float), C.c_int64, P(C.c_uint8)]
+        L.orc_depth_decode_log8_n.argtypes = [P(C.c_uint8), C.c_int64, P(C.c_double)]
         L.orc_ransac_pnp.restype = C.c_int
         L.orc_ransac_pnp.argtypes = [P(OrcCorr), P(OrcCam), P(OrcOpts), P(OrcResult), P(C.c_uint8),
                                      P(C.c_int64), P(C.c_double), C.c_int64]
@@ -239,3 +245,21 @@ def ransac_pnp(corr: Corr, K, max_rounds=256, **kw):
                 num_inliers=res.num_inliers, subset_inliers=res.subset_inliers, iterations=res.iterations,
                 rounds=res.rounds, lo_count=res.lo_count, hypotheses=res.hypotheses, best_hyp=res.best_hyp,
                 inlier_mask=mask[:corr.n].astype(bool), round_best_id=rb_id[:nr], round_best_score=rb_sc[:nr])
+
+
+# ---- depth codec (Sec. 3.3 "Data Compression", Sec. 4.3 "Depth Quantization") ----
+def depth_encode_log8(depth):
+    """float32 depth array -> uint8 codes (0 = no depth, 1..255 log levels over [0.25, 128] m)."""
+    d = np.ascontiguousarray(depth, dtype=np.float32)
+    out = np.zeros(d.shape, dtype=np.uint8)
+    L = lib()
+    L.orc_depth_encode_log8_n(_ptr(d, C.c_float), d.size, _ptr(out, C.c_uint8))
+    return out
+
+
+def depth_decode_log8(codes):
+    """uint8 codes -> float64 depth (0 for code 0)."""
+    c = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.zeros(c.shape, dtype=np.float64)
+    lib().orc_depth_decode_log8_n(_ptr(c, C.c_uint8), c.size, _ptr(out, C.c_double))
+    return out

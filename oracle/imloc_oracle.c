@@ -761,3 +761,40 @@ int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o, orc
     res->status = 0;
     return 0;
 }
+
+/* ==========================================================================
+ * Depth codec -- Sec. 3.3 "Data Compression" (clip to [0.25, 128] m, log
+ * space, 256 levels) and Sec. 4.3 "Depth Quantization" (8 bits, < 1.4 %
+ * relative error).  Reading: code 0 marks a pixel without depth (the mapping
+ * keeps only depths with enough support), codes 1..255 are the 255 log-
+ * uniform levels from 0.25 m to 128 m; nearest level in log space.
+ * ========================================================================== */
+double orc_depth_decode_log8(uint8_t code)
+{
+    if (code == 0) return 0.0;
+    return 0.25 * pow(512.0, (double)(code - 1) / 254.0);
+}
+
+uint8_t orc_depth_encode_log8(float depth)
+{
+    if (!isfinite(depth) || !(depth > 0.0f)) return 0;
+    double d = (double)depth;
+    if (d < 0.25) d = 0.25;
+    if (d > 128.0) d = 128.0;
+    /* position on the level grid: 0 at 0.25 m, 254 at 128 m */
+    const double pos = 254.0 * log(d / 0.25) / log(512.0);
+    long level = (long)floor(pos + 0.5);
+    if (level < 0) level = 0;
+    if (level > 254) level = 254;
+    return (uint8_t)(level + 1);
+}
+
+void orc_depth_encode_log8_n(const float* depth, int64_t n, uint8_t* codes)
+{
+    for (int64_t i = 0; i < n; ++i) codes[i] = orc_depth_encode_log8(depth[i]);
+}
+
+void orc_depth_decode_log8_n(const uint8_t* codes, int64_t n, double* depth)
+{
+    for (int64_t i = 0; i < n; ++i) depth[i] = orc_depth_decode_log8(codes[i]);
+}

@@ -21,6 +21,9 @@
  *   orc_refine        Sec. 3.3 "Pose Estimation" (final refinement, all
  *                     inliers of the full set, Cauchy loss, confidence weights)
  *   orc_ransac_pnp    the whole loop of Sec. 3.3 "Pose Estimation"
+ *   orc_depth_*_log8  Sec. 3.3 "Data Compression" and Sec. 4.3 "Depth
+ *                     Quantization" (depth clipped to [0.25, 128] m and
+ *                     quantized in log space with 256 levels)
  *
  * Conventions: poses are cam_from_world, X_c = R X_w + t, R row-major.
  * Pixel coordinates are continuous with the image covering [0,W]x[0,H] and
@@ -124,6 +127,17 @@ typedef struct {
     int64_t best_hyp;           /* pose id (4*sample + k) of the last accepted round-best */
     int32_t status;             /* 0 ok, -1 degenerate */
 } orc_result;
+
+/* ---- depth codec ---------------------------------------------------------
+ * 8-bit log depth.  Code 0 = no depth; code c in 1..255 stands for the depth
+ * 0.25 * 512^((c - 1) / 254) m (255 levels log-uniform over [0.25, 128] m).
+ * Encoding: depth <= 0, NaN or infinite -> 0; otherwise the depth is clipped
+ * to [0.25, 128] m and rounded to the nearest level in log space (ties to
+ * the larger level).                                                      */
+double orc_depth_decode_log8(uint8_t code);
+uint8_t orc_depth_encode_log8(float depth);
+void orc_depth_encode_log8_n(const float* depth, int64_t n, uint8_t* codes);
+void orc_depth_decode_log8_n(const uint8_t* codes, int64_t n, double* depth);
 
 /* Optional per-round trace: round_best_id[r], round_best_score[r]. */
 int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o,
