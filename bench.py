@@ -521,12 +521,23 @@ def run_precision_study(args):
 # ---------------------------------------------------------------------------
 # lift roofline on a batched shape (many queries, ~10^7 matches per launch)
 # ---------------------------------------------------------------------------
-def run_lift_batched(dev, store_views_dev, queries, repeats=10):
+def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
     """One lift launch over all serving queries concatenated (each query's
-    matches against its own store views); algorithmic bytes / event time."""
+    matches against its own store views); algorithmic bytes / event time.
+    log8: the store views as 8-bit log depth codes (the depth codec of
+    Sec. 3.3 "Data Compression", decoded inside the lift)."""
     import torch
 
     from paper_2601_04185_gb300 import imloc
+
+    if log8:
+        enc = []
+        for v in store_views_dev:
+            d = dict(v)
+            d["depth"] = imloc.depth_encode_log8(v["depth"])
+            enc.append(d)
+        torch.cuda.synchronize()
+        store_views_dev = enc
 
     views, qb = [], [0]
     cat = {k: [] for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
@@ -573,7 +584,8 @@ def run_lift_batched(dev, store_views_dev, queries, repeats=10):
     nbytes = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 64, 32))) + 28 * n_valid
     # the same count with 64-byte DRAM atoms for the random depth taps (2 x 64 B bilinear, 64 B lookup)
     nbytes64 = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 128, 64))) + 28 * n_valid
-    return {"matches_per_launch": n, "valid": n_valid, "bytes_per_launch": nbytes, "launch_ms": launch_ms,
+    return {"depth_format": "log8" if log8 else "f32", "map_store_bytes": int(sum(v["depth"].numel() * v["depth"].element_size() for v in views)),
+            "matches_per_launch": n, "valid": n_valid, "bytes_per_launch": nbytes, "launch_ms": launch_ms,
             "achieved_gbs": nbytes / (launch_ms * 1e-3) / 1e9, "store_views": len(views),
             "bytes_per_launch_64b_atoms": nbytes64, "achieved_gbs_64b_atoms": nbytes64 / (launch_ms * 1e-3) / 1e9,
             "workload": f"{len(queries)} serving queries concatenated ({n} matches) against "
@@ -591,7 +603,8 @@ def run_lift_only(args):
         d = dict(v)
         d["depth"] = torch.from_numpy(v["depth"]).to(dev)
         dv.append(d)
-    print(json.dumps({"lift_batched": run_lift_batched(dev, dv, sq, repeats=args.steps)}))
+    print(json.dumps({"lift_batched": run_lift_batched(dev, dv, sq, repeats=args.steps),
+                      "lift_batched_log8": run_lift_batched(dev, dv, sq, repeats=args.steps, log8=True)}))
     return 0
 
 
@@ -814,6 +827,13 @@ def run_ours(args):
                                  "frac": lb["achieved_gbs"] / hbm_peak, "traffic": LIFT_TRAFFIC_PER_MATCH and
                                  LIFT_TRAFFIC_PER_MATCH * lb["matches_per_launch"],
                                  "kernel": "k_lift", "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)", **lb}
+        lb8 = run_lift_batched(dev, dv, sq, log8=True)
+        line["lift_log8"] = {"launch_ms": lb8["launch_ms"], "speedup_vs_f32": lb["launch_ms"] / lb8["launch_ms"],
+                             "matches_per_s": lb8["matches_per_launch"] / (lb8["launch_ms"] * 1e-3),
+                             "valid": lb8["valid"], "map_store_bytes": lb8["map_store_bytes"],
+                             "map_store_bytes_f32": lb["map_store_bytes"],
+                             "note": "same matches as roofline_lift, store views as 8-bit log depth codes "
+                                     "(Sec. 3.3 Data Compression) decoded inside k_lift; L2 flushed before each launch"}
         line["serving"] = run_serving(dev, SERVE_RATES, args.serve_per_rate, sq, dv)
         line["serving"]["workload"] = (f"C5: map store of {STORE_VIEWS} views (1024x768 float32 depth, resident), "
                                        f"{len(sq)} distinct queries of 10-40 views x 5,000 matches, "

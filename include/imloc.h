@@ -84,16 +84,43 @@ int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_pe
 typedef struct { float fx, fy, cx, cy; int32_t width, height; } imloc_camera;   /* pinhole */
 typedef struct { double R[9]; double t[3]; } imloc_pose;                        /* cam_from_world */
 
+/* Depth map formats of a view. */
+#define IMLOC_DEPTH_F32  0  /* float32 metres; <= 0 or non-finite = no depth */
+#define IMLOC_DEPTH_LOG8 1  /* 8-bit log codes of imloc_depth_encode_log8_async */
+
 /* One database view of the image-based map (ImLoc Sec. 3.1): a depth map
- * with its intrinsics and pose.  `depth` is a device pointer to
- * height x width float32 values, row stride `pitch` elements. */
+ * with its intrinsics and pose.  `depth` is a device pointer to height x
+ * width values of `depth_format` (float32, or one byte per pixel for
+ * IMLOC_DEPTH_LOG8), row stride `pitch` elements. */
 typedef struct {
-    const float* depth;
+    const void* depth;
     int32_t width, height;
     int64_t pitch;
     imloc_camera cam;
     imloc_pose pose;
+    int32_t depth_format;  /* IMLOC_DEPTH_F32 or IMLOC_DEPTH_LOG8 */
+    int32_t reserved;      /* 0 */
 } imloc_view;
+
+/* ---- depth codec (ImLoc Sec. 3.3 "Data Compression": depth clipped to
+ * [0.25 m, 128 m] and quantized in log space with 256 levels; Sec. 4.3
+ * "Depth Quantization": under 1.4 % relative error) -----------------------
+ * Code 0 = no depth; code c in 1..255 stands for 0.25 * 512^((c-1)/254) m.
+ * Encoding maps depth <= 0, NaN or infinite to 0, clips the rest to
+ * [0.25, 128] m and rounds to the nearest level in log space (ties to the
+ * larger level, decided exactly by comparison with the level midpoints);
+ * in-range depths come back within 512^(1/508) - 1 = 1.2357 %.  The lift
+ * decodes codes inside its depth fetch (IMLOC_DEPTH_LOG8 views): one byte per
+ * tap instead of four, and a map store four times smaller.
+ * depth / codes / out: device pointers, row strides in elements; the calls
+ * are asynchronous on `stream`, allocate nothing and need no context.
+ * IMLOC_ERR_INVALID_ARG on null pointers, width or height < 1 or a stride
+ * below the width. */
+int imloc_depth_encode_log8_async(const float* depth, int32_t width, int32_t height, int64_t pitch,
+                                  uint8_t* codes, int64_t code_pitch, void* stream);
+/* codes -> float32 metres (0 for code 0), the same values the lift uses. */
+int imloc_depth_decode_log8_async(const uint8_t* codes, int32_t width, int32_t height, int64_t code_pitch,
+                                  float* out, int64_t out_pitch, void* stream);
 
 /* ---- lifting (ImLoc Sec. 3.3, "Query Time Matching and 2D-3D Lifting") --
  * A match pairs a query pixel (q_u, q_v) with a database position (db_u,

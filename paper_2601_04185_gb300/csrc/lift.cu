@@ -11,21 +11,27 @@
 // published counts/prefixes (decoupled look-back) with a bounded spin.
 //
 // HBM-bound: per match 20 B of match data, the depth taps (two 32-B sectors
-// for a bilinear fetch) and 28 B of output.
+// for a bilinear fetch) and 28 B of output.  Views stored as 8-bit log codes
+// (the depth codec of Sec. 3.3 "Data Compression") are decoded in the fetch
+// through a 256-entry table in shared memory: one byte per tap and a map
+// store a quarter of the float32 size (which then mostly stays in L2).
 #include <stdio.h>
 #include <string.h>
 
 #include <vector>
 
+#include "codec.h"
 #include "common.cuh"
 #include "ctx.h"
 
 namespace imloc {
 
 struct LiftView {
-    const float* depth;
+    const void* depth;    // float32 metres or uint8 log codes (fmt)
     int64_t pitch;
     int32_t W, H;
+    int32_t fmt;          // IMLOC_DEPTH_F32 / IMLOC_DEPTH_LOG8
+    int32_t pad;
     float ifx, ify, cx, cy;
     float Rt[9];  // R^T, row-major
     float C[3];   // camera centre -R^T t
@@ -54,14 +60,22 @@ struct LiftParams {
     unsigned long long* tile_state;  // n_tiles words: (flag << 32) | value
     uint32_t* tile_counter;
     int* err;
+    float lut[256];         // log8 code -> metres (code 0 -> 0: no depth)
 };
 
 constexpr int kLiftThreads = 256;
+static_assert(kLiftThreads == 256, "one decode-table entry per thread");
 constexpr int kLiftItems = 4;
 constexpr int kLiftTile = kLiftThreads * kLiftItems;
 constexpr uint32_t kFlagAggregate = 1u, kFlagPrefix = 2u;
 
 __device__ __forceinline__ bool depth_ok(float d) { return d > 0.0f && d < INFINITY; }
+
+// depth tap at element offset `off` of the view's map (metres; 0 = no depth for codes)
+__device__ __forceinline__ float depth_tap(const LiftView& V, int64_t off, const float* lut) {
+    if (V.fmt == IMLOC_DEPTH_LOG8) return lut[__ldg(static_cast<const uint8_t*>(V.depth) + off)];
+    return __ldg(static_cast<const float*>(V.depth) + off);
+}
 
 __device__ __forceinline__ int find_segment(const LiftSeg* segs, int n_seg, int64_t j) {
     int lo = 0, hi = n_seg - 1;
@@ -82,8 +96,10 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ L
     __shared__ int s_seg0, s_nseg;
     __shared__ LiftSeg s_seg[kTileSegs];
     __shared__ LiftView s_view[kTileSegs];
+    __shared__ float s_lut[256];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kLiftThreads / 32;
+    s_lut[tid] = p.lut[tid];  // kLiftThreads == 256 entries
 
     if (tid == 0) {
         const int t = static_cast<int>(atomicAdd(p.tile_counter, 1u));
@@ -145,16 +161,16 @@ __global__ void __launch_bounds__(kLiftThreads) k_lift(const __grid_constant__ L
             good = (a >= 0.0f) && (a < static_cast<float>(V.W - 1)) && (b >= 0.0f) && (b < static_cast<float>(V.H - 1));
             if (!good) continue;
             const int i0 = static_cast<int>(a), j0 = static_cast<int>(b);
-            const float* r0 = V.depth + static_cast<int64_t>(j0) * V.pitch + i0;
-            const float* r1 = r0 + V.pitch;
-            const float d00 = __ldg(r0), d01 = __ldg(r0 + 1), d10 = __ldg(r1), d11 = __ldg(r1 + 1);
+            const int64_t o0 = static_cast<int64_t>(j0) * V.pitch + i0, o1 = o0 + V.pitch;
+            const float d00 = depth_tap(V, o0, s_lut), d01 = depth_tap(V, o0 + 1, s_lut);
+            const float d10 = depth_tap(V, o1, s_lut), d11 = depth_tap(V, o1 + 1, s_lut);
             good = depth_ok(d00) && depth_ok(d01) && depth_ok(d10) && depth_ok(d11);
             const float al = a - static_cast<float>(i0), be = b - static_cast<float>(j0);
             d = (1.0f - be) * ((1.0f - al) * d00 + al * d01) + be * ((1.0f - al) * d10 + al * d11);
         } else {
             good = (u >= 0.0f) && (u < static_cast<float>(V.W)) && (v >= 0.0f) && (v < static_cast<float>(V.H));
             if (!good) continue;
-            d = __ldg(V.depth + static_cast<int64_t>(static_cast<int>(v)) * V.pitch + static_cast<int>(u));
+            d = depth_tap(V, static_cast<int64_t>(static_cast<int>(v)) * V.pitch + static_cast<int>(u), s_lut);
             good = depth_ok(d);
         }
         if (!good) continue;
@@ -280,6 +296,7 @@ int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, con
         const imloc_view& V = views[v];
         if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
         if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
+        if (V.depth_format != IMLOC_DEPTH_F32 && V.depth_format != IMLOC_DEPTH_LOG8) return IMLOC_ERR_INVALID_ARG;
     }
 
     // Device segment table: non-empty segments only; every query must begin at
@@ -312,6 +329,8 @@ int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, con
         L.pitch = V.pitch;
         L.W = V.width;
         L.H = V.height;
+        L.fmt = V.depth_format;
+        L.pad = 0;
         L.ifx = static_cast<float>(1.0 / static_cast<double>(V.cam.fx));
         L.ify = static_cast<float>(1.0 / static_cast<double>(V.cam.fy));
         L.cx = V.cam.cx;
@@ -364,6 +383,7 @@ int lift_impl(imloc_ctx* ctx, int32_t n_queries, const int64_t* query_begin, con
     p.tile_state = state + 1;
     p.tile_counter = reinterpret_cast<uint32_t*>(state);
     p.err = ctx->d_err;
+    log8_decode_table(p.lut);
     ProfScope prof(ctx, stream, "k_lift");
     k_lift<<<n_tiles, kLiftThreads, 0, stream>>>(p);
     IMLOC_CUDA_TRY(cudaGetLastError());
@@ -462,6 +482,7 @@ extern "C" int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views
         const imloc_view& V = views[v];
         if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
         if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
+        if (V.depth_format != IMLOC_DEPTH_F32 && V.depth_format != IMLOC_DEPTH_LOG8) return IMLOC_ERR_INVALID_ARG;
     }
 
     // device address of the scratch array, looked up once per device
@@ -509,6 +530,8 @@ extern "C" int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views
         L.pitch = V.pitch;
         L.W = V.width;
         L.H = V.height;
+        L.fmt = V.depth_format;
+        L.pad = 0;
         L.ifx = static_cast<float>(1.0 / static_cast<double>(V.cam.fx));
         L.ify = static_cast<float>(1.0 / static_cast<double>(V.cam.fy));
         L.cx = V.cam.cx;
@@ -545,6 +568,7 @@ extern "C" int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views
     p.tile_state = scan + 1;
     p.tile_counter = reinterpret_cast<uint32_t*>(scan);
     p.err = d_err;
+    log8_decode_table(p.lut);
     k_lift<<<n_tiles, kLiftThreads, 0, st>>>(p);
     IMLOC_CUDA_TRY(cudaGetLastError());
     return IMLOC_OK;

@@ -30,9 +30,12 @@ class Pose(C.Structure):
     _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
 
 
+DEPTH_F32, DEPTH_LOG8 = 0, 1
+
+
 class View(C.Structure):
     _fields_ = [("depth", C.c_void_p), ("width", C.c_int32), ("height", C.c_int32), ("pitch", C.c_int64),
-                ("cam", Camera), ("pose", Pose)]
+                ("cam", Camera), ("pose", Pose), ("depth_format", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Segment(C.Structure):
@@ -89,7 +92,8 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_lift_async", "imloc_lift_batch_async", "imloc_ransac_default_opts", "imloc_ransac_pnp",
            "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
-           "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config"]
+           "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config",
+           "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async"]
 
 _lib = None
 
@@ -129,6 +133,8 @@ def load(path: str = LIB_PATH):
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     L.imloc_score_config.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.imloc_depth_encode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
+    L.imloc_depth_decode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     _lib = L
     return L
 
@@ -221,6 +227,8 @@ def _views_struct(views):
                             int(d.shape[0]))
         arr[i].pose.R[:] = [float(a) for a in np.asarray(v["R"], dtype=np.float64).ravel()]
         arr[i].pose.t[:] = [float(a) for a in np.asarray(v["t"], dtype=np.float64).ravel()]
+        # uint8 maps hold 8-bit log codes (depth_encode_log8), float32 maps metres
+        arr[i].depth_format = DEPTH_LOG8 if d.element_size() == 1 else DEPTH_F32
     return arr
 
 
@@ -441,3 +449,40 @@ def results_from_bytes(buf: np.ndarray, nq: int):
     """Decode `nq` device results copied to host as bytes."""
     arr = (Result * nq).from_buffer_copy(np.ascontiguousarray(buf).tobytes())
     return [result_dict(arr[i]) for i in range(nq)]
+
+
+# ---- depth codec (8-bit log codes; no context needed) ----
+def _stream_handle(stream):
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(st.cuda_stream)
+
+
+def depth_encode_log8(depth, out=None, stream=None):
+    """float32 CUDA tensor HxW (metres) -> uint8 CUDA tensor HxW of codes
+    (0 = no depth, 1..255 log levels over [0.25, 128] m), asynchronous."""
+    import torch
+
+    assert depth.dtype == torch.float32 and depth.dim() == 2 and depth.is_cuda and depth.stride(1) == 1
+    H, W = depth.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.uint8, device=depth.device)
+    _check(load().imloc_depth_encode_log8_async(C.c_void_p(depth.data_ptr()), W, H, depth.stride(0),
+                                                C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
+           "imloc_depth_encode_log8_async")
+    return out
+
+
+def depth_decode_log8(codes, out=None, stream=None):
+    """uint8 CUDA tensor of codes -> float32 CUDA tensor (metres, 0 for code 0)."""
+    import torch
+
+    assert codes.dtype == torch.uint8 and codes.dim() == 2 and codes.is_cuda and codes.stride(1) == 1
+    H, W = codes.shape
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=codes.device)
+    _check(load().imloc_depth_decode_log8_async(C.c_void_p(codes.data_ptr()), W, H, codes.stride(0),
+                                                C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
+           "imloc_depth_decode_log8_async")
+    return out

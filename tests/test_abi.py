@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_struct_sizes_match_the_header_layout():
     assert C.sizeof(imloc.RansacOpts) == 72
     assert C.sizeof(imloc.Result) == 264
-    assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96
+    assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96 + 8
     assert C.sizeof(imloc.Corr) == 8 * 9
     assert C.sizeof(imloc.Segment) == 16
 
@@ -66,3 +66,5 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_ransac_pnp(None, None, None, None, None, None, None) == -1
     lib.imloc_destroy(None)
     assert lib.imloc_score_config(None, None, None, None) == -1
+    assert lib.imloc_depth_encode_log8_async(None, 4, 4, 4, None, 4, None) == -1
+    assert lib.imloc_depth_decode_log8_async(None, 4, 4, 4, None, 4, None) == -1
