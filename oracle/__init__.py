@@ -51,6 +51,16 @@ class OrcResult(C.Structure):
                 ("status", C.c_int32)]
 
 
+class OrcTriCam(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class OrcTriOpts(C.Structure):
+    _fields_ = [("angle_deg", C.c_double), ("conf_min", C.c_double), ("keep_more_than", C.c_int64),
+                ("refine_iters", C.c_int64)]
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -84,6 +94,17 @@ def lib():
         L.orc_depth_encode_log8.argtypes = [C.c_float]
         L.orc_depth_encode_log8_n.argtypes = [P(C.c_float), C.c_int64, P(C.c_uint8)]
         L.orc_depth_decode_log8_n.argtypes = [P(C.c_uint8), C.c_int64, P(C.c_double)]
+        L.orc_angle.restype = C.c_double
+        L.orc_angle.argtypes = [P(C.c_double), P(C.c_double)]
+        L.orc_closest_depth.restype = C.c_double
+        L.orc_closest_depth.argtypes = [P(C.c_double)] * 4
+        L.orc_triangulate_pixel.restype = C.c_int64
+        L.orc_triangulate_pixel.argtypes = [P(OrcTriCam), C.c_int64, C.c_int64, C.c_int64, P(OrcTriCam), C.c_int64,
+                                            P(C.c_double), P(C.c_double), P(C.c_double), P(OrcTriOpts),
+                                            P(C.c_double)]
+        L.orc_triangulate_depth.argtypes = [P(OrcTriCam), C.c_int64, C.c_int64, P(OrcTriCam), C.c_int64,
+                                            P(C.c_float), P(C.c_float), P(C.c_float), C.c_int64, P(OrcTriOpts),
+                                            P(C.c_double), P(C.c_int64)]
         L.orc_ransac_pnp.restype = C.c_int
         L.orc_ransac_pnp.argtypes = [P(OrcCorr), P(OrcCam), P(OrcOpts), P(OrcResult), P(C.c_uint8),
                                      P(C.c_int64), P(C.c_double), C.c_int64]
@@ -263,3 +284,55 @@ def depth_decode_log8(codes):
     out = np.zeros(c.shape, dtype=np.float64)
     lib().orc_depth_decode_log8_n(_ptr(c, C.c_uint8), c.size, _ptr(out, C.c_double))
     return out
+
+
+# ---- dense triangulation (Sec. 3.3 "Depth Estimation by Dense Matching") ----
+def tri_cam(cam):
+    """cam: dict fx, fy, cx, cy, R (3x3), t (3)"""
+    c = OrcTriCam()
+    c.fx, c.fy, c.cx, c.cy = (float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"]))
+    c.R[:] = [float(a) for a in np.asarray(cam["R"], np.float64).ravel()]
+    c.t[:] = [float(a) for a in np.asarray(cam["t"], np.float64).ravel()]
+    return c
+
+
+def tri_opts(angle_deg=2.0, conf_min=0.05, keep_more_than=3, refine_iters=500):
+    return OrcTriOpts(float(angle_deg), float(conf_min), int(keep_more_than), int(refine_iters))
+
+
+def angle(a, b):
+    a = np.ascontiguousarray(a, np.float64)
+    b = np.ascontiguousarray(b, np.float64)
+    return lib().orc_angle(_ptr(a, C.c_double), _ptr(b, C.c_double))
+
+
+def closest_depth(C0, d0, C1, d1):
+    arrs = [np.ascontiguousarray(x, np.float64) for x in (C0, d0, C1, d1)]
+    return lib().orc_closest_depth(*[_ptr(a, C.c_double) for a in arrs])
+
+
+def triangulate_pixel(ref, srcs, width, px, py, u, v, conf, **kw):
+    """one pixel: (inliers, depth); u, v, conf: one value per source"""
+    r = tri_cam(ref)
+    arr = (OrcTriCam * len(srcs))(*[tri_cam(c) for c in srcs])
+    uu, vv, cc = (np.ascontiguousarray(x, np.float64) for x in (u, v, conf))
+    o = tri_opts(**kw)
+    d = C.c_double(0.0)
+    n = lib().orc_triangulate_pixel(C.byref(r), width, px, py, arr, len(srcs), _ptr(uu, C.c_double),
+                                    _ptr(vv, C.c_double), _ptr(cc, C.c_double), C.byref(o), C.byref(d))
+    return int(n), d.value
+
+
+def triangulate_depth(ref, srcs, u, v, conf, **kw):
+    """u, v, conf: float32 arrays (n_src, H, W). Returns depth (H, W) float64, inliers (H, W) int64."""
+    u, v, conf = (np.ascontiguousarray(x, np.float32) for x in (u, v, conf))
+    S, H, W = u.shape
+    r = tri_cam(ref)
+    arr = (OrcTriCam * S)(*[tri_cam(c) for c in srcs])
+    o = tri_opts(**kw)
+    depth = np.zeros((H, W), np.float64)
+    inl = np.zeros((H, W), np.int64)
+    lib().orc_triangulate_depth(C.byref(r), W, H, arr, S, _ptr(u, C.c_float), _ptr(v, C.c_float),
+                                _ptr(conf, C.c_float), H * W, C.byref(o), _ptr(depth, C.c_double),
+                                _ptr(inl, C.c_int64))
+    return depth, inl

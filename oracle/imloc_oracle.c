@@ -19,6 +19,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
 /* ======================================================================== */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw: "Parallel random numbers: as   */
 /* easy as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplies, with a   */
@@ -797,4 +801,166 @@ void orc_depth_encode_log8_n(const float* depth, int64_t n, uint8_t* codes)
 void orc_depth_decode_log8_n(const uint8_t* codes, int64_t n, double* depth)
 {
     for (int64_t i = 0; i < n; ++i) depth[i] = orc_depth_decode_log8(codes[i]);
+}
+
+/* ==========================================================================
+ * Dense triangulation -- Sec. 3.3 "Depth Estimation by Dense Matching".
+ * Readings (the paper does not spell them out): a match's depth hypothesis
+ * is where the reference ray passes closest to the match's source ray; the
+ * angular error of a match at a point is the angle between the source ray
+ * and the direction from the source centre to the point; ties between
+ * hypotheses go to the lowest source index; the refinement starts at the
+ * winning hypothesis and keeps its inlier set.
+ * ========================================================================== */
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+static double dot3(const double a[3], const double b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+double orc_angle(const double a[3], const double b[3])
+{
+    double c[3];
+    cross3(a, b, c);
+    return atan2(sqrt(dot3(c, c)), dot3(a, b));
+}
+
+double orc_closest_depth(const double C0[3], const double d0[3], const double C1[3], const double d1[3])
+{
+    /* minimise |C0 + z d0 - C1 - l d1|^2 over (z, l) */
+    const double w[3] = {C0[0] - C1[0], C0[1] - C1[1], C0[2] - C1[2]};
+    const double a = dot3(d0, d0), b = dot3(d0, d1), c = dot3(d1, d1), d = dot3(d0, w), e = dot3(d1, w);
+    const double den = a * c - b * b;
+    if (!(den > 1e-12 * a * c)) return 0.0;
+    return (b * e - c * d) / den;
+}
+
+static void tri_ray(const orc_tri_cam* cam, double x, double y, double C[3], double dir[3])
+{
+    /* C = -R^T t; dir = R^T K^-1 [x, y, 1] */
+    const double k[3] = {(x - cam->cx) / cam->fx, (y - cam->cy) / cam->fy, 1.0};
+    for (int r = 0; r < 3; ++r) {
+        C[r] = -(cam->R[0 * 3 + r] * cam->t[0] + cam->R[1 * 3 + r] * cam->t[1] + cam->R[2 * 3 + r] * cam->t[2]);
+        dir[r] = cam->R[0 * 3 + r] * k[0] + cam->R[1 * 3 + r] * k[1] + cam->R[2 * 3 + r] * k[2];
+    }
+}
+
+/* angle of match s at depth z and its derivative in z */
+static double tri_angle_at(const double C0[3], const double d0[3], double z, const double Cs[3], const double ds[3],
+                           double* dtheta)
+{
+    const double a[3] = {C0[0] + z * d0[0] - Cs[0], C0[1] + z * d0[1] - Cs[1], C0[2] + z * d0[2] - Cs[2]};
+    double u[3], g[3];
+    cross3(a, ds, u);
+    cross3(d0, ds, g);
+    const double sn = sqrt(dot3(u, u)), cs = dot3(a, ds);
+    const double th = atan2(sn, cs);
+    if (dtheta) {
+        /* theta = atan2(s, c): theta' = (c s' - s c') / (s^2 + c^2), c' = d0.ds, s' = u.(d0 x ds) / s */
+        const double cp = dot3(d0, ds);
+        const double sp = sn > 0.0 ? dot3(u, g) / sn : sqrt(dot3(g, g));
+        *dtheta = (cs * sp - sn * cp) / (sn * sn + cs * cs);
+    }
+    return th;
+}
+
+int64_t orc_triangulate_pixel(const orc_tri_cam* ref, int64_t width, int64_t px, int64_t py,
+                              const orc_tri_cam* src, int64_t n_src, const double* u, const double* v,
+                              const double* conf, const orc_tri_opts* o, double* depth)
+{
+    (void)width;
+    double C0[3], d0[3];
+    tri_ray(ref, (double)px + 0.5, (double)py + 0.5, C0, d0);
+    const double thr = o->angle_deg * M_PI / 180.0;
+    double Cs[64][3], ds[64][3];
+    int used[64];
+    const int64_t ns = n_src < 64 ? n_src : 64;
+    for (int64_t s = 0; s < ns; ++s) {
+        used[s] = conf[s] >= o->conf_min;
+        tri_ray(&src[s], u[s], v[s], Cs[s], ds[s]);
+    }
+    int64_t best_n = 0, best_s = -1;
+    double best_z = 0.0;
+    for (int64_t s = 0; s < ns; ++s) {
+        if (!used[s]) continue;
+        const double z = orc_closest_depth(C0, d0, Cs[s], ds[s]);
+        if (!(z > 0.0)) continue;
+        int64_t n = 0;
+        for (int64_t k = 0; k < ns; ++k)
+            if (used[k] && tri_angle_at(C0, d0, z, Cs[k], ds[k], NULL) < thr) ++n;
+        if (n > best_n) {
+            best_n = n;
+            best_s = s;
+            best_z = z;
+        }
+    }
+    *depth = 0.0;
+    if (best_s < 0) return 0;
+    /* the inlier set of the winning hypothesis */
+    int inl[64];
+    for (int64_t k = 0; k < ns; ++k) inl[k] = used[k] && tri_angle_at(C0, d0, best_z, Cs[k], ds[k], NULL) < thr;
+    /* minimise E(z) = sum conf * theta^2 over the inlier set: Gauss-Newton
+     * direction, step halved until E decreases (near a ray's closest approach
+     * the Gauss-Newton model underestimates the curvature and overshoots) */
+    double z = best_z;
+    double e = 0.0;
+    for (int64_t k = 0; k < ns; ++k)
+        if (inl[k]) {
+            const double th = tri_angle_at(C0, d0, z, Cs[k], ds[k], NULL);
+            e += conf[k] * th * th;
+        }
+    for (int64_t it = 0; it < o->refine_iters; ++it) {
+        double g = 0.0, h = 0.0;
+        for (int64_t k = 0; k < ns; ++k) {
+            if (!inl[k]) continue;
+            double dth;
+            const double th = tri_angle_at(C0, d0, z, Cs[k], ds[k], &dth);
+            g += conf[k] * th * dth;
+            h += conf[k] * dth * dth;
+        }
+        if (!(h > 0.0)) break;
+        double step = -g / h;
+        int accepted = 0;
+        for (int half = 0; half < 30; ++half, step *= 0.5) {
+            const double zn = z + step;
+            if (!(zn > 0.0) || !isfinite(zn)) continue;
+            double en = 0.0;
+            for (int64_t k = 0; k < ns; ++k)
+                if (inl[k]) {
+                    const double th = tri_angle_at(C0, d0, zn, Cs[k], ds[k], NULL);
+                    en += conf[k] * th * th;
+                }
+            if (en < e) {
+                z = zn;
+                e = en;
+                accepted = 1;
+                break;
+            }
+        }
+        if (!accepted || fabs(step) <= 1e-14 * z) break;
+    }
+    if (best_n > o->keep_more_than) *depth = z;
+    return best_n;
+}
+
+void orc_triangulate_depth(const orc_tri_cam* ref, int64_t width, int64_t height, const orc_tri_cam* src,
+                           int64_t n_src, const float* u, const float* v, const float* conf, int64_t stride,
+                           const orc_tri_opts* o, double* out_depth, int64_t* out_inliers)
+{
+    double uu[64], vv[64], cc[64];
+    const int64_t ns = n_src < 64 ? n_src : 64;
+    for (int64_t py = 0; py < height; ++py)
+        for (int64_t px = 0; px < width; ++px) {
+            const int64_t p = py * width + px;
+            for (int64_t s = 0; s < ns; ++s) {
+                uu[s] = u[s * stride + p];
+                vv[s] = v[s * stride + p];
+                cc[s] = conf[s * stride + p];
+            }
+            double d;
+            out_inliers[p] = orc_triangulate_pixel(ref, width, px, py, src, ns, uu, vv, cc, o, &d);
+            out_depth[p] = d;
+        }
 }

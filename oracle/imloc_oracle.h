@@ -24,6 +24,10 @@
  *   orc_depth_*_log8  Sec. 3.3 "Data Compression" and Sec. 4.3 "Depth
  *                     Quantization" (depth clipped to [0.25, 128] m and
  *                     quantized in log space with 256 levels)
+ *   orc_triangulate_* Sec. 3.3 "Depth Estimation by Dense Matching" (per
+ *                     pixel: one depth hypothesis per match, most inliers at
+ *                     2 degrees, confidence-weighted refinement of the
+ *                     squared angular errors, kept with more than 3 inliers)
  *
  * Conventions: poses are cam_from_world, X_c = R X_w + t, R row-major.
  * Pixel coordinates are continuous with the image covering [0,W]x[0,H] and
@@ -138,6 +142,47 @@ double orc_depth_decode_log8(uint8_t code);
 uint8_t orc_depth_encode_log8(float depth);
 void orc_depth_encode_log8_n(const float* depth, int64_t n, uint8_t* codes);
 void orc_depth_decode_log8_n(const uint8_t* codes, int64_t n, double* depth);
+
+/* ---- dense triangulation of a mapping depth map ---------------------------
+ * Reference camera (the mapping image) and n_src source cameras with known
+ * poses.  Pixel p = j * width + i (centre (i + 0.5, j + 0.5)) carries one match
+ * per source s: u[s * stride + p], v[...], conf[...] (source pixel position,
+ * confidence).  Per pixel, with X(z) = C0 + z * R0^T K0^-1 [x, y, 1]^T (z the
+ * reference z-depth):
+ *   - matches with conf >= conf_min are used;
+ *   - each used match s gives the hypothesis z_s where the reference ray passes
+ *     closest to the source ray (hypotheses with z_s <= 0 or parallel rays are
+ *     dropped);
+ *   - the inliers of a hypothesis are the used matches whose angular error
+ *     angle(X(z) - C_s', ray_s') is below angle_deg;
+ *   - the hypothesis with the most inliers wins (ties: the lowest source index);
+ *   - its depth is refined to the minimum of sum_{inliers} conf * angle^2
+ *     reached by descent from the winning hypothesis: Gauss-Newton steps,
+ *     each halved until the sum decreases, until a step is below 1e-14 of the
+ *     depth (at most refine_iters steps);
+ *   - the depth is kept if the inliers number more than keep_more_than.
+ * out_depth[p] = refined z (0 if not kept); out_inliers[p] = inlier count of
+ * the winning hypothesis (0 if none).                                       */
+typedef struct { double fx, fy, cx, cy; double R[9], t[3]; } orc_tri_cam;
+typedef struct {
+    double angle_deg;       /* 2 */
+    double conf_min;        /* 0.05 */
+    int64_t keep_more_than; /* 3 */
+    int64_t refine_iters;   /* cap of the descent steps (500: to convergence) */
+} orc_tri_opts;
+
+/* Angle (radians) between a and b (atan2 of the cross and dot products). */
+double orc_angle(const double a[3], const double b[3]);
+/* Closest-approach depth of ray 0 (C0 + z d0) to ray 1 (C1 + l d1); returns
+ * 0 for (nearly) parallel rays. */
+double orc_closest_depth(const double C0[3], const double d0[3], const double C1[3], const double d1[3]);
+/* One pixel; returns the inlier count and writes the depth (0 = none). */
+int64_t orc_triangulate_pixel(const orc_tri_cam* ref, int64_t width, int64_t px, int64_t py,
+                              const orc_tri_cam* src, int64_t n_src, const double* u, const double* v,
+                              const double* conf, const orc_tri_opts* o, double* depth);
+void orc_triangulate_depth(const orc_tri_cam* ref, int64_t width, int64_t height, const orc_tri_cam* src,
+                           int64_t n_src, const float* u, const float* v, const float* conf, int64_t stride,
+                           const orc_tri_opts* o, double* out_depth, int64_t* out_inliers);
 
 /* Optional per-round trace: round_best_id[r], round_best_score[r]. */
 int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o,

@@ -370,3 +370,52 @@ def config4(seed=0, n_queries=64, **kw):
         q.update(hypotheses=10000, tau=4.0, query_id=qi)
         out.append(q)
     return out
+
+
+def mapping_image(rng, n_src=8, width=560, height=560, f=480.0, inlier_prob=0.8, pixel_noise=0.5,
+                  max_rot_deg=15.0, max_shift_m=3.0):
+    """Input of the mapping-time dense triangulation (ImLoc Sec. 3.3 "Depth
+    Estimation by Dense Matching"): a reference (mapping) camera looking at a
+    piecewise-planar scene, `n_src` covisible source cameras (its pose
+    perturbed by <= 15 deg / <= 3 m), and for every reference pixel one match
+    per source.  A match of a pixel whose surface point is visible in the
+    source (in front, inside, not occluded) is, with probability
+    `inlier_prob`, the point's projection + N(0, pixel_noise) with confidence
+    U[0.3, 1]; every other match is a uniform source pixel with confidence
+    U[0, 1].  Returns cameras as dicts (fx, fy, cx, cy, R, t), the match
+    planes u, v, conf (float32, n_src x H x W), the true reference z-depth
+    and the visibility mask."""
+    K = (f, f, width / 2.0, height / 2.0)
+    R0 = random_rotation(rng)
+    t0 = rng.normal(size=3)
+    scene = PlanarScene(rng, R0, t0, K, width, height)
+    depth_gt = scene.depth_map(R0, t0, K, width, height).astype(np.float64)
+    jj, ii = np.meshgrid(np.arange(height) + 0.5, np.arange(width) + 0.5, indexing="ij")
+    has = depth_gt > 0
+    Xw = _backproject(R0, t0, K, ii.ravel(), jj.ravel(), depth_gt.ravel())
+    cam = lambda R, t: dict(fx=K[0], fy=K[1], cx=K[2], cy=K[3], R=R, t=t)
+    srcs = []
+    u = np.zeros((n_src, height, width), np.float32)
+    v = np.zeros_like(u)
+    conf = np.zeros_like(u)
+    vis = np.zeros((n_src, height, width), bool)
+    for s in range(n_src):
+        R_s, t_s = perturbed_view_pose(rng, R0, t0, max_rot_deg, max_shift_m)
+        srcs.append(cam(R_s, t_s))
+        us, vs, zs = _project(R_s, t_s, K, Xw)
+        inside = has.ravel() & (zs > 0) & (us >= 0) & (us < width) & (vs >= 0) & (vs < height)
+        hit = np.zeros_like(zs)
+        hit[inside] = scene.raycast(R_s, t_s, K, us[inside], vs[inside])
+        visible = inside & (np.abs(hit - zs) <= 1e-3 * np.abs(zs))
+        good = visible & (rng.random(zs.shape) < inlier_prob)
+        uo = rng.uniform(0, width, zs.shape)
+        vo = rng.uniform(0, height, zs.shape)
+        uu = np.where(good, us + rng.normal(0, pixel_noise, zs.shape), uo)
+        vv = np.where(good, vs + rng.normal(0, pixel_noise, zs.shape), vo)
+        cc = np.where(good, rng.uniform(0.3, 1.0, zs.shape), rng.uniform(0.0, 1.0, zs.shape))
+        u[s] = uu.reshape(height, width)
+        v[s] = vv.reshape(height, width)
+        conf[s] = cc.reshape(height, width)
+        vis[s] = good.reshape(height, width)
+    return dict(ref=cam(R0, t0), srcs=srcs, u=u, v=v, conf=conf, depth_gt=depth_gt, good=vis,
+                width=width, height=height)
