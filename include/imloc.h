@@ -122,6 +122,42 @@ int imloc_depth_encode_log8_async(const float* depth, int32_t width, int32_t hei
 int imloc_depth_decode_log8_async(const uint8_t* codes, int32_t width, int32_t height, int64_t code_pitch,
                                   float* out, int64_t out_pitch, void* stream);
 
+/* ---- dense triangulation of a mapping depth map (ImLoc Sec. 3.3 "Depth
+ * Estimation by Dense Matching") ------------------------------------------
+ * Mapping time: the depth map of a reference (mapping) image from its dense
+ * matches to n_src covisible source images, all poses known.  Pixel
+ * p = j * width + i (centre (i + 0.5, j + 0.5)) has one match per source s:
+ * u[s * plane_stride + p], v[...] (source pixel position) and conf[...]
+ * (matcher confidence); device arrays.  Per pixel: matches with
+ * conf >= conf_min are used; each gives the depth hypothesis where the
+ * pixel's ray passes closest to the match's ray; a hypothesis's inliers are
+ * the used matches whose angular error (between the match's ray and the
+ * direction from its camera centre to the hypothesised point) is below
+ * angle_deg; the hypothesis with the most inliers wins (ties: lowest source
+ * index); its depth is refined to the minimum of the confidence-weighted
+ * squared angular errors of its inliers (Gauss-Newton on the angular error
+ * vectors, steps halved until the sum decreases, at most refine_iters);
+ * the depth is kept if the inliers number more than keep_more_than.
+ * depth_out[p] = reference z-depth in metres (0 = none); inliers_out[p]
+ * (may be NULL) = inlier count of the winner.  Asynchronous on `stream`;
+ * allocates nothing and needs no context.  IMLOC_ERR_INVALID_ARG for null
+ * pointers, n_src outside 1..IMLOC_TRIANGULATE_MAX_SOURCES or a plane
+ * stride below width * height. */
+#define IMLOC_TRIANGULATE_MAX_SOURCES 16
+typedef struct {
+    float angle_deg;        /* inlier threshold, 2 degrees */
+    float conf_min;         /* 0.05 (matches with conf >= conf_min are used) */
+    int32_t keep_more_than; /* 3 */
+    int32_t refine_iters;   /* 20 */
+} imloc_triangulate_opts;
+
+void imloc_triangulate_default_opts(imloc_triangulate_opts* out);
+int imloc_triangulate_depth_async(const imloc_camera* ref_cam, const imloc_pose* ref_pose, int32_t width,
+                                  int32_t height, const imloc_camera* src_cams, const imloc_pose* src_poses,
+                                  int32_t n_src, const float* u, const float* v, const float* conf,
+                                  int64_t plane_stride, const imloc_triangulate_opts* opts, float* depth_out,
+                                  uint8_t* inliers_out, void* stream);
+
 /* ---- lifting (ImLoc Sec. 3.3, "Query Time Matching and 2D-3D Lifting") --
  * A match pairs a query pixel (q_u, q_v) with a database position (db_u,
  * db_v) in one view and carries the matcher confidence.  Matches are grouped

@@ -38,6 +38,11 @@ class View(C.Structure):
                 ("cam", Camera), ("pose", Pose), ("depth_format", C.c_int32), ("reserved", C.c_int32)]
 
 
+class TriangulateOpts(C.Structure):
+    _fields_ = [("angle_deg", C.c_float), ("conf_min", C.c_float), ("keep_more_than", C.c_int32),
+                ("refine_iters", C.c_int32)]
+
+
 class Segment(C.Structure):
     _fields_ = [("begin", C.c_int64), ("view", C.c_int32), ("direction", C.c_int32)]
 
@@ -93,7 +98,8 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
            "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config",
-           "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async"]
+           "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
+           "imloc_triangulate_depth_async"]
 
 _lib = None
 
@@ -133,6 +139,10 @@ def load(path: str = LIB_PATH):
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     L.imloc_score_config.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.imloc_triangulate_default_opts.argtypes = [P(TriangulateOpts)]
+    L.imloc_triangulate_default_opts.restype = None
+    L.imloc_triangulate_depth_async.argtypes = [P(Camera), P(Pose), C.c_int32, C.c_int32, P(Camera), P(Pose),
+                                                C.c_int32, V, V, V, C.c_int64, P(TriangulateOpts), V, V, V]
     L.imloc_depth_encode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     L.imloc_depth_decode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     _lib = L
@@ -486,3 +496,47 @@ def depth_decode_log8(codes, out=None, stream=None):
                                                 C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
            "imloc_depth_decode_log8_async")
     return out
+
+
+# ---- dense triangulation of a mapping depth map ----
+def triangulate_opts(**kw):
+    o = TriangulateOpts()
+    load().imloc_triangulate_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _cam_pose(c, width=0, height=0):
+    cam = Camera(float(c["fx"]), float(c["fy"]), float(c["cx"]), float(c["cy"]), int(width), int(height))
+    pose = Pose()
+    pose.R[:] = [float(a) for a in np.asarray(c["R"], dtype=np.float64).ravel()]
+    pose.t[:] = [float(a) for a in np.asarray(c["t"], dtype=np.float64).ravel()]
+    return cam, pose
+
+
+def triangulate_depth(ref, srcs, u, v, conf, opts=None, depth=None, inliers=None, stream=None):
+    """ref, srcs: camera dicts (fx, fy, cx, cy, R, t); u, v, conf: float32 CUDA
+    tensors (n_src, H, W).  Returns (depth float32 HxW, inliers uint8 HxW)."""
+    import torch
+
+    S, H, W = u.shape
+    for t in (u, v, conf):
+        assert t.dtype == torch.float32 and t.is_cuda and t.is_contiguous() and tuple(t.shape) == (S, H, W)
+    if depth is None:
+        depth = torch.empty((H, W), dtype=torch.float32, device=u.device)
+    if inliers is None:
+        inliers = torch.empty((H, W), dtype=torch.uint8, device=u.device)
+    rc, rp = _cam_pose(ref, W, H)
+    cams = (Camera * S)()
+    poses = (Pose * S)()
+    for i, c in enumerate(srcs):
+        cams[i], poses[i] = _cam_pose(c)
+    o = opts if opts is not None else triangulate_opts()
+    _check(load().imloc_triangulate_depth_async(C.byref(rc), C.byref(rp), W, H, cams, poses, S,
+                                                C.c_void_p(u.data_ptr()), C.c_void_p(v.data_ptr()),
+                                                C.c_void_p(conf.data_ptr()), H * W, C.byref(o),
+                                                C.c_void_p(depth.data_ptr()), C.c_void_p(inliers.data_ptr()),
+                                                _stream_handle(stream)),
+           "imloc_triangulate_depth_async")
+    return depth, inliers

@@ -68,3 +68,12 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_score_config(None, None, None, None) == -1
     assert lib.imloc_depth_encode_log8_async(None, 4, 4, 4, None, 4, None) == -1
     assert lib.imloc_depth_decode_log8_async(None, 4, 4, 4, None, 4, None) == -1
+    assert lib.imloc_triangulate_depth_async(None, None, 4, 4, None, None, 1, None, None, None, 16, None, None,
+                                             None, None) == -1
+
+
+def test_triangulation_defaults_are_the_papers_constants(lib):
+    o = imloc.triangulate_opts()
+    assert o.angle_deg == 2.0            # 2-degree angular error threshold (Sec. 3.3)
+    assert abs(o.conf_min - 0.05) < 1e-9 # matches with confidence >= 0.05 (Sec. 3.3)
+    assert o.keep_more_than == 3         # keep depths with more than 3 inliers (Sec. 3.3)
