@@ -105,6 +105,10 @@ def lib():
         L.orc_triangulate_depth.argtypes = [P(OrcTriCam), C.c_int64, C.c_int64, P(OrcTriCam), C.c_int64,
                                             P(C.c_float), P(C.c_float), P(C.c_float), C.c_int64, P(OrcTriOpts),
                                             P(C.c_double), P(C.c_int64)]
+        L.orc_bf16_to_double.restype = C.c_double
+        L.orc_bf16_to_double.argtypes = [C.c_uint16]
+        L.orc_retrieve_topk.argtypes = [P(C.c_uint16), C.c_int64, P(C.c_uint16), C.c_int64, C.c_int64, C.c_int64,
+                                        P(C.c_double), P(C.c_int64)]
         L.orc_ransac_pnp.restype = C.c_int
         L.orc_ransac_pnp.argtypes = [P(OrcCorr), P(OrcCam), P(OrcOpts), P(OrcResult), P(C.c_uint8),
                                      P(C.c_int64), P(C.c_double), C.c_int64]
@@ -336,3 +340,22 @@ def triangulate_depth(ref, srcs, u, v, conf, **kw):
                                 _ptr(conf, C.c_float), H * W, C.byref(o), _ptr(depth, C.c_double),
                                 _ptr(inl, C.c_int64))
     return depth, inl
+
+
+# ---- retrieval nearest-neighbour search (Sec. 3.1, Sec. 4.4 "Runtime") ----
+def bf16_to_double(bits):
+    return lib().orc_bf16_to_double(int(bits))
+
+
+def retrieve_topk(queries_bf16, db_bf16, k):
+    """queries_bf16: uint16 (Q, D), db_bf16: uint16 (N, D) bfloat16 bit patterns.
+    Returns scores (Q, k) float64 and indices (Q, k) int64."""
+    q = np.ascontiguousarray(queries_bf16, np.uint16)
+    d = np.ascontiguousarray(db_bf16, np.uint16)
+    Q, D = q.shape
+    N = d.shape[0]
+    sc = np.zeros((Q, k), np.float64)
+    ix = np.zeros((Q, k), np.int64)
+    lib().orc_retrieve_topk(_ptr(q, C.c_uint16), Q, _ptr(d, C.c_uint16), N, D, k, _ptr(sc, C.c_double),
+                            _ptr(ix, C.c_int64))
+    return sc, ix

@@ -964,3 +964,47 @@ void orc_triangulate_depth(const orc_tri_cam* ref, int64_t width, int64_t height
             out_depth[p] = d;
         }
 }
+
+/* ==========================================================================
+ * Retrieval nearest-neighbour search -- Sec. 3.1 (precomputed global
+ * retrieval features per database image) and Sec. 4.4 "Runtime" (the
+ * nearest-neighbour search of retrieval features on the GPU).  FP64 dot
+ * products of the bfloat16 values (each product is exact in FP64), then a
+ * plain selection of the K best.
+ * ========================================================================== */
+double orc_bf16_to_double(uint16_t bits)
+{
+    /* bfloat16 = the upper 16 bits of an IEEE binary32 */
+    const uint32_t u = (uint32_t)bits << 16;
+    float f;
+    memcpy(&f, &u, sizeof(f));
+    return (double)f;
+}
+
+void orc_retrieve_topk(const uint16_t* queries, int64_t Q, const uint16_t* db, int64_t N, int64_t D,
+                       int64_t K, double* out_score, int64_t* out_index)
+{
+    double* sc = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double* qd = (double*)malloc(sizeof(double) * (size_t)(D > 0 ? D : 1));
+    for (int64_t q = 0; q < Q; ++q) {
+        for (int64_t d = 0; d < D; ++d) qd[d] = orc_bf16_to_double(queries[q * D + d]);
+        for (int64_t n = 0; n < N; ++n) {
+            double s = 0.0;
+            for (int64_t d = 0; d < D; ++d) s += qd[d] * orc_bf16_to_double(db[n * D + d]);
+            sc[n] = s;
+        }
+        /* K passes of "best remaining": highest score, lowest index among equals */
+        for (int64_t k = 0; k < K; ++k) {
+            int64_t best = -1;
+            for (int64_t n = 0; n < N; ++n) {
+                if (sc[n] != sc[n]) continue; /* taken (NaN marker) */
+                if (best < 0 || sc[n] > sc[best]) best = n;
+            }
+            out_index[q * K + k] = best;
+            out_score[q * K + k] = best >= 0 ? sc[best] : 0.0;
+            if (best >= 0) sc[best] = NAN;
+        }
+    }
+    free(sc);
+    free(qd);
+}

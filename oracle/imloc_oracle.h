@@ -24,6 +24,9 @@
  *   orc_depth_*_log8  Sec. 3.3 "Data Compression" and Sec. 4.3 "Depth
  *                     Quantization" (depth clipped to [0.25, 128] m and
  *                     quantized in log space with 256 levels)
+ *   orc_retrieve_topk Sec. 3.1 / Sec. 4.4 "Runtime" (nearest-neighbour
+ *                     search of global retrieval features: top-K database
+ *                     images by descriptor dot product)
  *   orc_triangulate_* Sec. 3.3 "Depth Estimation by Dense Matching" (per
  *                     pixel: one depth hypothesis per match, most inliers at
  *                     2 degrees, confidence-weighted refinement of the
@@ -183,6 +186,15 @@ int64_t orc_triangulate_pixel(const orc_tri_cam* ref, int64_t width, int64_t px,
 void orc_triangulate_depth(const orc_tri_cam* ref, int64_t width, int64_t height, const orc_tri_cam* src,
                            int64_t n_src, const float* u, const float* v, const float* conf, int64_t stride,
                            const orc_tri_opts* o, double* out_depth, int64_t* out_inliers);
+
+/* ---- retrieval nearest-neighbour search -----------------------------------
+ * queries: Q x D, db: N x D descriptors as bfloat16 bit patterns (row-major);
+ * score(q, n) = sum_d q[d] * db[n][d] (the descriptors are L2-normalised by
+ * the caller: cosine similarity).  Top-K per query by descending score, ties
+ * to the lower database index; out_score / out_index: Q x K (K <= N).      */
+double orc_bf16_to_double(uint16_t bits);
+void orc_retrieve_topk(const uint16_t* queries, int64_t Q, const uint16_t* db, int64_t N, int64_t D,
+                       int64_t K, double* out_score, int64_t* out_index);
 
 /* Optional per-round trace: round_best_id[r], round_best_score[r]. */
 int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o,

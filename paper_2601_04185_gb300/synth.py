@@ -419,3 +419,29 @@ def mapping_image(rng, n_src=8, width=560, height=560, f=480.0, inlier_prob=0.8,
         vis[s] = good.reshape(height, width)
     return dict(ref=cam(R0, t0), srcs=srcs, u=u, v=v, conf=conf, depth_gt=depth_gt, good=vis,
                 width=width, height=height)
+
+
+def to_bf16_bits(x):
+    """float32 array -> bfloat16 bit patterns (uint16), round to nearest even."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
+
+
+def retrieval_set(rng, n_db, n_query, dim, n_places=None, spread=0.35, noise=0.5):
+    """Global retrieval descriptors (stand-ins for MegaLoc / NetVLAD features of
+    the map images and the queries): database images are grouped in places
+    (a random unit direction each, images of a place scattered around it),
+    each query is a noisy view of one place; all L2-normalised, stored as
+    bfloat16.  Returns db (n_db, dim) and queries (n_query, dim) uint16 bit
+    patterns and the place of every query."""
+    n_places = n_places or max(1, n_db // 20)
+    centres = rng.normal(size=(n_places, dim)).astype(np.float32)
+    centres /= np.linalg.norm(centres, axis=1, keepdims=True)
+    place = rng.integers(0, n_places, n_db)
+    db = centres[place] + spread * rng.normal(size=(n_db, dim)).astype(np.float32) / np.sqrt(dim)
+    db /= np.linalg.norm(db, axis=1, keepdims=True)
+    qp = rng.integers(0, n_places, n_query)
+    q = centres[qp] + noise * rng.normal(size=(n_query, dim)).astype(np.float32) / np.sqrt(dim)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return to_bf16_bits(db), to_bf16_bits(q), qp
