@@ -158,6 +158,27 @@ int imloc_triangulate_depth_async(const imloc_camera* ref_cam, const imloc_pose*
                                   int64_t plane_stride, const imloc_triangulate_opts* opts, float* depth_out,
                                   uint8_t* inliers_out, void* stream);
 
+/* ---- retrieval nearest-neighbour search (ImLoc Sec. 3.1: a global
+ * retrieval feature per database image; Sec. 4.4 "Runtime": the nearest-
+ * neighbour search of the retrieval features on the GPU) -----------------
+ * queries: n_queries x dim, db: n_db x dim, bfloat16 bit patterns, row-major,
+ * device memory, 16-byte aligned; the caller L2-normalises the descriptors,
+ * so score = dot product = cosine similarity.  Writes, per query, the k best
+ * database rows by descending score (ties: lower index first) to out_score /
+ * out_index (device, n_queries x k; slots beyond n_db hold -inf / -1).
+ * Scores accumulate in FP32 on the tensor cores (bf16 products are exact).
+ * Asynchronous on `stream`; scratch from the context's workspace
+ * (4 * min(n_queries, 256) * n_db bytes of scores, n_db rounded up to a
+ * multiple of 4, plus the selection buffers).  The order is that of the
+ * scores' float bit patterns made monotone, so a NaN score (from non-finite
+ * descriptors) ranks above +inf with its sign bit clear, below -inf with it
+ * set.  IMLOC_ERR_INVALID_ARG unless 1 <= k <= 128, dim is a positive
+ * multiple of 8 and the pointers are 16-byte aligned; IMLOC_ERR_OOM if the
+ * workspace is too small. */
+int imloc_retrieve_topk_async(imloc_ctx* ctx, const uint16_t* queries, int32_t n_queries, const uint16_t* db,
+                              int64_t n_db, int32_t dim, int32_t k, float* out_score, int32_t* out_index,
+                              void* stream);
+
 /* ---- lifting (ImLoc Sec. 3.3, "Query Time Matching and 2D-3D Lifting") --
  * A match pairs a query pixel (q_u, q_v) with a database position (db_u,
  * db_v) in one view and carries the matcher confidence.  Matches are grouped

@@ -99,7 +99,7 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
            "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config",
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
-           "imloc_triangulate_depth_async"]
+           "imloc_triangulate_depth_async", "imloc_retrieve_topk_async"]
 
 _lib = None
 
@@ -139,6 +139,7 @@ def load(path: str = LIB_PATH):
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     L.imloc_score_config.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.imloc_retrieve_topk_async.argtypes = [V, V, C.c_int32, V, C.c_int64, C.c_int32, C.c_int32, V, V, V]
     L.imloc_triangulate_default_opts.argtypes = [P(TriangulateOpts)]
     L.imloc_triangulate_default_opts.restype = None
     L.imloc_triangulate_depth_async.argtypes = [P(Camera), P(Pose), C.c_int32, C.c_int32, P(Camera), P(Pose),
@@ -311,6 +312,27 @@ class Context:
             return None
         _check(rc, "imloc_score_config")
         return (t.value, h.value, tile.value)
+
+    # ---- retrieval nearest-neighbour search ----
+    def retrieve_topk(self, queries, db, k, out_score=None, out_index=None, stream=None):
+        """queries (Q, D), db (N, D): CUDA tensors of bfloat16 values or their
+        16-bit patterns (int16 / uint16), row-major.  Returns (scores float32
+        (Q, k), database indices int32 (Q, k)), best first."""
+        import torch
+
+        assert queries.is_cuda and db.is_cuda and queries.is_contiguous() and db.is_contiguous()
+        assert queries.element_size() == 2 and db.element_size() == 2 and queries.shape[1] == db.shape[1]
+        Q, D = queries.shape
+        N = db.shape[0]
+        if out_score is None:
+            out_score = torch.empty((Q, k), dtype=torch.float32, device=queries.device)
+        if out_index is None:
+            out_index = torch.empty((Q, k), dtype=torch.int32, device=queries.device)
+        _check(self.lib.imloc_retrieve_topk_async(self.h, C.c_void_p(queries.data_ptr()), Q, C.c_void_p(db.data_ptr()),
+                                                  N, D, k, C.c_void_p(out_score.data_ptr()),
+                                                  C.c_void_p(out_index.data_ptr()), _stream_handle(stream)),
+               "imloc_retrieve_topk_async")
+        return out_score, out_index
 
     def profile_read(self, reset=True):
         """{kernel name: (launches, total device ms)} of the traced launches."""

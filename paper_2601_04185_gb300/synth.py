@@ -445,3 +445,27 @@ def retrieval_set(rng, n_db, n_query, dim, n_places=None, spread=0.35, noise=0.5
     q = centres[qp] + noise * rng.normal(size=(n_query, dim)).astype(np.float32) / np.sqrt(dim)
     q /= np.linalg.norm(q, axis=1, keepdims=True)
     return to_bf16_bits(db), to_bf16_bits(q), qp
+
+
+def retrieval_set_torch(seed, n_db, n_query, dim, device, n_places=None, spread=0.35, noise=0.5):
+    """retrieval_set generated on the GPU with torch (the same construction, a
+    torch random stream): for benchmark sizes (10^5 x 8448) that numpy would
+    take long to draw.  Returns bfloat16 tensors db (n_db, dim), queries
+    (n_query, dim)."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    n_places = n_places or max(1, n_db // 20)
+    centres = torch.randn(n_places, dim, generator=g, device=device)
+    centres /= centres.norm(dim=1, keepdim=True)
+    place = torch.randint(0, n_places, (n_db,), generator=g, device=device)
+    db = torch.empty(n_db, dim, dtype=torch.bfloat16, device=device)
+    for b in range(0, n_db, 8192):
+        e = min(n_db, b + 8192)
+        x = centres[place[b:e]] + spread * torch.randn(e - b, dim, generator=g, device=device) / dim ** 0.5
+        db[b:e] = (x / x.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+    qp = torch.randint(0, n_places, (n_query,), generator=g, device=device)
+    q = centres[qp] + noise * torch.randn(n_query, dim, generator=g, device=device) / dim ** 0.5
+    q = (q / q.norm(dim=1, keepdim=True)).to(torch.bfloat16)
+    return db, q

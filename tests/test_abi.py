@@ -77,3 +77,4 @@ def test_triangulation_defaults_are_the_papers_constants(lib):
     assert o.angle_deg == 2.0            # 2-degree angular error threshold (Sec. 3.3)
     assert abs(o.conf_min - 0.05) < 1e-9 # matches with confidence >= 0.05 (Sec. 3.3)
     assert o.keep_more_than == 3         # keep depths with more than 3 inliers (Sec. 3.3)
+    assert lib.imloc_retrieve_topk_async(None, None, 1, None, 1, 8, 1, None, None, None) == -1
