@@ -51,6 +51,10 @@ class OrcResult(C.Structure):
                 ("status", C.c_int32)]
 
 
+class OrcRig(C.Structure):
+    _fields_ = [("n_cams", C.c_int64), ("cam", OrcCam * 8), ("R", (C.c_double * 9) * 8), ("t", (C.c_double * 3) * 8)]
+
+
 class OrcTriCam(C.Structure):
     _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
                 ("R", C.c_double * 9), ("t", C.c_double * 3)]
@@ -109,6 +113,20 @@ def lib():
         L.orc_bf16_to_double.argtypes = [C.c_uint16]
         L.orc_retrieve_topk.argtypes = [P(C.c_uint16), C.c_int64, P(C.c_uint16), C.c_int64, C.c_int64, C.c_int64,
                                         P(C.c_double), P(C.c_int64)]
+        L.orc_gp3p.restype = C.c_int
+        L.orc_gp3p.argtypes = [P(C.c_double)] * 6
+        L.orc_rig_score.restype = C.c_double
+        L.orc_rig_score.argtypes = [P(OrcCorr), P(C.c_int32), P(C.c_int64), C.c_int64, P(OrcRig), P(C.c_double),
+                                    P(C.c_double), C.c_double, P(C.c_int64)]
+        L.orc_rig_lo.restype = C.c_double
+        L.orc_rig_lo.argtypes = [P(OrcCorr), P(C.c_int32), P(C.c_int64), C.c_int64, P(OrcRig), C.c_double,
+                                 C.c_int64, P(C.c_double), P(C.c_double)]
+        L.orc_rig_refine.restype = C.c_int
+        L.orc_rig_refine.argtypes = [P(OrcCorr), P(C.c_int32), P(C.c_int64), C.c_int64, P(OrcRig), C.c_double,
+                                     C.c_double, C.c_int64, P(C.c_double), P(C.c_double)]
+        L.orc_rig_ransac.restype = C.c_int
+        L.orc_rig_ransac.argtypes = [P(OrcCorr), P(C.c_int32), P(OrcRig), P(OrcOpts), P(OrcResult), P(C.c_uint8),
+                                     P(C.c_int64), P(C.c_double), C.c_int64]
         L.orc_ransac_pnp.restype = C.c_int
         L.orc_ransac_pnp.argtypes = [P(OrcCorr), P(OrcCam), P(OrcOpts), P(OrcResult), P(C.c_uint8),
                                      P(C.c_int64), P(C.c_double), C.c_int64]
@@ -359,3 +377,78 @@ def retrieve_topk(queries_bf16, db_bf16, k):
     lib().orc_retrieve_topk(_ptr(q, C.c_uint16), Q, _ptr(d, C.c_uint16), N, D, k, _ptr(sc, C.c_double),
                             _ptr(ix, C.c_int64))
     return sc, ix
+
+
+# ---- generalized absolute pose of a camera rig (supplementary "LaMAR HoloLens Results") ----
+def rig(cams, R_cam, t_cam):
+    """cams: list of (fx, fy, cx, cy); R_cam, t_cam: cam_from_rig per camera."""
+    r = OrcRig()
+    r.n_cams = len(cams)
+    for k, K in enumerate(cams):
+        r.cam[k] = _cam(K)
+        r.R[k][:] = [float(a) for a in np.asarray(R_cam[k], np.float64).ravel()]
+        r.t[k][:] = [float(a) for a in np.asarray(t_cam[k], np.float64).ravel()]
+    return r
+
+
+def gp3p(origins, dirs, points):
+    """origins, dirs (unit), points: (3, 3) -> list of (R, t, lambdas), ascending lambda_1."""
+    o = np.ascontiguousarray(origins, np.float64).ravel().copy()
+    d = np.ascontiguousarray(dirs, np.float64).ravel().copy()
+    X = np.ascontiguousarray(points, np.float64).ravel().copy()
+    R = np.zeros(72); t = np.zeros(24); lam = np.zeros(24)
+    ns = lib().orc_gp3p(*[_ptr(a, C.c_double) for a in (o, d, X, R, t, lam)])
+    return [(R[9 * k:9 * k + 9].reshape(3, 3).copy(), t[3 * k:3 * k + 3].copy(), lam[3 * k:3 * k + 3].copy())
+            for k in range(ns)]
+
+
+def _pose(R, t):
+    return (np.ascontiguousarray(R, np.float64).ravel().copy(), np.ascontiguousarray(t, np.float64).ravel().copy())
+
+
+def rig_score(corr: Corr, cam_of, rg, R, t, tau, idx=None):
+    co = np.ascontiguousarray(cam_of, np.int32)
+    Rd, td = _pose(R, t)
+    cnt = C.c_int64(0)
+    ii = None if idx is None else np.ascontiguousarray(idx, np.int64)
+    s = lib().orc_rig_score(C.byref(corr.c), _ptr(co, C.c_int32), None if ii is None else _ptr(ii, C.c_int64),
+                            corr.n if ii is None else len(ii), C.byref(rg), _ptr(Rd, C.c_double),
+                            _ptr(td, C.c_double), tau, C.byref(cnt))
+    return s, cnt.value
+
+
+def rig_lo(corr: Corr, cam_of, rg, R, t, tau, iters=10, idx=None):
+    co = np.ascontiguousarray(cam_of, np.int32)
+    Rd, td = _pose(R, t)
+    ii = None if idx is None else np.ascontiguousarray(idx, np.int64)
+    s = lib().orc_rig_lo(C.byref(corr.c), _ptr(co, C.c_int32), None if ii is None else _ptr(ii, C.c_int64),
+                         corr.n if ii is None else len(ii), C.byref(rg), tau, iters, _ptr(Rd, C.c_double),
+                         _ptr(td, C.c_double))
+    return Rd.reshape(3, 3), td, s
+
+
+def rig_refine(corr: Corr, cam_of, rg, R, t, sel, cauchy_c, tau, iters=25):
+    co = np.ascontiguousarray(cam_of, np.int32)
+    Rd, td = _pose(R, t)
+    ss = np.ascontiguousarray(sel, np.int64)
+    steps = lib().orc_rig_refine(C.byref(corr.c), _ptr(co, C.c_int32), _ptr(ss, C.c_int64), len(ss), C.byref(rg),
+                                 cauchy_c, tau, iters, _ptr(Rd, C.c_double), _ptr(td, C.c_double))
+    return Rd.reshape(3, 3), td, steps
+
+
+def rig_ransac(corr: Corr, cam_of, rg, max_rounds=256, **kw):
+    o = default_opts(**kw)
+    opts = OrcOpts(**o)
+    co = np.ascontiguousarray(cam_of, np.int32)
+    res = OrcResult()
+    mask = np.zeros(max(corr.n, 1), dtype=np.uint8)
+    rb_id = np.full(max_rounds, -1, dtype=np.int64)
+    rb_sc = np.full(max_rounds, np.inf)
+    lib().orc_rig_ransac(C.byref(corr.c), _ptr(co, C.c_int32), C.byref(rg), C.byref(opts), C.byref(res),
+                         _ptr(mask, C.c_uint8), _ptr(rb_id, C.c_int64), _ptr(rb_sc, C.c_double), max_rounds)
+    nr = min(res.rounds, max_rounds)
+    return dict(status=res.status, R=np.array(res.R).reshape(3, 3), t=np.array(res.t),
+                R_best=np.array(res.R_best).reshape(3, 3), t_best=np.array(res.t_best), score=res.score,
+                num_inliers=res.num_inliers, subset_inliers=res.subset_inliers, iterations=res.iterations,
+                rounds=res.rounds, lo_count=res.lo_count, hypotheses=res.hypotheses, best_hyp=res.best_hyp,
+                inlier_mask=mask[:corr.n].astype(bool), round_best_id=rb_id[:nr], round_best_score=rb_sc[:nr])

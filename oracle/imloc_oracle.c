@@ -1008,3 +1008,523 @@ void orc_retrieve_topk(const uint16_t* queries, int64_t Q, const uint16_t* db, i
     free(sc);
     free(qd);
 }
+
+/* ==========================================================================
+ * Generalized absolute pose of a camera rig (supplementary "LaMAR HoloLens
+ * Results": queries taken by a multi-camera rig, a GPU generalized absolute
+ * pose estimator).  The rig pose is rig_from_world, X_r = R X_w + t; camera k
+ * of the rig sees X_c = R_k X_r + t_k through its own pinhole intrinsics.
+ * Scoring, LO, the adaptive stop and the final refinement are those of the
+ * single-camera loop with every correspondence reprojected into its camera.
+ * ========================================================================== */
+
+/* real roots of sum_k c[k] x^k for deg <= 8 (Durand-Kerner on the monic
+ * polynomial, Newton polish of the real ones); returns the count */
+static int poly_real_roots8(const double* c_in, int deg, double* roots)
+{
+    double c[9];
+    for (int k = 0; k <= deg; ++k) c[k] = c_in[k];
+    /* only an exactly vanishing leading coefficient lowers the degree: the
+     * coefficients carry powers of a length, so a small one is not negligible */
+    while (deg > 0 && c[deg] == 0.0) --deg;
+    if (deg == 0) return 0;
+    if (deg == 1) { roots[0] = -c[0] / c[1]; return 1; }
+    /* x = sigma y with sigma = |c0 / c_deg|^(1/deg): balanced coefficients, so
+     * that the iteration starts near the roots whatever their scale */
+    double sigma = 1.0;
+    if (c[0] != 0.0) sigma = pow(fabs(c[0] / c[deg]), 1.0 / deg);
+    double complex z[8];
+    double a[9];
+    for (int k = 0; k <= deg; ++k) a[k] = c[k] * pow(sigma, k) / (c[deg] * pow(sigma, deg));
+    double bound = 1.0;
+    for (int k = 0; k < deg; ++k) bound = fmax(bound, 1.0 + fabs(a[k]));
+    double complex seed = 0.4 + 0.9 * I;
+    double complex p = 1.0;
+    for (int k = 0; k < deg; ++k) { p *= seed; z[k] = p * (0.5 * bound); }
+    for (int it = 0; it < 5000; ++it) {
+        double change = 0.0;
+        for (int k = 0; k < deg; ++k) {
+            double complex num = 0.0;
+            for (int j = deg; j >= 0; --j) num = num * z[k] + a[j];
+            double complex den = 1.0;
+            for (int j = 0; j < deg; ++j)
+                if (j != k) den *= (z[k] - z[j]);
+            if (cabs(den) == 0.0) den = 1e-300;
+            double complex dz = num / den;
+            z[k] -= dz;
+            change = fmax(change, cabs(dz) / (1.0 + cabs(z[k])));
+        }
+        if (change < 1e-16) break;
+    }
+    int nr = 0;
+    for (int k = 0; k < deg; ++k) {
+        if (fabs(cimag(z[k])) > 1e-3 * (1.0 + cabs(z[k]))) continue;
+        double x = creal(z[k]) * sigma;
+        for (int it = 0; it < 8; ++it) {
+            double d = poly_deriv_eval(c, deg, x);
+            if (d == 0.0) break;
+            double step = poly_eval(c, deg, x) / d;
+            x -= step;
+            if (fabs(step) <= 1e-17 * (1.0 + fabs(x))) break;
+        }
+        roots[nr++] = x;
+    }
+    return nr;
+}
+
+static void poly_add_to(double* acc, const double* a, int da, double s)
+{
+    for (int k = 0; k <= da; ++k) acc[k] += s * a[k];
+}
+
+/* residuals of the three distance equations along the rays */
+static void gp3p_residual(const double o[9], const double d[9], const double D2[3], const double L[3], double f[3])
+{
+    static const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    for (int e = 0; e < 3; ++e) {
+        int i = pr[e][0], j = pr[e][1];
+        double v[3];
+        for (int a = 0; a < 3; ++a) v[a] = o[3 * i + a] + L[i] * d[3 * i + a] - o[3 * j + a] - L[j] * d[3 * j + a];
+        f[e] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2] - D2[e];
+    }
+}
+
+/* GP3P.  The points must land on the rays o_i + lambda_i d_i (rig frame,
+ * |d_i| = 1).  A rigid motion keeps the pairwise distances, so for i < j
+ *   |o_i + lambda_i d_i - o_j - lambda_j d_j|^2 = |X_i - X_j|^2,
+ * three quadrics in the lambdas; a real solution gives a triangle congruent to
+ * the world one and hence exactly one proper rigid motion.  Written out, pair
+ * (i, j) reads lambda_i^2 + lambda_j^2 - 2 c lambda_i lambda_j + 2 a lambda_i
+ * - 2 b lambda_j + e = 0 with c = d_i.d_j, a = d_i.(o_i - o_j),
+ * b = d_j.(o_i - o_j), e = |o_i - o_j|^2 - |X_i - X_j|^2.  With lambda_1 as
+ * the parameter: pair (1,2) is a monic quadratic G in lambda_2 and pair (1,3)
+ * one in lambda_3; subtracting both from pair (2,3) leaves the bilinear
+ * A l2 l3 + B l2 + C l3 + E = 0, so l3 = -(B l2 + E) / (A l2 + C); putting
+ * that into pair (1,3) gives a second quadratic F in lambda_2; the resultant
+ * of F and G in lambda_2 is a polynomial of degree 8 in lambda_1. */
+int orc_gp3p(const double o[9], const double d[9], const double X[9], double R_out[72], double t_out[24],
+             double lambda_out[24])
+{
+    double D2[3];
+    static const int pr[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    double cc[3], aa[3], bb[3], ee[3];
+    for (int e = 0; e < 3; ++e) {
+        int i = pr[e][0], j = pr[e][1];
+        double oij[3], dx[3];
+        for (int a = 0; a < 3; ++a) { oij[a] = o[3 * i + a] - o[3 * j + a]; dx[a] = X[3 * i + a] - X[3 * j + a]; }
+        D2[e] = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+        cc[e] = d[3 * i] * d[3 * j] + d[3 * i + 1] * d[3 * j + 1] + d[3 * i + 2] * d[3 * j + 2];
+        aa[e] = d[3 * i] * oij[0] + d[3 * i + 1] * oij[1] + d[3 * i + 2] * oij[2];
+        bb[e] = d[3 * j] * oij[0] + d[3 * j + 1] * oij[1] + d[3 * j + 2] * oij[2];
+        ee[e] = oij[0] * oij[0] + oij[1] * oij[1] + oij[2] * oij[2] - D2[e];
+    }
+    /* polynomials in lambda_1, ascending coefficients */
+    double p[2] = {bb[0], cc[0]}, q[3] = {ee[0], 2.0 * aa[0], 1.0};   /* G: l2^2 - 2 p l2 + q */
+    double r[2] = {bb[1], cc[1]}, s[3] = {ee[1], 2.0 * aa[1], 1.0};   /* l3^2 - 2 r l3 + s */
+    double A = -2.0 * cc[2];
+    double B[2] = {2.0 * (p[0] + aa[2]), 2.0 * p[1]};
+    double Cc[2] = {2.0 * (r[0] - bb[2]), 2.0 * r[1]};
+    double E[3] = {ee[2] - q[0] - s[0], -q[1] - s[1], -q[2] - s[2]};
+    /* F = f2 l2^2 + f1 l2 + f0 */
+    double f2[3] = {0}, f1[4] = {0}, f0[5] = {0}, tmp[5], tmp2[5];
+    poly_mul(B, 1, B, 1, tmp);        poly_add_to(f2, tmp, 2, 1.0);
+    poly_mul(r, 1, B, 1, tmp);        poly_add_to(f2, tmp, 2, 2.0 * A);
+    poly_add_to(f2, s, 2, A * A);
+    poly_mul(B, 1, E, 2, tmp);        poly_add_to(f1, tmp, 3, 2.0);
+    poly_mul(B, 1, Cc, 1, tmp2);      poly_mul(r, 1, tmp2, 2, tmp); poly_add_to(f1, tmp, 3, 2.0);
+    poly_mul(r, 1, E, 2, tmp);        poly_add_to(f1, tmp, 3, 2.0 * A);
+    poly_mul(s, 2, Cc, 1, tmp);       poly_add_to(f1, tmp, 3, 2.0 * A);
+    poly_mul(E, 2, E, 2, tmp);        poly_add_to(f0, tmp, 4, 1.0);
+    poly_mul(r, 1, E, 2, tmp2);       poly_mul(tmp2, 3, Cc, 1, tmp); poly_add_to(f0, tmp, 4, 2.0);
+    poly_mul(Cc, 1, Cc, 1, tmp2);     poly_mul(s, 2, tmp2, 2, tmp); poly_add_to(f0, tmp, 4, 1.0);
+    /* G = l2^2 + g1 l2 + g0 */
+    double g1[2] = {-2.0 * p[0], -2.0 * p[1]}, g0[3] = {q[0], q[1], q[2]};
+    /* resultant of two quadratics: (f2 g0 - f0)^2 - (f2 g1 - f1)(f1 g0 - f0 g1) */
+    double t1[5] = {0}, t2[4] = {0}, t3[6] = {0}, oct[9] = {0}, w[9];
+    poly_mul(f2, 2, g0, 2, tmp);      poly_add_to(t1, tmp, 4, 1.0); poly_add_to(t1, f0, 4, -1.0);
+    poly_mul(f2, 2, g1, 1, tmp);      poly_add_to(t2, tmp, 3, 1.0); poly_add_to(t2, f1, 3, -1.0);
+    double u6[6];
+    poly_mul(f1, 3, g0, 2, u6);       poly_add_to(t3, u6, 5, 1.0);
+    poly_mul(f0, 4, g1, 1, u6);       poly_add_to(t3, u6, 5, -1.0);
+    poly_mul(t1, 4, t1, 4, w);        poly_add_to(oct, w, 8, 1.0);
+    poly_mul(t2, 3, t3, 5, w);        poly_add_to(oct, w, 8, -1.0);
+
+    double l1s[8];
+    int nr = poly_real_roots8(oct, 8, l1s);
+    double sol[8][3], sol_res[8];
+    int ns = 0;
+    for (int k = 0; k < nr; ++k) {
+        double l1 = l1s[k];
+        if (!(l1 > 0.0)) continue;
+        double f2v = poly_eval(f2, 2, l1), f1v = poly_eval(f1, 3, l1), f0v = poly_eval(f0, 4, l1);
+        double g1v = poly_eval(g1, 1, l1), g0v = poly_eval(g0, 2, l1);
+        /* lambda_2 candidates: the common root of F and G, and both roots of G
+         * (the common-root formula loses accuracy when two roots are close);
+         * every candidate is verified on the distance equations below */
+        double l2c[3];
+        int n2 = 0;
+        double den = f1v - f2v * g1v;
+        if (fabs(den) > 1e-12 * (fabs(f1v) + fabs(f2v * g1v) + 1e-300)) l2c[n2++] = -(f0v - f2v * g0v) / den;
+        {
+            /* a slightly negative discriminant from rounding: the double root */
+            double disc = 0.25 * g1v * g1v - g0v;
+            if (disc >= -1e-8 * (0.25 * g1v * g1v + fabs(g0v))) {
+                disc = fmax(disc, 0.0);
+                l2c[n2++] = -0.5 * g1v + sqrt(disc);
+                l2c[n2++] = -0.5 * g1v - sqrt(disc);
+            }
+        }
+        for (int a2 = 0; a2 < n2; ++a2) {
+            double l2 = l2c[a2];
+            double Bv = poly_eval(B, 1, l1), Cv = poly_eval(Cc, 1, l1), Ev = poly_eval(E, 2, l1);
+            double rv = poly_eval(r, 1, l1), sv = poly_eval(s, 2, l1);
+            double l3c[3];
+            int n3 = 0;
+            double den3 = A * l2 + Cv;
+            if (fabs(den3) > 1e-12 * (fabs(A * l2) + fabs(Cv) + 1e-300)) l3c[n3++] = -(Bv * l2 + Ev) / den3;
+            {
+                double disc = rv * rv - sv;
+                if (disc >= -1e-8 * (rv * rv + fabs(sv))) {
+                    disc = fmax(disc, 0.0);
+                    l3c[n3++] = rv + sqrt(disc);
+                    l3c[n3++] = rv - sqrt(disc);
+                }
+            }
+            for (int a3 = 0; a3 < n3; ++a3) {
+                double L[3] = {l1, l2, l3c[a3]};
+                /* Newton on the three distance equations */
+                for (int it = 0; it < 50; ++it) {
+                    double f[3], J[3][3] = {{0}}, dl[3];
+                    gp3p_residual(o, d, D2, L, f);
+                    for (int e = 0; e < 3; ++e) {
+                        int i = pr[e][0], j = pr[e][1];
+                        double v[3];
+                        for (int a = 0; a < 3; ++a)
+                            v[a] = o[3 * i + a] + L[i] * d[3 * i + a] - o[3 * j + a] - L[j] * d[3 * j + a];
+                        J[e][i] = 2.0 * (v[0] * d[3 * i] + v[1] * d[3 * i + 1] + v[2] * d[3 * i + 2]);
+                        J[e][j] = -2.0 * (v[0] * d[3 * j] + v[1] * d[3 * j + 1] + v[2] * d[3 * j + 2]);
+                    }
+                    if (!solve3(J, f, dl)) break;
+                    double mx = 0.0;
+                    for (int a = 0; a < 3; ++a) { L[a] -= dl[a]; mx = fmax(mx, fabs(dl[a]) / (1.0 + fabs(L[a]))); }
+                    if (mx < 1e-16) break;
+                }
+                double f[3];
+                gp3p_residual(o, d, D2, L, f);
+                int ok = L[0] > 0.0 && L[1] > 0.0 && L[2] > 0.0;
+                double res = 0.0;
+                for (int e = 0; e < 3; ++e) {
+                    ok = ok && fabs(f[e]) <= 1e-8 * (1.0 + D2[e]);
+                    res = fmax(res, fabs(f[e]) / (1.0 + D2[e]));
+                }
+                /* one solution: closer than 1e-6 (relative) in all three depths
+                 * (a nearly double solution pins down only to ~sqrt(eps)); of
+                 * two such, the one with the smaller residual stays */
+                for (int j = 0; j < ns && ok; ++j)
+                    if (fabs(sol[j][0] - L[0]) <= 1e-6 * (1.0 + L[0]) && fabs(sol[j][1] - L[1]) <= 1e-6 * (1.0 + L[1]) &&
+                        fabs(sol[j][2] - L[2]) <= 1e-6 * (1.0 + L[2])) {
+                        if (res < sol_res[j]) { memcpy(sol[j], L, sizeof(L)); sol_res[j] = res; }
+                        ok = 0;
+                    }
+                if (ok && ns < 8) { memcpy(sol[ns], L, sizeof(L)); sol_res[ns] = res; ++ns; }
+            }
+        }
+    }
+    /* ascending lambda_1 */
+    for (int a = 1; a < ns; ++a)
+        for (int b = a; b > 0 && sol[b][0] < sol[b - 1][0]; --b) {
+            double t3s[3];
+            memcpy(t3s, sol[b], sizeof(t3s));
+            memcpy(sol[b], sol[b - 1], sizeof(t3s));
+            memcpy(sol[b - 1], t3s, sizeof(t3s));
+        }
+    for (int k = 0; k < ns; ++k) {
+        double P[9];
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 3; ++a) P[3 * i + a] = o[3 * i + a] + sol[k][i] * d[3 * i + a];
+        horn_absolute_orientation(X, P, &R_out[9 * k], &t_out[3 * k]);
+        if (lambda_out)
+            for (int i = 0; i < 3; ++i) lambda_out[3 * k + i] = sol[k][i];
+    }
+    return ns;
+}
+
+/* X_r = R X_w + t, X_c = R_k X_r + t_k; 0 if the point is not in front of its camera */
+static int rig_residual(const orc_corr* c, const int32_t* cam_of, int64_t i, const orc_rig* rig, const double R[9],
+                        const double t[3], double Xr[3], double Xc[3], double r[2])
+{
+    const double* Xw = &c->X[3 * i];
+    const int k = cam_of[i];
+    const double* Rk = rig->R[k];
+    const double* tk = rig->t[k];
+    for (int a = 0; a < 3; ++a) Xr[a] = R[3 * a] * Xw[0] + R[3 * a + 1] * Xw[1] + R[3 * a + 2] * Xw[2] + t[a];
+    for (int a = 0; a < 3; ++a) Xc[a] = Rk[3 * a] * Xr[0] + Rk[3 * a + 1] * Xr[1] + Rk[3 * a + 2] * Xr[2] + tk[a];
+    if (!(Xc[2] > 0.0)) return 0;
+    const orc_cam* cam = &rig->cam[k];
+    r[0] = cam->fx * Xc[0] / Xc[2] + cam->cx - c->x[i];
+    r[1] = cam->fy * Xc[1] / Xc[2] + cam->cy - c->y[i];
+    return 1;
+}
+
+double orc_rig_score(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m, const orc_rig* rig,
+                     const double R[9], const double t[3], double tau, int64_t* inliers)
+{
+    double tau2 = tau * tau, s = 0.0;
+    int64_t cnt = 0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = idx ? idx[k] : k;
+        double Xr[3], Xc[3], r[2];
+        double r2 = tau2;
+        if (rig_residual(c, cam_of, i, rig, R, t, Xr, Xc, r)) {
+            r2 = r[0] * r[0] + r[1] * r[1];
+            if (r2 < tau2) ++cnt;
+        }
+        s += c->w[i] * (r2 < tau2 ? r2 : tau2);
+    }
+    if (inliers) *inliers = cnt;
+    return s;
+}
+
+/* pixel Jacobian w.r.t. the left perturbation of the rig pose,
+ * X_r' = Exp(w) X_r + v:  d X_c / d(w, v) = R_k [ -[X_r]_x | I ] */
+static void rig_jacobian(const double Xr[3], const double Xc[3], const double Rk[9], const orc_cam* cam,
+                         double J[2][6])
+{
+    double X = Xc[0], Y = Xc[1], Z = Xc[2];
+    double du[3] = {cam->fx / Z, 0.0, -cam->fx * X / (Z * Z)};
+    double dv[3] = {0.0, cam->fy / Z, -cam->fy * Y / (Z * Z)};
+    double M[3][3] = {{0.0, Xr[2], -Xr[1]}, {-Xr[2], 0.0, Xr[0]}, {Xr[1], -Xr[0], 0.0}};
+    double RM[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) RM[a][b] = Rk[3 * a] * M[0][b] + Rk[3 * a + 1] * M[1][b] + Rk[3 * a + 2] * M[2][b];
+    for (int b = 0; b < 3; ++b) {
+        J[0][b] = du[0] * RM[0][b] + du[1] * RM[1][b] + du[2] * RM[2][b];
+        J[1][b] = dv[0] * RM[0][b] + dv[1] * RM[1][b] + dv[2] * RM[2][b];
+        J[0][3 + b] = du[0] * Rk[b] + du[1] * Rk[3 + b] + du[2] * Rk[6 + b];
+        J[1][3 + b] = dv[0] * Rk[b] + dv[1] * Rk[3 + b] + dv[2] * Rk[6 + b];
+    }
+}
+
+static double rig_robust_cost(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m,
+                              const orc_rig* rig, int loss, double tau, double cs, const double R[9],
+                              const double t[3])
+{
+    double tau2 = tau * tau, cs2 = cs * cs, s = 0.0;
+    for (int64_t k = 0; k < m; ++k) {
+        int64_t i = idx ? idx[k] : k;
+        double Xr[3], Xc[3], r[2], r2 = tau2;
+        if (rig_residual(c, cam_of, i, rig, R, t, Xr, Xc, r)) r2 = r[0] * r[0] + r[1] * r[1];
+        if (loss == LOSS_TRUNCATED) s += c->w[i] * (r2 < tau2 ? r2 : tau2);
+        else s += c->w[i] * cs2 * log1p(r2 / cs2);
+    }
+    return s;
+}
+
+/* the Gauss-Newton schedule of the single-camera loop, rig residuals */
+static int rig_gauss_newton(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m,
+                            const orc_rig* rig, int loss, double tau, double cs, int64_t iters, double R[9],
+                            double t[3], double* cost_io)
+{
+    double tau2 = tau * tau, cs2 = cs * cs;
+    double cost = rig_robust_cost(c, cam_of, idx, m, rig, loss, tau, cs, R, t);
+    int accepted_steps = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        double H[36] = {0}, g[6] = {0};
+        int64_t used = 0;
+        for (int64_t k = 0; k < m; ++k) {
+            int64_t i = idx ? idx[k] : k;
+            double Xr[3], Xc[3], r[2];
+            if (!rig_residual(c, cam_of, i, rig, R, t, Xr, Xc, r)) continue;
+            double r2 = r[0] * r[0] + r[1] * r[1];
+            double wt;
+            if (loss == LOSS_TRUNCATED) {
+                if (!(r2 < tau2)) continue;
+                wt = c->w[i];
+            } else {
+                wt = c->w[i] / (1.0 + r2 / cs2);
+            }
+            double J[2][6];
+            rig_jacobian(Xr, Xc, rig->R[cam_of[i]], &rig->cam[cam_of[i]], J);
+            for (int a = 0; a < 6; ++a) {
+                g[a] += wt * (J[0][a] * r[0] + J[1][a] * r[1]);
+                for (int b = 0; b < 6; ++b) H[6 * a + b] += wt * (J[0][a] * J[0][b] + J[1][a] * J[1][b]);
+            }
+            ++used;
+        }
+        if (used < 3) break;
+        double mu = 0.0;
+        int ok = 0;
+        double d[6], Rn[9], tn[3], cn = cost;
+        for (int attempt = 0; attempt < 4; ++attempt) {
+            double Hd[36], mg[6];
+            memcpy(Hd, H, sizeof(Hd));
+            for (int a = 0; a < 6; ++a) { Hd[7 * a] += mu * H[7 * a]; mg[a] = -g[a]; }
+            if (cholesky_solve6(Hd, mg, d)) {
+                apply_update(d, R, t, Rn, tn);
+                cn = rig_robust_cost(c, cam_of, idx, m, rig, loss, tau, cs, Rn, tn);
+                if (cn < cost) { ok = 1; break; }
+            }
+            mu = (mu == 0.0) ? 1e-3 : mu * 10.0;
+        }
+        if (!ok) break;
+        const double decrease = cost - cn;
+        memcpy(R, Rn, sizeof(Rn));
+        memcpy(t, tn, sizeof(tn));
+        ++accepted_steps;
+        double dn = 0;
+        for (int a = 0; a < 6; ++a) dn += d[a] * d[a];
+        const int converged = sqrt(dn) < 1e-10 || decrease < 1e-6 * cost;
+        cost = cn;
+        if (converged) break;
+    }
+    *cost_io = cost;
+    return accepted_steps;
+}
+
+double orc_rig_lo(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m, const orc_rig* rig,
+                  double tau, int64_t iters, double R[9], double t[3])
+{
+    double cost;
+    rig_gauss_newton(c, cam_of, idx, m, rig, LOSS_TRUNCATED, tau, 1.0, iters, R, t, &cost);
+    return cost;
+}
+
+int orc_rig_refine(const orc_corr* c, const int32_t* cam_of, const int64_t* sel, int64_t n_sel, const orc_rig* rig,
+                   double cauchy_c, double tau, int64_t iters, double R[9], double t[3])
+{
+    double cost;
+    return rig_gauss_newton(c, cam_of, sel, n_sel, rig, LOSS_CAUCHY, tau, cauchy_c, iters, R, t, &cost);
+}
+
+/* ray of correspondence i in the rig frame: origin = centre of its camera,
+ * direction = its unit bearing rotated into the rig */
+static void rig_ray(const orc_corr* c, const int32_t* cam_of, int64_t i, const orc_rig* rig, double o[3],
+                    double d[3])
+{
+    const int k = cam_of[i];
+    const orc_cam* cam = &rig->cam[k];
+    const double* Rk = rig->R[k];
+    const double* tk = rig->t[k];
+    double b[3] = {(c->x[i] - cam->cx) / cam->fx, (c->y[i] - cam->cy) / cam->fy, 1.0};
+    double n = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+    for (int a = 0; a < 3; ++a) b[a] /= n;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = Rk[a] * b[0] + Rk[3 + a] * b[1] + Rk[6 + a] * b[2];
+        o[a] = -(Rk[a] * tk[0] + Rk[3 + a] * tk[1] + Rk[6 + a] * tk[2]);
+    }
+}
+
+/* The LO-RANSAC loop of the single-camera case with GP3P hypotheses
+ * (pose id = 8 * sample + solution index) and rig residuals. */
+int orc_rig_ransac(const orc_corr* c, const int32_t* cam_of, const orc_rig* rig, const orc_opts* o,
+                   orc_result* res, uint8_t* inlier_mask, int64_t* round_best_id, double* round_best_score,
+                   int64_t max_rounds)
+{
+    memset(res, 0, sizeof(*res));
+    res->best_hyp = -1;
+    int64_t n = c->n;
+    if (n < 3) { res->status = -1; return -1; }
+    int64_t m = n < o->max_score_corr ? n : o->max_score_corr;
+    int64_t* idx = (int64_t*)malloc(sizeof(int64_t) * (size_t)m);
+    orc_subsample(n, m, idx);
+    int64_t total = o->max_iters, batch = o->batch;
+
+    double best_R[9], best_t[3], best_score = INFINITY;
+    int have_best = 0;
+    int64_t subset_inliers = 0, hyps = 0, rounds = 0, iters = 0;
+    for (int64_t r = 0;; ++r) {
+        int64_t s0 = r * batch, s1 = s0 + batch < total ? s0 + batch : total;
+        if (s0 >= total) break;
+        double rb_score = INFINITY, rb_R[9], rb_t[3];
+        int64_t rb_id = -1;
+        for (int64_t s = s0; s < s1; ++s) {
+            int64_t tri[3];
+            if (orc_sample(o->seed, o->query_id, (uint32_t)s, m, tri) < 0) continue;
+            double ro[9], rd[9], X[9];
+            for (int k = 0; k < 3; ++k) {
+                int64_t i = idx[tri[k]];
+                rig_ray(c, cam_of, i, rig, &ro[3 * k], &rd[3 * k]);
+                for (int a = 0; a < 3; ++a) X[3 * k + a] = c->X[3 * i + a];
+            }
+            double Rs[72], ts[24];
+            int ns = orc_gp3p(ro, rd, X, Rs, ts, NULL);
+            for (int k = 0; k < ns; ++k) {
+                double sc = orc_rig_score(c, cam_of, idx, m, rig, &Rs[9 * k], &ts[3 * k], o->tau, NULL);
+                ++hyps;
+                if (sc < rb_score) {
+                    rb_score = sc;
+                    rb_id = 8 * s + k;
+                    memcpy(rb_R, &Rs[9 * k], sizeof(rb_R));
+                    memcpy(rb_t, &ts[3 * k], sizeof(rb_t));
+                }
+            }
+        }
+        if (r < max_rounds) {
+            if (round_best_id) round_best_id[r] = rb_id;
+            if (round_best_score) round_best_score[r] = rb_score;
+        }
+        if (rb_id >= 0 && rb_score < best_score) {
+            memcpy(best_R, rb_R, sizeof(rb_R));
+            memcpy(best_t, rb_t, sizeof(rb_t));
+            best_score = rb_score;
+            res->best_hyp = rb_id;
+            have_best = 1;
+            if (o->lo_enabled) {
+                double lR[9], lt[3];
+                memcpy(lR, best_R, sizeof(lR));
+                memcpy(lt, best_t, sizeof(lt));
+                double ls = orc_rig_lo(c, cam_of, idx, m, rig, o->tau, o->lo_iters, lR, lt);
+                res->lo_count++;
+                if (ls < best_score) {
+                    memcpy(best_R, lR, sizeof(lR));
+                    memcpy(best_t, lt, sizeof(lt));
+                    best_score = ls;
+                }
+            }
+            orc_rig_score(c, cam_of, idx, m, rig, best_R, best_t, o->tau, &subset_inliers);
+        }
+        iters = s1;
+        rounds = r + 1;
+        if (iters >= total) break;
+        if (o->p_miss > 0.0 && have_best &&
+            (double)iters >= orc_needed_iters((double)subset_inliers / (double)m, o->p_miss))
+            break;
+    }
+    res->iterations = iters;
+    res->rounds = rounds;
+    res->hypotheses = hyps;
+    if (!have_best) { free(idx); res->status = -1; return -1; }
+    memcpy(res->R_best, best_R, sizeof(best_R));
+    memcpy(res->t_best, best_t, sizeof(best_t));
+    res->score = best_score;
+    res->subset_inliers = subset_inliers;
+
+    double R[9], t[3];
+    memcpy(R, best_R, sizeof(R));
+    memcpy(t, best_t, sizeof(t));
+    double tau2 = o->tau * o->tau;
+    if (o->final_enabled) {
+        int64_t* sel = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        int64_t ns = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            double Xr[3], Xc[3], rr[2];
+            if (rig_residual(c, cam_of, i, rig, R, t, Xr, Xc, rr) && rr[0] * rr[0] + rr[1] * rr[1] < tau2)
+                sel[ns++] = i;
+        }
+        orc_rig_refine(c, cam_of, sel, ns, rig, o->cauchy_scale, o->tau, o->final_iters, R, t);
+        free(sel);
+    }
+    memcpy(res->R, R, sizeof(R));
+    memcpy(res->t, t, sizeof(t));
+    int64_t cnt = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double Xr[3], Xc[3], rr[2];
+        int in = rig_residual(c, cam_of, i, rig, R, t, Xr, Xc, rr) && rr[0] * rr[0] + rr[1] * rr[1] < tau2;
+        if (inlier_mask) inlier_mask[i] = (uint8_t)in;
+        cnt += in;
+    }
+    res->num_inliers = cnt;
+    free(idx);
+    res->status = 0;
+    return 0;
+}

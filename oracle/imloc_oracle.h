@@ -24,6 +24,9 @@
  *   orc_depth_*_log8  Sec. 3.3 "Data Compression" and Sec. 4.3 "Depth
  *                     Quantization" (depth clipped to [0.25, 128] m and
  *                     quantized in log space with 256 levels)
+ *   orc_gp3p, orc_rig_*  supplementary "LaMAR HoloLens Results" (generalized
+ *                     absolute pose of a multi-camera rig: the Sec. 3.3 loop
+ *                     with a generalized P3P and per-camera residuals)
  *   orc_retrieve_topk Sec. 3.1 / Sec. 4.4 "Runtime" (nearest-neighbour
  *                     search of global retrieval features: top-K database
  *                     images by descriptor dot product)
@@ -195,6 +198,35 @@ void orc_triangulate_depth(const orc_tri_cam* ref, int64_t width, int64_t height
 double orc_bf16_to_double(uint16_t bits);
 void orc_retrieve_topk(const uint16_t* queries, int64_t Q, const uint16_t* db, int64_t N, int64_t D,
                        int64_t K, double* out_score, int64_t* out_index);
+
+/* ---- generalized absolute pose of a camera rig -----------------------------
+ * The rig pose is rig_from_world (X_r = R X_w + t); camera k sees
+ * X_c = R[k] X_r + t[k] (cam_from_rig) through intrinsics cam[k].  Every
+ * correspondence i belongs to camera cam_of[i].                           */
+#define ORC_RIG_MAX_CAMS 8
+typedef struct {
+    int64_t n_cams;
+    orc_cam cam[ORC_RIG_MAX_CAMS];
+    double R[ORC_RIG_MAX_CAMS][9];
+    double t[ORC_RIG_MAX_CAMS][3];
+} orc_rig;
+
+/* GP3P: every rig pose with R X_i + t = o_i + lambda_i d_i, lambda_i > 0, for
+ * rays with origins o_i and unit directions d_i in the rig frame; sorted by
+ * ascending lambda_1.  Returns the count (0..8).                        */
+int orc_gp3p(const double o[9], const double d[9], const double X[9], double R_out[72], double t_out[24],
+             double lambda_out[24]);
+double orc_rig_score(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m, const orc_rig* rig,
+                     const double R[9], const double t[3], double tau, int64_t* inliers);
+double orc_rig_lo(const orc_corr* c, const int32_t* cam_of, const int64_t* idx, int64_t m, const orc_rig* rig,
+                  double tau, int64_t iters, double R[9], double t[3]);
+int orc_rig_refine(const orc_corr* c, const int32_t* cam_of, const int64_t* sel, int64_t n_sel, const orc_rig* rig,
+                   double cauchy_c, double tau, int64_t iters, double R[9], double t[3]);
+/* The loop of orc_ransac_pnp with GP3P hypotheses (pose id = 8 * sample + k)
+ * and rig residuals; the result pose is rig_from_world.                  */
+int orc_rig_ransac(const orc_corr* c, const int32_t* cam_of, const orc_rig* rig, const orc_opts* o,
+                   orc_result* res, uint8_t* inlier_mask, int64_t* round_best_id, double* round_best_score,
+                   int64_t max_rounds);
 
 /* Optional per-round trace: round_best_id[r], round_best_score[r]. */
 int orc_ransac_pnp(const orc_corr* c, const orc_cam* cam, const orc_opts* o,

@@ -469,3 +469,57 @@ def retrieval_set_torch(seed, n_db, n_query, dim, device, n_places=None, spread=
     q = centres[qp] + noise * torch.randn(n_query, dim, generator=g, device=device) / dim ** 0.5
     q = (q / q.norm(dim=1, keepdim=True)).to(torch.bfloat16)
     return db, q
+
+
+# ---------------------------------------------------------------------------
+# Multi-camera rig queries (generalized absolute pose)
+# ---------------------------------------------------------------------------
+def rig_layout(rng, n_cams=4, yaw_deg=(-60.0, -20.0, 20.0, 60.0), baseline=0.1):
+    """A head-mounted rig in the manner of the HoloLens tracking cameras:
+    camera k looks out at yaw yaw_deg[k] about the rig's y axis (with a small
+    random tilt), centred within `baseline` metres of the rig origin.  Returns
+    cam_from_rig rotations and translations (X_c = R_k X_r + t_k)."""
+    Rs, ts = [], []
+    for k in range(n_cams):
+        yaw = math.radians(yaw_deg[k % len(yaw_deg)])
+        R = axis_angle([0.0, 1.0, 0.0], yaw) @ axis_angle(rng.normal(size=3), rng.uniform(0, math.radians(5)))
+        c = rng.uniform(-baseline, baseline, 3)
+        Rs.append(R)
+        ts.append(-R @ c)
+    return Rs, ts
+
+
+def rig_query(rng, n_per_cam=500, inlier_ratio=0.4, n_cams=4, width=640, height=480, f=450.0, noise_px=1.0,
+              depth_range=(1.0, 15.0), weights="conf", baseline=0.1):
+    """Correspondences of one rig query with a known rig pose (rig_from_world,
+    X_r = R X_w + t).  Per camera, as direct_query: a uniform pixel and depth
+    back-projected into the world; inliers observed with N(0, noise_px) noise,
+    outliers at a uniform pixel.  Correspondences are grouped by camera; `cam`
+    gives each one's camera."""
+    R_cam, t_cam = rig_layout(rng, n_cams, baseline=baseline)
+    R = random_rotation(rng)
+    t = rng.normal(size=3)
+    cx, cy = width / 2.0, height / 2.0
+    xs, ys, Xs, ws, cams, inls = [], [], [], [], [], []
+    for k in range(n_cams):
+        n = n_per_cam
+        u = rng.uniform(0, width, n)
+        v = rng.uniform(0, height, n)
+        d = rng.uniform(depth_range[0], depth_range[1], n)
+        Xc = np.stack([(u - cx) / f * d, (v - cy) / f * d, d], axis=1)
+        Xr = (Xc - t_cam[k]) @ R_cam[k]
+        Xw = (Xr - t) @ R
+        n_in = int(round(inlier_ratio * n))
+        inl = np.zeros(n, dtype=bool)
+        inl[rng.permutation(n)[:n_in]] = True
+        xs.append(np.where(inl, u + rng.normal(0, noise_px, n), rng.uniform(0, width, n)))
+        ys.append(np.where(inl, v + rng.normal(0, noise_px, n), rng.uniform(0, height, n)))
+        Xs.append(Xw)
+        ws.append(np.ones(n) if weights == "ones" else np.where(inl, rng.uniform(0.3, 1.0, n),
+                                                                 rng.uniform(0.05, 1.0, n)))
+        cams.append(np.full(n, k, np.int32))
+        inls.append(inl)
+    return dict(x=np.concatenate(xs).astype(np.float32), y=np.concatenate(ys).astype(np.float32),
+                X=np.concatenate(Xs).astype(np.float32), w=np.concatenate(ws).astype(np.float32),
+                cam=np.concatenate(cams), K=[(float(f), float(f), cx, cy)] * n_cams, R_cam=R_cam, t_cam=t_cam,
+                width=width, height=height, R_gt=R, t_gt=t, inlier=np.concatenate(inls))
