@@ -319,6 +319,37 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
                                  const imloc_ransac_opts* opts, imloc_result* d_results,
                                  uint8_t* d_masks, void* stream);
 
+/* ---- generalized absolute pose of a multi-camera rig (ImLoc supplementary
+ * "LaMAR HoloLens Results": queries taken by a camera rig) ----------------
+ * The query is a rig of n_cams pinhole cameras with known cam_from_rig poses
+ * (X_c = R X_r + t); every correspondence carries the index of the camera
+ * that observed it (d_cam, device int32, same offsets as the
+ * correspondences).  The pose estimated is rig_from_world (X_r = R X_w + t).
+ * The loop is that of imloc_ransac_pnp with two changes: the minimal solver
+ * is a generalized P3P (the rig poses putting three points on their cameras'
+ * rays at positive depth, at most 8 per minimal set, ordered by ascending
+ * depth along the first ray; pose id = 8 * sample + solution index), and
+ * each residual is the reprojection error in the correspondence's own
+ * camera.  Options as imloc_ransac_opts; enumerate_all must be 0,
+ * max_iters <= 2^28; p3p_fp64_polish and lo_fp64_accumulate are ignored.
+ * Query q uses [d_offsets[q], d_offsets[q+1]) of `corr` and rigs[q] /
+ * opts[q] (host arrays).  Results (R, t, R_best, t_best are rig_from_world)
+ * go to d_results[q] (device); masks, if d_masks != NULL, as in
+ * imloc_ransac_pnp_batch_async.  A query with a camera index outside
+ * [0, n_cams) gets status IMLOC_ERR_INVALID_ARG.  Synchronous: returns once
+ * the results are written (it reads back one word per wave of rounds). */
+#define IMLOC_RIG_MAX_CAMERAS 8
+typedef struct {
+    int32_t n_cams;                                  /* 1..IMLOC_RIG_MAX_CAMERAS */
+    int32_t reserved;
+    imloc_camera cams[IMLOC_RIG_MAX_CAMERAS];        /* intrinsics (width/height unused) */
+    imloc_pose cam_from_rig[IMLOC_RIG_MAX_CAMERAS];  /* X_c = R X_r + t */
+} imloc_rig;
+
+int imloc_ransac_rig_batch(imloc_ctx* ctx, int32_t n_queries, const imloc_corr* corr, const int32_t* d_cam,
+                           const int64_t* d_offsets, const imloc_rig* rigs, const imloc_ransac_opts* opts,
+                           imloc_result* d_results, uint8_t* d_masks, void* stream);
+
 /* ---- serving: continuous batching (lift + LO-RANSAC PnP) ---------------
  * A server owns a scheduler thread, a device memory pool and a pinned host
  * ring.  Queries are submitted with their matches in HOST memory (copied into

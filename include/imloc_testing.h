@@ -34,6 +34,16 @@ int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_cam
                          const imloc_ransac_opts* opts, const imloc_debug* dbg, imloc_result* out,
                          uint8_t* d_inlier_mask, void* stream);
 
+/* One rig query (imloc_ransac_rig_batch) with the debug buffers above, sized
+ * for 8 pose ids per minimal set: poses 8 * H * 12, scores and counts 8 * H
+ * (pose id = 8 * sample + solution; ids without a solution hold NaN / -1);
+ * injected poses take id 8 k.  The adaptive stop must be off (opts->p_miss
+ * <= 0): every round is scored in one wave.  N is corr->capacity; d_cam as
+ * in imloc_ransac_rig_batch.  Synchronous. */
+int imloc_testing_rig(imloc_ctx* ctx, const imloc_corr* corr, const int32_t* d_cam, const imloc_rig* rig,
+                      const imloc_ransac_opts* opts, const imloc_debug* dbg, imloc_result* out,
+                      uint8_t* d_inlier_mask, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

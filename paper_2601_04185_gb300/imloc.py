@@ -72,6 +72,25 @@ class Result(C.Structure):
                 ("best_hyp", C.c_int64), ("status", C.c_int32), ("passes", C.c_int32)]
 
 
+RIG_MAX_CAMERAS = 8
+
+
+class Rig(C.Structure):
+    _fields_ = [("n_cams", C.c_int32), ("reserved", C.c_int32), ("cams", Camera * RIG_MAX_CAMERAS),
+                ("cam_from_rig", Pose * RIG_MAX_CAMERAS)]
+
+
+def rig(Ks, R_cam, t_cam) -> Rig:
+    """Ks: per camera (fx, fy, cx, cy); R_cam, t_cam: cam_from_rig per camera."""
+    r = Rig()
+    r.n_cams = len(Ks)
+    for k, K in enumerate(Ks):
+        r.cams[k] = camera(K)
+        r.cam_from_rig[k].R[:] = [float(a) for a in np.asarray(R_cam[k], dtype=np.float64).ravel()]
+        r.cam_from_rig[k].t[:] = [float(a) for a in np.asarray(t_cam[k], dtype=np.float64).ravel()]
+    return r
+
+
 class ServeConfig(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("max_queue", C.c_int32), ("device_budget_bytes", C.c_size_t),
                 ("host_staging_bytes", C.c_size_t), ("rounds_per_step", C.c_int32), ("reserved", C.c_int32)]
@@ -99,7 +118,8 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
            "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config",
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
-           "imloc_triangulate_depth_async", "imloc_retrieve_topk_async"]
+           "imloc_triangulate_depth_async", "imloc_retrieve_topk_async", "imloc_ransac_rig_batch",
+           "imloc_testing_rig"]
 
 _lib = None
 
@@ -144,6 +164,8 @@ def load(path: str = LIB_PATH):
     L.imloc_triangulate_default_opts.restype = None
     L.imloc_triangulate_depth_async.argtypes = [P(Camera), P(Pose), C.c_int32, C.c_int32, P(Camera), P(Pose),
                                                 C.c_int32, V, V, V, C.c_int64, P(TriangulateOpts), V, V, V]
+    L.imloc_ransac_rig_batch.argtypes = [V, C.c_int32, P(Corr), V, V, P(Rig), P(RansacOpts), V, V, V]
+    L.imloc_testing_rig.argtypes = [V, P(Corr), V, P(Rig), P(RansacOpts), P(Debug), P(Result), V, V]
     L.imloc_depth_encode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     L.imloc_depth_decode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     _lib = L
@@ -390,6 +412,27 @@ class Context:
         _check(self.lib.imloc_ransac_pnp_batch_async(self.h, p.nq, C.byref(cs), _ptr(offsets), p.cams, p.opts,
                                                      _ptr(results), _ptr(masks), _stream(stream)),
                "imloc_ransac_pnp_batch_async")
+
+    def ransac_rig_batch(self, corr, cam, offsets, rigs, opts, results, masks=None, stream=None):
+        """Rig queries (generalized absolute pose).  cam: device int32 camera index per correspondence;
+        offsets: device int64 (n_queries + 1); rigs: list of Rig; opts: list of RansacOpts;
+        results: cuda uint8 tensor of n_queries * RESULT_BYTES.  Returns when the results are written."""
+        nq = len(rigs)
+        cs = _corr_struct(corr)
+        _check(self.lib.imloc_ransac_rig_batch(self.h, nq, C.byref(cs), _ptr(cam), _ptr(offsets),
+                                               (Rig * nq)(*rigs), (RansacOpts * nq)(*opts), _ptr(results),
+                                               _ptr(masks), _stream(stream)), "imloc_ransac_rig_batch")
+
+    def testing_rig(self, corr, cam, rg, opts, n, debug: dict, mask=None, stream=None):
+        cs = _corr_struct(corr, capacity=n)
+        cs.count = None
+        dbg = Debug(_ptr(debug.get("triples")), _ptr(debug.get("poses")), _ptr(debug.get("scores")),
+                    _ptr(debug.get("counts")), _ptr(debug.get("round_best")), _ptr(debug.get("inject_poses")),
+                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0)
+        res = Result()
+        _check(self.lib.imloc_testing_rig(self.h, C.byref(cs), _ptr(cam), C.byref(rg), C.byref(opts), C.byref(dbg),
+                                          C.byref(res), _ptr(mask), _stream(stream)), "imloc_testing_rig")
+        return result_dict(res)
 
     def testing_ransac(self, corr, K, opts, n, debug: dict, mask=None, stream=None):
         cs = _corr_struct(corr, capacity=n)

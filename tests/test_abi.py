@@ -43,6 +43,7 @@ def test_struct_sizes_match_the_header_layout():
     assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96 + 8
     assert C.sizeof(imloc.Corr) == 8 * 9
     assert C.sizeof(imloc.Segment) == 16
+    assert C.sizeof(imloc.Rig) == 8 + 8 * 24 + 8 * 96
 
 
 def test_default_options_are_the_papers_constants(lib):
@@ -70,6 +71,8 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_depth_decode_log8_async(None, 4, 4, 4, None, 4, None) == -1
     assert lib.imloc_triangulate_depth_async(None, None, 4, 4, None, None, 1, None, None, None, 16, None, None,
                                              None, None) == -1
+    assert lib.imloc_ransac_rig_batch(None, 1, None, None, None, None, None, None, None, None) == -1
+    assert lib.imloc_testing_rig(None, None, None, None, None, None, None, None, None) == -1
 
 
 def test_triangulation_defaults_are_the_papers_constants(lib):
