@@ -381,6 +381,77 @@ def run_triangulation(dev, repeats=20):
             "paper_context": "~30 ms per image on an RTX 4090 for matching + triangulation, matching dominating (Sec. 3.3)"}
 
 
+def run_rig(dev, peaks, repeats=5, n_queries=16):
+    """Generalized absolute pose of camera-rig queries (supplementary "LaMAR
+    HoloLens Results"): 16 queries of a 4-camera head-mounted rig (cameras at
+    -60, -20, 20, 60 degrees of yaw, within 10 cm of the rig origin), 2,500
+    correspondences per camera (N = 10,000), inlier ratio U[15%, 50%],
+    default options (batches of 1,024, at most 100K minimal sets, adaptive
+    stop at 1e-4); one call per step, L2 flushed before each."""
+    import torch
+
+    from paper_2601_04185_gb300 import imloc, synth
+
+    rng = np.random.default_rng(2031)
+    qs = [synth.rig_query(rng, n_per_cam=2500, inlier_ratio=float(rng.uniform(0.15, 0.5)), n_cams=4, weights="conf")
+          for _ in range(n_queries)]
+    off = np.concatenate([[0], np.cumsum([len(q["x"]) for q in qs])]).astype(np.int64)
+    c = imloc.corr_from_arrays(np.concatenate([q["x"] for q in qs]), np.concatenate([q["y"] for q in qs]),
+                               np.concatenate([q["X"] for q in qs]), np.concatenate([q["w"] for q in qs]), device=dev)
+    cam = torch.from_numpy(np.concatenate([q["cam"] for q in qs]).astype(np.int32)).to(dev)
+    d_off = torch.from_numpy(off).to(dev)
+    rigs = [imloc.rig(q["K"], q["R_cam"], q["t_cam"]) for q in qs]
+    opts = [imloc.default_opts(query_id=i, seed=77) for i in range(n_queries)]
+    out = torch.zeros(n_queries * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    ctx = imloc.Context(dev.index, 1 << 30)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(2):
+        ctx.ransac_rig_batch(c, cam, d_off, rigs, opts, out, stream=stream)
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    ctx.profile_read(reset=True)
+    times = []
+    for _ in range(repeats):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.ransac_rig_batch(c, cam, d_off, rigs, opts, out, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    prof = ctx.profile_read(reset=True)
+    ctx.profile(False)
+    ctx.close()
+    res = imloc.results_from_bytes(out.cpu().numpy(), n_queries)
+    ms = statistics.median(times)
+    hyps = sum(r["hypotheses"] for r in res)
+    m = [min(len(q["x"]), 10000) for q in qs]
+    work = sum(r["hypotheses"] * mq for r, mq in zip(res, m))
+    errs = []
+    for r, q in zip(res, qs):
+        dR = r["R"] @ q["R_gt"].T
+        ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(dR) - 1) / 2))))
+        errs.append((ang, float(np.linalg.norm(r["R"].T @ r["t"] - q["R_gt"].T @ q["t_gt"]))))
+    score_ms = prof["k_rig_score"][1] / repeats if "k_rig_score" in prof else None
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    line = {"workload": f"{n_queries} rig queries x 4 cameras x 2,500 correspondences, inlier ratio U[15%, 50%], "
+                        "default options, one call",
+            "ms_per_call": ms, "queries_per_s": n_queries / (ms * 1e-3),
+            "hyp_corr_per_s": work / (ms * 1e-3), "hypotheses": hyps,
+            "rounds": [int(r["rounds"]) for r in res],
+            "status_ok": sum(r["status"] == 0 for r in res),
+            "max_rot_err_deg": max(e[0] for e in errs), "max_centre_err_m": max(e[1] for e in errs),
+            "kernel_ms_per_call": {k: prof[k][1] / repeats for k in prof},
+            "launches_per_call": {k: prof[k][0] / repeats for k in prof}}
+    if score_ms:
+        tflops = work * 27 / (score_ms * 1e-3) / 1e12
+        line["roofline"] = {"kernel": "k_rig_score", "bound": "alu", "achieved": tflops, "peak": fp32_peak,
+                            "unit": "TFLOP/s", "frac": tflops / fp32_peak,
+                            "note": "27 flops per (pose, correspondence) / summed k_rig_score time; derived FP32 peak"}
+    return line
+
+
 def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
     """Offer Poisson streams to the server and to the plain loop; returns per-rate q/s and latency percentiles."""
     import queue
@@ -921,6 +992,9 @@ def run_ours(args):
     # ---- retrieval nearest-neighbour search (next row f4) ----
     if world == 1 and not args.no_retrieval:
         line["retrieval"] = run_retrieval(dev, peaks)
+    # ---- generalized absolute pose of rig queries (next row f3) ----
+    if world == 1 and not args.no_rig:
+        line["rig"] = run_rig(dev, peaks)
     # ---- mapping-time dense triangulation (next row f2) ----
     if world == 1 and not args.no_triangulation:
         line["triangulation"] = run_triangulation(dev)
@@ -977,10 +1051,12 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-triangulation", action="store_true")
+    ap.add_argument("--no-rig", action="store_true")
     ap.add_argument("--no-retrieval", action="store_true")
     ap.add_argument("--precision-study", action="store_true", help="C4: precision variants vs the oracle")
     ap.add_argument("--lift-only", action="store_true", help="only the batched lift measurement")
     ap.add_argument("--retrieval-only", action="store_true", help="only the retrieval search measurement")
+    ap.add_argument("--rig-only", action="store_true", help="only the rig-query measurement")
     ap.add_argument("--serve-queries", type=int, default=80, help="distinct serving queries")
     ap.add_argument("--serve-per-rate", type=int, default=200, help="arrivals per offered rate")
     args = ap.parse_args()
@@ -994,6 +1070,12 @@ def main():
         return run_lift_only(args)
     if args.retrieval_only:
         return run_retrieval_only(args)
+    if args.rig_only:
+        import torch
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"rig": run_rig(torch.device("cuda", 0), load_peaks(), repeats=args.steps)}))
+        return 0
     return run_ours(args)
 
 

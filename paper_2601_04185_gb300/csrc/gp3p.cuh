@@ -148,8 +148,18 @@ __device__ inline double gp_refine(const double (&c)[9], double l, double u, dou
     return x;
 }
 
-// All solutions (lambda triples, ascending lambda_1, all positive).
-__device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], const double X[3][3], Gp3pSol& out) {
+// grid point j of kGp3pGrid over [lo, hi] (Chebyshev spacing)
+__device__ __forceinline__ double gp_node(int j, double lo, double hi) {
+    if (j <= 0) return lo;
+    if (j >= kGp3pGrid) return hi;
+    return 0.5 * (lo + hi) - 0.5 * (hi - lo) * cospi(static_cast<double>(j) / kGp3pGrid);
+}
+
+// The solutions (lambda triples, ascending lambda_1, all positive) whose
+// lambda_1 lies in grid cells [cell0, cell1) (all: 0, kGp3pGrid), so that several
+// threads can share one minimal sample, each scanning a slice of the grid.
+__device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], const double X[3][3], Gp3pSol& out,
+                                    int cell0 = 0, int cell1 = kGp3pGrid) {
     out.n = 0;
     const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
     double c[3], a[3], b[3], e[3], D2[3];
@@ -239,13 +249,12 @@ __device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], 
     // changes sign between them: such a cell is split at the extremum of p.
     // Chebyshev spacing: roots crowd towards the ends of the feasible interval
     // (where lambda_2 or lambda_3 turns complex), so the cells are finest there
-    const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
-    double xa = lo, pa, dpa;
-    gp_eval_d<8>(oct, lo, pa, dpa);
+    double xa = gp_node(cell0, lo, hi), pa, dpa;
+    gp_eval_d<8>(oct, xa, pa, dpa);
     double roots[kGp3pMaxSol];
     int nroots = 0;
-    for (int gi = 1; gi <= kGp3pGrid && nroots < kGp3pMaxSol; ++gi) {
-        const double xb = (gi == kGp3pGrid) ? hi : mid - half * cospi(static_cast<double>(gi) / kGp3pGrid);
+    for (int gi = cell0 + 1; gi <= cell1 && nroots < kGp3pMaxSol; ++gi) {
+        const double xb = gp_node(gi, lo, hi);
         double pb, dpb;
         gp_eval_d<8>(oct, xb, pb, dpb);
         if (pa == 0.0) {

@@ -8,14 +8,17 @@
 // Kernels (per wave of rounds, all queries of the batch in each launch):
 //   k_rig_setup   per query: N, the subset (uniform stride) regrouped by
 //                 camera with a stable counting sort, round words
-//   k_rig_sample  one minimal sample per thread: Philox triple, the three rays
-//                 in the rig frame, GP3P in FP64 (gp3p.cuh), <= 8 poses into
-//                 slot 8 s + k, a compact list of the valid slots
-//   k_rig_score   (query, tile of 512 poses) per CTA, 4 poses per thread: per
-//                 camera the poses are composed with that camera
-//                 (K_k [R_k R | R_k t + t_k], FP32) and run over the camera's
-//                 records staged in shared memory; truncated cost, inlier
-//                 count, one 64-bit atomic min per pose into its round word
+//   k_rig_sample  one minimal sample per 8 threads: Philox triple, the three
+//                 rays in the rig frame, GP3P in FP64 (gp3p.cuh; each thread
+//                 scans 1/8 of the root grid), <= 8 poses into slot 8 s + k,
+//                 a compact list of the valid slots
+//   k_rig_score   (query, tile of 256 poses, chunk of 1,024 subset records)
+//                 per CTA, 2 poses per thread: the chunk staged in shared
+//                 memory, per camera run the poses composed with that camera
+//                 (K_k [R_k R | R_k t + t_k], FP32); partial truncated cost
+//                 and inlier count per (pose, chunk)
+//   k_rig_reduce  per pose: the partials in chunk order, one 64-bit atomic
+//                 min into its round word
 //   k_rig_replay  one CTA per query: the rounds of the wave in order (new best
 //                 -> LO on the subset), the adaptive stop, and once a query is
 //                 done the final Cauchy refinement over all its
@@ -42,10 +45,12 @@ namespace {
 constexpr int kRigMaxCams = IMLOC_RIG_MAX_CAMERAS;
 constexpr int kRigSlots = 8;           // GP3P solutions per minimal sample
 constexpr int kRigSampleThreads = 128;
+constexpr int kRigLanes = 8;           // threads per minimal sample (GP3P grid slices)
+constexpr int kRigLaneSols = 4;        // solutions one slice keeps
 constexpr int kRigScoreThreads = 128;
-constexpr int kRigHT = 4;              // poses per scoring thread
+constexpr int kRigHT = 2;              // poses per scoring thread
 constexpr int kRigTile = kRigScoreThreads * kRigHT;
-constexpr int kRigStage = 1024;        // records staged per shared-memory chunk
+constexpr int kRigChunk = 1024;        // subset records per scoring CTA (staged in shared memory)
 constexpr int kRigReplayThreads = 512;
 constexpr int kRigMaxWaveRounds = 8;
 
@@ -78,6 +83,7 @@ struct RigQuery {
     PoseF* slots;        // wave samples * 8
     int32_t* compact;    // wave samples * 8: valid slots of the wave
     int32_t* n_compact;
+    float2* part;        // wave samples * 8 * chunks: partial (cost, count bits) per pose and chunk
     uint64_t* round_best;
     int32_t* round_hyps;
     uint8_t* fix;        // fixed set of the final refinement, at the correspondences' offsets
@@ -230,76 +236,108 @@ __device__ __forceinline__ void rig_ray(const RigQuery& d, int64_t i, double o[3
     X[2] = __ldg(d.Z + i);
 }
 
+// kRigLanes threads per minimal sample: each scans 1/kRigLanes of the GP3P
+// root grid (and finishes the roots it finds); the group then writes its
+// poses in ascending lambda_1 order.
 __global__ void __launch_bounds__(kRigSampleThreads) k_rig_sample(const __grid_constant__ RigWave w) {
     const int q = blockIdx.y;
     const RigQuery& d = w.qd[q];
     const RigState& st = w.qs[q];
-    const int sl = blockIdx.x * kRigSampleThreads + threadIdx.x;
-    if (sl >= (w.r1 - w.r0) * d.batch || st.done) return;
+    const int lane = threadIdx.x % kRigLanes;
+    const int sl = (blockIdx.x * kRigSampleThreads + threadIdx.x) / kRigLanes;
     const int64_t s = static_cast<int64_t>(w.r0) * d.batch + sl;
-    if (s >= d.max_iters) return;
-    const int r = static_cast<int>(s / d.batch);
+    // every thread reaches the group shuffles below; `live` marks real work
+    bool live = sl < (w.r1 - w.r0) * d.batch && !st.done && s < d.max_iters;
     PoseF* slot = d.slots + static_cast<int64_t>(sl) * kRigSlots;
-    int nsol = 0;
-    if (d.inject) {
-        if (s < d.n_inject) {
-            slot[0] = d.inject[s];
-            nsol = 1;
-        }
-    } else {
+    PoseF mine[kRigLaneSols];
+    int nmine = 0;
+    if (live && d.inject) {
+        if (lane == 0 && s < d.n_inject) mine[nmine++] = d.inject[s];
+    } else if (live) {
         int tri[3];
         const bool ok = draw_triple(d.seed, d.query_id, static_cast<uint32_t>(s), static_cast<uint32_t>(st.m), tri);
-        if (d.triples) {
+        if (d.triples && lane == 0) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) d.triples[3 * s + k] = ok ? tri[k] : -1;
         }
-        if (!ok) return;
-        double o[3][3], dir[3][3], X[3][3];
+        if (ok) {
+            double o[3][3], dir[3][3], X[3][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) rig_ray(d, st.off + (static_cast<int64_t>(tri[k]) * st.n) / st.m, o[k], dir[k], X[k]);
-        Gp3pSol sol;
-        gp3p_lambdas(o, dir, X, sol);
-        for (int k = 0; k < sol.n; ++k) {
-            double P[3][3], R[9], t[3];
+            for (int k = 0; k < 3; ++k)
+                rig_ray(d, st.off + (static_cast<int64_t>(tri[k]) * st.n) / st.m, o[k], dir[k], X[k]);
+            Gp3pSol sol;
+            const int cells = kGp3pGrid / kRigLanes;
+            gp3p_lambdas(o, dir, X, sol, lane * cells, (lane + 1) * cells);
+            for (int k = 0; k < sol.n && nmine < kRigLaneSols; ++k) {
+                double P[3][3], R[9], t[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int a = 0; a < 3; ++a) P[i][a] = o[i][a] + sol.lam[k][i] * dir[i][a];
-            if (!gp_pose(X, P, R, t)) continue;
-            PoseF pf;
+                    for (int a = 0; a < 3; ++a) P[i][a] = o[i][a] + sol.lam[k][i] * dir[i][a];
+                if (!gp_pose(X, P, R, t)) continue;
+                PoseF pf;
 #pragma unroll
-            for (int a = 0; a < 9; ++a) pf.R[a] = static_cast<float>(R[a]);
+                for (int a = 0; a < 9; ++a) pf.R[a] = static_cast<float>(R[a]);
 #pragma unroll
-            for (int a = 0; a < 3; ++a) pf.t[a] = static_cast<float>(t[a]);
-            slot[nsol++] = pf;
+                for (int a = 0; a < 3; ++a) pf.t[a] = static_cast<float>(t[a]);
+                mine[nmine++] = pf;
+            }
         }
     }
-    if (nsol == 0) return;
-    const int at = atomicAdd(d.n_compact, nsol);
-    for (int k = 0; k < nsol; ++k) d.compact[at + k] = sl * kRigSlots + k;
-    atomicAdd(d.round_hyps + r, nsol);
+    // exclusive prefix of the solution counts within the group (lane order = ascending lambda_1)
+    int incl = nmine;
+#pragma unroll
+    for (int o = 1; o < kRigLanes; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o, kRigLanes);
+        if (lane >= o) incl += v;
+    }
+    const int total = min(__shfl_sync(0xffffffffu, incl, kRigLanes - 1, kRigLanes), kRigSlots);
+    const int first = incl - nmine;
+    int at = 0;
+    if (lane == kRigLanes - 1 && total > 0) at = atomicAdd(d.n_compact, total);
+    at = __shfl_sync(0xffffffffu, at, kRigLanes - 1, kRigLanes);
+    for (int k = 0; k < nmine; ++k) {
+        const int pos = first + k;
+        if (pos >= kRigSlots) break;
+        slot[pos] = mine[k];
+        d.compact[at + pos] = sl * kRigSlots + pos;
+    }
+    if (lane == 0 && total > 0) atomicAdd(d.round_hyps + static_cast<int>(s / d.batch), total);
 }
 
 // ============================================================================
 // scoring
 // ============================================================================
+// One CTA per (query, tile of kRigTile poses, chunk of kRigChunk subset
+// records): the chunk is staged in shared memory once; for each camera run in
+// it the poses are composed with that camera and evaluated on its records.
+// Partial sums go to part[pose][chunk] (added in chunk order by k_rig_reduce:
+// deterministic).
 __global__ void __launch_bounds__(kRigScoreThreads) k_rig_score(const __grid_constant__ RigWave w) {
-    const int q = blockIdx.y, tid = threadIdx.x;
+    const int q = blockIdx.z, tid = threadIdx.x;
     const RigQuery& d = w.qd[q];
     const int n_valid = *d.n_compact;
     const int base = blockIdx.x * kRigTile;
-    if (base >= n_valid || w.qs[q].done) return;
-    __shared__ float4 s_rec[kRigStage];
-    __shared__ float2 s_xy[kRigStage];
+    const int m = w.qs[q].m;
+    const int c0 = blockIdx.y * kRigChunk;
+    if (base >= n_valid || c0 >= m || w.qs[q].done) return;
+    const int c1 = min(m, c0 + kRigChunk);
+    const int n_chunks = (m + kRigChunk - 1) / kRigChunk;
+    __shared__ float4 s_rec[kRigChunk];
+    __shared__ float2 s_xy[kRigChunk];
     __shared__ int32_t s_seg[kRigMaxCams + 1];
     if (tid <= d.n_cams) s_seg[tid] = d.seg[tid];
-    int slot[kRigHT];
+    for (int i = tid; i < c1 - c0; i += kRigScoreThreads) {
+        s_rec[i] = d.rec[c0 + i];
+        s_xy[i] = d.recxy[c0 + i];
+    }
+    int idx[kRigHT];
     float R[kRigHT][9], t[kRigHT][3];
 #pragma unroll
     for (int j = 0; j < kRigHT; ++j) {
-        const int idx = base + j * kRigScoreThreads + tid;
-        slot[j] = idx < n_valid ? d.compact[idx] : -1;
-        const PoseF p = d.slots[slot[j] >= 0 ? slot[j] : 0];
+        idx[j] = base + j * kRigScoreThreads + tid;
+        const int slot = idx[j] < n_valid ? d.compact[idx[j]] : d.compact[0];
+        const PoseF p = d.slots[slot];
 #pragma unroll
         for (int a = 0; a < 9; ++a) R[j][a] = p.R[a];
 #pragma unroll
@@ -315,7 +353,7 @@ __global__ void __launch_bounds__(kRigScoreThreads) k_rig_score(const __grid_con
     const float tau2 = d.tau2;
     __syncthreads();
     for (int k = 0; k < d.n_cams; ++k) {
-        const int b0 = s_seg[k], b1 = s_seg[k + 1];
+        const int b0 = max(s_seg[k], c0), b1 = min(s_seg[k + 1], c1);
         if (b1 <= b0) continue;
         const RigCam& c = d.cams[k];
         // P_j = K_k [R_k R_j | R_k t_j + t_k]
@@ -326,59 +364,68 @@ __global__ void __launch_bounds__(kRigScoreThreads) k_rig_score(const __grid_con
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
 #pragma unroll
-                for (int b = 0; b < 3; ++b)
-                    M[a][b] = fmaf(c.R[3 * a], R[j][b], fmaf(c.R[3 * a + 1], R[j][3 + b], c.R[3 * a + 2] * R[j][6 + b]));
+                for (int bb = 0; bb < 3; ++bb)
+                    M[a][bb] = fmaf(c.R[3 * a], R[j][bb], fmaf(c.R[3 * a + 1], R[j][3 + bb], c.R[3 * a + 2] * R[j][6 + bb]));
                 M[a][3] = fmaf(c.R[3 * a], t[j][0], fmaf(c.R[3 * a + 1], t[j][1], fmaf(c.R[3 * a + 2], t[j][2], c.t[a])));
             }
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                P[j][b] = fmaf(c.fx, M[0][b], c.cx * M[2][b]);
-                P[j][4 + b] = fmaf(c.fy, M[1][b], c.cy * M[2][b]);
-                P[j][8 + b] = M[2][b];
+            for (int bb = 0; bb < 4; ++bb) {
+                P[j][bb] = fmaf(c.fx, M[0][bb], c.cx * M[2][bb]);
+                P[j][4 + bb] = fmaf(c.fy, M[1][bb], c.cy * M[2][bb]);
+                P[j][8 + bb] = M[2][bb];
             }
         }
-        for (int c0 = b0; c0 < b1; c0 += kRigStage) {
-            const int nc = min(kRigStage, b1 - c0);
-            __syncthreads();
-            for (int i = tid; i < nc; i += kRigScoreThreads) {
-                s_rec[i] = d.rec[c0 + i];
-                s_xy[i] = d.recxy[c0 + i];
-            }
-            __syncthreads();
-#pragma unroll 2
-            for (int i = 0; i < nc; ++i) {
-                const float4 X = s_rec[i];
-                const float2 xy = s_xy[i];
+#pragma unroll 4
+        for (int i = b0 - c0; i < b1 - c0; ++i) {
+            const float4 X = s_rec[i];
+            const float2 xy = s_xy[i];
 #pragma unroll
-                for (int j = 0; j < kRigHT; ++j) {
-                    const float u = fmaf(P[j][0], X.x, fmaf(P[j][1], X.y, fmaf(P[j][2], X.z, P[j][3])));
-                    const float v = fmaf(P[j][4], X.x, fmaf(P[j][5], X.y, fmaf(P[j][6], X.z, P[j][7])));
-                    const float z = fmaf(P[j][8], X.x, fmaf(P[j][9], X.y, fmaf(P[j][10], X.z, P[j][11])));
-                    float r2 = tau2;
-                    if (z > 0.f) {
-                        const float iz = __frcp_rn(z);
-                        const float du = fmaf(u, iz, -xy.x), dv = fmaf(v, iz, -xy.y);
-                        const float rr = fmaf(du, du, dv * dv);
-                        if (rr < tau2) {
-                            r2 = rr;
-                            ++cnt[j];
-                        }
+            for (int j = 0; j < kRigHT; ++j) {
+                const float u = fmaf(P[j][0], X.x, fmaf(P[j][1], X.y, fmaf(P[j][2], X.z, P[j][3])));
+                const float v = fmaf(P[j][4], X.x, fmaf(P[j][5], X.y, fmaf(P[j][6], X.z, P[j][7])));
+                const float z = fmaf(P[j][8], X.x, fmaf(P[j][9], X.y, fmaf(P[j][10], X.z, P[j][11])));
+                float r2 = tau2;
+                if (z > 0.f) {
+                    const float iz = __frcp_rn(z);
+                    const float du = fmaf(u, iz, -xy.x), dv = fmaf(v, iz, -xy.y);
+                    const float rr = fmaf(du, du, dv * dv);
+                    if (rr < tau2) {
+                        r2 = rr;
+                        ++cnt[j];
                     }
-                    cost[j] = fmaf(X.w, r2, cost[j]);
                 }
+                cost[j] = fmaf(X.w, r2, cost[j]);
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < kRigHT; ++j) {
-        if (slot[j] < 0) continue;
-        const int64_t gid = static_cast<int64_t>(w.r0) * d.batch * kRigSlots + slot[j];  // 8 * sample + solution
-        if (d.score_by_id) d.score_by_id[gid] = cost[j];
-        if (d.count_by_id) d.count_by_id[gid] = cnt[j];
-        const int r = static_cast<int>((gid / kRigSlots) / d.batch);
-        const uint64_t key = (static_cast<uint64_t>(__float_as_uint(cost[j])) << 32) | static_cast<uint32_t>(gid);
-        atomicMin(reinterpret_cast<unsigned long long*>(d.round_best + r), static_cast<unsigned long long>(key));
+    for (int j = 0; j < kRigHT; ++j)
+        if (idx[j] < n_valid)
+            d.part[static_cast<int64_t>(idx[j]) * n_chunks + blockIdx.y] = make_float2(cost[j], __int_as_float(cnt[j]));
+}
+
+// Per valid pose: the chunk partial sums in chunk order, its score and count,
+// and the 64-bit atomic min (score bits << 32 | pose id) into its round word.
+__global__ void __launch_bounds__(256) k_rig_reduce(const __grid_constant__ RigWave w) {
+    const int q = blockIdx.y;
+    const RigQuery& d = w.qd[q];
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= *d.n_compact || w.qs[q].done) return;
+    const int m = w.qs[q].m;
+    const int n_chunks = (m + kRigChunk - 1) / kRigChunk;
+    float cost = 0.f;
+    int cnt = 0;
+    for (int c = 0; c < n_chunks; ++c) {
+        const float2 pc = d.part[static_cast<int64_t>(i) * n_chunks + c];
+        cost += pc.x;
+        cnt += __float_as_int(pc.y);
     }
+    const int64_t gid = static_cast<int64_t>(w.r0) * d.batch * kRigSlots + d.compact[i];  // 8 * sample + solution
+    if (d.score_by_id) d.score_by_id[gid] = cost;
+    if (d.count_by_id) d.count_by_id[gid] = cnt;
+    const int r = static_cast<int>((gid / kRigSlots) / d.batch);
+    const uint64_t key = (static_cast<uint64_t>(__float_as_uint(cost)) << 32) | static_cast<uint32_t>(gid);
+    atomicMin(reinterpret_cast<unsigned long long*>(d.round_best + r), static_cast<unsigned long long>(key));
 }
 
 // ============================================================================
@@ -915,8 +962,11 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
     }
     int wave_rounds = 0;
     for (auto& wv : waves) wave_rounds = std::max(wave_rounds, wv.second - wv.first);
-    int max_batch = 0;
-    for (int q = 0; q < nq; ++q) max_batch = std::max(max_batch, hq[q].o.batch);
+    int max_batch = 0, max_chunks = 1;
+    for (int q = 0; q < nq; ++q) {
+        max_batch = std::max(max_batch, hq[q].o.batch);
+        max_chunks = std::max(max_chunks, (hq[q].o.max_score_corr + kRigChunk - 1) / kRigChunk);
+    }
     const int64_t wave_samples = static_cast<int64_t>(wave_rounds) * max_batch;
 
     RigQuery* hd = static_cast<RigQuery*>(staging_alloc(ctx, sizeof(RigQuery) * nq));
@@ -980,6 +1030,8 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
                                   : static_cast<PoseF*>(ws_alloc(ctx, sizeof(PoseF) * wave_samples * kRigSlots));
         d.compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * wave_samples * kRigSlots));
         d.n_compact = n_compact + q;
+        d.part = static_cast<float2*>(ws_alloc(ctx, sizeof(float2) * wave_samples * kRigSlots *
+                                                         ((o.max_score_corr + kRigChunk - 1) / kRigChunk)));
         d.round_best = hq[q].round_best_out
                            ? hq[q].round_best_out
                            : static_cast<uint64_t*>(ws_alloc(ctx, sizeof(uint64_t) * std::max(1, d.rounds)));
@@ -990,7 +1042,7 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         d.score_by_id = hq[q].score_by_id;
         d.count_by_id = hq[q].count_by_id;
         d.triples = hq[q].triples;
-        if (!d.rec || !d.recxy || !d.seg || !d.slots || !d.compact || !d.n_compact || !d.round_best ||
+        if (!d.rec || !d.recxy || !d.seg || !d.slots || !d.compact || !d.n_compact || !d.part || !d.round_best ||
             !d.round_hyps)
             return IMLOC_ERR_OOM;
     }
@@ -1017,7 +1069,7 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         IMLOC_CUDA_TRY(cudaMemsetAsync(n_compact, 0, sizeof(int32_t) * nq, st));
         {
             ProfScope prof(ctx, st, "k_rig_sample");
-            k_rig_sample<<<dim3(static_cast<unsigned>((ns + kRigSampleThreads - 1) / kRigSampleThreads), nq),
+            k_rig_sample<<<dim3(static_cast<unsigned>((ns * kRigLanes + kRigSampleThreads - 1) / kRigSampleThreads), nq),
                            kRigSampleThreads, 0, st>>>(w);
             IMLOC_CUDA_TRY(cudaGetLastError());
             prof.end();
@@ -1025,7 +1077,13 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         {
             const int tiles = static_cast<int>((ns * kRigSlots + kRigTile - 1) / kRigTile);
             ProfScope prof(ctx, st, "k_rig_score");
-            k_rig_score<<<dim3(tiles, nq), kRigScoreThreads, 0, st>>>(w);
+            k_rig_score<<<dim3(tiles, max_chunks, nq), kRigScoreThreads, 0, st>>>(w);
+            IMLOC_CUDA_TRY(cudaGetLastError());
+            prof.end();
+        }
+        {
+            ProfScope prof(ctx, st, "k_rig_reduce");
+            k_rig_reduce<<<dim3(static_cast<unsigned>((ns * kRigSlots + 255) / 256), nq), 256, 0, st>>>(w);
             IMLOC_CUDA_TRY(cudaGetLastError());
             prof.end();
         }
