@@ -59,6 +59,20 @@ __device__ __forceinline__ void gp_eval_d(const double (&c)[D + 1], double x, do
     }
 }
 
+template <int D>
+__device__ __forceinline__ void gp_eval_dd(const double (&c)[D + 1], double x, double& p, double& dp, double& ddp) {
+    p = c[D];
+    dp = 0.0;
+    ddp = 0.0;
+#pragma unroll
+    for (int k = D - 1; k >= 0; --k) {
+        ddp = fma(ddp, x, dp);
+        dp = fma(dp, x, p);
+        p = fma(p, x, c[k]);
+    }
+    ddp *= 2.0;
+}
+
 // out = a * b (degrees A, B)
 template <int A, int B>
 __device__ __forceinline__ void gp_mul(const double (&a)[A + 1], const double (&b)[B + 1], double (&out)[A + B + 1]) {
@@ -148,21 +162,28 @@ __device__ inline double gp_refine(const double (&c)[9], double l, double u, dou
     return x;
 }
 
-// grid point j of kGp3pGrid over [lo, hi] (Chebyshev spacing)
-__device__ __forceinline__ double gp_node(int j, double lo, double hi) {
-    if (j <= 0) return lo;
-    if (j >= kGp3pGrid) return hi;
-    return 0.5 * (lo + hi) - 0.5 * (hi - lo) * cospi(static_cast<double>(j) / kGp3pGrid);
-}
+// Everything the root search and the back-substitution need for one minimal
+// set (coefficient polynomials in lambda_1, ascending).
+struct Gp3pSys {
+    double oct[9];
+    double f2[3], f1[4], f0[5];   // F(l2) = f2 l2^2 + f1 l2 + f0
+    double q[3], g1[2];           // G(l2) = l2^2 + g1 l2 + q
+    double B[2], C[2], E[3];      // l3 = -(B l2 + E) / (A l2 + C)
+    double r[2], s[3];            // l3^2 - 2 r l3 + s (pair 1,3)
+    double A;
+    double D2[3];
+    double lo, hi;                // feasible lambda_1 (padded)
+};
 
-// The solutions (lambda triples, ascending lambda_1, all positive) whose
-// lambda_1 lies in grid cells [cell0, cell1) (all: 0, kGp3pGrid), so that several
-// threads can share one minimal sample, each scanning a slice of the grid.
-__device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], const double X[3][3], Gp3pSol& out,
-                                    int cell0 = 0, int cell1 = kGp3pGrid) {
-    out.n = 0;
+// A bracket [l, u] of one root of the octic (p(l) = pl has the other sign).
+struct Gp3pBracket {
+    double l, u, pl;
+};
+
+// Coefficients and the feasible interval; false if no real solution can exist.
+__device__ inline bool gp3p_setup(const double o[3][3], const double d[3][3], const double X[3][3], Gp3pSys& S) {
     const int pi[3] = {0, 0, 1}, pj[3] = {1, 2, 2};
-    double c[3], a[3], b[3], e[3], D2[3];
+    double c[3], a[3], b[3], e[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const int i = pi[k], j = pj[k];
@@ -172,151 +193,194 @@ __device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], 
             oij[m] = o[i][m] - o[j][m];
             x[m] = X[i][m] - X[j][m];
         }
-        D2[k] = dot3d(x, x);
+        S.D2[k] = dot3d(x, x);
         c[k] = dot3d(d[i], d[j]);
         a[k] = dot3d(d[i], oij);
         b[k] = dot3d(d[j], oij);
-        e[k] = dot3d(oij, oij) - D2[k];
+        e[k] = dot3d(oij, oij) - S.D2[k];
     }
     // feasible lambda_1: real lambda_2 (pair 1,2) and real lambda_3 (pair 1,3)
     double lo2, hi2, lo3, hi3;
-    if (!gp_feasible(c[0] * c[0] - 1.0, c[0] * b[0] - a[0], b[0] * b[0] - e[0], lo2, hi2)) return;
-    if (!gp_feasible(c[1] * c[1] - 1.0, c[1] * b[1] - a[1], b[1] * b[1] - e[1], lo3, hi3)) return;
+    if (!gp_feasible(c[0] * c[0] - 1.0, c[0] * b[0] - a[0], b[0] * b[0] - e[0], lo2, hi2)) return false;
+    if (!gp_feasible(c[1] * c[1] - 1.0, c[1] * b[1] - a[1], b[1] * b[1] - e[1], lo3, hi3)) return false;
     double lo = fmax(fmax(lo2, lo3), 0.0), hi = fmin(hi2, hi3);
-    if (!(hi > lo)) return;
+    if (!(hi > lo)) return false;
     const double pad = 1e-9 * (hi - lo) + 1e-12 * hi;
-    lo = fmax(lo - pad, 0.0);
-    hi += pad;
+    S.lo = fmax(lo - pad, 0.0);
+    S.hi = hi + pad;
 
-    // polynomials in lambda_1 (ascending)
-    const double p[2] = {b[0], c[0]}, q[3] = {e[0], 2.0 * a[0], 1.0};  // l2^2 - 2 p l2 + q
-    const double r[2] = {b[1], c[1]}, s[3] = {e[1], 2.0 * a[1], 1.0};  // l3^2 - 2 r l3 + s
-    const double A = -2.0 * c[2];
-    const double B[2] = {2.0 * (p[0] + a[2]), 2.0 * p[1]};
-    const double C[2] = {2.0 * (r[0] - b[2]), 2.0 * r[1]};
-    const double E[3] = {e[2] - q[0] - s[0], -q[1] - s[1], -q[2] - s[2]};
-    // F(l2) = f2 l2^2 + f1 l2 + f0 from pair (1,3) with l3 = -(B l2 + E) / (A l2 + C)
-    double f2[3], f1[4], f0[5];
+    const double p[2] = {b[0], c[0]};  // G: l2^2 - 2 p l2 + q
+    S.q[0] = e[0];
+    S.q[1] = 2.0 * a[0];
+    S.q[2] = 1.0;
+    S.r[0] = b[1];
+    S.r[1] = c[1];
+    S.s[0] = e[1];
+    S.s[1] = 2.0 * a[1];
+    S.s[2] = 1.0;
+    S.A = -2.0 * c[2];
+    S.B[0] = 2.0 * (p[0] + a[2]);
+    S.B[1] = 2.0 * p[1];
+    S.C[0] = 2.0 * (S.r[0] - b[2]);
+    S.C[1] = 2.0 * S.r[1];
+    S.E[0] = e[2] - S.q[0] - S.s[0];
+    S.E[1] = -S.q[1] - S.s[1];
+    S.E[2] = -S.q[2] - S.s[2];
+    const double A = S.A;
     {
         double BB[3], rB[3];
-        gp_mul<1, 1>(B, B, BB);
-        gp_mul<1, 1>(r, B, rB);
+        gp_mul<1, 1>(S.B, S.B, BB);
+        gp_mul<1, 1>(S.r, S.B, rB);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) f2[k] = BB[k] + 2.0 * A * rB[k] + A * A * s[k];
+        for (int k = 0; k < 3; ++k) S.f2[k] = BB[k] + 2.0 * A * rB[k] + A * A * S.s[k];
         double BE[4], BC[3], rBC[4], rE[4], sC[4];
-        gp_mul<1, 2>(B, E, BE);
-        gp_mul<1, 1>(B, C, BC);
-        gp_mul<1, 2>(r, BC, rBC);
-        gp_mul<1, 2>(r, E, rE);
-        gp_mul<2, 1>(s, C, sC);
+        gp_mul<1, 2>(S.B, S.E, BE);
+        gp_mul<1, 1>(S.B, S.C, BC);
+        gp_mul<1, 2>(S.r, BC, rBC);
+        gp_mul<1, 2>(S.r, S.E, rE);
+        gp_mul<2, 1>(S.s, S.C, sC);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) f1[k] = 2.0 * (BE[k] + rBC[k] + A * rE[k] + A * sC[k]);
+        for (int k = 0; k < 4; ++k) S.f1[k] = 2.0 * (BE[k] + rBC[k] + A * rE[k] + A * sC[k]);
         double EE[5], rEC[5], CC[3], sCC[5];
-        gp_mul<2, 2>(E, E, EE);
-        gp_mul<3, 1>(rE, C, rEC);
-        gp_mul<1, 1>(C, C, CC);
-        gp_mul<2, 2>(s, CC, sCC);
+        gp_mul<2, 2>(S.E, S.E, EE);
+        gp_mul<3, 1>(rE, S.C, rEC);
+        gp_mul<1, 1>(S.C, S.C, CC);
+        gp_mul<2, 2>(S.s, CC, sCC);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) f0[k] = EE[k] + 2.0 * rEC[k] + sCC[k];
+        for (int k = 0; k < 5; ++k) S.f0[k] = EE[k] + 2.0 * rEC[k] + sCC[k];
     }
-    // G(l2) = l2^2 + g1 l2 + g0; resultant (f2 g0 - f0)^2 - (f2 g1 - f1)(f1 g0 - f0 g1)
-    const double g1[2] = {-2.0 * p[0], -2.0 * p[1]};
-    double oct[9];
+    S.g1[0] = -2.0 * p[0];
+    S.g1[1] = -2.0 * p[1];
     {
-        double t1[5], t2[4], t3[6], tmp5[5], tmp4[4], tmp6[6];
-        gp_mul<2, 2>(f2, q, tmp5);
+        // resultant (f2 g0 - f0)^2 - (f2 g1 - f1)(f1 g0 - f0 g1)
+        double t1[5], t2[4], t3[6], tmp5[5], tmp4[4], tmp6[6], f0g1[6];
+        gp_mul<2, 2>(S.f2, S.q, tmp5);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) t1[k] = tmp5[k] - f0[k];
-        gp_mul<2, 1>(f2, g1, tmp4);
+        for (int k = 0; k < 5; ++k) t1[k] = tmp5[k] - S.f0[k];
+        gp_mul<2, 1>(S.f2, S.g1, tmp4);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) t2[k] = tmp4[k] - f1[k];
-        gp_mul<3, 2>(f1, q, tmp6);
+        for (int k = 0; k < 4; ++k) t2[k] = tmp4[k] - S.f1[k];
+        gp_mul<3, 2>(S.f1, S.q, tmp6);
+        gp_mul<4, 1>(S.f0, S.g1, f0g1);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) t3[k] = tmp6[k];
-        double f0g1[6];
-        gp_mul<4, 1>(f0, g1, f0g1);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) t3[k] -= f0g1[k];
+        for (int k = 0; k < 6; ++k) t3[k] = tmp6[k] - f0g1[k];
         double t11[9], t23[9];
         gp_mul<4, 4>(t1, t1, t11);
         gp_mul<3, 5>(t2, t3, t23);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) oct[k] = t11[k] - t23[k];
+        for (int k = 0; k < 9; ++k) S.oct[k] = t11[k] - t23[k];
     }
+    return true;
+}
 
-    // sign changes of the octic on a grid over [lo, hi], refined by safeguarded
-    // Newton.  Two roots closer than the grid step leave no sign change, but p'
-    // changes sign between them: such a cell is split at the extremum of p.
-    // Chebyshev spacing: roots crowd towards the ends of the feasible interval
-    // (where lambda_2 or lambda_3 turns complex), so the cells are finest there
-    double xa = gp_node(cell0, lo, hi), pa, dpa;
-    gp_eval_d<8>(oct, xa, pa, dpa);
-    double roots[kGp3pMaxSol];
-    int nroots = 0;
-    for (int gi = cell0 + 1; gi <= cell1 && nroots < kGp3pMaxSol; ++gi) {
-        const double xb = gp_node(gi, lo, hi);
+// Root brackets of the octic over the feasible interval, ascending: sign
+// changes between grid nodes, and cells whose ends agree in sign but not in
+// slope split at the extremum of p (two close roots).  Chebyshev spacing
+// (roots crowd towards the ends of the interval, where lambda_2 or lambda_3
+// turns complex): node j = mid - half cos(pi j / G), the cosines by the
+// three-term recurrence cos((j+1)a) = 2 cos(a) cos(ja) - cos((j-1)a)
+// (error ~1e-14 over the grid; the nodes need no more).  Returns the count.
+__device__ inline int gp3p_brackets(const Gp3pSys& S, Gp3pBracket* br, int nmax) {
+    static_assert(kGp3pGrid == 64, "the recurrence constant is cos(pi / 64)");
+    constexpr double kCos = 0.9987954562051724;  // cos(pi / 64)
+    const double mid = 0.5 * (S.lo + S.hi), half = 0.5 * (S.hi - S.lo);
+    double cprev = kCos, ccur = 1.0;
+    int n = 0;
+    double xa = S.lo, pa, dpa;
+    gp_eval_d<8>(S.oct, xa, pa, dpa);
+    for (int gi = 1; gi <= kGp3pGrid && n < nmax; ++gi) {
+        const double cnext = 2.0 * kCos * ccur - cprev;
+        cprev = ccur;
+        ccur = cnext;
+        const double xb = gi == kGp3pGrid ? S.hi : mid - half * ccur;
         double pb, dpb;
-        gp_eval_d<8>(oct, xb, pb, dpb);
+        gp_eval_d<8>(S.oct, xb, pb, dpb);
         if (pa == 0.0) {
-            roots[nroots++] = xa;
+            br[n++] = Gp3pBracket{xa, xa, 0.0};
         } else if (pb != 0.0 && (pa < 0.0) != (pb < 0.0)) {
-            roots[nroots++] = gp_refine(oct, xa, xb, pa);
+            br[n++] = Gp3pBracket{xa, xb, pa};
         } else if (pb != 0.0 && (dpa < 0.0) != (dpb < 0.0)) {
-            // extremum of p inside the cell: bisection on p'
-            double l = xa, u = xb;
-            for (int it = 0; it < 50; ++it) {
-                const double m = 0.5 * (l + u);
-                double pm, dpm;
-                gp_eval_d<8>(oct, m, pm, dpm);
-                if ((dpm < 0.0) == (dpa < 0.0)) l = m; else u = m;
+            // the extremum: Newton on p' kept inside the bracket where p' changes sign
+            double l = xa, u = xb, x = 0.5 * (xa + xb), pe = pa;
+            for (int it = 0; it < 16; ++it) {
+                double p0, p1, p2;
+                gp_eval_dd<8>(S.oct, x, p0, p1, p2);
+                pe = p0;
+                if ((p1 < 0.0) == (dpa < 0.0)) l = x; else u = x;
+                double xn = x - p1 / p2;
+                if (!(xn > l && xn < u)) xn = 0.5 * (l + u);
+                const bool conv = fabs(xn - x) <= 1e-13 * fabs(x) || (u - l) <= 1e-13 * fabs(u);
+                x = xn;
+                if (conv) break;
             }
-            const double xe = 0.5 * (l + u);
-            const double pe = gp_eval<8>(oct, xe);
-            if ((pe < 0.0) != (pa < 0.0) && nroots + 2 <= kGp3pMaxSol) {
-                roots[nroots++] = gp_refine(oct, xa, xe, pa);
-                roots[nroots++] = gp_refine(oct, xe, xb, pe);
+            const double xe = x;
+            pe = gp_eval<8>(S.oct, xe);
+            if ((pe < 0.0) != (pa < 0.0) && n + 2 <= nmax) {
+                br[n++] = Gp3pBracket{xa, xe, pa};
+                br[n++] = Gp3pBracket{xe, xb, pe};
             }
         }
         xa = xb;
         pa = pb;
         dpa = dpb;
     }
+    return n;
+}
 
-    for (int ri = 0; ri < nroots; ++ri) {
-        // back-substitution: the common root of F and G, then l3 from the bilinear relation
-        const double l1 = roots[ri];
-        const double f2v = gp_eval<2>(f2, l1), f1v = gp_eval<3>(f1, l1), f0v = gp_eval<4>(f0, l1);
-        const double g1v = gp_eval<1>(g1, l1), g0v = gp_eval<2>(q, l1);
-        double l2;
-        const double den = f1v - f2v * g1v;
-        if (fabs(den) > 1e-12 * (fabs(f1v) + fabs(f2v * g1v))) {
-            l2 = -(f0v - f2v * g0v) / den;
-        } else {  // F = f2 G: take the root of G nearer to the vertex (double-root case)
-            l2 = -0.5 * g1v + sqrt(fmax(0.25 * g1v * g1v - g0v, 0.0));
-        }
-        const double Bv = gp_eval<1>(B, l1), Cv = gp_eval<1>(C, l1), Ev = gp_eval<2>(E, l1);
-        const double den3 = A * l2 + Cv;
-        double l3;
-        if (fabs(den3) > 1e-12 * (fabs(A * l2) + fabs(Cv))) {
-            l3 = -(Bv * l2 + Ev) / den3;
-        } else {
-            const double rv = gp_eval<1>(r, l1), sv = gp_eval<2>(s, l1);
-            l3 = rv + sqrt(fmax(rv * rv - sv, 0.0));
-        }
-        double L[3] = {l1, l2, l3};
-        for (int it = 0; it < 4; ++it) {
-            double f[3], J[3][3], dl[3];
-            gp_system(o, d, D2, L, f, J);
-            if (!gp_solve3(J, f, dl)) break;
-            L[0] -= dl[0];
-            L[1] -= dl[1];
-            L[2] -= dl[2];
-        }
-        double f[3], J[3][3];
-        gp_system(o, d, D2, L, f, J);
-        bool ok = L[0] > 0.0 && L[1] > 0.0 && L[2] > 0.0;
+// The root in a bracket, lambda_2 and lambda_3 by back-substitution (the
+// common root of F and G, then the bilinear relation), Newton on the three
+// distance equations; true if the triple is a solution with positive depths.
+__device__ inline bool gp3p_finish(const Gp3pSys& S, const double o[3][3], const double d[3][3],
+                                   const Gp3pBracket& b, double L[3]) {
+    const double l1 = b.u > b.l ? gp_refine(S.oct, b.l, b.u, b.pl) : b.l;
+    const double f2v = gp_eval<2>(S.f2, l1), f1v = gp_eval<3>(S.f1, l1), f0v = gp_eval<4>(S.f0, l1);
+    const double g1v = gp_eval<1>(S.g1, l1), g0v = gp_eval<2>(S.q, l1);
+    double l2;
+    const double den = f1v - f2v * g1v;
+    if (fabs(den) > 1e-12 * (fabs(f1v) + fabs(f2v * g1v))) {
+        l2 = -(f0v - f2v * g0v) / den;
+    } else {  // F = f2 G: take the root of G nearer to the vertex (double-root case)
+        l2 = -0.5 * g1v + sqrt(fmax(0.25 * g1v * g1v - g0v, 0.0));
+    }
+    const double Bv = gp_eval<1>(S.B, l1), Cv = gp_eval<1>(S.C, l1), Ev = gp_eval<2>(S.E, l1);
+    const double den3 = S.A * l2 + Cv;
+    double l3;
+    if (fabs(den3) > 1e-12 * (fabs(S.A * l2) + fabs(Cv))) {
+        l3 = -(Bv * l2 + Ev) / den3;
+    } else {
+        const double rv = gp_eval<1>(S.r, l1), sv = gp_eval<2>(S.s, l1);
+        l3 = rv + sqrt(fmax(rv * rv - sv, 0.0));
+    }
+    L[0] = l1;
+    L[1] = l2;
+    L[2] = l3;
+    for (int it = 0; it < 4; ++it) {
+        double f[3], J[3][3], dl[3];
+        gp_system(o, d, S.D2, L, f, J);
+        if (!gp_solve3(J, f, dl)) break;
+        L[0] -= dl[0];
+        L[1] -= dl[1];
+        L[2] -= dl[2];
+    }
+    double f[3], J[3][3];
+    gp_system(o, d, S.D2, L, f, J);
+    bool ok = L[0] > 0.0 && L[1] > 0.0 && L[2] > 0.0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ok = ok && fabs(f[k]) <= 1e-8 * (1.0 + D2[k]);
+    for (int k = 0; k < 3; ++k) ok = ok && fabs(f[k]) <= 1e-8 * (1.0 + S.D2[k]);
+    return ok;
+}
+
+// All solutions on one thread (lambda triples, ascending lambda_1, all
+// positive; solutions closer than 1e-6 relative are one).
+__device__ inline void gp3p_lambdas(const double o[3][3], const double d[3][3], const double X[3][3], Gp3pSol& out) {
+    out.n = 0;
+    Gp3pSys S;
+    if (!gp3p_setup(o, d, X, S)) return;
+    Gp3pBracket br[kGp3pMaxSol];
+    const int nb = gp3p_brackets(S, br, kGp3pMaxSol);
+    for (int i = 0; i < nb; ++i) {
+        double L[3];
+        bool ok = gp3p_finish(S, o, d, br[i], L);
         for (int j = 0; j < out.n && ok; ++j)
             if (fabs(out.lam[j][0] - L[0]) <= 1e-6 * (1.0 + L[0]) && fabs(out.lam[j][1] - L[1]) <= 1e-6 * (1.0 + L[1]) &&
                 fabs(out.lam[j][2] - L[2]) <= 1e-6 * (1.0 + L[2]))

@@ -8,10 +8,12 @@
 // Kernels (per wave of rounds, all queries of the batch in each launch):
 //   k_rig_setup   per query: N, the subset (uniform stride) regrouped by
 //                 camera with a stable counting sort, round words
-//   k_rig_sample  one minimal sample per 8 threads: Philox triple, the three
-//                 rays in the rig frame, GP3P in FP64 (gp3p.cuh; each thread
-//                 scans 1/8 of the root grid), <= 8 poses into slot 8 s + k,
-//                 a compact list of the valid slots
+//   k_rig_sample  one minimal sample per thread: Philox triple, the three
+//                 rays in the rig frame, the GP3P octic (gp3p.cuh, FP64) and
+//                 its root brackets, appended to a list
+//   k_rig_solve   one root bracket per thread: the root, back-substitution,
+//                 Newton polish, the pose into slot 8 s + k (k = the root's
+//                 rank in its sample), a compact list of the valid slots
 //   k_rig_score   (query, tile of 256 poses, chunk of 1,024 subset records)
 //                 per CTA, 2 poses per thread: the chunk staged in shared
 //                 memory, per camera run the poses composed with that camera
@@ -45,8 +47,6 @@ namespace {
 constexpr int kRigMaxCams = IMLOC_RIG_MAX_CAMERAS;
 constexpr int kRigSlots = 8;           // GP3P solutions per minimal sample
 constexpr int kRigSampleThreads = 128;
-constexpr int kRigLanes = 8;           // threads per minimal sample (GP3P grid slices)
-constexpr int kRigLaneSols = 4;        // solutions one slice keeps
 constexpr int kRigScoreThreads = 128;
 constexpr int kRigHT = 2;              // poses per scoring thread
 constexpr int kRigTile = kRigScoreThreads * kRigHT;
@@ -59,6 +59,11 @@ struct RigCam {
     float R[9], t[3];      // cam_from_rig
     double Rd[9], td[3];
     double o[3];           // camera centre in the rig frame, -R^T t
+};
+
+struct RigBracket {
+    double l, u, pl;     // root bracket of the sample's octic
+    int32_t sl, k;       // sample within the wave, rank of the root
 };
 
 struct RigQuery {
@@ -83,6 +88,8 @@ struct RigQuery {
     PoseF* slots;        // wave samples * 8
     int32_t* compact;    // wave samples * 8: valid slots of the wave
     int32_t* n_compact;
+    RigBracket* brk;     // wave samples * 8 root brackets
+    int32_t* n_brk;
     float2* part;        // wave samples * 8 * chunks: partial (cost, count bits) per pose and chunk
     uint64_t* round_best;
     int32_t* round_hyps;
@@ -236,73 +243,79 @@ __device__ __forceinline__ void rig_ray(const RigQuery& d, int64_t i, double o[3
     X[2] = __ldg(d.Z + i);
 }
 
-// kRigLanes threads per minimal sample: each scans 1/kRigLanes of the GP3P
-// root grid (and finishes the roots it finds); the group then writes its
-// poses in ascending lambda_1 order.
+// Phase 1, one thread per minimal sample: the triple, the rays, the GP3P
+// coefficients and the root brackets over the whole grid, appended to the
+// query's bracket list with their rank k (ascending lambda_1).
 __global__ void __launch_bounds__(kRigSampleThreads) k_rig_sample(const __grid_constant__ RigWave w) {
     const int q = blockIdx.y;
     const RigQuery& d = w.qd[q];
     const RigState& st = w.qs[q];
-    const int lane = threadIdx.x % kRigLanes;
-    const int sl = (blockIdx.x * kRigSampleThreads + threadIdx.x) / kRigLanes;
+    const int sl = blockIdx.x * kRigSampleThreads + threadIdx.x;
+    if (sl >= (w.r1 - w.r0) * d.batch || st.done) return;
     const int64_t s = static_cast<int64_t>(w.r0) * d.batch + sl;
-    // every thread reaches the group shuffles below; `live` marks real work
-    bool live = sl < (w.r1 - w.r0) * d.batch && !st.done && s < d.max_iters;
-    PoseF* slot = d.slots + static_cast<int64_t>(sl) * kRigSlots;
-    PoseF mine[kRigLaneSols];
-    int nmine = 0;
-    if (live && d.inject) {
-        if (lane == 0 && s < d.n_inject) mine[nmine++] = d.inject[s];
-    } else if (live) {
-        int tri[3];
-        const bool ok = draw_triple(d.seed, d.query_id, static_cast<uint32_t>(s), static_cast<uint32_t>(st.m), tri);
-        if (d.triples && lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) d.triples[3 * s + k] = ok ? tri[k] : -1;
-        }
-        if (ok) {
-            double o[3][3], dir[3][3], X[3][3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                rig_ray(d, st.off + (static_cast<int64_t>(tri[k]) * st.n) / st.m, o[k], dir[k], X[k]);
-            Gp3pSol sol;
-            const int cells = kGp3pGrid / kRigLanes;
-            gp3p_lambdas(o, dir, X, sol, lane * cells, (lane + 1) * cells);
-            for (int k = 0; k < sol.n && nmine < kRigLaneSols; ++k) {
-                double P[3][3], R[9], t[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) P[i][a] = o[i][a] + sol.lam[k][i] * dir[i][a];
-                if (!gp_pose(X, P, R, t)) continue;
-                PoseF pf;
-#pragma unroll
-                for (int a = 0; a < 9; ++a) pf.R[a] = static_cast<float>(R[a]);
-#pragma unroll
-                for (int a = 0; a < 3; ++a) pf.t[a] = static_cast<float>(t[a]);
-                mine[nmine++] = pf;
-            }
-        }
+    if (s >= d.max_iters) return;
+    if (d.inject) {  // test mode: the given pose, id 8 s
+        if (s >= d.n_inject) return;
+        d.slots[static_cast<int64_t>(sl) * kRigSlots] = d.inject[s];
+        const int at = atomicAdd(d.n_compact, 1);
+        d.compact[at] = sl * kRigSlots;
+        atomicAdd(d.round_hyps + static_cast<int>(s / d.batch), 1);
+        return;
     }
-    // exclusive prefix of the solution counts within the group (lane order = ascending lambda_1)
-    int incl = nmine;
+    int tri[3];
+    const bool ok = draw_triple(d.seed, d.query_id, static_cast<uint32_t>(s), static_cast<uint32_t>(st.m), tri);
+    if (d.triples) {
 #pragma unroll
-    for (int o = 1; o < kRigLanes; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o, kRigLanes);
-        if (lane >= o) incl += v;
+        for (int k = 0; k < 3; ++k) d.triples[3 * s + k] = ok ? tri[k] : -1;
     }
-    const int total = min(__shfl_sync(0xffffffffu, incl, kRigLanes - 1, kRigLanes), kRigSlots);
-    const int first = incl - nmine;
-    int at = 0;
-    if (lane == kRigLanes - 1 && total > 0) at = atomicAdd(d.n_compact, total);
-    at = __shfl_sync(0xffffffffu, at, kRigLanes - 1, kRigLanes);
-    for (int k = 0; k < nmine; ++k) {
-        const int pos = first + k;
-        if (pos >= kRigSlots) break;
-        slot[pos] = mine[k];
-        d.compact[at + pos] = sl * kRigSlots + pos;
-    }
-    if (lane == 0 && total > 0) atomicAdd(d.round_hyps + static_cast<int>(s / d.batch), total);
+    if (!ok) return;
+    double o[3][3], dir[3][3], X[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rig_ray(d, st.off + (static_cast<int64_t>(tri[k]) * st.n) / st.m, o[k], dir[k], X[k]);
+    Gp3pSys S;
+    if (!gp3p_setup(o, dir, X, S)) return;
+    Gp3pBracket br[kRigSlots];
+    const int nb = gp3p_brackets(S, br, kRigSlots);
+    if (nb == 0) return;
+    const int at = atomicAdd(d.n_brk, nb);
+    for (int k = 0; k < nb; ++k) d.brk[at + k] = RigBracket{br[k].l, br[k].u, br[k].pl, sl, k};
+}
+
+// Phase 2, one thread per root bracket: the sample's system again, the root,
+// back-substitution and Newton polish, the pose into slot 8 s + k.
+__global__ void __launch_bounds__(kRigSampleThreads) k_rig_solve(const __grid_constant__ RigWave w) {
+    const int q = blockIdx.y;
+    const RigQuery& d = w.qd[q];
+    const RigState& st = w.qs[q];
+    const int i = blockIdx.x * kRigSampleThreads + threadIdx.x;
+    if (st.done || i >= *d.n_brk) return;
+    const RigBracket b = d.brk[i];
+    const int64_t s = static_cast<int64_t>(w.r0) * d.batch + b.sl;
+    int tri[3];
+    draw_triple(d.seed, d.query_id, static_cast<uint32_t>(s), static_cast<uint32_t>(st.m), tri);
+    double o[3][3], dir[3][3], X[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) rig_ray(d, st.off + (static_cast<int64_t>(tri[k]) * st.n) / st.m, o[k], dir[k], X[k]);
+    Gp3pSys S;
+    gp3p_setup(o, dir, X, S);
+    double L[3];
+    if (!gp3p_finish(S, o, dir, Gp3pBracket{b.l, b.u, b.pl}, L)) return;
+    double P[3][3], R[9], t[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) P[k][a] = o[k][a] + L[k] * dir[k][a];
+    if (!gp_pose(X, P, R, t)) return;
+    PoseF pf;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) pf.R[a] = static_cast<float>(R[a]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) pf.t[a] = static_cast<float>(t[a]);
+    const int slot = b.sl * kRigSlots + b.k;
+    d.slots[slot] = pf;
+    const int at = atomicAdd(d.n_compact, 1);
+    d.compact[at] = slot;
+    atomicAdd(d.round_hyps + static_cast<int>(s / d.batch), 1);
 }
 
 // ============================================================================
@@ -435,6 +448,7 @@ struct RigReplaySmem {
     double R[9], t[3];        // pose of the pass
     double Rc[9], tc[3];      // candidate pose
     double H[21], g[6], cost;
+    double Hs[21], gs[6];     // normal equations of the current pose (damping retries)
     int32_t count, used;
     double wsum[kRigReplayThreads / 32][30];
     float Pc[kRigMaxCams][12];   // K_k [R_k R | R_k t + t_k] of the pass pose, FP32
@@ -655,17 +669,20 @@ __device__ void rig_apply(const double dl[6], const double R[9], const double t[
 // Gauss-Newton with the schedule of the single-camera loop: steps kept only if
 // the cost drops (Marquardt damping 0, 1e-3, 1e-2, 1e-1 of diag H), stop on a
 // step below 1e-10 or a decrease below 1e-6 of the cost.  Pose in S.R/S.t.
+// Each pass at a candidate also forms its normal equations, so an accepted
+// step costs one pass (the equations of the next step are already there).
 template <int SRC, int LOSS>
 __device__ double rig_gauss_newton(RigReplaySmem& S, const RigQuery& d, RigState& st, int iters) {
     const int tid = threadIdx.x;
     rig_set_pose(S, d);
-    rig_pass<SRC, LOSS, false>(S, d, st);
+    rig_pass<SRC, LOSS, true>(S, d, st);
     double cost = S.cost;
     if (tid == 0) st.passes += 1;
     for (int it = 0; it < iters; ++it) {
-        rig_pass<SRC, LOSS, true>(S, d, st);
-        if (tid == 0) st.passes += 1;
         if (S.used < 3) break;
+        __syncthreads();
+        if (tid < 21) S.Hs[tid] = S.H[tid];
+        if (tid < 6) S.gs[tid] = S.g[tid];
         const double R0[9] = {S.R[0], S.R[1], S.R[2], S.R[3], S.R[4], S.R[5], S.R[6], S.R[7], S.R[8]};
         const double t0[3] = {S.t[0], S.t[1], S.t[2]};
         bool ok = false;
@@ -674,7 +691,7 @@ __device__ double rig_gauss_newton(RigReplaySmem& S, const RigQuery& d, RigState
             __syncthreads();
             if (tid == 0) {
                 double dl[6];
-                S.ok = rig_solve6(S.H, S.g, mu, dl);
+                S.ok = rig_solve6(S.Hs, S.gs, mu, dl);
                 if (S.ok) {
                     rig_apply(dl, R0, t0, S.R, S.t);
                     double n2 = 0.0;
@@ -685,7 +702,7 @@ __device__ double rig_gauss_newton(RigReplaySmem& S, const RigQuery& d, RigState
             __syncthreads();
             if (S.ok) {
                 rig_set_pose(S, d);
-                rig_pass<SRC, LOSS, false>(S, d, st);
+                rig_pass<SRC, LOSS, true>(S, d, st);
                 if (tid == 0) st.passes += 1;
                 cn = S.cost;
                 step2 = S.step2;
@@ -975,7 +992,7 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
     int32_t* active = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t)));
     int32_t* h_active = static_cast<int32_t*>(staging_alloc(ctx, sizeof(int32_t)));
     uint8_t* fix = static_cast<uint8_t*>(ws_alloc(ctx, static_cast<size_t>(std::max<int64_t>(corr->capacity, 1))));
-    int32_t* n_compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * nq));
+    int32_t* n_compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * 2 * nq));  // poses, brackets
     if (!hd || !dd || !qs || !active || !h_active || !fix || !n_compact) return IMLOC_ERR_OOM;
     for (int q = 0; q < nq; ++q) {
         const imloc_ransac_opts& o = hq[q].o;
@@ -1030,6 +1047,8 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
                                   : static_cast<PoseF*>(ws_alloc(ctx, sizeof(PoseF) * wave_samples * kRigSlots));
         d.compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * wave_samples * kRigSlots));
         d.n_compact = n_compact + q;
+        d.n_brk = n_compact + nq + q;
+        d.brk = static_cast<RigBracket*>(ws_alloc(ctx, sizeof(RigBracket) * wave_samples * kRigSlots));
         d.part = static_cast<float2*>(ws_alloc(ctx, sizeof(float2) * wave_samples * kRigSlots *
                                                          ((o.max_score_corr + kRigChunk - 1) / kRigChunk)));
         d.round_best = hq[q].round_best_out
@@ -1042,7 +1061,7 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         d.score_by_id = hq[q].score_by_id;
         d.count_by_id = hq[q].count_by_id;
         d.triples = hq[q].triples;
-        if (!d.rec || !d.recxy || !d.seg || !d.slots || !d.compact || !d.n_compact || !d.part || !d.round_best ||
+        if (!d.rec || !d.recxy || !d.seg || !d.slots || !d.compact || !d.brk || !d.part || !d.round_best ||
             !d.round_hyps)
             return IMLOC_ERR_OOM;
     }
@@ -1066,11 +1085,18 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         w.final_wave = wi + 1 == waves.size();
         w.pad = 0;
         const int64_t ns = static_cast<int64_t>(w.r1 - w.r0) * max_batch;  // samples of the largest batch
-        IMLOC_CUDA_TRY(cudaMemsetAsync(n_compact, 0, sizeof(int32_t) * nq, st));
+        IMLOC_CUDA_TRY(cudaMemsetAsync(n_compact, 0, sizeof(int32_t) * 2 * nq, st));
         {
             ProfScope prof(ctx, st, "k_rig_sample");
-            k_rig_sample<<<dim3(static_cast<unsigned>((ns * kRigLanes + kRigSampleThreads - 1) / kRigSampleThreads), nq),
+            k_rig_sample<<<dim3(static_cast<unsigned>((ns + kRigSampleThreads - 1) / kRigSampleThreads), nq),
                            kRigSampleThreads, 0, st>>>(w);
+            IMLOC_CUDA_TRY(cudaGetLastError());
+            prof.end();
+        }
+        {
+            ProfScope prof(ctx, st, "k_rig_solve");
+            k_rig_solve<<<dim3(static_cast<unsigned>((ns * kRigSlots + kRigSampleThreads - 1) / kRigSampleThreads), nq),
+                          kRigSampleThreads, 0, st>>>(w);
             IMLOC_CUDA_TRY(cudaGetLastError());
             prof.end();
         }
