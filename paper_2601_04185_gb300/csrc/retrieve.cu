@@ -170,6 +170,86 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_retrieve_gemm(const __grid_
 // ---- top-K selection ---------------------------------------------------------
 // key: orderable score bits << 32 | (0xffffffff - index): larger key = higher
 // score, then lower index; 0 = padding (below every real key)
+// ---- one or two queries: the search is a matrix-vector product, bound by
+// reading the database once.  Each warp streams whole rows (16-byte loads,
+// 8 in flight per lane, consecutive lanes on consecutive 16 bytes) against
+// the queries held as FP32 in shared memory (two planes, so that the 16-byte
+// shared loads of a warp are contiguous); per-lane FP32 sums in a fixed
+// order, then a fixed shuffle tree: identical rows give identical scores.
+constexpr int kGemvThreads = 512;
+constexpr int kGemvMaxQ = 2;
+constexpr int kGemvUnroll = 8;
+
+struct GemvParams {
+    const uint4* db;  // [N][D / 8]: 8 bf16 per uint4
+    const uint4* q;   // [Q][D / 8]
+    float* scores;    // [Q][ld]
+    int64_t ld, N;
+    int32_t D8, pad;
+};
+
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+template <int Q>
+__global__ void __launch_bounds__(kGemvThreads) k_retrieve_gemv(const __grid_constant__ GemvParams p) {
+    extern __shared__ float4 s_q[];  // [Q][2][D8]: values 0-3 and 4-7 of each group of 8
+    const int D8 = p.D8;
+    for (int i = threadIdx.x; i < Q * D8; i += kGemvThreads) {
+        const int qq = i / D8, j = i - qq * D8;
+        const uint4 v = p.q[static_cast<int64_t>(qq) * D8 + j];
+        s_q[(2 * qq) * D8 + j] = make_float4(bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y));
+        s_q[(2 * qq + 1) * D8 + j] = make_float4(bf16_lo(v.z), bf16_hi(v.z), bf16_lo(v.w), bf16_hi(v.w));
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = static_cast<int64_t>(gridDim.x) * (kGemvThreads / 32);
+    for (int64_t row = static_cast<int64_t>(blockIdx.x) * (kGemvThreads / 32) + (threadIdx.x >> 5); row < p.N;
+         row += nw) {
+        const uint4* r = p.db + row * D8;
+        float acc[Q];
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) acc[qq] = 0.f;
+        for (int j0 = lane; j0 < D8; j0 += 32 * kGemvUnroll) {
+            uint4 v[kGemvUnroll];
+#pragma unroll
+            for (int u = 0; u < kGemvUnroll; ++u) {
+                const int j = j0 + 32 * u;
+                v[u] = j < D8 ? __ldcs(r + j) : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < kGemvUnroll; ++u) {
+                const int j = j0 + 32 * u;
+                if (j < D8) {
+#pragma unroll
+                    for (int qq = 0; qq < Q; ++qq) {
+                        const float4 a = s_q[(2 * qq) * D8 + j], b = s_q[(2 * qq + 1) * D8 + j];
+                        float t = acc[qq];
+                        t = fmaf(bf16_lo(v[u].x), a.x, t);
+                        t = fmaf(bf16_hi(v[u].x), a.y, t);
+                        t = fmaf(bf16_lo(v[u].y), a.z, t);
+                        t = fmaf(bf16_hi(v[u].y), a.w, t);
+                        t = fmaf(bf16_lo(v[u].z), b.x, t);
+                        t = fmaf(bf16_hi(v[u].z), b.y, t);
+                        t = fmaf(bf16_lo(v[u].w), b.z, t);
+                        t = fmaf(bf16_hi(v[u].w), b.w, t);
+                        acc[qq] = t;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int qq = 0; qq < Q; ++qq) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc[qq] += __shfl_xor_sync(0xffffffffu, acc[qq], o);
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int qq = 0; qq < Q; ++qq) p.scores[qq * p.ld + row] = acc[qq];
+        }
+    }
+}
+
 __device__ __forceinline__ uint64_t score_key(float s, uint32_t idx) {
     const uint32_t u = __float_as_uint(s);
     const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
@@ -599,7 +679,30 @@ extern "C" int imloc_retrieve_topk_async(imloc_ctx* ctx, const uint16_t* queries
             IMLOC_CUDA_TRY(cudaFuncSetAttribute(k_topk_select<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                                 cudaSharedmemCarveoutMaxShared));
             const int grid = std::min(n_tiles, ctx->sm_count);
-            {
+            const size_t vsmem = sizeof(float) * static_cast<size_t>(Qg) * dim;
+            if (Qg <= kGemvMaxQ && vsmem <= (160u << 10)) {
+                GemvParams vp;
+                vp.db = reinterpret_cast<const uint4*>(db);
+                vp.q = reinterpret_cast<const uint4*>(queries + static_cast<int64_t>(q0) * dim);
+                vp.scores = scores;
+                vp.ld = ld;
+                vp.N = n_db;
+                vp.D8 = dim / 8;
+                vp.pad = 0;
+                auto kern = Qg == 1 ? k_retrieve_gemv<1> : k_retrieve_gemv<2>;
+                IMLOC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    static_cast<int>(vsmem)));
+                int per_sm = 0;
+                IMLOC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGemvThreads, vsmem));
+                if (per_sm < 1) return IMLOC_ERR_CUDA;
+                const int64_t rows_per_block = kGemvThreads / 32;
+                const int vgrid = static_cast<int>(
+                    std::min<int64_t>(static_cast<int64_t>(per_sm) * ctx->sm_count, (n_db + rows_per_block - 1) / rows_per_block));
+                ProfScope prof(ctx, st, "k_retrieve_gemv");
+                kern<<<vgrid, kGemvThreads, vsmem, st>>>(vp);
+                IMLOC_CUDA_TRY(cudaGetLastError());
+                prof.end();
+            } else {
                 ProfScope prof(ctx, st, "k_retrieve_gemm");
                 k_retrieve_gemm<<<grid, kGemmThreads, smem, st>>>(gp);
                 IMLOC_CUDA_TRY(cudaGetLastError());

@@ -67,7 +67,11 @@ def run(ctx, q, db, k):
 
 
 @pytest.mark.parametrize("seed,Q,N,D,k", [(0, 33, 5000, 768, 50), (1, 1, 1000, 64, 10), (2, 300, 3000, 256, 10),
-                                           (3, 17, 20, 128, 50), (4, 256, 1029, 4096, 128)])
+                                           (3, 17, 20, 128, 50), (4, 256, 1029, 4096, 128),
+                                           # one or two queries: the matrix-vector kernel, rows of D / 8
+                                           # 16-byte words not a multiple of the warp, k > N
+                                           (5, 2, 777, 296, 7), (6, 1, 3, 8, 5), (7, 2, 20, 200, 50),
+                                           (8, 1, 4099, 2056, 128)])
 def test_against_the_oracle(ctx, seed, Q, N, D, k):
     db, q, _ = synth.retrieval_set(np.random.default_rng(seed), N, Q, D)
     gs, gi = run(ctx, q, db, k)
