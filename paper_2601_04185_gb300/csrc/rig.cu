@@ -21,7 +21,7 @@
 //                 and inlier count per (pose, chunk)
 //   k_rig_reduce  per pose: the partials in chunk order, one 64-bit atomic
 //                 min into its round word
-//   k_rig_replay  one CTA per query: the rounds of the wave in order (new best
+//   k_rig_replay  one cluster of CTAs per query: the rounds of the wave in order (new best
 //                 -> LO on the subset), the adaptive stop, and once a query is
 //                 done the final Cauchy refinement over all its
 //                 correspondences; Gauss-Newton passes reduce FP32 per-thread
@@ -451,6 +451,7 @@ struct RigReplaySmem {
     double Hs[21], gs[6];     // normal equations of the current pose (damping retries)
     int32_t count, used;
     double wsum[kRigReplayThreads / 32][30];
+    double part[32];             // this CTA's sums of a pass (read by the whole cluster)
     float Pc[kRigMaxCams][12];   // K_k [R_k R | R_k t + t_k] of the pass pose, FP32
     float Rk[kRigMaxCams][9];    // R_k
     float Rf[9], tf[3];          // pass pose, FP32
@@ -570,15 +571,18 @@ __device__ void rig_pass(RigReplaySmem& S, const RigQuery& d, const RigState& st
             }
         }
     };
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = static_cast<int>(cluster.block_rank()), ncl = static_cast<int>(cluster.num_blocks());
+    const int stride = ncl * kRigReplayThreads, first = rank * kRigReplayThreads + tid;
     if (SRC == kSrcSubset) {
         for (int k = 0; k < d.n_cams; ++k)
-            for (int i = S.seg[k] + tid; i < S.seg[k + 1]; i += kRigReplayThreads) {
+            for (int i = S.seg[k] + first; i < S.seg[k + 1]; i += stride) {
                 const float4 X = d.rec[i];
                 const float2 xy = d.recxy[i];
                 point(k, X.x, X.y, X.z, X.w, xy.x, xy.y);
             }
     } else {
-        for (int64_t i = st.off + tid; i < st.off + st.n; i += kRigReplayThreads) {
+        for (int64_t i = st.off + first; i < st.off + st.n; i += stride) {
             if (SRC == kSrcFixed && !d.fix[i]) continue;
             point(__ldg(d.cam + i), __ldg(d.X + i), __ldg(d.Y + i), __ldg(d.Z + i), __ldg(d.w + i), __ldg(d.x + i),
                   __ldg(d.y + i));
@@ -597,13 +601,20 @@ __device__ void rig_pass(RigReplaySmem& S, const RigQuery& d, const RigState& st
     if (tid < 30 && (NORMAL || tid >= 27)) {
         double s = 0.0;
         for (int w = 0; w < kRigReplayThreads / 32; ++w) s += S.wsum[w][tid];
+        S.part[tid] = s;
+    }
+    cluster.sync();
+    // every CTA of the cluster adds the CTAs' sums in rank order: identical totals
+    if (tid < 30 && (NORMAL || tid >= 27)) {
+        double s = 0.0;
+        for (int r = 0; r < ncl; ++r) s += cluster.map_shared_rank(S.part, r)[tid];
         if (tid < 21) S.H[tid] = s;
         else if (tid < 27) S.g[tid - 21] = s;
         else if (tid == 27) S.cost = s;
         else if (tid == 28) S.count = static_cast<int32_t>(s + 0.5);
         else S.used = static_cast<int32_t>(s + 0.5);
     }
-    __syncthreads();
+    cluster.sync();  // the partial sums may be overwritten by the next pass only now
 }
 
 __device__ bool rig_solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
@@ -752,14 +763,21 @@ __device__ double rig_needed_iters(double eps, double p_miss) {
     return log(p_miss) / log(1.0 - e3);
 }
 
+// One cluster of CTAs per query: every CTA runs the same decisions on the
+// same cluster-reduced sums; the points of each pass are split across the
+// CTAs; rank 0 writes the state and the result.
 __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_constant__ RigWave w) {
-    const int q = blockIdx.x, tid = threadIdx.x;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = static_cast<int>(cluster.block_rank()), ncl = static_cast<int>(cluster.num_blocks());
+    const int q = blockIdx.x / ncl, tid = threadIdx.x;
+    const bool lead = rank == 0 && tid == 0;
+    const int first = rank * kRigReplayThreads + tid, stride = ncl * kRigReplayThreads;
     const RigQuery& d = w.qd[q];
     __shared__ RigReplaySmem S;
     __shared__ RigState st;
     if (tid == 0) st = w.qs[q];
     if (tid <= kRigMaxCams) S.seg[tid] = tid <= d.n_cams ? d.seg[tid] : 0;
-    __syncthreads();
+    cluster.sync();  // every CTA has read the state before rank 0 may write it
     if (st.finished) return;
     const int64_t rounds_total = (d.max_iters + d.batch - 1) / d.batch;
     if (!st.done) {
@@ -824,7 +842,7 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         __syncthreads();
     }
     if (!st.done) {
-        if (tid == 0) w.qs[q] = st;
+        if (lead) w.qs[q] = st;
         return;
     }
     // final refinement over all correspondences: fixed set = inliers of the best model
@@ -835,7 +853,7 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         __syncthreads();
         rig_set_pose(S, d);
         const float tau2 = d.tau2;
-        for (int64_t i = st.off + tid; i < st.off + st.n; i += kRigReplayThreads) {
+        for (int64_t i = st.off + first; i < st.off + st.n; i += stride) {
             const int k = __ldg(d.cam + i);
             const float* P = S.Pc[k];
             const float X = __ldg(d.X + i), Y = __ldg(d.Y + i), Z = __ldg(d.Z + i);
@@ -848,7 +866,7 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
                 const float r0 = fmaf(u, iz, -__ldg(d.x + i)), r1 = fmaf(v, iz, -__ldg(d.y + i));
                 in = fmaf(r0, r0, r1 * r1) < tau2;
             }
-            d.fix[i] = in ? 1 : 0;
+            d.fix[i] = in ? 1 : 0;  // read back by this CTA only (same partition)
         }
         __syncthreads();
         if (d.final_iters > 0) rig_gauss_newton<kSrcFixed, kLossCauchy>(S, d, st, d.final_iters);
@@ -856,7 +874,7 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         rig_set_pose(S, d);
         // inliers of the final pose over all correspondences (and the mask)
         int cnt = 0;
-        for (int64_t i = st.off + tid; i < st.off + st.n; i += kRigReplayThreads) {
+        for (int64_t i = st.off + first; i < st.off + st.n; i += stride) {
             const int k = __ldg(d.cam + i);
             const float* P = S.Pc[k];
             const float X = __ldg(d.X + i), Y = __ldg(d.Y + i), Z = __ldg(d.Z + i);
@@ -878,6 +896,12 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         if (tid == 0) {
             double tot = 0.0;
             for (int w2 = 0; w2 < kRigReplayThreads / 32; ++w2) tot += S.wsum[w2][0];
+            S.part[0] = tot;
+        }
+        cluster.sync();
+        if (lead) {
+            double tot = 0.0;
+            for (int r2 = 0; r2 < ncl; ++r2) tot += cluster.map_shared_rank(S.part, r2)[0];
             imloc_result r;
             memset(&r, 0, sizeof(r));
             for (int a = 0; a < 9; ++a) {
@@ -902,8 +926,8 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         }
     } else {
         if (d.mask)
-            for (int64_t i = st.off + tid; i < st.off + st.n; i += kRigReplayThreads) d.mask[i] = 0;
-        if (tid == 0) {
+            for (int64_t i = st.off + first; i < st.off + st.n; i += stride) d.mask[i] = 0;
+        if (lead) {
             imloc_result r;
             memset(&r, 0, sizeof(r));
             r.iterations = st.iters;
@@ -914,11 +938,12 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
             *res = r;
         }
     }
-    if (tid == 0) {
+    if (lead) {
         st.finished = 1;
         w.qs[q] = st;
         atomicSub(w.active, 1);
     }
+    cluster.sync();  // no CTA leaves while another may still read its shared memory
 }
 
 // ============================================================================
@@ -937,6 +962,24 @@ struct RigHostQuery {
     PoseF* slots_out;
     uint64_t* round_best_out;
 };
+
+template <typename K, typename P>
+int rig_launch_cluster(K kernel, const P& params, int grid, int block, int cluster, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    IMLOC_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, params));
+    return IMLOC_OK;
+}
 
 bool rig_ok(const imloc_rig& r) {
     if (r.n_cams < 1 || r.n_cams > kRigMaxCams) return false;
@@ -979,6 +1022,9 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
     }
     int wave_rounds = 0;
     for (auto& wv : waves) wave_rounds = std::max(wave_rounds, wv.second - wv.first);
+    // replay: a cluster of up to 8 CTAs per query while the batch leaves SMs free
+    int replay_cl = 8;
+    while (replay_cl > 1 && static_cast<int64_t>(nq) * replay_cl > ctx->sm_count) replay_cl >>= 1;
     int max_batch = 0, max_chunks = 1;
     for (int q = 0; q < nq; ++q) {
         max_batch = std::max(max_batch, hq[q].o.batch);
@@ -1115,8 +1161,8 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
         }
         {
             ProfScope prof(ctx, st, "k_rig_replay");
-            k_rig_replay<<<nq, kRigReplayThreads, 0, st>>>(w);
-            IMLOC_CUDA_TRY(cudaGetLastError());
+            rc = rig_launch_cluster(k_rig_replay, w, nq * replay_cl, kRigReplayThreads, replay_cl, st);
+            if (rc != IMLOC_OK) return rc;
             prof.end();
         }
         if (w.final_wave) break;
