@@ -123,7 +123,7 @@ struct RigWave {
 // ============================================================================
 // setup
 // ============================================================================
-__global__ void __launch_bounds__(1024) k_rig_setup(const RigQuery* __restrict__ qd, RigState* qs, int32_t* active) {
+__global__ void __launch_bounds__(1024) k_rig_setup(const RigQuery* __restrict__ qd, RigState* qs) {
     const int q = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const RigQuery& d = qd[q];
     __shared__ int64_t s_off, s_n;
@@ -220,7 +220,6 @@ __global__ void __launch_bounds__(1024) k_rig_setup(const RigQuery* __restrict__
         qs[q].done = 1;
         if (qs[q].status == IMLOC_OK) qs[q].status = IMLOC_ERR_DEGENERATE;
     }
-    (void)active;
 }
 
 // ============================================================================
@@ -1117,7 +1116,7 @@ int rig_impl(imloc_ctx* ctx, int nq, const imloc_corr* corr, const int32_t* d_ca
     IMLOC_CUDA_TRY(cudaMemcpyAsync(active, h_active, sizeof(int32_t), cudaMemcpyHostToDevice, st));
     {
         ProfScope prof(ctx, st, "k_rig_setup");
-        k_rig_setup<<<nq, 1024, 0, st>>>(dd, qs, active);
+        k_rig_setup<<<nq, 1024, 0, st>>>(dd, qs);
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
     }
