@@ -18,12 +18,15 @@
 // Root finding is bracketing, not a full polynomial solve: every real
 // solution has real lambda_2 and lambda_3, so lambda_1 lies where the
 // discriminants of both quadratics are >= 0 -- a bounded interval (the rays
-// are not parallel).  The octic is sampled on a grid over that interval with
-// Chebyshev spacing (roots crowd towards its ends); each sign change is
-// refined by safeguarded Newton, and a cell whose ends agree in sign but not
-// in slope is split at the extremum (two close roots).  lambda_2 and
-// lambda_3 follow by back-substitution, and Newton on the three distance
-// equations polishes the triple.  The pose comes from the two triangles'
+// are not parallel).  The octic, rewritten in mu over that interval, is
+// scanned at Chebyshev nodes (roots crowd towards the interval's ends); each
+// sign change brackets a root, and a cell whose ends agree in sign but not in
+// slope is split at the extremum (two close roots).  Each root is refined to
+// float precision, lambda_2 and lambda_3 follow by back-substitution, and
+// Newton on the three distance equations (FP64) polishes the triple.  The
+// scan and the root refinement run in double-float on the FP32 pipe (this
+// GPU's FP64 rate is 1/64 of FP32); the coefficients, the back-substitution
+// and the polish are FP64.  The pose comes from the two triangles'
 // orthonormal frames.  Roots that touch zero without a sign change (a double
 // solution: an ill-conditioned, degenerate configuration) are not reported.
 #pragma once
@@ -48,31 +51,6 @@ __device__ __forceinline__ double gp_eval(const double (&c)[D + 1], double x) {
     for (int k = D - 1; k >= 0; --k) a = fma(a, x, c[k]);
     return a;
 }
-template <int D>
-__device__ __forceinline__ void gp_eval_d(const double (&c)[D + 1], double x, double& p, double& dp) {
-    p = c[D];
-    dp = 0.0;
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-        dp = fma(dp, x, p);
-        p = fma(p, x, c[k]);
-    }
-}
-
-template <int D>
-__device__ __forceinline__ void gp_eval_dd(const double (&c)[D + 1], double x, double& p, double& dp, double& ddp) {
-    p = c[D];
-    dp = 0.0;
-    ddp = 0.0;
-#pragma unroll
-    for (int k = D - 1; k >= 0; --k) {
-        ddp = fma(ddp, x, dp);
-        dp = fma(dp, x, p);
-        p = fma(p, x, c[k]);
-    }
-    ddp *= 2.0;
-}
-
 // out = a * b (degrees A, B)
 template <int A, int B>
 __device__ __forceinline__ void gp_mul(const double (&a)[A + 1], const double (&b)[B + 1], double (&out)[A + B + 1]) {
@@ -83,13 +61,6 @@ __device__ __forceinline__ void gp_mul(const double (&a)[A + 1], const double (&
 #pragma unroll
         for (int j = 0; j <= B; ++j) out[i + j] = fma(a[i], b[j], out[i + j]);
 }
-// acc += s * a (deg(a) <= deg(acc))
-template <int A, int N>
-__device__ __forceinline__ void gp_axpy(double (&acc)[N + 1], double s, const double (&a)[A + 1]) {
-#pragma unroll
-    for (int k = 0; k <= A; ++k) acc[k] = fma(s, a[k], acc[k]);
-}
-
 __device__ __forceinline__ double dot3d(const double* a, const double* b) {
     return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
 }
@@ -137,29 +108,6 @@ __device__ __forceinline__ bool gp_solve3(const double A[3][3], const double b[3
 #pragma unroll
     for (int r = 0; r < 3; ++r) x[r] = inv[r][0] * b[0] + inv[r][1] * b[1] + inv[r][2] * b[2];
     return true;
-}
-
-// root of p in [l, u] where p changes sign (p(l) = pl): Newton steps kept
-// inside the shrinking bracket, bisection otherwise
-__device__ inline double gp_refine(const double (&c)[9], double l, double u, double pl) {
-    double x = 0.5 * (l + u);
-    for (int it = 0; it < 60; ++it) {
-        double px, dpx;
-        gp_eval_d<8>(c, x, px, dpx);
-        if (px == 0.0) return x;
-        if ((px < 0.0) == (pl < 0.0)) {
-            l = x;
-            pl = px;
-        } else {
-            u = x;
-        }
-        double xn = x - px / dpx;
-        if (!(xn > l && xn < u)) xn = 0.5 * (l + u);
-        const bool conv = fabs(xn - x) <= 1e-15 * fabs(x) || (u - l) <= 1e-15 * fabs(u);
-        x = xn;
-        if (conv) break;
-    }
-    return x;
 }
 
 // Everything the root search and the back-substitution need for one minimal
@@ -273,54 +221,122 @@ __device__ inline bool gp3p_setup(const double o[3][3], const double d[3][3], co
     return true;
 }
 
+// Double-float (float hi + lo, ~48-bit significand on the FP32 pipe; this
+// GPU's FP64 rate is 1/64 of FP32) for the grid scan of the octic.
+struct gdf {
+    float hi, lo;
+};
+__device__ __forceinline__ gdf gdf_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return gdf{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ gdf gdf_fast_two_sum(float a, float b) {  // |a| >= |b|
+    const float s = __fadd_rn(a, b);
+    return gdf{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ gdf gdf_add(gdf a, gdf b) {
+    const gdf s = gdf_two_sum(a.hi, b.hi);
+    return gdf_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ gdf gdf_mul_f(gdf a, float b) {  // a * b, b exact in float
+    const float p = __fmul_rn(a.hi, b);
+    return gdf_fast_two_sum(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+__device__ __forceinline__ bool gdf_neg(gdf a) { return a.hi < 0.0f || (a.hi == 0.0f && a.lo < 0.0f); }
+__device__ __forceinline__ bool gdf_zero(gdf a) { return a.hi == 0.0f && a.lo == 0.0f; }
+
+// p, p' and p''/2 at mu of the polynomial with double-float coefficients c[0..8]
+__device__ __forceinline__ void gdf_horner(const gdf (&c)[9], float mu, gdf& p, gdf& dp, gdf& ddp, bool second) {
+    p = c[8];
+    dp = gdf{0.0f, 0.0f};
+    ddp = gdf{0.0f, 0.0f};
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        if (second) ddp = gdf_add(gdf_mul_f(ddp, mu), dp);
+        dp = gdf_add(gdf_mul_f(dp, mu), p);
+        p = gdf_add(gdf_mul_f(p, mu), c[k]);
+    }
+}
+
 // Root brackets of the octic over the feasible interval, ascending: sign
 // changes between grid nodes, and cells whose ends agree in sign but not in
-// slope split at the extremum of p (two close roots).  Chebyshev spacing
-// (roots crowd towards the ends of the interval, where lambda_2 or lambda_3
-// turns complex): node j = mid - half cos(pi j / G), the cosines by the
-// three-term recurrence cos((j+1)a) = 2 cos(a) cos(ja) - cos((j-1)a)
-// (error ~1e-14 over the grid; the nodes need no more).  Returns the count.
+// slope split at the extremum of p (two close roots).  The octic is first
+// rewritten in mu, x = mid + half mu (Taylor shift in FP64, coefficients
+// scaled to a largest magnitude of 1) and scanned in double-float at the
+// Chebyshev nodes mu_j = -cos(pi j / G) (roots crowd towards the ends of the
+// interval, where lambda_2 or lambda_3 turns complex).  Brackets are
+// returned in x.  Returns the count.
+// The octic in mu, x = mid + half mu: Taylor shift in FP64, coefficients
+// scaled to a largest magnitude of 1, as double-floats; false if degenerate.
+__device__ inline bool gp3p_shifted(const Gp3pSys& S, double mid, double half, gdf (&c)[9]) {
+    {
+        double b[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) b[k] = S.oct[k];
+        // coefficients of p(mid + y): repeated synthetic division by (y - mid)
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int k = 7; k >= i; --k) b[k] = fma(mid, b[k + 1], b[k]);
+        double h = 1.0, mx = 0.0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            b[k] *= h;
+            h *= half;
+            mx = fmax(mx, fabs(b[k]));
+        }
+        if (!(mx > 0.0) || !isfinite(mx)) return false;
+        const double inv = 1.0 / mx;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const double v = b[k] * inv;
+            const float hi = static_cast<float>(v);
+            c[k] = gdf{hi, static_cast<float>(v - static_cast<double>(hi))};
+        }
+    }
+    return true;
+}
+
 __device__ inline int gp3p_brackets(const Gp3pSys& S, Gp3pBracket* br, int nmax) {
-    static_assert(kGp3pGrid == 64, "the recurrence constant is cos(pi / 64)");
-    constexpr double kCos = 0.9987954562051724;  // cos(pi / 64)
     const double mid = 0.5 * (S.lo + S.hi), half = 0.5 * (S.hi - S.lo);
-    double cprev = kCos, ccur = 1.0;
+    gdf c[9];
+    if (!gp3p_shifted(S, mid, half, c)) return 0;
+    auto x_of = [&](float mu) { return mu == -1.0f ? S.lo : (mu == 1.0f ? S.hi : mid + half * static_cast<double>(mu)); };
     int n = 0;
-    double xa = S.lo, pa, dpa;
-    gp_eval_d<8>(S.oct, xa, pa, dpa);
+    float ma = -1.0f;
+    gdf pa, dpa, dd;
+    gdf_horner(c, ma, pa, dpa, dd, false);
     for (int gi = 1; gi <= kGp3pGrid && n < nmax; ++gi) {
-        const double cnext = 2.0 * kCos * ccur - cprev;
-        cprev = ccur;
-        ccur = cnext;
-        const double xb = gi == kGp3pGrid ? S.hi : mid - half * ccur;
-        double pb, dpb;
-        gp_eval_d<8>(S.oct, xb, pb, dpb);
-        if (pa == 0.0) {
-            br[n++] = Gp3pBracket{xa, xa, 0.0};
-        } else if (pb != 0.0 && (pa < 0.0) != (pb < 0.0)) {
-            br[n++] = Gp3pBracket{xa, xb, pa};
-        } else if (pb != 0.0 && (dpa < 0.0) != (dpb < 0.0)) {
+        const float mb = gi == kGp3pGrid ? 1.0f : -cospif(static_cast<float>(gi) * (1.0f / kGp3pGrid));
+        gdf pb, dpb;
+        gdf_horner(c, mb, pb, dpb, dd, false);
+        if (gdf_zero(pa)) {
+            br[n++] = Gp3pBracket{x_of(ma), x_of(ma), 0.0};
+        } else if (!gdf_zero(pb) && gdf_neg(pa) != gdf_neg(pb)) {
+            br[n++] = Gp3pBracket{x_of(ma), x_of(mb), gdf_neg(pa) ? -1.0 : 1.0};
+        } else if (!gdf_zero(pb) && gdf_neg(dpa) != gdf_neg(dpb)) {
             // the extremum: Newton on p' kept inside the bracket where p' changes sign
-            double l = xa, u = xb, x = 0.5 * (xa + xb), pe = pa;
-            for (int it = 0; it < 16; ++it) {
-                double p0, p1, p2;
-                gp_eval_dd<8>(S.oct, x, p0, p1, p2);
-                pe = p0;
-                if ((p1 < 0.0) == (dpa < 0.0)) l = x; else u = x;
-                double xn = x - p1 / p2;
-                if (!(xn > l && xn < u)) xn = 0.5 * (l + u);
-                const bool conv = fabs(xn - x) <= 1e-13 * fabs(x) || (u - l) <= 1e-13 * fabs(u);
-                x = xn;
+            float l = ma, u = mb, m = 0.5f * (ma + mb);
+            for (int it = 0; it < 20; ++it) {
+                gdf p0, p1, p2;
+                gdf_horner(c, m, p0, p1, p2, true);
+                if (gdf_neg(p1) == gdf_neg(dpa)) l = m; else u = m;
+                const float d2 = 2.0f * __fadd_rn(p2.hi, p2.lo);  // the recurrence gives p'' / 2
+                float mn = m - __fadd_rn(p1.hi, p1.lo) / d2;
+                if (!(mn > l && mn < u)) mn = 0.5f * (l + u);
+                const bool conv = mn == m || u - l <= 4e-7f * fabsf(u) + 1e-30f;
+                m = mn;
                 if (conv) break;
             }
-            const double xe = x;
-            pe = gp_eval<8>(S.oct, xe);
-            if ((pe < 0.0) != (pa < 0.0) && n + 2 <= nmax) {
-                br[n++] = Gp3pBracket{xa, xe, pa};
-                br[n++] = Gp3pBracket{xe, xb, pe};
+            gdf pe, de;
+            gdf_horner(c, m, pe, de, dd, false);
+            if (gdf_neg(pe) != gdf_neg(pa) && !gdf_zero(pe) && n + 2 <= nmax && m > ma && m < mb) {
+                br[n++] = Gp3pBracket{x_of(ma), x_of(m), gdf_neg(pa) ? -1.0 : 1.0};
+                br[n++] = Gp3pBracket{x_of(m), x_of(mb), gdf_neg(pe) ? -1.0 : 1.0};
             }
         }
-        xa = xb;
+        ma = mb;
         pa = pb;
         dpa = dpb;
     }
@@ -332,7 +348,29 @@ __device__ inline int gp3p_brackets(const Gp3pSys& S, Gp3pBracket* br, int nmax)
 // distance equations; true if the triple is a solution with positive depths.
 __device__ inline bool gp3p_finish(const Gp3pSys& S, const double o[3][3], const double d[3][3],
                                    const Gp3pBracket& b, double L[3]) {
-    const double l1 = b.u > b.l ? gp_refine(S.oct, b.l, b.u, b.pl) : b.l;
+    // the root to float precision in mu (double-float octic, Newton kept in the
+    // bracket); the Newton steps on the distance equations below finish it
+    double l1 = b.l;
+    if (b.u > b.l) {
+        const double mid = 0.5 * (S.lo + S.hi), half = 0.5 * (S.hi - S.lo);
+        gdf c[9];
+        if (!gp3p_shifted(S, mid, half, c)) return false;
+        float l = static_cast<float>((b.l - mid) / half), u = static_cast<float>((b.u - mid) / half);
+        const bool neg_l = b.pl < 0.0;
+        float m = 0.5f * (l + u);
+        for (int it = 0; it < 40; ++it) {
+            gdf p, dp, dd;
+            gdf_horner(c, m, p, dp, dd, false);
+            if (gdf_zero(p)) break;
+            if (gdf_neg(p) == neg_l) l = m; else u = m;
+            float mn = m - __fadd_rn(p.hi, p.lo) / __fadd_rn(dp.hi, dp.lo);
+            if (!(mn > l && mn < u)) mn = 0.5f * (l + u);
+            const bool conv = mn == m || u - l <= 2.4e-7f * fabsf(u) + 1e-30f;
+            m = mn;
+            if (conv) break;
+        }
+        l1 = mid + half * static_cast<double>(m);
+    }
     const double f2v = gp_eval<2>(S.f2, l1), f1v = gp_eval<3>(S.f1, l1), f0v = gp_eval<4>(S.f0, l1);
     const double g1v = gp_eval<1>(S.g1, l1), g0v = gp_eval<2>(S.q, l1);
     double l2;
