@@ -14,8 +14,8 @@
 //   k_rig_solve   one root bracket per thread: the root, back-substitution,
 //                 Newton polish, the pose into slot 8 s + k (k = the root's
 //                 rank in its sample), a compact list of the valid slots
-//   k_rig_score   (query, tile of 256 poses, chunk of 1,024 subset records)
-//                 per CTA, 2 poses per thread: the chunk staged in shared
+//   k_rig_score   (query, tile of 128 poses, chunk of 1,024 subset records)
+//                 per CTA, one pose per thread: the chunk staged in shared
 //                 memory, per camera run the poses composed with that camera
 //                 (K_k [R_k R | R_k t + t_k], FP32); partial truncated cost
 //                 and inlier count per (pose, chunk)
@@ -48,7 +48,7 @@ constexpr int kRigMaxCams = IMLOC_RIG_MAX_CAMERAS;
 constexpr int kRigSlots = 8;           // GP3P solutions per minimal sample
 constexpr int kRigSampleThreads = 128;
 constexpr int kRigScoreThreads = 128;
-constexpr int kRigHT = 2;              // poses per scoring thread
+constexpr int kRigHT = 1;              // poses per scoring thread
 constexpr int kRigTile = kRigScoreThreads * kRigHT;
 constexpr int kRigChunk = 1024;        // subset records per scoring CTA (staged in shared memory)
 constexpr int kRigReplayThreads = 512;
