@@ -152,7 +152,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # distributed plumbing (one process per GPU, no data-path collective)
 # ---------------------------------------------------------------------------
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """Join the process group of a torchrun launch (RANK / WORLD_SIZE /
+    LOCAL_RANK / MASTER_* from the environment): one process per GPU over
+    NCCL; `backend="gloo"` runs the same plumbing on CPU processes."""
     import torch
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -161,9 +164,12 @@ def dist_setup(n_gpus):
     if world > 1:
         import torch.distributed as dist
 
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
+    elif backend == "nccl":
         torch.cuda.set_device(0)
     return rank, world, local
 
@@ -175,26 +181,35 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def _over_ranks(v, world, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(v, world):
+    """The slowest rank's time (the job's time): MAX over ranks."""
+    import torch.distributed as dist
+
+    return v if world == 1 else _over_ranks(v, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
+    """Work of the whole job: SUM over ranks (weak scaling, fixed work per rank)."""
     import torch.distributed as dist
 
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return v if world == 1 else _over_ranks(v, world, dist.ReduceOp.SUM)
+
+
+def rank_seed(base, rank):
+    """Each rank localizes its own queries (independent problems: no data-path collective)."""
+    return base + 1000 * rank
 
 
 # ---------------------------------------------------------------------------
@@ -799,7 +814,7 @@ def run_ours(args):
     from paper_2601_04185_gb300 import imloc
 
     # inputs first (process pools before CUDA starts in this process)
-    queries = make_queries(args.queries, 100 + 1000 * int(os.environ.get("RANK", "0")))
+    queries = make_queries(args.queries, rank_seed(100, int(os.environ.get("RANK", "0"))))
     serving_inputs = None
     if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_serving:
         serving_inputs = make_store_and_queries(2024, args.serve_queries)
