@@ -686,7 +686,7 @@ def run_precision_study(args):
                                  for r, q in zip(res, qs)])
             within = float(np.mean((rot <= 0.05) & (trans <= 5.0)))
             out["variants"].append({
-                "p3p": "fp32+fp64 polish" if polish else "fp32", "lo_normal_equations": "fp64" if lo64 else "fp32",
+                "p3p": "fp32 + double-float polish" if polish else "fp32", "lo_normal_equations": "fp64" if lo64 else "fp32",
                 "vs_oracle_rot_deg": {"median": float(np.median(rot)), "p90": float(np.percentile(rot, 90)),
                                       "max": float(rot.max())},
                 "vs_oracle_trans_mm": {"median": float(np.median(trans)), "p90": float(np.percentile(trans, 90)),
