@@ -167,9 +167,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_retrieve_gemm(const __grid_
     }
 }
 
-// ---- top-K selection ---------------------------------------------------------
-// key: orderable score bits << 32 | (0xffffffff - index): larger key = higher
-// score, then lower index; 0 = padding (below every real key)
 // ---- one or two queries: the search is a matrix-vector product, bound by
 // reading the database once.  Each warp streams whole rows (16-byte loads,
 // 8 in flight per lane, consecutive lanes on consecutive 16 bytes) against
@@ -250,6 +247,9 @@ __global__ void __launch_bounds__(kGemvThreads) k_retrieve_gemv(const __grid_con
     }
 }
 
+// ---- top-K selection ---------------------------------------------------------
+// key: orderable score bits << 32 | (0xffffffff - index): larger key = higher
+// score, then lower index; 0 = padding (below every real key)
 __device__ __forceinline__ uint64_t score_key(float s, uint32_t idx) {
     const uint32_t u = __float_as_uint(s);
     const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
