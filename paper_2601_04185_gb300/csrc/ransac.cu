@@ -1000,11 +1000,12 @@ struct ScoreParams {
 // chunk 0 while the rest lands, no block barrier between chunks, and the
 // next item of the same query reuses the data.  Every thread scores HT poses
 // held in registers against every record pair of the share: the projection
-// (9 of the 14 FP32-pipe operations per pose and record) runs as fma.f32x2
-// on both records of a pair (the pose coefficients are duplicated into both
-// halves), the rest in scalar FP32 on the unpacked halves, so that the
-// issue slots the packed instructions free serve the reciprocal, min/max
-// and shared-memory loads and the FP32 pipe, not issue, is the limit.  Per
+// and the residual (13 of the 14 FP32-pipe operations per pose and record)
+// run as fma/mul.f32x2 on both records of a pair (the pose coefficients are
+// duplicated into both halves; the observed pixels of a pair are stored as
+// pairs), the reciprocal, the truncation and the weighted sum in scalar FP32
+// on the unpacked halves, so that the issue slots the packed instructions
+// free serve the reciprocal, min/max and shared-memory loads.  Per
 // chunk, the even and the odd records of the chunk are summed separately, in
 // order, and the chunk adds even + odd to the pose's total: the partial sums
 // do not depend on (THREADS, HT).
@@ -1134,16 +1135,16 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
                         const uint64_t zu = f2_fma(P[h][0], X2, f2_fma(P[h][1], Y2, f2_fma(P[h][2], Z2, P[h][3])));
                         const uint64_t zv = f2_fma(P[h][4], X2, f2_fma(P[h][5], Y2, f2_fma(P[h][6], Z2, P[h][7])));
                         const uint64_t zz = f2_fma(P[h][8], X2, f2_fma(P[h][9], Y2, f2_fma(P[h][10], Z2, P[h][11])));
-                        float u0, u1, v0, v1, z0, z1;
-                        f2_unpack(zu, u0, u1);
-                        f2_unpack(zv, v0, v1);
+                        float z0, z1;
                         f2_unpack(zz, z0, z1);
-                        // the rest per record in scalar FP32 (no repacking)
                         // z <= 0 (or NaN) -> 1/0 = inf -> r2 inf/NaN -> min(., tau2) = tau2
                         const float i0 = rcp_approx(fmaxf(z0, 0.0f)), i1 = rcp_approx(fmaxf(z1, 0.0f));
-                        const float du0 = fmaf(u0, i0, E.x), dv0 = fmaf(v0, i0, E.z);
-                        const float du1 = fmaf(u1, i1, E.y), dv1 = fmaf(v1, i1, E.w);
-                        const float r0 = fmaf(du0, du0, dv0 * dv0), r1 = fmaf(du1, du1, dv1 * dv1);
+                        // residuals of both records packed again (E holds -x0 -x1 -y0 -y1 as pairs)
+                        const uint64_t iz2 = f2_pack(i0, i1);
+                        const uint64_t du2 = f2_fma(zu, iz2, f2_pack(E.x, E.y));
+                        const uint64_t dv2 = f2_fma(zv, iz2, f2_pack(E.z, E.w));
+                        float r0, r1;
+                        f2_unpack(f2_fma(du2, du2, f2_mul(dv2, dv2)), r0, r1);
                         pe[h] = fmaf(B.z, fminf(r0, tau2), pe[h]);
                         po[h] = fmaf(B.w, fminf(r1, tau2), po[h]);
                         if (COUNT) cnt[h] += ((r0 < tau2) ? 1 : 0) + ((r1 < tau2) ? 1 : 0);
