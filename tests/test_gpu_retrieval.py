@@ -109,3 +109,15 @@ def test_thousands_of_equal_scores(ctx):
     gs, gi = run(ctx, q, same, 64)  # 256 queries: chunks of 4,096
     assert (gi == np.arange(64)[None, :]).all()
     assert (gs == gs[:, :1]).all()
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    t = torch()
+    q = t.zeros((2, 64), dtype=t.int16, device="cuda")
+    db = t.zeros((10, 64), dtype=t.int16, device="cuda")
+    for bad in (dict(k=0), dict(k=129)):
+        with pytest.raises(imloc.ImlocError):
+            ctx.retrieve_topk(q, db, bad["k"])
+    with pytest.raises(imloc.ImlocError):  # dim not a multiple of 8
+        ctx.retrieve_topk(t.zeros((2, 60), dtype=t.int16, device="cuda"), t.zeros((10, 60), dtype=t.int16, device="cuda"), 5)
+    assert ctx.device_error() == 0

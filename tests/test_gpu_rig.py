@@ -275,3 +275,24 @@ def test_bad_camera_index_and_degenerate_queries(ctx):
     assert res[0]["status"] == 0
     assert res[1]["status"] == -1  # invalid argument
     assert res[2]["status"] == -7
+
+
+def test_invalid_rigs_and_options_are_rejected(ctx):
+    q = synth.rig_query(np.random.default_rng(65), n_per_cam=50, n_cams=2)
+    for mutate in ("no_cams", "nine_cams", "zero_focal", "enumerate"):
+        rg = imloc.rig(q["K"], q["R_cam"], q["t_cam"])
+        opts = imloc.default_opts(max_iters=512, batch=256)
+        if mutate == "no_cams":
+            rg.n_cams = 0
+        elif mutate == "nine_cams":
+            rg.n_cams = 9
+        elif mutate == "zero_focal":
+            rg.cams[1].fx = 0.0
+        else:
+            opts.enumerate_all = 1
+        t = torch()
+        c, cam = upload(q)
+        off = t.tensor([0, len(q["x"])], dtype=t.int64, device="cuda")
+        out = t.zeros(imloc.RESULT_BYTES, dtype=t.uint8, device="cuda")
+        with pytest.raises(imloc.ImlocError):
+            ctx.ransac_rig_batch(c, cam, off, [rg], [opts], out)
