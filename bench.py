@@ -44,7 +44,7 @@ UNIT = "hyp*corr/s"
 HYPOTHESES = 10000
 MATCHES_PER_PAIR = 5000
 N_VIEWS = 10
-FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored pair, see the design doc
+FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored (pose, correspondence) pair
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of k_score on the 16-query C2 step, from
