@@ -450,7 +450,8 @@ struct RigReplaySmem {
     double Hs[21], gs[6];     // normal equations of the current pose (damping retries)
     int32_t count, used;
     double wsum[kRigReplayThreads / 32][30];
-    double part[32];             // this CTA's sums of a pass (read by the whole cluster)
+    double part[2][32];          // this CTA's sums of a pass (read by the whole cluster), double-buffered
+    int32_t pbuf;                // buffer of the next pass
     float Pc[kRigMaxCams][12];   // K_k [R_k R | R_k t + t_k] of the pass pose, FP32
     float Rk[kRigMaxCams][9];    // R_k
     float Rf[9], tf[3];          // pass pose, FP32
@@ -587,33 +588,55 @@ __device__ void rig_pass(RigReplaySmem& S, const RigQuery& d, const RigState& st
                   __ldg(d.y + i));
         }
     }
-    constexpr int NV = NORMAL ? 30 : 30;
+    if (NORMAL) {
+        // butterfly reduce-scatter across the warp: after the 5 steps lane l holds
+        // the warp's total of value l (31 shuffles for 32 values instead of 5 each)
+        float v[32];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        if (!NORMAL && k < 27) continue;
-        float v = acc[k];
+        for (int k = 0; k < 32; ++k) v[k] = k < 30 ? acc[k] : 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) S.wsum[warp][k] = v;
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                const float send = upper ? v[i] : v[i + o];
+                const float keep = upper ? v[i + o] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        if (lane < 30) S.wsum[warp][lane] = v[0];
+    } else {
+#pragma unroll
+        for (int k = 27; k < 30; ++k) {
+            float v = acc[k];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) S.wsum[warp][k] = v;
+        }
     }
+    // cluster sums through a double-buffered array: a CTA writes buffer pb of
+    // this pass while a slower CTA may still read the other one from the last
+    const int pb = S.pbuf;
     __syncthreads();
     if (tid < 30 && (NORMAL || tid >= 27)) {
         double s = 0.0;
         for (int w = 0; w < kRigReplayThreads / 32; ++w) s += S.wsum[w][tid];
-        S.part[tid] = s;
+        S.part[pb][tid] = s;
     }
     cluster.sync();
     // every CTA of the cluster adds the CTAs' sums in rank order: identical totals
     if (tid < 30 && (NORMAL || tid >= 27)) {
         double s = 0.0;
-        for (int r = 0; r < ncl; ++r) s += cluster.map_shared_rank(S.part, r)[tid];
+        for (int r = 0; r < ncl; ++r) s += cluster.map_shared_rank(&S.part[pb][0], r)[tid];
         if (tid < 21) S.H[tid] = s;
         else if (tid < 27) S.g[tid - 21] = s;
         else if (tid == 27) S.cost = s;
         else if (tid == 28) S.count = static_cast<int32_t>(s + 0.5);
         else S.used = static_cast<int32_t>(s + 0.5);
     }
-    cluster.sync();  // the partial sums may be overwritten by the next pass only now
+    __syncthreads();
+    if (tid == 0) S.pbuf = pb ^ 1;
+    __syncthreads();
 }
 
 __device__ bool rig_solve6(const double Hu[21], const double g[6], double mu, double x[6]) {
@@ -774,7 +797,10 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
     const RigQuery& d = w.qd[q];
     __shared__ RigReplaySmem S;
     __shared__ RigState st;
-    if (tid == 0) st = w.qs[q];
+    if (tid == 0) {
+        st = w.qs[q];
+        S.pbuf = 0;
+    }
     if (tid <= kRigMaxCams) S.seg[tid] = tid <= d.n_cams ? d.seg[tid] : 0;
     cluster.sync();  // every CTA has read the state before rank 0 may write it
     if (st.finished) return;
@@ -895,12 +921,12 @@ __global__ void __launch_bounds__(kRigReplayThreads) k_rig_replay(const __grid_c
         if (tid == 0) {
             double tot = 0.0;
             for (int w2 = 0; w2 < kRigReplayThreads / 32; ++w2) tot += S.wsum[w2][0];
-            S.part[0] = tot;
+            S.part[S.pbuf][0] = tot;
         }
         cluster.sync();
         if (lead) {
             double tot = 0.0;
-            for (int r2 = 0; r2 < ncl; ++r2) tot += cluster.map_shared_rank(S.part, r2)[0];
+            for (int r2 = 0; r2 < ncl; ++r2) tot += cluster.map_shared_rank(&S.part[S.pbuf][0], r2)[0];
             imloc_result r;
             memset(&r, 0, sizeof(r));
             for (int a = 0; a < 9; ++a) {
