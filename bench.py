@@ -887,6 +887,19 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     kstats_unfused = ctx.profile_read(reset=True)
+    # the opt-in tensor-core scoring kernel on the same step, for comparison
+    os.environ["IMLOC_SCORE_TC"] = "1"
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_read(reset=True)
+    for _ in range(n_unfused):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    kstats_tc = ctx.profile_read(reset=True)
+    del os.environ["IMLOC_SCORE_TC"]
     del os.environ["IMLOC_NO_FUSE"]
     ctx.profile(False)
     total_s = sum(step_ms) / 1e3
@@ -1008,6 +1021,9 @@ def run_ours(args):
                      "launch_ms": score_launch_ms,
                      "note": "batches of >= 32 queries run k_score fused (each query's replay inside it once its "
                              "last pose tile is scored); this 16-query step runs scoring and replay as two kernels"},
+        "score_tc": {"launch_ms": kstats_tc.get("k_score", (1, 0))[1] / max(1, kstats_tc.get("k_score", (1, 0))[0]),
+                     "note": "opt-in tensor-core scoring kernel (IMLOC_SCORE_TC=1: projection as split-bf16 "
+                             "tcgen05.mma, FP32 epilogue from TMEM) on the same step, unfused"},
         "roofline_score_only": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                                 "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
                                 "launch_ms": score_only_ms, "replay_kernel_ms": kstats_unfused.get("k_replay", (1, 0))[1]

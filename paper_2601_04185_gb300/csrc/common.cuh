@@ -57,10 +57,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: on timeout record the error and return false; the caller
 // carries on with whatever is in shared memory so that every barrier of the
-// block (and cluster) is still reached and the kernel ends.
+// block (and cluster) is still reached and the kernel ends.  A phase that is
+// already complete returns after one non-blocking test.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_test_wait(bar, parity)) return true;
     for (uint32_t i = 0; i < kSpinLimit; ++i)
         if (mbar_try_wait(bar, parity)) return true;
     if (err) atomicCAS(err, 0, kDevTimeoutMbar);
@@ -188,6 +201,9 @@ struct QueryDesc {
     int32_t n_cap;          // capacity bound of N (mask / fixed-set buffer)
     // workspace
     ScorePair* subset;      // (m_cap + 1) / 2 record pairs
+    float4* tc_rec;         // optional, tensor-core scoring: per subset record (padded to a multiple of
+                            // 32) one 128-byte operand row of split TF32 pieces, 128-byte swizzled
+    float4* tc_e;           // with tc_rec: per record pair {-x0, -x1, -y0, -y1}, {w0, w1, 0, 0}
     PoseF* slots;           // wave_samples * 4
     int32_t* compact;       // wave_samples * 4 pose ids (valid poses of the wave)
     uint64_t* round_best;   // rounds: (score bits << 32) | pose id, min-reduced
@@ -195,7 +211,7 @@ struct QueryDesc {
     int32_t* fixidx;        // fixed inlier set of the final refinement: per replay thread, the indices of its
                             // fixed points at its own positions (same offsets as the correspondences)
     int32_t inject;         // 1: poses are given (one per sample) instead of sampled + solved
-    int32_t pad1;
+    int32_t tc_bf16;        // tc_rec rows hold bf16 pieces (else TF32 pieces)
     // optional outputs for the parity tests (one wave only)
     float* score_by_id;     // score of every pose id
     int32_t* count_by_id;   // inlier count of every pose id

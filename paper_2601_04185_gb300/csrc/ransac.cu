@@ -30,6 +30,7 @@
 //                  Gauss-Newton on SE(3) (cluster-reduced normal equations,
 //                  Jacobi-scaled 6x6 Cholesky), termination, final Cauchy
 //                  IRLS.
+#include <cuda_bf16.h>
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -45,6 +46,7 @@
 #include "ctx.h"
 #include "p3p.cuh"
 #include "ransac_internal.h"
+#include "tc.cuh"
 #include "../../include/imloc_testing.h"
 
 namespace imloc {
@@ -62,6 +64,55 @@ struct SetupParams {
 };
 
 constexpr int kSetupBlocks = 8;  // CTAs per query: they split the subset gather
+constexpr int kTcBlock = 64;     // tensor-core operand rows are padded to a multiple of this (records per MMA: 32 or 64)
+
+// FP32 -> nearest bf16 value (as an FP32)
+__device__ __forceinline__ float to_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ uint32_t bf16_pair(float lo, float hi) {
+    return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(lo))) |
+           (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(hi))) << 16);
+}
+// v = p0 + p1 + p2 up to 2^-33 |v| (TF32 pieces) or 2^-26 |v| (bf16 pieces);
+// each difference is exact in FP32
+__device__ __forceinline__ void split3(float v, bool bf, float& p0, float& p1, float& p2) {
+    p0 = bf ? to_bf16(v) : to_tf32(v);
+    const float r1 = v - p0;
+    p1 = bf ? to_bf16(r1) : to_tf32(r1);
+    const float r2 = r1 - p1;
+    p2 = bf ? to_bf16(r2) : to_tf32(r2);
+}
+// which piece of the 4-vector each of the six K terms takes: records
+// (b0, b1, b0, b2, b1, b0), poses (a0, a0, a1, a0, a1, a2)
+__host__ __device__ constexpr int term_piece(bool pose, int t) {
+    return pose ? (t == 2 || t == 4 ? 1 : (t == 5 ? 2 : 0)) : (t == 1 || t == 4 ? 1 : (t == 3 ? 2 : 0));
+}
+// One 128-byte operand row (8 chunks of 16 bytes, unswizzled order) of the
+// 4-vector v: term t (t < 6) holds piece term_piece(pose, t) of v.  TF32: chunk t = term
+// t (K = 24 of 32); bf16: chunk c = terms 2c, 2c + 1 (K = 24 of 32).  The
+// other chunks are zero.
+__device__ __forceinline__ void tc_operand_row(const float v[4], bool bf, bool pose, uint4 ch[8]) {
+    float pc[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) split3(v[j], bf, pc[0][j], pc[1][j], pc[2][j]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ch[c] = make_uint4(0u, 0u, 0u, 0u);
+    if (bf) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* lo = pc[term_piece(pose, 2 * c)];
+            const float* hi = pc[term_piece(pose, 2 * c + 1)];
+            ch[c] = make_uint4(bf16_pair(lo[0], lo[1]), bf16_pair(lo[2], lo[3]), bf16_pair(hi[0], hi[1]),
+                               bf16_pair(hi[2], hi[3]));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < 6; ++t) {
+            const float* pt = pc[term_piece(pose, t)];
+            ch[t] = make_uint4(__float_as_uint(pt[0]), __float_as_uint(pt[1]), __float_as_uint(pt[2]),
+                               __float_as_uint(pt[3]));
+        }
+    }
+}
 
 __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupParams p) {
     const int qi = blockIdx.x / kSetupBlocks, g = blockIdx.x % kSetupBlocks;
@@ -132,6 +183,37 @@ __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupPara
         dst[0] = make_float4(v[0], v[1], v[2], v[3]);
         dst[1] = make_float4(v[4], v[5], v[6], v[7]);
         dst[2] = make_float4(v[8], v[9], v[10], v[11]);
+    }
+    if (!d.tc_rec) return;
+    // Operand rows of the tensor-core scoring: record k is the 4-vector
+    // (X, Y, Z, 1) split into pieces b0 + b1 + b2 (TF32 or bf16 values); the
+    // row holds the 4-wide terms (b0, b1, b0, b2, b1, b0), matched in the pose
+    // rows by (a0, a0, a1, a0, a1, a2), so that one K = 24 product sums the
+    // six piece products that carry the FP32 value of a . b.  The row is 128
+    // bytes in 16-byte chunks; chunk c of row k sits at position c ^ (k mod 8)
+    // (128-byte swizzle of 8-row atoms).  Rows past M up to the next multiple
+    // of kTcBlock are zero with weight 0 and a NaN pixel: they add +0 to every
+    // score and no inlier.
+    const int m_pad = (m + kTcBlock - 1) / kTcBlock * kTcBlock;
+    for (int k = g * 256 + threadIdx.x; k < m_pad; k += kSetupBlocks * 256) {
+        float c[4] = {0.f, 0.f, 0.f, 0.f}, w = 0.f, nx = __int_as_float(0x7fc00000), ny = nx;
+        if (k < m) {
+            const int64_t i = off + (static_cast<int64_t>(k) * n) / m;
+            c[0] = __ldg(d.X + i); c[1] = __ldg(d.Y + i); c[2] = __ldg(d.Z + i); c[3] = 1.f;
+            w = __ldg(d.w + i); nx = -__ldg(d.x + i); ny = -__ldg(d.y + i);
+        }
+        uint4 ch[8];
+        tc_operand_row(c, d.tc_bf16 != 0, false, ch);
+        uint4* row = reinterpret_cast<uint4*>(d.tc_rec) + static_cast<int64_t>(k) * 8;
+        const int sw = k & 7;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) row[j ^ sw] = ch[j];
+        float* e = reinterpret_cast<float*>(d.tc_e + static_cast<int64_t>(k >> 1) * 2);
+        const int l = k & 1;
+        e[l] = nx;
+        e[2 + l] = ny;
+        e[4 + l] = w;
+        e[6 + l] = 0.f;
     }
 }
 
@@ -1223,6 +1305,321 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
     }
 }
 
+// ============================================================================
+// k_score_tc: hypothesis scoring with the projection on the tensor cores
+// ============================================================================
+// The projections of a tile of 128 poses on a block of NB subset records are
+// three matrix products (rows K [R | t]_u, _v, _z of the poses times the
+// records' (X, Y, Z, 1)).  They run as tcgen05.mma with K = 24 (of 32): both
+// operands are split into three pieces (pose coefficient a = a0 + a1 + a2,
+// record component b = b0 + b1 + b2; bf16 pieces for kind::f16, two K steps
+// of 16, or TF32 pieces for kind::tf32, three K steps of 8) and the six piece
+// products that carry the FP32 value (a0 b0, a0 b1, a1 b0, a0 b2, a1 b1,
+// a2 b0) are the K lanes; every piece product is exact in FP32, so the
+// accumulator holds the FP32 projection to a few FP32 ulps.
+// The FP32 accumulators land in TMEM; the epilogue warps (thread = pose =
+// TMEM lane) read them back with tcgen05.ld and do the rest of the cost in
+// FP32: reciprocal of the depth (z <= 0 or NaN -> tau^2), residual,
+// truncation, weighted sum.
+//
+// One CTA per SM, persistent over the (query, 128-pose tile) queue; every
+// CTA streams all records of its item's query (bulk copies of NB operand
+// rows of 128 bytes + NB x 16 bytes of pixels and weights per block, a ring
+// of stages):
+//   warp 9 (lane 0)    producer: bulk copies into the ring
+//   warp 8             TMEM allocation; lane 0 issues the MMAs of a block
+//                      (3 rows x K steps) into an accumulator buffer and
+//                      commits them to the buffer's and the stage's mbarriers
+//   warps 0-7          epilogue in two groups of four warps, group g takes
+//                      the blocks of parity g; warps 0-3 also write the
+//                      pose rows of each item
+// Per pose, each group sums its blocks in order (within a block the even
+// and the odd records separately, then even + odd), and the score is group
+// 0's sum + group 1's sum: independent of timing and of the grid.
+constexpr int kTcPoses = 128;
+constexpr uint32_t kTcCols = 512;
+constexpr uint32_t kTcATile = 128 * 128;  // one pose-row operand in shared memory: 128 rows of 128 bytes
+
+// NB records per block, NG epilogue groups of 4 warps (a group per TMEM buffer or two)
+template <int NB, int NG>
+struct TcShape {
+    static constexpr int kThreads = NG * 128 + 64;          // + the MMA warp and the producer warp
+    static constexpr int kStages = NB == 32 ? 16 : 8;
+    static constexpr int kBufs = NB == 32 ? 4 : 2;         // accumulator buffers of 3 x NB columns (384 of 512)
+    static_assert(kBufs % NG == 0, "each group owns its buffers");
+    static constexpr uint32_t kBStage = NB * 128;
+    static constexpr uint32_t kEStage = NB * 16;
+    // at least 116 KB, so that one CTA holds an SM (and all of its TMEM)
+    static constexpr size_t kSmemNeed = 1024 + 3 * kTcATile + kStages * (kBStage + kEStage) + NG * kTcPoses * 8 +
+                                        (2 * kStages + 2 * kBufs) * 8 + 16;
+    static constexpr size_t kSmem = kSmemNeed > 116 * 1024 ? kSmemNeed : 116 * 1024;
+};
+static_assert(kTcBlock % 64 == 0, "record padding covers both block sizes");
+
+template <int NB, int NG, bool BF, bool COUNT>
+__global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const __grid_constant__ ScoreParams p) {
+    using TS = TcShape<NB, NG>;
+    constexpr int S = TS::kStages, NBUF = TS::kBufs;
+    constexpr int KSTEPS = BF ? 2 : 3;  // 32-byte K steps of one MMA each
+    constexpr int WMMA = 4 * NG, WPROD = 4 * NG + 1;
+    extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tc_smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sA = smem;                                   // rows u, v, z: 3 x 16 KB
+    unsigned char* sB = sA + 3 * kTcATile;                      // ring of record operand blocks
+    float4* sE = reinterpret_cast<float4*>(sB + S * TS::kBStage);  // ring of pixel / weight blocks
+    float* s_part = reinterpret_cast<float*>(sE + S * (TS::kEStage / 16));  // [NG][128] per residue class
+    int* s_cntp = reinterpret_cast<int*>(s_part + NG * kTcPoses);          // [NG][128]
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_cntp + NG * kTcPoses);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;
+    uint64_t* tempty = tfull + NBUF;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + NBUF);
+    int* s_item = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            // the 4 epilogue warps that consumed the block: they waited for its MMAs, and read the pixels
+            mbar_init(&empty[st], 4);
+        }
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
+        mbar_fence_init();
+    }
+    if (warp == WMMA) {
+        tmem_alloc(tmem_slot, kTcCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int total_tiles = p.tile_prefix[p.nq];
+    uint32_t base = 0;  // record blocks of the earlier items of this CTA (ring and buffer positions)
+
+    for (;;) {
+        if (tid == 0) *s_item = static_cast<int>(atomicAdd(p.work_counter, 1u));
+        __syncthreads();  // also: every MMA of the previous item has completed (its epilogue consumed them)
+        const int item = *s_item;
+        if (item >= total_tiles) break;
+        int lo = 0, hi = p.nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_prefix[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int q = lo;
+        const int tile = item - p.tile_prefix[q];
+        const QueryDesc& d = p.qd[q];
+        const bool active = tile < p.ntiles[q];
+        const int m = active ? p.qs[q].m : 0;
+        const int nh = p.n_hyp[q];
+        const int nblk = (m + NB - 1) / NB;
+        const int64_t slot_base = 4 * p.wq[q].s_begin;
+
+        if (active && warp < 4) {
+            // pose rows of this item: thread tid writes pose tile * 128 + tid
+            const int j = tile * kTcPoses + tid;
+            float c12[12];
+            if (j < nh) {
+                const PoseF ps = d.slots[d.compact[j] - slot_base];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    c12[c] = d.fx * ps.R[c] + d.cx * ps.R[6 + c];
+                    c12[4 + c] = d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c];
+                    c12[8 + c] = ps.R[6 + c];
+                }
+                c12[3] = d.fx * ps.t[0] + d.cx * ps.t[2];
+                c12[7] = d.fy * ps.t[1] + d.cy * ps.t[2];
+                c12[11] = ps.t[2];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) c12[c] = 0.f;
+            }
+            const int sw = tid & 7;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                uint4 ch[8];
+                tc_operand_row(c12 + 4 * r, BF, true, ch);
+                uint4* row = reinterpret_cast<uint4*>(sA + r * kTcATile + (tid >> 3) * 1024 + (tid & 7) * 128);
+#pragma unroll
+                for (int c = 0; c < 2 * KSTEPS; ++c) row[c ^ sw] = ch[c];  // the chunks the K steps read
+            }
+            // the generic-proxy writes become visible to the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.arrive 2, 160;" ::: "memory");
+        } else if (active && warp == WMMA) {
+            // the whole warp walks the blocks (it stays converged); lane 0 issues
+            asm volatile("bar.sync 2, 160;" ::: "memory");  // pose rows written
+            constexpr uint32_t idesc = BF ? umma_idesc_bf16(kTcPoses, NB) : umma_idesc_tf32(kTcPoses, NB);
+            // descriptor start addresses advance by byte offset >> 4 (fields stay below 2^14)
+            const uint64_t adesc = umma_desc_k_sw128(smem_u32(sA)), bdesc = umma_desc_k_sw128(smem_u32(sB));
+            for (int b = 0; b < nblk; ++b) {
+                const uint32_t gb = base + b;
+                const uint32_t st = gb % S, buf = gb % NBUF;
+                mbar_wait_bounded(&tempty[buf], ((gb / NBUF) & 1u) ^ 1u, p.err);
+                mbar_wait_bounded(&full[st], (gb / S) & 1u, p.err);
+                tc_fence_after();
+                const uint64_t bd0 = bdesc + ((st * TS::kBStage) >> 4);
+                const uint32_t d0 = tmem_base + buf * 3 * NB;
+                if (elect_one()) {
+#pragma unroll
+                    for (int kk = 0; kk < KSTEPS; ++kk) {
+#pragma unroll
+                        for (int r = 0; r < 3; ++r) {
+                            const uint64_t ad = adesc + ((r * kTcATile + kk * 32) >> 4);
+                            const uint64_t bd = bd0 + ((kk * 32) >> 4);
+                            if constexpr (BF) umma_bf16(d0 + r * NB, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                            else umma_tf32(d0 + r * NB, ad, bd, idesc, kk > 0 ? 1u : 0u);
+                        }
+                    }
+                    // accumulators ready; the stage is freed by the epilogue, which waits for this
+                    umma_commit(&tfull[buf]);
+                }
+                __syncwarp();
+            }
+        } else if (active && warp == WPROD) {
+            for (int b = 0; b < nblk; ++b) {
+                const uint32_t gb = base + b;
+                const uint32_t st = gb % S;
+                mbar_wait_bounded(&empty[st], ((gb / S) & 1u) ^ 1u, p.err);
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[st], TS::kBStage + TS::kEStage);
+                    bulk_g2s(sB + st * TS::kBStage, d.tc_rec + static_cast<int64_t>(b) * NB * 8, TS::kBStage, &full[st]);
+                    bulk_g2s(sE + st * (TS::kEStage / 16), d.tc_e + static_cast<int64_t>(b) * NB, TS::kEStage, &full[st]);
+                }
+                __syncwarp();
+            }
+        }
+        if (active && warp < 4 * NG) {
+            const int g = warp >> 2, wq = warp & 3;
+            const float tau2 = d.tau2;
+            float tot = 0.f;
+            int cnt = 0;
+            const uint32_t lane_addr = tmem_base + (static_cast<uint32_t>(wq * 32) << 16);
+            // group g takes the blocks b with (base + b) mod NG == g
+            const int b0 = (g - static_cast<int>(base % NG) + NG) % NG;
+            for (int b = b0; b < nblk; b += NG) {
+                const uint32_t gb = base + b;
+                const uint32_t st = gb % S, buf = gb % NBUF;
+                mbar_wait_bounded(&tfull[buf], (gb / NBUF) & 1u, p.err);
+                tc_fence_after();
+                const float4* E = sE + st * (TS::kEStage / 16);
+                uint64_t acc2 = f2_pack(0.f, 0.f);
+#pragma unroll 1
+                for (int h = 0; h < NB / 16; ++h) {
+                    uint32_t zu[16], zv[16], zz[16];
+                    const uint32_t ta = lane_addr + buf * 3 * NB + h * 16;
+                    tmem_ld_32x32b_x16_nowait(ta, zu);
+                    tmem_ld_32x32b_x16_nowait(ta + NB, zv);
+                    tmem_ld_32x32b_x16_nowait(ta + 2 * NB, zz);
+                    tmem_wait_ld();
+                    if (h == NB / 16 - 1) {
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[buf]);
+                    }
+                    // the pixels and weights of the block (landed with the operand rows)
+                    if (h == 0) mbar_wait_bounded(&full[st], (gb / S) & 1u, p.err);
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float4 e = E[16 * h + 2 * k];  // -x0 -x1 -y0 -y1
+                        const float2 w = *reinterpret_cast<const float2*>(E + 16 * h + 2 * k + 1);
+                        const float z0 = __uint_as_float(zz[2 * k]), z1 = __uint_as_float(zz[2 * k + 1]);
+                        const float i0 = rcp_approx(fmaxf(z0, 0.0f)), i1 = rcp_approx(fmaxf(z1, 0.0f));
+                        const uint64_t iz2 = f2_pack(i0, i1);
+                        const uint64_t du2 = f2_fma(f2_pack(__uint_as_float(zu[2 * k]), __uint_as_float(zu[2 * k + 1])),
+                                                    iz2, f2_pack(e.x, e.y));
+                        const uint64_t dv2 = f2_fma(f2_pack(__uint_as_float(zv[2 * k]), __uint_as_float(zv[2 * k + 1])),
+                                                    iz2, f2_pack(e.z, e.w));
+                        float r0, r1;
+                        f2_unpack(f2_fma(du2, du2, f2_mul(dv2, dv2)), r0, r1);
+                        acc2 = f2_fma(f2_pack(w.x, w.y), f2_pack(fminf(r0, tau2), fminf(r1, tau2)), acc2);
+                        if (COUNT) cnt += ((r0 < tau2) ? 1 : 0) + ((r1 < tau2) ? 1 : 0);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[st]);
+                float ae, ao;
+                f2_unpack(acc2, ae, ao);
+                tot += ae + ao;
+            }
+            // partial sums by residue class of the block index, added in class order
+            const int cls = (g - static_cast<int>(base % NG) + NG) % NG;
+            s_part[cls * kTcPoses + wq * 32 + lane] = tot;
+            if (COUNT) s_cntp[cls * kTcPoses + wq * 32 + lane] = cnt;
+            asm volatile("bar.sync 1, %0;" ::"n"(NG * 128) : "memory");
+            if (g == 0) {
+                const int e = wq * 32 + lane;
+                float sc = s_part[e];
+                int ct = COUNT ? s_cntp[e] : 0;
+#pragma unroll
+                for (int c = 1; c < NG; ++c) {
+                    sc += s_part[c * kTcPoses + e];
+                    if (COUNT) ct += s_cntp[c * kTcPoses + e];
+                }
+                const int j = tile * kTcPoses + e;
+                const bool valid = j < nh;
+                uint32_t id = 0xffffffffu, rd = 0xffffffffu, sb = 0xffffffffu;
+                if (valid) {
+                    id = static_cast<uint32_t>(d.compact[j]);
+                    rd = static_cast<uint32_t>((id >> 2) / static_cast<uint32_t>(d.batch));
+                    sb = __float_as_uint(sc);
+                    if (d.score_by_id) d.score_by_id[id - slot_base] = sc;
+                    if (COUNT && d.count_by_id) d.count_by_id[id - slot_base] = ct;
+                }
+                // per round, the minimum (score bits, pose id) of the warp, then one atomic
+                unsigned long long kv = valid ? ((static_cast<unsigned long long>(sb) << 32) | id) : ~0ull;
+                bool pending = valid;
+                while (__any_sync(0xffffffffu, pending)) {
+                    const int first = __ffs(__ballot_sync(0xffffffffu, pending)) - 1;
+                    const uint32_t r0 = __shfl_sync(0xffffffffu, rd, first);
+                    unsigned long long v = (pending && rd == r0) ? kv : ~0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+                        v = u < v ? u : v;
+                    }
+                    if (lane == first) atomicMin(reinterpret_cast<unsigned long long*>(&d.round_best[r0]), v);
+                    if (rd == r0) pending = false;
+                }
+            }
+        }
+        base += static_cast<uint32_t>(nblk);
+    }
+    // every MMA completed before the epilogue read its accumulator
+    tc_fence_before();
+    __syncthreads();
+    if (warp == WMMA) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTcCols);
+    }
+}
+
+// tensor-core scoring variants: records per MMA x epilogue groups x bf16 or TF32 pieces
+struct TcVariant {
+    int nb, ng;
+    bool bf;
+    int threads;
+    size_t smem;
+    void (*fn)(ScoreParams);
+    void (*fn_count)(ScoreParams);
+};
+#define IMLOC_TC_VARIANT(NB, NG, BF)                                                              \
+    {NB, NG, BF, TcShape<NB, NG>::kThreads, TcShape<NB, NG>::kSmem, k_score_tc<NB, NG, BF, false>, \
+     k_score_tc<NB, NG, BF, true>}
+static const TcVariant kTcVariants[] = {
+    IMLOC_TC_VARIANT(32, 4, true),   // 0: 32-record blocks, 4 epilogue groups, bf16 pieces (2 K steps)
+    IMLOC_TC_VARIANT(64, 2, true),   // 1: 64-record blocks, 2 epilogue groups, bf16 pieces
+    IMLOC_TC_VARIANT(32, 4, false),  // 2: 32-record blocks, 4 epilogue groups, TF32 pieces (3 K steps)
+};
+#undef IMLOC_TC_VARIANT
+constexpr int kNumTcVariants = sizeof(kTcVariants) / sizeof(kTcVariants[0]);
+
 // score kernel variants the autotuner chooses from (same results, different speed)
 struct ScoreVariant {
     int threads, ht;
@@ -1419,6 +1816,22 @@ static int tune_score(imloc_ctx* ctx, const StepBuffers& b, int nq, const ScoreP
     return IMLOC_OK;
 }
 
+// IMLOC_FUSE=1 / IMLOC_NO_FUSE=1 force the fused / unfused form
+static bool fuse_of(bool dflt) { return getenv("IMLOC_NO_FUSE") ? false : (getenv("IMLOC_FUSE") ? true : dflt); }
+
+// IMLOC_SCORE_TC=0 / 1 turns the tensor-core scoring kernel off / on
+static bool score_tc_enabled() {
+    const char* env = getenv("IMLOC_SCORE_TC");
+    if (env) return atoi(env) != 0;
+    return false;
+}
+
+// IMLOC_TC_VARIANT=<k> picks the tensor-core scoring variant
+static int tc_variant() {
+    const char* env = getenv("IMLOC_TC_VARIANT");
+    return env ? std::min(std::max(atoi(env), 0), kNumTcVariants - 1) : 0;
+}
+
 int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t total_samples, bool want_counts,
              cudaStream_t stream) {
     int rc;
@@ -1439,28 +1852,41 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
     }
     ScoreParams scp{b.d_qd,       b.d_qs,      b.d_wq, b.d_nhyp,   b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1,
                     b.d_counter, nq,          ctx->d_err};
-    // autotune the score kernel variant once per context on a large enough wave
-    if (ctx->score_variant < 0 && (max_items_of(total_samples, nq, kMaxTileHyps) >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
-        rc = tune_score(ctx, b, nq, scp, want_counts, total_samples, stream);
-        if (rc != IMLOC_OK) return rc;
-    }
-    const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
-    const int tile = V.threads * V.ht;
-    const size_t score_smem = score_smem_bytes(want_counts, tile);
-    const int64_t max_items = max_items_of(total_samples, nq, tile);
-    rc = launch_tiles(ctx, b, nq, tile, stream);
-    if (rc != IMLOC_OK) return rc;
     // the fused kernel scores and replays each query when its last item is done
     // (replays overlap the scoring of later queries: worth it with many
     // queries); otherwise the scoring runs alone, followed by the replay kernel.
-    // IMLOC_FUSE=1 / IMLOC_NO_FUSE=1 force either form.
-    const bool fuse = getenv("IMLOC_NO_FUSE") ? false : (getenv("IMLOC_FUSE") ? true : b.fuse);
-    auto score_kernel = fuse ? (want_counts ? V.fused_count : V.fused) : (want_counts ? V.fn_count : V.fn);
-    int n_clusters = 0;
-    rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
-    if (rc != IMLOC_OK) return rc;
-    const int grid_clusters = static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items));
-    {
+    const bool fuse = fuse_of(b.fuse);
+    if (b.tc && !fuse) {
+        // projections on the tensor cores: one persistent CTA per SM
+        rc = launch_tiles(ctx, b, nq, kTcPoses, stream);
+        if (rc != IMLOC_OK) return rc;
+        const TcVariant& TV = kTcVariants[tc_variant()];
+        auto kern = want_counts ? TV.fn_count : TV.fn;
+        IMLOC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(TV.smem)));
+        const int grid = static_cast<int>(
+            std::min<int64_t>(std::max(1, ctx->sm_count), max_items_of(total_samples, nq, kTcPoses)));
+        ProfScope prof(ctx, stream, "k_score");
+        kern<<<grid, TV.threads, TV.smem, stream>>>(scp);
+        IMLOC_CUDA_TRY(cudaGetLastError());
+        prof.end();
+    } else {
+        // autotune the score kernel variant once per context on a large enough wave
+        if (ctx->score_variant < 0 &&
+            (max_items_of(total_samples, nq, kMaxTileHyps) >= 64 || getenv("IMLOC_SCORE_VARIANT"))) {
+            rc = tune_score(ctx, b, nq, scp, want_counts, total_samples, stream);
+            if (rc != IMLOC_OK) return rc;
+        }
+        const ScoreVariant& V = kScoreVariants[ctx->score_variant >= 0 ? ctx->score_variant : 0];
+        const int tile = V.threads * V.ht;
+        const size_t score_smem = score_smem_bytes(want_counts, tile);
+        const int64_t max_items = max_items_of(total_samples, nq, tile);
+        rc = launch_tiles(ctx, b, nq, tile, stream);
+        if (rc != IMLOC_OK) return rc;
+        auto score_kernel = fuse ? (want_counts ? V.fused_count : V.fused) : (want_counts ? V.fn_count : V.fn);
+        int n_clusters = 0;
+        rc = max_clusters(score_kernel, V.threads, score_smem, kScoreCluster, &n_clusters);
+        if (rc != IMLOC_OK) return rc;
+        const int grid_clusters = static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items));
         ProfScope prof(ctx, stream, "k_score");
         rc = launch_cluster(score_kernel, scp, grid_clusters * kScoreCluster, V.threads, score_smem, kScoreCluster,
                             stream);
@@ -1562,6 +1988,9 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     }
 
     // ---- workspace ----
+    // tensor-core scoring: only in the unfused form (the fused kernel replays
+    // queries inside the FP32 scoring kernel)
+    bool tc_on = score_tc_enabled() && !fuse_of(nq >= 32);
     std::vector<QueryDesc> qd(nq);
     int64_t est_hyp = 0;
     for (int q = 0; q < nq; ++q) {
@@ -1600,6 +2029,16 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.inject = h.inject ? 1 : 0;
         const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
         d.subset = static_cast<ScorePair*>(ws_alloc(ctx, sizeof(ScorePair) * ((std::max(1, o.max_score_corr) + 1) / 2)));
+        d.tc_bf16 = kTcVariants[tc_variant()].bf ? 1 : 0;
+        if (tc_on) {
+            const int64_t mp = (std::max(1, o.max_score_corr) + kTcBlock - 1) / kTcBlock * kTcBlock;
+            d.tc_rec = static_cast<float4*>(ws_alloc(ctx, 128 * mp));
+            d.tc_e = d.tc_rec ? static_cast<float4*>(ws_alloc(ctx, 16 * mp)) : nullptr;
+            if (!d.tc_e) {
+                d.tc_rec = nullptr;
+                tc_on = false;  // no room: every query of the call takes the FP32 scoring kernel
+            }
+        }
         if (h.slots_out) d.slots = h.slots_out;
         else d.slots = static_cast<PoseF*>(ws_alloc(ctx, sizeof(PoseF) * slots));
         d.compact = static_cast<int32_t*>(ws_alloc(ctx, sizeof(int32_t) * slots));
@@ -1664,8 +2103,9 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     std::string key;
     if (use_graph) {
         char buf[160];
-        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
+        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
                  int(getenv("IMLOC_NO_FUSE") != nullptr) + 2 * int(getenv("IMLOC_FUSE") != nullptr),
+                 tc_on ? 1 + tc_variant() : 0,
                  (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
         key = buf;
         for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);
@@ -1695,6 +2135,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.any_fp64 = false;
         for (int q = 0; q < nq; ++q) sb.any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
         sb.fuse = nq >= 32;
+        sb.tc = tc_on;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
             if (capturing) {

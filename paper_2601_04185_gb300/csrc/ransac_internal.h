@@ -30,6 +30,7 @@ struct StepBuffers {
     const int32_t* d_init; // queries to set up (null: 0 .. n_init-1)
     bool any_fp64 = false;  // some query asks for FP64 accumulation in LO / refinement
     bool fuse = false;      // replay inside the scoring kernel (see run_step)
+    bool tc = false;        // every query has tensor-core operand rows (QueryDesc::tc_rec)
 };
 
 // One step: set up n_init queries, then sample + P3P, tiles, score, replay.
