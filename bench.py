@@ -45,6 +45,10 @@ HYPOTHESES = 10000
 MATCHES_PER_PAIR = 5000
 N_VIEWS = 10
 FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored (pose, correspondence) pair
+# tensor-core scoring: per pair the FP32 epilogue does 4 FFMA + 1 FMUL (9 flops) after the projection,
+# which runs as 3 coordinate rows x 2 MMA K steps of 16 (24 split-piece terms + 8 zero) x 2 flops
+TC_FP32_FLOPS_PER_PAIR = 9
+TC_MMA_FLOPS_PER_PAIR = 192
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of k_score on the 16-query C2 step, from
@@ -52,6 +56,9 @@ FP32_LANES_PER_SM = 128
 # scoring variant (threads, poses per thread) it was taken on; the line reports
 # it only when the autotuner picked that variant.
 SCORE_TRAFFIC_PER_LAUNCH = {(64, 4): 25.754e6 + 0.0}
+# the same for k_score_tc (80-record blocks, bf16 pieces) on that step
+# (profiles/k_score_tc_c2_16queries.md)
+SCORE_TC_TRAFFIC_PER_LAUNCH = 44.955e6 + 0.102e6
 # DRAM bytes (read + write) per lifted match from the committed ncu capture of
 # k_lift on the batched 9.48M-match shape (profiles/k_lift_batched_9.5M.md)
 LIFT_TRAFFIC_PER_MATCH = (1.229412e9 + 0.234057e9) / 9.48e6
@@ -874,8 +881,9 @@ def run_ours(args):
     barrier(world)
     step_ms = [a.elapsed_time(b) for a, b in ev]
     kstats = ctx.profile_read(reset=True)
-    # the scoring kernel alone (replay in its own kernel) for its roofline: a few extra steps
+    # the FP32 scoring kernel on the same step (replay in its own kernel) for its roofline: a few extra steps
     os.environ["IMLOC_NO_FUSE"] = "1"
+    os.environ["IMLOC_SCORE_TC"] = "0"
     for _ in range(3):
         flush.zero_()
         step()
@@ -887,18 +895,6 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     kstats_unfused = ctx.profile_read(reset=True)
-    # the opt-in tensor-core scoring kernel on the same step, for comparison
-    os.environ["IMLOC_SCORE_TC"] = "1"
-    for _ in range(3):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    ctx.profile_read(reset=True)
-    for _ in range(n_unfused):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    kstats_tc = ctx.profile_read(reset=True)
     del os.environ["IMLOC_SCORE_TC"]
     del os.environ["IMLOC_NO_FUSE"]
     ctx.profile(False)
@@ -948,8 +944,10 @@ def run_ours(args):
     res_full = imloc.results_from_bytes(results_full.cpu().numpy(), nq)
     n_corr_full = np.diff(offsets.cpu().numpy())
     pairs_full = float(sum(r["hypotheses"] * min(int(n), full_cap) for r, n in zip(res_full, n_corr_full)))
-    full_ms = kfull["k_score"][1] / max(1, kfull["k_score"][0]) if "k_score" in kfull else None
-    full_tflops = pairs_full * FLOPS_PER_PAIR / (full_ms * 1e-3) / 1e12 if full_ms else None
+    full_key = "k_score_tc" if "k_score_tc" in kfull else "k_score"
+    full_ms = kfull[full_key][1] / max(1, kfull[full_key][0]) if full_key in kfull else None
+    full_fpp = TC_FP32_FLOPS_PER_PAIR if full_key == "k_score_tc" else FLOPS_PER_PAIR
+    full_tflops = pairs_full * full_fpp / (full_ms * 1e-3) / 1e12 if full_ms else None
 
     # ---- plain form: one query per call (lift, then RANSAC), host-synchronous ----
     lat = []
@@ -974,20 +972,28 @@ def run_ours(args):
     p50 = lat_sorted[len(lat) // 2]
     p99 = lat_sorted[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
 
-    # ---- roofline of the dominant kernel (k_score: FP32 pipe) ----
+    # ---- roofline of the dominant kernel (the scoring kernel of the step) ----
     clocks = clk.summary()
     launches = {k: v[0] for k, v in kstats.items()}
     kms = {k: v[1] for k, v in kstats.items()}
-    score_launch_ms = kms.get("k_score", 0.0) / max(1, launches.get("k_score", 1))
-    pairs_per_launch = pairs_per_step * args.steps / max(1, launches.get("k_score", 1))
-    achieved_tflops = FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
+    score_key = "k_score_tc" if "k_score_tc" in kms else "k_score"
+    score_launch_ms = kms.get(score_key, 0.0) / max(1, launches.get(score_key, 1))
+    pairs_per_launch = pairs_per_step * args.steps / max(1, launches.get(score_key, 1))
+    score_fpp = TC_FP32_FLOPS_PER_PAIR if score_key == "k_score_tc" else FLOPS_PER_PAIR
+    achieved_tflops = score_fpp * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
     u_launches, u_ms = kstats_unfused.get("k_score", (1, 0.0))
     score_only_ms = u_ms / max(1, u_launches)
     score_only_tflops = FLOPS_PER_PAIR * pairs_per_step / (score_only_ms * 1e-3) / 1e12 if score_only_ms else None
     score_cfg = ctx.score_config()
-    score_traffic = SCORE_TRAFFIC_PER_LAUNCH.get(tuple(score_cfg[:2])) if (score_cfg and nq == 16) else None
+    if score_key == "k_score_tc":
+        score_traffic = SCORE_TC_TRAFFIC_PER_LAUNCH if nq == 16 else None
+    else:
+        score_traffic = SCORE_TRAFFIC_PER_LAUNCH.get(tuple(score_cfg[:2])) if (score_cfg and nq == 16) else None
     peak_clock_mhz = 2070.0
     peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_clock_mhz * 1e6 / 1e12
+    bf16_peak = load_peaks().get("bf16_tflops", 1900.0)
+    tc_tensor_tflops = (TC_MMA_FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12
+                        if (score_key == "k_score_tc" and score_launch_ms) else None)
     lift_ms = kms.get("k_lift", 0.0) / max(1, launches.get("k_lift", 1))
     # algorithmic bytes of one lift launch: 20 B per match, 64 B (bilinear) or 32 B (lookup) of depth
     # sectors per match that passes the confidence filter, 28 B per correspondence written
@@ -1013,28 +1019,45 @@ def run_ours(args):
         "plain": {"latency_ms_p50": p50, "latency_ms_p99": p99, "queries_per_s": 1e3 / statistics.mean(lat),
                   "form": "one query per call: imloc_lift_async + imloc_ransac_pnp (host-synchronous)",
                   "samples": len(lat)},
-        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
-                     "traffic": score_traffic, "kernel": "k_score", "variant": score_cfg,
-                     "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
-                     "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
-                     "launch_ms": score_launch_ms,
-                     "note": "batches of >= 32 queries run k_score fused (each query's replay inside it once its "
-                             "last pose tile is scored); this 16-query step runs scoring and replay as two kernels"},
-        "score_tc": {"launch_ms": kstats_tc.get("k_score", (1, 0))[1] / max(1, kstats_tc.get("k_score", (1, 0))[0]),
-                     "note": "opt-in tensor-core scoring kernel (IMLOC_SCORE_TC=1: projection as split-bf16 "
-                             "tcgen05.mma, FP32 epilogue from TMEM) on the same step, unfused"},
-        "roofline_score_only": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                                "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
-                                "launch_ms": score_only_ms, "replay_kernel_ms": kstats_unfused.get("k_replay", (1, 0))[1]
-                                / max(1, kstats_unfused.get("k_replay", (1, 0))[0]),
-                                "note": "scoring kernel alone, replay in its own kernel (IMLOC_NO_FUSE=1)"},
+        "roofline": ({"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
+                      "traffic": score_traffic, "kernel": "k_score_tc", "variant": "80-record blocks, bf16 pieces",
+                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
+                      "flops_per_pair": TC_FP32_FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
+                      "launch_ms": score_launch_ms,
+                      "tensor": {"achieved": tc_tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                 "frac": (tc_tensor_tflops / bf16_peak) if tc_tensor_tflops else None,
+                                 "flops_per_pair": TC_MMA_FLOPS_PER_PAIR,
+                                 "peak_basis": "measured bf16 burst (cuBLAS)"},
+                      "note": "tensor-core scoring: the projection runs on the tensor pipe (6 split bf16 piece "
+                              "products per coordinate row, 3 rows, K padded to 32: 192 MMA flops per pair); "
+                              "achieved counts the FP32 epilogue's 9 flops per pair against the FP32 pipe; the "
+                              "kernel is latency-bound (see roofline_fp32_kernel for the FP32-only kernel)"}
+                     if score_key == "k_score_tc" else
+                     {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
+                      "traffic": score_traffic, "kernel": "k_score", "variant": score_cfg,
+                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
+                      "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
+                      "launch_ms": score_launch_ms}),
+        "roofline_fp32_kernel": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops,
+                                 "unit": "TFLOP/s", "kernel": "k_score",
+                                 "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
+                                 "flops_per_pair": FLOPS_PER_PAIR, "launch_ms": score_only_ms,
+                                 "traffic": SCORE_TRAFFIC_PER_LAUNCH.get(tuple(score_cfg[:2]))
+                                 if (score_cfg and nq == 16) else None, "variant": score_cfg,
+                                 "replay_kernel_ms": kstats_unfused.get("k_replay", (1, 0))[1]
+                                 / max(1, kstats_unfused.get("k_replay", (1, 0))[0]),
+                                 "note": "the FP32-only scoring kernel (IMLOC_SCORE_TC=0) on the same step: 27 "
+                                         "flops per pair on the FMA pipe; it scores batches of >= 32 queries fused "
+                                         "with the replay, and single queries"},
         "roofline_full_n": {"bound": "alu", "achieved": full_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                             "frac": (full_tflops / peak_tflops) if full_tflops else None, "launch_ms": full_ms,
                             "pairs_per_launch": pairs_full,
                             "mean_scored_corr": float(np.mean(np.minimum(n_corr_full, full_cap))),
+                            "kernel": full_key, "flops_per_pair": full_fpp,
                             "note": "stress mode: the same step's poses scored against all N correspondences "
-                                    "(subset cap raised to 65,536), one k_score launch"},
+                                    "(subset cap raised to 65,536), one scoring launch"},
         "lift_in_step": {"bound": "hbm", "achieved": lift_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": (lift_gbs / hbm_peak) if lift_gbs else None, "bytes_per_launch": lift_bytes,
                          "launch_ms": lift_ms, "note": "16-query step: 800k matches, latency-bound"},

@@ -64,7 +64,7 @@ struct SetupParams {
 };
 
 constexpr int kSetupBlocks = 8;  // CTAs per query: they split the subset gather
-constexpr int kTcBlock = 64;     // tensor-core operand rows are padded to a multiple of this (records per MMA: 32 or 64)
+constexpr int kTcBlock = 640;    // tensor-core operand rows are padded to a multiple of this (of every block size)
 
 // FP32 -> nearest bf16 value (as an FP32)
 __device__ __forceinline__ float to_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -1340,13 +1340,15 @@ constexpr int kTcPoses = 128;
 constexpr uint32_t kTcCols = 512;
 constexpr uint32_t kTcATile = 128 * 128;  // one pose-row operand in shared memory: 128 rows of 128 bytes
 
-// NB records per block, NG epilogue groups of 4 warps (a group per TMEM buffer or two)
+// NB records per block, NG epilogue groups of 4 warps; every group reads NB / NG
+// columns (records) of every block
 template <int NB, int NG>
 struct TcShape {
     static constexpr int kThreads = NG * 128 + 64;          // + the MMA warp and the producer warp
-    static constexpr int kStages = NB == 32 ? 16 : 8;
-    static constexpr int kBufs = NB == 32 ? 4 : 2;         // accumulator buffers of 3 x NB columns (384 of 512)
-    static_assert(kBufs % NG == 0, "each group owns its buffers");
+    static constexpr int kStages = NB <= 32 ? 16 : (NB <= 80 ? 8 : 6);
+    static constexpr int kBufs = 512 / (3 * NB);           // accumulator buffers of 3 x NB TMEM columns
+    static constexpr int kCols = NB / NG;                  // records of a block per group
+    static_assert(kCols % 16 == 0 && kBufs >= 1, "shape");
     static constexpr uint32_t kBStage = NB * 128;
     static constexpr uint32_t kEStage = NB * 16;
     // at least 116 KB, so that one CTA holds an SM (and all of its TMEM)
@@ -1354,7 +1356,7 @@ struct TcShape {
                                         (2 * kStages + 2 * kBufs) * 8 + 16;
     static constexpr size_t kSmem = kSmemNeed > 116 * 1024 ? kSmemNeed : 116 * 1024;
 };
-static_assert(kTcBlock % 64 == 0, "record padding covers both block sizes");
+static_assert(kTcBlock % 128 == 0 && kTcBlock % 80 == 0, "record padding covers every block size");
 
 template <int NB, int NG, bool BF, bool COUNT>
 __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const __grid_constant__ ScoreParams p) {
@@ -1381,12 +1383,12 @@ __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const
     if (tid == 0) {
         for (int st = 0; st < S; ++st) {
             mbar_init(&full[st], 1);
-            // the 4 epilogue warps that consumed the block: they waited for its MMAs, and read the pixels
-            mbar_init(&empty[st], 4);
+            // every epilogue warp, once done with the block: it waited for its MMAs and read its pixels
+            mbar_init(&empty[st], 4 * NG);
         }
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], 4);
+            mbar_init(&tempty[b], 4 * NG);
         }
         mbar_fence_init();
     }
@@ -1501,24 +1503,24 @@ __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const
             float tot = 0.f;
             int cnt = 0;
             const uint32_t lane_addr = tmem_base + (static_cast<uint32_t>(wq * 32) << 16);
-            // group g takes the blocks b with (base + b) mod NG == g
-            const int b0 = (g - static_cast<int>(base % NG) + NG) % NG;
-            for (int b = b0; b < nblk; b += NG) {
+            constexpr int CW = TS::kCols;
+            for (int b = 0; b < nblk; ++b) {
                 const uint32_t gb = base + b;
                 const uint32_t st = gb % S, buf = gb % NBUF;
                 mbar_wait_bounded(&tfull[buf], (gb / NBUF) & 1u, p.err);
                 tc_fence_after();
-                const float4* E = sE + st * (TS::kEStage / 16);
+                // this group's records of the block: g * CW .. g * CW + CW - 1
+                const float4* E = sE + st * (TS::kEStage / 16) + g * CW;
                 uint64_t acc2 = f2_pack(0.f, 0.f);
 #pragma unroll 1
-                for (int h = 0; h < NB / 16; ++h) {
+                for (int h = 0; h < CW / 16; ++h) {
                     uint32_t zu[16], zv[16], zz[16];
-                    const uint32_t ta = lane_addr + buf * 3 * NB + h * 16;
+                    const uint32_t ta = lane_addr + buf * 3 * NB + g * CW + h * 16;
                     tmem_ld_32x32b_x16_nowait(ta, zu);
                     tmem_ld_32x32b_x16_nowait(ta + NB, zv);
                     tmem_ld_32x32b_x16_nowait(ta + 2 * NB, zz);
                     tmem_wait_ld();
-                    if (h == NB / 16 - 1) {
+                    if (h == CW / 16 - 1) {
                         tc_fence_before();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&tempty[buf]);
@@ -1548,10 +1550,9 @@ __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const
                 f2_unpack(acc2, ae, ao);
                 tot += ae + ao;
             }
-            // partial sums by residue class of the block index, added in class order
-            const int cls = (g - static_cast<int>(base % NG) + NG) % NG;
-            s_part[cls * kTcPoses + wq * 32 + lane] = tot;
-            if (COUNT) s_cntp[cls * kTcPoses + wq * 32 + lane] = cnt;
+            // partial sums by column group, added in group order
+            s_part[g * kTcPoses + wq * 32 + lane] = tot;
+            if (COUNT) s_cntp[g * kTcPoses + wq * 32 + lane] = cnt;
             asm volatile("bar.sync 1, %0;" ::"n"(NG * 128) : "memory");
             if (g == 0) {
                 const int e = wq * 32 + lane;
@@ -1613,9 +1614,10 @@ struct TcVariant {
     {NB, NG, BF, TcShape<NB, NG>::kThreads, TcShape<NB, NG>::kSmem, k_score_tc<NB, NG, BF, false>, \
      k_score_tc<NB, NG, BF, true>}
 static const TcVariant kTcVariants[] = {
-    IMLOC_TC_VARIANT(32, 4, true),   // 0: 32-record blocks, 4 epilogue groups, bf16 pieces (2 K steps)
-    IMLOC_TC_VARIANT(64, 2, true),   // 1: 64-record blocks, 2 epilogue groups, bf16 pieces
-    IMLOC_TC_VARIANT(32, 4, false),  // 2: 32-record blocks, 4 epilogue groups, TF32 pieces (3 K steps)
+    IMLOC_TC_VARIANT(80, 5, true),    // 0: 80-record blocks (2 TMEM buffers), 5 groups x 16 records, bf16 pieces
+    IMLOC_TC_VARIANT(128, 4, true),   // 1: 128-record blocks (1 buffer), 4 groups x 32 records, bf16 pieces
+    IMLOC_TC_VARIANT(80, 5, false),   // 2: as 0 with TF32 pieces (3 K steps)
+    IMLOC_TC_VARIANT(64, 4, true),    // 3: 64-record blocks (2 buffers), 4 groups x 16 records, bf16 pieces
 };
 #undef IMLOC_TC_VARIANT
 constexpr int kNumTcVariants = sizeof(kTcVariants) / sizeof(kTcVariants[0]);
@@ -1819,11 +1821,14 @@ static int tune_score(imloc_ctx* ctx, const StepBuffers& b, int nq, const ScoreP
 // IMLOC_FUSE=1 / IMLOC_NO_FUSE=1 force the fused / unfused form
 static bool fuse_of(bool dflt) { return getenv("IMLOC_NO_FUSE") ? false : (getenv("IMLOC_FUSE") ? true : dflt); }
 
-// IMLOC_SCORE_TC=0 / 1 turns the tensor-core scoring kernel off / on
-static bool score_tc_enabled() {
+// Which scoring kernel an unfused call takes: the tensor-core one when the
+// call has enough pose tiles (~1.2 poses per minimal set, 128 per tile) for
+// two per SM, the FP32 one otherwise (a single query: the cluster-split FP32
+// kernel spreads it over more SMs).  IMLOC_SCORE_TC=0 / 1 forces either.
+static bool score_tc_enabled(const imloc_ctx* ctx, int64_t total_samples) {
     const char* env = getenv("IMLOC_SCORE_TC");
     if (env) return atoi(env) != 0;
-    return false;
+    return total_samples * 6 / 5 >= 2LL * std::max(1, ctx->sm_count) * kTcPoses;
 }
 
 // IMLOC_TC_VARIANT=<k> picks the tensor-core scoring variant
@@ -1865,7 +1870,7 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         IMLOC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(TV.smem)));
         const int grid = static_cast<int>(
             std::min<int64_t>(std::max(1, ctx->sm_count), max_items_of(total_samples, nq, kTcPoses)));
-        ProfScope prof(ctx, stream, "k_score");
+        ProfScope prof(ctx, stream, "k_score_tc");
         kern<<<grid, TV.threads, TV.smem, stream>>>(scp);
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
@@ -1990,7 +1995,9 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     // ---- workspace ----
     // tensor-core scoring: only in the unfused form (the fused kernel replays
     // queries inside the FP32 scoring kernel)
-    bool tc_on = score_tc_enabled() && !fuse_of(nq >= 32);
+    int64_t all_samples = 0;
+    for (int q = 0; q < nq; ++q) all_samples += H[q];
+    bool tc_on = score_tc_enabled(ctx, all_samples) && !fuse_of(nq >= 32);
     std::vector<QueryDesc> qd(nq);
     int64_t est_hyp = 0;
     for (int q = 0; q < nq; ++q) {
@@ -2098,7 +2105,8 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     const bool real_stream = stream != nullptr && stream != cudaStreamLegacy && stream != cudaStreamPerThread &&
                              cudaStreamIsCapturing(stream, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
     cudaGetLastError();
-    const bool use_graph = real_stream && !ctx->prof_on && ctx->score_variant >= 0 && !debug &&
+    // (the FP32 kernel's autotuner times launches: no capture before it has run)
+    const bool use_graph = real_stream && !ctx->prof_on && (ctx->score_variant >= 0 || tc_on) && !debug &&
                            !getenv("IMLOC_NO_GRAPHS");
     std::string key;
     if (use_graph) {

@@ -1,8 +1,10 @@
-"""The tensor-core scoring kernel (opt-in, IMLOC_SCORE_TC=1), each of its
-variants (IMLOC_TC_VARIANT), against the FP64 oracle: per-pose truncated
-scores (Sec. 3.3 MSAC cost) and inlier counts on subsets whose size is not a
-multiple of the kernel's record block, pose tiles with a ragged last tile, the
-round minima, and end-to-end poses of a batched call.
+"""Both scoring kernels, each forced on every call: the FP32 one
+(IMLOC_SCORE_TC=0) and the tensor-core one (IMLOC_SCORE_TC=1, which large
+unfused batches take by default) with each of its variants
+(IMLOC_TC_VARIANT), against the FP64 oracle: per-pose truncated scores
+(Sec. 3.3 MSAC cost) and inlier counts on subsets whose size is not a
+multiple of the tensor-core kernel's record block, pose tiles with a ragged
+last tile, the round minima, and end-to-end poses of a batched call.
 
 Bars as for the FP32 scoring kernel: per-pose score 1e-5 relative, counts
 exact except points within 1e-3 px of tau, final pose 0.05 deg / 5 mm.
@@ -20,10 +22,13 @@ from gpu_helpers import pose_close, residuals, torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["32rec-4groups-bf16", "64rec-2groups-bf16", "32rec-4groups-tf32"])
+@pytest.fixture(params=[-1, 0, 1, 2], ids=["fp32", "tc-80rec-bf16", "tc-128rec-bf16", "tc-80rec-tf32"])
 def tc_ctx(request, monkeypatch):
-    monkeypatch.setenv("IMLOC_SCORE_TC", "1")
-    monkeypatch.setenv("IMLOC_TC_VARIANT", str(request.param))
+    if request.param < 0:
+        monkeypatch.setenv("IMLOC_SCORE_TC", "0")
+    else:
+        monkeypatch.setenv("IMLOC_SCORE_TC", "1")
+        monkeypatch.setenv("IMLOC_TC_VARIANT", str(request.param))
     c = imloc.Context(0, 1 << 30)
     yield c
     c.close()
