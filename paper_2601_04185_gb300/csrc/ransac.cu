@@ -1993,11 +1993,15 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     }
 
     // ---- workspace ----
-    // tensor-core scoring: only in the unfused form (the fused kernel replays
-    // queries inside the FP32 scoring kernel)
+    // Scoring form: the tensor-core kernel (unfused) when the call is large
+    // enough for it; else the FP32 kernel, fused with the replay for >= 32
+    // queries.  On 256 queries the tensor-core kernel plus a replay kernel
+    // beats the fused FP32 form (15.0 vs 16.2 ms).
     int64_t all_samples = 0;
     for (int q = 0; q < nq; ++q) all_samples += H[q];
-    bool tc_on = score_tc_enabled(ctx, all_samples) && !fuse_of(nq >= 32);
+    const bool want_tc = score_tc_enabled(ctx, all_samples);
+    const bool dflt_fuse = nq >= 32 && !want_tc;
+    bool tc_on = want_tc && !fuse_of(dflt_fuse);
     std::vector<QueryDesc> qd(nq);
     int64_t est_hyp = 0;
     for (int q = 0; q < nq; ++q) {
@@ -2142,7 +2146,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.d_init = nullptr;
         sb.any_fp64 = false;
         for (int q = 0; q < nq; ++q) sb.any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
-        sb.fuse = nq >= 32;
+        sb.fuse = dflt_fuse;
         sb.tc = tc_on;
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
