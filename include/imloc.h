@@ -73,11 +73,15 @@ int imloc_profile_enable(imloc_ctx* ctx, int on);
 /* Writes min(n, max_out) entries to `out` (host) and the number of kernels
  * seen to *n_out; reset != 0 clears the totals afterwards. */
 int imloc_profile_read(imloc_ctx* ctx, imloc_kernel_stat* out, int32_t max_out, int32_t* n_out, int reset);
-/* Configuration of the hypothesis-scoring kernel the context's autotuner chose
- * on its first large enough RANSAC wave (variants differ in speed only, not in
- * results; the paper has no counterpart): CTA threads, poses per thread and
- * poses per work item.  Returns IMLOC_ERR_NOT_FOUND (outputs untouched) before
- * the first tuning; host pointers, any of them may be NULL. */
+/* Configuration of the FP32 hypothesis-scoring kernel the context's autotuner
+ * chose on its first large enough RANSAC wave (variants differ in speed only,
+ * not in results; the paper has no counterpart): CTA threads, poses per thread
+ * and poses per work item.  Returns IMLOC_ERR_NOT_FOUND (outputs untouched)
+ * before the first tuning; host pointers, any of them may be NULL.
+ * Calls with enough pose tiles for two per SM (about 39K minimal sets on 152
+ * SMs) score on the tensor cores instead (projection as split-bf16 MMAs, same
+ * FP32-level scores up to rounding) and do not tune this kernel; the
+ * environment variable IMLOC_SCORE_TC=0 or 1 forces either kernel. */
 int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_per_thread, int32_t* tile_poses);
 
 /* ---- cameras and views -------------------------------------------------- */
