@@ -1325,17 +1325,21 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
 // One CTA per SM, persistent over the (query, 128-pose tile) queue; every
 // CTA streams all records of its item's query (bulk copies of NB operand
 // rows of 128 bytes + NB x 16 bytes of pixels and weights per block, a ring
-// of stages):
-//   warp 9 (lane 0)    producer: bulk copies into the ring
-//   warp 8             TMEM allocation; lane 0 issues the MMAs of a block
-//                      (3 rows x K steps) into an accumulator buffer and
-//                      commits them to the buffer's and the stage's mbarriers
-//   warps 0-7          epilogue in two groups of four warps, group g takes
-//                      the blocks of parity g; warps 0-3 also write the
-//                      pose rows of each item
-// Per pose, each group sums its blocks in order (within a block the even
-// and the odd records separately, then even + odd), and the score is group
-// 0's sum + group 1's sum: independent of timing and of the grid.
+// of stages).  Warps:
+//   4 NG + 1           producer: waits for a free stage, bulk copies into it
+//   4 NG               TMEM allocation; the converged warp walks the blocks,
+//                      one elected lane issues the block's MMAs (3 rows x K
+//                      steps) into a free accumulator buffer and commits them
+//                      to the buffer's mbarrier
+//   0 .. 4 NG - 1      epilogue: NG groups of four warps (warp w reads TMEM
+//                      lanes 32 (w mod 4) ..); group g takes records g NB/NG ..
+//                      (g + 1) NB/NG - 1 of every block, frees the buffer once
+//                      it has loaded them and the stage once it has used the
+//                      pixels; warps 0-3 also write the pose rows of each item
+// Per pose, each group sums its records in block order (within its part of
+// a block the even and the odd records separately, then even + odd), and the
+// score adds the group sums in group order: independent of timing and of the
+// grid.
 constexpr int kTcPoses = 128;
 constexpr uint32_t kTcCols = 512;
 constexpr uint32_t kTcATile = 128 * 128;  // one pose-row operand in shared memory: 128 rows of 128 bytes
@@ -1370,7 +1374,7 @@ __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const
     unsigned char* sA = smem;                                   // rows u, v, z: 3 x 16 KB
     unsigned char* sB = sA + 3 * kTcATile;                      // ring of record operand blocks
     float4* sE = reinterpret_cast<float4*>(sB + S * TS::kBStage);  // ring of pixel / weight blocks
-    float* s_part = reinterpret_cast<float*>(sE + S * (TS::kEStage / 16));  // [NG][128] per residue class
+    float* s_part = reinterpret_cast<float*>(sE + S * (TS::kEStage / 16));  // [NG][128] per group
     int* s_cntp = reinterpret_cast<int*>(s_part + NG * kTcPoses);          // [NG][128]
     uint64_t* full = reinterpret_cast<uint64_t*>(s_cntp + NG * kTcPoses);
     uint64_t* empty = full + S;
