@@ -14,7 +14,9 @@
 //
 // Kernels (in launch order per wave):
 //   k_setup        per query: N, subset size M, uniform-stride subset gather
-//                  into 48-byte record pairs, reset of the per-round reductions
+//                  into 48-byte record pairs (and, for tensor-core scoring,
+//                  swizzled operand rows of split pieces), reset of the
+//                  per-round reductions
 //   k_sample_p3p   one minimal sample per thread: Philox triple, bearings,
 //                  P3P (FP32 + FP64 Newton polish), pose slots, compact list
 //   k_tiles        per-query hypothesis-tile prefix for the work queue
@@ -26,6 +28,9 @@
 //                  sums are combined across the cluster
 //                  through distributed shared memory; per round, the best
 //                  (score, pose id) is kept by a 64-bit atomic minimum
+//   k_score_tc     (instead of k_score for large unfused calls) the same
+//                  scores with the projection as split-piece tcgen05.mma
+//                  into TMEM and the rest of the cost in an FP32 epilogue
 //   k_replay       per query (one cluster): rounds in order, LO by
 //                  Gauss-Newton on SE(3) (cluster-reduced normal equations,
 //                  Jacobi-scaled 6x6 Cholesky), termination, final Cauchy
