@@ -138,3 +138,34 @@ def test_batch_end_to_end(tc_ctx):
         ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=2048, p_miss=0.0,
                                 query_id=i, seed=5)
         assert pose_close(res[i]["R"], res[i]["t"], ref["R"], ref["t"]), i
+
+
+def test_batch_with_degenerate_and_tiny_queries(tc_ctx):
+    """A batched call mixing queries of 0, 2, 3 and 5 correspondences (no or
+    too few points: status -7; 3 noise-free points: exact) with full-size ones:
+    the small queries get their own status, the others their poses, and no
+    device error is raised."""
+    rng = np.random.default_rng(11)
+    sizes = [20000, 0, 2, 3, 5, 20000, 20000, 3]
+    qs = [synth.direct_query(rng, max(n, 1), 0.3 if n > 10 else 1.0, 1024, 768, 800.0, noise_px=0.0 if n <= 10 else 1.0,
+                             weights="conf") for n in sizes]
+    t = torch()
+    offs = np.cumsum([0] + sizes)
+    cat = lambda k: np.concatenate([q[k][:n] for q, n in zip(qs, sizes)])
+    corr = imloc.corr_from_arrays(cat("x"), cat("y"), np.concatenate([q["X"][:n] for q, n in zip(qs, sizes)]),
+                                  cat("w"))
+    d_offs = t.from_numpy(offs.astype(np.int64)).cuda()
+    opts = [imloc.default_opts(max_iters=4096, p_miss=0.0, query_id=i, seed=9) for i in range(len(qs))]
+    res_buf = t.zeros(len(qs) * imloc.RESULT_BYTES, dtype=t.uint8, device="cuda")
+    tc_ctx.ransac_pnp_batch_async(corr, d_offs, [q["K"] for q in qs], opts, res_buf)
+    t.cuda.synchronize()
+    res = imloc.results_from_bytes(res_buf.cpu().numpy(), len(qs))
+    for q, n, r in zip(qs, sizes, res):
+        if n < 3:
+            assert r["status"] == -7, (n, r["status"])
+        elif n <= 10:
+            assert r["status"] == 0 and r["num_inliers"] == n, (n, r)
+        else:
+            assert r["status"] == 0
+            assert pose_close(r["R"], r["t"], q["R_gt"], q["t_gt"], deg=0.5, mm=100)
+    assert tc_ctx.device_error() == 0
