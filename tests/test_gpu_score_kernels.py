@@ -169,3 +169,32 @@ def test_batch_with_degenerate_and_tiny_queries(tc_ctx):
             assert r["status"] == 0
             assert pose_close(r["R"], r["t"], q["R_gt"], q["t_gt"], deg=0.5, mm=100)
     assert tc_ctx.device_error() == 0
+
+
+def test_batch_with_the_adaptive_stop(tc_ctx):
+    """The adaptive stop (p_miss = 1e-4) on a batch: several waves of
+    sampling and scoring per call, the operand rows written once.  Poses
+    against the ground truth and, for two queries, the oracle's."""
+    rng = np.random.default_rng(21)
+    qs = [synth.direct_query(rng, 30000, r, 1024, 768, 800.0, weights="conf")
+          for r in (0.5, 0.3, 0.2, 0.4, 0.6, 0.25, 0.35, 0.45)]
+    t = torch()
+    offs = np.cumsum([0] + [len(q["x"]) for q in qs])
+    cat = lambda k: np.concatenate([q[k] for q in qs])
+    corr = imloc.corr_from_arrays(cat("x"), cat("y"), np.concatenate([q["X"] for q in qs]), cat("w"))
+    d_offs = t.from_numpy(offs.astype(np.int64)).cuda()
+    opts = [imloc.default_opts(max_iters=10000, p_miss=1e-4, query_id=i, seed=13) for i in range(len(qs))]
+    res_buf = t.zeros(len(qs) * imloc.RESULT_BYTES, dtype=t.uint8, device="cuda")
+    tc_ctx.ransac_pnp_batch_async(corr, d_offs, [q["K"] for q in qs], opts, res_buf)
+    t.cuda.synchronize()
+    res = imloc.results_from_bytes(res_buf.cpu().numpy(), len(qs))
+    for q, r in zip(qs, res):
+        assert r["status"] == 0
+        assert r["iterations"] < 10000  # the stop fired before the cap
+        assert pose_close(r["R"], r["t"], q["R_gt"], q["t_gt"], deg=0.5, mm=100)
+    for i in (1, 5):
+        q = qs[i]
+        ref = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=10000, p_miss=1e-4,
+                                query_id=i, seed=13)
+        assert pose_close(res[i]["R"], res[i]["t"], ref["R"], ref["t"]), i
+    assert tc_ctx.device_error() == 0
