@@ -80,9 +80,21 @@ int imloc_profile_read(imloc_ctx* ctx, imloc_kernel_stat* out, int32_t max_out, 
  * before the first tuning; host pointers, any of them may be NULL.
  * Calls with enough pose tiles for two per SM (about 39K minimal sets on 152
  * SMs) score on the tensor cores instead (projection as split-bf16 MMAs, same
- * FP32-level scores up to rounding) and do not tune this kernel; the
- * environment variable IMLOC_SCORE_TC=0 or 1 forces either kernel. */
+ * FP32-level scores up to rounding) and do not tune this kernel; see
+ * imloc_set_scoring. */
 int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_per_thread, int32_t* tile_poses);
+/* Scoring kernel of the context's later RANSAC calls (the MSAC scoring of
+ * Sec. 3.3; both kernels compute the same FP32-level scores, they differ in
+ * speed and in rounding): kernel -1 = by call size (the tensor-core kernel
+ * when the call has about two 128-pose tiles per SM; the environment
+ * variable IMLOC_SCORE_TC=0 or 1 overrides), 0 = the FP32 kernel, 1 = the
+ * tensor-core kernel; tc_variant -1 = default (environment IMLOC_TC_VARIANT),
+ * 0 = 80-record blocks with bf16 pieces, 1 = 128-record blocks with bf16
+ * pieces, 2 = 80-record blocks with TF32 pieces, 3 = 64-record blocks with
+ * bf16 pieces.  The continuous-batching
+ * server always uses the FP32 kernel.  IMLOC_ERR_INVALID_ARG for a null
+ * context or values out of range. */
+int imloc_set_scoring(imloc_ctx* ctx, int32_t kernel, int32_t tc_variant);
 
 /* ---- cameras and views -------------------------------------------------- */
 typedef struct { float fx, fy, cx, cy; int32_t width, height; } imloc_camera;   /* pinhole */

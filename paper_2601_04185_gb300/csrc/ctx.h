@@ -31,6 +31,10 @@ struct imloc_ctx {
     std::map<std::string, cudaGraphExec_t> graphs;
     // autotuned score-kernel variant (-1: not tuned yet)
     int score_variant = -1;
+    // scoring kernel chosen with imloc_set_scoring (-1: by call size / environment; 0 FP32; 1 tensor cores)
+    // and the tensor-core variant (-1: by environment, else the default)
+    int scoring_kernel = -1;
+    int scoring_tc_variant = -1;
     float score_variant_ms = 0.f;
     // co-resident clusters of the replay kernel (FP32 / FP64 accumulation x cluster size 8, 4, 2, 1); 0 = not queried
     int replay_occ[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};

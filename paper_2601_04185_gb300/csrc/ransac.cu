@@ -1833,15 +1833,18 @@ static bool fuse_of(bool dflt) { return getenv("IMLOC_NO_FUSE") ? false : (geten
 // Which scoring kernel an unfused call takes: the tensor-core one when the
 // call has enough pose tiles (~1.2 poses per minimal set, 128 per tile) for
 // two per SM, the FP32 one otherwise (a single query: the cluster-split FP32
-// kernel spreads it over more SMs).  IMLOC_SCORE_TC=0 / 1 forces either.
+// kernel spreads it over more SMs).  imloc_set_scoring, else IMLOC_SCORE_TC=0
+// / 1, forces either.
 static bool score_tc_enabled(const imloc_ctx* ctx, int64_t total_samples) {
+    if (ctx->scoring_kernel >= 0) return ctx->scoring_kernel == 1;
     const char* env = getenv("IMLOC_SCORE_TC");
     if (env) return atoi(env) != 0;
     return total_samples * 6 / 5 >= 2LL * std::max(1, ctx->sm_count) * kTcPoses;
 }
 
-// IMLOC_TC_VARIANT=<k> picks the tensor-core scoring variant
-static int tc_variant() {
+// The tensor-core scoring variant: imloc_set_scoring's, else IMLOC_TC_VARIANT=<k>, else 0
+static int tc_variant(const imloc_ctx* ctx) {
+    if (ctx->scoring_tc_variant >= 0) return std::min(ctx->scoring_tc_variant, kNumTcVariants - 1);
     const char* env = getenv("IMLOC_TC_VARIANT");
     return env ? std::min(std::max(atoi(env), 0), kNumTcVariants - 1) : 0;
 }
@@ -1874,7 +1877,7 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         // projections on the tensor cores: one persistent CTA per SM
         rc = launch_tiles(ctx, b, nq, kTcPoses, stream);
         if (rc != IMLOC_OK) return rc;
-        const TcVariant& TV = kTcVariants[tc_variant()];
+        const TcVariant& TV = kTcVariants[tc_variant(ctx)];
         auto kern = want_counts ? TV.fn_count : TV.fn;
         IMLOC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(TV.smem)));
         const int grid = static_cast<int>(
@@ -2049,7 +2052,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.inject = h.inject ? 1 : 0;
         const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
         d.subset = static_cast<ScorePair*>(ws_alloc(ctx, sizeof(ScorePair) * ((std::max(1, o.max_score_corr) + 1) / 2)));
-        d.tc_bf16 = kTcVariants[tc_variant()].bf ? 1 : 0;
+        d.tc_bf16 = kTcVariants[tc_variant(ctx)].bf ? 1 : 0;
         if (tc_on) {
             const int64_t mp = (std::max(1, o.max_score_corr) + kTcBlock - 1) / kTcBlock * kTcBlock;
             d.tc_rec = static_cast<float4*>(ws_alloc(ctx, 128 * mp));
@@ -2126,7 +2129,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         char buf[160];
         snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
                  int(getenv("IMLOC_NO_FUSE") != nullptr) + 2 * int(getenv("IMLOC_FUSE") != nullptr),
-                 tc_on ? 1 + tc_variant() : 0,
+                 tc_on ? 1 + tc_variant(ctx) : 0,
                  (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
         key = buf;
         for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);
@@ -2250,6 +2253,15 @@ int imloc_ransac_pnp_batch_async(imloc_ctx* ctx, int32_t n_queries, const imloc_
     rc = imloc::ransac_impl(ctx, n_queries, hq.data(), st, false);
     int rc2 = imloc::end_call(ctx, st);
     return rc != IMLOC_OK ? rc : rc2;
+}
+
+int imloc_set_scoring(imloc_ctx* ctx, int32_t kernel, int32_t tc_variant) {
+    if (!ctx || kernel < -1 || kernel > 1 || tc_variant < -1 || tc_variant >= imloc::kNumTcVariants)
+        return IMLOC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->scoring_kernel = kernel;
+    ctx->scoring_tc_variant = tc_variant;
+    return IMLOC_OK;
 }
 
 int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_per_thread, int32_t* tile_poses) {

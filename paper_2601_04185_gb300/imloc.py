@@ -117,6 +117,7 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_ransac_pnp_batch_async", "imloc_testing_ransac", "imloc_profile_enable", "imloc_profile_read",
            "imloc_lift_noalloc_async", "imloc_serve_default_config", "imloc_serve_create", "imloc_serve_submit",
            "imloc_serve_poll", "imloc_serve_read_stats", "imloc_serve_destroy", "imloc_score_config",
+           "imloc_set_scoring",
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
            "imloc_triangulate_depth_async", "imloc_retrieve_topk_async", "imloc_ransac_rig_batch",
            "imloc_testing_rig"]
@@ -159,6 +160,7 @@ def load(path: str = LIB_PATH):
     L.imloc_profile_enable.argtypes = [V, C.c_int]
     L.imloc_profile_read.argtypes = [V, P(KernelStat), C.c_int32, P(C.c_int32), C.c_int]
     L.imloc_score_config.argtypes = [V, P(C.c_int32), P(C.c_int32), P(C.c_int32)]
+    L.imloc_set_scoring.argtypes = [V, C.c_int32, C.c_int32]
     L.imloc_retrieve_topk_async.argtypes = [V, V, C.c_int32, V, C.c_int64, C.c_int32, C.c_int32, V, V, V]
     L.imloc_triangulate_default_opts.argtypes = [P(TriangulateOpts)]
     L.imloc_triangulate_default_opts.restype = None
@@ -324,6 +326,11 @@ class Context:
 
     def profile(self, on: bool):
         _check(self.lib.imloc_profile_enable(self.h, 1 if on else 0), "imloc_profile_enable")
+
+    def set_scoring(self, kernel: int = -1, tc_variant: int = -1):
+        """Scoring kernel of later RANSAC calls: -1 by call size, 0 the FP32
+        kernel, 1 the tensor-core kernel; tc_variant -1 default, else 0-3."""
+        _check(self.lib.imloc_set_scoring(self.h, int(kernel), int(tc_variant)), "imloc_set_scoring")
 
     def score_config(self):
         """(threads, poses per thread, poses per tile) of the scoring variant the

@@ -67,6 +67,7 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_ransac_pnp(None, None, None, None, None, None, None) == -1
     lib.imloc_destroy(None)
     assert lib.imloc_score_config(None, None, None, None) == -1
+    assert lib.imloc_set_scoring(None, 0, -1) == -1
     assert lib.imloc_depth_encode_log8_async(None, 4, 4, 4, None, 4, None) == -1
     assert lib.imloc_depth_decode_log8_async(None, 4, 4, 4, None, 4, None) == -1
     assert lib.imloc_triangulate_depth_async(None, None, 4, 4, None, None, 1, None, None, None, 16, None, None,

@@ -1,7 +1,7 @@
-"""Both scoring kernels, each forced on every call: the FP32 one
-(IMLOC_SCORE_TC=0) and the tensor-core one (IMLOC_SCORE_TC=1, which large
-unfused batches take by default) with each of its variants
-(IMLOC_TC_VARIANT), against the FP64 oracle: per-pose truncated scores
+"""Both scoring kernels, each forced for every call of a context
+(imloc_set_scoring): the FP32 one and the tensor-core one (which large
+unfused batches take by default) with each of its variants, against the FP64
+oracle: per-pose truncated scores
 (Sec. 3.3 MSAC cost) and inlier counts on subsets whose size is not a
 multiple of the tensor-core kernel's record block, pose tiles with a ragged
 last tile, the round minima, and end-to-end poses of a batched call.
@@ -23,14 +23,22 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(params=[-1, 0, 1, 2], ids=["fp32", "tc-80rec-bf16", "tc-128rec-bf16", "tc-80rec-tf32"])
-def tc_ctx(request, monkeypatch):
-    if request.param < 0:
-        monkeypatch.setenv("IMLOC_SCORE_TC", "0")
-    else:
-        monkeypatch.setenv("IMLOC_SCORE_TC", "1")
-        monkeypatch.setenv("IMLOC_TC_VARIANT", str(request.param))
+def tc_ctx(request):
     c = imloc.Context(0, 1 << 30)
+    if request.param < 0:
+        c.set_scoring(0)
+    else:
+        c.set_scoring(1, request.param)
     yield c
+    c.close()
+
+
+def test_set_scoring_rejects_bad_values():
+    c = imloc.Context(0, 1 << 20)
+    for kernel, variant in ((2, -1), (-2, -1), (1, 4), (1, -2)):
+        with pytest.raises(imloc.ImlocError):
+            c.set_scoring(kernel, variant)
+    c.set_scoring(-1, -1)
     c.close()
 
 
