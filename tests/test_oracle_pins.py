@@ -419,6 +419,45 @@ def test_lo_is_stationary_and_matches_scipy_least_squares():
     Jf = J.T @ f0
     predicted = float(Jf @ np.linalg.solve(J.T @ J, Jf))
     assert predicted <= 1e-6 * float(f0 @ f0)
+    # first order, directly: the gradient of the weighted squared residuals on
+    # that set, by central differences of the cost, is within the bound that
+    # the stopping rule implies.  A Gauss-Newton step predicts the decrease
+    # g^T (J^T J)^-1 g >= |g|^2 / lambda_max(J^T J) (g = J^T f), and the loop
+    # stops once an accepted step lowers the truncated cost C by < 1e-6 of C,
+    # so at the output |J^T f| <= sqrt(lambda_max * 1e-6 * C), i.e. the cost's
+    # gradient 2 J^T f is at most twice that
+    assert _grad_norm(fun) <= _stationarity_bound(J, s1)
+
+
+def _grad_norm(fun, h=1e-7):
+    cost = lambda p: float(fun(p) @ fun(p))  # noqa: E731
+    return float(np.linalg.norm([(cost(np.eye(6)[k] * h) - cost(-np.eye(6)[k] * h)) / (2 * h) for k in range(6)]))
+
+
+def _stationarity_bound(J, truncated_cost):
+    return 2.0 * math.sqrt(float(np.linalg.eigvalsh(J.T @ J).max()) * 1e-6 * truncated_cost)
+
+
+def test_stationarity_bound_rejects_an_unconverged_lo():
+    # the same check on an LO cut off after one Gauss-Newton step fails: the
+    # bound separates a converged output from one that stopped early
+    q, c, rng = _noisy_query(21)
+    K = q["K"]
+    R0, t0 = _perturb(q["R_gt"], q["t_gt"], rng, 0.3, 0.03)
+    R1, t1, s1 = oracle.lo(c, K, R0, t0, 4.0, iters=1)
+    fx, fy, cx, cy = K
+    Xc = c.X @ R1.T + t1
+    r2 = (fx * Xc[:, 0] / Xc[:, 2] + cx - c.x) ** 2 + (fy * Xc[:, 1] / Xc[:, 2] + cy - c.y) ** 2
+    sel = np.nonzero((Xc[:, 2] > 0) & (r2 < 16.0))[0]
+    sw = np.sqrt(np.concatenate([c.w[sel], c.w[sel]]))
+
+    def fun(p):
+        Rp = Rotation.from_rotvec(p[:3]).as_matrix() @ R1
+        return sw * _residuals(c, K, Rp, p[3:] + t1, sel)
+
+    h = 1e-7
+    J = np.stack([(fun(np.eye(6)[k] * h) - fun(-np.eye(6)[k] * h)) / (2 * h) for k in range(6)], 1)
+    assert _grad_norm(fun) > 10 * _stationarity_bound(J, s1)
 
 
 def test_lo_never_increases_cost_and_handles_no_inliers():
