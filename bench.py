@@ -44,12 +44,16 @@ UNIT = "hyp*corr/s"
 HYPOTHESES = 10000
 MATCHES_PER_PAIR = 5000
 N_VIEWS = 10
-FLOPS_PER_PAIR = 27          # 13 FFMA (2 flops) + 1 FMUL per scored (pose, correspondence) pair
+# The method's work per scored (pose, correspondence) pair, with the projection folded into
+# P = K [R | t]: 9 FMA for P [X; 1], 2 FMA for the pixel residual, 1 MUL + 1 FMA for r^2 and 1 FMA
+# for the weighted truncated sum = 13 FMA (2 flops each) + 1 MUL = 27 flops on the FP32 pipe (plus
+# 1 reciprocal on the MUFU and 2 min/max).  Every scoring roofline below counts these 27 flops per
+# pair against the FP32 FMA peak, whichever unit executes the projection.
+FLOPS_PER_PAIR = 27
 # tensor-core scoring: per pair the FP32 epilogue does 4 FFMA + 1 FMUL (9 flops) after the projection,
 # which runs as 3 coordinate rows x 2 MMA K steps of 16 (24 split-piece terms + 8 zero) x 2 flops
 TC_FP32_FLOPS_PER_PAIR = 9
 TC_MMA_FLOPS_PER_PAIR = 192
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch of k_score on the 16-query C2 step, from
 # the committed ncu capture (profiles/k_score_c2_16queries.md), keyed by the
@@ -271,7 +275,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals, served (continuous batching) vs plain
 # ---------------------------------------------------------------------------
-STORE_VIEWS = 64
+STORE_VIEWS = 1024
 SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
 
 
@@ -458,7 +462,7 @@ def run_rig(dev, peaks, repeats=5, n_queries=16):
         ang = math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(dR) - 1) / 2))))
         errs.append((ang, float(np.linalg.norm(r["R"].T @ r["t"] - q["R_gt"].T @ q["t_gt"]))))
     score_ms = prof["k_rig_score"][1] / repeats if "k_rig_score" in prof else None
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    fp32_peak = fp32_peak_tflops(dev, peaks)[0]
     line = {"workload": f"{n_queries} rig queries x 4 cameras x 2,500 correspondences, inlier ratio U[15%, 50%], "
                         "default options, one call",
             "ms_per_call": ms, "queries_per_s": n_queries / (ms * 1e-3),
@@ -602,28 +606,72 @@ def run_batched_c3(dev, steps=5):
     kst = ctx.profile_read(reset=True)
     res = imloc.results_from_bytes(res_buf.cpu().numpy(), nq)
     pairs = float(sum(r["hypotheses"] * min(int(n), 10000) for r, n in zip(res, np.diff(offs))))
+    ctx.profile(False)
+    # scoring forms on the same batch: the FP32 kernel, and bf16-packed coordinates with FP32 rescoring
+    forms = {}
+    for name, scoring, bf in (("fp32_kernel", 0, 0), ("bf16_rescore", -1, 1)):
+        ctx.set_scoring(scoring)
+        opts_f = [imloc.default_opts(max_iters=q["hypotheses"], p_miss=0.0, query_id=i, seed=5, score_bf16=bf)
+                  for i, q in enumerate(qs)]
+        prep_f = imloc.prepare_ransac_batch([q["K"] for q in qs], opts_f)
+        buf_f = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        for _ in range(2):
+            ctx.ransac_pnp_batch_async(corr, d_offs, None, None, buf_f, stream=stream, prepared=prep_f)
+        torch.cuda.synchronize()
+        a2, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a2.record(stream)
+        for _ in range(steps):
+            ctx.ransac_pnp_batch_async(corr, d_offs, None, None, buf_f, stream=stream, prepared=prep_f)
+        b2.record(stream)
+        torch.cuda.synchronize()
+        rf = imloc.results_from_bytes(buf_f.cpu().numpy(), nq)
+        rot = [_rot_err_deg(x["R"], y["R"]) for x, y in zip(rf, res)]
+        tr = [1e3 * float(np.linalg.norm(-x["R"].T @ x["t"] + y["R"].T @ y["t"])) for x, y in zip(rf, res)]
+        forms[name] = {"ms_per_batch": a2.elapsed_time(b2) / steps,
+                       "vs_default_rot_deg_max": float(max(rot)), "vs_default_trans_mm_max": float(max(tr)),
+                       "status": sorted({x["status"] for x in rf})}
+    ctx.set_scoring(-1)
+    # share of (pose, record) pairs the bf16 test left to the FP32 rescoring, on 8 of the batch's queries
+    resc, tot = 0, 0
+    for i in range(0, nq, nq // 8):
+        q = qs[i]
+        n = len(q["x"])
+        H = q["hypotheses"]
+        c1 = imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"], device=dev)
+        cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+        dbg = dict(scores=torch.full((4 * H,), float("nan"), device=dev), rescored_pairs=cnt)
+        ctx.testing_ransac(c1, q["K"], imloc.default_opts(max_iters=H, p_miss=0.0, query_id=i, seed=5, score_bf16=1),
+                           n, dbg)
+        scored = int(torch.isfinite(dbg["scores"]).sum().item())
+        m = min(n, 10000)
+        resc += int(cnt.item())
+        tot += scored * (m + (m & 1))
+    forms["bf16_rescore"]["rescored_fraction"] = resc / max(1, tot)
+    forms["bf16_rescore"]["note"] = ("bf16 world coordinates (centred, scaled by a power of two per query) give a "
+                                     "per-pair bound of several pixels at these scales, so every pair that the bound "
+                                     "cannot place beyond tau is rescored in FP32 with the FP32 kernel's arithmetic")
     ctx.close()
     skey = "k_score_tc" if "k_score_tc" in kst else "k_score"
     score_ms = kst.get(skey, (1, 0.0))[1] / max(1, kst.get(skey, (1, 0.0))[0])
-    fpp = TC_FP32_FLOPS_PER_PAIR if skey == "k_score_tc" else FLOPS_PER_PAIR
     return {"workload": "C3: 256 direct queries, N log-uniform in [2k, 100k], inlier ratio U[5%, 70%], "
                         "4,096-16,384 minimal sets, LO + refinement, one batched call",
             "ms_per_batch": ms, "hyp_corr_per_s": pairs / (ms * 1e-3), "queries_per_s": nq / (ms * 1e-3),
             "correspondences": int(offs[-1]), "scoring_kernel": skey, "score_ms": score_ms,
-            "score_fp32_tflops": fpp * pairs / (score_ms * 1e-3) / 1e12 if score_ms else None,
-            "score_fp32_flops_per_pair": fpp,
+            "score_tflops": FLOPS_PER_PAIR * pairs / (score_ms * 1e-3) / 1e12 if score_ms else None,
+            "score_flops_per_pair": FLOPS_PER_PAIR,
             "kernels_ms": {k: v[1] / steps for k, v in kst.items()},
-            "status": sorted({r["status"] for r in res})}
+            "status": sorted({r["status"] for r in res}), "scoring_forms": forms}
 
 
 # ---------------------------------------------------------------------------
 # precision study (C4): P3P polish and LO accumulation variants vs the oracle
 # ---------------------------------------------------------------------------
-def _gen_c4_query(i):
+def _gen_c4_query(args):
     from paper_2601_04185_gb300 import synth
 
+    i, n = args
     rng = np.random.default_rng(500 + i)
-    sig = (0.5, 1.0, 1.5, 2.0)[i * 4 // PRECISION_QUERIES]
+    sig = (0.5, 1.0, 1.5, 2.0)[i * 4 // n]
     q = synth.localization_query(rng, pixel_noise=sig, depth_noise=0.01)
     q.pop("scene", None)
     q["sigma"] = sig
@@ -648,19 +696,38 @@ def _rot_err_deg(Ra, Rb):
     return math.degrees(2.0 * math.asin(min(1.0, chord / (2.0 * math.sqrt(2.0)))))
 
 
-def run_precision_study(args):
+def _c4_queries(n):
+    with cf.ProcessPoolExecutor(max_workers=min(n, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_c4_query, [(i, n) for i in range(n)]))
+
+
+def _c4_oracle(qs):
+    """The FP64 oracle's final pose of every C4 query (threads; the C oracle releases the GIL)."""
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        ref = list(ex.map(_oracle_pose, [(q, i) for i, q in enumerate(qs)]))
+    return ref, time.perf_counter() - t0
+
+
+PRECISION_VARIANTS = (
+    # (P3P polish, LO / refinement accumulation, LO / refinement 6x6 solve, scoring coordinates)
+    ("fp32 + double-float polish", "fp32", "fp32", "fp32"),
+    ("fp32 + double-float polish", "fp64", "fp32", "fp32"),
+    ("fp32 + double-float polish", "fp32", "fp64", "fp32"),
+    ("fp32 + double-float polish", "fp64", "fp64", "fp32"),
+    ("fp32", "fp32", "fp32", "fp32"),
+    ("fp32", "fp64", "fp64", "fp32"),
+    ("fp32 + double-float polish", "fp32", "fp32", "bf16 + fp32 rescore"),
+)
+
+
+def precision_study(dev, qs, ref, oracle_s):
+    """C4: every precision variant on the same lifted queries; final poses
+    against the FP64 oracle's (and against ground truth), batch time."""
     import torch
 
     from paper_2601_04185_gb300 import imloc
 
-    with cf.ProcessPoolExecutor(max_workers=os.cpu_count() or 1, mp_context=mp.get_context("spawn")) as ex:
-        qs = list(ex.map(_gen_c4_query, range(PRECISION_QUERIES)))
-    t0 = time.perf_counter()
-    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
-        ref = list(ex.map(_oracle_pose, [(q, i) for i, q in enumerate(qs)]))
-    oracle_s = time.perf_counter() - t0
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
     views, big, qb = concat_batch(qs)
     d_views = []
     for v in views:
@@ -669,66 +736,128 @@ def run_precision_study(args):
         d_views.append(d)
     d_match = {k: torch.from_numpy(big[k]).to(dev) for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
     d_match.update({k: big[k] for k in ("seg_off", "seg_view", "seg_dir")})
-    ctx = imloc.Context(0, 2 << 30)
+    ctx = imloc.Context(dev.index, 2 << 30)
     corr, offsets = ctx.lift_batch(qb, d_views, d_match)
     nq = len(qs)
     out = {"workload": f"C4: {nq} queries of 50k matches (10 views x 5,000), depth x (1 + N(0, 0.01)), pixel noise "
-                       "0.5/1/1.5/2 px (16 each), 10,000 minimal sets, LO + refinement; errors vs the FP64 oracle's "
-                       "final pose and vs ground truth",
+                       "0.5/1/1.5/2 px (a quarter each), 10,000 minimal sets, LO + refinement; errors vs the FP64 "
+                       "oracle's final pose and vs ground truth",
            "oracle_seconds": oracle_s, "variants": []}
-    for polish in (1, 0):
-        for lo64 in (0, 1):
-            opts = [imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=31, p3p_fp64_polish=polish,
-                                       lo_fp64_accumulate=lo64) for i in range(nq)]
-            res_buf = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
-            ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
-            ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
-            b.record()
-            torch.cuda.synchronize()
-            res = imloc.results_from_bytes(res_buf.cpu().numpy(), nq)
-            rot = np.array([_rot_err_deg(r["R"], o[0]) for r, o in zip(res, ref)])
-            trans = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + o[0].T @ o[1]) for r, o in zip(res, ref)])
-            rot_gt = np.array([_rot_err_deg(r["R"], q["R_gt"]) for r, q in zip(res, qs)])
-            trans_gt = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + q["R_gt"].T @ q["t_gt"])
-                                 for r, q in zip(res, qs)])
-            within = float(np.mean((rot <= 0.05) & (trans <= 5.0)))
-            out["variants"].append({
-                "p3p": "fp32 + double-float polish" if polish else "fp32", "lo_normal_equations": "fp64" if lo64 else "fp32",
-                "vs_oracle_rot_deg": {"median": float(np.median(rot)), "p90": float(np.percentile(rot, 90)),
-                                      "max": float(rot.max())},
-                "vs_oracle_trans_mm": {"median": float(np.median(trans)), "p90": float(np.percentile(trans, 90)),
-                                       "max": float(trans.max())},
-                "within_0.05deg_5mm": within,
-                "vs_gt_rot_deg_median": float(np.median(rot_gt)), "vs_gt_trans_mm_median": float(np.median(trans_gt)),
-                "batch_ms": a.elapsed_time(b), "status": sorted({r["status"] for r in res})})
+    for p3p, acc, solve, coords in PRECISION_VARIANTS:
+        opts = [imloc.default_opts(max_iters=HYPOTHESES, p_miss=0.0, query_id=i, seed=31,
+                                   p3p_fp64_polish=int(p3p != "fp32"), lo_fp64_accumulate=int(acc == "fp64"),
+                                   lo_fp64_solve=int(solve == "fp64"), score_bf16=int(coords != "fp32"))
+                for i in range(nq)]
+        res_buf = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+        ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.ransac_pnp_batch_async(corr, offsets, [q["K"] for q in qs], opts, res_buf)
+        b.record()
+        torch.cuda.synchronize()
+        res = imloc.results_from_bytes(res_buf.cpu().numpy(), nq)
+        rot = np.array([_rot_err_deg(r["R"], o[0]) for r, o in zip(res, ref)])
+        trans = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + o[0].T @ o[1]) for r, o in zip(res, ref)])
+        rot_gt = np.array([_rot_err_deg(r["R"], q["R_gt"]) for r, q in zip(res, qs)])
+        trans_gt = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + q["R_gt"].T @ q["t_gt"])
+                             for r, q in zip(res, qs)])
+        within = float(np.mean((rot <= 0.05) & (trans <= 5.0)))
+        out["variants"].append({
+            "p3p": p3p, "lo_accumulate": acc, "lo_solve": solve, "scoring_coordinates": coords,
+            "vs_oracle_rot_deg": {"median": float(np.median(rot)), "p90": float(np.percentile(rot, 90)),
+                                  "max": float(rot.max())},
+            "vs_oracle_trans_mm": {"median": float(np.median(trans)), "p90": float(np.percentile(trans, 90)),
+                                   "max": float(trans.max())},
+            "within_0.05deg_5mm": within,
+            "vs_gt_rot_deg_median": float(np.median(rot_gt)), "vs_gt_trans_mm_median": float(np.median(trans_gt)),
+            "batch_ms": a.elapsed_time(b), "status": sorted({r["status"] for r in res})})
     ctx.close()
-    print(json.dumps({"precision_study": out}))
+    return out
+
+
+def run_precision_study(args):
+    import torch
+
+    qs = _c4_queries(PRECISION_QUERIES)
+    ref, oracle_s = _c4_oracle(qs)
+    torch.cuda.set_device(0)
+    print(json.dumps({"precision_study": precision_study(torch.device("cuda", 0), qs, ref, oracle_s)}))
     return 0
+
+
+# ---------------------------------------------------------------------------
+# C1: one plain query per call
+# ---------------------------------------------------------------------------
+C1_QUERIES = 16
+
+
+def c1_inputs(n=C1_QUERIES):
+    """C1 queries and the FP64 oracle's final pose of each (same seed and query id as the GPU calls)."""
+    import oracle
+
+    from paper_2601_04185_gb300 import synth
+
+    qs = [synth.config1(300 + i) for i in range(n)]
+
+    def one(i):
+        q = qs[i]
+        r = oracle.ransac_pnp(oracle.Corr(q["x"], q["y"], q["X"], q["w"]), q["K"], max_iters=q["hypotheses"],
+                              p_miss=0.0, tau=q["tau"], query_id=i, seed=41)
+        return r["R"], r["t"]
+
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        ref = list(ex.map(one, range(n)))
+    return qs, ref, time.perf_counter() - t0
+
+
+def run_c1(dev, qs, ref, oracle_s, reps=5):
+    """C1: a single query per imloc_ransac_pnp call (2,000 correspondences,
+    1,000 minimal sets, LO, refinement; host-synchronous), timed on the host
+    clock per call: p50/p99 latency, queries/s, hyp*corr/s; final poses
+    against the FP64 oracle's."""
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    ctx = imloc.Context(dev.index, 256 << 20)
+    corrs = [imloc.corr_from_arrays(q["x"], q["y"], q["X"], q["w"], device=dev) for q in qs]
+    opts = [imloc.default_opts(max_iters=q["hypotheses"], p_miss=0.0, tau_px=q["tau"], query_id=i, seed=41)
+            for i, q in enumerate(qs)]
+    stream = torch.cuda.Stream(dev)
+    for i, q in enumerate(qs):
+        ctx.ransac_pnp(corrs[i], q["K"], opts[i], stream=stream)
+    lat, res, pairs = [], [None] * len(qs), 0.0
+    for _ in range(reps):
+        for i, q in enumerate(qs):
+            t0 = time.perf_counter()
+            r = ctx.ransac_pnp(corrs[i], q["K"], opts[i], stream=stream)
+            lat.append(1e3 * (time.perf_counter() - t0))
+            res[i] = r
+            pairs += r["hypotheses"] * min(len(q["x"]), 10000)
+    ctx.close()
+    lat_s = sorted(lat)
+    rot = np.array([_rot_err_deg(r["R"], o[0]) for r, o in zip(res, ref)])
+    trans = np.array([1e3 * np.linalg.norm(-r["R"].T @ r["t"] + o[0].T @ o[1]) for r, o in zip(res, ref)])
+    return {"workload": "C1: one query per call, 2,000 correspondences (640x480, f = 500, 30 % inliers, N(0, 1 px)), "
+                        "1,000 minimal sets, tau 4 px, LO + Cauchy refinement; host-synchronous imloc_ransac_pnp, "
+                        "correspondences resident on the device",
+            "latency_ms_p50": lat_s[len(lat_s) // 2],
+            "latency_ms_p99": lat_s[min(len(lat_s) - 1, int(math.ceil(0.99 * len(lat_s))) - 1)],
+            "queries_per_s": 1e3 / statistics.mean(lat), "hyp_corr_per_s": pairs / (sum(lat) * 1e-3),
+            "calls": len(lat), "status": sorted({r["status"] for r in res}), "oracle_seconds": oracle_s,
+            "vs_oracle_rot_deg_max": float(rot.max()), "vs_oracle_trans_mm_max": float(trans.max()),
+            "within_0.05deg_5mm": float(np.mean((rot <= 0.05) & (trans <= 5.0)))}
 
 
 # ---------------------------------------------------------------------------
 # lift roofline on a batched shape (many queries, ~10^7 matches per launch)
 # ---------------------------------------------------------------------------
-def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
-    """One lift launch over all serving queries concatenated (each query's
-    matches against its own store views); algorithmic bytes / event time.
-    log8: the store views as 8-bit log depth codes (the depth codec of
-    Sec. 3.3 "Data Compression", decoded inside the lift)."""
+def concat_store_queries(dev, store_views_dev, queries):
+    """The matches of serving queries concatenated (each query's segments
+    pointing at the store views it uses) and moved to the device."""
     import torch
-
-    from paper_2601_04185_gb300 import imloc
-
-    if log8:
-        enc = []
-        for v in store_views_dev:
-            d = dict(v)
-            d["depth"] = imloc.depth_encode_log8(v["depth"])
-            enc.append(d)
-        torch.cuda.synchronize()
-        store_views_dev = enc
 
     views, qb = [], [0]
     cat = {k: [] for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
@@ -748,10 +877,77 @@ def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
             seg_dir.append(int(m["seg_dir"][s_]))
         qb.append(qb[-1] + int(m["seg_off"][-1]))
     big = {k: np.concatenate(v).astype(np.float32) for k, v in cat.items()}
-    n = int(qb[-1])
     d_match = {k: torch.from_numpy(big[k]).to(dev) for k in big}
     d_match.update(seg_off=np.array(seg_off, np.int64), seg_view=np.array(seg_view, np.int32),
                    seg_dir=np.array(seg_dir, np.int32))
+    return views, np.array(qb, np.int64), big, d_match, seg_off, seg_dir
+
+
+def run_batched_c5(dev, store_views_dev, queries, repeats=5):
+    """The serving queries in one batched call (lift + LO-RANSAC with the
+    served options: at most 10,000 minimal sets, adaptive stop 1e-4), matches
+    resident on the device: the batched rate the served form is compared with."""
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    views, qb, big, d_match, _, _ = concat_store_queries(dev, store_views_dev, queries)
+    nq = len(queries)
+    ctx = imloc.Context(dev.index, 2 << 30)
+    stream = torch.cuda.Stream(dev)
+    corr = imloc.alloc_corr(int(qb[-1]), dev)
+    offs = torch.zeros(nq + 1, dtype=torch.int64, device=dev)
+    res = torch.zeros(nq * imloc.RESULT_BYTES, dtype=torch.uint8, device=dev)
+    opts = [imloc.default_opts(max_iters=10000, p_miss=1e-4, query_id=i, seed=4321) for i in range(nq)]
+    pl = imloc.prepare_lift_batch(qb, views, d_match)
+    pr = imloc.prepare_ransac_batch([q["K"] for q in queries], opts)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def once():
+        ctx.lift_batch(qb, views, d_match, out=corr, offsets=offs, stream=stream, prepared=pl)
+        ctx.ransac_pnp_batch_async(corr, offs, None, None, res, stream=stream, prepared=pr)
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(repeats):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        once()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    r = imloc.results_from_bytes(res.cpu().numpy(), nq)
+    ctx.close()
+    m = statistics.median(ms)
+    return {"queries": nq, "matches": int(qb[-1]), "ms_per_batch": m, "queries_per_s": nq / (m * 1e-3),
+            "status": sorted({x["status"] for x in r}),
+            "note": "the serving queries lifted and localized in one batched call each repetition (L2 flushed)"}
+
+
+def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
+    """One lift launch over all serving queries concatenated (each query's
+    matches against its own store views); algorithmic bytes / event time.
+    log8: the store views as 8-bit log depth codes (the depth codec of
+    Sec. 3.3 "Data Compression", decoded inside the lift)."""
+    import torch
+
+    from paper_2601_04185_gb300 import imloc
+
+    if log8:
+        enc = []
+        for v in store_views_dev:
+            d = dict(v)
+            d["depth"] = imloc.depth_encode_log8(v["depth"])
+            enc.append(d)
+        torch.cuda.synchronize()
+        store_views_dev = enc
+
+    views, qb, big, d_match, seg_off, seg_dir = concat_store_queries(dev, store_views_dev, queries)
+    n = int(qb[-1])
     ctx = imloc.Context(dev.index, 512 << 20)
     out = imloc.alloc_corr(n, dev)
     offs = torch.zeros(len(queries) + 1, dtype=torch.int64, device=dev)
@@ -781,6 +977,17 @@ def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
             "bytes_per_launch_64b_atoms": nbytes64, "achieved_gbs_64b_atoms": nbytes64 / (launch_ms * 1e-3) / 1e9,
             "workload": f"{len(queries)} serving queries concatenated ({n} matches) against "
                         f"{len(views)} resident 1024x768 depth maps, L2 flushed before each launch"}
+
+
+def fp32_peak_tflops(dev, peaks):
+    """Derived FP32 FMA peak of the device: SMs (queried) x 128 lanes x 2 flops x max SM clock."""
+    import torch
+
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return (sm_count * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12,
+            f"{sm_count} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {mhz:.0f} MHz "
+            "(max SM clock, MEASURED_PEAKS.json; derived FP32 FMA peak)")
 
 
 def load_peaks():
@@ -828,6 +1035,14 @@ def run_ours(args):
     serving_inputs = None
     if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_serving:
         serving_inputs = make_store_and_queries(2024, args.serve_queries)
+    # C1 and C4 inputs with the FP64 oracle's poses (host cores, before the GPU work)
+    c1_in = c4_in = None
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        if not args.no_c1:
+            c1_in = c1_inputs()
+        if not args.no_c4:
+            qs4 = _c4_queries(args.c4_queries)
+            c4_in = (qs4,) + _c4_oracle(qs4)
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", torch.cuda.current_device())
     views, big, qb = concat_batch(queries)
@@ -949,8 +1164,7 @@ def run_ours(args):
     pairs_full = float(sum(r["hypotheses"] * min(int(n), full_cap) for r, n in zip(res_full, n_corr_full)))
     full_key = "k_score_tc" if "k_score_tc" in kfull else "k_score"
     full_ms = kfull[full_key][1] / max(1, kfull[full_key][0]) if full_key in kfull else None
-    full_fpp = TC_FP32_FLOPS_PER_PAIR if full_key == "k_score_tc" else FLOPS_PER_PAIR
-    full_tflops = pairs_full * full_fpp / (full_ms * 1e-3) / 1e12 if full_ms else None
+    full_tflops = pairs_full * FLOPS_PER_PAIR / (full_ms * 1e-3) / 1e12 if full_ms else None
 
     # ---- plain form: one query per call (lift, then RANSAC), host-synchronous ----
     lat = []
@@ -982,8 +1196,7 @@ def run_ours(args):
     score_key = "k_score_tc" if "k_score_tc" in kms else "k_score"
     score_launch_ms = kms.get(score_key, 0.0) / max(1, launches.get(score_key, 1))
     pairs_per_launch = pairs_per_step * args.steps / max(1, launches.get(score_key, 1))
-    score_fpp = TC_FP32_FLOPS_PER_PAIR if score_key == "k_score_tc" else FLOPS_PER_PAIR
-    achieved_tflops = score_fpp * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
+    achieved_tflops = FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12 if score_launch_ms else None
     u_launches, u_ms = kstats_unfused.get("k_score", (1, 0.0))
     score_only_ms = u_ms / max(1, u_launches)
     score_only_tflops = FLOPS_PER_PAIR * pairs_per_step / (score_only_ms * 1e-3) / 1e12 if score_only_ms else None
@@ -992,9 +1205,11 @@ def run_ours(args):
         score_traffic = SCORE_TC_TRAFFIC_PER_LAUNCH if nq == 16 else None
     else:
         score_traffic = SCORE_TRAFFIC_PER_LAUNCH.get(tuple(score_cfg[:2])) if (score_cfg and nq == 16) else None
-    peak_clock_mhz = 2070.0
-    peak_tflops = SM_COUNT * FP32_LANES_PER_SM * 2 * peak_clock_mhz * 1e6 / 1e12
-    bf16_peak = load_peaks().get("bf16_tflops", 1900.0)
+    peaks = load_peaks()
+    peak_tflops, peak_basis = fp32_peak_tflops(dev, peaks)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
+    tc_epi_tflops = (TC_FP32_FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12
+                     if (score_key == "k_score_tc" and score_launch_ms) else None)
     tc_tensor_tflops = (TC_MMA_FLOPS_PER_PAIR * pairs_per_launch / (score_launch_ms * 1e-3) / 1e12
                         if (score_key == "k_score_tc" and score_launch_ms) else None)
     lift_ms = kms.get("k_lift", 0.0) / max(1, launches.get("k_lift", 1))
@@ -1003,7 +1218,6 @@ def run_ours(args):
     conf_ok = big["conf"] > np.float32(0.05)
     dirs = np.repeat(big["seg_dir"], np.diff(big["seg_off"]))
     lift_bytes = 20 * n_matches + int(np.sum(np.where(dirs[conf_ok] == 0, 64, 32))) + 28 * int(offs[-1])
-    peaks = load_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     lift_gbs = lift_bytes / (lift_ms * 1e-3) / 1e9 if lift_ms else None
 
@@ -1022,27 +1236,25 @@ def run_ours(args):
         "plain": {"latency_ms_p50": p50, "latency_ms_p99": p99, "queries_per_s": 1e3 / statistics.mean(lat),
                   "form": "one query per call: imloc_lift_async + imloc_ransac_pnp (host-synchronous)",
                   "samples": len(lat)},
-        "roofline": ({"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
-                      "traffic": score_traffic, "kernel": "k_score_tc", "variant": "80-record blocks, bf16 pieces",
-                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
-                      "flops_per_pair": TC_FP32_FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
-                      "launch_ms": score_launch_ms,
-                      "tensor": {"achieved": tc_tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                                 "frac": (tc_tensor_tflops / bf16_peak) if tc_tensor_tflops else None,
-                                 "flops_per_pair": TC_MMA_FLOPS_PER_PAIR,
-                                 "peak_basis": "measured bf16 burst (cuBLAS)"},
-                      "note": "tensor-core scoring: the projection runs on the tensor pipe (6 split bf16 piece "
-                              "products per coordinate row, 3 rows, K padded to 32: 192 MMA flops per pair); "
-                              "achieved counts the FP32 epilogue's 9 flops per pair against the FP32 pipe; the "
-                              "kernel is latency-bound (see roofline_fp32_kernel for the FP32-only kernel)"}
-                     if score_key == "k_score_tc" else
-                     {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
-                      "traffic": score_traffic, "kernel": "k_score", "variant": score_cfg,
-                      "peak_basis": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (derived, FP32 FMA pipe)",
-                      "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
-                      "launch_ms": score_launch_ms}),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
+                     "traffic": score_traffic, "kernel": score_key,
+                     "variant": "80-record blocks, bf16 pieces" if score_key == "k_score_tc" else score_cfg,
+                     "peak_basis": peak_basis, "flops_per_pair": FLOPS_PER_PAIR,
+                     "flops_per_pair_basis": "13 FMA + 1 MUL per (pose, correspondence) pair",
+                     "pairs_per_launch": pairs_per_launch, "launch_ms": score_launch_ms,
+                     **({"tensor": {"achieved": tc_tensor_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                                    "frac": (tc_tensor_tflops / bf16_peak) if tc_tensor_tflops else None,
+                                    "flops_per_pair": TC_MMA_FLOPS_PER_PAIR,
+                                    "peak_basis": "measured bf16 burst (cuBLAS)"},
+                         "fp32_epilogue": {"achieved": tc_epi_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                                           "frac": (tc_epi_tflops / peak_tflops) if tc_epi_tflops else None,
+                                           "flops_per_pair": TC_FP32_FLOPS_PER_PAIR},
+                         "note": "tensor-core scoring: achieved counts the method's 27 flops per pair; the "
+                                 "projection runs on the tensor pipe (6 split bf16 piece products per coordinate "
+                                 "row, 3 rows, K padded to 32: 192 MMA flops per pair, sub-entry tensor) and the "
+                                 "FP32 epilogue does 9 flops per pair (sub-entry fp32_epilogue)"}
+                        if score_key == "k_score_tc" else {})},
         "roofline_fp32_kernel": {"bound": "alu", "achieved": score_only_tflops, "peak": peak_tflops,
                                  "unit": "TFLOP/s", "kernel": "k_score",
                                  "frac": (score_only_tflops / peak_tflops) if score_only_tflops else None,
@@ -1058,7 +1270,7 @@ def run_ours(args):
                             "frac": (full_tflops / peak_tflops) if full_tflops else None, "launch_ms": full_ms,
                             "pairs_per_launch": pairs_full,
                             "mean_scored_corr": float(np.mean(np.minimum(n_corr_full, full_cap))),
-                            "kernel": full_key, "flops_per_pair": full_fpp,
+                            "kernel": full_key, "flops_per_pair": FLOPS_PER_PAIR,
                             "note": "stress mode: the same step's poses scored against all N correspondences "
                                     "(subset cap raised to 65,536), one scoring launch"},
         "lift_in_step": {"bound": "hbm", "achieved": lift_gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -1078,6 +1290,12 @@ def run_ours(args):
     # ---- batched C3 ----
     if world == 1 and not args.no_c3:
         line["batched_c3"] = run_batched_c3(dev)
+    # ---- C1: one plain query per call ----
+    if c1_in is not None:
+        line["c1"] = run_c1(dev, *c1_in)
+    # ---- C4: precision variants against the FP64 oracle ----
+    if c4_in is not None:
+        line["precision_study"] = precision_study(dev, *c4_in)
     # ---- retrieval nearest-neighbour search (next row f4) ----
     if world == 1 and not args.no_retrieval:
         line["retrieval"] = run_retrieval(dev, peaks)
@@ -1108,6 +1326,9 @@ def run_ours(args):
                              "note": "same matches as roofline_lift, store views as 8-bit log depth codes "
                                      "(Sec. 3.3 Data Compression) decoded inside k_lift; L2 flushed before each launch"}
         line["serving"] = run_serving(dev, SERVE_RATES, args.serve_per_rate, sq, dv)
+        line["serving"]["batched"] = run_batched_c5(dev, dv, sq)
+        peak = max(x["q_per_s"] for x in line["serving"]["served"])
+        line["serving"]["served_peak_over_batched"] = peak / line["serving"]["batched"]["queries_per_s"]
         line["serving"]["workload"] = (f"C5: map store of {STORE_VIEWS} views (1024x768 float32 depth, resident), "
                                        f"{len(sq)} distinct queries of 10-40 views x 5,000 matches, "
                                        "10,000 minimal sets max with the adaptive stop (p = 1e-4); Poisson arrivals")
@@ -1139,6 +1360,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--no-c4", action="store_true")
+    ap.add_argument("--c4-queries", type=int, default=16, help="queries of the precision study in the bench line")
     ap.add_argument("--no-triangulation", action="store_true")
     ap.add_argument("--no-rig", action="store_true")
     ap.add_argument("--no-retrieval", action="store_true")

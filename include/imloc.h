@@ -252,17 +252,24 @@ int imloc_lift_batch_async(imloc_ctx* ctx, int32_t n_queries, const int64_t* que
  * device memory for other components up front, or callers that must not
  * create a context (imloc_create allocates its workspace): it lifts one
  * query exactly like imloc_lift_async but needs no context and performs no
- * allocation.  Its scratch (scan state of the compaction, view and segment
- * tables; 113,152 bytes) is a fixed array inside the library that every GPU
- * loading the library holds until the process exits.
+ * allocation.  Its scratch (scan state of the compaction, view, segment and
+ * tile tables, an error word; 147,968 bytes) is a fixed array inside the
+ * library that every GPU loading the library holds until the process exits.
  *   - Uses the calling thread's current CUDA device.  The first call on a
- *     device looks the array's device address up (cudaGetSymbolAddress);
- *     make that first call before any stream capture.
+ *     device looks the array's device address up (cudaGetSymbolAddress) and
+ *     keeps it for the process: do not call it again on a device after
+ *     cudaDeviceReset there.
  *   - Limits: m->n <= 8,388,608 matches, n_views <= 256, n_segments <= 1024;
  *     larger inputs return IMLOC_ERR_INVALID_ARG without doing any work.
+ *   - The view and segment tables are copied from host memory that lives
+ *     only during the call, so a call on a stream that is being captured
+ *     into a CUDA graph is refused with IMLOC_ERR_INVALID_ARG.
  *   - Every call shares the one array: calls that overlap on the GPU (on
  *     different streams, or from several threads without ordering) race and
  *     give wrong results.  Calls on one stream are ordered and safe.
+ *   - If the compaction's bounded wait for a predecessor tile gives up (it
+ *     does not in a fault-free run), *out->count (when given) receives
+ *     IMLOC_ERR_TIMEOUT instead of the count.
  *   - Host buffers (views, segments) may be freed once the call returns. */
 int imloc_lift_noalloc_async(const imloc_view* views, int32_t n_views, const imloc_matches* m, imloc_corr* out,
                              void* stream);
@@ -294,9 +301,15 @@ typedef struct {
     uint32_t query_id;
     int32_t enumerate_all;   /* test mode: every triple of the subset in one round */
     int32_t lo_fp64_accumulate; /* 1: LO / refinement sums each point's normal-equation terms in FP64
-                                   (default 0: FP32 per thread, FP64 across warps and CTAs); the 6x6
-                                   solve is FP64 either way */
-    int32_t reserved;
+                                   (default 0: FP32 per thread, FP64 across warps and CTAs) */
+    int32_t lo_fp64_solve;   /* 1: LO / refinement solve their 6x6 normal equations (Cholesky of the
+                                Jacobi-scaled system) in FP64 from the FP64 sums; default 0: the same
+                                solve in FP32.  The pose itself is kept and updated in FP64 either way */
+    int32_t score_bf16;      /* 1: score the minimal-sample poses with bf16-packed subset coordinates
+                                (centred and scaled per query) and rescore in FP32 every pair that the
+                                bf16 bound cannot classify as an outlier; same scores and counts as the
+                                FP32 scoring up to FP32 rounding.  Default 0 */
+    int32_t reserved;        /* 0 */
 } imloc_ransac_opts;
 
 /* Fill `o` with the defaults above. */

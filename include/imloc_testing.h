@@ -25,6 +25,8 @@ typedef struct {
     uint64_t* round_best;      /* ceil(H / batch): (score bits << 32) | pose id, ~0 if the round had no pose */
     const float* inject_poses; /* n_inject * 12: score these poses (pose id 4 k) instead of sampling */
     int64_t n_inject;
+    uint64_t* rescored_pairs;  /* 1 word, added to: with opts->score_bf16, the (pose, record) pairs that the
+                                  bf16 test could not classify as outliers and that were rescored in FP32 */
 } imloc_debug;
 
 /* One query with the debug buffers above.  The adaptive stop must be off
@@ -43,6 +45,15 @@ int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_cam
 int imloc_testing_rig(imloc_ctx* ctx, const imloc_corr* corr, const int32_t* d_cam, const imloc_rig* rig,
                       const imloc_ransac_opts* opts, const imloc_debug* dbg, imloc_result* out,
                       uint8_t* d_inlier_mask, void* stream);
+
+/* The lift of imloc_lift_async with its first `skip_tiles` tiles (1..255)
+ * never taken, so that their successors' look-back waits can only end by
+ * their iteration limit `spin_limit` (>= 1): exercises the bounded wait and
+ * its error report.  The kernel ends; the context's error word then reads
+ * IMLOC_ERR_TIMEOUT (imloc_device_error) and the output is not meaningful.
+ * Needs more than `skip_tiles` tiles of 1,024 matches. */
+int imloc_testing_lift_stalled(imloc_ctx* ctx, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                               imloc_corr* out, int32_t skip_tiles, uint32_t spin_limit, void* stream);
 
 #ifdef __cplusplus
 }

@@ -192,6 +192,8 @@ int imloc_device_error(imloc_ctx* c) {
 
 const char* imloc_last_cuda_error(void) { return imloc::g_last_cuda_error; }
 
+static_assert(sizeof(imloc_ransac_opts) == 80, "imloc_ransac_opts layout of the header");
+
 void imloc_ransac_default_opts(imloc_ransac_opts* o) {
     if (!o) return;
     memset(o, 0, sizeof(*o));

@@ -150,6 +150,23 @@ __device__ __forceinline__ SubsetRecord subset_record(const ScorePair* s, int64_
     return r;
 }
 
+// ---- bf16-packed scoring records (option score_bf16) ----------------------
+// Subset records 2k and 2k+1: world coordinates centred and scaled per query,
+// X' = (X - c) / s with s a power of two (|X'| <= 1), rounded to bf16 and
+// packed in pairs (low half = record 2k); the observed pixels negated in FP32.
+// Element 0 of the array is the query's header instead of a pair.
+struct __align__(16) ScorePairB {
+    uint32_t X2, Y2, Z2, pad;  // bf16 pairs of X', Y', Z'
+    float nx[2], ny[2];        // -observed query pixel
+};
+struct __align__(16) ScoreHeadB {
+    float c[3], s;   // centre and scale of the query's subset (bounding box of its records)
+    float e;         // bound on |X - (c + s X')| per world coordinate (bf16 and FP32 rounding)
+    float xmax, ymax;// max |x|, |y| of the observed pixels
+    float wsum;      // sum of the subset's weights
+};
+static_assert(sizeof(ScorePairB) == 32 && sizeof(ScoreHeadB) == 32, "header in the slot of one pair");
+
 // ---- packed FP32 pairs (fma/mul .f32x2: two IEEE FP32 operations per lane) --
 __device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
     uint64_t r;
@@ -184,7 +201,7 @@ struct QueryDesc {
     const int32_t* d_count; // else if non-null: off = 0, N = *d_count
     int64_t n_host;         // else off = 0, N = n_host
     int32_t q_off;
-    int32_t pad0;
+    int32_t score_bf16;     // score with the bf16-packed records (subset_b) and FP32 rescoring
     uint8_t* mask;          // optional output, same offsets as the correspondences
     imloc_result* result;   // device result slot
     // camera and options
@@ -194,7 +211,7 @@ struct QueryDesc {
     float tau2, cauchy2;
     int32_t m_cap, batch, hyps, rounds;
     int32_t lo_iters, final_iters, polish, enumerate_all;
-    int32_t lo_fp64, pad2;
+    int32_t lo_fp64, lo_solve64;  // FP64 accumulation / FP64 6x6 solve in LO and the refinement
     double p_miss;
     uint64_t seed;
     uint32_t query_id;
@@ -204,6 +221,7 @@ struct QueryDesc {
     float4* tc_rec;         // optional, tensor-core scoring: per subset record (padded to a multiple of
                             // 32) one 128-byte operand row of split TF32 pieces, 128-byte swizzled
     float4* tc_e;           // with tc_rec: per record pair {-x0, -x1, -y0, -y1}, {w0, w1, 0, 0}
+    ScorePairB* subset_b;   // option score_bf16: header + (m_cap + 1) / 2 bf16-packed record pairs
     PoseF* slots;           // wave_samples * 4
     int32_t* compact;       // wave_samples * 4 pose ids (valid poses of the wave)
     uint64_t* round_best;   // rounds: (score bits << 32) | pose id, min-reduced

@@ -426,9 +426,10 @@ enum PassMode { kLO = 0, kCountSub = 1, kFinInit = 2, kFin = 3, kCountFull = 4 }
 // conversions) sits on the critical path of every Gauss-Newton step.  FP64
 // instructions are slow on this part and cost the same for one lane as for
 // 32, so the FP64 pose arithmetic is spread over the lanes of warp 0 (one
-// output entry per lane) and the 6x6 solve runs in FP32 on a Jacobi-scaled
-// system: only the step direction depends on it, the fixed point of the
-// iteration (zero gradient, FP64 sums) does not.
+// output entry per lane) and by default the 6x6 solve runs in FP32 on a
+// Jacobi-scaled system: only the step direction depends on it, the fixed
+// point of the iteration (zero gradient, FP64 sums) does not.  The option
+// lo_fp64_solve solves the same system in FP64 from the FP64 sums.
 struct ReplaySmem {
     double R[9], t[3];    // current pose
     double Rc[9], tc[3];  // candidate pose
@@ -442,8 +443,9 @@ struct ReplaySmem {
     int32_t rhyps[kKeyCache];
     float Hf[21], gf[6];  // normal equations at the current pose (FP32 copy for the solve)
     float totf[27];
-    float dl[6];          // step of the last solve
-    float step2;          // its squared norm
+    double Hd[27];        // the same in FP64 (H upper triangle, g) for the FP64 solve
+    double dl[6];         // step of the last solve
+    double step2;         // its squared norm
     float P[12];
     int flag;
     int skip;             // rounds passed over by the last scan
@@ -639,12 +641,19 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     __syncthreads();
 }
 
+__device__ __forceinline__ float solve_rsqrt(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double solve_rsqrt(double v) { return rsqrt(v); }
+__device__ __forceinline__ float solve_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double solve_fma(double a, double b, double c) { return fma(a, b, c); }
+
 // (H + mu diag H) x = -g for the 6x6 normal equations (H packed upper
-// triangle), in FP32 after Jacobi scaling D = diag(H)^(-1/2): the scaled
-// matrix has the diagonal 1 + mu.  Cholesky with the scaled system; returns
-// false if H is not positive definite.
-__device__ __forceinline__ bool solve6f(const float Hu[21], const float g[6], float mu, float x[6], float* dn) {
-    float A[6][6], s[6];
+// triangle), after Jacobi scaling D = diag(H)^(-1/2): the scaled matrix has
+// the diagonal 1 + mu.  Cholesky of the scaled system in the precision T
+// (float: FP32 pipe; double: the FP64 solve of the option lo_fp64_solve);
+// returns false if H is not positive definite.
+template <typename T>
+__device__ __forceinline__ bool solve6(const T* Hu, const T* g, T mu, double x[6], double* dn) {
+    T A[6][6], s[6];
     int k = 0;
 #pragma unroll
     for (int a = 0; a < 6; ++a)
@@ -652,58 +661,59 @@ __device__ __forceinline__ bool solve6f(const float Hu[21], const float g[6], fl
         for (int b = a; b < 6; ++b) A[a][b] = Hu[k++];
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-        if (!(A[a][a] > 0.f)) return false;
-        s[a] = rsqrtf(A[a][a]);
+        if (!(A[a][a] > T(0))) return false;
+        s[a] = solve_rsqrt(A[a][a]);
     }
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-        A[a][a] = 1.0f + mu;
+        A[a][a] = T(1) + mu;
 #pragma unroll
         for (int b = a + 1; b < 6; ++b) {
             A[a][b] *= s[a] * s[b];
             A[b][a] = A[a][b];
         }
     }
-    float inv[6];
+    T inv[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
 #pragma unroll
         for (int j = 0; j <= i; ++j) {
-            float v = A[i][j];
+            T v = A[i][j];
 #pragma unroll
-            for (int c = 0; c < j; ++c) v = fmaf(-A[i][c], A[j][c], v);
+            for (int c = 0; c < j; ++c) v = solve_fma(-A[i][c], A[j][c], v);
             if (i == j) {
-                if (!(v > 0.f)) return false;
-                inv[i] = rsqrtf(v);
+                if (!(v > T(0))) return false;
+                inv[i] = solve_rsqrt(v);
                 A[i][i] = v * inv[i];
             } else {
                 A[i][j] = v * inv[j];
             }
         }
     }
-    float z[6];
+    T z[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        float v = -g[i] * s[i];
+        T v = -g[i] * s[i];
 #pragma unroll
-        for (int c = 0; c < i; ++c) v = fmaf(-A[i][c], z[c], v);
+        for (int c = 0; c < i; ++c) v = solve_fma(-A[i][c], z[c], v);
         z[i] = v * inv[i];
     }
-    float y[6];
+    T y[6];
 #pragma unroll
     for (int i = 5; i >= 0; --i) {
-        float v = z[i];
+        T v = z[i];
 #pragma unroll
-        for (int c = i + 1; c < 6; ++c) v = fmaf(-A[c][i], y[c], v);
+        for (int c = i + 1; c < 6; ++c) v = solve_fma(-A[c][i], y[c], v);
         y[i] = v * inv[i];
     }
-    float n2 = 0.f;
+    T n2 = T(0);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        x[i] = y[i] * s[i];
-        n2 = fmaf(x[i], x[i], n2);
+        const T xi = y[i] * s[i];
+        x[i] = static_cast<double>(xi);
+        n2 = solve_fma(xi, xi, n2);
     }
-    *dn = n2;
+    *dn = static_cast<double>(n2);
     return true;
 }
 
@@ -788,6 +798,7 @@ __device__ void orthonormalize_warp(double* R) {
 __device__ void take_totals(ReplaySmem& S) {
     for (int k = 0; k < 21; ++k) S.Hf[k] = S.totf[k];
     for (int k = 0; k < 6; ++k) S.gf[k] = S.totf[21 + k];
+    for (int k = 0; k < 27; ++k) S.Hd[k] = S.tot[k];
     S.cost = S.tot[27];
     S.cnt = S.tot[28];
 }
@@ -807,7 +818,9 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
         bool accepted = false;
         float mu = 0.f;
         for (int attempt = 0; attempt < 4; ++attempt) {
-            if (tid == 0) S.flag = solve6f(S.Hf, S.gf, mu, S.dl, &S.step2) ? 1 : 0;
+            if (tid == 0)
+                S.flag = (d.lo_solve64 ? solve6<double>(S.Hd, S.Hd + 21, static_cast<double>(mu), S.dl, &S.step2)
+                                       : solve6<float>(S.Hf, S.gf, mu, S.dl, &S.step2)) ? 1 : 0;
             __syncthreads();
             const bool solved = S.flag != 0;
             if (solved && tid < 32) apply_step_warp(S);
@@ -835,7 +848,7 @@ __device__ void gauss_newton(ReplaySmem& S, const QueryDesc& d, cg::cluster_grou
         }
         if (!accepted) break;
         // converged: a tiny step, or a step that lowered the cost by < 1e-6 of it
-        if (S.step2 < 1e-20f || S.decrease < 1e-6 * S.prev_cost) break;
+        if (S.step2 < 1e-20 || S.decrease < 1e-6 * S.prev_cost) break;
     }
 }
 
@@ -1080,6 +1093,7 @@ struct ScoreParams {
     uint32_t* work_counter;
     int32_t nq;
     int* err;
+    unsigned long long* rescored;  // bf16 scoring: (pose, record) pairs rescored in FP32 (may be null)
 };
 
 // Each CTA keeps its share of the query's subset resident in shared memory:
@@ -1307,6 +1321,353 @@ __global__ void __launch_bounds__(THREADS, FUSED ? MINB_FUSED : MINB) k_score(co
                 replay_query<float, THREADS>(S_rep, d, p.qs + q, p.wq[q], cluster, CS, rank);
             }
         }
+    }
+}
+
+// ============================================================================
+// bf16-packed scoring (option score_bf16)
+// ============================================================================
+// k_setup_bf16 (one CTA per query, after k_setup): the bounding box of the
+// subset's records (the zero-weight padding record of an odd subset
+// included) gives the centre c (its midpoint) and the scale s (the smallest
+// power of two >= its half extent), so |X'| = |X - c| / s <= 1 per
+// coordinate; X' is rounded to bf16 (relative error <= 2^-9 of |X'| <= 1).
+// Reconstruction error per world coordinate: |X - c - s bf16(fl(X - c) / s)|
+// <= 2^-24 s + 2^-9 s = e.  The header also holds max |x|, max |y| of the
+// observed pixels and the sum of the weights.
+__global__ void __launch_bounds__(512) k_setup_bf16(const QueryDesc* qd, const QueryState* qs, const int32_t* init_list) {
+    const int q = init_list ? init_list[blockIdx.x] : blockIdx.x;
+    const QueryDesc& d = qd[q];
+    if (!d.subset_b) return;
+    const int m = qs[q].m, m2 = (m + 1) >> 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float xm = 0.f, ym = 0.f, ws = 0.f;
+    for (int k2 = tid; k2 < m2; k2 += 512) {
+        const ScorePair& P = d.subset[k2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+            lo[0] = fminf(lo[0], P.X[l]); hi[0] = fmaxf(hi[0], P.X[l]);
+            lo[1] = fminf(lo[1], P.Y[l]); hi[1] = fmaxf(hi[1], P.Y[l]);
+            lo[2] = fminf(lo[2], P.Z[l]); hi[2] = fmaxf(hi[2], P.Z[l]);
+            xm = fmaxf(xm, fabsf(P.nx[l]));
+            ym = fmaxf(ym, fabsf(P.ny[l]));
+            ws += P.w[l];
+        }
+    }
+    __shared__ float s_red[16][9];
+    __shared__ ScoreHeadB s_head;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fminf(lo[a], __shfl_xor_sync(0xffffffffu, lo[a], o));
+            hi[a] = fmaxf(hi[a], __shfl_xor_sync(0xffffffffu, hi[a], o));
+        }
+        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+        ym = fmaxf(ym, __shfl_xor_sync(0xffffffffu, ym, o));
+        ws += __shfl_xor_sync(0xffffffffu, ws, o);
+    }
+    if (lane == 0) {
+        for (int a = 0; a < 3; ++a) { s_red[warp][a] = lo[a]; s_red[warp][3 + a] = hi[a]; }
+        s_red[warp][6] = xm; s_red[warp][7] = ym; s_red[warp][8] = ws;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float L[3], Hh[3], X = 0.f, Y = 0.f, W = 0.f;
+        for (int a = 0; a < 3; ++a) { L[a] = s_red[0][a]; Hh[a] = s_red[0][3 + a]; }
+        X = s_red[0][6]; Y = s_red[0][7]; W = s_red[0][8];
+        for (int w = 1; w < 16; ++w) {
+            for (int a = 0; a < 3; ++a) { L[a] = fminf(L[a], s_red[w][a]); Hh[a] = fmaxf(Hh[a], s_red[w][3 + a]); }
+            X = fmaxf(X, s_red[w][6]); Y = fmaxf(Y, s_red[w][7]); W += s_red[w][8];
+        }
+        ScoreHeadB h;
+        float half = 0.f;
+        for (int a = 0; a < 3; ++a) {
+            if (!(L[a] <= Hh[a])) { L[a] = 0.f; Hh[a] = 0.f; }  // empty subset
+            h.c[a] = 0.5f * L[a] + 0.5f * Hh[a];
+            half = fmaxf(half, fmaxf(Hh[a] - h.c[a], h.c[a] - L[a]));
+        }
+        // smallest power of two >= half (1 + 2^-16), at least 2^-40
+        float sc = 0x1p-40f;
+        while (sc < half * (1.0f + 0x1p-16f)) sc *= 2.0f;
+        h.s = sc;
+        h.e = sc * (0x1p-9f + 0x1p-23f);
+        h.xmax = X;
+        h.ymax = Y;
+        h.wsum = W;
+        s_head = h;
+        *reinterpret_cast<ScoreHeadB*>(d.subset_b) = h;
+    }
+    __syncthreads();
+    const ScoreHeadB h = s_head;
+    const float inv_s = 1.0f / h.s;  // a power of two: exact
+    for (int k2 = tid; k2 < m2; k2 += 512) {
+        const ScorePair& P = d.subset[k2];
+        ScorePairB b;
+        b.X2 = bf16_pair((P.X[0] - h.c[0]) * inv_s, (P.X[1] - h.c[0]) * inv_s);
+        b.Y2 = bf16_pair((P.Y[0] - h.c[1]) * inv_s, (P.Y[1] - h.c[1]) * inv_s);
+        b.Z2 = bf16_pair((P.Z[0] - h.c[2]) * inv_s, (P.Z[1] - h.c[2]) * inv_s);
+        b.pad = 0u;
+        b.nx[0] = P.nx[0]; b.nx[1] = P.nx[1];
+        b.ny[0] = P.ny[0]; b.ny[1] = P.ny[1];
+        d.subset_b[1 + k2] = b;
+    }
+}
+
+// k_score_bf16: the persistent, cluster-split scoring of k_score (same work
+// queue, same shares of the subset per CTA), with the shares held as
+// bf16-packed record pairs (32 B instead of 48 B) and every (pose, record)
+// pair first classified from them.  Per pose, folded with the header,
+// F = [s P_{0:3} | P (c, 1)] gives the homogeneous residual
+// d = (F_u X' - x F_z X', F_v X' - y F_z X') and depth z = F_z X'.  Against
+// the FP32 values of the same pair they differ by at most
+// A_u = (|P_u|_1 + xmax |P_z|_1) e + rho M_u..., bz = |P_z|_1 e + rho M_z
+// (e: the header's reconstruction bound, rho M: FP32 rounding of both
+// evaluations), so the pair is surely an outlier of the FP32 scoring (r >= tau)
+// if z <= -bz, or if z > bz and |d| >= tau_e (z + bz) + |A| (triangle
+// inequality; tau_e = tau plus a 1e-3 px margin).  Such a pair contributes
+// w tau^2 and no inlier; every other pair is rescored in FP32 from the FP32
+// record (global memory, L1) and the unfolded pose (shared memory) with the
+// FP32 kernel's arithmetic, so the inlier counts equal the FP32 kernel's and
+// the scores agree with them up to FP32 summation order:
+// score = tau^2 sum(w) + sum over rescored pairs of w (min(r^2, tau^2) - tau^2).
+constexpr int kBfThreads = 128, kBfHT = 4, kBfTile = kBfThreads * kBfHT;
+static_assert(kBfTile <= kMaxTileHyps && kBfTile % kScoreCluster == 0, "tile size");
+
+static size_t score_bf16_smem_bytes() {
+    return sizeof(ScorePairB) * kWinPairs + sizeof(float) * 12 * kBfTile + sizeof(float) * kBfTile +
+           sizeof(int) * kBfTile;
+}
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kBfThreads, 1) k_score_bf16(const __grid_constant__ ScoreParams p) {
+    constexpr int THREADS = kBfThreads, HT = kBfHT, TH = kBfTile;
+    extern __shared__ __align__(128) unsigned char smem[];
+    ScorePairB* buf = reinterpret_cast<ScorePairB*>(smem);
+    float* s_pose = reinterpret_cast<float*>(buf + kWinPairs);  // unfolded pose coefficient k of pose e at [k * TH + e]
+    float* s_part = s_pose + 12 * TH;
+    int* s_cnt = reinterpret_cast<int*>(s_part + TH);
+    __shared__ __align__(8) uint64_t bar[kWinChunks];
+    __shared__ int s_item;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int CS = static_cast<int>(cluster.num_blocks());
+    const int rank = static_cast<int>(cluster.block_rank());
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        for (int c = 0; c < kWinChunks; ++c) mbar_init(&bar[c], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t phases = 0u;
+    int loaded_q = -1, loaded_w0 = -1, loaded_n = -1;
+    const int total_tiles = p.tile_prefix[p.nq];
+    unsigned long long rescored = 0ull;
+    constexpr float kRho = 0x1p-20f;
+
+    for (;;) {
+        if (rank == 0 && tid == 0) s_item = static_cast<int>(atomicAdd(p.work_counter, 1u));
+        cluster.sync();
+        const int item = *cluster.map_shared_rank(&s_item, 0);
+        cluster.sync();
+        if (item >= total_tiles) break;
+        int lo = 0, hi = p.nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_prefix[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int q = lo;
+        const int tile = item - p.tile_prefix[q];
+        const QueryDesc& d = p.qd[q];
+        if (tile >= p.ntiles[q]) continue;
+        const int m = p.qs[q].m;
+        const int nh = p.n_hyp[q];
+        const int64_t slot_base = 4 * p.wq[q].s_begin;
+        const float tau2 = d.tau2;
+        const ScoreHeadB H = *reinterpret_cast<const ScoreHeadB*>(d.subset_b);
+        const float cmax = fmaxf(fabsf(H.c[0]), fmaxf(fabsf(H.c[1]), fabsf(H.c[2])));
+        const float tau_e = (sqrtf(tau2) * (1.0f + kRho) + 1e-3f + kRho * fmaxf(H.xmax, H.ymax)) * (1.0f + kRho);
+        const uint64_t TAU = f2_pack(tau_e, tau_e);
+
+        // poses: folded coefficients (packed, duplicated), the bounds, and the
+        // unfolded coefficients in shared memory for the FP32 rescoring
+        uint64_t F[HT][12], CST[HT];
+        float BZ[HT];
+#pragma unroll
+        for (int h = 0; h < HT; ++h) {
+            const int e = h * THREADS + tid;
+            const int j = tile * TH + e;
+            float c12[12];
+            if (j < nh) {
+                const int id = d.compact[j];
+                const PoseF ps = d.slots[id - slot_base];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    c12[c] = d.fx * ps.R[c] + d.cx * ps.R[6 + c];
+                    c12[4 + c] = d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c];
+                    c12[8 + c] = ps.R[6 + c];
+                }
+                c12[3] = d.fx * ps.t[0] + d.cx * ps.t[2];
+                c12[7] = d.fy * ps.t[1] + d.cy * ps.t[2];
+                c12[11] = ps.t[2];
+            } else {
+#pragma unroll
+                for (int c = 0; c < 12; ++c) c12[c] = 0.f;
+            }
+            float N[3], M[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const float* P = c12 + 4 * r;
+                N[r] = fabsf(P[0]) + fabsf(P[1]) + fabsf(P[2]);
+                M[r] = N[r] * (cmax + H.s) + fabsf(P[3]);
+                const float f3 = fmaf(P[0], H.c[0], fmaf(P[1], H.c[1], fmaf(P[2], H.c[2], P[3])));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) F[h][4 * r + k] = f2_pack(H.s * P[k], H.s * P[k]);
+                F[h][4 * r + 3] = f2_pack(f3, f3);
+            }
+            const float Au = (N[0] + H.xmax * N[2]) * H.e + kRho * (M[0] + H.xmax * M[2]);
+            const float Av = (N[1] + H.ymax * N[2]) * H.e + kRho * (M[1] + H.ymax * M[2]);
+            const float A = sqrtf(Au * Au + Av * Av) * (1.0f + kRho);
+            BZ[h] = N[2] * H.e + kRho * M[2];
+            const float cst = (tau_e * BZ[h] + A) * (1.0f + kRho);
+            CST[h] = f2_pack(cst, cst);
+#pragma unroll
+            for (int k = 0; k < 12; ++k) s_pose[k * TH + e] = c12[k];
+        }
+        __syncthreads();  // s_pose of this item (rewritten only after the next item's cluster barriers)
+
+        const int m2 = (m + 1) >> 1;
+        const int c0 = static_cast<int>(static_cast<int64_t>(m2) * rank / CS);
+        const int c1 = static_cast<int>(static_cast<int64_t>(m2) * (rank + 1) / CS);
+        const int nwin = (c1 - c0 + kWinPairs - 1) / kWinPairs;
+        float acc[HT];
+        int cnt[HT];
+#pragma unroll
+        for (int h = 0; h < HT; ++h) { acc[h] = 0.f; cnt[h] = 0; }
+
+        for (int w = 0; w < nwin; ++w) {
+            const int w0 = c0 + w * kWinPairs;
+            const int npair_w = min(kWinPairs, c1 - w0);
+            const int nch = (npair_w + kChunkPairs - 1) / kChunkPairs;
+            const bool reuse = (nwin == 1 && q == loaded_q && w0 == loaded_w0 && npair_w == loaded_n);
+            if (!reuse) {
+                if (nwin > 1) __syncthreads();
+                if (tid == 0) {
+                    for (int c = 0; c < nch; ++c) {
+                        const int np = min(kChunkPairs, npair_w - c * kChunkPairs);
+                        const uint32_t bytes = static_cast<uint32_t>(np * sizeof(ScorePairB));
+                        mbar_arrive_expect_tx(&bar[c], bytes);
+                        bulk_g2s(buf + c * kChunkPairs, d.subset_b + 1 + w0 + c * kChunkPairs, bytes, &bar[c]);
+                    }
+                }
+                if (nwin == 1) { loaded_q = q; loaded_w0 = w0; loaded_n = npair_w; }
+                else loaded_q = -1;
+            }
+            for (int c = 0; c < nch; ++c) {
+                if (!reuse) {
+                    mbar_wait_bounded(&bar[c], (phases >> c) & 1u, p.err);
+                    phases ^= (1u << c);
+                }
+                const int np = min(kChunkPairs, npair_w - c * kChunkPairs);
+                const uint4* rq = reinterpret_cast<const uint4*>(buf + c * kChunkPairs);
+                const float4* rf = reinterpret_cast<const float4*>(buf + c * kChunkPairs);
+                const float4* gsub = reinterpret_cast<const float4*>(d.subset + w0 + c * kChunkPairs);
+                for (int k = 0; k < np; ++k) {
+                    const uint4 Q = rq[2 * k];
+                    const float4 E = rf[2 * k + 1];  // -x0 -x1 -y0 -y1
+                    const uint64_t X2 = f2_pack(__uint_as_float(Q.x << 16), __uint_as_float(Q.x & 0xffff0000u));
+                    const uint64_t Y2 = f2_pack(__uint_as_float(Q.y << 16), __uint_as_float(Q.y & 0xffff0000u));
+                    const uint64_t Z2 = f2_pack(__uint_as_float(Q.z << 16), __uint_as_float(Q.z & 0xffff0000u));
+                    const uint64_t NX = f2_pack(E.x, E.y), NY = f2_pack(E.z, E.w);
+#pragma unroll
+                    for (int h = 0; h < HT; ++h) {
+                        const uint64_t zu = f2_fma(F[h][0], X2, f2_fma(F[h][1], Y2, f2_fma(F[h][2], Z2, F[h][3])));
+                        const uint64_t zv = f2_fma(F[h][4], X2, f2_fma(F[h][5], Y2, f2_fma(F[h][6], Z2, F[h][7])));
+                        const uint64_t zz = f2_fma(F[h][8], X2, f2_fma(F[h][9], Y2, f2_fma(F[h][10], Z2, F[h][11])));
+                        const uint64_t du = f2_fma(NX, zz, zu), dv = f2_fma(NY, zz, zv);
+                        const uint64_t T = f2_fma(TAU, zz, CST[h]);
+                        float z0, z1, d0, d1, t0, t1;
+                        f2_unpack(zz, z0, z1);
+                        f2_unpack(f2_fma(du, du, f2_mul(dv, dv)), d0, d1);
+                        f2_unpack(f2_mul(T, T), t0, t1);
+                        const float bz = BZ[h];
+                        const bool out0 = (z0 <= -bz) || (z0 > bz && d0 >= t0);
+                        const bool out1 = (z1 <= -bz) || (z1 > bz && d1 >= t1);
+                        if (!(out0 && out1)) {
+                            // FP32 rescoring with the FP32 kernel's arithmetic
+                            const int e = h * THREADS + tid;
+                            float P[12];
+#pragma unroll
+                            for (int a = 0; a < 12; ++a) P[a] = s_pose[a * TH + e];
+                            const float4 A4 = __ldg(gsub + 3 * k), B4 = __ldg(gsub + 3 * k + 1), E4 = __ldg(gsub + 3 * k + 2);
+#pragma unroll
+                            for (int l = 0; l < 2; ++l) {
+                                if (l == 0 ? out0 : out1) continue;
+                                const float X = l ? A4.y : A4.x, Y = l ? A4.w : A4.z, Z = l ? B4.y : B4.x;
+                                const float wl = l ? B4.w : B4.z, nx = l ? E4.y : E4.x, ny = l ? E4.w : E4.z;
+                                const float u_ = fmaf(P[0], X, fmaf(P[1], Y, fmaf(P[2], Z, P[3])));
+                                const float v_ = fmaf(P[4], X, fmaf(P[5], Y, fmaf(P[6], Z, P[7])));
+                                const float z_ = fmaf(P[8], X, fmaf(P[9], Y, fmaf(P[10], Z, P[11])));
+                                const float iz = rcp_approx(fmaxf(z_, 0.0f));
+                                const float ru = fmaf(u_, iz, nx), rv = fmaf(v_, iz, ny);
+                                const float r2 = fmaf(ru, ru, rv * rv);
+                                acc[h] = fmaf(wl, fminf(r2, tau2) - tau2, acc[h]);
+                                if (COUNT) cnt[h] += (r2 < tau2) ? 1 : 0;
+                                ++rescored;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+#pragma unroll
+        for (int h = 0; h < HT; ++h) {
+            s_part[h * THREADS + tid] = acc[h];
+            if (COUNT) s_cnt[h * THREADS + tid] = cnt[h];
+        }
+        cluster.sync();
+        const int per = TH / CS;
+        for (int e = rank * per + tid; e < (rank + 1) * per; e += THREADS) {
+            float sc = 0.f;
+            int ct = 0;
+            for (int r = 0; r < CS; ++r) {
+                sc += cluster.map_shared_rank(s_part, r)[e];
+                if (COUNT) ct += cluster.map_shared_rank(s_cnt, r)[e];
+            }
+            sc = fmaf(tau2, H.wsum, sc);
+            const int j = tile * TH + e;
+            const bool valid = j < nh;
+            uint32_t id = 0xffffffffu, rd = 0xffffffffu, sb = 0xffffffffu;
+            if (valid) {
+                id = static_cast<uint32_t>(d.compact[j]);
+                rd = static_cast<uint32_t>((id >> 2) / static_cast<uint32_t>(d.batch));
+                sb = __float_as_uint(sc);
+                if (d.score_by_id) d.score_by_id[id - slot_base] = sc;
+                if (COUNT && d.count_by_id) d.count_by_id[id - slot_base] = ct;
+            }
+            unsigned long long kv = valid ? ((static_cast<unsigned long long>(sb) << 32) | id) : ~0ull;
+            bool pending = valid;
+            while (__any_sync(0xffffffffu, pending)) {
+                const int first = __ffs(__ballot_sync(0xffffffffu, pending)) - 1;
+                const uint32_t r0 = __shfl_sync(0xffffffffu, rd, first);
+                unsigned long long v = (pending && rd == r0) ? kv : ~0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long u = __shfl_xor_sync(0xffffffffu, v, o);
+                    v = u < v ? u : v;
+                }
+                if (lane == first) atomicMin(reinterpret_cast<unsigned long long*>(&d.round_best[r0]), v);
+                if (rd == r0) pending = false;
+            }
+        }
+    }
+    if (p.rescored) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rescored += __shfl_xor_sync(0xffffffffu, rescored, o);
+        if (lane == 0 && rescored) atomicAdd(p.rescored, rescored);
     }
 }
 
@@ -1684,6 +2045,7 @@ struct HostQuery {
     int32_t* triples;
     PoseF* slots_out;
     uint64_t* round_best_out;
+    uint64_t* rescored_out;
 };
 
 
@@ -1858,6 +2220,12 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         k_setup<<<n_init * kSetupBlocks, 256, 0, stream>>>(sp);
         IMLOC_CUDA_TRY(cudaGetLastError());
         prof.end();
+        if (b.bf16) {
+            ProfScope prof2(ctx, stream, "k_setup_bf16");
+            k_setup_bf16<<<n_init, 512, 0, stream>>>(b.d_qd, b.d_qs, b.d_init);
+            IMLOC_CUDA_TRY(cudaGetLastError());
+            prof2.end();
+        }
     }
     if (total_samples > 0) {
         SampleParams sp{b.d_qd, b.d_qs, b.d_wq, b.d_prefix, b.d_nhyp, total_samples, nq};
@@ -1868,12 +2236,27 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         prof.end();
     }
     ScoreParams scp{b.d_qd,       b.d_qs,      b.d_wq, b.d_nhyp,   b.d_tiles, b.d_tiles + nq + 1, b.d_tiles + 2 * nq + 1,
-                    b.d_counter, nq,          ctx->d_err};
+                    b.d_counter, nq,          ctx->d_err, b.d_rescored};
     // the fused kernel scores and replays each query when its last item is done
     // (replays overlap the scoring of later queries: worth it with many
     // queries); otherwise the scoring runs alone, followed by the replay kernel.
-    const bool fuse = fuse_of(b.fuse);
-    if (b.tc && !fuse) {
+    const bool fuse = fuse_of(b.fuse) && !b.bf16;
+    if (b.bf16) {
+        // bf16-packed records with FP32 rescoring: the FP32 kernel's work queue and cluster split
+        rc = launch_tiles(ctx, b, nq, kBfTile, stream);
+        if (rc != IMLOC_OK) return rc;
+        auto kern = want_counts ? k_score_bf16<true> : k_score_bf16<false>;
+        const size_t smem = score_bf16_smem_bytes();
+        int n_clusters = 0;
+        rc = max_clusters(kern, kBfThreads, smem, kScoreCluster, &n_clusters);
+        if (rc != IMLOC_OK) return rc;
+        const int grid_clusters =
+            static_cast<int>(std::min<int64_t>(std::max(1, n_clusters), max_items_of(total_samples, nq, kBfTile)));
+        ProfScope prof(ctx, stream, "k_score_bf16");
+        rc = launch_cluster(kern, scp, grid_clusters * kScoreCluster, kBfThreads, smem, kScoreCluster, stream);
+        if (rc != IMLOC_OK) return rc;
+        prof.end();
+    } else if (b.tc && !fuse) {
         // projections on the tensor cores: one persistent CTA per SM
         rc = launch_tiles(ctx, b, nq, kTcPoses, stream);
         if (rc != IMLOC_OK) return rc;
@@ -2011,8 +2394,11 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     // beats the fused FP32 form (15.0 vs 16.2 ms).
     int64_t all_samples = 0;
     for (int q = 0; q < nq; ++q) all_samples += H[q];
-    const bool want_tc = score_tc_enabled(ctx, all_samples);
-    const bool dflt_fuse = nq >= 32 && !want_tc;
+    // bf16-packed scoring when every query of the call asks for it
+    bool bf16_on = true;
+    for (int q = 0; q < nq; ++q) bf16_on = bf16_on && hq[q].o.score_bf16 != 0;
+    const bool want_tc = score_tc_enabled(ctx, all_samples) && !bf16_on;
+    const bool dflt_fuse = nq >= 32 && !want_tc && !bf16_on;
     bool tc_on = want_tc && !fuse_of(dflt_fuse);
     std::vector<QueryDesc> qd(nq);
     int64_t est_hyp = 0;
@@ -2045,6 +2431,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.polish = o.p3p_fp64_polish;
         d.enumerate_all = o.enumerate_all;
         d.lo_fp64 = o.lo_fp64_accumulate;
+        d.lo_solve64 = o.lo_fp64_solve;
         d.p_miss = o.p_miss;
         d.seed = o.seed;
         d.query_id = o.query_id;
@@ -2053,6 +2440,12 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
         d.subset = static_cast<ScorePair*>(ws_alloc(ctx, sizeof(ScorePair) * ((std::max(1, o.max_score_corr) + 1) / 2)));
         d.tc_bf16 = kTcVariants[tc_variant(ctx)].bf ? 1 : 0;
+        if (bf16_on) {
+            d.score_bf16 = 1;
+            d.subset_b = static_cast<ScorePairB*>(
+                ws_alloc(ctx, sizeof(ScorePairB) * (1 + (std::max(1, o.max_score_corr) + 1) / 2)));
+            if (!d.subset_b) return IMLOC_ERR_OOM;
+        }
         if (tc_on) {
             const int64_t mp = (std::max(1, o.max_score_corr) + kTcBlock - 1) / kTcBlock * kTcBlock;
             d.tc_rec = static_cast<float4*>(ws_alloc(ctx, 128 * mp));
@@ -2125,11 +2518,14 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
     const bool use_graph = real_stream && !ctx->prof_on && (ctx->score_variant >= 0 || tc_on) && !debug &&
                            !getenv("IMLOC_NO_GRAPHS");
     std::string key;
+    bool any_fp64 = false;  // FP64-accumulation queries add a replay launch: part of the bucket key
+    for (int q = 0; q < nq; ++q) any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
     if (use_graph) {
         char buf[160];
-        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), ctx->score_variant,
+        snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%p|%p|%p|%p|%p", nq, W, int(want_counts), int(any_fp64),
+                 ctx->score_variant,
                  int(getenv("IMLOC_NO_FUSE") != nullptr) + 2 * int(getenv("IMLOC_FUSE") != nullptr),
-                 tc_on ? 1 + tc_variant(ctx) : 0,
+                 bf16_on ? -1 : (tc_on ? 1 + tc_variant(ctx) : 0),
                  (const void*)d_qd, (void*)d_qs, (void*)d_nhyp, (void*)d_tiles, (const void*)d_wq);
         key = buf;
         for (int w = 0; w < W; ++w) key += "|" + std::to_string(wtotal[w]);
@@ -2156,10 +2552,11 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         sb.d_nhyp_all = d_nhyp;
         sb.nhyp_all_len = W * nq;
         sb.d_init = nullptr;
-        sb.any_fp64 = false;
-        for (int q = 0; q < nq; ++q) sb.any_fp64 |= hq[q].o.lo_fp64_accumulate != 0;
+        sb.any_fp64 = any_fp64;
         sb.fuse = dflt_fuse;
         sb.tc = tc_on;
+        sb.bf16 = bf16_on;
+        sb.d_rescored = reinterpret_cast<unsigned long long*>(hq[0].rescored_out);
         rc = run_step(ctx, sb, nq, w == 0 ? nq : 0, wtotal[w], want_counts, stream);
         if (rc != IMLOC_OK) {
             if (capturing) {
@@ -2302,6 +2699,7 @@ int imloc_testing_ransac(imloc_ctx* ctx, const imloc_corr* corr, const imloc_cam
     h.triples = dbg->triples;
     h.slots_out = reinterpret_cast<imloc::PoseF*>(dbg->poses);
     h.round_best_out = dbg->round_best;
+    h.rescored_out = dbg->rescored_pairs;
     rc = imloc::ransac_impl(ctx, 1, &h, st, dbg->counts != nullptr);
     if (rc != IMLOC_OK) return rc;
     IMLOC_CUDA_TRY(cudaMemcpyAsync(out, d_res, sizeof(imloc_result), cudaMemcpyDeviceToHost, st));

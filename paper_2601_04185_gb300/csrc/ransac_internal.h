@@ -31,6 +31,8 @@ struct StepBuffers {
     bool any_fp64 = false;  // some query asks for FP64 accumulation in LO / refinement
     bool fuse = false;      // replay inside the scoring kernel (see run_step)
     bool tc = false;        // every query has tensor-core operand rows (QueryDesc::tc_rec)
+    bool bf16 = false;      // every query scores with bf16-packed records (QueryDesc::subset_b)
+    unsigned long long* d_rescored = nullptr;  // bf16 scoring: pairs rescored in FP32 (may be null)
 };
 
 // One step: set up n_init queries, then sample + P3P, tiles, score, replay.

@@ -62,7 +62,8 @@ class RansacOpts(C.Structure):
                 ("max_iters", C.c_int32), ("lo_iters", C.c_int32), ("p_miss", C.c_double),
                 ("final_iters", C.c_int32), ("p3p_fp64_polish", C.c_int32), ("cauchy_scale", C.c_double),
                 ("seed", C.c_uint64), ("query_id", C.c_uint32), ("enumerate_all", C.c_int32),
-                ("lo_fp64_accumulate", C.c_int32), ("reserved", C.c_int32)]
+                ("lo_fp64_accumulate", C.c_int32), ("lo_fp64_solve", C.c_int32), ("score_bf16", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -108,7 +109,8 @@ class KernelStat(C.Structure):
 
 class Debug(C.Structure):
     _fields_ = [("triples", C.c_void_p), ("poses", C.c_void_p), ("scores", C.c_void_p), ("counts", C.c_void_p),
-                ("round_best", C.c_void_p), ("inject_poses", C.c_void_p), ("n_inject", C.c_int64)]
+                ("round_best", C.c_void_p), ("inject_poses", C.c_void_p), ("n_inject", C.c_int64),
+                ("rescored_pairs", C.c_void_p)]
 
 
 # every symbol declared in include/imloc.h and include/imloc_testing.h
@@ -120,7 +122,7 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_set_scoring",
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
            "imloc_triangulate_depth_async", "imloc_retrieve_topk_async", "imloc_ransac_rig_batch",
-           "imloc_testing_rig"]
+           "imloc_testing_rig", "imloc_testing_lift_stalled"]
 
 _lib = None
 
@@ -150,6 +152,7 @@ def load(path: str = LIB_PATH):
     L.imloc_ransac_pnp_batch_async.argtypes = [V, C.c_int32, P(Corr), V, P(Camera), P(RansacOpts), V, V, V]
     L.imloc_testing_ransac.argtypes = [V, P(Corr), P(Camera), P(RansacOpts), P(Debug), P(Result), V, V]
     L.imloc_lift_noalloc_async.argtypes = [P(View), C.c_int32, P(Matches), P(Corr), V]
+    L.imloc_testing_lift_stalled.argtypes = [V, P(View), C.c_int32, P(Matches), P(Corr), C.c_int32, C.c_uint32, V]
     L.imloc_serve_default_config.argtypes = [P(ServeConfig)]
     L.imloc_serve_default_config.restype = None
     L.imloc_serve_create.argtypes = [V, P(ServeConfig), P(V)]
@@ -383,6 +386,15 @@ class Context:
                "imloc_lift_async")
         return out
 
+    def testing_lift_stalled(self, views, matches, out, skip_tiles=1, spin_limit=64, stream=None):
+        """Test hook: the lift with its first tiles never taken, so that the look-back waits end by their
+        iteration limit (imloc_testing_lift_stalled); returns the call's status."""
+        vs = _views_struct(views)
+        ms, keep = _matches_struct(matches)
+        cs = _corr_struct(out)
+        return self.lib.imloc_testing_lift_stalled(self.h, vs, len(views), C.byref(ms), C.byref(cs), int(skip_tiles),
+                                                   int(spin_limit), _stream(stream))
+
     def lift_batch(self, query_begin, views, matches, out=None, offsets=None, stream=None, prepared=None):
         torch = _torch()
         p = prepared if prepared is not None else prepare_lift_batch(query_begin, views, matches)
@@ -435,7 +447,8 @@ class Context:
         cs.count = None
         dbg = Debug(_ptr(debug.get("triples")), _ptr(debug.get("poses")), _ptr(debug.get("scores")),
                     _ptr(debug.get("counts")), _ptr(debug.get("round_best")), _ptr(debug.get("inject_poses")),
-                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0)
+                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0,
+                    _ptr(debug.get("rescored_pairs")))
         res = Result()
         _check(self.lib.imloc_testing_rig(self.h, C.byref(cs), _ptr(cam), C.byref(rg), C.byref(opts), C.byref(dbg),
                                           C.byref(res), _ptr(mask), _stream(stream)), "imloc_testing_rig")
@@ -446,7 +459,8 @@ class Context:
         cs.count = None
         dbg = Debug(_ptr(debug.get("triples")), _ptr(debug.get("poses")), _ptr(debug.get("scores")),
                     _ptr(debug.get("counts")), _ptr(debug.get("round_best")), _ptr(debug.get("inject_poses")),
-                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0)
+                    int(debug["inject_poses"].shape[0]) if debug.get("inject_poses") is not None else 0,
+                    _ptr(debug.get("rescored_pairs")))
         res = Result()
         _check(self.lib.imloc_testing_ransac(self.h, C.byref(cs), C.byref(camera(K)), C.byref(opts), C.byref(dbg),
                                              C.byref(res), _ptr(mask), _stream(stream)), "imloc_testing_ransac")

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_struct_sizes_match_the_header_layout():
-    assert C.sizeof(imloc.RansacOpts) == 72
+    assert C.sizeof(imloc.RansacOpts) == 80
     assert C.sizeof(imloc.Result) == 264
     assert C.sizeof(imloc.View) == 8 + 4 + 4 + 8 + 24 + 96 + 8
     assert C.sizeof(imloc.Corr) == 8 * 9
@@ -53,6 +53,8 @@ def test_default_options_are_the_papers_constants(lib):
     assert o.max_iters == 100000       # stop after 100K iterations (Sec. 3.3)
     assert o.p_miss == 1e-4            # or P(missing the best model) < 1e-4 (Sec. 3.3)
     assert o.tau_px == 4.0 and o.p3p_fp64_polish == 1
+    # precision options off by default: FP32 accumulation and solve, FP32 scoring coordinates
+    assert o.lo_fp64_accumulate == 0 and o.lo_fp64_solve == 0 and o.score_bf16 == 0
 
 
 def test_status_strings(lib):
@@ -74,6 +76,8 @@ def test_null_arguments_are_rejected_without_a_device(lib):
                                              None, None) == -1
     assert lib.imloc_ransac_rig_batch(None, 1, None, None, None, None, None, None, None, None) == -1
     assert lib.imloc_testing_rig(None, None, None, None, None, None, None, None, None) == -1
+    assert lib.imloc_testing_lift_stalled(None, None, 0, None, None, 1, 32, None) == -1
+    assert lib.imloc_lift_noalloc_async(None, 0, None, None, None) == -1
 
 
 def test_triangulation_defaults_are_the_papers_constants(lib):
