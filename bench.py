@@ -276,7 +276,7 @@ def run_reference(args):
 # serving: Poisson arrivals, served (continuous batching) vs plain
 # ---------------------------------------------------------------------------
 STORE_VIEWS = 1024
-SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000)
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000, 5000, 10000, 20000, 40000)
 
 
 def _gen_store_view(args):
@@ -480,8 +480,13 @@ def run_rig(dev, peaks, repeats=5, n_queries=16):
     return line
 
 
-def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
-    """Offer Poisson streams to the server and to the plain loop; returns per-rate q/s and latency percentiles."""
+def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=3.0):
+    """Offer Poisson streams to the server and to the plain loop; returns per-rate q/s and latency percentiles.
+
+    Two input forms each: matches in host memory (the server copies them into
+    its pinned ring at submission and uploads them; the plain loop uploads
+    them per query) and matches already in device memory, as a GPU matcher
+    leaves them (imloc_serve_submit_device; the plain loop lifts them in place)."""
     import queue
     import torch
 
@@ -492,28 +497,35 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
 
     prepared = [imloc.Server.prepare([dev_views[j] for j in q["view_ids"]], q["matches"], q["K"], opts_for(i))
                 for i, q in enumerate(queries)]
-    out = {"rates": list(rates), "served": [], "plain": []}
+    d_matches = []
+    for q in queries:
+        dm = {k: torch.from_numpy(np.ascontiguousarray(q["matches"][k], dtype=np.float32)).to(dev)
+              for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+        dm.update({k: q["matches"][k] for k in ("seg_off", "seg_view", "seg_dir")})
+        d_matches.append(dm)
+    prepared_dev = [imloc.Server.prepare_device([dev_views[j] for j in q["view_ids"]], d_matches[i], q["K"],
+                                                opts_for(i)) for i, q in enumerate(queries)]
+    pinned = [{k: torch.from_numpy(q["matches"][k]).pin_memory() for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+              for q in queries]
+    out = {"rates": list(rates), "served": [], "plain": [], "served_device": [], "plain_device": []}
     rng = np.random.default_rng(77)
     ctx = imloc.Context(dev.index, 512 << 20)
     srv = imloc.Server(ctx, max_slots=64, device_budget_bytes=64 << 30, host_staging_bytes=1 << 30,
                        rounds_per_step=2)
     # warm the server (autotuning, module load)
-    tk = [srv.submit_prepared(prepared[i]) for i in range(8)]
+    tk = [srv.submit_prepared(prepared[i]) for i in range(8)] + [srv.submit_prepared(prepared_dev[i]) for i in range(8)]
     while any(srv.poll(t)[0] == 1 for t in tk):
         time.sleep(0.001)
-    for lam in rates:
-        n = min(per_rate, int(lam * seconds_cap))
-        arrivals = np.cumsum(rng.exponential(1.0 / lam, n))
-        order = rng.integers(0, len(queries), n)
-        # ---- served ----
+    corr = imloc.alloc_corr(max(len(q["matches"]["q_u"]) for q in queries), dev)
+
+    def served(arrivals, order, preps):
         tickets = []
         t0 = time.perf_counter()
-        for k in range(n):
+        for k in range(len(order)):
             wait = arrivals[k] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
-            t = srv.submit_prepared(prepared[order[k]])
-            tickets.append(t)
+            tickets.append(srv.submit_prepared(preps[order[k]]))
         lats, pending = [], [t for t in tickets if t is not None]
         while pending:
             keep = []
@@ -528,15 +540,14 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
                 time.sleep(0.0005)
         elapsed = time.perf_counter() - t0
         lats.sort()
-        out["served"].append({"lambda": lam, "queries": n, "refused": sum(t is None for t in tickets),
-                              "q_per_s": len(lats) / elapsed, "p50_ms": lats[len(lats) // 2],
-                              "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))]})
-        # ---- plain: one query at a time, upload + lift + RANSAC per call ----
+        return {"queries": len(order), "refused": sum(t is None for t in tickets), "q_per_s": len(lats) / elapsed,
+                "p50_ms": lats[len(lats) // 2], "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))]}
+
+    def plain(arrivals, order, on_device):
+        # one query at a time: (upload +) lift + RANSAC per call
         qq = queue.Queue()
         lat_p = []
-        corr = imloc.alloc_corr(max(len(q["matches"]["q_u"]) for q in queries), dev)
-        pinned = [{k: torch.from_numpy(queries[i]["matches"][k]).pin_memory() for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
-                  for i in range(len(queries))] if lam == rates[0] else pinned
+
         def worker():
             stream = torch.cuda.current_stream(dev)
             while True:
@@ -546,15 +557,18 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
                 k, t_arr = item
                 i = order[k]
                 q = queries[i]
-                dm = {kk: v.to(dev, non_blocking=True) for kk, v in pinned[i].items()}
-                dm.update({kk: q["matches"][kk] for kk in ("seg_off", "seg_view", "seg_dir")})
+                if on_device:
+                    dm = d_matches[i]
+                else:
+                    dm = {kk: v.to(dev, non_blocking=True) for kk, v in pinned[i].items()}
+                    dm.update({kk: q["matches"][kk] for kk in ("seg_off", "seg_view", "seg_dir")})
                 ctx.lift([dev_views[j] for j in q["view_ids"]], dm, out=corr, stream=stream)
                 ctx.ransac_pnp(corr, q["K"], opts_for(i), stream=stream)
                 lat_p.append(1e3 * (time.perf_counter() - t_arr))
         th = threading.Thread(target=worker)
         th.start()
         t0 = time.perf_counter()
-        for k in range(n):
+        for k in range(len(order)):
             wait = arrivals[k] - (time.perf_counter() - t0)
             if wait > 0:
                 time.sleep(wait)
@@ -563,9 +577,17 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=20.0):
         th.join()
         elapsed = time.perf_counter() - t0
         lat_p.sort()
-        out["plain"].append({"lambda": lam, "queries": n, "q_per_s": len(lat_p) / elapsed,
-                             "p50_ms": lat_p[len(lat_p) // 2],
-                             "p99_ms": lat_p[min(len(lat_p) - 1, int(0.99 * len(lat_p)))]})
+        return {"queries": len(order), "q_per_s": len(lat_p) / elapsed, "p50_ms": lat_p[len(lat_p) // 2],
+                "p99_ms": lat_p[min(len(lat_p) - 1, int(0.99 * len(lat_p)))]}
+
+    for lam in rates:
+        n = min(per_rate, int(lam * seconds_cap))
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, n))
+        order = rng.integers(0, len(queries), n)
+        out["served"].append({"lambda": lam, **served(arrivals, order, prepared)})
+        out["served_device"].append({"lambda": lam, **served(arrivals, order, prepared_dev)})
+        out["plain"].append({"lambda": lam, **plain(arrivals, order, False)})
+        out["plain_device"].append({"lambda": lam, **plain(arrivals, order, True)})
     out["server_stats"] = srv.stats()
     srv.close()
     ctx.close()
@@ -928,21 +950,25 @@ def run_batched_c5(dev, store_views_dev, queries, repeats=5):
             "note": "the serving queries lifted and localized in one batched call each repetition (L2 flushed)"}
 
 
-def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
+def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False, tile4=False):
     """One lift launch over all serving queries concatenated (each query's
     matches against its own store views); algorithmic bytes / event time.
     log8: the store views as 8-bit log depth codes (the depth codec of
-    Sec. 3.3 "Data Compression", decoded inside the lift)."""
+    Sec. 3.3 "Data Compression", decoded inside the lift); tile4: the float32
+    maps in 4x4-pixel blocks of 64 bytes."""
     import torch
 
     from paper_2601_04185_gb300 import imloc
 
-    if log8:
+    if log8 or tile4:
         enc = []
         for v in store_views_dev:
-            d = dict(v)
-            d["depth"] = imloc.depth_encode_log8(v["depth"])
-            enc.append(d)
+            if tile4:
+                enc.append(imloc.tile4_view(v))
+            else:
+                d = dict(v)
+                d["depth"] = imloc.depth_encode_log8(v["depth"])
+                enc.append(d)
         torch.cuda.synchronize()
         store_views_dev = enc
 
@@ -971,7 +997,7 @@ def run_lift_batched(dev, store_views_dev, queries, repeats=10, log8=False):
     nbytes = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 64, 32))) + 28 * n_valid
     # the same count with 64-byte DRAM atoms for the random depth taps (2 x 64 B bilinear, 64 B lookup)
     nbytes64 = 20 * n + int(np.sum(np.where(dirs[conf_ok] == 0, 128, 64))) + 28 * n_valid
-    return {"depth_format": "log8" if log8 else "f32", "map_store_bytes": int(sum(v["depth"].numel() * v["depth"].element_size() for v in views)),
+    return {"depth_format": "log8" if log8 else ("f32 4x4 blocks" if tile4 else "f32"), "map_store_bytes": int(sum(v["depth"].numel() * v["depth"].element_size() for v in views)),
             "matches_per_launch": n, "valid": n_valid, "bytes_per_launch": nbytes, "launch_ms": launch_ms,
             "achieved_gbs": nbytes / (launch_ms * 1e-3) / 1e9, "store_views": len(views),
             "bytes_per_launch_64b_atoms": nbytes64, "achieved_gbs_64b_atoms": nbytes64 / (launch_ms * 1e-3) / 1e9,
@@ -1018,6 +1044,7 @@ def run_lift_only(args):
         d["depth"] = torch.from_numpy(v["depth"]).to(dev)
         dv.append(d)
     print(json.dumps({"lift_batched": run_lift_batched(dev, dv, sq, repeats=args.steps),
+                      "lift_batched_tile4": run_lift_batched(dev, dv, sq, repeats=args.steps, tile4=True),
                       "lift_batched_log8": run_lift_batched(dev, dv, sq, repeats=args.steps, log8=True)}))
     return 0
 
@@ -1318,6 +1345,14 @@ def run_ours(args):
                                  "frac": lb["achieved_gbs"] / hbm_peak, "traffic": LIFT_TRAFFIC_PER_MATCH and
                                  LIFT_TRAFFIC_PER_MATCH * lb["matches_per_launch"],
                                  "kernel": "k_lift", "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)", **lb}
+        lbt = run_lift_batched(dev, dv, sq, tile4=True)
+        line["lift_tile4"] = {"bound": "hbm", "achieved": lbt["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+                              "frac": lbt["achieved_gbs"] / hbm_peak, "launch_ms": lbt["launch_ms"],
+                              "speedup_vs_f32": lb["launch_ms"] / lbt["launch_ms"], "valid": lbt["valid"],
+                              "bytes_per_launch": lbt["bytes_per_launch"],
+                              "note": "same matches and algorithmic bytes as roofline_lift, the float32 store maps "
+                                      "in 4x4-pixel blocks of 64 B (imloc_depth_tile4_async); L2 flushed before "
+                                      "each launch"}
         lb8 = run_lift_batched(dev, dv, sq, log8=True)
         line["lift_log8"] = {"launch_ms": lb8["launch_ms"], "speedup_vs_f32": lb["launch_ms"] / lb8["launch_ms"],
                              "matches_per_s": lb8["matches_per_launch"] / (lb8["launch_ms"] * 1e-3),
@@ -1327,8 +1362,10 @@ def run_ours(args):
                                      "(Sec. 3.3 Data Compression) decoded inside k_lift; L2 flushed before each launch"}
         line["serving"] = run_serving(dev, SERVE_RATES, args.serve_per_rate, sq, dv)
         line["serving"]["batched"] = run_batched_c5(dev, dv, sq)
-        peak = max(x["q_per_s"] for x in line["serving"]["served"])
-        line["serving"]["served_peak_over_batched"] = peak / line["serving"]["batched"]["queries_per_s"]
+        bq = line["serving"]["batched"]["queries_per_s"]
+        line["serving"]["served_peak_over_batched"] = max(x["q_per_s"] for x in line["serving"]["served"]) / bq
+        line["serving"]["served_device_peak_over_batched"] = max(
+            x["q_per_s"] for x in line["serving"]["served_device"]) / bq
         line["serving"]["workload"] = (f"C5: map store of {STORE_VIEWS} views (1024x768 float32 depth, resident), "
                                        f"{len(sq)} distinct queries of 10-40 views x 5,000 matches, "
                                        "10,000 minimal sets max with the adaptive stop (p = 1e-4); Poisson arrivals")
@@ -1371,7 +1408,7 @@ def main():
     ap.add_argument("--retrieval-only", action="store_true", help="only the retrieval search measurement")
     ap.add_argument("--rig-only", action="store_true", help="only the rig-query measurement")
     ap.add_argument("--serve-queries", type=int, default=80, help="distinct serving queries")
-    ap.add_argument("--serve-per-rate", type=int, default=200, help="arrivals per offered rate")
+    ap.add_argument("--serve-per-rate", type=int, default=600, help="arrivals per offered rate (at most 3 s of arrivals)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

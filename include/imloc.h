@@ -91,7 +91,8 @@ int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_pe
  * tensor-core kernel; tc_variant -1 = default (environment IMLOC_TC_VARIANT),
  * 0 = 80-record blocks with bf16 pieces, 1 = 128-record blocks with bf16
  * pieces, 2 = 80-record blocks with TF32 pieces, 3 = 64-record blocks with
- * bf16 pieces.  The continuous-batching
+ * bf16 pieces, 4 = 160-record blocks with bf16 pieces, 5 = 96-record blocks
+ * with bf16 pieces.  The continuous-batching
  * server always uses the FP32 kernel.  IMLOC_ERR_INVALID_ARG for a null
  * context or values out of range. */
 int imloc_set_scoring(imloc_ctx* ctx, int32_t kernel, int32_t tc_variant);
@@ -103,11 +104,14 @@ typedef struct { double R[9]; double t[3]; } imloc_pose;                        
 /* Depth map formats of a view. */
 #define IMLOC_DEPTH_F32  0  /* float32 metres; <= 0 or non-finite = no depth */
 #define IMLOC_DEPTH_LOG8 1  /* 8-bit log codes of imloc_depth_encode_log8_async */
+#define IMLOC_DEPTH_F32_TILE4 2  /* float32 metres in 4x4 blocks (imloc_depth_tile4_async) */
 
 /* One database view of the image-based map (ImLoc Sec. 3.1): a depth map
  * with its intrinsics and pose.  `depth` is a device pointer to height x
  * width values of `depth_format` (float32, or one byte per pixel for
- * IMLOC_DEPTH_LOG8), row stride `pitch` elements. */
+ * IMLOC_DEPTH_LOG8), row stride `pitch` elements; for IMLOC_DEPTH_F32_TILE4
+ * the blocked layout of imloc_depth_tile4_async, `pitch` = its tile-row
+ * stride. */
 typedef struct {
     const void* depth;
     int32_t width, height;
@@ -137,6 +141,26 @@ int imloc_depth_encode_log8_async(const float* depth, int32_t width, int32_t hei
 /* codes -> float32 metres (0 for code 0), the same values the lift uses. */
 int imloc_depth_decode_log8_async(const uint8_t* codes, int32_t width, int32_t height, int64_t code_pitch,
                                   float* out, int64_t out_pitch, void* stream);
+
+/* ---- blocked float32 depth layout (a storage layout of the map store, not
+ * a step of the paper) ---------------------------------------------------
+ * The lift's bilinear fetch reads a 2x2 pixel footprint.  In a row-major
+ * float32 map it spans two rows, i.e. two DRAM atoms of 64 bytes (three when
+ * the pair of columns straddles an atom).  Stored in blocks of 4x4 pixels
+ * (64 bytes, one atom), the footprint lies in one block for 9 of 16
+ * positions: 1.56 atoms on average instead of 2.13.  Block (bx, by) holds
+ * pixels x in [4 bx, 4 bx + 4), y in [4 by, 4 by + 4) in row-major order;
+ * pixel (x, y) is element (y / 4) * tiled_pitch + (x / 4) * 16 + (y % 4) * 4
+ * + x % 4.  tiled_pitch: elements per block row, a multiple of 16 and
+ * >= 16 * ceil(width / 4); the buffer holds ceil(height / 4) * tiled_pitch
+ * floats; pixels beyond width / height are written as 0 (no depth).  Written
+ * once when a view enters the map store; views with depth_format =
+ * IMLOC_DEPTH_F32_TILE4 and pitch = tiled_pitch are lifted with the same
+ * values as the row-major map.  Device pointers, asynchronous on `stream`,
+ * no allocation, no context; IMLOC_ERR_INVALID_ARG on null pointers, sizes
+ * below 1, pitch < width or a bad tiled_pitch. */
+int imloc_depth_tile4_async(const float* depth, int32_t width, int32_t height, int64_t pitch, float* tiled,
+                            int64_t tiled_pitch, void* stream);
 
 /* ---- dense triangulation of a mapping depth map (ImLoc Sec. 3.3 "Depth
  * Estimation by Dense Matching") ------------------------------------------
@@ -417,6 +441,13 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
  * device budget. */
 int imloc_serve_submit(imloc_server* srv, const imloc_view* views, int32_t n_views, const imloc_matches* m,
                        const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket);
+/* The same with the matches already in device memory (m: DEVICE arrays on the
+ * server's device, host segments), as a GPU matcher produces them: nothing is
+ * copied at submission and the lift reads the arrays in place.  The caller
+ * keeps them valid and unchanged until the ticket's result has been polled
+ * (or the server is destroyed). */
+int imloc_serve_submit_device(imloc_server* srv, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                              const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket);
 /* IMLOC_PENDING until done; then IMLOC_OK once with the result (out->status
  * holds the query's own status) and the submit-to-ready latency in ms
  * (optional); IMLOC_ERR_NOT_FOUND for an unknown or already consumed ticket. */

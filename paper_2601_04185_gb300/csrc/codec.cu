@@ -12,6 +12,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "codec.h"
@@ -148,3 +149,34 @@ int imloc_depth_decode_log8_async(const uint8_t* codes, int32_t width, int32_t h
 }
 
 }  // extern "C"
+
+// ---- blocked float32 layout (4x4 pixels per 64-byte block) -----------------
+namespace imloc {
+namespace {
+// one thread per output element: consecutive threads write consecutive
+// elements of a block row; each group of 4 reads 4 consecutive pixels
+__global__ void __launch_bounds__(256) k_depth_tile4(const float* __restrict__ depth, int64_t pitch, int32_t W,
+                                                     int32_t H, float* __restrict__ tiled, int64_t tiled_pitch,
+                                                     int64_t total) {
+    for (int64_t o = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; o < total;
+         o += static_cast<int64_t>(gridDim.x) * 256) {
+        const int64_t by = o / tiled_pitch, r = o - by * tiled_pitch;
+        const int64_t bx = r >> 4, k = r & 15;
+        const int64_t y = 4 * by + (k >> 2), x = 4 * bx + (k & 3);
+        tiled[o] = (x < W && y < H) ? __ldg(depth + y * pitch + x) : 0.0f;
+    }
+}
+}  // namespace
+}  // namespace imloc
+
+extern "C" int imloc_depth_tile4_async(const float* depth, int32_t width, int32_t height, int64_t pitch, float* tiled,
+                                       int64_t tiled_pitch, void* stream) {
+    if (!depth || !tiled || width < 1 || height < 1 || pitch < width) return IMLOC_ERR_INVALID_ARG;
+    if (tiled_pitch % 16 != 0 || tiled_pitch < 16 * ((static_cast<int64_t>(width) + 3) / 4)) return IMLOC_ERR_INVALID_ARG;
+    const int64_t total = ((static_cast<int64_t>(height) + 3) / 4) * tiled_pitch;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    imloc::k_depth_tile4<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        depth, pitch, width, height, tiled, tiled_pitch, total);
+    IMLOC_CUDA_TRY(cudaGetLastError());
+    return IMLOC_OK;
+}

@@ -11,7 +11,9 @@
 // published counts/prefixes (decoupled look-back) with a bounded spin.
 //
 // HBM-bound: per match 20 B of match data, the depth taps (two 32-B sectors
-// for a bilinear fetch) and 28 B of output.  Views stored as 8-bit log codes
+// for a bilinear fetch) and 28 B of output.  Float32 maps may also be stored
+// in 4x4-pixel blocks of 64 bytes (one DRAM atom), so that most bilinear
+// footprints fall in one atom.  Views stored as 8-bit log codes
 // (the depth codec of Sec. 3.3 "Data Compression") are decoded in the fetch
 // through a 256-entry table in shared memory: one byte per tap and a map
 // store a quarter of the float32 size (which then mostly stays in L2).
@@ -75,6 +77,13 @@ struct LiftParams {
 };
 
 __device__ __forceinline__ bool depth_ok(float d) { return d > 0.0f && d < INFINITY; }
+
+// element offset of pixel (x, y) in the view's map: row-major, or 4x4 blocks
+__device__ __forceinline__ int64_t tap_offset(const LiftView& V, int x, int y) {
+    if (V.fmt == IMLOC_DEPTH_F32_TILE4)
+        return static_cast<int64_t>(y >> 2) * V.pitch + ((x >> 2) << 4) + ((y & 3) << 2) + (x & 3);
+    return static_cast<int64_t>(y) * V.pitch + x;
+}
 
 // depth tap at element offset `off` of the view's map (metres; 0 = no depth for codes)
 __device__ __forceinline__ float depth_tap(const LiftView& V, int64_t off, const float* lut) {
@@ -172,15 +181,14 @@ __global__ void __launch_bounds__(kLiftThreads, 4) k_lift(const __grid_constant_
             if (!((a >= 0.0f) && (a < static_cast<float>(V.W - 1)) && (b >= 0.0f) && (b < static_cast<float>(V.H - 1))))
                 continue;
             const int i0 = static_cast<int>(a), j0 = static_cast<int>(b);
-            const int64_t o0 = static_cast<int64_t>(j0) * V.pitch + i0, o1 = o0 + V.pitch;
-            t00[k] = depth_tap(V, o0, s_lut);
-            t01[k] = depth_tap(V, o0 + 1, s_lut);
-            t10[k] = depth_tap(V, o1, s_lut);
-            t11[k] = depth_tap(V, o1 + 1, s_lut);
+            t00[k] = depth_tap(V, tap_offset(V, i0, j0), s_lut);
+            t01[k] = depth_tap(V, tap_offset(V, i0 + 1, j0), s_lut);
+            t10[k] = depth_tap(V, tap_offset(V, i0, j0 + 1), s_lut);
+            t11[k] = depth_tap(V, tap_offset(V, i0 + 1, j0 + 1), s_lut);
         } else {
             if (!((u >= 0.0f) && (u < static_cast<float>(V.W)) && (v >= 0.0f) && (v < static_cast<float>(V.H))))
                 continue;
-            t00[k] = depth_tap(V, static_cast<int64_t>(static_cast<int>(v)) * V.pitch + static_cast<int>(u), s_lut);
+            t00[k] = depth_tap(V, tap_offset(V, static_cast<int>(u), static_cast<int>(v)), s_lut);
         }
         want[k] = true;
     }
@@ -333,7 +341,11 @@ static int check_lift_args(const imloc_view* views, int32_t n_views, const imloc
         const imloc_view& V = views[v];
         if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
         if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
-        if (V.depth_format != IMLOC_DEPTH_F32 && V.depth_format != IMLOC_DEPTH_LOG8) return IMLOC_ERR_INVALID_ARG;
+        if (V.depth_format != IMLOC_DEPTH_F32 && V.depth_format != IMLOC_DEPTH_LOG8 &&
+            V.depth_format != IMLOC_DEPTH_F32_TILE4)
+            return IMLOC_ERR_INVALID_ARG;
+        if (V.depth_format == IMLOC_DEPTH_F32_TILE4 && (V.pitch % 16 != 0 || V.pitch < 16 * ((V.width + 3) / 4)))
+            return IMLOC_ERR_INVALID_ARG;
     }
     return IMLOC_OK;
 }

@@ -14,6 +14,14 @@
 //      rounds share the launches;
 //   4. finished queries hand their result to the ticket table and free their
 //      slot and memory.
+// Steps are pipelined two deep on the server's stream: the scheduler
+// enqueues step k+1 (uploads, lifts, launches, the read-back of the query
+// states) before it waits for step k's event and retires step k's finished
+// queries, so the GPU runs step k+1 while the host retires, admits and
+// marshals.  A query that finished in step k is still part of step k+1,
+// whose kernels skip it (its state is done).  The host blocks of a step
+// (descriptors, round plan, states, results) are double-buffered pinned
+// memory, and each step remembers which query sat in which slot.
 // A query that arrives while others are on the GPU joins at the next step.
 #include <stdio.h>
 #include <string.h>
@@ -90,6 +98,8 @@ struct ServeQuery {
     imloc_camera cam{};
     imloc_ransac_opts opts{};
     size_t ring_off = 0, ring_size = 0, ring_waste = 0;
+    const float* dmatch[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // device-submitted matches (caller's)
+    bool on_device = false;
     double t_submit = 0.0;
     size_t footprint = 0;
     // resident
@@ -103,7 +113,7 @@ struct Layout {
     size_t match[5], cx, cy, cX, cY, cZ, cw, csrc, ccount, fixidx, subset, slots, compact, round_best, round_hyps, total;
 };
 
-static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t rounds) {
+static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t rounds, bool with_matches = true) {
     Layout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -111,7 +121,7 @@ static Layout layout_of(int64_t n, int32_t m_cap, int64_t step_samples, int64_t 
         o = align_up(o + std::max<size_t>(bytes, 1), 256);
         return at;
     };
-    for (int k = 0; k < 5; ++k) L.match[k] = take(sizeof(float) * n);
+    for (int k = 0; k < 5; ++k) L.match[k] = with_matches ? take(sizeof(float) * n) : 0;
     L.cx = take(sizeof(float) * n);
     L.cy = take(sizeof(float) * n);
     L.cX = take(sizeof(float) * n);
@@ -152,12 +162,19 @@ struct imloc_server {
     uint32_t* d_counter = nullptr;
     int32_t* d_init = nullptr;
     imloc_result* d_res = nullptr;
-    imloc::QueryDesc* h_qd = nullptr;
-    imloc::WaveQ* h_wq = nullptr;
-    int64_t* h_prefix = nullptr;
-    int32_t* h_init = nullptr;
-    imloc::QueryState* h_qs = nullptr;
-    imloc_result* h_res = nullptr;
+    // host side: the descriptors of every slot, and per step parity the pinned
+    // copies the step's transfers read or write, its completion event and its
+    // slot occupants
+    std::vector<imloc::QueryDesc> qd_master;
+    imloc::QueryDesc* h_qd[2] = {nullptr, nullptr};
+    imloc::WaveQ* h_wq[2] = {nullptr, nullptr};
+    int64_t* h_prefix[2] = {nullptr, nullptr};
+    int32_t* h_init[2] = {nullptr, nullptr};
+    imloc::QueryState* h_qs[2] = {nullptr, nullptr};
+    imloc_result* h_res[2] = {nullptr, nullptr};
+    cudaEvent_t step_done[2] = {nullptr, nullptr};
+    std::vector<ServeQuery*> occ[2];
+    std::vector<ServeQuery*> step_admitted[2];
     // pinned FIFO ring holding submitted matches until their upload
     char* ring = nullptr;
     size_t ring_bytes = 0, ring_head = 0, ring_tail = 0, ring_used = 0;
@@ -213,7 +230,7 @@ static void ring_release(imloc_server* S, ServeQuery* q) {
 
 static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     char* base = S->pool + q->pool_off;
-    QueryDesc& d = S->h_qd[q->slot];
+    QueryDesc& d = S->qd_master[q->slot];
     memset(&d, 0, sizeof(d));
     d.x = reinterpret_cast<float*>(base + L.cx);
     d.y = reinterpret_cast<float*>(base + L.cy);
@@ -245,6 +262,7 @@ static void fill_desc(imloc_server* S, ServeQuery* q, const Layout& L) {
     d.polish = o.p3p_fp64_polish;
     d.enumerate_all = 0;
     d.lo_fp64 = o.lo_fp64_accumulate;
+    d.lo_solve64 = o.lo_fp64_solve;
     d.p_miss = o.p_miss;
     d.seed = o.seed;
     d.query_id = o.query_id;
@@ -271,42 +289,58 @@ static void fail_all(imloc_server* S, int status) {
     S->live.clear();
 }
 
-// One scheduler step; returns false when the worker should stop.
-static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted) {
+// Enqueue one scheduler step with host buffers of parity p: newly admitted
+// queries (upload, lift, descriptors), then every resident query's next
+// rounds in one merged launch sequence, then the read-back of the query
+// states and results; records the step's event.  Does not wait for the GPU.
+static int enqueue_step(imloc_server* S, const std::vector<ServeQuery*>& admitted, int p) {
     cudaStream_t st = S->stream;
     const int ns = S->cfg.max_slots;
-    // newly admitted: upload matches, lift, descriptors
+    // one call on the lift context per step: its staging buffer and workspace
+    // hold the tables of every newly admitted query
+    if (!admitted.empty()) {
+        int rc = begin_call(S->ictx, st);
+        if (rc != IMLOC_OK) return rc;
+    }
     for (ServeQuery* q : admitted) {
         const int64_t m_cap = q->opts.max_score_corr;
-        const Layout L = layout_of(q->n, static_cast<int32_t>(m_cap), step_samples(S->cfg, q->B), q->R);
+        const Layout L = layout_of(q->n, static_cast<int32_t>(m_cap), step_samples(S->cfg, q->B), q->R, !q->on_device);
         char* base = S->pool + q->pool_off;
-        float* dm[5];
+        const float* dm[5];
         for (int k = 0; k < 5; ++k) {
-            dm[k] = reinterpret_cast<float*>(base + L.match[k]);
-            IMLOC_CUDA_TRY(cudaMemcpyAsync(dm[k], S->ring + q->ring_off + k * sizeof(float) * q->n,
+            if (q->on_device) {
+                dm[k] = q->dmatch[k];  // the lift reads the caller's device arrays
+                continue;
+            }
+            float* dst = reinterpret_cast<float*>(base + L.match[k]);
+            IMLOC_CUDA_TRY(cudaMemcpyAsync(dst, S->ring + q->ring_off + k * sizeof(float) * q->n,
                                            sizeof(float) * q->n, cudaMemcpyHostToDevice, st));
+            dm[k] = dst;
         }
         imloc_matches m{dm[0], dm[1], dm[2], dm[3], dm[4], q->n, q->segs.data(), static_cast<int32_t>(q->segs.size())};
         imloc_corr c{reinterpret_cast<float*>(base + L.cx), reinterpret_cast<float*>(base + L.cy),
                      reinterpret_cast<float*>(base + L.cX), reinterpret_cast<float*>(base + L.cY),
                      reinterpret_cast<float*>(base + L.cZ), reinterpret_cast<float*>(base + L.cw),
                      reinterpret_cast<int32_t*>(base + L.csrc), reinterpret_cast<int32_t*>(base + L.ccount), q->n};
-        int rc = begin_call(S->ictx, st);
-        if (rc != IMLOC_OK) return rc;
         const int64_t qb[2] = {0, q->n};
-        rc = lift_impl(S->ictx, 1, qb, q->views.data(), static_cast<int32_t>(q->views.size()), &m, &c, nullptr, st);
+        int rc = lift_impl(S->ictx, 1, qb, q->views.data(), static_cast<int32_t>(q->views.size()), &m, &c, nullptr, st);
         if (rc != IMLOC_OK) return rc;
         fill_desc(S, q, L);
     }
+    if (!admitted.empty()) {
+        int rc = end_call(S->ictx, st);
+        if (rc != IMLOC_OK) return rc;
+    }
     int n_init = 0;
-    for (ServeQuery* q : admitted) S->h_init[n_init++] = q->slot;
+    for (ServeQuery* q : admitted) S->h_init[p][n_init++] = q->slot;
     // rounds of this step per resident query
     int64_t total = 0;
     for (int s = 0; s < ns; ++s) {
         ServeQuery* q = S->slots[s];
-        WaveQ& w = S->h_wq[s];
+        S->occ[p][s] = q;
+        WaveQ& w = S->h_wq[p][s];
         memset(&w, 0, sizeof(w));
-        S->h_prefix[s] = total;
+        S->h_prefix[p][s] = total;
         if (!q) continue;
         const int64_t r0 = q->r_next;
         const int64_t r1 = std::min<int64_t>(q->R, r0 + (r0 == 0 ? 1 : std::max(1, S->cfg.rounds_per_step)));
@@ -318,13 +352,14 @@ static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted)
         total += se - sb;
         q->r_next = r1;
     }
-    S->h_prefix[ns] = total;
+    S->h_prefix[p][ns] = total;
     if (!admitted.empty()) {
-        IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_qd, S->h_qd, sizeof(QueryDesc) * ns, cudaMemcpyHostToDevice, st));
-        IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_init, S->h_init, sizeof(int32_t) * n_init, cudaMemcpyHostToDevice, st));
+        memcpy(S->h_qd[p], S->qd_master.data(), sizeof(QueryDesc) * ns);
+        IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_qd, S->h_qd[p], sizeof(QueryDesc) * ns, cudaMemcpyHostToDevice, st));
+        IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_init, S->h_init[p], sizeof(int32_t) * n_init, cudaMemcpyHostToDevice, st));
     }
-    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_wq, S->h_wq, sizeof(WaveQ) * ns, cudaMemcpyHostToDevice, st));
-    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_prefix, S->h_prefix, sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st));
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_wq, S->h_wq[p], sizeof(WaveQ) * ns, cudaMemcpyHostToDevice, st));
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->d_prefix, S->h_prefix[p], sizeof(int64_t) * (ns + 1), cudaMemcpyHostToDevice, st));
     IMLOC_CUDA_TRY(cudaMemsetAsync(S->d_nhyp, 0, sizeof(int32_t) * ns, st));
     StepBuffers b;
     b.d_qd = S->d_qd;
@@ -343,17 +378,28 @@ static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted)
         if (S->slots[s] && S->slots[s]->opts.lo_fp64_accumulate) b.any_fp64 = true;
     int rc = run_step(S->ictx, b, ns, n_init, total, false, st);
     if (rc != IMLOC_OK) return rc;
-    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->h_qs, S->d_qs, sizeof(QueryState) * ns, cudaMemcpyDeviceToHost, st));
-    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->h_res, S->d_res, sizeof(imloc_result) * ns, cudaMemcpyDeviceToHost, st));
-    IMLOC_CUDA_TRY(cudaStreamSynchronize(st));
-    // retire finished queries
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->h_qs[p], S->d_qs, sizeof(QueryState) * ns, cudaMemcpyDeviceToHost, st));
+    IMLOC_CUDA_TRY(cudaMemcpyAsync(S->h_res[p], S->d_res, sizeof(imloc_result) * ns, cudaMemcpyDeviceToHost, st));
+    IMLOC_CUDA_TRY(cudaEventRecord(S->step_done[p], st));
+    S->step_admitted[p] = admitted;
+    return IMLOC_OK;
+}
+
+// Wait for the step of parity p and retire its finished queries (only those
+// still in the slot they held during that step).
+static int retire_step(imloc_server* S, int p) {
+    IMLOC_CUDA_TRY(cudaEventSynchronize(S->step_done[p]));
+    const int ns = S->cfg.max_slots;
     const double t = now_ms();
     std::lock_guard<std::mutex> lk(S->mu);
-    for (ServeQuery* q : admitted) ring_release(S, q);
+    for (ServeQuery* q : S->step_admitted[p])
+        if (!q->on_device) ring_release(S, q);
+    S->step_admitted[p].clear();
     for (int s = 0; s < ns; ++s) {
-        ServeQuery* q = S->slots[s];
-        if (!q || !S->h_qs[s].finished) continue;
-        S->done[q->ticket] = {S->h_res[s], t - q->t_submit};
+        ServeQuery* q = S->occ[p][s];
+        S->occ[p][s] = nullptr;
+        if (!q || S->slots[s] != q || !S->h_qs[p][s].finished) continue;
+        S->done[q->ticket] = {S->h_res[p][s], t - q->t_submit};
         S->live.erase(q->ticket);
         S->pool_alloc.release(q->pool_off, q->footprint);
         S->slots[s] = nullptr;
@@ -368,8 +414,11 @@ static int serve_step(imloc_server* S, const std::vector<ServeQuery*>& admitted)
 
 static void worker_main(imloc_server* S) {
     cudaSetDevice(S->device);
+    int p = 0;               // parity of the next step to enqueue
+    bool in_flight = false;  // a step of parity p ^ 1 is enqueued and not yet retired
     for (;;) {
         std::vector<ServeQuery*> admitted;
+        bool any_resident;
         {
             std::unique_lock<std::mutex> lk(S->mu);
             if (S->stop) break;
@@ -392,17 +441,34 @@ static void worker_main(imloc_server* S) {
                 S->stats.resident++;
                 admitted.push_back(q);
             }
-            if (admitted.empty() && S->stats.resident == 0) {
+            any_resident = S->stats.resident > 0;
+            if (!any_resident && !in_flight) {
                 S->cv.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
             }
         }
-        const int rc = serve_step(S, admitted);
-        if (rc != IMLOC_OK) {
-            fail_all(S, rc);
-            break;
+        // the next step goes onto the stream before the previous one is retired
+        bool enqueued = false;
+        if (any_resident) {
+            const int rc = enqueue_step(S, admitted, p);
+            if (rc != IMLOC_OK) {
+                fail_all(S, rc);
+                break;
+            }
+            enqueued = true;
         }
+        if (in_flight) {
+            const int rc = retire_step(S, p ^ 1);
+            if (rc != IMLOC_OK) {
+                fail_all(S, rc);
+                break;
+            }
+        }
+        in_flight = enqueued;
+        if (enqueued) p ^= 1;
     }
+    // the last enqueued step completes before the server's memory goes away
+    if (in_flight) cudaEventSynchronize(S->step_done[p ^ 1]);
 }
 
 }  // namespace imloc
@@ -443,12 +509,16 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
     ok = ok && cudaMalloc(&S->d_counter, sizeof(uint32_t)) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_init, sizeof(int32_t) * ns) == cudaSuccess;
     ok = ok && cudaMalloc(&S->d_res, sizeof(imloc_result) * ns) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_qd, sizeof(imloc::QueryDesc) * ns) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_wq, sizeof(imloc::WaveQ) * ns) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_prefix, sizeof(int64_t) * (ns + 1)) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_init, sizeof(int32_t) * ns) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_qs, sizeof(imloc::QueryState) * ns) == cudaSuccess;
-    ok = ok && cudaMallocHost(&S->h_res, sizeof(imloc_result) * ns) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && cudaMallocHost(&S->h_qd[k], sizeof(imloc::QueryDesc) * ns) == cudaSuccess;
+        ok = ok && cudaMallocHost(&S->h_wq[k], sizeof(imloc::WaveQ) * ns) == cudaSuccess;
+        ok = ok && cudaMallocHost(&S->h_prefix[k], sizeof(int64_t) * (ns + 1)) == cudaSuccess;
+        ok = ok && cudaMallocHost(&S->h_init[k], sizeof(int32_t) * ns) == cudaSuccess;
+        ok = ok && cudaMallocHost(&S->h_qs[k], sizeof(imloc::QueryState) * ns) == cudaSuccess;
+        ok = ok && cudaMallocHost(&S->h_res[k], sizeof(imloc_result) * ns) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&S->step_done[k], cudaEventDisableTiming) == cudaSuccess;
+        S->occ[k].assign(ns, nullptr);
+    }
     ok = ok && cudaMallocHost(&S->ring, cfg->host_staging_bytes) == cudaSuccess;
     if (!ok) {
         imloc_serve_destroy(S);
@@ -457,15 +527,16 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
     S->ring_bytes = cfg->host_staging_bytes;
     S->pool_alloc.reset(cfg->device_budget_bytes);
     S->slots.assign(ns, nullptr);
-    memset(S->h_qd, 0, sizeof(imloc::QueryDesc) * ns);
+    S->qd_master.assign(ns, imloc::QueryDesc());
+    memset(S->qd_master.data(), 0, sizeof(imloc::QueryDesc) * ns);
     // every slot starts finished: the kernels skip it until a query is set up there
     for (int s = 0; s < ns; ++s) {
-        memset(&S->h_qs[s], 0, sizeof(imloc::QueryState));
-        S->h_qs[s].done = 1;
-        S->h_qs[s].finished = 1;
+        memset(&S->h_qs[0][s], 0, sizeof(imloc::QueryState));
+        S->h_qs[0][s].done = 1;
+        S->h_qs[0][s].finished = 1;
     }
-    if (cudaMemcpy(S->d_qs, S->h_qs, sizeof(imloc::QueryState) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(S->d_qd, S->h_qd, sizeof(imloc::QueryDesc) * ns, cudaMemcpyHostToDevice) != cudaSuccess) {
+    if (cudaMemcpy(S->d_qs, S->h_qs[0], sizeof(imloc::QueryState) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(S->d_qd, S->qd_master.data(), sizeof(imloc::QueryDesc) * ns, cudaMemcpyHostToDevice) != cudaSuccess) {
         imloc_serve_destroy(S);
         return IMLOC_ERR_CUDA;
     }
@@ -474,8 +545,12 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
     return IMLOC_OK;
 }
 
-int imloc_serve_submit(imloc_server* S, const imloc_view* views, int32_t n_views, const imloc_matches* m,
-                       const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket) {
+}  // extern "C"
+
+namespace imloc {
+
+static int serve_submit_impl(imloc_server* S, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                             const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket, bool on_device) {
     if (!S || !views || n_views <= 0 || !m || !qcam || !opts || !ticket) return IMLOC_ERR_INVALID_ARG;
     if (m->n < 0 || m->n >= (int64_t(1) << 31) || (m->n > 0 && (!m->q_u || !m->q_v || !m->db_u || !m->db_v || !m->conf)))
         return IMLOC_ERR_INVALID_ARG;
@@ -498,7 +573,11 @@ int imloc_serve_submit(imloc_server* S, const imloc_view* views, int32_t n_views
     q->H = opts->max_iters;
     q->B = opts->batch;
     q->R = (q->H + q->B - 1) / q->B;
-    q->footprint = imloc::layout_of(q->n, opts->max_score_corr, imloc::step_samples(S->cfg, q->B), q->R).total;
+    q->on_device = on_device;
+    q->footprint = layout_of(q->n, opts->max_score_corr, step_samples(S->cfg, q->B), q->R, !on_device).total;
+    const float* src[5] = {m->q_u, m->q_v, m->db_u, m->db_v, m->conf};
+    if (on_device)
+        for (int k = 0; k < 5; ++k) q->dmatch[k] = src[k];
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->worker_error != IMLOC_OK || S->stop) {
         delete q;
@@ -506,16 +585,16 @@ int imloc_serve_submit(imloc_server* S, const imloc_view* views, int32_t n_views
     }
     // never admissible, queue full, or no room in the staging ring: refused
     if (q->footprint > S->cfg.device_budget_bytes || static_cast<int>(S->pending.size()) >= S->cfg.max_queue ||
-        !imloc::ring_alloc(S, sizeof(float) * 5 * static_cast<size_t>(q->n), q)) {
+        (!on_device && !ring_alloc(S, sizeof(float) * 5 * static_cast<size_t>(q->n), q))) {
         S->stats.rejected++;
         delete q;
         return IMLOC_ERR_REJECTED;
     }
-    const float* src[5] = {m->q_u, m->q_v, m->db_u, m->db_v, m->conf};
-    for (int k = 0; k < 5; ++k)
-        if (q->n) memcpy(S->ring + q->ring_off + k * sizeof(float) * q->n, src[k], sizeof(float) * q->n);
+    if (!on_device)
+        for (int k = 0; k < 5; ++k)
+            if (q->n) memcpy(S->ring + q->ring_off + k * sizeof(float) * q->n, src[k], sizeof(float) * q->n);
     q->ticket = S->next_ticket++;
-    q->t_submit = imloc::now_ms();
+    q->t_submit = now_ms();
     S->pending.push_back(q);
     S->live[q->ticket] = 1;
     S->stats.submitted++;
@@ -523,6 +602,20 @@ int imloc_serve_submit(imloc_server* S, const imloc_view* views, int32_t n_views
     *ticket = q->ticket;
     S->cv.notify_one();
     return IMLOC_OK;
+}
+
+}  // namespace imloc
+
+extern "C" {
+
+int imloc_serve_submit(imloc_server* S, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                       const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket) {
+    return imloc::serve_submit_impl(S, views, n_views, m, qcam, opts, ticket, false);
+}
+
+int imloc_serve_submit_device(imloc_server* S, const imloc_view* views, int32_t n_views, const imloc_matches* m,
+                              const imloc_camera* qcam, const imloc_ransac_opts* opts, uint64_t* ticket) {
+    return imloc::serve_submit_impl(S, views, n_views, m, qcam, opts, ticket, true);
 }
 
 int imloc_serve_poll(imloc_server* S, uint64_t ticket, imloc_result* out, double* latency_ms) {
@@ -560,8 +653,12 @@ int imloc_serve_destroy(imloc_server* S) {
     cudaFree(S->pool);
     cudaFree(S->d_qd); cudaFree(S->d_qs); cudaFree(S->d_wq); cudaFree(S->d_prefix); cudaFree(S->d_nhyp);
     cudaFree(S->d_tiles); cudaFree(S->d_counter); cudaFree(S->d_init); cudaFree(S->d_res);
-    cudaFreeHost(S->h_qd); cudaFreeHost(S->h_wq); cudaFreeHost(S->h_prefix); cudaFreeHost(S->h_init);
-    cudaFreeHost(S->h_qs); cudaFreeHost(S->h_res); cudaFreeHost(S->ring);
+    for (int k = 0; k < 2; ++k) {
+        cudaFreeHost(S->h_qd[k]); cudaFreeHost(S->h_wq[k]); cudaFreeHost(S->h_prefix[k]); cudaFreeHost(S->h_init[k]);
+        cudaFreeHost(S->h_qs[k]); cudaFreeHost(S->h_res[k]);
+        if (S->step_done[k]) cudaEventDestroy(S->step_done[k]);
+    }
+    cudaFreeHost(S->ring);
     if (S->stream) cudaStreamDestroy(S->stream);
     if (S->ictx) imloc_destroy(S->ictx);
     delete S;

@@ -30,7 +30,7 @@ class Pose(C.Structure):
     _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
 
 
-DEPTH_F32, DEPTH_LOG8 = 0, 1
+DEPTH_F32, DEPTH_LOG8, DEPTH_F32_TILE4 = 0, 1, 2
 
 
 class View(C.Structure):
@@ -122,7 +122,8 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_set_scoring",
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
            "imloc_triangulate_depth_async", "imloc_retrieve_topk_async", "imloc_ransac_rig_batch",
-           "imloc_testing_rig", "imloc_testing_lift_stalled"]
+           "imloc_testing_rig", "imloc_testing_lift_stalled", "imloc_serve_submit_device",
+           "imloc_depth_tile4_async"]
 
 _lib = None
 
@@ -157,6 +158,8 @@ def load(path: str = LIB_PATH):
     L.imloc_serve_default_config.restype = None
     L.imloc_serve_create.argtypes = [V, P(ServeConfig), P(V)]
     L.imloc_serve_submit.argtypes = [V, P(View), C.c_int32, P(Matches), P(Camera), P(RansacOpts), P(C.c_uint64)]
+    L.imloc_serve_submit_device.argtypes = [V, P(View), C.c_int32, P(Matches), P(Camera), P(RansacOpts),
+                                            P(C.c_uint64)]
     L.imloc_serve_poll.argtypes = [V, C.c_uint64, P(Result), P(C.c_double)]
     L.imloc_serve_read_stats.argtypes = [V, P(ServeStats)]
     L.imloc_serve_destroy.argtypes = [V]
@@ -173,6 +176,7 @@ def load(path: str = LIB_PATH):
     L.imloc_testing_rig.argtypes = [V, P(Corr), V, P(Rig), P(RansacOpts), P(Debug), P(Result), V, V]
     L.imloc_depth_encode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     L.imloc_depth_decode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
+    L.imloc_depth_tile4_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     _lib = L
     return L
 
@@ -259,14 +263,19 @@ def _views_struct(views):
     for i, v in enumerate(views):
         d = v["depth"]
         arr[i].depth = d.data_ptr()
-        arr[i].height, arr[i].width = int(d.shape[0]), int(d.shape[1])
         arr[i].pitch = int(d.stride(0))
-        arr[i].cam = Camera(float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"]), int(d.shape[1]),
-                            int(d.shape[0]))
+        if v.get("layout") == "tile4":
+            # 4x4-blocked float32 map (depth_tile4): rows of blocks, the image size given with the view
+            H, W = int(v["height"]), int(v["width"])
+            arr[i].depth_format = DEPTH_F32_TILE4
+        else:
+            H, W = int(d.shape[0]), int(d.shape[1])
+            # uint8 maps hold 8-bit log codes (depth_encode_log8), float32 maps metres
+            arr[i].depth_format = DEPTH_LOG8 if d.element_size() == 1 else DEPTH_F32
+        arr[i].height, arr[i].width = H, W
+        arr[i].cam = Camera(float(v["fx"]), float(v["fy"]), float(v["cx"]), float(v["cy"]), W, H)
         arr[i].pose.R[:] = [float(a) for a in np.asarray(v["R"], dtype=np.float64).ravel()]
         arr[i].pose.t[:] = [float(a) for a in np.asarray(v["t"], dtype=np.float64).ravel()]
-        # uint8 maps hold 8-bit log codes (depth_encode_log8), float32 maps metres
-        arr[i].depth_format = DEPTH_LOG8 if d.element_size() == 1 else DEPTH_F32
     return arr
 
 
@@ -497,18 +506,27 @@ class Server:
         ms = Matches(*[a.ctypes.data for a in arrs], n, segs, n_seg)
         return Prepared(vs=vs, n_views=len(views), ms=ms, keep=(arrs, segs, views), cam=camera(K), opts=opts)
 
+    def submit(self, views, matches, K, opts):
+        return self.submit_prepared(self.prepare(views, matches, K, opts))
+
+    @staticmethod
+    def prepare_device(views, matches, K, opts):
+        """Marshal one query whose matches are cuda float32 tensors (kept alive by the returned object,
+        which must outlive the query's result)."""
+        vs = _views_struct(views)
+        ms, segs = _matches_struct(matches)
+        return Prepared(vs=vs, n_views=len(views), ms=ms, keep=(matches, segs, views), cam=camera(K), opts=opts,
+                        device=True)
+
     def submit_prepared(self, p):
         """Returns the ticket, or None when the server refuses the query."""
         t = C.c_uint64(0)
-        rc = self.lib.imloc_serve_submit(self.h, p.vs, p.n_views, C.byref(p.ms), C.byref(p.cam), C.byref(p.opts),
-                                         C.byref(t))
+        fn = self.lib.imloc_serve_submit_device if getattr(p, "device", False) else self.lib.imloc_serve_submit
+        rc = fn(self.h, p.vs, p.n_views, C.byref(p.ms), C.byref(p.cam), C.byref(p.opts), C.byref(t))
         if rc == -3:
             return None
         _check(rc, "imloc_serve_submit")
         return t.value
-
-    def submit(self, views, matches, K, opts):
-        return self.submit_prepared(self.prepare(views, matches, K, opts))
 
     def poll(self, ticket):
         """(status, result dict or None, latency ms or None); status 1 = pending, -6 = unknown ticket."""
@@ -568,6 +586,29 @@ def depth_encode_log8(depth, out=None, stream=None):
                                                 C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
            "imloc_depth_encode_log8_async")
     return out
+
+
+def depth_tile4(depth, stream=None):
+    """float32 CUDA tensor HxW -> the 4x4-blocked layout (imloc_depth_tile4_async): a float32 CUDA tensor of
+    ceil(H/4) block rows x 16 ceil(W/4) elements.  Use it as a view's depth with layout="tile4" and the
+    view's width and height."""
+    import torch
+
+    assert depth.dtype == torch.float32 and depth.dim() == 2 and depth.is_cuda and depth.stride(1) == 1
+    H, W = depth.shape
+    out = torch.empty(((H + 3) // 4, 16 * ((W + 3) // 4)), dtype=torch.float32, device=depth.device)
+    _check(load().imloc_depth_tile4_async(C.c_void_p(depth.data_ptr()), W, H, depth.stride(0),
+                                          C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
+           "imloc_depth_tile4_async")
+    return out
+
+
+def tile4_view(v):
+    """A view dict with its float32 depth map re-laid out in 4x4 blocks."""
+    d = dict(v)
+    H, W = v["depth"].shape
+    d.update(depth=depth_tile4(v["depth"]), layout="tile4", width=W, height=H)
+    return d
 
 
 def depth_decode_log8(codes, out=None, stream=None):

@@ -196,3 +196,32 @@ def test_many_client_threads(store, ctx):
     assert all(v[0]["status"] == 0 for v in got.values())
     assert len(set(tickets)) == len(qs)
     srv.close()
+
+
+def test_device_submitted_matches_give_the_host_submitted_results(store, ctx):
+    """imloc_serve_submit_device (matches already in device memory, read in
+    place by the lift): the same results as host submission of the same
+    queries, mixed in one stream of submissions."""
+    ms, dev_views = store
+    qs = make_queries(ms, 8, 5)
+    t = torch()
+    srv = imloc.Server(ctx, max_slots=6, device_budget_bytes=256 << 20)
+    keep, tickets_h, tickets_d = [], [], []
+    for i, q in enumerate(qs):
+        tickets_h.append(srv.submit(query_views(dev_views, q), q["matches"], q["K"], opts_for(i)))
+        dm = {k: t.from_numpy(np.ascontiguousarray(q["matches"][k], dtype=np.float32)).cuda()
+              for k in ("q_u", "q_v", "db_u", "db_v", "conf")}
+        dm.update({k: q["matches"][k] for k in ("seg_off", "seg_view", "seg_dir")})
+        p = imloc.Server.prepare_device(query_views(dev_views, q), dm, q["K"], opts_for(i))
+        keep.append(p)
+        tickets_d.append(srv.submit_prepared(p))
+    got = wait_all(srv, tickets_h + tickets_d)
+    for i, q in enumerate(qs):
+        rh, _ = got[tickets_h[i]]
+        rd, _ = got[tickets_d[i]]
+        assert rh["status"] == 0 and rd["status"] == 0
+        assert pose_close(rh["R"], rh["t"], rd["R"], rd["t"]), i
+        assert rh["num_inliers"] == rd["num_inliers"], i
+        assert pose_close(rd["R"], rd["t"], q["R_gt"], q["t_gt"], deg=0.5, mm=50), i
+    assert srv.stats()["worker_status"] == 0
+    srv.close()
