@@ -91,8 +91,7 @@ int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_pe
  * tensor-core kernel; tc_variant -1 = default (environment IMLOC_TC_VARIANT),
  * 0 = 80-record blocks with bf16 pieces, 1 = 128-record blocks with bf16
  * pieces, 2 = 80-record blocks with TF32 pieces, 3 = 64-record blocks with
- * bf16 pieces, 4 = 160-record blocks with bf16 pieces, 5 = 96-record blocks
- * with bf16 pieces.  The continuous-batching
+ * bf16 pieces.  The continuous-batching
  * server always uses the FP32 kernel.  IMLOC_ERR_INVALID_ARG for a null
  * context or values out of range. */
 int imloc_set_scoring(imloc_ctx* ctx, int32_t kernel, int32_t tc_variant);
