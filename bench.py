@@ -406,7 +406,25 @@ def run_triangulation(dev, repeats=20):
             "kept_fraction": float(kept.mean()),
             "median_rel_depth_error": float(np.median(np.abs(d[kept] - gt[kept]) / gt[kept])) if kept.any() else None,
             "input_bytes": int(3 * 8 * 560 * 560 * 4),
+            "roofline": _triangulation_roofline(dev, ms, 560 * 560, 8),
             "paper_context": "~30 ms per image on an RTX 4090 for matching + triangulation, matching dominating (Sec. 3.3)"}
+
+
+# Triangulation work per pixel: S depth hypotheses (closest approach of two rays, ~40 flops each) and
+# S x S inlier tests of a hypothesis against a source (point on the pixel's ray, offset from the source
+# centre, cross and dot products with the match's ray, the tan^2 comparison: ~30 flops each); the
+# refinement of the kept pixels is not counted.
+TRI_FLOPS_HYP, TRI_FLOPS_TEST = 40, 30
+
+
+def _triangulation_roofline(dev, ms, pixels, sources):
+    peak, basis = fp32_peak_tflops(dev, load_peaks())
+    flops = pixels * (sources * TRI_FLOPS_HYP + sources * sources * TRI_FLOPS_TEST)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "k_triangulate", "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flops_per_pixel": flops / pixels, "peak_basis": basis,
+            "note": "hypothesis-and-test core per pixel (S hypotheses x 40 + S^2 tests x 30 flops) / event time per "
+                    "image; the refinement of kept pixels is extra work not counted"}
 
 
 def run_rig(dev, peaks, repeats=5, n_queries=16):

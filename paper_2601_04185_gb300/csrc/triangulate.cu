@@ -5,7 +5,9 @@
 // and is refined on the confidence-weighted squared angular errors of its
 // inliers; depths with more than 3 inliers are kept.
 //
-// One thread per reference pixel, FP32.  Per-source ray matrices
+// One CTA per 256 reference pixels, FP32: selection per pixel, then the
+// kept pixels compacted in shared memory and refined one per thread.
+// Per-source ray matrices
 // M_s = R_s^T K_s^-1 and centres live in the kernel parameters.  The
 // closest-approach depth is evaluated with cross products (no cancellation
 // in |d0 x d1|^2 for small ray angles); the inlier test compares
@@ -73,36 +75,60 @@ __device__ __forceinline__ float angle_residual(const float a[3], const float q[
     return th;
 }
 
+// The rays of pixel px: its own (d0) and one per source match (ds), the
+// match confidences and the mask of matches with conf >= conf_min.
 template <int MAXS>
-__global__ void __launch_bounds__(256) k_triangulate(const __grid_constant__ TriParams p) {
-    const int64_t n = static_cast<int64_t>(p.W) * p.H;
-    for (int64_t px = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; px < n;
-         px += static_cast<int64_t>(gridDim.x) * 256) {
-        const int j = static_cast<int>(px / p.W), i = static_cast<int>(px - static_cast<int64_t>(j) * p.W);
-        const float x = static_cast<float>(i) + 0.5f, y = static_cast<float>(j) + 0.5f;
-        float d0[3];
+__device__ __forceinline__ void pixel_rays(const TriParams& p, int64_t px, float d0[3], float ds[MAXS][3], float cf[MAXS],
+                                           uint32_t& used) {
+    const int j = static_cast<int>(px / p.W), i = static_cast<int>(px - static_cast<int64_t>(j) * p.W);
+    const float x = static_cast<float>(i) + 0.5f, y = static_cast<float>(j) + 0.5f;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) d0[r] = fmaf(p.M0[3 * r], x, fmaf(p.M0[3 * r + 1], y, p.M0[3 * r + 2]));
-        float ds[MAXS][3], cf[MAXS];
-        uint32_t used = 0u;
+    for (int r = 0; r < 3; ++r) d0[r] = fmaf(p.M0[3 * r], x, fmaf(p.M0[3 * r + 1], y, p.M0[3 * r + 2]));
+    used = 0u;
 #pragma unroll
-        for (int s = 0; s < MAXS; ++s) {
-            cf[s] = 0.f;
-            ds[s][0] = ds[s][1] = ds[s][2] = 0.f;
-            if (s < p.S) {
-                const float us = __ldg(p.u + s * p.stride + px), vs = __ldg(p.v + s * p.stride + px);
-                cf[s] = __ldg(p.conf + s * p.stride + px);
-                if (cf[s] >= p.conf_min) used |= 1u << s;
+    for (int s = 0; s < MAXS; ++s) {
+        cf[s] = 0.f;
+        ds[s][0] = ds[s][1] = ds[s][2] = 0.f;
+        if (s < p.S) {
+            const float us = __ldg(p.u + s * p.stride + px), vs = __ldg(p.v + s * p.stride + px);
+            cf[s] = __ldg(p.conf + s * p.stride + px);
+            if (cf[s] >= p.conf_min) used |= 1u << s;
 #pragma unroll
-                for (int r = 0; r < 3; ++r) ds[s][r] = fmaf(p.M[s][3 * r], us, fmaf(p.M[s][3 * r + 1], vs, p.M[s][3 * r + 2]));
-            }
+            for (int r = 0; r < 3; ++r) ds[s][r] = fmaf(p.M[s][3 * r], us, fmaf(p.M[s][3 * r + 1], vs, p.M[s][3 * r + 2]));
         }
+    }
+}
+
+// One CTA per 256 pixels, in two phases.  Selection (every pixel): the
+// hypotheses and their inlier tests, branch-free; pixels without a kept
+// depth are written at once, kept ones go to a queue in shared memory
+// (pixel, winning depth, inlier mask).  Refinement: thread t refines queue
+// entry t (its rays recomputed from the match planes, now in L1/L2), so that
+// the warps of this phase hold kept pixels only, instead of the ~60 % of
+// lanes a per-pixel loop would keep busy.  Results do not depend on the
+// queue order.
+template <int MAXS>
+__global__ void __launch_bounds__(256, MAXS <= 8 ? 3 : 1) k_triangulate(const __grid_constant__ TriParams p) {
+    __shared__ int s_nq;
+    __shared__ int s_pix[256];
+    __shared__ float s_z[256];
+    __shared__ uint32_t s_set[256];
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t n = static_cast<int64_t>(p.W) * p.H;
+    const int64_t px = static_cast<int64_t>(blockIdx.x) * 256 + tid;
+    if (tid == 0) s_nq = 0;
+    __syncthreads();
+    bool kept = false;
+    float best_z = 0.f;
+    uint32_t best_set = 0u;
+    if (px < n) {
+        float d0[3], ds[MAXS][3], cf[MAXS];
+        uint32_t used;
+        pixel_rays<MAXS>(p, px, d0, ds, cf, used);
         // hypotheses: closest approach of the reference ray to each used match's ray;
         // every loop runs over all sources with predicated updates (pixels of a
         // warp use different matches: branches would serialise them)
         int best_n = 0, best_s = -1;
-        float best_z = 0.f;
-        uint32_t best_set = 0u;
 #pragma unroll
         for (int s = 0; s < MAXS; ++s) {
             float nrm[3], wx[3];
@@ -130,74 +156,89 @@ __global__ void __launch_bounds__(256) k_triangulate(const __grid_constant__ Tri
             best_z = take ? z : best_z;
             best_set = take ? set : best_set;
         }
-        float out = 0.f;
-        if (best_s >= 0 && best_n > p.keep_more_than) {
-            // refinement (only for depths that are kept): Gauss-Newton on the
-            // angular error vectors of the inliers, weight 0 for the others
-            float wk[MAXS], e1[MAXS][3], e2[MAXS][3], dh[MAXS][3];
-#pragma unroll
-            for (int k = 0; k < MAXS; ++k) {
-                wk[k] = ((best_set >> k) & 1u) ? cf[k] : 0.f;
-                // unit ray and an orthonormal basis of the plane across it
-                const float inv = rsqrtf(fmaxf(dot(ds[k], ds[k]), 1e-30f));
-                dh[k][0] = ds[k][0] * inv; dh[k][1] = ds[k][1] * inv; dh[k][2] = ds[k][2] * inv;
-                const bool xs = fabsf(dh[k][0]) < 0.9f;
-                const float hx[3] = {xs ? 1.f : 0.f, xs ? 0.f : 1.f, 0.f};
-                cross(dh[k], hx, e1[k]);
-                const float i1 = rsqrtf(fmaxf(dot(e1[k], e1[k]), 1e-30f));
-                e1[k][0] *= i1; e1[k][1] *= i1; e1[k][2] *= i1;
-                cross(dh[k], e1[k], e2[k]);
-            }
-            auto cost = [&](float zz) {
-                float e = 0.f;
-#pragma unroll
-                for (int k = 0; k < MAXS; ++k) {
-                    float a[3], c[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) a[r] = fmaf(zz, d0[r], p.W0[k][r]);
-                    cross(a, dh[k], c);
-                    const float th = atan2f(sqrtf(dot(c, c)), dot(a, dh[k]));
-                    e = fmaf(wk[k] * th, th, e);
-                }
-                return e;
-            };
-            float z = best_z;
-            float e = cost(z);
-            for (int it = 0; it < p.refine_iters; ++it) {
-                float g = 0.f, h = 0.f;
-#pragma unroll
-                for (int k = 0; k < MAXS; ++k) {
-                    float a[3];
-#pragma unroll
-                    for (int r = 0; r < 3; ++r) a[r] = fmaf(z, d0[r], p.W0[k][r]);
-                    float rv[2], J[2];
-                    angle_residual(a, d0, dh[k], e1[k], e2[k], rv, J);
-                    g = fmaf(wk[k], fmaf(rv[0], J[0], rv[1] * J[1]), g);
-                    h = fmaf(wk[k], fmaf(J[0], J[0], J[1] * J[1]), h);
-                }
-                if (!(h > 0.f)) break;
-                // steps below ~8 float ulps of z cannot be resolved: that is convergence
-                const float tiny = 1e-6f * z;
-                float step = -g / h;
-                bool accepted = false;
-                for (int half = 0; half < 8 && fabsf(step) > tiny; ++half, step *= 0.5f) {
-                    const float zn = z + step;
-                    if (!(zn > 0.f)) continue;
-                    const float en = cost(zn);
-                    if (en < e) {
-                        z = zn;
-                        e = en;
-                        accepted = true;
-                        break;
-                    }
-                }
-                if (!accepted || fabsf(step) <= tiny) break;
-            }
-            out = z;
-        }
-        p.depth[px] = out;
+        kept = best_s >= 0 && best_n > p.keep_more_than;
+        if (!kept) p.depth[px] = 0.f;
         if (p.inliers) p.inliers[px] = static_cast<uint8_t>(best_n);
     }
+    // queue the kept pixels of the block (one shared atomic per warp)
+    const uint32_t bal = __ballot_sync(0xffffffffu, kept);
+    int at = 0;
+    if (lane == 0 && bal) at = atomicAdd(&s_nq, __popc(bal));
+    at = __shfl_sync(0xffffffffu, at, 0) + __popc(bal & ((1u << lane) - 1u));
+    if (kept) {
+        s_pix[at] = tid;
+        s_z[at] = best_z;
+        s_set[at] = best_set;
+    }
+    __syncthreads();
+    if (tid >= s_nq) return;
+    // refinement of queue entry tid: Gauss-Newton on the angular error vectors
+    // of the winner's inliers, weight 0 for the others
+    const int64_t qx = static_cast<int64_t>(blockIdx.x) * 256 + s_pix[tid];
+    const uint32_t set = s_set[tid];
+    float d0[3], ds[MAXS][3], cf[MAXS];
+    uint32_t used;
+    pixel_rays<MAXS>(p, qx, d0, ds, cf, used);
+    float wk[MAXS], e1[MAXS][3], e2[MAXS][3], dh[MAXS][3];
+#pragma unroll
+    for (int k = 0; k < MAXS; ++k) {
+        wk[k] = ((set >> k) & 1u) ? cf[k] : 0.f;
+        // unit ray and an orthonormal basis of the plane across it
+        const float inv = rsqrtf(fmaxf(dot(ds[k], ds[k]), 1e-30f));
+        dh[k][0] = ds[k][0] * inv; dh[k][1] = ds[k][1] * inv; dh[k][2] = ds[k][2] * inv;
+        const bool xs = fabsf(dh[k][0]) < 0.9f;
+        const float hx[3] = {xs ? 1.f : 0.f, xs ? 0.f : 1.f, 0.f};
+        cross(dh[k], hx, e1[k]);
+        const float i1 = rsqrtf(fmaxf(dot(e1[k], e1[k]), 1e-30f));
+        e1[k][0] *= i1; e1[k][1] *= i1; e1[k][2] *= i1;
+        cross(dh[k], e1[k], e2[k]);
+    }
+    auto cost = [&](float zz) {
+        float e = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+            float a[3], c[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a[r] = fmaf(zz, d0[r], p.W0[k][r]);
+            cross(a, dh[k], c);
+            const float th = atan2f(sqrtf(dot(c, c)), dot(a, dh[k]));
+            e = fmaf(wk[k] * th, th, e);
+        }
+        return e;
+    };
+    float z = s_z[tid];
+    float e = cost(z);
+    for (int it = 0; it < p.refine_iters; ++it) {
+        float g = 0.f, h = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAXS; ++k) {
+            float a[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) a[r] = fmaf(z, d0[r], p.W0[k][r]);
+            float rv[2], J[2];
+            angle_residual(a, d0, dh[k], e1[k], e2[k], rv, J);
+            g = fmaf(wk[k], fmaf(rv[0], J[0], rv[1] * J[1]), g);
+            h = fmaf(wk[k], fmaf(J[0], J[0], J[1] * J[1]), h);
+        }
+        if (!(h > 0.f)) break;
+        // steps below ~8 float ulps of z cannot be resolved: that is convergence
+        const float tiny = 1e-6f * z;
+        float step = -g / h;
+        bool accepted = false;
+        for (int half = 0; half < 8 && fabsf(step) > tiny; ++half, step *= 0.5f) {
+            const float zn = z + step;
+            if (!(zn > 0.f)) continue;
+            const float en = cost(zn);
+            if (en < e) {
+                z = zn;
+                e = en;
+                accepted = true;
+                break;
+            }
+        }
+        if (!accepted || fabsf(step) <= tiny) break;
+    }
+    p.depth[qx] = z;
 }
 
 void ray_matrix(const imloc_camera& K, const imloc_pose& P, float M[9], float C[3]) {
@@ -270,10 +311,9 @@ int imloc_triangulate_depth_async(const imloc_camera* ref_cam, const imloc_pose*
         }
     }
     const int64_t n = static_cast<int64_t>(width) * height;
-    int dev = 0, sms = 132;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t want = (n + 255) / 256;
-    const int grid = static_cast<int>(want < 16LL * sms ? want : 16LL * sms);
+    const int64_t blocks = (n + 255) / 256;  // one CTA per 256 pixels
+    if (blocks > INT32_MAX) return IMLOC_ERR_INVALID_ARG;
+    const int grid = static_cast<int>(blocks);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (n_src <= 8) k_triangulate<8><<<grid, 256, 0, st>>>(p);
     else k_triangulate<16><<<grid, 256, 0, st>>>(p);
