@@ -422,3 +422,54 @@ def test_graph_replay_on_a_user_stream_matches(ctx):
             np.testing.assert_array_equal(a["R"], b["R"])
             assert a["num_inliers"] == b["num_inliers"]
     assert ctx.device_error() == 0
+
+
+def test_scores_invariant_under_permutation_of_the_correspondences(ctx):
+    """Permutation invariance of a fixed hypothesis set (N <= 10,000, so the
+    subset is every correspondence): per-pose scores agree to FP32 summation
+    order and inlier counts exactly (both kernels), and the brute-force best
+    of a tiny set is the same pose."""
+    rng = np.random.default_rng(23)
+    q = synth.direct_query(rng, 8000, 0.3, 1024, 768, 800.0, weights="conf")
+    P = 600
+    poses = []
+    for k in range(P):
+        dR = synth.axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, 3)))
+        poses.append(np.concatenate([(dR @ q["R_gt"]).ravel(), q["t_gt"] + rng.normal(size=3) * 0.2]))
+    t = torch()
+    inj = t.from_numpy(np.array(poses, np.float32)).cuda()
+    perm = rng.permutation(8000)
+    opts = imloc.default_opts(max_iters=P, batch=1024, p_miss=0.0, final_iters=0, lo_iters=0)
+    out = {}
+    for kernel in (0, 1):
+        ctx.set_scoring(kernel)
+        for name, order in (("id", np.arange(8000)), ("perm", perm)):
+            c = imloc.corr_from_arrays(q["x"][order], q["y"][order], q["X"][order], q["w"][order])
+            dbg = dict(inject_poses=inj, scores=t.full((4 * P,), float("nan"), device="cuda"),
+                       counts=t.full((4 * P,), -1, dtype=t.int32, device="cuda"))
+            ctx.testing_ransac(c, q["K"], opts, 8000, dbg)
+            out[(kernel, name)] = (dbg["scores"].cpu().numpy()[::4], dbg["counts"].cpu().numpy()[::4])
+    ctx.set_scoring(-1)
+    for kernel in (0, 1):
+        sa, ca = out[(kernel, "id")]
+        sb, cb = out[(kernel, "perm")]
+        np.testing.assert_array_equal(ca, cb)
+        np.testing.assert_allclose(sa, sb, rtol=1e-5)
+    # brute force on a tiny noise-free set: the same best pose whatever the order
+    rs = np.random.default_rng(33)
+    n = 12
+    K = (500.0, 500.0, 320.0, 240.0)
+    R = synth.random_rotation(rs)
+    tt = rs.normal(size=3)
+    u = rs.uniform(40, 600, n); v = rs.uniform(40, 440, n); d = rs.uniform(3, 15, n)
+    Xw = (np.column_stack([(u - 320) / 500 * d, (v - 240) / 500 * d, d]) - tt) @ R
+    x, y = u.copy(), v.copy()
+    x[9:] += 60.0  # three outliers
+    w = np.ones(n)
+    p2 = np.random.default_rng(3).permutation(n)
+    res = []
+    for order in (np.arange(n), p2):
+        c = imloc.corr_from_arrays(x[order], y[order], Xw[order], w[order])
+        o = imloc.default_opts(max_iters=220, batch=220, enumerate_all=1, p_miss=0.0, lo_iters=0, final_iters=0)
+        res.append(ctx.ransac_pnp(c, K, o, n=n))
+    assert pose_close(res[0]["R_best"], res[0]["t_best"], res[1]["R_best"], res[1]["t_best"], deg=1e-3, mm=0.01)
