@@ -558,7 +558,11 @@ def run_serving(dev, rates, per_rate, queries, dev_views, seconds_cap=3.0):
                 time.sleep(0.0005)
         elapsed = time.perf_counter() - t0
         lats.sort()
-        return {"queries": len(order), "refused": sum(t is None for t in tickets), "q_per_s": len(lats) / elapsed,
+        refused = sum(t is None for t in tickets)
+        if not lats:
+            return {"queries": len(order), "refused": refused, "q_per_s": 0.0, "p50_ms": None, "p99_ms": None,
+                    "server_stats": srv.stats()}
+        return {"queries": len(order), "refused": refused, "q_per_s": len(lats) / elapsed,
                 "p50_ms": lats[len(lats) // 2], "p99_ms": lats[min(len(lats) - 1, int(0.99 * len(lats)))]}
 
     def plain(arrivals, order, on_device):
@@ -1174,16 +1178,45 @@ def run_ours(args):
     q_per_s = sum_over_ranks(nq * args.steps, world) / total_s_max
 
     # ---- end to end through the public API with host buffers ----
+    # Every step uploads its matches from pinned host memory and reads its
+    # results back.  The upload of step i+1 runs on a copy stream into the
+    # other of two device buffers while step i computes (events order the
+    # reuse of a buffer); all copies and the read-backs are inside the timed
+    # region, which spans the K steps.  No L2 flush between steps: a step's
+    # inputs (the depth maps of its views and its matches) exceed the L2.
     h2d = sum(h_match[k].numel() * 4 for k in h_match)
     d2h = results.numel()
-    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.zero_()
-        ev2[i][0].record(stream)
-        step(from_host=True)
-        ev2[i][1].record(stream)
+    d_match_b = [d_match, dict(d_match, **{k: torch.empty_like(d_match[k]) for k in h_match})]
+    prep_b = [prep_lift, imloc.prepare_lift_batch(qb, d_views, d_match_b[1])]
+    copy_stream = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def upload(b):
+        with torch.cuda.stream(copy_stream):
+            for k in h_match:
+                d_match_b[b][k].copy_(h_match[k], non_blocking=True)
+        copied[b].record(copy_stream)
+
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev2) / 1e3, world)
+    t_start.record(stream)
+    copy_stream.wait_event(t_start)
+    upload(0)
+    for i in range(args.steps):
+        b = i % 2
+        if i + 1 < args.steps:
+            if i >= 1:
+                copy_stream.wait_event(consumed[1 - b])  # step i-1 is done with that buffer
+            upload(1 - b)
+        stream.wait_event(copied[b])
+        ctx.lift_batch(qb, d_views, d_match_b[b], out=corr, offsets=offsets, stream=stream, prepared=prep_b[b])
+        consumed[b].record(stream)
+        ctx.ransac_pnp_batch_async(corr, offsets, Ks, opts, results, stream=stream, prepared=prep_ransac)
+        h_results.copy_(results, non_blocking=True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, world)
     e2e_value = pairs_all / e2e_s
 
     # ---- roofline stress mode: every pose scored against all N correspondences (M = N) ----
@@ -1277,7 +1310,10 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
         "queries_per_s": q_per_s,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                "queries_per_s": sum_over_ranks(nq * args.steps, world) / e2e_s},
+                "queries_per_s": sum_over_ranks(nq * args.steps, world) / e2e_s,
+                "form": "matches uploaded from pinned host memory every step on a copy stream (double-buffered, "
+                        "overlapping the previous step's compute), results read back every step; timed over the K "
+                        "steps, no L2 flush (a step's depth maps and matches exceed L2)"},
         "plain": {"latency_ms_p50": p50, "latency_ms_p99": p99, "queries_per_s": 1e3 / statistics.mean(lat),
                   "form": "one query per call: imloc_lift_async + imloc_ransac_pnp (host-synchronous)",
                   "samples": len(lat)},

@@ -21,7 +21,8 @@
 // marshals.  A query that finished in step k is still part of step k+1,
 // whose kernels skip it (its state is done).  The host blocks of a step
 // (descriptors, round plan, states, results) are double-buffered pinned
-// memory, and each step remembers which query sat in which slot.
+// memory, and each step remembers the ticket of the query in each slot, so
+// that a slot refilled meanwhile is not retired with the old query's state.
 // A query that arrives while others are on the GPU joins at the next step.
 #include <stdio.h>
 #include <string.h>
@@ -173,7 +174,8 @@ struct imloc_server {
     imloc::QueryState* h_qs[2] = {nullptr, nullptr};
     imloc_result* h_res[2] = {nullptr, nullptr};
     cudaEvent_t step_done[2] = {nullptr, nullptr};
-    std::vector<ServeQuery*> occ[2];
+    std::vector<uint64_t> occ[2];  // ticket of each slot's query during the step (0: empty); tickets are
+                                   // never reused, unlike the addresses of freed queries
     std::vector<ServeQuery*> step_admitted[2];
     // pinned FIFO ring holding submitted matches until their upload
     char* ring = nullptr;
@@ -337,7 +339,7 @@ static int enqueue_step(imloc_server* S, const std::vector<ServeQuery*>& admitte
     int64_t total = 0;
     for (int s = 0; s < ns; ++s) {
         ServeQuery* q = S->slots[s];
-        S->occ[p][s] = q;
+        S->occ[p][s] = q ? q->ticket : 0;
         WaveQ& w = S->h_wq[p][s];
         memset(&w, 0, sizeof(w));
         S->h_prefix[p][s] = total;
@@ -396,9 +398,10 @@ static int retire_step(imloc_server* S, int p) {
         if (!q->on_device) ring_release(S, q);
     S->step_admitted[p].clear();
     for (int s = 0; s < ns; ++s) {
-        ServeQuery* q = S->occ[p][s];
-        S->occ[p][s] = nullptr;
-        if (!q || S->slots[s] != q || !S->h_qs[p][s].finished) continue;
+        const uint64_t ticket = S->occ[p][s];
+        S->occ[p][s] = 0;
+        ServeQuery* q = S->slots[s];
+        if (!ticket || !q || q->ticket != ticket || !S->h_qs[p][s].finished) continue;
         S->done[q->ticket] = {S->h_res[p][s], t - q->t_submit};
         S->live.erase(q->ticket);
         S->pool_alloc.release(q->pool_off, q->footprint);
@@ -517,7 +520,7 @@ int imloc_serve_create(imloc_ctx* ctx, const imloc_serve_config* cfg, imloc_serv
         ok = ok && cudaMallocHost(&S->h_qs[k], sizeof(imloc::QueryState) * ns) == cudaSuccess;
         ok = ok && cudaMallocHost(&S->h_res[k], sizeof(imloc_result) * ns) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&S->step_done[k], cudaEventDisableTiming) == cudaSuccess;
-        S->occ[k].assign(ns, nullptr);
+        S->occ[k].assign(ns, 0);
     }
     ok = ok && cudaMallocHost(&S->ring, cfg->host_staging_bytes) == cudaSuccess;
     if (!ok) {

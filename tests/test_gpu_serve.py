@@ -225,3 +225,31 @@ def test_device_submitted_matches_give_the_host_submitted_results(store, ctx):
         assert pose_close(rd["R"], rd["t"], q["R_gt"], q["t_gt"], deg=0.5, mm=50), i
     assert srv.stats()["worker_status"] == 0
     srv.close()
+
+
+def test_slots_reused_while_steps_are_in_flight(store, ctx):
+    """Many short queries through two slots: slots are freed and refilled
+    while the next step is already on the GPU (the steps are pipelined), and
+    a refilled slot must not be retired with the previous query's state.
+    Every result equals the same query served alone, the staging ring drains
+    (a long second burst is admitted in full), nothing is refused."""
+    ms, dev_views = store
+    qs = make_queries(ms, 16, 13, views=(3, 5), per_pair=(800, 1500))
+    srv = imloc.Server(ctx, max_slots=2, device_budget_bytes=256 << 20, rounds_per_step=1,
+                       host_staging_bytes=64 << 20)
+    alone = []
+    for i, q in enumerate(qs):
+        t = srv.submit(query_views(dev_views, q), q["matches"], q["K"], opts_for(i))
+        alone.append(wait_all(srv, [t])[t][0])
+    for burst in range(3):
+        tickets = [srv.submit(query_views(dev_views, q), q["matches"], q["K"], opts_for(i)) for i, q in enumerate(qs)]
+        assert all(t is not None for t in tickets)
+        got = wait_all(srv, tickets)
+        for i, t in enumerate(tickets):
+            r = got[t][0]
+            assert r["status"] == alone[i]["status"] == 0
+            assert pose_close(r["R"], r["t"], alone[i]["R"], alone[i]["t"]), (burst, i)
+            assert r["iterations"] == alone[i]["iterations"] and r["num_inliers"] == alone[i]["num_inliers"]
+    st = srv.stats()
+    assert st["completed"] == 64 and st["rejected"] == 0 and st["resident"] == 0 and st["worker_status"] == 0
+    srv.close()
