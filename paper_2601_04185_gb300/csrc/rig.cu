@@ -387,8 +387,44 @@ __global__ void __launch_bounds__(kRigScoreThreads) k_rig_score(const __grid_con
                 P[j][8 + bb] = M[2][bb];
             }
         }
-#pragma unroll 4
-        for (int i = b0 - c0; i < b1 - c0; ++i) {
+        // two records of the run per step, their projections and residuals as
+        // packed f32x2 operations (the pose coefficients duplicated in both
+        // halves), branch-free: z <= 0 (or NaN) gives 1/0 = inf, an inf or
+        // NaN residual, min(., tau^2) = tau^2 and no inlier; the even and the
+        // odd records are summed separately, then even + odd
+        uint64_t P2[kRigHT][12];
+#pragma unroll
+        for (int j = 0; j < kRigHT; ++j)
+#pragma unroll
+            for (int a = 0; a < 12; ++a) P2[j][a] = f2_pack(P[j][a], P[j][a]);
+        float pe[kRigHT], po[kRigHT];
+#pragma unroll
+        for (int j = 0; j < kRigHT; ++j) { pe[j] = 0.f; po[j] = 0.f; }
+        const int i0 = b0 - c0, i1 = b1 - c0;
+        int i = i0;
+#pragma unroll 2
+        for (; i + 2 <= i1; i += 2) {
+            const float4 A = s_rec[i], B = s_rec[i + 1];
+            const float2 xa = s_xy[i], xb = s_xy[i + 1];
+            const uint64_t X2 = f2_pack(A.x, B.x), Y2 = f2_pack(A.y, B.y), Z2 = f2_pack(A.z, B.z);
+            const uint64_t NX = f2_pack(-xa.x, -xb.x), NY = f2_pack(-xa.y, -xb.y);
+#pragma unroll
+            for (int j = 0; j < kRigHT; ++j) {
+                const uint64_t zu = f2_fma(P2[j][0], X2, f2_fma(P2[j][1], Y2, f2_fma(P2[j][2], Z2, P2[j][3])));
+                const uint64_t zv = f2_fma(P2[j][4], X2, f2_fma(P2[j][5], Y2, f2_fma(P2[j][6], Z2, P2[j][7])));
+                const uint64_t zz = f2_fma(P2[j][8], X2, f2_fma(P2[j][9], Y2, f2_fma(P2[j][10], Z2, P2[j][11])));
+                float z0, z1;
+                f2_unpack(zz, z0, z1);
+                const uint64_t iz = f2_pack(rcp_approx(fmaxf(z0, 0.0f)), rcp_approx(fmaxf(z1, 0.0f)));
+                const uint64_t du = f2_fma(zu, iz, NX), dv = f2_fma(zv, iz, NY);
+                float r0, r1;
+                f2_unpack(f2_fma(du, du, f2_mul(dv, dv)), r0, r1);
+                cnt[j] += ((r0 < tau2) ? 1 : 0) + ((r1 < tau2) ? 1 : 0);
+                pe[j] = fmaf(A.w, fminf(r0, tau2), pe[j]);
+                po[j] = fmaf(B.w, fminf(r1, tau2), po[j]);
+            }
+        }
+        if (i < i1) {  // odd run length: the last record alone
             const float4 X = s_rec[i];
             const float2 xy = s_xy[i];
 #pragma unroll
@@ -396,19 +432,15 @@ __global__ void __launch_bounds__(kRigScoreThreads) k_rig_score(const __grid_con
                 const float u = fmaf(P[j][0], X.x, fmaf(P[j][1], X.y, fmaf(P[j][2], X.z, P[j][3])));
                 const float v = fmaf(P[j][4], X.x, fmaf(P[j][5], X.y, fmaf(P[j][6], X.z, P[j][7])));
                 const float z = fmaf(P[j][8], X.x, fmaf(P[j][9], X.y, fmaf(P[j][10], X.z, P[j][11])));
-                float r2 = tau2;
-                if (z > 0.f) {
-                    const float iz = __frcp_rn(z);
-                    const float du = fmaf(u, iz, -xy.x), dv = fmaf(v, iz, -xy.y);
-                    const float rr = fmaf(du, du, dv * dv);
-                    if (rr < tau2) {
-                        r2 = rr;
-                        ++cnt[j];
-                    }
-                }
-                cost[j] = fmaf(X.w, r2, cost[j]);
+                const float iz = rcp_approx(fmaxf(z, 0.0f));
+                const float du = fmaf(u, iz, -xy.x), dv = fmaf(v, iz, -xy.y);
+                const float rr = fmaf(du, du, dv * dv);
+                cnt[j] += (rr < tau2) ? 1 : 0;
+                pe[j] = fmaf(X.w, fminf(rr, tau2), pe[j]);
             }
         }
+#pragma unroll
+        for (int j = 0; j < kRigHT; ++j) cost[j] += pe[j] + po[j];
     }
 #pragma unroll
     for (int j = 0; j < kRigHT; ++j)

@@ -155,3 +155,27 @@ def test_lift_batch_offsets(ctx):
         g = {k: v[a:b] for k, v in g_all.items() if k != "n"}
         g["n"] = b - a
         check_lift(g, ref, q["views"], q["matches"], src_base=qb[pos])
+
+
+def test_lift_many_small_segments(ctx):
+    """Tiles that touch more than 8 segments (here ~200 per tile of 1,024
+    matches: every view's segment cut into runs of 5) take the kernel's
+    per-match segment search instead of the staged tile table; the result
+    is the oracle's either way, and the same as the coarse segmentation."""
+    q = synth.localization_query(np.random.default_rng(9), n_views=4, matches_per_pair=3001, width=320, height=240,
+                                 f=260.0)
+    m = dict(q["matches"])
+    so, sv, sd = np.asarray(m["seg_off"]), np.asarray(m["seg_view"]), np.asarray(m["seg_dir"])
+    off, view, dirn = [], [], []
+    for s in range(len(sv)):
+        for b in range(int(so[s]), int(so[s + 1]), 5):
+            off.append(b); view.append(int(sv[s])); dirn.append(int(sd[s]))
+    fine = dict(m, seg_off=np.array(off + [int(so[-1])], np.int64), seg_view=np.array(view, np.int32),
+                seg_dir=np.array(dirn, np.int32))
+    assert len(view) > 2000
+    views = views_to_device(q["views"])
+    g = lifted_to_host(ctx.lift(views, matches_to_device(fine)))
+    check_lift(g, oracle.lift(q["views"], fine), q["views"], fine)
+    coarse = lifted_to_host(ctx.lift(views, matches_to_device(m)))
+    for k in ("x", "y", "X", "Y", "Z", "w", "src"):
+        np.testing.assert_array_equal(g[k], coarse[k])
