@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import concurrent.futures as cf
+import gc
 import json
 import math
 import multiprocessing as mp
@@ -60,9 +61,9 @@ FP32_LANES_PER_SM = 128
 # scoring variant (threads, poses per thread) it was taken on; the line reports
 # it only when the autotuner picked that variant.
 SCORE_TRAFFIC_PER_LAUNCH = {(64, 4): 25.754e6 + 0.0}
-# the same for k_score_tc (80-record blocks, bf16 pieces) on that step
-# (profiles/k_score_tc_c2_16queries.md)
-SCORE_TC_TRAFFIC_PER_LAUNCH = 44.955e6 + 0.102e6
+# the same for the tensor-core scoring kernel (k_score_tcr: records on the MMA's
+# M side, 80-pose items) on that step (profiles/k_score_tcr_c2_16queries.md)
+SCORE_TC_TRAFFIC_PER_LAUNCH = 45.220e6 + 0.110e6
 # DRAM bytes (read + write) per lifted match from the committed ncu capture of
 # k_lift on the batched 9.48M-match shape (profiles/k_lift_batched_9.5M.md)
 LIFT_TRAFFIC_PER_MATCH = (1.229412e9 + 0.234057e9) / 9.48e6
@@ -1320,7 +1321,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": (achieved_tflops / peak_tflops) if achieved_tflops else None,
                      "traffic": score_traffic, "kernel": score_key,
-                     "variant": "80-record blocks, bf16 pieces" if score_key == "k_score_tc" else score_cfg,
+                     "variant": ("k_score_tcr: 128-record blocks x 80-pose items, bf16 pieces"
+                                 if score_key == "k_score_tc" else score_cfg),
                      "peak_basis": peak_basis, "flops_per_pair": FLOPS_PER_PAIR,
                      "flops_per_pair_basis": "13 FMA + 1 MUL per (pose, correspondence) pair",
                      "pairs_per_launch": pairs_per_launch, "launch_ms": score_launch_ms,
@@ -1388,6 +1390,9 @@ def run_ours(args):
         line["triangulation"] = run_triangulation(dev)
     # ---- serving (C5): Poisson arrivals, served vs plain ----
     if serving_inputs is not None:
+        # the earlier legs' buffers go before the host-timed serving loop
+        gc.collect()
+        torch.cuda.empty_cache()
         store, store_views, sq = serving_inputs
         dv = []
         for v in store_views:

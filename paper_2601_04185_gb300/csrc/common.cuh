@@ -220,7 +220,8 @@ struct QueryDesc {
     ScorePair* subset;      // (m_cap + 1) / 2 record pairs
     float4* tc_rec;         // optional, tensor-core scoring: per subset record (padded to a multiple of
                             // 32) one 128-byte operand row of split TF32 pieces, 128-byte swizzled
-    float4* tc_e;           // with tc_rec: per record pair {-x0, -x1, -y0, -y1}, {w0, w1, 0, 0}
+    float4* tc_e;           // with tc_rec, tc_mode 0 / 1: per record pair {-x0, -x1, -y0, -y1}, {w0, w1, 0, 0};
+                            // tc_mode 2: per record {-x / tau, -y / tau, w tau^2, 0}
     ScorePairB* subset_b;   // option score_bf16: header + (m_cap + 1) / 2 bf16-packed record pairs
     PoseF* slots;           // wave_samples * 4
     int32_t* compact;       // wave_samples * 4 pose ids (valid poses of the wave)
@@ -229,7 +230,8 @@ struct QueryDesc {
     int32_t* fixidx;        // fixed inlier set of the final refinement: per replay thread, the indices of its
                             // fixed points at its own positions (same offsets as the correspondences)
     int32_t inject;         // 1: poses are given (one per sample) instead of sampled + solved
-    int32_t tc_bf16;        // tc_rec rows hold bf16 pieces (else TF32 pieces)
+    int32_t tc_mode;        // tc_rec rows: 0 TF32 pieces, 1 bf16 pieces, 2 bf16 pieces with 1 in K lane 24 (for
+                            // the records-on-M scoring kernel; tc_e per record, see above)
     // optional outputs for the parity tests (one wave only)
     float* score_by_id;     // score of every pose id
     int32_t* count_by_id;   // inlier count of every pose id

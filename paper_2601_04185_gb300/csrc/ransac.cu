@@ -70,6 +70,8 @@ struct SetupParams {
 
 constexpr int kSetupBlocks = 8;  // CTAs per query: they split the subset gather
 constexpr int kTcBlock = 640;    // tensor-core operand rows are padded to a multiple of this (of every block size)
+constexpr uint32_t kBf16Eps = 0x0D80u;  // 2^-100 as bf16 (exponent 27, mantissa 0)
+constexpr uint32_t kBf16One = 0x3F80u;  // 1.0 as bf16
 
 // FP32 -> nearest bf16 value (as an FP32)
 __device__ __forceinline__ float to_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
@@ -208,17 +210,25 @@ __global__ void __launch_bounds__(256) k_setup(const __grid_constant__ SetupPara
             w = __ldg(d.w + i); nx = -__ldg(d.x + i); ny = -__ldg(d.y + i);
         }
         uint4 ch[8];
-        tc_operand_row(c, d.tc_bf16 != 0, false, ch);
+        tc_operand_row(c, d.tc_mode != 0, false, ch);
+        // mode 2: K lane 24 holds 1 (real records), matched by 2^-100 in the u and v pose rows of k_score_tcr
+        if (d.tc_mode == 2 && k < m) ch[3].x = kBf16One;
         uint4* row = reinterpret_cast<uint4*>(d.tc_rec) + static_cast<int64_t>(k) * 8;
         const int sw = k & 7;
 #pragma unroll
         for (int j = 0; j < 8; ++j) row[j ^ sw] = ch[j];
-        float* e = reinterpret_cast<float*>(d.tc_e + static_cast<int64_t>(k >> 1) * 2);
-        const int l = k & 1;
-        e[l] = nx;
-        e[2 + l] = ny;
-        e[4 + l] = w;
-        e[6 + l] = 0.f;
+        if (d.tc_mode == 2) {
+            // pixel scaled by 1 / tau and weight by tau^2 (NaN pixel, weight 0 past M)
+            const float inv_tau = 1.0f / sqrtf(d.tau2);
+            d.tc_e[k] = make_float4(nx * inv_tau, ny * inv_tau, w * d.tau2, 0.f);
+        } else {
+            float* e = reinterpret_cast<float*>(d.tc_e + static_cast<int64_t>(k >> 1) * 2);
+            const int l = k & 1;
+            e[l] = nx;
+            e[2 + l] = ny;
+            e[4 + l] = w;
+            e[6 + l] = 0.f;
+        }
     }
 }
 
@@ -1971,6 +1981,373 @@ __global__ void __launch_bounds__(TcShape<NB, NG>::kThreads, 1) k_score_tc(const
     }
 }
 
+// ============================================================================
+// k_score_tcr: the same products with the records on the MMA's M side
+// ============================================================================
+// Transposed form of k_score_tc: one MMA (M = 128 records of a block, N = 48 NG
+// = the u, v and z rows of 16 NG poses, bf16 split pieces as above) per K
+// step, so a block takes KSTEPS MMAs instead of 3 KSTEPS.  TMEM lane =
+// record, column = (row, pose): column r 16 NG + p of a 256-column
+// accumulator buffer (two buffers).  An epilogue thread owns one record of
+// every block and keeps running sums for the 16 poses of its group; its
+// pixel and weight come from global memory (L2), loaded one block ahead, so
+// the epilogue waits only for the accumulators.  The MMA's commit frees the
+// ring stage of the record rows.
+// The cost of a (pose, record) pair is w tau^2 min(r^2 / tau^2, 1): the u and
+// v rows of the pose are scaled by 1 / tau and the pixel by -1 / tau, so that
+// the residual components come out divided by tau and one saturating FMA
+// (clamp to [0, 1]) gives min(r^2 / tau^2, 1).  Points at or behind the
+// camera (z <= 0, reciprocal +inf) must cost tau^2: the u and v rows carry
+// 2^-100 in K lane 24 against a 1 in the record rows, so that u and v are
+// never exactly 0 there and the scaled residual is infinite (saturates to 1)
+// rather than 0 x inf = NaN (which a saturating FMA turns into 0).  The term
+// is far below one FP32 ulp of any projection in front of the camera.
+// Subset padding rows (all zero, weight 0) add 0.
+// At the end of the item the sums are reduced across the 32 lanes of each
+// warp (halving exchanges: 8 + 4 + 2 + 1 + 1 shuffles for 16 poses) and
+// across the group's four warps in warp order.  Per pose the summation order
+// is fixed by the record's position in the block and the block order:
+// independent of timing and of the grid.
+// Warps: 4 NG epilogue warps (NG groups of 16 poses; warp w reads TMEM lanes
+// 32 (w mod 4) ..), the MMA warp, the producer warp; items are (query,
+// 16 NG-pose tile).
+constexpr int kTcrRecs = 128;                      // records per block (M)
+constexpr int kTcrStages = 8;                      // ring of record operand blocks
+constexpr uint32_t kTcrRStage = kTcrRecs * 128;    // record operand rows of a block
+static_assert(kTcBlock % kTcrRecs == 0, "record padding covers the block size");
+
+// NG groups of 16 poses, NBUF accumulator buffers of 3 x 16 NG columns (32-column aligned)
+template <int NG, int NBUF>
+struct TcrShape {
+    static constexpr int kPoses = 16 * NG;
+    static constexpr int kThreads = NG * 128 + 64;  // + the MMA warp and the producer warp
+    static constexpr uint32_t kBufCols = (3 * kPoses + 31) / 32 * 32;
+    static_assert(NBUF >= 2 && NBUF * kBufCols <= kTcCols, "accumulator buffers fit the TMEM columns");
+    static constexpr uint32_t kPTile = 3 * kPoses * 128;  // pose rows: 3 x kPoses rows of 128 bytes
+    static constexpr size_t kSmemNeed =
+        1024 + kPTile + kTcrStages * kTcrRStage + 2 * 4 * kPoses * 4 + (2 * kTcrStages + 2 * NBUF) * 8 + 16;
+    static constexpr size_t kSmem = kSmemNeed > 116 * 1024 ? kSmemNeed : 116 * 1024;
+    static_assert(3 * kPoses <= 256 && (3 * kPoses) % 16 == 0 && kPTile % 1024 == 0, "MMA shape");
+};
+
+__device__ __forceinline__ float fma_sat(float a, float b, float c) {
+    float d;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Rows u, v, z of pose j of query d (zero rows past nh) as bf16 split-piece
+// operand rows n = r P + t of the 128-byte-swizzled pose tile sP; u and v
+// scaled by inv_tau and carrying 2^-100 in K lane 24.  Kept out of line: it
+// runs once per item, and inlined its temporaries crowd the epilogue's
+// registers.
+__device__ __noinline__ void tcr_pose_rows(const QueryDesc& d, int j, int nh, int64_t slot_base, float inv_tau,
+                                           int t, int P, unsigned char* sP) {
+    float c12[12];
+    if (j < nh) {
+        const PoseF ps = d.slots[d.compact[j] - slot_base];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            c12[c] = (d.fx * ps.R[c] + d.cx * ps.R[6 + c]) * inv_tau;
+            c12[4 + c] = (d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c]) * inv_tau;
+            c12[8 + c] = ps.R[6 + c];
+        }
+        c12[3] = (d.fx * ps.t[0] + d.cx * ps.t[2]) * inv_tau;
+        c12[7] = (d.fy * ps.t[1] + d.cy * ps.t[2]) * inv_tau;
+        c12[11] = ps.t[2];
+    } else {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) c12[c] = 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        uint4 ch[8];
+        tc_operand_row(c12 + 4 * r, true, true, ch);
+        if (r < 2) ch[3].x = kBf16Eps;  // K lane 24: 2^-100 x the records' 1
+        const int n = r * P + t;
+        uint4* row = reinterpret_cast<uint4*>(sP + (n >> 3) * 1024 + (n & 7) * 128);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) row[c ^ (n & 7)] = ch[c];  // the chunks of the two K steps
+    }
+}
+
+// PARTS: the epilogue reads a block's accumulators for its 16 poses in PARTS
+// parts of 16 / PARTS poses (fewer registers of accumulator values live);
+// PIPE: the next part's load is in flight while a part is computed.
+template <int NG, int NBUF, int PARTS, bool PIPE, bool COUNT>
+__global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(const __grid_constant__ ScoreParams p) {
+    using TS = TcrShape<NG, NBUF>;
+    constexpr uint32_t kTcrBufCols = TS::kBufCols;
+    constexpr int P = TS::kPoses;
+    constexpr int S = kTcrStages;
+    constexpr int KSTEPS = 2;  // bf16 pieces: two K steps of 16
+    constexpr int WMMA = 4 * NG, WPROD = WMMA + 1;
+    extern __shared__ __align__(1024) unsigned char tcr_smem_raw[];
+    unsigned char* smem =
+        reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tcr_smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sP = smem;                     // pose rows (B operand)
+    unsigned char* sR = sP + TS::kPTile;          // ring of record operand blocks (A operand)
+    float* s_part = reinterpret_cast<float*>(sR + S * kTcrRStage);  // [4][P] per warp quarter
+    int* s_cntp = reinterpret_cast<int*>(s_part + 4 * P);            // [4][P]
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_cntp + 4 * P);
+    uint64_t* empty = full + S;
+    uint64_t* tfull = empty + S;
+    uint64_t* tempty = tfull + NBUF;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + NBUF);
+    int* s_item = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int st = 0; st < S; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);  // the MMA's commit: the stage's MMAs have read it
+        }
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], WMMA * 32);  // every epilogue thread, once it has loaded the buffer
+        }
+        mbar_fence_init();
+    }
+    if (warp == WMMA) {
+        tmem_alloc(tmem_slot, kTcCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int total_tiles = p.tile_prefix[p.nq];
+    uint32_t base = 0;  // record blocks of the earlier items of this CTA (ring and buffer positions)
+
+    for (;;) {
+        if (tid == 0) *s_item = static_cast<int>(atomicAdd(p.work_counter, 1u));
+        __syncthreads();  // also: every MMA of the previous item has completed (its epilogue consumed them)
+        const int item = *s_item;
+        if (item >= total_tiles) break;
+        int lo = 0, hi = p.nq - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.tile_prefix[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const int q = lo;
+        const int tile = item - p.tile_prefix[q];
+        const QueryDesc& d = p.qd[q];
+        const bool active = tile < p.ntiles[q];
+        const int m = active ? p.qs[q].m : 0;
+        const int nh = p.n_hyp[q];
+        const int nblk = (m + kTcrRecs - 1) / kTcrRecs;
+        const int64_t slot_base = 4 * p.wq[q].s_begin;
+        const float tau2 = d.tau2;
+        const float inv_tau = 1.0f / sqrtf(tau2);
+
+        if (active && warp < 4) {
+            // pose rows of this item: thread tid < P writes rows tid, P + tid, 2 P + tid (u, v, z)
+            if (tid < P) tcr_pose_rows(d, tile * P + tid, nh, slot_base, inv_tau, tid, P, sP);
+            // the generic-proxy writes become visible to the tensor core's reads
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("bar.arrive 2, 160;" ::: "memory");
+        } else if (active && warp == WMMA) {
+            // the whole warp walks the blocks (it stays converged); one elected lane issues
+            asm volatile("bar.sync 2, 160;" ::: "memory");  // pose rows written
+            constexpr uint32_t idesc = umma_idesc_bf16(kTcrRecs, 3 * P);
+            const uint64_t rdesc = umma_desc_k_sw128(smem_u32(sR)), pdesc = umma_desc_k_sw128(smem_u32(sP));
+            for (int b = 0; b < nblk; ++b) {
+                const uint32_t gb = base + b;
+                const uint32_t st = gb % S, buf = gb % NBUF;
+                mbar_wait_bounded(&tempty[buf], ((gb / NBUF) & 1u) ^ 1u, p.err);
+                mbar_wait_bounded(&full[st], (gb / S) & 1u, p.err);
+                tc_fence_after();
+                const uint64_t ad0 = rdesc + ((st * kTcrRStage) >> 4);
+                const uint32_t d0 = tmem_base + buf * kTcrBufCols;
+                if (elect_one()) {
+#pragma unroll
+                    for (int kk = 0; kk < KSTEPS; ++kk)
+                        umma_bf16(d0, ad0 + ((kk * 32) >> 4), pdesc + ((kk * 32) >> 4), idesc, kk > 0 ? 1u : 0u);
+                    umma_commit(&tfull[buf]);
+                    umma_commit(&empty[st]);
+                }
+                __syncwarp();
+            }
+        } else if (active && warp == WPROD) {
+            for (int b = 0; b < nblk; ++b) {
+                const uint32_t gb = base + b;
+                const uint32_t st = gb % S;
+                mbar_wait_bounded(&empty[st], ((gb / S) & 1u) ^ 1u, p.err);
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(&full[st], kTcrRStage);
+                    bulk_g2s(sR + st * kTcrRStage, d.tc_rec + static_cast<int64_t>(b) * kTcrRecs * 8, kTcrRStage,
+                             &full[st]);
+                }
+                __syncwarp();
+            }
+        }
+        if (active && warp < WMMA) {
+            const int g = warp >> 2, wq = warp & 3;
+            // running sums of this lane's records for poses 16 g .. 16 g + 15 (pairs of poses)
+            uint64_t acc2[8];
+            uint32_t cnt2[8];  // with COUNT: inliers of poses 2i (low 16 bits) and 2i + 1 (high 16 bits)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                acc2[i] = f2_pack(0.f, 0.f);
+                cnt2[i] = 0u;
+            }
+            const uint32_t lane_addr = tmem_base + (static_cast<uint32_t>(wq * 32) << 16) + 16 * g;
+            // this thread's record of every block: {-x / tau, -y / tau, w tau^2, 0}
+            const float* te = reinterpret_cast<const float*>(d.tc_e + wq * 32 + lane);
+            float ex = __ldg(te), ey = __ldg(te + 1), ew = __ldg(te + 2);  // block 0
+            for (int b = 0; b < nblk; ++b) {
+                const uint32_t gb = base + b;
+                const uint32_t buf = gb % NBUF;
+                // the next block's pixel and weight, in flight during this block
+                const float* tn = te + static_cast<int64_t>(b + 1 < nblk ? b + 1 : b) * (kTcrRecs * 4);
+                const float ex_n = __ldg(tn), ey_n = __ldg(tn + 1), ew_n = __ldg(tn + 2);
+                mbar_wait_bounded(&tfull[buf], (gb / NBUF) & 1u, p.err);
+                tc_fence_after();
+                const uint32_t ta = lane_addr + buf * kTcrBufCols;
+                const uint64_t nx2 = f2_pack(ex, ex), ny2 = f2_pack(ey, ey), w2 = f2_pack(ew, ew);
+                constexpr int H = PARTS, KH = 8 / H, W = 16 / H;  // parts, pose pairs and columns per part
+                uint32_t z[PIPE ? 2 : 1][3][W];                      // u, v, z columns of a part (two sets: PIPE)
+                auto load_part = [&](int h, uint32_t (&zs)[3][W]) {
+                    tmem_ld_nowait<W>(ta + W * h, zs[0]);
+                    tmem_ld_nowait<W>(ta + P + W * h, zs[1]);
+                    tmem_ld_nowait<W>(ta + 2 * P + W * h, zs[2]);
+                };
+                auto ready = [&](uint32_t (&zs)[3][W]) {
+                    tmem_regs_ready<W>(zs[0]);
+                    tmem_regs_ready<W>(zs[1]);
+                    tmem_regs_ready<W>(zs[2]);
+                };
+                if constexpr (PIPE) {
+                    load_part(0, z[0]);
+                    tmem_wait_ld();
+                    ready(z[0]);
+                }
+#pragma unroll
+                for (int h = 0; h < H; ++h) {
+                    uint32_t (&zc)[3][W] = z[PIPE ? (h & 1) : 0];
+                    if constexpr (PIPE) {
+                        if (h + 1 < H) load_part(h + 1, z[(h + 1) & 1]);
+                    } else {
+                        load_part(h, zc);
+                        tmem_wait_ld();
+                        ready(zc);
+                    }
+                    if (h == H - 1) {
+                        // every load of this buffer has completed
+                        tc_fence_before();
+                        mbar_arrive(&tempty[buf]);
+                    }
+#pragma unroll
+                    for (int kh = 0; kh < KH; ++kh) {
+                        const int k = h * KH + kh;  // pose pair of the group's 16
+                        const float z0 = __uint_as_float(zc[2][2 * kh]), z1 = __uint_as_float(zc[2][2 * kh + 1]);
+                        const float i0 = rcp_approx(fmaxf(z0, 0.0f)), i1 = rcp_approx(fmaxf(z1, 0.0f));
+                        const uint64_t iz2 = f2_pack(i0, i1);
+                        const uint64_t du2 = f2_fma(
+                            f2_pack(__uint_as_float(zc[0][2 * kh]), __uint_as_float(zc[0][2 * kh + 1])), iz2, nx2);
+                        const uint64_t dv2 = f2_fma(
+                            f2_pack(__uint_as_float(zc[1][2 * kh]), __uint_as_float(zc[1][2 * kh + 1])), iz2, ny2);
+                        float du0, du1, q0, q1;
+                        f2_unpack(du2, du0, du1);
+                        f2_unpack(f2_mul(dv2, dv2), q0, q1);
+                        if (COUNT) {
+                            // the unclamped scaled residual decides the inlier count (NaN: not an inlier)
+                            const float r0 = fmaf(du0, du0, q0), r1 = fmaf(du1, du1, q1);
+                            cnt2[k] += ((r0 < 1.0f) ? 1u : 0u) + ((r1 < 1.0f) ? 0x10000u : 0u);
+                            acc2[k] = f2_fma(w2, f2_pack(fminf(r0, 1.0f), fminf(r1, 1.0f)), acc2[k]);
+                        } else {
+                            acc2[k] = f2_fma(w2, f2_pack(fma_sat(du0, du0, q0), fma_sat(du1, du1, q1)), acc2[k]);
+                        }
+                    }
+                    if constexpr (PIPE) {
+                        if (h + 1 < H) {
+                            tmem_wait_ld();
+                            ready(z[(h + 1) & 1]);
+                        }
+                    }
+                }
+                ex = ex_n;
+                ey = ey_n;
+                ew = ew_n;
+            }
+            // sums over the warp's 32 records per pose: halving exchanges leave pose
+            // (lane >> 1) of the group's 16 in lanes 2 (lane >> 1) and 2 (lane >> 1) + 1
+            float v[16];
+            int c[16];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                f2_unpack(acc2[i], v[2 * i], v[2 * i + 1]);
+                c[2 * i] = static_cast<int>(cnt2[i] & 0xffffu);
+                c[2 * i + 1] = static_cast<int>(cnt2[i] >> 16);
+            }
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const int off = 16 >> s, half = 8 >> s;
+                const bool upper = (lane & off) != 0;
+#pragma unroll
+                for (int i = 0; i < half; ++i) {
+                    const float send = upper ? v[i] : v[half + i];
+                    const float keep = upper ? v[half + i] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                    if (COUNT) {
+                        const int cs = upper ? c[i] : c[half + i];
+                        const int ck = upper ? c[half + i] : c[i];
+                        c[i] = ck + __shfl_xor_sync(0xffffffffu, cs, off);
+                    }
+                }
+            }
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+            if (COUNT) c[0] += __shfl_xor_sync(0xffffffffu, c[0], 1);
+            if ((lane & 1) == 0) {
+                s_part[wq * P + 16 * g + (lane >> 1)] = v[0];
+                if (COUNT) s_cntp[wq * P + 16 * g + (lane >> 1)] = c[0];
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(WMMA * 32) : "memory");
+            if (warp < (P + 31) / 32) {
+                const int e = tid;  // pose of the tile
+                const int j = tile * P + e;
+                const bool valid = e < P && j < nh;
+                uint32_t id = 0xffffffffu, rd = 0xffffffffu, sb = 0xffffffffu;
+                if (valid) {
+                    // the four warp quarters (records 0-31, 32-63, ... of every block) in order
+                    const float sc = ((s_part[e] + s_part[P + e]) + s_part[2 * P + e]) + s_part[3 * P + e];
+                    const int ct =
+                        COUNT ? s_cntp[e] + s_cntp[P + e] + s_cntp[2 * P + e] + s_cntp[3 * P + e] : 0;
+                    id = static_cast<uint32_t>(d.compact[j]);
+                    rd = static_cast<uint32_t>((id >> 2) / static_cast<uint32_t>(d.batch));
+                    sb = __float_as_uint(sc);
+                    if (d.score_by_id) d.score_by_id[id - slot_base] = sc;
+                    if (COUNT && d.count_by_id) d.count_by_id[id - slot_base] = ct;
+                }
+                // per round, the minimum (score bits, pose id) of the warp, then one atomic
+                unsigned long long kv = valid ? ((static_cast<unsigned long long>(sb) << 32) | id) : ~0ull;
+                bool pending = valid;
+                while (__any_sync(0xffffffffu, pending)) {
+                    const int first = __ffs(__ballot_sync(0xffffffffu, pending)) - 1;
+                    const uint32_t r0 = __shfl_sync(0xffffffffu, rd, first);
+                    unsigned long long v2 = (pending && rd == r0) ? kv : ~0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const unsigned long long u = __shfl_xor_sync(0xffffffffu, v2, o);
+                        v2 = u < v2 ? u : v2;
+                    }
+                    if (lane == first) atomicMin(reinterpret_cast<unsigned long long*>(&d.round_best[r0]), v2);
+                    if (rd == r0) pending = false;
+                }
+            }
+        }
+        base += static_cast<uint32_t>(nblk);
+    }
+    // every MMA completed before the epilogue read its accumulator
+    tc_fence_before();
+    __syncthreads();
+    if (warp == WMMA) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, kTcCols);
+    }
+}
+
 // tensor-core scoring variants: records per MMA x epilogue groups x bf16 or TF32 pieces
 struct TcVariant {
     int nb, ng;
@@ -1979,17 +2356,26 @@ struct TcVariant {
     size_t smem;
     void (*fn)(ScoreParams);
     void (*fn_count)(ScoreParams);
+    int poses;  // poses per work item
+    int mode;   // QueryDesc::tc_mode of the operand rows it reads
 };
 #define IMLOC_TC_VARIANT(NB, NG, BF)                                                              \
     {NB, NG, BF, TcShape<NB, NG>::kThreads, TcShape<NB, NG>::kSmem, k_score_tc<NB, NG, BF, false>, \
-     k_score_tc<NB, NG, BF, true>}
+     k_score_tc<NB, NG, BF, true>, kTcPoses, BF ? 1 : 0}
+#define IMLOC_TCR_VARIANT(NG, NBUF, PARTS, PIPE)                                                         \
+    {kTcrRecs, NG, true, TcrShape<NG, NBUF>::kThreads, TcrShape<NG, NBUF>::kSmem,                          \
+     k_score_tcr<NG, NBUF, PARTS, PIPE, false>, k_score_tcr<NG, NBUF, PARTS, PIPE, true>, TcrShape<NG, NBUF>::kPoses, 2}
 static const TcVariant kTcVariants[] = {
-    IMLOC_TC_VARIANT(80, 5, true),    // 0: 80-record blocks (2 TMEM buffers), 5 groups x 16 records, bf16 pieces
-    IMLOC_TC_VARIANT(128, 4, true),   // 1: 128-record blocks (1 buffer), 4 groups x 32 records, bf16 pieces
-    IMLOC_TC_VARIANT(80, 5, false),   // 2: as 0 with TF32 pieces (3 K steps)
-    IMLOC_TC_VARIANT(64, 4, true),    // 3: 64-record blocks (2 buffers), 4 groups x 16 records, bf16 pieces
+    // records on the M side (128-record blocks x 16 NG-pose items, bf16 pieces, 2 accumulator buffers)
+    IMLOC_TCR_VARIANT(5, 2, 4, true),   // 0: 80-pose items, accumulators read in quarters, the next in flight
+    IMLOC_TCR_VARIANT(5, 2, 2, false),  // 1: 80-pose items, read in halves
+    IMLOC_TCR_VARIANT(4, 2, 1, false),  // 2: 64-pose items, read whole (16 columns per row)
+    // poses on the M side (128-pose tiles)
+    IMLOC_TC_VARIANT(80, 5, true),      // 3: 80-record blocks (2 TMEM buffers), 5 groups x 16 records, bf16 pieces
+    IMLOC_TC_VARIANT(80, 5, false),     // 4: as 3 with TF32 pieces (3 K steps)
 };
 #undef IMLOC_TC_VARIANT
+#undef IMLOC_TCR_VARIANT
 constexpr int kNumTcVariants = sizeof(kTcVariants) / sizeof(kTcVariants[0]);
 
 // score kernel variants the autotuner chooses from (same results, different speed)
@@ -2258,13 +2644,13 @@ int run_step(imloc_ctx* ctx, const StepBuffers& b, int nq, int n_init, int64_t t
         prof.end();
     } else if (b.tc && !fuse) {
         // projections on the tensor cores: one persistent CTA per SM
-        rc = launch_tiles(ctx, b, nq, kTcPoses, stream);
-        if (rc != IMLOC_OK) return rc;
         const TcVariant& TV = kTcVariants[tc_variant(ctx)];
+        rc = launch_tiles(ctx, b, nq, TV.poses, stream);
+        if (rc != IMLOC_OK) return rc;
         auto kern = want_counts ? TV.fn_count : TV.fn;
         IMLOC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(TV.smem)));
         const int grid = static_cast<int>(
-            std::min<int64_t>(std::max(1, ctx->sm_count), max_items_of(total_samples, nq, kTcPoses)));
+            std::min<int64_t>(std::max(1, ctx->sm_count), max_items_of(total_samples, nq, TV.poses)));
         ProfScope prof(ctx, stream, "k_score_tc");
         kern<<<grid, TV.threads, TV.smem, stream>>>(scp);
         IMLOC_CUDA_TRY(cudaGetLastError());
@@ -2439,7 +2825,7 @@ int ransac_impl(imloc_ctx* ctx, int nq, const HostQuery* hq, cudaStream_t stream
         d.inject = h.inject ? 1 : 0;
         const int64_t slots = std::max<int64_t>(1, max_wave_samples[q] * 4);
         d.subset = static_cast<ScorePair*>(ws_alloc(ctx, sizeof(ScorePair) * ((std::max(1, o.max_score_corr) + 1) / 2)));
-        d.tc_bf16 = kTcVariants[tc_variant(ctx)].bf ? 1 : 0;
+        d.tc_mode = kTcVariants[tc_variant(ctx)].mode;
         if (bf16_on) {
             d.score_bf16 = 1;
             d.subset_b = static_cast<ScorePairB*>(

@@ -121,6 +121,32 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16_nowait(uint32_t taddr, uint32
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+// 32 lanes x 8 consecutive 32-bit columns, without waiting (valid after tmem_wait_ld())
+__device__ __forceinline__ void tmem_ld_32x32b_x8_nowait(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+// 32 lanes x 4 consecutive 32-bit columns, without waiting (valid after tmem_wait_ld())
+__device__ __forceinline__ void tmem_ld_32x32b_x4_nowait(uint32_t taddr, uint32_t (&r)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+}
+// W = 4, 8 or 16 columns
+template <int W>
+__device__ __forceinline__ void tmem_ld_nowait(uint32_t taddr, uint32_t (&r)[W]) {
+    if constexpr (W == 4) tmem_ld_32x32b_x4_nowait(taddr, r);
+    else if constexpr (W == 8) tmem_ld_32x32b_x8_nowait(taddr, r);
+    else tmem_ld_32x32b_x16_nowait(taddr, r);
+}
+// After tmem_wait_ld(): ties the loaded registers to a point after the wait, so
+// that no use of them can be scheduled before it.
+template <int W>
+__device__ __forceinline__ void tmem_regs_ready(uint32_t (&r)[W]) {
+#pragma unroll
+    for (int i = 0; i < W; ++i) asm volatile("" : "+r"(r[i]));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {

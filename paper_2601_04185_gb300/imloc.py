@@ -341,7 +341,7 @@ class Context:
 
     def set_scoring(self, kernel: int = -1, tc_variant: int = -1):
         """Scoring kernel of later RANSAC calls: -1 by call size, 0 the FP32
-        kernel, 1 the tensor-core kernel; tc_variant -1 default, else 0-3."""
+        kernel, 1 the tensor-core kernel; tc_variant -1 default, else 0-4."""
         _check(self.lib.imloc_set_scoring(self.h, int(kernel), int(tc_variant)), "imloc_set_scoring")
 
     def score_config(self):

@@ -22,7 +22,9 @@ from gpu_helpers import pose_close, residuals, torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=[-1, 0, 1, 2], ids=["fp32", "tc-80rec-bf16", "tc-128rec-bf16", "tc-80rec-tf32"])
+@pytest.fixture(params=[-1, 0, 1, 2, 3, 4],
+                ids=["fp32", "tc-rec-m-80p-quarters", "tc-rec-m-80p-halves", "tc-rec-m-64p-whole", "tc-pose-m-bf16",
+                     "tc-pose-m-tf32"])
 def tc_ctx(request):
     c = imloc.Context(0, 1 << 30)
     if request.param < 0:
@@ -35,7 +37,7 @@ def tc_ctx(request):
 
 def test_set_scoring_rejects_bad_values():
     c = imloc.Context(0, 1 << 20)
-    for kernel, variant in ((2, -1), (-2, -1), (1, 4), (1, -2)):
+    for kernel, variant in ((2, -1), (-2, -1), (1, 5), (1, -2)):
         with pytest.raises(imloc.ImlocError):
             c.set_scoring(kernel, variant)
     c.set_scoring(-1, -1)
