@@ -422,6 +422,7 @@ template <typename ACC>
 __host__ __device__ constexpr int replay_threads() { return sizeof(ACC) == 4 ? 512 : 256; }
 constexpr int kMaxReplayThreads = 512;
 constexpr int kMaxReplayCluster = 8;
+constexpr int kReplayClusterChoices = 5;  // cluster sizes the replay tries (8, 6, 4, 2, 1)
 constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
 constexpr int kPassUnroll = 4;   // correspondences whose loads are in flight together per thread
 // shared memory of the stand-alone replay kernel (one CTA per SM) that caches
@@ -2487,14 +2488,15 @@ static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out)
     return IMLOC_OK;
 }
 
-// CTAs per query in the replay: the largest cluster (8, 4, 2, 1) of which all
-// nq can be resident at once (a query whose cluster waits for another to
-// finish adds a whole replay to the kernel time)
+// CTAs per query in the replay: the largest cluster (8, 6, 4, 2, 1) of which
+// all nq can be resident at once (a query whose cluster waits for another to
+// finish adds a whole replay to the kernel time).  With one CTA per SM, 16
+// clusters of 8 do not fit the GPCs of a 152-SM GB300 (15 do), 23 of 6 do.
 template <typename ACC>
 static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
-    static const int kCl[4] = {8, 4, 2, 1};
+    static const int kCl[kReplayClusterChoices] = {8, 6, 4, 2, 1};
     const int a = sizeof(ACC) == 8 ? 1 : 0;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kReplayClusterChoices; ++i) {
         int& occ = ctx->replay_occ[a][i];
         if (occ == 0) {
             int v = 0;
