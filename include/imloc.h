@@ -90,8 +90,8 @@ int imloc_score_config(const imloc_ctx* ctx, int32_t* threads, int32_t* poses_pe
  * variable IMLOC_SCORE_TC=0 or 1 overrides), 0 = the FP32 kernel, 1 = the
  * tensor-core kernel; tc_variant -1 = default (environment IMLOC_TC_VARIANT),
  * else 0, 1, 2 = records on the MMA's M side (128-record blocks against
- * items of 80, 80 and 64 poses; accumulators read in quarters with the next
- * one in flight, in halves, whole; bf16 pieces), 3 = poses on the M side
+ * items of 80, 80 and 64 poses; accumulators read in halves, in quarters
+ * with the next one in flight, whole; bf16 pieces), 3 = poses on the M side
  * (80-record blocks against 128-pose tiles, bf16 pieces), 4 = as 3 with TF32
  * pieces.  The continuous-batching
  * server always uses the FP32 kernel.  IMLOC_ERR_INVALID_ARG for a null

@@ -2025,8 +2025,8 @@ struct TcrShape {
     static constexpr uint32_t kBufCols = (3 * kPoses + 31) / 32 * 32;
     static_assert(NBUF >= 2 && NBUF * kBufCols <= kTcCols, "accumulator buffers fit the TMEM columns");
     static constexpr uint32_t kPTile = 3 * kPoses * 128;  // pose rows: 3 x kPoses rows of 128 bytes
-    static constexpr size_t kSmemNeed =
-        1024 + kPTile + kTcrStages * kTcrRStage + 2 * 4 * kPoses * 4 + (2 * kTcrStages + 2 * NBUF) * 8 + 16;
+    static constexpr size_t kSmemNeed = 1024 + 2 * kPTile + kTcrStages * kTcrRStage + 2 * 2 * 4 * kPoses * 4 +
+                                        (2 * kTcrStages + 2 * NBUF + 4) * 8 + 2 * 32 + 16;
     static constexpr size_t kSmem = kSmemNeed > 116 * 1024 ? kSmemNeed : 116 * 1024;
     static_assert(3 * kPoses <= 256 && (3 * kPoses) % 16 == 0 && kPTile % 1024 == 0, "MMA shape");
 };
@@ -2037,44 +2037,77 @@ __device__ __forceinline__ float fma_sat(float a, float b, float c) {
     return d;
 }
 
-// Rows u, v, z of pose j of query d (zero rows past nh) as bf16 split-piece
-// operand rows n = r P + t of the 128-byte-swizzled pose tile sP; u and v
-// scaled by inv_tau and carrying 2^-100 in K lane 24.  Kept out of line: it
-// runs once per item, and inlined its temporaries crowd the epilogue's
-// registers.
-__device__ __noinline__ void tcr_pose_rows(const QueryDesc& d, int j, int nh, int64_t slot_base, float inv_tau,
-                                           int t, int P, unsigned char* sP) {
-    float c12[12];
-    if (j < nh) {
-        const PoseF ps = d.slots[d.compact[j] - slot_base];
+// Rows u, v, z of the poses lane, lane + 32, lane + 64 (< P) of pose tile
+// `tile` of query d (zero rows past nh) as bf16 split-piece operand rows
+// n = r P + t of the 128-byte-swizzled pose tile sP; u and v scaled by
+// inv_tau and carrying 2^-100 in K lane 24.  Run by one warp; the pose
+// loads of all its poses are issued before any row is written.  Kept out of
+// line: inlined, its temporaries would crowd the kernel's registers.
+__device__ __noinline__ void tcr_pose_rows_warp(const QueryDesc& d, int tile, int nh, int64_t slot_base,
+                                                float inv_tau, int lane, int P, unsigned char* sP) {
+    constexpr int J = 3;  // poses per lane (P <= 96)
+    int id[J];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            c12[c] = (d.fx * ps.R[c] + d.cx * ps.R[6 + c]) * inv_tau;
-            c12[4 + c] = (d.fy * ps.R[3 + c] + d.cy * ps.R[6 + c]) * inv_tau;
-            c12[8 + c] = ps.R[6 + c];
-        }
-        c12[3] = (d.fx * ps.t[0] + d.cx * ps.t[2]) * inv_tau;
-        c12[7] = (d.fy * ps.t[1] + d.cy * ps.t[2]) * inv_tau;
-        c12[11] = ps.t[2];
-    } else {
-#pragma unroll
-        for (int c = 0; c < 12; ++c) c12[c] = 0.f;
+    for (int j = 0; j < J; ++j) {
+        const int t = lane + 32 * j, pj = tile * P + t;
+        id[j] = (t < P && pj < nh) ? d.compact[pj] : -1;
     }
+    PoseF ps[J];
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        uint4 ch[8];
-        tc_operand_row(c12 + 4 * r, true, true, ch);
-        if (r < 2) ch[3].x = kBf16Eps;  // K lane 24: 2^-100 x the records' 1
-        const int n = r * P + t;
-        uint4* row = reinterpret_cast<uint4*>(sP + (n >> 3) * 1024 + (n & 7) * 128);
+    for (int j = 0; j < J; ++j)
+        if (id[j] >= 0) ps[j] = d.slots[id[j] - slot_base];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) row[c ^ (n & 7)] = ch[c];  // the chunks of the two K steps
+    for (int j = 0; j < J; ++j) {
+        const int t = lane + 32 * j;
+        if (t >= P) break;
+        float c12[12];
+        if (id[j] >= 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                c12[c] = (d.fx * ps[j].R[c] + d.cx * ps[j].R[6 + c]) * inv_tau;
+                c12[4 + c] = (d.fy * ps[j].R[3 + c] + d.cy * ps[j].R[6 + c]) * inv_tau;
+                c12[8 + c] = ps[j].R[6 + c];
+            }
+            c12[3] = (d.fx * ps[j].t[0] + d.cx * ps[j].t[2]) * inv_tau;
+            c12[7] = (d.fy * ps[j].t[1] + d.cy * ps[j].t[2]) * inv_tau;
+            c12[11] = ps[j].t[2];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 12; ++c) c12[c] = 0.f;
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            uint4 ch[8];
+            tc_operand_row(c12 + 4 * r, true, true, ch);
+            if (r < 2) ch[3].x = kBf16Eps;  // K lane 24: 2^-100 x the records' 1
+            const int n = r * P + t;
+            uint4* row = reinterpret_cast<uint4*>(sP + (n >> 3) * 1024 + (n & 7) * 128);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) row[c ^ (n & 7)] = ch[c];  // the chunks of the two K steps
+        }
     }
 }
+
+// One work item of k_score_tcr, decoded by the producer warp for the others.
+struct __align__(8) TcrItem {
+    int64_t slot_base;  // first pose slot of the query's wave
+    int32_t item;       // >= the item count: no more items
+    int32_t q, tile, active, nblk, nh;
+};
 
 // PARTS: the epilogue reads a block's accumulators for its 16 poses in PARTS
 // parts of 16 / PARTS poses (fewer registers of accumulator values live);
 // PIPE: the next part's load is in flight while a part is computed.
+// Work items flow through a two-slot queue in shared memory: the producer
+// warp takes the next item from the global counter as soon as it has issued
+// the record copies of the current one, decodes it, writes its pose rows
+// into the slot's pose buffer and publishes it (ifull); the MMA warp and the
+// epilogue warps take items from the queue in order, each at its own pace,
+// and free a slot (iempty) once they have read it; the MMA warp's commit
+// frees it only when the item's MMAs, which read the slot's pose rows, have
+// completed.  So the next item's decoding, pose rows and first copies
+// overlap the current item, and its first MMAs the current item's
+// end-of-item reduction.
 template <int NG, int NBUF, int PARTS, bool PIPE, bool COUNT>
 __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(const __grid_constant__ ScoreParams p) {
     using TS = TcrShape<NG, NBUF>;
@@ -2086,16 +2119,18 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
     extern __shared__ __align__(1024) unsigned char tcr_smem_raw[];
     unsigned char* smem =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(tcr_smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* sP = smem;                     // pose rows (B operand)
-    unsigned char* sR = sP + TS::kPTile;          // ring of record operand blocks (A operand)
-    float* s_part = reinterpret_cast<float*>(sR + S * kTcrRStage);  // [4][P] per warp quarter
-    int* s_cntp = reinterpret_cast<int*>(s_part + 4 * P);            // [4][P]
-    uint64_t* full = reinterpret_cast<uint64_t*>(s_cntp + 4 * P);
+    unsigned char* sP = smem;                     // pose rows (B operand) of the two queue slots
+    unsigned char* sR = sP + 2 * TS::kPTile;      // ring of record operand blocks (A operand)
+    float* s_part = reinterpret_cast<float*>(sR + S * kTcrRStage);  // [2 slots][4 warp quarters][P]
+    int* s_cntp = reinterpret_cast<int*>(s_part + 2 * 4 * P);        // [2][4][P]
+    uint64_t* full = reinterpret_cast<uint64_t*>(s_cntp + 2 * 4 * P);
     uint64_t* empty = full + S;
     uint64_t* tfull = empty + S;
     uint64_t* tempty = tfull + NBUF;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + NBUF);
-    int* s_item = reinterpret_cast<int*>(tmem_slot + 1);
+    uint64_t* ifull = tempty + NBUF;
+    uint64_t* iempty = ifull + 2;
+    TcrItem* s_info = reinterpret_cast<TcrItem*>(iempty + 2);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(s_info + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -2106,6 +2141,11 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], WMMA * 32);  // every epilogue thread, once it has loaded the buffer
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&ifull[k], 1);          // the producer, once the slot's item and pose rows are written
+            mbar_init(&iempty[k], WMMA + 1);  // every epilogue warp once it has read the slot, and the MMA
+                                              // warp once the item's MMAs have completed
         }
         mbar_fence_init();
     }
@@ -2118,42 +2158,74 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
     const int total_tiles = p.tile_prefix[p.nq];
-    uint32_t base = 0;  // record blocks of the earlier items of this CTA (ring and buffer positions)
 
-    for (;;) {
-        if (tid == 0) *s_item = static_cast<int>(atomicAdd(p.work_counter, 1u));
-        __syncthreads();  // also: every MMA of the previous item has completed (its epilogue consumed them)
-        const int item = *s_item;
-        if (item >= total_tiles) break;
-        int lo = 0, hi = p.nq - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (p.tile_prefix[mid] <= item) lo = mid;
-            else hi = mid - 1;
+    if (warp == WPROD) {
+        // ---- producer: items into the queue, record blocks into the ring ----
+        uint32_t base = 0;  // record blocks of the earlier items of this CTA (ring positions)
+        for (int it = 0;; ++it) {
+            const int k = it & 1;
+            mbar_wait_bounded(&iempty[k], ((it >> 1) & 1u) ^ 1u, p.err);
+            int item = 0;
+            if (lane == 0) item = static_cast<int>(atomicAdd(p.work_counter, 1u));
+            item = __shfl_sync(0xffffffffu, item, 0);
+            TcrItem I;
+            I.item = item;
+            I.q = I.tile = I.active = I.nblk = I.nh = 0;
+            I.slot_base = 0;
+            if (item < total_tiles) {
+                int lo = 0, hi = p.nq - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.tile_prefix[mid] <= item) lo = mid;
+                    else hi = mid - 1;
+                }
+                I.q = lo;
+                I.tile = item - p.tile_prefix[lo];
+                I.active = I.tile < p.ntiles[lo] ? 1 : 0;
+                const int m = I.active ? p.qs[lo].m : 0;
+                I.nblk = (m + kTcrRecs - 1) / kTcrRecs;
+                I.nh = p.n_hyp[lo];
+                I.slot_base = 4 * p.wq[lo].s_begin;
+            }
+            if (I.active) {
+                const QueryDesc& d = p.qd[I.q];
+                tcr_pose_rows_warp(d, I.tile, I.nh, I.slot_base, 1.0f / sqrtf(d.tau2), lane, P, sP + k * TS::kPTile);
+                // the generic-proxy writes become visible to the tensor core's reads
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            if (lane == 0) s_info[k] = I;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ifull[k]);
+            if (item >= total_tiles) break;
+            if (I.active) {
+                const QueryDesc& d = p.qd[I.q];
+                for (int b = 0; b < I.nblk; ++b) {
+                    const uint32_t gb = base + b;
+                    const uint32_t st = gb % S;
+                    mbar_wait_bounded(&empty[st], ((gb / S) & 1u) ^ 1u, p.err);
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&full[st], kTcrRStage);
+                        bulk_g2s(sR + st * kTcrRStage, d.tc_rec + static_cast<int64_t>(b) * kTcrRecs * 8, kTcrRStage,
+                                 &full[st]);
+                    }
+                    __syncwarp();
+                }
+            }
+            base += static_cast<uint32_t>(I.nblk);
         }
-        const int q = lo;
-        const int tile = item - p.tile_prefix[q];
-        const QueryDesc& d = p.qd[q];
-        const bool active = tile < p.ntiles[q];
-        const int m = active ? p.qs[q].m : 0;
-        const int nh = p.n_hyp[q];
-        const int nblk = (m + kTcrRecs - 1) / kTcrRecs;
-        const int64_t slot_base = 4 * p.wq[q].s_begin;
-        const float tau2 = d.tau2;
-        const float inv_tau = 1.0f / sqrtf(tau2);
-
-        if (active && warp < 4) {
-            // pose rows of this item: thread tid < P writes rows tid, P + tid, 2 P + tid (u, v, z)
-            if (tid < P) tcr_pose_rows(d, tile * P + tid, nh, slot_base, inv_tau, tid, P, sP);
-            // the generic-proxy writes become visible to the tensor core's reads
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("bar.arrive 2, 160;" ::: "memory");
-        } else if (active && warp == WMMA) {
-            // the whole warp walks the blocks (it stays converged); one elected lane issues
-            asm volatile("bar.sync 2, 160;" ::: "memory");  // pose rows written
-            constexpr uint32_t idesc = umma_idesc_bf16(kTcrRecs, 3 * P);
-            const uint64_t rdesc = umma_desc_k_sw128(smem_u32(sR)), pdesc = umma_desc_k_sw128(smem_u32(sP));
-            for (int b = 0; b < nblk; ++b) {
+    } else if (warp == WMMA) {
+        // ---- MMA warp: the whole warp walks the blocks (it stays converged); one elected lane issues ----
+        constexpr uint32_t idesc = umma_idesc_bf16(kTcrRecs, 3 * P);
+        const uint64_t rdesc = umma_desc_k_sw128(smem_u32(sR));
+        uint32_t base = 0;
+        int it = 0;
+        for (;; ++it) {
+            const int k = it & 1;
+            mbar_wait_bounded(&ifull[k], (it >> 1) & 1u, p.err);
+            const TcrItem I = s_info[k];
+            if (I.item >= total_tiles) break;
+            const uint64_t pdesc = umma_desc_k_sw128(smem_u32(sP + k * TS::kPTile));
+            for (int b = 0; b < I.nblk; ++b) {
                 const uint32_t gb = base + b;
                 const uint32_t st = gb % S, buf = gb % NBUF;
                 mbar_wait_bounded(&tempty[buf], ((gb / NBUF) & 1u) ^ 1u, p.err);
@@ -2170,21 +2242,31 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
                 }
                 __syncwarp();
             }
-        } else if (active && warp == WPROD) {
-            for (int b = 0; b < nblk; ++b) {
-                const uint32_t gb = base + b;
-                const uint32_t st = gb % S;
-                mbar_wait_bounded(&empty[st], ((gb / S) & 1u) ^ 1u, p.err);
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[st], kTcrRStage);
-                    bulk_g2s(sR + st * kTcrRStage, d.tc_rec + static_cast<int64_t>(b) * kTcrRecs * 8, kTcrRStage,
-                             &full[st]);
-                }
-                __syncwarp();
+            // the slot is free once every MMA issued so far (those that read its pose rows) has completed
+            if (elect_one()) {
+                if (I.nblk > 0) umma_commit(&iempty[k]);
+                else mbar_arrive(&iempty[k]);
             }
+            __syncwarp();
+            base += static_cast<uint32_t>(I.nblk);
         }
-        if (active && warp < WMMA) {
-            const int g = warp >> 2, wq = warp & 3;
+        // the last items' commits have landed before the CTA (and its barriers) can go
+        for (int l = it - 2 > 0 ? it - 2 : 0; l < it; ++l) mbar_wait_bounded(&iempty[l & 1], (l >> 1) & 1u, p.err);
+    } else if (warp < WMMA) {
+        // ---- epilogue warps ----
+        const int g = warp >> 2, wq = warp & 3;
+        const uint32_t lane_addr = tmem_base + (static_cast<uint32_t>(wq * 32) << 16) + 16 * g;
+        uint32_t base = 0;
+        for (int it = 0;; ++it) {
+            const int k = it & 1;
+            mbar_wait_bounded(&ifull[k], (it >> 1) & 1u, p.err);
+            const TcrItem I = s_info[k];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&iempty[k]);
+            if (I.item >= total_tiles) break;
+            if (!I.active) continue;
+            const QueryDesc& d = p.qd[I.q];
+            const int nblk = I.nblk;
             // running sums of this lane's records for poses 16 g .. 16 g + 15 (pairs of poses)
             uint64_t acc2[8];
             uint32_t cnt2[8];  // with COUNT: inliers of poses 2i (low 16 bits) and 2i + 1 (high 16 bits)
@@ -2193,7 +2275,6 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
                 acc2[i] = f2_pack(0.f, 0.f);
                 cnt2[i] = 0u;
             }
-            const uint32_t lane_addr = tmem_base + (static_cast<uint32_t>(wq * 32) << 16) + 16 * g;
             // this thread's record of every block: {-x / tau, -y / tau, w tau^2, 0}
             const float* te = reinterpret_cast<const float*>(d.tc_e + wq * 32 + lane);
             float ex = __ldg(te), ey = __ldg(te + 1), ew = __ldg(te + 2);  // block 0
@@ -2301,25 +2382,28 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
             v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
             if (COUNT) c[0] += __shfl_xor_sync(0xffffffffu, c[0], 1);
             if ((lane & 1) == 0) {
-                s_part[wq * P + 16 * g + (lane >> 1)] = v[0];
-                if (COUNT) s_cntp[wq * P + 16 * g + (lane >> 1)] = c[0];
+                s_part[(k * 4 + wq) * P + 16 * g + (lane >> 1)] = v[0];
+                if (COUNT) s_cntp[(k * 4 + wq) * P + 16 * g + (lane >> 1)] = c[0];
             }
             asm volatile("bar.sync 1, %0;" ::"n"(WMMA * 32) : "memory");
             if (warp < (P + 31) / 32) {
                 const int e = tid;  // pose of the tile
-                const int j = tile * P + e;
-                const bool valid = e < P && j < nh;
+                const int j = I.tile * P + e;
+                const bool valid = e < P && j < I.nh;
                 uint32_t id = 0xffffffffu, rd = 0xffffffffu, sb = 0xffffffffu;
                 if (valid) {
                     // the four warp quarters (records 0-31, 32-63, ... of every block) in order
-                    const float sc = ((s_part[e] + s_part[P + e]) + s_part[2 * P + e]) + s_part[3 * P + e];
+                    const float* sp = s_part + k * 4 * P;
+                    const float sc = ((sp[e] + sp[P + e]) + sp[2 * P + e]) + sp[3 * P + e];
                     const int ct =
-                        COUNT ? s_cntp[e] + s_cntp[P + e] + s_cntp[2 * P + e] + s_cntp[3 * P + e] : 0;
+                        COUNT ? s_cntp[k * 4 * P + e] + s_cntp[(k * 4 + 1) * P + e] + s_cntp[(k * 4 + 2) * P + e] +
+                                    s_cntp[(k * 4 + 3) * P + e]
+                                  : 0;
                     id = static_cast<uint32_t>(d.compact[j]);
                     rd = static_cast<uint32_t>((id >> 2) / static_cast<uint32_t>(d.batch));
                     sb = __float_as_uint(sc);
-                    if (d.score_by_id) d.score_by_id[id - slot_base] = sc;
-                    if (COUNT && d.count_by_id) d.count_by_id[id - slot_base] = ct;
+                    if (d.score_by_id) d.score_by_id[id - I.slot_base] = sc;
+                    if (COUNT && d.count_by_id) d.count_by_id[id - I.slot_base] = ct;
                 }
                 // per round, the minimum (score bits, pose id) of the warp, then one atomic
                 unsigned long long kv = valid ? ((static_cast<unsigned long long>(sb) << 32) | id) : ~0ull;
@@ -2337,8 +2421,8 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
                     if (rd == r0) pending = false;
                 }
             }
+            base += static_cast<uint32_t>(nblk);
         }
-        base += static_cast<uint32_t>(nblk);
     }
     // every MMA completed before the epilogue read its accumulator
     tc_fence_before();
@@ -2368,8 +2452,8 @@ struct TcVariant {
      k_score_tcr<NG, NBUF, PARTS, PIPE, false>, k_score_tcr<NG, NBUF, PARTS, PIPE, true>, TcrShape<NG, NBUF>::kPoses, 2}
 static const TcVariant kTcVariants[] = {
     // records on the M side (128-record blocks x 16 NG-pose items, bf16 pieces, 2 accumulator buffers)
-    IMLOC_TCR_VARIANT(5, 2, 4, true),   // 0: 80-pose items, accumulators read in quarters, the next in flight
-    IMLOC_TCR_VARIANT(5, 2, 2, false),  // 1: 80-pose items, read in halves
+    IMLOC_TCR_VARIANT(5, 2, 2, false),  // 0: 80-pose items, accumulators read in halves
+    IMLOC_TCR_VARIANT(5, 2, 4, true),   // 1: 80-pose items, read in quarters, the next quarter in flight
     IMLOC_TCR_VARIANT(4, 2, 1, false),  // 2: 64-pose items, read whole (16 columns per row)
     // poses on the M side (128-pose tiles)
     IMLOC_TC_VARIANT(80, 5, true),      // 3: 80-record blocks (2 TMEM buffers), 5 groups x 16 records, bf16 pieces

@@ -23,7 +23,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(params=[-1, 0, 1, 2, 3, 4],
-                ids=["fp32", "tc-rec-m-80p-quarters", "tc-rec-m-80p-halves", "tc-rec-m-64p-whole", "tc-pose-m-bf16",
+                ids=["fp32", "tc-rec-m-80p-halves", "tc-rec-m-80p-quarters", "tc-rec-m-64p-whole", "tc-pose-m-bf16",
                      "tc-pose-m-tf32"])
 def tc_ctx(request):
     c = imloc.Context(0, 1 << 30)
