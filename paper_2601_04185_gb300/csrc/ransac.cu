@@ -460,7 +460,7 @@ struct ReplaySmem {
     float P[12];
     int flag;
     int skip;             // rounds passed over by the last scan
-    float* stg;           // per-thread point cache (null: none): field f, slot j at stg[(f * stg_cap + j) * NT + tid]
+    float* stg;           // per-thread point cache (null: none): field f, slot j at stg[(f * stg_cap + j) * (NT + 1) + tid]
     int stg_cap;          // slots per thread
     int sub_staged;       // the cache holds this thread's subset records (else: fixed points or nothing)
     int32_t fixcnt[kMaxReplayThreads];  // fixed inliers of each thread (final refinement)
@@ -479,6 +479,9 @@ __device__ __forceinline__ void pass_pose_warp(ReplaySmem& S, const double* R, c
     const int l = threadIdx.x & 31;
     if (l < 12) S.P[l] = static_cast<float>(l < 9 ? R[l] : t[l - 9]);
 }
+
+__device__ __forceinline__ float acc_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double acc_fma(double a, double b, double c) { return fma(a, b, c); }
 
 template <int MODE, typename ACC, int NT>
 __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& cluster, int rank, int CL, int& slot) {
@@ -505,43 +508,78 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     // only the fixed inliers among them, whose indices the kFinInit pass
     // recorded at the thread's own positions i0 + k stride (k-th inlier)
     int32_t* fixidx = d.fixidx + off;
-    const int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
+    int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
+    // kFin: the warp's fixed points (lane l owns fixcnt of them, in its own
+    // cache column / positions) are spread evenly over its lanes: lane l takes
+    // the warp's points l, l + 32, ... in (owner lane, k-th point) order, so a
+    // warp runs ceil(total / 32) points instead of its busiest lane's count
+    int fix_pre = 0, fix_tot = 0;
+    if constexpr (MODE == kFin) {
+        const int cnt = S.fixcnt[tid];
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        fix_pre = incl - cnt;
+        fix_tot = __shfl_sync(0xffffffffu, incl, 31);
+        nj = (fix_tot + 31) / 32;  // warp-uniform
+    }
     // the thread's point cache in shared memory: the first J points of the
     // subset (cached by the first subset pass of the call) or of the fixed set
     // (cached by kFinInit); the rest come from global memory
     const int64_t J = S.stg_cap;
+    constexpr int64_t SP = NT + 1;  // row stride of the cache: rows of one column fall in different banks
     float* stg = S.stg;
     const bool sub_cached = kSub && S.sub_staged;
     int64_t nfix = 0;
     for (int64_t j0 = 0; j0 < nj; j0 += U) {
         float X[U], Y[U], Z[U], w[U], x[U], y[U];
-        int64_t idx[U];
+        int64_t idx[U], jr[U];  // point index (or 0 if cached), row in the cache column
+        int col[U];             // cache column (owner thread)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
-            // in the kFin passes: an index this thread wrote in kFinInit (a coherent load)
-            idx[u] = j >= nj ? -1
-                             : (MODE == kFin ? (j < J ? 0 : static_cast<int64_t>(fixidx[i0 + j * stride]))
-                                             : i0 + j * stride);
+            jr[u] = j;
+            col[u] = tid;
+            if constexpr (MODE == kFin) {
+                // owner lane of the warp's point v: the largest o with prefix(o) <= v
+                const int v = lane + 32 * static_cast<int>(j);
+                int lo = 0;  // prefix(0) = 0 <= v; lo + step stays <= 31
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1)
+                    if (__shfl_sync(0xffffffffu, fix_pre, lo + step) <= v) lo += step;
+                const int po = __shfl_sync(0xffffffffu, fix_pre, lo);
+                jr[u] = v - po;
+                col[u] = (warp << 5) + lo;
+                // an index the owner wrote in kFinInit (a coherent load)
+                const int64_t i0o = static_cast<int64_t>(rank) * NT + col[u];
+                idx[u] = (j >= nj || v >= fix_tot) ? -1
+                                                   : (jr[u] < J ? 0 : static_cast<int64_t>(fixidx[i0o + jr[u] * stride]));
+            } else {
+                idx[u] = j >= nj ? -1 : i0 + j * stride;
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t j = j0 + u;
+            const int64_t j = jr[u];
+            const int c = col[u];
             const int64_t i = idx[u];
             X[u] = Y[u] = Z[u] = w[u] = x[u] = y[u] = 0.f;
             if (i < 0) continue;
             const bool cached = (MODE == kFin || sub_cached) && j < J;
             if (cached) {
-                X[u] = stg[(0 * J + j) * NT + tid]; Y[u] = stg[(1 * J + j) * NT + tid];
-                Z[u] = stg[(2 * J + j) * NT + tid]; w[u] = stg[(3 * J + j) * NT + tid];
-                x[u] = stg[(4 * J + j) * NT + tid]; y[u] = stg[(5 * J + j) * NT + tid];
+                X[u] = stg[(0 * J + j) * SP + c]; Y[u] = stg[(1 * J + j) * SP + c];
+                Z[u] = stg[(2 * J + j) * SP + c]; w[u] = stg[(3 * J + j) * SP + c];
+                x[u] = stg[(4 * J + j) * SP + c]; y[u] = stg[(5 * J + j) * SP + c];
             } else if (kSub) {
                 const SubsetRecord c = subset_record(d.subset, i);
                 X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
                 if (j < J) {
-                    stg[(0 * J + j) * NT + tid] = X[u]; stg[(1 * J + j) * NT + tid] = Y[u];
-                    stg[(2 * J + j) * NT + tid] = Z[u]; stg[(3 * J + j) * NT + tid] = w[u];
-                    stg[(4 * J + j) * NT + tid] = x[u]; stg[(5 * J + j) * NT + tid] = y[u];
+                    stg[(0 * J + j) * SP + tid] = X[u]; stg[(1 * J + j) * SP + tid] = Y[u];
+                    stg[(2 * J + j) * SP + tid] = Z[u]; stg[(3 * J + j) * SP + tid] = w[u];
+                    stg[(4 * J + j) * SP + tid] = x[u]; stg[(5 * J + j) * SP + tid] = y[u];
                 }
             } else {
                 X[u] = __ldg(d.X + off + i); Y[u] = __ldg(d.Y + off + i); Z[u] = __ldg(d.Z + off + i);
@@ -577,9 +615,9 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
                 const bool in_set = (MODE == kFin) || inl;
                 if (MODE == kFinInit && inl) {
                     if (nfix < J) {
-                        stg[(0 * J + nfix) * NT + tid] = X[u]; stg[(1 * J + nfix) * NT + tid] = Y[u];
-                        stg[(2 * J + nfix) * NT + tid] = Z[u]; stg[(3 * J + nfix) * NT + tid] = w[u];
-                        stg[(4 * J + nfix) * NT + tid] = x[u]; stg[(5 * J + nfix) * NT + tid] = y[u];
+                        stg[(0 * J + nfix) * SP + tid] = X[u]; stg[(1 * J + nfix) * SP + tid] = Y[u];
+                        stg[(2 * J + nfix) * SP + tid] = Z[u]; stg[(3 * J + nfix) * SP + tid] = w[u];
+                        stg[(4 * J + nfix) * SP + tid] = x[u]; stg[(5 * J + nfix) * SP + tid] = y[u];
                     } else {
                         fixidx[i0 + nfix * stride] = static_cast<int32_t>(i);
                     }
@@ -597,13 +635,23 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
                 const float dvy = fy * iz, dvz = -fy * yc * iz * iz;
                 const float Ju[6] = {duz * yc, dux * zc - duz * xc, -dux * yc, dux, 0.f, duz};
                 const float Jv[6] = {-dvy * zc + dvz * yc, -dvz * xc, dvy * xc, 0.f, dvy, dvz};
+                // H += w (Ju Ju^T + Jv Jv^T), g += w (Ju ru + Jv rv) as FMA chains; Ju[4] and Jv[3] are
+                // zero, so their terms are left out (H[3][4] stays 0)
                 int k = 0;
 #pragma unroll
                 for (int a = 0; a < 6; ++a) {
                     const float wa = wt * Ju[a], wb = wt * Jv[a];
 #pragma unroll
-                    for (int b = a; b < 6; ++b) acc[k++] += ACC(wa) * ACC(Ju[b]) + ACC(wb) * ACC(Jv[b]);
-                    acc[21 + a] += ACC(wa) * ACC(ru) + ACC(wb) * ACC(rv);
+                    for (int b = a; b < 6; ++b) {
+                        ACC t = acc[k];
+                        if (a != 3 && b != 3) t = acc_fma(ACC(wb), ACC(Jv[b]), t);
+                        if (a != 4 && b != 4) t = acc_fma(ACC(wa), ACC(Ju[b]), t);
+                        acc[k++] = t;
+                    }
+                    ACC t = acc[21 + a];
+                    if (a != 3) t = acc_fma(ACC(wb), ACC(rv), t);
+                    if (a != 4) t = acc_fma(ACC(wa), ACC(ru), t);
+                    acc[21 + a] = t;
                 }
             }
         }
@@ -1072,7 +1120,7 @@ __global__ void __launch_bounds__(replay_threads<ACC>()) k_replay(const __grid_c
     constexpr int NT = replay_threads<ACC>();
     if (threadIdx.x == 0) {
         S.stg = replay_stage;
-        S.stg_cap = kReplayStageBytes / (6 * static_cast<int>(sizeof(float)) * NT);
+        S.stg_cap = kReplayStageBytes / (6 * static_cast<int>(sizeof(float)) * (NT + 1));
     }
     cg::cluster_group cluster = cg::this_cluster();
     const int CL = static_cast<int>(cluster.num_blocks());
