@@ -508,24 +508,7 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     // only the fixed inliers among them, whose indices the kFinInit pass
     // recorded at the thread's own positions i0 + k stride (k-th inlier)
     int32_t* fixidx = d.fixidx + off;
-    int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
-    // kFin: the warp's fixed points (lane l owns fixcnt of them, in its own
-    // cache column / positions) are spread evenly over its lanes: lane l takes
-    // the warp's points l, l + 32, ... in (owner lane, k-th point) order, so a
-    // warp runs ceil(total / 32) points instead of its busiest lane's count
-    int fix_pre = 0, fix_tot = 0;
-    if constexpr (MODE == kFin) {
-        const int cnt = S.fixcnt[tid];
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        fix_pre = incl - cnt;
-        fix_tot = __shfl_sync(0xffffffffu, incl, 31);
-        nj = (fix_tot + 31) / 32;  // warp-uniform
-    }
+    const int64_t nj = (MODE == kFin) ? static_cast<int64_t>(S.fixcnt[tid]) : (n > i0 ? (n - i0 + stride - 1) / stride : 0);
     // the thread's point cache in shared memory: the first J points of the
     // subset (cached by the first subset pass of the call) or of the fixed set
     // (cached by kFinInit); the rest come from global memory
@@ -536,43 +519,26 @@ __device__ void pass(ReplaySmem& S, const QueryDesc& d, cg::cluster_group& clust
     int64_t nfix = 0;
     for (int64_t j0 = 0; j0 < nj; j0 += U) {
         float X[U], Y[U], Z[U], w[U], x[U], y[U];
-        int64_t idx[U], jr[U];  // point index (or 0 if cached), row in the cache column
-        int col[U];             // cache column (owner thread)
+        int64_t idx[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int64_t j = j0 + u;
-            jr[u] = j;
-            col[u] = tid;
-            if constexpr (MODE == kFin) {
-                // owner lane of the warp's point v: the largest o with prefix(o) <= v
-                const int v = lane + 32 * static_cast<int>(j);
-                int lo = 0;  // prefix(0) = 0 <= v; lo + step stays <= 31
-#pragma unroll
-                for (int step = 16; step >= 1; step >>= 1)
-                    if (__shfl_sync(0xffffffffu, fix_pre, lo + step) <= v) lo += step;
-                const int po = __shfl_sync(0xffffffffu, fix_pre, lo);
-                jr[u] = v - po;
-                col[u] = (warp << 5) + lo;
-                // an index the owner wrote in kFinInit (a coherent load)
-                const int64_t i0o = static_cast<int64_t>(rank) * NT + col[u];
-                idx[u] = (j >= nj || v >= fix_tot) ? -1
-                                                   : (jr[u] < J ? 0 : static_cast<int64_t>(fixidx[i0o + jr[u] * stride]));
-            } else {
-                idx[u] = j >= nj ? -1 : i0 + j * stride;
-            }
+            // in the kFin passes: an index this thread wrote in kFinInit (a coherent load)
+            idx[u] = j >= nj ? -1
+                             : (MODE == kFin ? (j < J ? 0 : static_cast<int64_t>(fixidx[i0 + j * stride]))
+                                             : i0 + j * stride);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t j = jr[u];
-            const int c = col[u];
+            const int64_t j = j0 + u;
             const int64_t i = idx[u];
             X[u] = Y[u] = Z[u] = w[u] = x[u] = y[u] = 0.f;
             if (i < 0) continue;
             const bool cached = (MODE == kFin || sub_cached) && j < J;
             if (cached) {
-                X[u] = stg[(0 * J + j) * SP + c]; Y[u] = stg[(1 * J + j) * SP + c];
-                Z[u] = stg[(2 * J + j) * SP + c]; w[u] = stg[(3 * J + j) * SP + c];
-                x[u] = stg[(4 * J + j) * SP + c]; y[u] = stg[(5 * J + j) * SP + c];
+                X[u] = stg[(0 * J + j) * SP + tid]; Y[u] = stg[(1 * J + j) * SP + tid];
+                Z[u] = stg[(2 * J + j) * SP + tid]; w[u] = stg[(3 * J + j) * SP + tid];
+                x[u] = stg[(4 * J + j) * SP + tid]; y[u] = stg[(5 * J + j) * SP + tid];
             } else if (kSub) {
                 const SubsetRecord c = subset_record(d.subset, i);
                 X[u] = c.X; Y[u] = c.Y; Z[u] = c.Z; w[u] = c.w; x[u] = c.x; y[u] = c.y;
