@@ -1211,21 +1211,29 @@ def run_ours(args):
                 d_match_b[b][k].copy_(h_match[k], non_blocking=True)
         copied[b].record(copy_stream)
 
+    def e2e_steps(k, start_ev=None):
+        if start_ev is not None:
+            copy_stream.wait_event(start_ev)
+        else:
+            copy_stream.wait_stream(stream)
+        upload(0)
+        for i in range(k):
+            b = i % 2
+            if i + 1 < k:
+                if i >= 1:
+                    copy_stream.wait_event(consumed[1 - b])  # step i-1 is done with that buffer
+                upload(1 - b)
+            stream.wait_event(copied[b])
+            ctx.lift_batch(qb, d_views, d_match_b[b], out=corr, offsets=offsets, stream=stream, prepared=prep_b[b])
+            consumed[b].record(stream)
+            ctx.ransac_pnp_batch_async(corr, offsets, Ks, opts, results, stream=stream, prepared=prep_ransac)
+            h_results.copy_(results, non_blocking=True)
+
+    # untimed: both match buffers once (the library captures a launch graph per buffer on first use)
+    e2e_steps(max(2, args.warmup))
     torch.cuda.synchronize()
     t_start.record(stream)
-    copy_stream.wait_event(t_start)
-    upload(0)
-    for i in range(args.steps):
-        b = i % 2
-        if i + 1 < args.steps:
-            if i >= 1:
-                copy_stream.wait_event(consumed[1 - b])  # step i-1 is done with that buffer
-            upload(1 - b)
-        stream.wait_event(copied[b])
-        ctx.lift_batch(qb, d_views, d_match_b[b], out=corr, offsets=offsets, stream=stream, prepared=prep_b[b])
-        consumed[b].record(stream)
-        ctx.ransac_pnp_batch_async(corr, offsets, Ks, opts, results, stream=stream, prepared=prep_ransac)
-        h_results.copy_(results, non_blocking=True)
+    e2e_steps(args.steps, t_start)
     t_end.record(stream)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(t_start.elapsed_time(t_end) / 1e3, world)
