@@ -245,29 +245,39 @@ def oracle_queries(queries, hypotheses, threads):
     return time.perf_counter() - t0, pairs
 
 
+def c2_workload(nq):
+    """The C2 step's workload, as both arms name it."""
+    return (f"C2: {nq} queries/step x (lift of {N_VIEWS} views x {MATCHES_PER_PAIR} matches "
+            f"+ LO-RANSAC PnP, {HYPOTHESES} minimal sets, LO, Cauchy refinement)")
+
+
 def run_reference(args):
     rank, world, _ = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), 0)
     if rank != 0:
         return 0
     cores = os.cpu_count() or 1
-    # a step: one query per core, one round of 1,024 minimal sets (bounded CPU sample)
-    hyps = 1024
-    queries = make_queries(cores, 1000)
+    # the C2 step's own queries (same seeds, sizes and minimal sets as the GPU arm's step), one per host thread
+    nq = args.queries
+    queries = make_queries(nq, rank_seed(100, 0))
+    threads = min(cores, nq)
     for _ in range(args.warmup):
-        oracle_queries(queries[:1], hyps, 1)
+        oracle_queries(queries[:1], HYPOTHESES, 1)
     total_t, total_pairs = 0.0, 0
     for _ in range(args.steps):
-        t, p = oracle_queries(queries, hyps, cores)
+        t, p = oracle_queries(queries, HYPOTHESES, threads)
         total_t += t
         total_pairs += p
     v = total_pairs / total_t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"C2-shaped lift + LO-RANSAC PnP, FP64 CPU oracle, {cores} queries/step "
-                                   f"(one per core), {hyps} minimal sets each, LO + Cauchy refinement"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{cores} synthetic C2 queries per step, {hyps} minimal sets each"},
+            "config": {"workload": c2_workload(nq), "queries_per_step": nq,
+                       "matches_per_query": N_VIEWS * MATCHES_PER_PAIR, "depth": "1024x768 float32, 10 views/query",
+                       "hypotheses": HYPOTHESES, "score_corr_cap": 10000,
+                       "parallelism": f"FP64 CPU oracle, {threads} host threads (one query each)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"the C2 step's {nq} queries per step (lift + {HYPOTHESES} minimal sets + LO "
+                                       f"+ refinement), one per thread"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -1323,8 +1333,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total_s_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"C2: {nq} queries/step x (lift of {N_VIEWS} views x {MATCHES_PER_PAIR} matches "
-                               f"+ LO-RANSAC PnP, {HYPOTHESES} minimal sets, LO, Cauchy refinement)",
+        "config": {"workload": c2_workload(nq),
                    "queries_per_step": nq, "matches_per_query": N_VIEWS * MATCHES_PER_PAIR,
                    "depth": "1024x768 float32, 10 views/query", "hypotheses": HYPOTHESES, "score_corr_cap": 10000,
                    "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{world}"},
