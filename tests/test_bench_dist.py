@@ -63,7 +63,7 @@ def _reference_worker(rank, world, port, out):
     bench.make_queries = lambda n, seed: [None] * n
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
-        rc = bench.run_reference(argparse.Namespace(gpus=world, steps=2, warmup=3))
+        rc = bench.run_reference(argparse.Namespace(gpus=world, steps=2, warmup=3, queries=16))
     out[rank] = (rc, buf.getvalue(), len(called))
 
 
