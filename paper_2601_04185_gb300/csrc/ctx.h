@@ -36,9 +36,9 @@ struct imloc_ctx {
     int scoring_kernel = -1;
     int scoring_tc_variant = -1;
     float score_variant_ms = 0.f;
-    // co-resident clusters of the replay kernel (FP32 / FP64 accumulation x cluster size 8, 6, 4, 2, 1); 0 = not
+    // co-resident clusters of the replay kernel (FP32 / FP64 accumulation x cluster size 8 down to 1); 0 = not
     // queried
-    int replay_occ[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+    int replay_occ[2][8] = {};
     // tracing: CUDA events around every kernel launch while enabled
     bool prof_on = false;
     struct ProfRec { const char* name; cudaEvent_t a, b; };

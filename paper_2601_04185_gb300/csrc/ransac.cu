@@ -45,6 +45,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -318,7 +319,9 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                 }
                 float l1[4];
                 nsol = p3p_solve(y, d.polish ? yd : nullptr, X, sol, l1);
-                for (int k = 0; k < nsol; ++k) d.slots[4 * local + k] = sol[k];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < nsol) d.slots[4 * local + k] = sol[k];
             }
         } else if (d.triples) {
             d.triples[3 * local + 0] = -1;
@@ -422,7 +425,7 @@ template <typename ACC>
 __host__ __device__ constexpr int replay_threads() { return sizeof(ACC) == 4 ? 512 : 256; }
 constexpr int kMaxReplayThreads = 512;
 constexpr int kMaxReplayCluster = 8;
-constexpr int kReplayClusterChoices = 5;  // cluster sizes the replay tries (8, 6, 4, 2, 1)
+constexpr int kReplayClusterChoices = 8;  // cluster sizes the replay tries (8 down to 1)
 constexpr int kNV = 29;  // H (21, upper triangle), g (6), cost, count
 constexpr int kPassUnroll = 4;   // correspondences whose loads are in flight together per thread
 // shared memory of the stand-alone replay kernel (one CTA per SM) that caches
@@ -2292,9 +2295,11 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
             // this thread's record of every block: {-x / tau, -y / tau, w tau^2, 0}
             const float* te = reinterpret_cast<const float*>(d.tc_e + wq * 32 + lane);
             float ex = __ldg(te), ey = __ldg(te + 1), ew = __ldg(te + 2);  // block 0
-            for (int b = 0; b < nblk; ++b) {
+            // one block: accumulator buffer BUF (a compile-time constant, so that its
+            // TMEM addresses and barrier are loop-invariant)
+            auto do_block = [&](auto buf_c, int b) {
+                constexpr uint32_t buf = decltype(buf_c)::value;
                 const uint32_t gb = base + b;
-                const uint32_t buf = gb % NBUF;
                 // the next block's pixel and weight, in flight during this block
                 const float* tn = te + static_cast<int64_t>(b + 1 < nblk ? b + 1 : b) * (kTcrRecs * 4);
                 const float ex_n = __ldg(tn), ey_n = __ldg(tn + 1), ew_n = __ldg(tn + 2);
@@ -2366,6 +2371,25 @@ __global__ void __launch_bounds__(TcrShape<NG, NBUF>::kThreads, 1) k_score_tcr(c
                 ex = ex_n;
                 ey = ey_n;
                 ew = ew_n;
+            };
+            // blocks alternate between the two buffers in the CTA's block order (gb);
+            // the item's first block takes buffer base mod 2
+            using B0 = std::integral_constant<uint32_t, 0>;
+            using B1 = std::integral_constant<uint32_t, 1>;
+            static_assert(NBUF == 2, "the block loop is unrolled over two accumulator buffers");
+            int b = 0;
+            if ((base & 1u) == 0u) {
+                for (; b + 1 < nblk; b += 2) {
+                    do_block(B0{}, b);
+                    do_block(B1{}, b + 1);
+                }
+                if (b < nblk) do_block(B0{}, b);
+            } else {
+                for (; b + 1 < nblk; b += 2) {
+                    do_block(B1{}, b);
+                    do_block(B0{}, b + 1);
+                }
+                if (b < nblk) do_block(B1{}, b);
             }
             // sums over the warp's 32 records per pose: halving exchanges leave pose
             // (lane >> 1) of the group's 16 in lanes 2 (lane >> 1) and 2 (lane >> 1) + 1
@@ -2586,13 +2610,14 @@ static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out)
     return IMLOC_OK;
 }
 
-// CTAs per query in the replay: the largest cluster (8, 6, 4, 2, 1) of which
-// all nq can be resident at once (a query whose cluster waits for another to
-// finish adds a whole replay to the kernel time).  With one CTA per SM, 16
-// clusters of 8 do not fit the GPCs of a 152-SM GB300 (15 do), 23 of 6 do.
+// CTAs per query in the replay: the largest cluster (8 down to 1 CTAs) of
+// which all nq can be resident at once (a query whose cluster waits for
+// another to finish adds a whole replay to the kernel time).  With one CTA per
+// SM, 16 clusters of 8 do not fit the GPCs of a 152-SM GB300 (15 do), 23 of 6
+// do.
 template <typename ACC>
 static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
-    static const int kCl[kReplayClusterChoices] = {8, 6, 4, 2, 1};
+    static const int kCl[kReplayClusterChoices] = {8, 7, 6, 5, 4, 3, 2, 1};
     const int a = sizeof(ACC) == 8 ? 1 : 0;
     for (int i = 0; i < kReplayClusterChoices; ++i) {
         int& occ = ctx->replay_occ[a][i];
