@@ -319,9 +319,7 @@ __global__ void __launch_bounds__(128) k_sample_p3p(const __grid_constant__ Samp
                 }
                 float l1[4];
                 nsol = p3p_solve(y, d.polish ? yd : nullptr, X, sol, l1);
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k < nsol) d.slots[4 * local + k] = sol[k];
+                for (int k = 0; k < nsol; ++k) d.slots[4 * local + k] = sol[k];
             }
         } else if (d.triples) {
             d.triples[3 * local + 0] = -1;
@@ -2629,6 +2627,8 @@ static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
         }
         if (occ >= nq) {
             *cl_out = kCl[i];
+            if (getenv("IMLOC_VERBOSE"))
+                fprintf(stderr, "imloc: replay of %d queries in clusters of %d (%d co-resident)\n", nq, kCl[i], occ);
             return IMLOC_OK;
         }
     }
