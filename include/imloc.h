@@ -48,7 +48,12 @@ typedef struct imloc_ctx imloc_ctx;
 
 /* Create a context on CUDA device `device` with a device workspace of
  * `workspace_bytes` (0 = 512 MiB).  All scratch memory of later calls is
- * carved from this workspace; no later call allocates device memory. */
+ * carved from this workspace; no later call allocates device memory.  The
+ * context also holds 32 MiB of pinned host memory for the small tables a call
+ * uploads, used by four calls in turn: an asynchronous call returns once its
+ * tables are enqueued and waits on the host only for the uploads of the call
+ * four calls back, so the host can enqueue the next calls while the device
+ * still runs the earlier ones (their device work stays ordered). */
 int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes);
 void imloc_destroy(imloc_ctx* ctx);
 const char* imloc_status_str(int status);

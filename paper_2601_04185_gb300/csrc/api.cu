@@ -17,7 +17,8 @@ void record_cuda_error(cudaError_t e, const char* what, const char* file, int li
 int begin_call(imloc_ctx* ctx, cudaStream_t stream) {
     ctx->ws_top = 0;
     ctx->staging_top = 0;
-    IMLOC_CUDA_TRY(cudaEventSynchronize(ctx->staging_free));
+    ctx->staging_slot = static_cast<int>(ctx->call_seq++ % imloc_ctx::kStagingSlots);
+    IMLOC_CUDA_TRY(cudaEventSynchronize(ctx->staging_free[ctx->staging_slot]));
     IMLOC_CUDA_TRY(cudaStreamWaitEvent(stream, ctx->call_done, 0));
     return IMLOC_OK;
 }
@@ -37,15 +38,15 @@ void* ws_alloc(imloc_ctx* ctx, size_t bytes) {
 
 void* staging_alloc(imloc_ctx* ctx, size_t bytes) {
     size_t off = align_up(ctx->staging_top, 256);
-    if (off + bytes > ctx->staging_bytes) return nullptr;
+    if (off + bytes > ctx->staging_slot_bytes) return nullptr;
     ctx->staging_top = off + bytes;
-    return ctx->staging + off;
+    return ctx->staging + static_cast<size_t>(ctx->staging_slot) * ctx->staging_slot_bytes + off;
 }
 
 int upload(imloc_ctx* ctx, void* d_dst, const void* h_staged, size_t bytes, cudaStream_t stream) {
     if (bytes == 0) return IMLOC_OK;
     IMLOC_CUDA_TRY(cudaMemcpyAsync(d_dst, h_staged, bytes, cudaMemcpyHostToDevice, stream));
-    IMLOC_CUDA_TRY(cudaEventRecord(ctx->staging_free, stream));
+    IMLOC_CUDA_TRY(cudaEventRecord(ctx->staging_free[ctx->staging_slot], stream));
     return IMLOC_OK;
 }
 
@@ -131,15 +132,17 @@ int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes) {
     c->device = device;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     c->ws_bytes = workspace_bytes ? workspace_bytes : (size_t(512) << 20);
-    c->staging_bytes = size_t(8) << 20;
+    c->staging_slot_bytes = size_t(8) << 20;
     if (cudaMalloc(&c->ws, c->ws_bytes) != cudaSuccess) {
         delete c;
         return IMLOC_ERR_OOM;
     }
-    if (cudaMallocHost(&c->staging, c->staging_bytes) != cudaSuccess ||
-        cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->staging_free, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&c->call_done, cudaEventDisableTiming) != cudaSuccess) {
+    bool ok = cudaMallocHost(&c->staging, c->staging_slot_bytes * imloc_ctx::kStagingSlots) == cudaSuccess &&
+              cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
+              cudaEventCreateWithFlags(&c->call_done, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < imloc_ctx::kStagingSlots; ++k)
+        ok = ok && cudaEventCreateWithFlags(&c->staging_free[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         imloc_destroy(c);
         return IMLOC_ERR_OOM;
     }
@@ -152,12 +155,14 @@ int imloc_create(imloc_ctx** out, int device, size_t workspace_bytes) {
 void imloc_destroy(imloc_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
-    if (c->staging_free) cudaEventSynchronize(c->staging_free);
+    for (int k = 0; k < imloc_ctx::kStagingSlots; ++k)
+        if (c->staging_free[k]) cudaEventSynchronize(c->staging_free[k]);
     cudaDeviceSynchronize();
     if (c->ws) cudaFree(c->ws);
     if (c->d_err) cudaFree(c->d_err);
     if (c->staging) cudaFreeHost(c->staging);
-    if (c->staging_free) cudaEventDestroy(c->staging_free);
+    for (int k = 0; k < imloc_ctx::kStagingSlots; ++k)
+        if (c->staging_free[k]) cudaEventDestroy(c->staging_free[k]);
     if (c->call_done) cudaEventDestroy(c->call_done);
     for (auto& r : c->prof_pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->prof_pool) cudaEventDestroy(e);

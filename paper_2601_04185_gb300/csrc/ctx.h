@@ -19,10 +19,16 @@ struct imloc_ctx {
     char* ws = nullptr;           // device workspace
     size_t ws_bytes = 0;
     size_t ws_top = 0;            // bump pointer of the current call
-    char* staging = nullptr;      // pinned host memory for descriptor uploads
-    size_t staging_bytes = 0;
-    size_t staging_top = 0;
-    cudaEvent_t staging_free = nullptr;  // recorded after the last upload read the staging buffer
+    // pinned host memory for descriptor uploads: a ring of kStagingSlots slots, one per call in turn, so
+    // that a call waits (host) only for the uploads of the call kStagingSlots calls back, and the host can
+    // enqueue the next calls while the device still runs the previous ones
+    static constexpr int kStagingSlots = 4;
+    char* staging = nullptr;
+    size_t staging_slot_bytes = 0;
+    size_t staging_top = 0;       // bump pointer of the current call within its slot
+    int staging_slot = 0;         // slot of the current call
+    uint64_t call_seq = 0;        // calls begun on this context
+    cudaEvent_t staging_free[kStagingSlots] = {};  // per slot: recorded after the last upload that read it
     cudaEvent_t call_done = nullptr;     // recorded after the last call's work; the next call's stream waits on it
     int* d_err = nullptr;         // sticky device error word
     cudaStream_t last_stream = nullptr;
@@ -49,17 +55,18 @@ struct imloc_ctx {
 
 namespace imloc {
 
-// Start a call on `stream`: reset the bump allocators, wait (host) until the
-// previous upload has consumed the staging buffer, and make `stream` wait for
-// the previous call's device work, which used the same workspace.
+// Start a call on `stream`: reset the bump allocators, take the next staging
+// slot and wait (host) until the uploads of its previous use have read it, and
+// make `stream` wait for the previous call's device work, which used the same
+// workspace.
 int begin_call(imloc_ctx* ctx, cudaStream_t stream);
 // End a call: record the completion event on `stream`.
 int end_call(imloc_ctx* ctx, cudaStream_t stream);
 // Device workspace sub-allocation (256-byte aligned); nullptr when it does not fit.
 void* ws_alloc(imloc_ctx* ctx, size_t bytes);
-// Pinned staging sub-allocation (256-byte aligned); nullptr when it does not fit.
+// Pinned staging sub-allocation in the call's slot (256-byte aligned); nullptr when it does not fit.
 void* staging_alloc(imloc_ctx* ctx, size_t bytes);
-// Copy a staged block to the device on `stream`; records the staging event.
+// Copy a staged block to the device on `stream`; records the slot's staging event.
 int upload(imloc_ctx* ctx, void* d_dst, const void* h_staged, size_t bytes, cudaStream_t stream);
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }

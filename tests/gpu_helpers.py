@@ -39,6 +39,25 @@ def lifted_to_host(out, n=None):
     return g
 
 
+def check_lift(g, ref, views, matches, src_base=0):
+    """Lifted correspondences g (lifted_to_host) against the oracle's lift:
+    kept matches and source indices bit-exact, x, y, w identical, world points
+    within 2e-6 (|X_w| + 2 |C|), C the centre of the point's database camera."""
+    assert g["n"] == len(ref["src"])
+    np.testing.assert_array_equal(g["src"].astype(np.int64) - src_base, ref["src"])
+    np.testing.assert_array_equal(g["x"].astype(np.float64), ref["x"])
+    np.testing.assert_array_equal(g["y"].astype(np.float64), ref["y"])
+    np.testing.assert_array_equal(g["w"].astype(np.float64), ref["w"])
+    if g["n"] == 0:
+        return
+    seg_of = np.searchsorted(np.asarray(matches["seg_off"])[1:], ref["src"], side="right")
+    vid = np.asarray(matches["seg_view"])[seg_of]
+    C = np.stack([-np.asarray(views[v]["R"]).T @ np.asarray(views[v]["t"]) for v in range(len(views))])[vid]
+    err = np.linalg.norm(g["Xw"] - ref["X"], axis=1)
+    bound = 2e-6 * (np.linalg.norm(ref["X"], axis=1) + 2 * np.linalg.norm(C, axis=1))
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 def rot_deg(Ra, Rb):
     """Angle between two rotations from the chord |Ra - Rb|_F = 2 sqrt(2) sin(angle / 2):
     exact for rotations and 0 for identical matrices."""

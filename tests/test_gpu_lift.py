@@ -13,7 +13,7 @@ import pytest
 import oracle
 from paper_2601_04185_gb300 import imloc, synth
 
-from gpu_helpers import lifted_to_host, matches_to_device, torch, views_to_device
+from gpu_helpers import check_lift, lifted_to_host, matches_to_device, torch, views_to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -23,22 +23,6 @@ def ctx():
     c = imloc.Context(0, 1 << 30)
     yield c
     c.close()
-
-
-def check_lift(g, ref, views, matches, src_base=0):
-    assert g["n"] == len(ref["src"])
-    np.testing.assert_array_equal(g["src"].astype(np.int64) - src_base, ref["src"])
-    np.testing.assert_array_equal(g["x"].astype(np.float64), ref["x"])
-    np.testing.assert_array_equal(g["y"].astype(np.float64), ref["y"])
-    np.testing.assert_array_equal(g["w"].astype(np.float64), ref["w"])
-    if g["n"] == 0:
-        return
-    seg_of = np.searchsorted(np.asarray(matches["seg_off"])[1:], ref["src"], side="right")
-    vid = np.asarray(matches["seg_view"])[seg_of]
-    C = np.stack([-np.asarray(views[v]["R"]).T @ np.asarray(views[v]["t"]) for v in range(len(views))])[vid]
-    err = np.linalg.norm(g["Xw"] - ref["X"], axis=1)
-    bound = 2e-6 * (np.linalg.norm(ref["X"], axis=1) + 2 * np.linalg.norm(C, axis=1))
-    assert np.all(err <= bound), float(np.max(err / bound))
 
 
 def test_lift_config2_full_size(ctx):
