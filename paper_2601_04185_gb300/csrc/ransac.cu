@@ -2608,16 +2608,22 @@ static int max_clusters(K kernel, int block, size_t smem, int cluster, int* out)
     return IMLOC_OK;
 }
 
-// CTAs per query in the replay: the largest cluster (8 down to 1 CTAs) of
-// which all nq can be resident at once (a query whose cluster waits for
-// another to finish adds a whole replay to the kernel time).  With one CTA per
-// SM, 16 clusters of 8 do not fit the GPCs of a 152-SM GB300 (15 do), 23 of 6
-// do.
+// CTAs per query in the replay: the largest cluster (8 down to 1 CTAs, at
+// most IMLOC_REPLAY_CLUSTER when set) of which all nq can be resident at once
+// (a query whose cluster waits for another to finish adds a whole replay to
+// the kernel time).  With one CTA per SM, 16 clusters of 8 do not fit the GPCs
+// of a 152-SM GB300 (15 do), 23 of 6 do.
 template <typename ACC>
 static int replay_cluster_size(imloc_ctx* ctx, int nq, int* cl_out) {
     static const int kCl[kReplayClusterChoices] = {8, 7, 6, 5, 4, 3, 2, 1};
+    // IMLOC_REPLAY_CLUSTER=<k>: at most k CTAs per query
+    static const int cap = [] {
+        const char* env = getenv("IMLOC_REPLAY_CLUSTER");
+        return env ? std::min(std::max(atoi(env), 1), 8) : 8;
+    }();
     const int a = sizeof(ACC) == 8 ? 1 : 0;
     for (int i = 0; i < kReplayClusterChoices; ++i) {
+        if (kCl[i] > cap) continue;
         int& occ = ctx->replay_occ[a][i];
         if (occ == 0) {
             int v = 0;
