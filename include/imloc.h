@@ -111,20 +111,21 @@ typedef struct { double R[9]; double t[3]; } imloc_pose;                        
 #define IMLOC_DEPTH_F32  0  /* float32 metres; <= 0 or non-finite = no depth */
 #define IMLOC_DEPTH_LOG8 1  /* 8-bit log codes of imloc_depth_encode_log8_async */
 #define IMLOC_DEPTH_F32_TILE4 2  /* float32 metres in 4x4 blocks (imloc_depth_tile4_async) */
+#define IMLOC_DEPTH_F32_HALO 3   /* float32 metres in overlapping 8x4 blocks (imloc_depth_halo_async) */
 
 /* One database view of the image-based map (ImLoc Sec. 3.1): a depth map
  * with its intrinsics and pose.  `depth` is a device pointer to height x
  * width values of `depth_format` (float32, or one byte per pixel for
  * IMLOC_DEPTH_LOG8), row stride `pitch` elements; for IMLOC_DEPTH_F32_TILE4
- * the blocked layout of imloc_depth_tile4_async, `pitch` = its tile-row
- * stride. */
+ * and IMLOC_DEPTH_F32_HALO the blocked layouts of imloc_depth_tile4_async and
+ * imloc_depth_halo_async, `pitch` = their block-row stride. */
 typedef struct {
     const void* depth;
     int32_t width, height;
     int64_t pitch;
     imloc_camera cam;
     imloc_pose pose;
-    int32_t depth_format;  /* IMLOC_DEPTH_F32 or IMLOC_DEPTH_LOG8 */
+    int32_t depth_format;  /* IMLOC_DEPTH_F32, _LOG8, _F32_TILE4 or _F32_HALO */
     int32_t reserved;      /* 0 */
 } imloc_view;
 
@@ -167,6 +168,28 @@ int imloc_depth_decode_log8_async(const uint8_t* codes, int32_t width, int32_t h
  * below 1, pitch < width or a bad tiled_pitch. */
 int imloc_depth_tile4_async(const float* depth, int32_t width, int32_t height, int64_t pitch, float* tiled,
                             int64_t tiled_pitch, void* stream);
+
+/* ---- overlapping-block float32 depth layout (a storage layout of the map
+ * store, not a step of the paper) ---------------------------------------
+ * A random depth tap costs the lift a whole 128-byte line of DRAM, so the
+ * fewest bytes per match come from every 2x2 bilinear footprint lying in one
+ * line.  Blocks of 8x4 pixels (128 bytes) placed every 7 columns and every 3
+ * rows overlap by one column and one row, so the footprint with top-left
+ * pixel (i, j) lies in block (i / 7, j / 3), and a single lookup at pixel
+ * (x, y) reads block (x / 7, y / 3): one line per match, for 32 / 21 = 1.52
+ * times the storage of the row-major map.  Block (bx, by) holds pixels
+ * x in [7 bx, 7 bx + 8), y in [3 by, 3 by + 4) in row-major order: pixel
+ * (7 bx + lx, 3 by + ly) is element by * halo_pitch + bx * 32 + ly * 8 + lx;
+ * halo_pitch: elements per block row, a multiple of 32 and
+ * >= 32 * ((width - 1) / 7 + 1); the buffer holds ((height - 1) / 3 + 1) *
+ * halo_pitch floats; pixels beyond width / height are written as 0 (no
+ * depth).  Written once when a view enters the map store; views with
+ * depth_format = IMLOC_DEPTH_F32_HALO and pitch = halo_pitch are lifted with
+ * the same values as the row-major map.  Device pointers, asynchronous on
+ * `stream`, no allocation, no context; IMLOC_ERR_INVALID_ARG on null
+ * pointers, sizes below 1, pitch < width or a bad halo_pitch. */
+int imloc_depth_halo_async(const float* depth, int32_t width, int32_t height, int64_t pitch, float* halo,
+                           int64_t halo_pitch, void* stream);
 
 /* ---- dense triangulation of a mapping depth map (ImLoc Sec. 3.3 "Depth
  * Estimation by Dense Matching") ------------------------------------------

@@ -9,6 +9,10 @@
 // a rounded logarithm: codes do not depend on a transcendental function's
 // last bits.  The decode table (code -> float32 metres, FP64 values rounded
 // to nearest) is the one the lift kernel reads its taps through.
+//
+// Also the two blocked float32 layouts of the map store that the lift
+// addresses: 4x4-pixel blocks (imloc_depth_tile4_async) and overlapping
+// 8x4-pixel blocks every 7 x 3 pixels (imloc_depth_halo_async).
 #include <math.h>
 #include <string.h>
 
@@ -177,6 +181,38 @@ extern "C" int imloc_depth_tile4_async(const float* depth, int32_t width, int32_
     const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
     imloc::k_depth_tile4<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         depth, pitch, width, height, tiled, tiled_pitch, total);
+    IMLOC_CUDA_TRY(cudaGetLastError());
+    return IMLOC_OK;
+}
+
+// ---- overlapping-block float32 layout (8x4-pixel blocks every 7 x 3 pixels) --
+namespace imloc {
+namespace {
+// one thread per output element: consecutive threads write consecutive
+// elements of a block row; each group of 8 reads 8 consecutive pixels
+__global__ void __launch_bounds__(256) k_depth_halo(const float* __restrict__ depth, int64_t pitch, int32_t W,
+                                                    int32_t H, float* __restrict__ halo, int64_t halo_pitch,
+                                                    int64_t total) {
+    for (int64_t o = static_cast<int64_t>(blockIdx.x) * 256 + threadIdx.x; o < total;
+         o += static_cast<int64_t>(gridDim.x) * 256) {
+        const int64_t by = o / halo_pitch, r = o - by * halo_pitch;
+        const int64_t bx = r >> 5, k = r & 31;
+        const int64_t y = 3 * by + (k >> 3), x = 7 * bx + (k & 7);
+        halo[o] = (x < W && y < H) ? __ldg(depth + y * pitch + x) : 0.0f;
+    }
+}
+}  // namespace
+}  // namespace imloc
+
+extern "C" int imloc_depth_halo_async(const float* depth, int32_t width, int32_t height, int64_t pitch, float* halo,
+                                      int64_t halo_pitch, void* stream) {
+    if (!depth || !halo || width < 1 || height < 1 || pitch < width) return IMLOC_ERR_INVALID_ARG;
+    if (halo_pitch % 32 != 0 || halo_pitch < 32 * ((static_cast<int64_t>(width) - 1) / 7 + 1))
+        return IMLOC_ERR_INVALID_ARG;
+    const int64_t total = ((static_cast<int64_t>(height) - 1) / 3 + 1) * halo_pitch;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    imloc::k_depth_halo<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        depth, pitch, width, height, halo, halo_pitch, total);
     IMLOC_CUDA_TRY(cudaGetLastError());
     return IMLOC_OK;
 }

@@ -12,8 +12,9 @@
 //
 // HBM-bound: per match 20 B of match data, the depth taps (two 32-B sectors
 // for a bilinear fetch) and 28 B of output.  Float32 maps may also be stored
-// in 4x4-pixel blocks of 64 bytes (one DRAM atom), so that most bilinear
-// footprints fall in one atom.  Views stored as 8-bit log codes
+// in 4x4-pixel blocks of 64 bytes, so that most bilinear footprints fall in
+// one 128-byte line, or in overlapping 8x4-pixel blocks of 128 bytes, so
+// that every footprint does.  Views stored as 8-bit log codes
 // (the depth codec of Sec. 3.3 "Data Compression") are decoded in the fetch
 // through a 256-entry table in shared memory: one byte per tap and a map
 // store a quarter of the float32 size (which then mostly stays in L2).
@@ -33,7 +34,7 @@ struct __align__(16) LiftView {
     const void* depth;    // float32 metres or uint8 log codes (fmt)
     int64_t pitch;
     int32_t W, H;
-    int32_t fmt;          // IMLOC_DEPTH_F32 / IMLOC_DEPTH_LOG8
+    int32_t fmt;          // IMLOC_DEPTH_F32 / _LOG8 / _F32_TILE4 / _F32_HALO
     int32_t pad;
     float ifx, ify, cx, cy;
     float Rt[9];  // R^T, row-major
@@ -79,10 +80,19 @@ struct LiftParams {
 __device__ __forceinline__ bool depth_ok(float d) { return d > 0.0f && d < INFINITY; }
 
 // element offset of pixel (x, y) in the view's map: row-major, or 4x4 blocks
+// (the overlapping 8x4 blocks are addressed through halo_offset)
 __device__ __forceinline__ int64_t tap_offset(const LiftView& V, int x, int y) {
     if (V.fmt == IMLOC_DEPTH_F32_TILE4)
         return static_cast<int64_t>(y >> 2) * V.pitch + ((x >> 2) << 4) + ((y & 3) << 2) + (x & 3);
     return static_cast<int64_t>(y) * V.pitch + x;
+}
+
+// element offset of pixel (x, y) in the overlapping-block layout, read from
+// block (x / 7, y / 3): pixels (x + 1, y), (x, y + 1) and (x + 1, y + 1) of
+// the same footprint lie in that block at +1, +8 and +9
+__device__ __forceinline__ int64_t halo_offset(const LiftView& V, int x, int y) {
+    const int bx = x / 7, by = y / 3;
+    return static_cast<int64_t>(by) * V.pitch + bx * 32 + (y - 3 * by) * 8 + (x - 7 * bx);
 }
 
 // depth tap at element offset `off` of the view's map (metres; 0 = no depth for codes)
@@ -181,14 +191,24 @@ __global__ void __launch_bounds__(kLiftThreads, 4) k_lift(const __grid_constant_
             if (!((a >= 0.0f) && (a < static_cast<float>(V.W - 1)) && (b >= 0.0f) && (b < static_cast<float>(V.H - 1))))
                 continue;
             const int i0 = static_cast<int>(a), j0 = static_cast<int>(b);
-            t00[k] = depth_tap(V, tap_offset(V, i0, j0), s_lut);
-            t01[k] = depth_tap(V, tap_offset(V, i0 + 1, j0), s_lut);
-            t10[k] = depth_tap(V, tap_offset(V, i0, j0 + 1), s_lut);
-            t11[k] = depth_tap(V, tap_offset(V, i0 + 1, j0 + 1), s_lut);
+            if (V.fmt == IMLOC_DEPTH_F32_HALO) {
+                const float* h = static_cast<const float*>(V.depth) + halo_offset(V, i0, j0);
+                t00[k] = __ldg(h);
+                t01[k] = __ldg(h + 1);
+                t10[k] = __ldg(h + 8);
+                t11[k] = __ldg(h + 9);
+            } else {
+                t00[k] = depth_tap(V, tap_offset(V, i0, j0), s_lut);
+                t01[k] = depth_tap(V, tap_offset(V, i0 + 1, j0), s_lut);
+                t10[k] = depth_tap(V, tap_offset(V, i0, j0 + 1), s_lut);
+                t11[k] = depth_tap(V, tap_offset(V, i0 + 1, j0 + 1), s_lut);
+            }
         } else {
             if (!((u >= 0.0f) && (u < static_cast<float>(V.W)) && (v >= 0.0f) && (v < static_cast<float>(V.H))))
                 continue;
-            t00[k] = depth_tap(V, tap_offset(V, static_cast<int>(u), static_cast<int>(v)), s_lut);
+            const int x = static_cast<int>(u), y = static_cast<int>(v);
+            t00[k] = V.fmt == IMLOC_DEPTH_F32_HALO ? __ldg(static_cast<const float*>(V.depth) + halo_offset(V, x, y))
+                                                   : depth_tap(V, tap_offset(V, x, y), s_lut);
         }
         want[k] = true;
     }
@@ -342,9 +362,11 @@ static int check_lift_args(const imloc_view* views, int32_t n_views, const imloc
         if (!V.depth || V.width < 2 || V.height < 2 || V.pitch < V.width) return IMLOC_ERR_INVALID_ARG;
         if (!(V.cam.fx != 0.0f) || !(V.cam.fy != 0.0f)) return IMLOC_ERR_INVALID_ARG;
         if (V.depth_format != IMLOC_DEPTH_F32 && V.depth_format != IMLOC_DEPTH_LOG8 &&
-            V.depth_format != IMLOC_DEPTH_F32_TILE4)
+            V.depth_format != IMLOC_DEPTH_F32_TILE4 && V.depth_format != IMLOC_DEPTH_F32_HALO)
             return IMLOC_ERR_INVALID_ARG;
         if (V.depth_format == IMLOC_DEPTH_F32_TILE4 && (V.pitch % 16 != 0 || V.pitch < 16 * ((V.width + 3) / 4)))
+            return IMLOC_ERR_INVALID_ARG;
+        if (V.depth_format == IMLOC_DEPTH_F32_HALO && (V.pitch % 32 != 0 || V.pitch < 32 * ((V.width - 1) / 7 + 1)))
             return IMLOC_ERR_INVALID_ARG;
     }
     return IMLOC_OK;

@@ -30,7 +30,7 @@ class Pose(C.Structure):
     _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
 
 
-DEPTH_F32, DEPTH_LOG8, DEPTH_F32_TILE4 = 0, 1, 2
+DEPTH_F32, DEPTH_LOG8, DEPTH_F32_TILE4, DEPTH_F32_HALO = 0, 1, 2, 3
 
 
 class View(C.Structure):
@@ -123,7 +123,7 @@ EXPORTS = ["imloc_create", "imloc_destroy", "imloc_status_str", "imloc_last_cuda
            "imloc_depth_encode_log8_async", "imloc_depth_decode_log8_async", "imloc_triangulate_default_opts",
            "imloc_triangulate_depth_async", "imloc_retrieve_topk_async", "imloc_ransac_rig_batch",
            "imloc_testing_rig", "imloc_testing_lift_stalled", "imloc_serve_submit_device",
-           "imloc_depth_tile4_async"]
+           "imloc_depth_tile4_async", "imloc_depth_halo_async"]
 
 _lib = None
 
@@ -177,6 +177,7 @@ def load(path: str = LIB_PATH):
     L.imloc_depth_encode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     L.imloc_depth_decode_log8_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     L.imloc_depth_tile4_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
+    L.imloc_depth_halo_async.argtypes = [V, C.c_int32, C.c_int32, C.c_int64, V, C.c_int64, V]
     _lib = L
     return L
 
@@ -264,10 +265,10 @@ def _views_struct(views):
         d = v["depth"]
         arr[i].depth = d.data_ptr()
         arr[i].pitch = int(d.stride(0))
-        if v.get("layout") == "tile4":
-            # 4x4-blocked float32 map (depth_tile4): rows of blocks, the image size given with the view
+        if v.get("layout") in ("tile4", "halo"):
+            # blocked float32 map (depth_tile4 / depth_halo): rows of blocks, the image size given with the view
             H, W = int(v["height"]), int(v["width"])
-            arr[i].depth_format = DEPTH_F32_TILE4
+            arr[i].depth_format = DEPTH_F32_TILE4 if v["layout"] == "tile4" else DEPTH_F32_HALO
         else:
             H, W = int(d.shape[0]), int(d.shape[1])
             # uint8 maps hold 8-bit log codes (depth_encode_log8), float32 maps metres
@@ -608,6 +609,29 @@ def tile4_view(v):
     d = dict(v)
     H, W = v["depth"].shape
     d.update(depth=depth_tile4(v["depth"]), layout="tile4", width=W, height=H)
+    return d
+
+
+def depth_halo(depth, stream=None):
+    """float32 CUDA tensor HxW -> the overlapping-block layout (imloc_depth_halo_async): a float32 CUDA tensor
+    of (H-1)//3+1 block rows x 32 ((W-1)//7+1) elements.  Use it as a view's depth with layout="halo" and the
+    view's width and height."""
+    import torch
+
+    assert depth.dtype == torch.float32 and depth.dim() == 2 and depth.is_cuda and depth.stride(1) == 1
+    H, W = depth.shape
+    out = torch.empty(((H - 1) // 3 + 1, 32 * ((W - 1) // 7 + 1)), dtype=torch.float32, device=depth.device)
+    _check(load().imloc_depth_halo_async(C.c_void_p(depth.data_ptr()), W, H, depth.stride(0),
+                                         C.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
+           "imloc_depth_halo_async")
+    return out
+
+
+def halo_view(v):
+    """A view dict with its float32 depth map re-laid out in overlapping 8x4 blocks."""
+    d = dict(v)
+    H, W = v["depth"].shape
+    d.update(depth=depth_halo(v["depth"]), layout="halo", width=W, height=H)
     return d
 
 
