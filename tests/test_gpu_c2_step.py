@@ -9,8 +9,9 @@ runs on the tensor-core kernel, as in the benchmark.
 
 Checked: every query's lifted correspondences against the oracle's lift
 (source indices bit-exact, positions to the lift bar), the three calls'
-results identical, every final pose near its ground truth, and three
-sampled queries' final poses within 0.05 deg / 5 mm of the oracle's
+results identical, the same results from two contexts with calls in
+flight on two streams at once, every final pose near its ground truth, and
+three sampled queries' final poses within 0.05 deg / 5 mm of the oracle's
 LO-RANSAC run on the oracle's own lift.
 """
 import concurrent.futures as cf
@@ -118,9 +119,30 @@ def _run_gpu(queries):
         stream.synchronize()
         kernels = sorted(ctx.profile_read(reset=True))
         ctx.profile(False)
+        # two batches in flight, as the benchmark times them: a second context
+        # with its own buffers and stream, calls alternating between the two
+        ctx2 = imloc.Context(0, (256 << 20) + nq * (64 << 20))
+        try:
+            lanes = [(ctx, corr, offsets, stream), (ctx2, imloc.alloc_corr(int(qb[-1])),
+                                                    t.zeros(nq + 1, dtype=t.int64, device="cuda"), t.cuda.Stream())]
+            outs = [t.zeros(nq * imloc.RESULT_BYTES, dtype=t.uint8, device="cuda") for _ in range(4)]
+            start = t.cuda.Event()
+            start.record(t.cuda.current_stream())
+            for c, cr, of, st in lanes:
+                st.wait_event(start)
+            for i in range(4):
+                c, cr, of, st = lanes[i % 2]
+                with t.cuda.stream(st):
+                    c.lift_batch(qb, d_views, d_match, out=cr, offsets=of, stream=st, prepared=prep_lift)
+                    c.ransac_pnp_batch_async(cr, of, Ks, opts, outs[i], stream=st, prepared=prep_ransac)
+            t.cuda.synchronize()
+            in_flight = [imloc.results_from_bytes(o.cpu().numpy(), nq) for o in outs]
+            err2 = ctx2.device_error()
+        finally:
+            ctx2.close()
     finally:
         ctx.close()
-    return dict(qb=qb, offs=offs, corr=host, calls=calls, err=err, kernels=kernels)
+    return dict(qb=qb, offs=offs, corr=host, calls=calls, err=err, kernels=kernels, in_flight=in_flight, err2=err2)
 
 
 def test_lift_of_every_query_against_the_oracle(step):
@@ -162,3 +184,18 @@ def test_sampled_queries_against_the_oracle(step):
     for i, (R, t, status) in refs.items():
         assert status == 0
         assert pose_close(res[i]["R"], res[i]["t"], R, t), i
+
+
+def test_two_batches_in_flight_give_the_same_results(step):
+    """Two contexts with calls in flight on two streams at once (the
+    benchmark's timed form): every call's results equal the single-context
+    call's, bit for bit."""
+    _, gpu, _ = step
+    first = gpu["calls"][0]
+    for res in gpu["in_flight"]:
+        for a, b in zip(first, res):
+            assert b["status"] == 0
+            np.testing.assert_array_equal(a["R"], b["R"])
+            np.testing.assert_array_equal(a["t"], b["t"])
+            assert a["num_inliers"] == b["num_inliers"] and a["lo_count"] == b["lo_count"]
+    assert gpu["err2"] == 0
