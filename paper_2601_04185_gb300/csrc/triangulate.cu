@@ -45,34 +45,61 @@ __device__ __forceinline__ void cross(const float a[3], const float b[3], float 
 }
 __device__ __forceinline__ float dot(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
-// angle between a and d and the error vector's Jacobian along z (da/dz = q):
-// the error vector r = theta / rho (p1, p2) with p = (a.e1, a.e2, a.d^),
-// rho = |(p1, p2)|; returns theta, writes r and dr/dz
-__device__ __forceinline__ float angle_residual(const float a[3], const float q[3], const float dh[3], const float e1[3],
-                                                const float e2[3], float r[2], float J[2]) {
+// atan(x) / x and (d/dx (atan(x) / x)) / x for x^2 = x2 <= 0.04, by their
+// Taylor series about 0 (alternating; the first omitted terms, x^12 / 13
+// and 12 x^10 / 13, are below 3e-10 and 1e-7 of the sums at x = 0.2)
+__device__ __forceinline__ float atan_over_x(float x2) {
+    return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -1.0f / 11.0f, 1.0f / 9.0f), -1.0f / 7.0f), 0.2f),
+                         -1.0f / 3.0f), 1.0f);
+}
+__device__ __forceinline__ float datan_over_x_dx_over_x(float x2) {
+    return fmaf(x2, fmaf(x2, fmaf(x2, fmaf(x2, -10.0f / 11.0f, 8.0f / 9.0f), -6.0f / 7.0f), 0.8f), -2.0f / 3.0f);
+}
+
+// angle between a and d: atan2(|a x d^|, a.d^) (rho = |a x d^|, p3 = a.d^),
+// by the series when the angle is below atan(0.2) = 11.3 degrees
+__device__ __forceinline__ float ray_angle(float rho, float p3) {
+    if (p3 > 0.0f && rho <= 0.2f * p3) {
+        const float x = __fdividef(rho, p3);  // 2-ulp division: well below the angle's use as a cost
+        return x * atan_over_x(x * x);
+    }
+    return atan2f(rho, p3);
+}
+
+// the error vector's value and Jacobian along z (da/dz = q): the error vector
+// r = theta / rho (p1, p2) with p = (a.e1, a.e2, a.d^), rho = |(p1, p2)|,
+// theta = atan2(rho, p3); writes r and dr/dz (zero when a points exactly
+// away from d^, where no error vector is defined)
+__device__ __forceinline__ void angle_residual(const float a[3], const float q[3], const float dh[3], const float e1[3],
+                                               const float e2[3], float r[2], float J[2]) {
     const float p1 = dot(a, e1), p2 = dot(a, e2), p3 = dot(a, dh);
     const float q1 = dot(q, e1), q2 = dot(q, e2), q3 = dot(q, dh);
-    const float rho = sqrtf(p1 * p1 + p2 * p2);
-    const float th = atan2f(rho, p3);
-    const float den = rho * rho + p3 * p3;
-    float f, f_rho;
-    if (rho > 1e-2f * fabsf(p3)) {
+    const float rho2 = p1 * p1 + p2 * p2;
+    const float rho = sqrtf(rho2);
+    float f, f_rho, f_p3;
+    if (p3 > 0.0f && rho <= 0.2f * p3) {
+        // f = atan(x) / (x p3) with x = rho / p3: series in x^2
+        // (2-ulp divisions: the Jacobian steers the iteration, the cost test decides it)
+        const float ip3 = __fdividef(1.0f, p3);
+        const float x2 = rho2 * (ip3 * ip3);
+        f = atan_over_x(x2) * ip3;
+        f_rho = rho * datan_over_x_dx_over_x(x2) * (ip3 * ip3 * ip3);
+        f_p3 = -__fdividef(ip3 * ip3, 1.0f + x2);
+    } else if (rho > 0.0f) {
+        const float th = atan2f(rho, p3);
+        const float den = rho2 + p3 * p3;
         f = th / rho;
-        f_rho = (rho * p3 / den - th) / (rho * rho);
+        f_rho = (rho * p3 / den - th) / rho2;
+        f_p3 = -1.0f / den;
     } else {
-        // series of atan(x)/x about x = rho / p3 -> 0
-        const float x2 = (rho * rho) / (p3 * p3);
-        f = (1.0f - x2 * (1.0f / 3.0f) + x2 * x2 * 0.2f) / p3;
-        f_rho = -(2.0f / 3.0f) * rho / (p3 * p3 * p3) * (1.0f - 1.2f * x2);
+        f = f_rho = f_p3 = 0.0f;
     }
-    const float f_p3 = -1.0f / den;
-    const float drho = rho > 0.0f ? (p1 * q1 + p2 * q2) / rho : 0.0f;
+    const float drho = rho > 0.0f ? __fdividef(p1 * q1 + p2 * q2, rho) : 0.0f;
     const float df = f_rho * drho + f_p3 * q3;
     r[0] = f * p1;
     r[1] = f * p2;
     J[0] = df * p1 + f * q1;
     J[1] = df * p2 + f * q2;
-    return th;
 }
 
 // The rays of pixel px: its own (d0) and one per source match (ds), the
@@ -193,15 +220,18 @@ __global__ void __launch_bounds__(256, MAXS <= 8 ? 3 : 1) k_triangulate(const __
         e1[k][0] *= i1; e1[k][1] *= i1; e1[k][2] *= i1;
         cross(dh[k], e1[k], e2[k]);
     }
+    // weighted sum of squared angles over the winner's inliers (sources of
+    // weight 0 add nothing and are skipped)
     auto cost = [&](float zz) {
         float e = 0.f;
 #pragma unroll
         for (int k = 0; k < MAXS; ++k) {
+            if (!(wk[k] > 0.f)) continue;
             float a[3], c[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) a[r] = fmaf(zz, d0[r], p.W0[k][r]);
             cross(a, dh[k], c);
-            const float th = atan2f(sqrtf(dot(c, c)), dot(a, dh[k]));
+            const float th = ray_angle(sqrtf(dot(c, c)), dot(a, dh[k]));
             e = fmaf(wk[k] * th, th, e);
         }
         return e;
@@ -212,6 +242,7 @@ __global__ void __launch_bounds__(256, MAXS <= 8 ? 3 : 1) k_triangulate(const __
         float g = 0.f, h = 0.f;
 #pragma unroll
         for (int k = 0; k < MAXS; ++k) {
+            if (!(wk[k] > 0.f)) continue;
             float a[3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) a[r] = fmaf(z, d0[r], p.W0[k][r]);
