@@ -63,10 +63,11 @@ FP32_LANES_PER_SM = 128
 SCORE_TRAFFIC_PER_LAUNCH = {(64, 4): 25.754e6 + 0.0}
 # the same for the tensor-core scoring kernel (k_score_tcr: records on the MMA's
 # M side, 80-pose items) on that step (profiles/k_score_tcr_c2_16queries.md)
-SCORE_TC_TRAFFIC_PER_LAUNCH = 45.247e6 + 0.113e6
+SCORE_TC_TRAFFIC_PER_LAUNCH = 45.270e6 + 0.118e6
 # DRAM bytes (read + write) per lifted match from the committed ncu capture of
-# k_lift on the batched 9.48M-match shape (profiles/k_lift_batched_9.5M.md)
-LIFT_TRAFFIC_PER_MATCH = (1.229412e9 + 0.234057e9) / 9.48e6
+# k_lift (row-major float32 maps) on the batched 9.48M-match shape against the
+# 1,024-view store that roofline_lift measures (profiles/k_lift_batched_9.5M_1024views.md)
+LIFT_TRAFFIC_PER_MATCH = (1.713e9 + 0.2555e9) / 9.48e6
 
 
 # ---------------------------------------------------------------------------
