@@ -1440,8 +1440,8 @@ def run_ours(args):
                          "launch_ms": lift_ms, "note": "16-query step: 800k matches, latency-bound"},
         "kernels_ms_per_step": {k: v / args.steps for k, v in kms.items()},
         "kernel_timing": "per-kernel CUDA events on the launching stream over a second pass of the same K steps "
-                         "(L2 flushed the same way); tracing switches the library's CUDA-graph replay off, so the "
-                         "headline steps run untraced",
+                         "on one lane, the L2 flushed before each step; tracing switches the library's CUDA-graph "
+                         "replay off, so the headline steps run untraced",
         "gpu_launches": int(sum(launches.values())),
         "clocks": clocks,
         "result_status": statuses,
