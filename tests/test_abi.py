@@ -78,6 +78,26 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert lib.imloc_testing_rig(None, None, None, None, None, None, None, None, None) == -1
     assert lib.imloc_testing_lift_stalled(None, None, 0, None, None, 1, 32, None) == -1
     assert lib.imloc_lift_noalloc_async(None, 0, None, None, None) == -1
+    assert lib.imloc_depth_tile4_async(None, 4, 4, 4, None, 16, None) == -1
+    assert lib.imloc_depth_halo_async(None, 4, 4, 4, None, 32, None) == -1
+
+
+def test_blocked_layout_pitches_are_checked_on_the_host(lib):
+    """The re-layout calls check their block-row pitch before any device
+    work (the pointers are never dereferenced on these paths): 4x4 blocks need
+    a multiple of 16 elements >= 16 ceil(W / 4); overlapping 8x4 blocks a
+    multiple of 32 >= 32 ((W - 1) // 7 + 1), for W = 10 two blocks (64)."""
+    fake = C.c_void_p(0x1000)
+    assert lib.imloc_depth_tile4_async(fake, 10, 8, 10, fake, 40, None) == -1
+    assert lib.imloc_depth_tile4_async(fake, 10, 8, 10, fake, 36, None) == -1
+    assert lib.imloc_depth_tile4_async(fake, 10, 8, 9, fake, 48, None) == -1
+    assert lib.imloc_depth_halo_async(fake, 10, 8, 10, fake, 48, None) == -1
+    assert lib.imloc_depth_halo_async(fake, 10, 8, 10, fake, 32, None) == -1
+    assert lib.imloc_depth_halo_async(fake, 10, 8, 9, fake, 64, None) == -1
+    assert lib.imloc_depth_halo_async(fake, 0, 8, 10, fake, 64, None) == -1
+    assert lib.imloc_depth_halo_async(fake, 10, 0, 10, fake, 64, None) == -1
+    # 1024 columns: (1023 // 7 + 1) = 147 blocks of 32 elements
+    assert lib.imloc_depth_halo_async(fake, 1024, 768, 1024, fake, 32 * 146, None) == -1
 
 
 def test_triangulation_defaults_are_the_papers_constants(lib):
