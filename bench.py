@@ -64,10 +64,14 @@ SCORE_TRAFFIC_PER_LAUNCH = {(64, 4): 25.754e6 + 0.0}
 # the same for the tensor-core scoring kernel (k_score_tcr: records on the MMA's
 # M side, 80-pose items) on that step (profiles/k_score_tcr_c2_16queries.md)
 SCORE_TC_TRAFFIC_PER_LAUNCH = 45.270e6 + 0.118e6
-# DRAM bytes (read + write) per lifted match from the committed ncu capture of
-# k_lift (row-major float32 maps) on the batched 9.48M-match shape against the
-# 1,024-view store that roofline_lift measures (profiles/k_lift_batched_9.5M_1024views.md)
-LIFT_TRAFFIC_PER_MATCH = (1.713e9 + 0.2555e9) / 9.48e6
+# DRAM bytes (read + write) per lifted match from the committed ncu captures of
+# k_lift on the batched 9.48M-match shape against the 1,024-view store
+# (profiles/k_lift_batched_9.5M_1024views.md).  The row-major capture
+# (207.6 B per match) predates the kernel's overlapping-block branch, so the
+# row-major entry reports no traffic; the overlapping-block capture is of the
+# current kernel.
+LIFT_TRAFFIC_PER_MATCH = None
+LIFT_HALO_TRAFFIC_PER_MATCH = (1.277477e9 + 0.244294e9) / 9.48e6
 
 
 # ---------------------------------------------------------------------------
@@ -1485,6 +1489,8 @@ def run_ours(args):
         line["roofline_lift"] = {"bound": "hbm", "achieved": lb["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                                  "frac": lb["achieved_gbs"] / hbm_peak, "traffic": LIFT_TRAFFIC_PER_MATCH and
                                  LIFT_TRAFFIC_PER_MATCH * lb["matches_per_launch"],
+                                 "traffic_note": "null: the committed row-major capture (207.6 B per match) predates "
+                                                 "the kernel's overlapping-block branch; see lift_halo",
                                  "kernel": "k_lift", "peak_basis": "MEASURED_PEAKS.json hbm_gbs (measured)", **lb}
         lbt = run_lift_batched(dev, dv, sq, tile4=True)
         line["lift_tile4"] = {"bound": "hbm", "achieved": lbt["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
@@ -1497,6 +1503,7 @@ def run_ours(args):
         lbh = run_lift_batched(dev, dv, sq, halo=True)
         line["lift_halo"] = {"bound": "hbm", "achieved": lbh["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
                              "frac": lbh["achieved_gbs"] / hbm_peak, "launch_ms": lbh["launch_ms"],
+                             "traffic": LIFT_HALO_TRAFFIC_PER_MATCH * lbh["matches_per_launch"],
                              "speedup_vs_f32": lb["launch_ms"] / lbh["launch_ms"], "valid": lbh["valid"],
                              "bytes_per_launch": lbh["bytes_per_launch"], "map_store_bytes": lbh["map_store_bytes"],
                              "note": "same matches and algorithmic bytes as roofline_lift, the float32 store maps "
